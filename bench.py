@@ -1,0 +1,310 @@
+"""Benchmark: reverse k-ranks on the |U| = 1M, |P| = 100k, d = 200 workload.
+
+One step is one pass of the whole path over one batch of 10,000 queries:
+pre-processing (norms, sort, buckets, samples, f_min/f_max, rank table, level
+tables, exact count table) followed by the c-approximate query batch
+(Section 4.3, c = 2) and the exact query batch (Def. 2) of the same queries.
+The metric is queries per second of that pass; the index build is part of it.
+
+Inputs are resident in HBM when the timed region starts and are larger than
+L2 (U alone is 800 MB).  Device time is measured with CUDA events on the
+stream the library runs on.  ``e2e`` repeats the step through the C ABI with
+host buffers, host-device copies included.  ``cpu_baseline`` times the FP64
+oracle on a bounded sample of users and queries and scales it to the workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "approx"
+C = 2.0
+
+
+def _load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("RKR_BENCH_GLOO") is None else "gloo")
+        return dist, rank, ws
+    return None, 0, 1
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs():
+    w = synth.make_workload(WORKLOAD)
+    sizes = np.array([w.m // w.omega + (1 if l < w.m % w.omega else 0) for l in range(w.omega)])
+    pos = synth.sample_positions(w.seed, sizes, w.s)
+    return w, pos
+
+
+def run_step(rkr, U, P, Q, k, pos, w, device=True):
+    idx = rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s, fbounds="exact", exact_table=True,
+                    sample_pos=pos)
+    a = idx.query_approx(Q, k, C, device=device)
+    e = idx.query_exact(Q, k, device=device)
+    t = idx.timings()
+    idx.close()
+    return a, e, t
+
+
+def bench_ours(args):
+    import torch
+    import paper_2504_13446_gb300 as rkr
+
+    dist, rank, ws = _dist()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    peaks, peak_src = _load_peaks()
+    w, pos = make_inputs()
+    U = torch.from_numpy(w.U).cuda()
+    P = torch.from_numpy(w.P).cuda()
+    Q = torch.from_numpy(w.Q).cuda()
+    k = torch.from_numpy(w.k.astype(np.int32)).cuda()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        run_step(rkr, U, P, Q, k, pos, w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    launches0 = rkr.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage = []
+    qstats = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a, e, t = run_step(rkr, U, P, Q, k, pos, w)
+        stage.append(t)
+        qstats.append((a["stats"].as_dict(), e[3].as_dict()))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = rkr.kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # end to end through the C ABI with host buffers
+    t0 = time.perf_counter()
+    a_h, e_h, _ = run_step(rkr, w.U, w.P, w.Q, w.k.astype(np.int32), pos, w, device=False)
+    e2e_s = time.perf_counter() - t0
+    h2d = w.U.nbytes + w.P.nbytes + w.Q.nbytes + 4 * w.Q.shape[0] + pos.nbytes
+    d2h = sum(v.nbytes for kk, v in a_h.items() if isinstance(v, np.ndarray) and kk != "offsets")
+    d2h += e_h[0].nbytes + e_h[1].nbytes
+
+    if rank != 0:
+        return
+    nq = w.Q.shape[0]
+    value = ws * nq / (ms / 1000.0)
+    # dominant kernel: the longest build stage or query phase
+    mean = lambda key: float(np.mean([s[key] for s in stage]))  # noqa: E731
+    fl = 2.0 * w.n * w.m * w.d
+    phases = {
+        "k_exact_table": (mean("exact_table"), fl),
+        "k_fbounds": (mean("fbounds"), fl),
+        "k_rank_table": (mean("table"), 2.0 * w.n * (w.omega * w.s) * w.d),
+        "k_theta(approx)": (float(np.mean([qa["ms_theta"] for qa, _ in qstats])),
+                            2 * 2.0 * w.n * nq * w.d),
+    }
+    name = max(phases, key=lambda kk: phases[kk][0])
+    t_ms, flops = phases[name]
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (t_ms / 1000.0) / 1e12
+    qa0, qe0 = qstats[-1]
+    cpu = cpu_baseline(w, pos)
+    out = {
+        "metric": "queries/s",
+        "value": value,
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "c-approximate + exact reverse k-ranks, index build included: "
+                        "|U|=1,000,000 |P|=100,000 d=200 Gaussian mixture (256 centres), "
+                        "10,000 queries from P, k in {10,50,100}, c=2, tau=500, omega=10, s=100",
+            "l2": "inputs larger than L2 (U is 800 MB)",
+            "parallelism": f"replicas x{ws}",
+        },
+        "user_item_scores_per_s": w.n * w.m / (ms / 1000.0),
+        "phases_ms": {
+            "build": {kk: mean(kk) for kk in stage[0]},
+            "approx": {kk: qa0[kk] for kk in ("ms_theta", "ms_resolve", "ms_select")},
+            "exact": {kk: qe0[kk] for kk in ("ms_theta", "ms_resolve", "ms_select")},
+        },
+        "candidates": {"approx": qa0["candidates"], "exact": qe0["candidates"],
+                       "exact_near_ties": qe0["near_ties"], "wide_queries":
+                           [qa0["wide_queries"], qe0["wide_queries"]]},
+        "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "FP32 CUDA-core peak from SM count and max SM clock "
+                                    f"({peak_src} clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+
+
+def cpu_baseline(w, pos, n_sample=None, q_sample=None):
+    """The oracle on a user sample (all items), scaled by n / n_sample; queries of the
+    approximate step on a query sample, scaled by nq / q_sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    n_sample = n_sample or int(os.environ.get("RKR_CPU_USERS", "2000"))
+    q_sample = q_sample or int(os.environ.get("RKR_CPU_QUERIES", "500"))
+    rng = np.random.default_rng(0)
+    users = np.sort(rng.choice(w.n, size=n_sample, replace=False))
+    Us = np.ascontiguousarray(w.U[users])
+    nq = w.Q.shape[0]
+    t0 = time.perf_counter()
+    ora = oracle.build_index(Us, w.P, w.tau, w.omega, w.s, pos)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    R = oracle.ranks(Us, w.P, w.Q)
+    for q in range(nq):
+        oracle.select_exact(R[:, q], min(int(w.k[q]), n_sample))
+    t_exact = time.perf_counter() - t0
+    qs = np.arange(q_sample)
+    t0 = time.perf_counter()
+    oracle.approx_query(ora, Us, w.Q[qs], np.minimum(w.k[qs], n_sample), C)
+    t_approx = (time.perf_counter() - t0) * nq / q_sample
+    step = (t_build + t_exact + t_approx) * w.n / n_sample
+    return {"value": nq / step, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_sample} of {w.n} users with all {w.m} items; approximate queries on "
+                      f"{q_sample} of {nq} queries; scaled linearly to the full step",
+            "seconds": {"build": t_build, "exact": t_exact, "approx_scaled": t_approx}}
+
+
+def bench_reference(args):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return
+    w, pos = make_inputs()
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(w, pos, n_sample=400, q_sample=100))
+    vals = vals[args.warmup:]
+    value = statistics.mean(v["value"] for v in vals)
+    cb = dict(vals[-1])
+    cb["value"] = value
+    out = {"impl": "reference", "metric": "queries/s", "value": value, "unit": "queries/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 * w.Q.shape[0] / value, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "c-approximate + exact reverse k-ranks, index build included: "
+                                  "|U|=1,000,000 |P|=100,000 d=200, 10,000 queries (oracle "
+                                  "on a user sample, scaled)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

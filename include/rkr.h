@@ -1,0 +1,180 @@
+/*
+ * rkr.h -- C ABI of the GB300 reverse k-ranks library (librkr.so).
+ *
+ * Problem (Amagata et al., "Approximate Reverse k-Ranks Queries in High
+ * Dimensions"):
+ *   rank      r(q,u,P) = 1 + #{p in P : u.p > u.q}                 (Def. 1)
+ *   exact     the k users with the smallest rank                   (Def. 2)
+ *   c-approx  k users whose i-th rank is at most c times the i-th
+ *             rank of the exact answer                             (Def. 3)
+ * The c-approximate answer is computed with the paper's rank table
+ * (Alg. 1, Eq. 1) and its three query steps (Section 4.3).
+ *
+ * Arithmetic.  The paper fixes no precision.  This library defines the score
+ * of a user u and an item x (both float32 rows of length d) as the canonical
+ * value s(u,x) = left-to-right sum over k of (double)u[k] * (double)x[k],
+ * rounded to double after every addition.  Every comparison that decides a
+ * rank, a table entry or a bin is made on canonical scores, so results are
+ * bit-identical to a plain FP64 CPU evaluation.  Bulk scores are screened on
+ * the GPU in lower precision with rigorous error bounds; only undecided cases
+ * are recomputed canonically.
+ *
+ * Pointers.  Every array argument may be a host pointer or a device pointer of
+ * the current device; the library detects which.  Matrices are row-major and
+ * contiguous: U is n x d, P is m x d, Q is nq x d (float32).  The caller owns
+ * every array it passes; the index owns device copies of U and P and all
+ * derived data, released by rkr_index_free.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ * work is enqueued on it; each call synchronizes it before returning, so
+ * outputs (host or device) are complete when the call returns.
+ *
+ * Errors.  Every call returns an rkr_status; RKR_OK is 0.  On failure nothing
+ * is written to the outputs that the caller can rely on, and rkr_last_error()
+ * returns a message for the calling thread.  No call aborts or throws.
+ *
+ * Device.  Kernels are built for sm_103a (GB300) only; other devices get
+ * RKR_EUNSUPPORTED.
+ */
+#ifndef RKR_H
+#define RKR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RKR_OK = 0,
+  RKR_EINVAL = 1,        /* invalid argument (null pointer, size, k, c, non-finite input) */
+  RKR_ENOMEM = 2,        /* device or host allocation failed */
+  RKR_ECUDA = 3,         /* CUDA runtime error; see rkr_last_error() */
+  RKR_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+  RKR_EUNSUPPORTED = 5,  /* device is not sm_103, or feature not built */
+  RKR_EINTERNAL = 6      /* an internal consistency check failed */
+} rkr_status;
+
+typedef struct rkr_index rkr_index;
+
+/* Parameters of the pre-processing step (Alg. 1 inputs: tau, omega, s). */
+typedef struct {
+  int32_t tau;              /* number of thresholds per user, >= 2 (Section 4.2, step 2) */
+  int32_t omega;            /* number of norm buckets, 1 <= omega <= m (Alg. 1) */
+  int32_t s;                /* samples per bucket, >= 1 (Eq. 1); m * s must be < 2^32 */
+  int32_t fbounds;          /* 0: f_min/f_max are the exact min/max of u.p over P
+                               (Section 4.2, step 2); 1: +-||u|| * max ||p||
+                               (the bounded-domain variant of the footnote) */
+  int32_t exact_table;      /* 1: also build the exact count table rkr_query_exact needs */
+  int32_t floor_rank;       /* exact table: counts are kept exact only above the
+                               threshold whose estimated rank is floor_rank; 0 = default
+                               max(2048, m / 16).  Only speed depends on it. */
+  const int32_t *sample_pos;/* omega x s positions inside each bucket of the norm-sorted
+                               items, -1 = unused; a bucket of at most s items must list
+                               0..|P_l|-1.  Host or device.  NULL = draw them from `seed`
+                               (uniform without replacement, SplitMix64). */
+  uint64_t seed;
+} rkr_build_params;
+
+/* Counters of one query call (any pointer may be NULL). */
+typedef struct {
+  int64_t pairs;            /* user-query pairs screened */
+  int64_t candidates;       /* pairs that survived the rank-bound filter */
+  int64_t fp64_dots;        /* canonical FP64 inner products computed */
+  int64_t near_ties;        /* item scores too close to u.q for the screen to decide */
+  int32_t wide_queries;     /* queries whose cutoff fell to the last level */
+  double max_rel_screen_err;/* reserved */
+  double ms_theta;          /* device time of the u.q screening passes */
+  double ms_resolve;        /* device time of candidate resolution */
+  double ms_select;         /* device time of per-query selection */
+} rkr_query_stats;
+
+/*
+ * rkr_build: pre-processing (Alg. 1) on the GPU.
+ *   U (n x d), P (m x d): float32, finite.  1 <= n < 2^31, 1 <= m <= 2^30, 1 <= d <= 256.
+ *   Steps: norms of P and sort by (descending norm, index); omega buckets of
+ *   m / omega items (the first m % omega get one more); per-bucket samples;
+ *   f_min/f_max per user; thresholds t_j = f_min + (j-1) * ((f_max - f_min) / (tau - 1));
+ *   table numerators N[u][j] = sum_l w_l * #{p in sample_l : s(u,p) > t_j}
+ *   with w_l = |P_l| (s sampled) or s (whole bucket taken), so that
+ *   T-hat[u][j] = 1 + N[u][j] / s (Eq. 1).
+ *   On success *out receives a new index; free it with rkr_index_free.
+ */
+rkr_status rkr_build(const float *U, int64_t n, const float *P, int64_t m, int32_t d,
+                     const rkr_build_params *params, void *stream, rkr_index **out);
+
+/*
+ * rkr_query_exact: exact reverse k-ranks (Def. 1, Def. 2) for nq queries.
+ *   Q: nq x d float32, finite.  k: nq int32 values, 1 <= k[i] <= min(n, 4096).
+ *   Needs an index built with exact_table = 1.
+ *   Output per query i: k[i] users in ascending (rank, user index) order, written
+ *   at offset sum_{j<i} k[j] of out_users (int32 user index) and out_ranks (int32 rank).
+ *   Ties: among users of equal rank the smaller index comes first (any set of k
+ *   smallest ranks satisfies Def. 2; this picks one).
+ */
+rkr_status rkr_query_exact(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                           int32_t *out_users, int32_t *out_ranks, rkr_query_stats *stats,
+                           void *stream);
+
+/*
+ * rkr_query_approx: c-approximate reverse k-ranks (Def. 3) by the query steps
+ * of Section 4.3.  c >= 1, finite.  k[i] in [1, min(n, 4096)].
+ *   Step 1: j = max{j : t_j <= u.q} (0 if none); r_up = T-hat_j (m+1 if j = 0),
+ *           r_low = T-hat_{j+1} (1 if j = tau); R_low_k, R_up_k = k-th smallest.
+ *   Step 2: Case A if c * R_low_k >= R_up_k: the k users with smallest
+ *           (r_up, r_low, index).  Case B: U_c = {u : r_up <= c * R_low_k};
+ *           users with r_low > R_up_k are dropped.
+ *   Step 3: the other users get r_hat = r_up - (r_up - r_low) * (u.q - t_j) / (t_{j+1} - t_j)
+ *           (r_up outside the grid); the k - |U_c| smallest (r_hat, index) complete the answer.
+ *   Outputs per query i at offset sum_{j<i} k[j]: out_users (int32), out_nlow and
+ *   out_nup (uint32 numerators: r = 1 + N / s), out_est (double r_hat, computed for
+ *   every returned user with the step-3 formula).  Step-2 users come first in
+ *   (r_up, r_low, index) order, then step-3 users in (r_hat, index) order.
+ *   out_case[i] = 1 (Case A) or 2 (Case B); out_nc[i] = number of step-2 users.
+ *   Any output pointer except out_users may be NULL.
+ */
+rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                            double c, int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
+                            double *out_est, int32_t *out_case, int32_t *out_nc,
+                            rkr_query_stats *stats, void *stream);
+
+/* What rkr_index_export copies out. */
+typedef enum {
+  RKR_EXPORT_PERM = 1,      /* int32[m]: original item index of each norm-sorted position */
+  RKR_EXPORT_FMIN = 2,      /* double[n] */
+  RKR_EXPORT_FMAX = 3,      /* double[n] */
+  RKR_EXPORT_TABLE = 4,     /* uint32[n * tau]: N[u][j], j = 0..tau-1 */
+  RKR_EXPORT_SAMPLES = 5,   /* int32[total samples]: original item index, bucket after bucket */
+  RKR_EXPORT_XLO = 6,       /* uint32[n * tau]: lower bound of #{p : s(u,p) > t_j} */
+  RKR_EXPORT_XHI = 7,       /* uint32[n * tau]: upper bound of the same count */
+  RKR_EXPORT_PNORM = 8      /* double[m]: FP64 norms of P in original order */
+} rkr_export_what;
+
+/* Copy one internal array to dst (host or device); bytes must equal its size. */
+rkr_status rkr_index_export(const rkr_index *idx, int32_t what, void *dst, int64_t bytes);
+
+/* Sizes of the index: out[0..6] = n, m, d, tau, omega, s, total samples. */
+rkr_status rkr_index_info(const rkr_index *idx, int64_t *out7);
+
+/* Device time in ms of the build stages of an index: out[0] items (norms, sort,
+ * gather), [1] samples, [2] f_min/f_max, [3] rank table, [4] level tables,
+ * [5] exact count table, [6] total.  Entries beyond 6 are 0. */
+rkr_status rkr_index_timings(const rkr_index *idx, double *out, int32_t count);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t rkr_kernel_launches(void);
+
+/* Release an index (NULL is allowed). */
+void rkr_index_free(rkr_index *idx);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *rkr_last_error(void);
+
+/* Library version string. */
+const char *rkr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKR_H */

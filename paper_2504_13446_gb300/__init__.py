@@ -1,0 +1,270 @@
+"""GB300 reverse k-ranks: exact and c-approximate queries behind a C ABI.
+
+Thin ctypes binding over ``librkr.so`` (built from ``csrc/`` for sm_103a by
+``buildlib.build()``).  Functions carry the names of the C entry points
+(``rkr_build``, ``rkr_query_exact``, ``rkr_query_approx``); they only marshal
+arguments.  Every step of the computation runs in the library's CUDA kernels:
+there is no CPU fallback, and using this package without the built library
+raises ``RuntimeError``.
+
+Arrays may be numpy arrays (host memory) or torch CUDA tensors (device memory);
+the library detects which.  Outputs are numpy arrays unless ``device=True``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import buildlib
+
+__all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
+           "rkr_query_approx", "EXPORTS"]
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = dict(perm=1, fmin=2, fmax=3, table=4, samples=5, xlo=6, xhi=7, pnorm=8)
+_STATUS = {0: "RKR_OK", 1: "RKR_EINVAL", 2: "RKR_ENOMEM", 3: "RKR_ECUDA", 4: "RKR_ETIMEOUT",
+           5: "RKR_EUNSUPPORTED", 6: "RKR_EINTERNAL"}
+
+
+class RKRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _BuildParams(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_int32), ("omega", ctypes.c_int32), ("s", ctypes.c_int32),
+                ("fbounds", ctypes.c_int32), ("exact_table", ctypes.c_int32),
+                ("floor_rank", ctypes.c_int32), ("sample_pos", ctypes.c_void_p),
+                ("seed", ctypes.c_uint64)]
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("fp64_dots", ctypes.c_int64), ("near_ties", ctypes.c_int64),
+                ("wide_queries", ctypes.c_int32), ("max_rel_screen_err", ctypes.c_double),
+                ("ms_theta", ctypes.c_double), ("ms_resolve", ctypes.c_double),
+                ("ms_select", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def load() -> ctypes.CDLL:
+    """Load librkr.so; raises RuntimeError when it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(buildlib.LIB):
+            raise RuntimeError(f"{buildlib.LIB} is missing: build it with "
+                               "paper_2504_13446_gb300.buildlib.build()")
+        lib = ctypes.CDLL(buildlib.LIB)
+        V, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.rkr_build.restype = I32
+        lib.rkr_build.argtypes = [V, I64, V, I64, I32, ctypes.POINTER(_BuildParams), V,
+                                  ctypes.POINTER(V)]
+        lib.rkr_query_exact.restype = I32
+        lib.rkr_query_exact.argtypes = [V, V, I32, V, V, V, ctypes.POINTER(QueryStats), V]
+        lib.rkr_query_approx.restype = I32
+        lib.rkr_query_approx.argtypes = [V, V, I32, V, ctypes.c_double, V, V, V, V, V, V,
+                                         ctypes.POINTER(QueryStats), V]
+        lib.rkr_index_export.restype = I32
+        lib.rkr_index_export.argtypes = [V, I32, V, I64]
+        lib.rkr_index_info.restype = I32
+        lib.rkr_index_info.argtypes = [V, ctypes.POINTER(I64)]
+        lib.rkr_index_free.restype = None
+        lib.rkr_index_free.argtypes = [V]
+        lib.rkr_index_timings.restype = I32
+        lib.rkr_index_timings.argtypes = [V, ctypes.POINTER(ctypes.c_double), I32]
+        lib.rkr_kernel_launches.restype = ctypes.c_uint64
+        lib.rkr_kernel_launches.argtypes = []
+        lib.rkr_last_error.restype = ctypes.c_char_p
+        lib.rkr_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by librkr.so in this process so far."""
+    return int(load().rkr_kernel_launches())
+
+
+def _check(st: int):
+    if st != 0:
+        raise RKRError(st, load().rkr_last_error().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) for a numpy array or a contiguous torch tensor."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        want = {np.float32: torch.float32, np.int32: torch.int32, np.uint32: torch.int32,
+                np.float64: torch.float64}[dtype]
+        if x.dtype != want and not (dtype is np.uint32 and x.dtype == torch.int32):
+            raise TypeError(f"tensor dtype {x.dtype}, expected {want}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), a
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _empty(shape, dtype, device: bool):
+    if device:
+        import torch
+        tdt = {np.int32: torch.int32, np.uint32: torch.int32, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=tdt, device="cuda")
+    return np.empty(shape, dtype=dtype)
+
+
+def _shape(x):
+    return tuple(x.shape)
+
+
+def rkr_build(U, P, *, tau: int = 500, omega: int = 10, s: int = 100, fbounds: str = "exact",
+              exact_table: bool = True, floor_rank: int = 0, sample_pos=None, seed: int = 0,
+              stream=None) -> ctypes.c_void_p:
+    """Pre-processing (Alg. 1); returns an opaque index handle (free with rkr_index_free)."""
+    lib = load()
+    n, d = _shape(U)
+    m, d2 = _shape(P)
+    if d != d2:
+        raise ValueError("U and P must have the same dimension")
+    pu, ku = _ptr(U, np.float32)
+    pp, kp = _ptr(P, np.float32)
+    ps, ks = _ptr(sample_pos, np.int32)
+    prm = _BuildParams(tau, omega, s, {"exact": 0, "cs": 1}[fbounds], int(exact_table),
+                       floor_rank, ps, seed)
+    h = ctypes.c_void_p()
+    _check(lib.rkr_build(pu, n, pp, m, d, ctypes.byref(prm), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def rkr_query_exact(index, Q, k, *, device: bool = False, stream=None):
+    """Exact reverse k-ranks: (users, ranks, offsets, stats) with per-query segments."""
+    lib = load()
+    nq, _ = _shape(Q)
+    kk = np.broadcast_to(np.asarray(k if not _is_torch(k) else k.cpu().numpy(), np.int32), (nq,))
+    off = np.concatenate([[0], np.cumsum(kk, dtype=np.int64)])
+    pq, kq = _ptr(Q, np.float32)
+    pk, kk_ = _ptr(k if _is_torch(k) else np.ascontiguousarray(kk), np.int32)
+    users = _empty((int(off[-1]),), np.int32, device)
+    ranks = _empty((int(off[-1]),), np.int32, device)
+    pu, _ = _ptr(users, np.int32)
+    pr, _ = _ptr(ranks, np.int32)
+    stats = QueryStats()
+    _check(lib.rkr_query_exact(index, pq, nq, pk, pu, pr, ctypes.byref(stats), _stream(stream)))
+    return users, ranks, off, stats
+
+
+def rkr_query_approx(index, Q, k, c: float, *, device: bool = False, stream=None):
+    """c-approximate reverse k-ranks (Section 4.3): dict of per-user and per-query outputs."""
+    lib = load()
+    nq, _ = _shape(Q)
+    kk = np.broadcast_to(np.asarray(k if not _is_torch(k) else k.cpu().numpy(), np.int32), (nq,))
+    off = np.concatenate([[0], np.cumsum(kk, dtype=np.int64)])
+    tot = int(off[-1])
+    pq, kq = _ptr(Q, np.float32)
+    pk, kk_ = _ptr(k if _is_torch(k) else np.ascontiguousarray(kk), np.int32)
+    out = dict(users=_empty((tot,), np.int32, device), n_low=_empty((tot,), np.uint32, device),
+               n_up=_empty((tot,), np.uint32, device), est=_empty((tot,), np.float64, device),
+               case=_empty((nq,), np.int32, device), nc=_empty((nq,), np.int32, device))
+    ptrs = [_ptr(out[name], dt)[0] for name, dt in
+            (("users", np.int32), ("n_low", np.uint32), ("n_up", np.uint32),
+             ("est", np.float64), ("case", np.int32), ("nc", np.int32))]
+    stats = QueryStats()
+    _check(lib.rkr_query_approx(index, pq, nq, pk, ctypes.c_double(c), *ptrs,
+                                ctypes.byref(stats), _stream(stream)))
+    out["offsets"] = off
+    out["stats"] = stats
+    return out
+
+
+@dataclass
+class _Info:
+    n: int
+    m: int
+    d: int
+    tau: int
+    omega: int
+    s: int
+    nsamp: int
+
+
+class Index:
+    """Owns one index handle; see rkr_build for the parameters."""
+
+    def __init__(self, U, P, **kw):
+        self._h: Optional[ctypes.c_void_p] = rkr_build(U, P, **kw)
+        raw = (ctypes.c_int64 * 7)()
+        _check(load().rkr_index_info(self._h, raw))
+        self.info = _Info(*[int(v) for v in raw])
+
+    def query_exact(self, Q, k, **kw):
+        return rkr_query_exact(self._h, Q, k, **kw)
+
+    def query_approx(self, Q, k, c, **kw):
+        return rkr_query_approx(self._h, Q, k, c, **kw)
+
+    def export(self, what: str) -> np.ndarray:
+        i = self.info
+        shapes = dict(perm=((i.m,), np.int32), fmin=((i.n,), np.float64),
+                      fmax=((i.n,), np.float64), table=((i.n, i.tau), np.uint32),
+                      samples=((i.nsamp,), np.int32), xlo=((i.n, i.tau), np.uint32),
+                      xhi=((i.n, i.tau), np.uint32), pnorm=((i.m,), np.float64))
+        shape, dt = shapes[what]
+        a = np.empty(shape, dtype=dt)
+        _check(load().rkr_index_export(self._h, EXPORTS[what], a.ctypes.data_as(ctypes.c_void_p),
+                                       a.nbytes))
+        return a
+
+    def timings(self) -> dict:
+        """Device time (ms) of the build stages."""
+        raw = (ctypes.c_double * 8)()
+        _check(load().rkr_index_timings(self._h, raw, 8))
+        names = ("items", "samples", "fbounds", "table", "levels", "exact_table", "total")
+        return {k: float(raw[i]) for i, k in enumerate(names)}
+
+    def close(self):
+        if self._h is not None:
+            load().rkr_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,376 @@
+// api.cu -- the extern "C" entry points of librkr.so (see include/rkr.h).
+//
+// Argument checking, host/device staging of arrays, and dispatch to the build
+// (build.cu) and query (query.cu) code.  No entry point throws or aborts.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "index.cuh"
+
+namespace rkr {
+
+static thread_local char g_err[512] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+rkr_status fail(rkr_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+rkr_status cuda_fail(cudaError_t e, const char *what) {
+  set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? RKR_ENOMEM : RKR_ECUDA;
+}
+
+
+
+// 1 if p is memory of the current device (or managed), 0 for host memory.
+static int is_device(const void *p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static rkr_status check_device() {
+  int dev = 0;
+  RKR_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp pr;
+  RKR_CUDA(cudaGetDeviceProperties(&pr, dev));
+  if (!(pr.major == 10 && pr.minor == 3))
+    return fail(RKR_EUNSUPPORTED, "device sm_%d%d: this library is built for sm_103a (GB300)",
+                pr.major, pr.minor);
+  return RKR_OK;
+}
+
+// A device view of a caller array: the array itself if it is device memory,
+// else a stream-ordered device copy (owned here) of `bytes` bytes.
+struct InView {
+  const void *dev = nullptr;
+  void *own = nullptr;
+  cudaStream_t st = nullptr;
+  rkr_status init(const void *p, size_t bytes, cudaStream_t s) {
+    st = s;
+    if (is_device(p)) {
+      dev = p;
+      return RKR_OK;
+    }
+    cudaError_t e = cudaMallocAsync(&own, bytes ? bytes : 1, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      own = nullptr;
+      return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    RKR_CUDA(cudaMemcpyAsync(own, p, bytes, cudaMemcpyHostToDevice, s));
+    dev = own;
+    return RKR_OK;
+  }
+  ~InView() {
+    if (own) cudaFreeAsync(own, st);
+  }
+};
+
+// An output array: written in place if device memory, else through a device
+// buffer copied back by finish().
+struct OutView {
+  void *user = nullptr;
+  void *dev = nullptr;
+  void *own = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  rkr_status init(void *p, size_t b, cudaStream_t s) {
+    user = p;
+    bytes = b;
+    st = s;
+    if (!p) return RKR_OK;
+    if (is_device(p)) {
+      dev = p;
+      return RKR_OK;
+    }
+    cudaError_t e = cudaMallocAsync(&own, b ? b : 1, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      own = nullptr;
+      return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", b);
+    }
+    dev = own;
+    return RKR_OK;
+  }
+  rkr_status finish() {
+    if (own && bytes) RKR_CUDA(cudaMemcpyAsync(user, own, bytes, cudaMemcpyDeviceToHost, st));
+    return RKR_OK;
+  }
+  ~OutView() {
+    if (own) cudaFreeAsync(own, st);
+  }
+};
+
+}  // namespace rkr
+
+using namespace rkr;
+
+extern "C" {
+
+const char *rkr_last_error(void) { return g_err; }
+
+const char *rkr_version(void) { return "rkr 0.1 (sm_103a)"; }
+
+uint64_t rkr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rkr_status rkr_index_timings(const rkr_index *idx, double *out, int32_t count) {
+  if (!idx || !out || count < 0) return fail(RKR_EINVAL, "null argument");
+  for (int i = 0; i < count; ++i) out[i] = i < (int)(sizeof(idx->build_ms) / sizeof(double)) ? idx->build_ms[i] : 0.0;
+  return RKR_OK;
+}
+
+rkr_status rkr_build(const float *U, int64_t n, const float *P, int64_t m, int32_t d,
+                     const rkr_build_params *params, void *stream, rkr_index **out) {
+  g_err[0] = 0;
+  if (!U || !P || !params || !out) return fail(RKR_EINVAL, "null argument");
+  *out = nullptr;
+  if (n < 1 || m < 1 || d < 1) return fail(RKR_EINVAL, "need n, m, d >= 1");
+  if (d > kMaxD) return fail(RKR_EINVAL, "d = %d exceeds the supported maximum %d", d, kMaxD);
+  if (n > ((int64_t)1 << 31) - 1 || m > ((int64_t)1 << 30))
+    return fail(RKR_EINVAL, "n must be < 2^31 and m <= 2^30");
+  const rkr_build_params &p = *params;
+  if (p.tau < 2 || p.tau > 8192) return fail(RKR_EINVAL, "tau must be in [2, 8192]");
+  if (p.omega < 1 || p.omega > m) return fail(RKR_EINVAL, "omega must be in [1, m]");
+  if (p.s < 1) return fail(RKR_EINVAL, "s must be >= 1");
+  if ((uint64_t)m * (uint64_t)p.s >= ((uint64_t)1 << 32))
+    return fail(RKR_EINVAL, "m * s must be < 2^32");
+  if ((int64_t)p.omega * p.s > ((int64_t)1 << 26)) return fail(RKR_EINVAL, "omega * s too large");
+  if (p.fbounds != 0 && p.fbounds != 1) return fail(RKR_EINVAL, "fbounds must be 0 or 1");
+  if (p.floor_rank < 0) return fail(RKR_EINVAL, "floor_rank must be >= 0");
+  RKR_TRY(check_device());
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // sample positions: host copy for validation
+  std::vector<int32_t> spos;
+  if (p.sample_pos) {
+    spos.resize((size_t)p.omega * p.s);
+    if (is_device(p.sample_pos)) {
+      RKR_CUDA(cudaMemcpyAsync(spos.data(), p.sample_pos, sizeof(int32_t) * spos.size(),
+                               cudaMemcpyDeviceToHost, st));
+      RKR_CUDA(cudaStreamSynchronize(st));
+    } else {
+      memcpy(spos.data(), p.sample_pos, sizeof(int32_t) * spos.size());
+    }
+  }
+  InView vu, vp;
+  RKR_TRY(vu.init(U, sizeof(float) * n * d, st));
+  RKR_TRY(vp.init(P, sizeof(float) * m * d, st));
+  int ok_u = 0, ok_p = 0;
+  RKR_TRY(all_finite((const float *)vu.dev, n * d, &ok_u, st));
+  RKR_TRY(all_finite((const float *)vp.dev, m * d, &ok_p, st));
+  if (!ok_u || !ok_p) return fail(RKR_EINVAL, "U and P must be finite");
+
+  rkr_index *idx = new (std::nothrow) rkr_index();
+  if (!idx) return fail(RKR_ENOMEM, "host allocation failed");
+  idx->n = n;
+  idx->m = m;
+  idx->d = d;
+  idx->tau = p.tau;
+  idx->omega = p.omega;
+  idx->s = p.s;
+  idx->fbounds = p.fbounds;
+  idx->has_exact = p.exact_table ? 1 : 0;
+  idx->floor_rank = p.floor_rank ? p.floor_rank : (int)(m / 16 > 2048 ? m / 16 : 2048);
+  rkr_status stt = build_index(idx, (const float *)vu.dev, (const float *)vp.dev, &p,
+                               p.sample_pos ? spos.data() : nullptr, st);
+  if (stt != RKR_OK) {
+    cudaStreamSynchronize(st);
+    index_release(idx);
+    delete idx;
+    return stt;
+  }
+  *out = idx;
+  return RKR_OK;
+}
+
+static rkr_status query_prologue(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                 cudaStream_t st, std::vector<int32_t> &kh,
+                                 std::vector<int64_t> &off) {
+  if (!idx || !Q || !k) return fail(RKR_EINVAL, "null argument");
+  if (nq < 1) return fail(RKR_EINVAL, "nq must be >= 1");
+  kh.resize(nq);
+  if (is_device(k)) {
+    RKR_CUDA(cudaMemcpyAsync(kh.data(), k, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+  } else {
+    memcpy(kh.data(), k, sizeof(int32_t) * nq);
+  }
+  off.assign(nq + 1, 0);
+  for (int q = 0; q < nq; ++q) {
+    if (kh[q] < 1 || kh[q] > idx->n || kh[q] > kMaxK)
+      return fail(RKR_EINVAL, "k[%d] = %d must be in [1, min(n, %d)]", q, kh[q], kMaxK);
+    off[q + 1] = off[q] + kh[q];
+  }
+  return RKR_OK;
+}
+
+struct QueryStage {
+  InView vq, vk;
+  float *qnrm = nullptr;
+  int64_t *off_d = nullptr;
+  BinFP *bf_own = nullptr;
+  cudaStream_t st = nullptr;
+  ~QueryStage() {
+    if (qnrm) cudaFreeAsync(qnrm, st);
+    if (off_d) cudaFreeAsync(off_d, st);
+    if (bf_own) cudaFreeAsync(bf_own, st);
+  }
+};
+
+static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const int32_t *k,
+                                const std::vector<int64_t> &off, cudaStream_t st,
+                                QueryStage &qs, QueryCommon &qc) {
+  qs.st = st;
+  const int d = idx->d;
+  RKR_TRY(qs.vq.init(Q, sizeof(float) * (size_t)nq * d, st));
+  RKR_TRY(qs.vk.init(k, sizeof(int32_t) * nq, st));
+  int ok = 0;
+  RKR_TRY(all_finite((const float *)qs.vq.dev, (int64_t)nq * d, &ok, st));
+  if (!ok) return fail(RKR_EINVAL, "Q must be finite");
+  RKR_CUDA(cudaMallocAsync(&qs.qnrm, sizeof(float) * nq, st));
+  RKR_CUDA(cudaMallocAsync(&qs.off_d, sizeof(int64_t) * (nq + 1), st));
+  RKR_CUDA(cudaMemcpyAsync(qs.off_d, off.data(), sizeof(int64_t) * (nq + 1),
+                           cudaMemcpyHostToDevice, st));
+  RKR_TRY(row_norms((const float *)qs.vq.dev, nq, d, nullptr, qs.qnrm, st));
+  float qmax = 0.0f;
+  RKR_TRY(max_float(qs.qnrm, nq, &qmax, st));
+  qc.Qd = (float *)qs.vq.dev;
+  qc.qnrm = qs.qnrm;
+  qc.kq_d = (int32_t *)qs.vk.dev;
+  qc.out_off_d = qs.off_d;
+  qc.bf = idx->binfp;
+  if (qmax > idx->pmax) {  // |u.q| may exceed the range the stored bin bounds assume
+    RKR_CUDA(cudaMallocAsync(&qs.bf_own, sizeof(BinFP) * idx->n, st));
+    RKR_TRY(make_binfp(idx, qmax, qs.bf_own, st));
+    qc.bf = qs.bf_own;
+  }
+  return RKR_OK;
+}
+
+rkr_status rkr_query_exact(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                           int32_t *out_users, int32_t *out_ranks, rkr_query_stats *stats,
+                           void *stream) {
+  g_err[0] = 0;
+  if (!out_users || !out_ranks) return fail(RKR_EINVAL, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> kh;
+  std::vector<int64_t> off;
+  RKR_TRY(query_prologue(idx, Q, nq, k, st, kh, off));
+  if (!idx->has_exact) return fail(RKR_EINVAL, "index was built without exact_table");
+  QueryStage qs;
+  QueryCommon qc;
+  RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
+  OutView ou, orr;
+  size_t tot = (size_t)off[nq];
+  RKR_TRY(ou.init(out_users, sizeof(int32_t) * tot, st));
+  RKR_TRY(orr.init(out_ranks, sizeof(int32_t) * tot, st));
+  RKR_TRY(run_query_exact(idx, qc, nq, (int32_t *)ou.dev, (int32_t *)orr.dev, stats, st));
+  RKR_TRY(ou.finish());
+  RKR_TRY(orr.finish());
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                            double c, int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
+                            double *out_est, int32_t *out_case, int32_t *out_nc,
+                            rkr_query_stats *stats, void *stream) {
+  g_err[0] = 0;
+  if (!out_users) return fail(RKR_EINVAL, "null output");
+  if (!(c >= 1.0) || !isfinite(c)) return fail(RKR_EINVAL, "c must be a finite value >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> kh;
+  std::vector<int64_t> off;
+  RKR_TRY(query_prologue(idx, Q, nq, k, st, kh, off));
+  QueryStage qs;
+  QueryCommon qc;
+  RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
+  size_t tot = (size_t)off[nq];
+  OutView ou, olo, oup, oes, oca, onc;
+  RKR_TRY(ou.init(out_users, sizeof(int32_t) * tot, st));
+  RKR_TRY(olo.init(out_nlow, sizeof(uint32_t) * tot, st));
+  RKR_TRY(oup.init(out_nup, sizeof(uint32_t) * tot, st));
+  RKR_TRY(oes.init(out_est, sizeof(double) * tot, st));
+  RKR_TRY(oca.init(out_case, sizeof(int32_t) * nq, st));
+  RKR_TRY(onc.init(out_nc, sizeof(int32_t) * nq, st));
+  RKR_TRY(run_query_approx(idx, qc, nq, c, (int32_t *)ou.dev, (uint32_t *)olo.dev,
+                           (uint32_t *)oup.dev, (double *)oes.dev, (int32_t *)oca.dev,
+                           (int32_t *)onc.dev, stats, st));
+  RKR_TRY(ou.finish());
+  RKR_TRY(olo.finish());
+  RKR_TRY(oup.finish());
+  RKR_TRY(oes.finish());
+  RKR_TRY(oca.finish());
+  RKR_TRY(onc.finish());
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+rkr_status rkr_index_info(const rkr_index *idx, int64_t *out7) {
+  if (!idx || !out7) return fail(RKR_EINVAL, "null argument");
+  out7[0] = idx->n;
+  out7[1] = idx->m;
+  out7[2] = idx->d;
+  out7[3] = idx->tau;
+  out7[4] = idx->omega;
+  out7[5] = idx->s;
+  out7[6] = idx->nsamp;
+  return RKR_OK;
+}
+
+rkr_status rkr_index_export(const rkr_index *idx, int32_t what, void *dst, int64_t bytes) {
+  g_err[0] = 0;
+  if (!idx || !dst) return fail(RKR_EINVAL, "null argument");
+  const void *src = nullptr;
+  int64_t size = 0;
+  switch (what) {
+    case RKR_EXPORT_PERM: src = idx->perm; size = 4 * idx->m; break;
+    case RKR_EXPORT_FMIN: src = idx->fmin; size = 8 * idx->n; break;
+    case RKR_EXPORT_FMAX: src = idx->fmax; size = 8 * idx->n; break;
+    case RKR_EXPORT_TABLE: src = idx->N; size = 4 * idx->n * idx->tau; break;
+    case RKR_EXPORT_SAMPLES: src = idx->samp_items; size = 4 * (int64_t)idx->nsamp; break;
+    case RKR_EXPORT_XLO: src = idx->XLO; size = 4 * idx->n * idx->tau; break;
+    case RKR_EXPORT_XHI: src = idx->XHI; size = 4 * idx->n * idx->tau; break;
+    case RKR_EXPORT_PNORM: src = idx->pnorm; size = 8 * idx->m; break;
+    default: return fail(RKR_EINVAL, "unknown export %d", what);
+  }
+  if (!src) return fail(RKR_EINVAL, "export %d is not part of this index", what);
+  if (bytes != size) return fail(RKR_EINVAL, "export %d needs %lld bytes", what, (long long)size);
+  RKR_CUDA(cudaMemcpy(dst, src, (size_t)size, cudaMemcpyDefault));
+  return RKR_OK;
+}
+
+void rkr_index_free(rkr_index *idx) {
+  if (!idx) return;
+  cudaDeviceSynchronize();
+  index_release(idx);
+  delete idx;
+}
+
+}  // extern "C"

@@ -1,0 +1,739 @@
+// build.cu -- pre-processing on the GPU (Alg. 1) and the exact count table.
+//
+// Steps, each a kernel on the caller's stream:
+//   norms of P (FP64, canonical) and sort by (descending norm, index)   Alg. 1, norm/sort
+//   buckets and sampled rows                                           Alg. 1, partition/sample
+//   f_min / f_max per user (exact scan or Cauchy-Schwarz bound)        Section 4.2, step 2
+//   rank-table numerators N from the sampled rows                      Alg. 1 step 3, Eq. 1
+//   level tables JU / JL that map a bin to the rank level it implies   (candidate filter)
+//   exact count table XLO / XHI bounding #{p : s(u,p) > t_j}           (exact path)
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "index.cuh"
+#include "simt.cuh"
+
+namespace rkr {
+
+// ----------------------------------------------------------------- norms
+
+__global__ void k_row_norms(const float *__restrict__ X, int64_t rows, int d,
+                            double *__restrict__ nrm64, float *__restrict__ nrm32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const float *x = X + i * d;
+  double ss = canon_dot(x, x, d);
+  double nv = sqrt(ss);
+  if (nrm64) nrm64[i] = nv;
+  // upper bound of the exact norm: the canonical sum is within d 2^-53 (relative)
+  if (nrm32) nrm32[i] = __double2float_ru(nv * (1.0 + 0x1p-40) + 1e-300);
+}
+
+rkr_status row_norms(const float *X, int64_t rows, int d, double *nrm64, float *nrm32,
+                     cudaStream_t st) {
+  if (rows <= 0) return RKR_OK;
+  int bs = 128;
+  k_row_norms<<<(unsigned)((rows + bs - 1) / bs), bs, 0, st>>>(X, rows, d, nrm64, nrm32); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+__global__ void k_max_float(const float *__restrict__ x, int64_t count, unsigned *out) {
+  float m = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, x[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // m >= 0
+}
+
+rkr_status max_float(const float *x, int64_t count, float *out_host, cudaStream_t st) {
+  unsigned *dv;
+  RKR_CUDA(cudaMallocAsync(&dv, sizeof(unsigned), st));
+  RKR_CUDA(cudaMemsetAsync(dv, 0, sizeof(unsigned), st));
+  k_max_float<<<256, 256, 0, st>>>(x, count, dv); note_launch();
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, dv, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(dv, st);
+  if (e != cudaSuccess) return cuda_fail(e, "max_float");
+  memcpy(out_host, &h, sizeof(float));
+  return RKR_OK;
+}
+
+__global__ void k_all_finite(const float *__restrict__ x, int64_t count, int *bad) {
+  int b = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+rkr_status all_finite(const float *x, int64_t count, int *ok_host, cudaStream_t st) {
+  int *dv;
+  RKR_CUDA(cudaMallocAsync(&dv, sizeof(int), st));
+  RKR_CUDA(cudaMemsetAsync(dv, 0, sizeof(int), st));
+  k_all_finite<<<512, 256, 0, st>>>(x, count, dv); note_launch();
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, dv, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(dv, st);
+  if (e != cudaSuccess) return cuda_fail(e, "all_finite");
+  *ok_host = h == 0;
+  return RKR_OK;
+}
+
+// ------------------------------------------------------------------ sort
+
+// One compare-exchange stage of a bitonic network over (key, val), ascending by
+// (key, val).  Padding entries carry key = UINT64_MAX, val = INT32_MAX.
+__global__ void k_bitonic(uint64_t *key, int32_t *val, int64_t N, int64_t j, int64_t k) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t ixj = i ^ j;
+  if (ixj <= i) return;
+  bool asc = (i & k) == 0;
+  uint64_t a = key[i], b = key[ixj];
+  int32_t va = val[i], vb = val[ixj];
+  bool gt = (a > b) || (a == b && va > vb);
+  if (gt == asc) {
+    key[i] = b; key[ixj] = a;
+    val[i] = vb; val[ixj] = va;
+  }
+}
+
+rkr_status sort_pairs(uint64_t *key, int32_t *val, int64_t N_pow2, cudaStream_t st) {
+  int bs = 256;
+  unsigned grid = (unsigned)((N_pow2 + bs - 1) / bs);
+  for (int64_t k = 2; k <= N_pow2; k <<= 1)
+    for (int64_t j = k >> 1; j > 0; j >>= 1) {
+      k_bitonic<<<grid, bs, 0, st>>>(key, val, N_pow2, j, k); note_launch();
+    }
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+// Keys for the descending-norm sort: ~bits(norm) (norms are >= +0).
+__global__ void k_norm_keys(const double *__restrict__ nrm, int64_t m, int64_t N,
+                            uint64_t *key, int32_t *val) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (i < m) {
+    key[i] = ~(uint64_t)__double_as_longlong(nrm[i]);
+    val[i] = (int32_t)i;
+  } else {
+    key[i] = ~0ull;
+    val[i] = 0x7fffffff;
+  }
+}
+
+// Ps[i] = P[perm[i]], PT[k][i] = Ps[i][k], pnrm_s[i] = pnrm32[perm[i]].
+__global__ void k_gather_sorted(const float *__restrict__ P, const int32_t *__restrict__ perm,
+                                const float *__restrict__ pn32, int64_t m, int d,
+                                float *__restrict__ Ps, float *__restrict__ PT,
+                                float *__restrict__ pnrm_s) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int64_t src = perm[i];
+  for (int k = 0; k < d; ++k) {
+    float v = P[src * d + k];
+    Ps[i * d + k] = v;
+    PT[(int64_t)k * m + i] = v;
+  }
+  pnrm_s[i] = pn32[src];
+}
+
+// ------------------------------------------------------------- f-bounds
+
+// Exact f_max / f_min (canonical max/min of s(u,p) over P), one thread per user.
+// The FP32 screen decides most items; an item is evaluated canonically only if
+// its screened upper bound exceeds the running maximum (lower bound below the
+// running minimum), so the result is the canonical extreme.
+__global__ void __launch_bounds__(128) k_fbounds(const float *__restrict__ U, int64_t n,
+                                                 const float *__restrict__ Ps,
+                                                 const float *__restrict__ pnrm_s, int64_t m,
+                                                 int d, const float *__restrict__ unrm,
+                                                 double *__restrict__ fmin,
+                                                 double *__restrict__ fmax) {
+  extern __shared__ float smem[];
+  float *Us = smem;                      // [d][128]
+  float *Xs = smem + (size_t)d * 128;    // [d][32]
+  const int t = threadIdx.x;
+  const int64_t u0 = (int64_t)blockIdx.x * 128;
+  const int64_t u = u0 + t;
+  load_users_T(U, n, d, u0, Us);
+  const float cfac = screen_cfac(d);
+  const float nu = u < n ? unrm[u] : 0.0f;
+  double mx = -INFINITY, mn = INFINITY;
+  float mx_f = -INFINITY, mn_f = INFINITY;  // FP32 bounds: mx_f <= mx, mn_f >= mn
+  for (int64_t x0 = 0; x0 < m; x0 += 32) {
+    __syncthreads();
+    load_items_T<32>(Ps, m, d, x0, Xs);
+    __syncthreads();
+    float acc[32];
+    tile_dots<32>(Us, Xs, d, t, acc);
+    if (u >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      int64_t p = x0 + j;
+      if (p >= m) continue;
+      float b = screen_bound(cfac, nu, pnrm_s[p]);
+      float hi = __fadd_ru(acc[j], b), lo = __fsub_rd(acc[j], b);
+      bool need_max = hi > mx_f, need_min = lo < mn_f;
+      if (need_max || need_min) {
+        double sc = canon_dot_slow(U + u * d, Ps + p * d, d);
+        if (sc > mx) { mx = sc; mx_f = __double2float_rd(sc); }
+        if (sc < mn) { mn = sc; mn_f = __double2float_ru(sc); }
+      }
+    }
+  }
+  if (u < n) { fmax[u] = mx; fmin[u] = mn; }
+}
+
+// Cauchy-Schwarz variant: f_max = ||u|| * max ||p||, f_min = -f_max.
+__global__ void k_fbounds_cs(const float *__restrict__ U, int64_t n, int d, double pmax64,
+                             double *fmin, double *fmax) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const float *x = U + u * d;
+  double nu = sqrt(canon_dot(x, x, d));
+  double f = __dmul_rn(nu, pmax64);
+  fmax[u] = f;
+  fmin[u] = -f;
+}
+
+// delta = (f_max - f_min) / (tau - 1) and the FP32 bin parameters.
+// err bounds |v32 - v| in bins for |x| <= ||u|| * R (see BinFP).
+__global__ void k_binfp(int64_t n, const double *__restrict__ fmin,
+                        const double *__restrict__ fmax, int tau, const float *__restrict__ unrm,
+                        float R, double *__restrict__ delta_out, BinFP *__restrict__ out) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  double fm = fmin[u];
+  double dl = __ddiv_rn(__dsub_rn(fmax[u], fm), (double)(tau - 1));
+  if (delta_out) delta_out[u] = dl;
+  BinFP b;
+  b.fmin32 = (float)fm;
+  b.pad = 0.0f;
+  if (!(dl > 0.0)) {
+    b.invd32 = -1.0f;
+    b.err = 0.0f;
+  } else {
+    double xmax = (double)unrm[u] * (double)R * 1.001 + 1e-30;
+    double e = (ldexp(xmax + fabs(fm), -20) + ldexp(fabs(fm), -40)) / dl + ldexp((double)tau, -40) +
+               0x1p-30;
+    double inv = 1.0 / dl;
+    if (!(e < 1e6) || !(inv < 3e38)) {
+      b.invd32 = 1.0f;
+      b.err = 2e6f;
+    } else {
+      b.invd32 = (float)inv;
+      b.err = __double2float_ru(e * (1.0 + 0x1p-10));
+    }
+  }
+  out[u] = b;
+}
+
+rkr_status make_binfp(const rkr_index *idx, float R, BinFP *out, cudaStream_t st) {
+  int bs = 256;
+  k_binfp<<<(unsigned)((idx->n + bs - 1) / bs), bs, 0, st>>>(idx->n, idx->fmin, idx->fmax,
+                                                              idx->tau, idx->unrm, R, nullptr,
+                                                              out); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+// ------------------------------------------------------------ rank table
+
+// Sampled rows and their weights, bucket after bucket.
+__global__ void k_gather_samples(const float *__restrict__ Ps, const float *__restrict__ pnrm_s,
+                                 const int32_t *__restrict__ perm, int d,
+                                 const int64_t *__restrict__ samp_sorted_pos,
+                                 const uint32_t *__restrict__ samp_w, int nsamp,
+                                 float *__restrict__ S, float *__restrict__ snrm,
+                                 int32_t *__restrict__ items) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsamp) return;
+  int64_t p = samp_sorted_pos[i];
+  for (int k = 0; k < d; ++k) S[(int64_t)i * d + k] = Ps[p * d + k];
+  snrm[i] = pnrm_s[p];
+  items[i] = perm[p];
+}
+
+// Warp-per-user rank-table fill (Alg. 1 step 3, Eq. 1).  For each sampled row
+// the number of thresholds it exceeds, c = #{j : s(u,p) > t_j}, is decided by
+// the FP32 screen when its bin interval is a single value and by canonical
+// FP64 otherwise; W[c] += w.  Then N[j] = sum_{c > j} W[c].
+constexpr int kTableWarps = 8;
+constexpr int kTableTile = 64;
+
+__global__ void __launch_bounds__(kTableWarps * 32)
+    k_rank_table(const float *__restrict__ U, int64_t n, int d, const float *__restrict__ unrm,
+                 const float *__restrict__ S, const float *__restrict__ snrm,
+                 const uint32_t *__restrict__ sw, int nsamp, const double *__restrict__ fmin,
+                 const double *__restrict__ delta, const BinFP *__restrict__ binfp, int tau,
+                 uint32_t *__restrict__ N) {
+  extern __shared__ float smem[];
+  float *Xs = smem;                                   // [d][kTableTile]
+  float *Uw = Xs + (size_t)d * kTableTile;            // [warps][d]
+  uint32_t *W = (uint32_t *)(Uw + (size_t)kTableWarps * d);  // [warps][tau+1]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = (int64_t)blockIdx.x * kTableWarps + warp;
+  const bool active = u < n;
+  uint32_t *Wu = W + (size_t)warp * (tau + 1);
+  for (int c = lane; c <= tau; c += 32) Wu[c] = 0;
+  for (int k = lane; k < d; k += 32) Uw[warp * d + k] = active ? U[u * d + k] : 0.0f;
+  const float cfac = screen_cfac(d);
+  const float nu = active ? unrm[u] : 0.0f;
+  BinFP bf;
+  double fm = 0.0, dl = 0.0;
+  if (active) { bf = binfp[u]; fm = fmin[u]; dl = delta[u]; }
+  for (int x0 = 0; x0 < nsamp; x0 += kTableTile) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTableTile * d; e += blockDim.x) {
+      int j = e / d, k = e - j * d;
+      int p = x0 + j;
+      Xs[k * kTableTile + j] = p < nsamp ? S[(int64_t)p * d + k] : 0.0f;
+    }
+    __syncthreads();
+    if (!active) continue;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    const float *uw = Uw + warp * d;
+    for (int k = 0; k < d; ++k) {
+      float uk = uw[k];
+      acc0 = fmaf(uk, Xs[k * kTableTile + lane], acc0);
+      acc1 = fmaf(uk, Xs[k * kTableTile + lane + 32], acc1);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int p = x0 + lane + 32 * h;
+      if (p >= nsamp) continue;
+      float sh = h ? acc1 : acc0;
+      float b = screen_bound(cfac, nu, snrm[p]);
+      int jlo, jhi;
+      bin_interval(bf, fm, tau, __fsub_rd(sh, b), __fadd_ru(sh, b), jlo, jhi);
+      int c = jlo;
+      if (jlo != jhi) {
+        double sc = canon_dot_slow(U + u * d, S + (int64_t)p * d, d);
+        c = exact_c(sc, fm, dl, tau);
+      }
+      atomicAdd(&Wu[c], sw[p]);
+    }
+  }
+  __syncwarp();
+  if (!active) return;
+  // suffix sums: N[j] = sum_{c = j+1 .. tau} W[c]; lanes own contiguous chunks
+  const int chunk = (tau + 1 + 31) / 32;
+  int c0 = lane * chunk, c1 = min(tau + 1, c0 + chunk);
+  uint32_t part = 0;
+  for (int c = c0; c < c1; ++c) part += Wu[c];
+  uint32_t incl = part;  // inclusive suffix over lanes >= lane
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_down_sync(0xffffffffu, incl, o);
+    if (lane + o < 32) incl += v;
+  }
+  uint32_t run = incl - part;  // sum over c >= c1
+  for (int c = c1 - 1; c >= c0; --c) {
+    // N[c - 1] = sum over c' >= c
+    run += Wu[c];
+    if (c >= 1) N[u * tau + (c - 1)] = run;
+  }
+}
+
+// ---------------------------------------------------------- level tables
+
+// For each user and level L (bound B_L = scale (2^L - 1)):
+//   JU[L] = min{j in [0,tau] : UB(j) <= B_L},  UB(0) = top, UB(j) = hi[j-1]
+//   JL[L] = min{j in [0,tau] : LB(j) <= B_L},  LB(j) = lo[j] (j < tau), LB(tau) = 0
+// Both are non-increasing in L; levels >= nlev hold -1.
+__global__ void k_levels(int64_t n, int tau, const uint32_t *__restrict__ hi,
+                         const uint32_t *__restrict__ lo, uint32_t top, uint32_t scale, int nlev,
+                         int16_t *__restrict__ JU, int16_t *__restrict__ JL) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const uint32_t *h = hi + u * tau;
+  const uint32_t *l = lo + u * tau;
+  for (int L = 0; L < kMaxLevels; ++L) {
+    int16_t ju = -1, jl = -1;
+    if (L < nlev) {
+      uint64_t B = level_bound(L, scale);
+      // UB is non-increasing in j: binary search the first j with UB(j) <= B
+      int a = 0, b = tau + 1;
+      while (a < b) {
+        int mid = (a + b) >> 1;
+        uint64_t v = mid == 0 ? top : h[mid - 1];
+        if (v <= B) b = mid; else a = mid + 1;
+      }
+      ju = (int16_t)a;
+      a = 0; b = tau;
+      while (a < b) {
+        int mid = (a + b) >> 1;
+        if ((uint64_t)l[mid] <= B) b = mid; else a = mid + 1;
+      }
+      jl = (int16_t)a;  // LB(tau) = 0 <= B always
+    }
+    JU[u * kMaxLevels + L] = ju;
+    JL[u * kMaxLevels + L] = jl;
+  }
+}
+
+// ------------------------------------------------------ exact count table
+
+// floor column per user: the last column whose estimated count is at least
+// floor_rank (0 if none).  Counts are exact-bounded only for columns >= floor.
+__global__ void k_floor_cols(int64_t n, int tau, const uint32_t *__restrict__ N, uint32_t s,
+                             uint64_t floor_rank, int32_t *__restrict__ fl) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const uint32_t *r = N + u * tau;
+  uint64_t need = floor_rank * (uint64_t)s;
+  int a = 0, b = tau;  // first column with N < need
+  while (a < b) {
+    int mid = (a + b) >> 1;
+    if ((uint64_t)r[mid] < need) b = mid; else a = mid + 1;
+  }
+  fl[u] = a > 0 ? a - 1 : 0;
+}
+
+// Warp-per-user exact count table: XLO[j] <= #{p : s(u,p) > t_j} <= XHI[j].
+// Each item's c(s) is known to lie in [clo, chi] from the FP32 screen; items
+// with chi <= floor cannot count for any column >= floor and are skipped.
+constexpr int kXWarps = 8;
+constexpr int kXTile = 64;
+
+__global__ void __launch_bounds__(kXWarps * 32)
+    k_exact_table(const float *__restrict__ U, int64_t n, int d, const float *__restrict__ unrm,
+                  const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int64_t m,
+                  const double *__restrict__ fmin, const BinFP *__restrict__ binfp, int tau,
+                  const int32_t *__restrict__ xfloor, uint32_t *__restrict__ XLO,
+                  uint32_t *__restrict__ XHI) {
+  extern __shared__ float smem[];
+  float *Xs = smem;                                   // [d][kXTile]
+  float *Uw = Xs + (size_t)d * kXTile;                // [warps][d]
+  uint32_t *H = (uint32_t *)(Uw + (size_t)kXWarps * d);  // [warps][2][tau+1]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = (int64_t)blockIdx.x * kXWarps + warp;
+  const bool active = u < n;
+  uint32_t *Hlo = H + (size_t)warp * 2 * (tau + 1);
+  uint32_t *Hhi = Hlo + (tau + 1);
+  for (int c = lane; c <= tau; c += 32) { Hlo[c] = 0; Hhi[c] = 0; }
+  for (int k = lane; k < d; k += 32) Uw[warp * d + k] = active ? U[u * d + k] : 0.0f;
+  const float cfac = screen_cfac(d);
+  const float nu = active ? unrm[u] : 0.0f;
+  BinFP bf;
+  double fm = 0.0;
+  int fl = 0;
+  if (active) { bf = binfp[u]; fm = fmin[u]; fl = xfloor[u]; }
+  for (int64_t x0 = 0; x0 < m; x0 += kXTile) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kXTile * d; e += blockDim.x) {
+      int j = e / d, k = e - j * d;
+      int64_t p = x0 + j;
+      Xs[k * kXTile + j] = p < m ? Ps[p * d + k] : 0.0f;
+    }
+    __syncthreads();
+    if (!active) continue;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    const float *uw = Uw + warp * d;
+    for (int k = 0; k < d; ++k) {
+      float uk = uw[k];
+      acc0 = fmaf(uk, Xs[k * kXTile + lane], acc0);
+      acc1 = fmaf(uk, Xs[k * kXTile + lane + 32], acc1);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int64_t p = x0 + lane + 32 * h;
+      if (p >= m) continue;
+      float sh = h ? acc1 : acc0;
+      float b = screen_bound(cfac, nu, pnrm_s[p]);
+      int clo, chi;
+      bin_interval(bf, fm, tau, __fsub_rd(sh, b), __fadd_ru(sh, b), clo, chi);
+      if (chi <= fl) continue;
+      atomicAdd(&Hlo[max(clo, fl)], 1u);
+      atomicAdd(&Hhi[chi], 1u);
+    }
+  }
+  __syncwarp();
+  if (!active) return;
+  // suffix sums over c, then fill columns below the floor
+  const int chunk = (tau + 1 + 31) / 32;
+  int c0 = lane * chunk, c1 = min(tau + 1, c0 + chunk);
+  uint32_t plo = 0, phi = 0;
+  for (int c = c0; c < c1; ++c) { plo += Hlo[c]; phi += Hhi[c]; }
+  uint32_t ilo = plo, ihi = phi;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t a = __shfl_down_sync(0xffffffffu, ilo, o);
+    uint32_t b2 = __shfl_down_sync(0xffffffffu, ihi, o);
+    if (lane + o < 32) { ilo += a; ihi += b2; }
+  }
+  uint32_t rlo = ilo - plo, rhi = ihi - phi;
+  for (int c = c1 - 1; c >= c0; --c) {
+    rlo += Hlo[c];
+    rhi += Hhi[c];
+    int j = c - 1;
+    if (j >= fl) { XLO[u * tau + j] = rlo; XHI[u * tau + j] = rhi; }
+  }
+  __syncwarp();
+  uint32_t at_floor = XLO[u * tau + fl];
+  for (int j = lane; j < fl; j += 32) {
+    XLO[u * tau + j] = at_floor;
+    XHI[u * tau + j] = (uint32_t)m;
+  }
+}
+
+// ------------------------------------------------------------- sampling
+
+// SplitMix64 (Steele, Lea and Flood, 2014), used only when the caller supplies
+// no sample positions.
+static uint64_t splitmix64(uint64_t &x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ----------------------------------------------------------------- build
+
+template <class T>
+static rkr_status dalloc(T **p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+  }
+  return RKR_OK;
+}
+
+static int levels_for(uint64_t top_count) {
+  int L = 0;
+  while ((((uint64_t)1 << L) - 1) < top_count) ++L;
+  return L + 1;
+}
+
+rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
+                       const rkr_build_params *prm, const int32_t *sample_pos_host,
+                       cudaStream_t st) {
+  const int64_t n = idx->n, m = idx->m;
+  const int d = idx->d, tau = idx->tau, omega = idx->omega, s = idx->s;
+  const int bs = 256;
+  cudaEvent_t ev[7];
+  for (auto &e : ev) RKR_CUDA(cudaEventCreate(&e));
+  struct EvGuard {
+    cudaEvent_t *e;
+    ~EvGuard() {
+      for (int i = 0; i < 7; ++i) cudaEventDestroy(e[i]);
+    }
+  } evg{ev};
+  RKR_CUDA(cudaEventRecord(ev[0], st));
+
+  // users: own copy + norm bounds
+  RKR_TRY(dalloc(&idx->U, (size_t)n * d));
+  RKR_CUDA(cudaMemcpyAsync(idx->U, U_dev, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, st));
+  RKR_TRY(dalloc(&idx->unrm, n));
+  RKR_TRY(row_norms(idx->U, n, d, nullptr, idx->unrm, st));
+
+  // items: FP64 norms, sort by (descending norm, index)
+  float *pn32 = nullptr;
+  RKR_TRY(dalloc(&idx->pnorm, m));
+  RKR_TRY(dalloc(&pn32, m));
+  RKR_TRY(row_norms(P_dev, m, d, idx->pnorm, pn32, st));
+  int64_t Np2 = 1;
+  while (Np2 < m) Np2 <<= 1;
+  uint64_t *keys = nullptr;
+  int32_t *vals = nullptr;
+  RKR_TRY(dalloc(&keys, Np2));
+  RKR_TRY(dalloc(&vals, Np2));
+  k_norm_keys<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(idx->pnorm, m, Np2, keys, vals); note_launch();
+  RKR_TRY(sort_pairs(keys, vals, Np2, st));
+  RKR_TRY(dalloc(&idx->perm, m));
+  RKR_CUDA(cudaMemcpyAsync(idx->perm, vals, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
+  RKR_TRY(dalloc(&idx->Ps, (size_t)m * d));
+  RKR_TRY(dalloc(&idx->PT, (size_t)m * d));
+  RKR_TRY(dalloc(&idx->pnrm_s, m));
+  k_gather_sorted<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(P_dev, idx->perm, pn32, m, d,
+                                                               idx->Ps, idx->PT, idx->pnrm_s); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  RKR_TRY(max_float(idx->pnrm_s, m, &idx->pmax, st));
+  cudaFreeAsync(keys, st);
+  cudaFreeAsync(vals, st);
+  cudaFreeAsync(pn32, st);
+
+  RKR_CUDA(cudaEventRecord(ev[1], st));
+  // buckets and samples (positions inside buckets of the sorted order)
+  std::vector<int64_t> size(omega), off(omega + 1, 0);
+  for (int l = 0; l < omega; ++l) size[l] = m / omega + (l < m % omega ? 1 : 0);
+  for (int l = 0; l < omega; ++l) off[l + 1] = off[l] + size[l];
+  std::vector<int64_t> spos;
+  std::vector<uint32_t> sw;
+  std::vector<int32_t> scratch;
+  uint64_t rng = prm->seed;
+  for (int l = 0; l < omega; ++l) {
+    bool take_all = size[l] <= s;
+    if (sample_pos_host) {
+      const int32_t *row = sample_pos_host + (size_t)l * s;
+      std::vector<int32_t> got;
+      for (int i = 0; i < s; ++i)
+        if (row[i] >= 0) got.push_back(row[i]);
+      if (take_all) {
+        if ((int64_t)got.size() != size[l])
+          return fail(RKR_EINVAL, "bucket %d has %lld items: all must be listed", l,
+                      (long long)size[l]);
+        std::vector<int32_t> chk = got;
+        std::sort(chk.begin(), chk.end());
+        for (int64_t i = 0; i < size[l]; ++i)
+          if (chk[i] != i) return fail(RKR_EINVAL, "bucket %d must list positions 0..%lld", l,
+                                       (long long)size[l] - 1);
+      } else {
+        if ((int)got.size() != s)
+          return fail(RKR_EINVAL, "bucket %d needs %d sample positions", l, s);
+        std::vector<int32_t> chk = got;
+        std::sort(chk.begin(), chk.end());
+        for (int i = 0; i < s; ++i)
+          if (chk[i] >= size[l] || (i > 0 && chk[i] == chk[i - 1]))
+            return fail(RKR_EINVAL, "bucket %d: positions must be distinct and < %lld", l,
+                        (long long)size[l]);
+      }
+      for (int32_t v : got) {
+        spos.push_back(off[l] + v);
+        sw.push_back(take_all ? (uint32_t)s : (uint32_t)size[l]);
+      }
+    } else if (take_all) {
+      for (int64_t v = 0; v < size[l]; ++v) {
+        spos.push_back(off[l] + v);
+        sw.push_back((uint32_t)s);
+      }
+    } else {  // partial Fisher-Yates
+      scratch.resize(size[l]);
+      for (int64_t v = 0; v < size[l]; ++v) scratch[v] = (int32_t)v;
+      for (int i = 0; i < s; ++i) {
+        uint64_t r = splitmix64(rng) % (uint64_t)(size[l] - i);
+        std::swap(scratch[i], scratch[i + r]);
+        spos.push_back(off[l] + scratch[i]);
+        sw.push_back((uint32_t)size[l]);
+      }
+    }
+  }
+  idx->nsamp = (int)spos.size();
+  int64_t *spos_d = nullptr;
+  RKR_TRY(dalloc(&spos_d, spos.size()));
+  RKR_TRY(dalloc(&idx->sw, sw.size()));
+  RKR_CUDA(cudaMemcpyAsync(spos_d, spos.data(), sizeof(int64_t) * spos.size(),
+                           cudaMemcpyHostToDevice, st));
+  RKR_CUDA(cudaMemcpyAsync(idx->sw, sw.data(), sizeof(uint32_t) * sw.size(),
+                           cudaMemcpyHostToDevice, st));
+  RKR_TRY(dalloc(&idx->S, (size_t)idx->nsamp * d));
+  RKR_TRY(dalloc(&idx->snrm, idx->nsamp));
+  RKR_TRY(dalloc(&idx->samp_items, idx->nsamp));
+  k_gather_samples<<<(idx->nsamp + 127) / 128, 128, 0, st>>>(idx->Ps, idx->pnrm_s, idx->perm, d,
+                                                             spos_d, idx->sw, idx->nsamp, idx->S,
+                                                             idx->snrm, idx->samp_items); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  // host vectors above are read by the async copies: keep them alive until done
+  RKR_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(spos_d, st);
+
+  RKR_CUDA(cudaEventRecord(ev[2], st));
+  // f_min / f_max and bins
+  RKR_TRY(dalloc(&idx->fmin, n));
+  RKR_TRY(dalloc(&idx->fmax, n));
+  RKR_TRY(dalloc(&idx->delta, n));
+  RKR_TRY(dalloc(&idx->binfp, n));
+  if (idx->fbounds == 0) {
+    size_t sm = sizeof(float) * ((size_t)d * 128 + (size_t)d * 32);
+    RKR_CUDA(cudaFuncSetAttribute(k_fbounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fbounds<<<(unsigned)((n + 127) / 128), 128, sm, st>>>(idx->U, n, idx->Ps, idx->pnrm_s, m, d,
+                                                            idx->unrm, idx->fmin, idx->fmax); note_launch();
+  } else {
+    double pmax64 = 0.0;
+    // max FP64 norm: the first item of the sorted order
+    int32_t first = 0;
+    RKR_CUDA(cudaMemcpyAsync(&first, idx->perm, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+    RKR_CUDA(cudaMemcpyAsync(&pmax64, idx->pnorm + first, sizeof(double), cudaMemcpyDeviceToHost,
+                             st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+    k_fbounds_cs<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(idx->U, n, d, pmax64, idx->fmin,
+                                                               idx->fmax); note_launch();
+  }
+  RKR_CUDA(cudaGetLastError());
+  k_binfp<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, idx->fmin, idx->fmax, tau, idx->unrm,
+                                                        idx->pmax, idx->delta, idx->binfp); note_launch();
+  RKR_CUDA(cudaGetLastError());
+
+  RKR_CUDA(cudaEventRecord(ev[3], st));
+  // sampled rank table
+  RKR_TRY(dalloc(&idx->N, (size_t)n * tau));
+  {
+    size_t sm = sizeof(float) * ((size_t)d * kTableTile + (size_t)kTableWarps * d) +
+                sizeof(uint32_t) * (size_t)kTableWarps * (tau + 1);
+    if (sm > 227 * 1024) return fail(RKR_EINVAL, "tau too large for the table kernel");
+    RKR_CUDA(cudaFuncSetAttribute(k_rank_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+    k_rank_table<<<(unsigned)((n + kTableWarps - 1) / kTableWarps), kTableWarps * 32, sm, st>>>(
+        idx->U, n, d, idx->unrm, idx->S, idx->snrm, idx->sw, idx->nsamp, idx->fmin, idx->delta,
+        idx->binfp, tau, idx->N); note_launch();
+    RKR_CUDA(cudaGetLastError());
+  }
+  RKR_CUDA(cudaEventRecord(ev[4], st));
+  idx->nlev_a = levels_for((uint64_t)m);
+  RKR_TRY(dalloc(&idx->JU, (size_t)n * kMaxLevels));
+  RKR_TRY(dalloc(&idx->JL, (size_t)n * kMaxLevels));
+  k_levels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tau, idx->N, idx->N,
+                                                        (uint32_t)(m * s), (uint32_t)s,
+                                                        idx->nlev_a, idx->JU, idx->JL); note_launch();
+  RKR_CUDA(cudaGetLastError());
+
+  RKR_CUDA(cudaEventRecord(ev[5], st));
+  // exact count table
+  if (idx->has_exact) {
+    RKR_TRY(dalloc(&idx->XLO, (size_t)n * tau));
+    RKR_TRY(dalloc(&idx->XHI, (size_t)n * tau));
+    RKR_TRY(dalloc(&idx->xfloor, n));
+    k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
+                                                               (uint64_t)idx->floor_rank,
+                                                               idx->xfloor); note_launch();
+    size_t sm = sizeof(float) * ((size_t)d * kXTile + (size_t)kXWarps * d) +
+                sizeof(uint32_t) * (size_t)kXWarps * 2 * (tau + 1);
+    if (sm > 227 * 1024) return fail(RKR_EINVAL, "tau too large for the exact table kernel");
+    RKR_CUDA(cudaFuncSetAttribute(k_exact_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+    k_exact_table<<<(unsigned)((n + kXWarps - 1) / kXWarps), kXWarps * 32, sm, st>>>(
+        idx->U, n, d, idx->unrm, idx->Ps, idx->pnrm_s, m, idx->fmin, idx->binfp, tau,
+        idx->xfloor, idx->XLO, idx->XHI); note_launch();
+    RKR_CUDA(cudaGetLastError());
+    idx->nlev_x = levels_for((uint64_t)m);
+    RKR_TRY(dalloc(&idx->XJU, (size_t)n * kMaxLevels));
+    RKR_TRY(dalloc(&idx->XJL, (size_t)n * kMaxLevels));
+    k_levels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tau, idx->XHI, idx->XLO,
+                                                          (uint32_t)m, 1u, idx->nlev_x, idx->XJU,
+                                                          idx->XJL); note_launch();
+    RKR_CUDA(cudaGetLastError());
+  }
+  RKR_CUDA(cudaEventRecord(ev[6], st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < 6; ++i) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+    idx->build_ms[i] = ms;
+  }
+  float tot = 0.0f;
+  cudaEventElapsedTime(&tot, ev[0], ev[6]);
+  idx->build_ms[6] = tot;
+  return RKR_OK;
+}
+
+void index_release(rkr_index *idx) {
+  void *ptrs[] = {idx->U,      idx->Ps,   idx->PT,   idx->perm, idx->pnorm, idx->unrm,
+                  idx->pnrm_s, idx->fmin, idx->fmax, idx->delta, idx->binfp, idx->N,
+                  idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
+                  idx->XLO,    idx->XHI,  idx->XJU,  idx->XJL,  idx->xfloor};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace rkr

@@ -1,0 +1,166 @@
+// common.cuh -- shared definitions of the GB300 reverse k-ranks library.
+//
+// Score arithmetic.  The canonical score s(u,x) is the left-to-right FP64 sum
+// of the exact products (double)u[k]*(double)x[k] (the library's reading of
+// Def. 1, which fixes no precision).  Bulk work computes cheaper screened
+// scores s_hat together with a rigorous bound b such that
+// |s_hat - s(u,x)| <= b; a decision is taken from the screen when the bound
+// settles it and from canonical FP64 otherwise.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rkr.h"
+
+namespace rkr {
+
+constexpr int kMaxD = 256;          // largest supported dimension
+constexpr int kMaxLevels = 32;      // rank levels 2^L used by the candidate filter
+constexpr int kMaxK = 4096;         // largest k per query
+
+// ------------------------------------------------------------ error state
+
+void set_error(const char *fmt, ...);
+rkr_status fail(rkr_status st, const char *fmt, ...);
+rkr_status cuda_fail(cudaError_t e, const char *what);
+
+// Count of kernels this library has launched (reported by rkr_kernel_launches).
+void note_launch();
+
+#define RKR_CUDA(expr)                                            \
+  do {                                                            \
+    cudaError_t _e = (expr);                                      \
+    if (_e != cudaSuccess) return ::rkr::cuda_fail(_e, #expr);    \
+  } while (0)
+
+#define RKR_TRY(expr)                                             \
+  do {                                                            \
+    rkr_status _s = (expr);                                       \
+    if (_s != RKR_OK) return _s;                                  \
+  } while (0)
+
+// ------------------------------------------------------- canonical scores
+
+// s(a, b): left-to-right FP64 sum of exact float products.
+__device__ __forceinline__ double canon_dot(const float *__restrict__ a,
+                                            const float *__restrict__ b, int d) {
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) acc = __dadd_rn(acc, __dmul_rn((double)a[k], (double)b[k]));
+  return acc;
+}
+
+// Out-of-line copy for rarely taken paths inside unrolled loops.
+static __device__ __noinline__ double canon_dot_slow(const float *__restrict__ a,
+                                                     const float *__restrict__ b, int d) {
+  return canon_dot(a, b, d);
+}
+
+// Threshold t_{j+1} (0-based i = j): f_min + i * delta, delta = (f_max - f_min) / (tau - 1),
+// each operation rounded to double in that order (Section 4.2, step 2).
+__device__ __forceinline__ double thr_at(double fmin, double delta, int i) {
+  return __dadd_rn(fmin, __dmul_rn((double)i, delta));
+}
+
+// j(theta) = #{i in [0, tau) : t_i <= theta}: the 1-based index of the largest
+// threshold not above theta (0 when theta < t_1), Section 4.3 step 1.
+__device__ __forceinline__ int exact_j(double theta, double fmin, double delta, int tau) {
+  int g;
+  if (delta > 0.0) {
+    double x = (theta - fmin) / delta;
+    g = x < 0.0 ? 0 : (x >= (double)tau ? tau : (int)floor(x) + 1);
+  } else {
+    g = theta >= fmin ? tau : 0;
+  }
+  while (g < tau && thr_at(fmin, delta, g) <= theta) ++g;
+  while (g > 0 && thr_at(fmin, delta, g - 1) > theta) --g;
+  return g;
+}
+
+// c(s) = #{i in [0, tau) : t_i < s}: the number of thresholds a score exceeds
+// (Alg. 1 counts p in column j when s(u,p) > t_j).
+__device__ __forceinline__ int exact_c(double s, double fmin, double delta, int tau) {
+  int g;
+  if (delta > 0.0) {
+    double x = (s - fmin) / delta;
+    g = x < 0.0 ? 0 : (x >= (double)tau ? tau : (int)floor(x) + 1);
+  } else {
+    g = s > fmin ? tau : 0;
+  }
+  while (g < tau && thr_at(fmin, delta, g) < s) ++g;
+  while (g > 0 && thr_at(fmin, delta, g - 1) >= s) --g;
+  return g;
+}
+
+// Per-user data for fast FP32 bin estimates.  For a value x the ideal bin
+// coordinate is v = (x - f_min) / delta; t_i <= x iff i <= v.  v is computed
+// in FP32 as (x - fmin32) * invd32 with an error of at most err bins (see
+// make_binfp), so every integer outside [v - err, v + err] is decided.
+struct BinFP {
+  float fmin32;
+  float invd32;   // 1/delta, or -1 when delta == 0 (degenerate grid)
+  float err;      // error bound of v in bins; > 1e6 means "never decide by FP32"
+  float pad;
+};
+
+// FP32 bin coordinate lower/upper bounds for x in [xlo, xhi].
+__device__ __forceinline__ void bin_coord(const BinFP &b, float xlo, float xhi, float &vlo,
+                                          float &vhi) {
+  vlo = __fsub_rd(__fmul_rd(__fsub_rd(xlo, b.fmin32), b.invd32), b.err);
+  vhi = __fadd_ru(__fmul_ru(__fsub_ru(xhi, b.fmin32), b.invd32), b.err);
+}
+
+// Lower end: ceil(v) clamped into [0, tau] (a lower bound of both c and j).
+__device__ __forceinline__ int bin_lo(float v, int tau) {
+  if (!(v > 0.0f)) return 0;            // also catches NaN
+  if (v >= (float)tau) return tau;
+  return (int)ceilf(v);
+}
+
+// Upper end: floor(v) + 1 clamped into [0, tau] (an upper bound of both c and j).
+__device__ __forceinline__ int bin_hi(float v, int tau) {
+  if (!(v >= 0.0f)) return v == v ? 0 : tau;
+  if (v >= (float)tau) return tau;
+  return (int)floorf(v) + 1;
+}
+
+// Rigorous interval [jlo, jhi] containing j(x) = #{t_i <= x} and c(x) = #{t_i < x}
+// for every x in [xlo, xhi].  jlo == jhi means both are decided and equal.
+// fmin is the FP64 grid origin, used only when delta == 0.
+__device__ __forceinline__ void bin_interval(const BinFP &b, double fmin, int tau, float xlo,
+                                             float xhi, int &jlo, int &jhi) {
+  if (b.invd32 < 0.0f) {  // delta == 0: all thresholds equal f_min
+    jlo = ((double)xlo > fmin) ? tau : 0;
+    jhi = ((double)xhi >= fmin) ? tau : 0;
+    return;
+  }
+  if (b.err > 1e6f) { jlo = 0; jhi = tau; return; }
+  float vlo, vhi;
+  bin_coord(b, xlo, xhi, vlo, vhi);
+  jlo = bin_lo(vlo, tau);
+  jhi = bin_hi(vhi, tau);
+}
+
+// FP32 screen bound: |fma-chain(u,x) - s(u,x)| <= cfac * |u| * |x| with
+// cfac = ((d + 4) 2^-24 + d 2^-53 + 2^-40)(1 + 2^-20); nu, nx are FP32 upper
+// bounds of the Euclidean norms.  The FMA chain rounds once per step, each
+// partial sum is at most sum_k |u_k x_k| <= |u||x| (Cauchy-Schwarz); the extra
+// terms cover the canonical sum's own rounding and the rounding of s_hat -+ b.
+__host__ __device__ __forceinline__ float screen_cfac(int d) {
+  double c = ((double)(d + 4) * 0x1p-24 + (double)d * 0x1p-53 + 0x1p-40) * (1.0 + 0x1p-20);
+  return (float)c * (1.0f + 0x1p-20f);
+}
+
+__device__ __forceinline__ float screen_bound(float cfac, float nu, float nx) {
+  return __fadd_ru(__fmul_ru(__fmul_ru(cfac, nu), nx), 1e-30f);
+}
+
+// Level boundaries: level L holds counts N <= B_L = scale * (2^L - 1).
+__host__ __device__ __forceinline__ uint64_t level_bound(int L, uint32_t scale) {
+  return (uint64_t)scale * (((uint64_t)1 << L) - 1);
+}
+
+// Order-preserving key of a non-negative double.
+__device__ __forceinline__ uint64_t dkey(double x) { return (uint64_t)__double_as_longlong(x); }
+
+}  // namespace rkr

@@ -1,0 +1,89 @@
+// index.cuh -- the device-resident index behind rkr_index.
+#pragma once
+
+#include "common.cuh"
+
+struct rkr_index {
+  // sizes
+  int64_t n = 0, m = 0;
+  int d = 0;
+  int tau = 0, omega = 0, s = 0;
+  int fbounds = 0;
+  int has_exact = 0;
+  int floor_rank = 0;
+  int nsamp = 0;
+  int nlev_a = 0;  // levels used with the sampled table (scale s)
+  int nlev_x = 0;  // levels used with the exact table (scale 1)
+
+  // items and users (device)
+  float *U = nullptr;        // n x d, caller order
+  float *Ps = nullptr;       // m x d, sorted by (descending norm, index)
+  float *PT = nullptr;       // d x m, transpose of Ps (coalesced item streaming)
+  int32_t *perm = nullptr;   // m: original index of sorted position
+  double *pnorm = nullptr;   // m: FP64 norm, original order
+  float *unrm = nullptr;     // n: FP32 upper bound of ||u||
+  float *pnrm_s = nullptr;   // m: FP32 upper bound of ||p||, sorted order
+  float pmax = 0.0f;         // max over P of the FP32 norm bounds (host copy)
+
+  // sampled rank table (Alg. 1)
+  double *fmin = nullptr, *fmax = nullptr, *delta = nullptr;  // n
+  rkr::BinFP *binfp = nullptr;                                 // n, built with R = pmax
+  uint32_t *N = nullptr;       // n x tau numerators, T-hat = 1 + N / s
+  int16_t *JU = nullptr;       // n x 32 level starts of the upper bound (sampled table)
+  int16_t *JL = nullptr;       // n x 32 level starts of the lower bound
+  float *S = nullptr;          // nsamp x d sampled rows, bucket after bucket
+  float *snrm = nullptr;       // nsamp FP32 norm bounds
+  uint32_t *sw = nullptr;      // nsamp weights (|P_l| or s)
+  int32_t *samp_items = nullptr;  // nsamp original item index
+
+  // exact count table
+  uint32_t *XLO = nullptr, *XHI = nullptr;  // n x tau
+  int16_t *XJU = nullptr, *XJL = nullptr;   // n x 32
+  int32_t *xfloor = nullptr;                // n
+
+  // device time of the build stages (ms): items (norms, sort, gather), samples,
+  // f-bounds, rank table, level tables, exact table, total
+  double build_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace rkr {
+
+// Free everything the index owns.
+void index_release(rkr_index *idx);
+
+// Build steps (build.cu).  All run on `st`.
+rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
+                       const rkr_build_params *prm, const int32_t *sample_pos_host,
+                       cudaStream_t st);
+
+// Per-batch bin parameters for values bounded by ||u|| * R.
+rkr_status make_binfp(const rkr_index *idx, float R, BinFP *out, cudaStream_t st);
+
+// Row norms: FP64 canonical norms (optional) and FP32 upper bounds.
+rkr_status row_norms(const float *X, int64_t rows, int d, double *nrm64, float *nrm32,
+                     cudaStream_t st);
+
+// Largest element of a float array (device -> host), used for norm bounds.
+rkr_status max_float(const float *x, int64_t count, float *out_host, cudaStream_t st);
+
+// Check that every element is finite; *ok_host = 1 if so.
+rkr_status all_finite(const float *x, int64_t count, int *ok_host, cudaStream_t st);
+
+// Device views of one query batch.
+struct QueryCommon {
+  float *Qd;          // nq x d
+  float *qnrm;        // nq FP32 norm bounds
+  int32_t *kq_d;      // nq
+  int64_t *out_off_d; // nq + 1 output offsets
+  BinFP *bf;          // n bin parameters valid for this batch
+};
+
+rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq, double c,
+                            int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
+                            int32_t *case_d, int32_t *nc_d, rkr_query_stats *stats,
+                            cudaStream_t st);
+rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
+                           int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
+                           cudaStream_t st);
+
+}  // namespace rkr

@@ -1,0 +1,874 @@
+// query.cu -- query processing for both paths.
+//
+// Both paths share one plan.  For every user u the index holds a table of
+// rank bounds on the threshold grid t_1..t_tau of u (the sampled table N of
+// Alg. 1 for the c-approximate path; the exact count bounds XLO/XHI for the
+// exact path) and two level tables JU/JL that turn a bin j into the rank level
+// 2^L the table implies.  A query batch is processed as
+//   pass 1  u.q screened for every (u, q) -> bin interval [jlo, jhi] ->
+//           per-query histograms of the upper-bound level and the lower-bound level
+//   cutoff  L*(q) = smallest level holding k upper bounds: R_up_k (approximate
+//           path) or the k-th smallest rank (exact path) is at most 2^L* on the scale
+//   pass 2  u.q screened again; users whose lower bound may reach 2^L* are
+//           written to the candidate list of q (all others provably cannot matter)
+//   resolve canonical FP64 u.q for each candidate; exact bin and table values
+//           (approximate) or an exact recount of the rank over P (exact)
+//   select  one CTA per query: Section 4.3 steps 1-3 (approximate) or the k
+//           smallest (rank, index) (exact) over the candidates.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "index.cuh"
+#include "select.cuh"
+#include "simt.cuh"
+
+namespace rkr {
+
+constexpr int kQT = 32;     // queries per tile in the screening passes
+constexpr int kLevStride = 33;
+
+// #{L : arr[L] > x} for a non-increasing array of 32 entries ending in -1.
+__device__ __forceinline__ int count_gt(const int *arr, int x) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1)
+    if (arr[lo + step - 1] > x) lo += step;
+  return lo;
+}
+
+// Screening pass over all (user, query) pairs of queries [qa, qb).
+// PASS 1 accumulates level histograms; PASS 2 writes candidates.
+template <int PASS>
+__global__ void __launch_bounds__(128)
+    k_theta(const float *__restrict__ U, int64_t n, int d, const float *__restrict__ unrm,
+            const float *__restrict__ Q, const float *__restrict__ qnrm, int qa, int qb,
+            const double *__restrict__ fmin, const BinFP *__restrict__ binfp, int tau,
+            const int16_t *__restrict__ JU, const int16_t *__restrict__ JL,
+            uint32_t *__restrict__ hist_up, uint32_t *__restrict__ hist_lo,
+            const int32_t *__restrict__ lstar, const int64_t *__restrict__ qoff,
+            uint32_t *__restrict__ qcursor, int32_t *__restrict__ cand_u,
+            int32_t *__restrict__ cand_q) {
+  extern __shared__ float smem[];
+  float *Us = smem;                                  // [d][128]
+  float *Qs = Us + (size_t)d * 128;                  // [d][kQT]
+  int *Js = (int *)(Qs + (size_t)d * kQT);           // [128][33] JU then [128][33] JL
+  int *Hs = Js + 2 * 128 * kLevStride;               // PASS 1: [kQT][32] up, [kQT][32] lo
+  const int t = threadIdx.x;
+  const int64_t u0 = (int64_t)blockIdx.x * 128;
+  const int64_t u = u0 + t;
+  const bool active = u < n;
+  load_users_T(U, n, d, u0, Us);
+  for (int L = 0; L < 32; ++L) {
+    Js[t * kLevStride + L] = active ? JU[u * kMaxLevels + L] : -1;
+    Js[128 * kLevStride + t * kLevStride + L] = active ? JL[u * kMaxLevels + L] : -1;
+  }
+  if (PASS == 1)
+    for (int i = t; i < 2 * kQT * 32; i += blockDim.x) Hs[i] = 0;
+  const float cfac = screen_cfac(d);
+  const float nu = active ? unrm[u] : 0.0f;
+  BinFP bf = active ? binfp[u] : BinFP{0.f, 1.f, 2e6f, 0.f};
+  const double fm = active ? fmin[u] : 0.0;
+  const int *ju = Js + t * kLevStride;
+  const int *jl = Js + 128 * kLevStride + t * kLevStride;
+  for (int q0 = qa; q0 < qb; q0 += kQT) {
+    __syncthreads();
+    load_items_T<kQT>(Q, qb, d, q0, Qs);
+    __syncthreads();
+    float acc[kQT];
+    tile_dots<kQT>(Us, Qs, d, t, acc);
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < kQT; ++j) {
+        int q = q0 + j;
+        if (q < qb) {
+          float b = screen_bound(cfac, nu, qnrm[q]);
+          int jlo, jhi;
+          bin_interval(bf, fm, tau, __fsub_rd(acc[j], b), __fadd_ru(acc[j], b), jlo, jhi);
+          if (PASS == 1) {
+            int lu = count_gt(ju, jlo);
+            int ll = count_gt(jl, jhi);
+            atomicAdd(&Hs[j * 32 + lu], 1);
+            atomicAdd(&Hs[kQT * 32 + j * 32 + ll], 1);
+          } else {
+            if (jhi >= jl[lstar[q]]) {
+              uint32_t pos = atomicAdd(&qcursor[q], 1u);
+              int64_t at = qoff[q] + pos;
+              cand_u[at] = (int32_t)u;
+              cand_q[at] = q;
+            }
+          }
+        }
+      }
+    }
+    if (PASS == 1) {
+      __syncthreads();
+      for (int i = t; i < kQT * 32; i += blockDim.x) {
+        int j = i >> 5, L = i & 31;
+        int q = q0 + j;
+        int a = Hs[i], b = Hs[kQT * 32 + i];
+        if (q < qb) {
+          if (a) atomicAdd(&hist_up[(int64_t)q * 32 + L], (uint32_t)a);
+          if (b) atomicAdd(&hist_lo[(int64_t)q * 32 + L], (uint32_t)b);
+        }
+        Hs[i] = 0;
+        Hs[kQT * 32 + i] = 0;
+      }
+    }
+  }
+}
+
+// Cutoff level and candidate count of each query.
+__global__ void k_cutoff(int nq, const uint32_t *__restrict__ hist_up,
+                         const uint32_t *__restrict__ hist_lo, const int32_t *__restrict__ kq,
+                         int nlev, int32_t *__restrict__ lstar, int64_t *__restrict__ ncand) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  uint64_t cum = 0;
+  int L = nlev - 1;
+  for (int l = 0; l < 32; ++l) {
+    cum += hist_up[(int64_t)q * 32 + l];
+    if (cum >= (uint64_t)kq[q]) { L = l; break; }
+  }
+  if (L > nlev - 1) L = nlev - 1;
+  uint64_t c = 0;
+  for (int l = 0; l <= L; ++l) c += hist_lo[(int64_t)q * 32 + l];
+  lstar[q] = L;
+  ncand[q] = (int64_t)c;
+}
+
+// --------------------------------------------------------- approximate path
+
+__global__ void k_resolve_approx(int64_t count, const int32_t *__restrict__ cu,
+                                 const int32_t *__restrict__ cq, const float *__restrict__ U,
+                                 const float *__restrict__ Q, int d,
+                                 const double *__restrict__ fmin,
+                                 const double *__restrict__ delta, const uint32_t *__restrict__ N,
+                                 int tau, uint32_t top, double *__restrict__ th,
+                                 int32_t *__restrict__ cj, uint32_t *__restrict__ nlo,
+                                 uint32_t *__restrict__ nup) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  int64_t u = cu[i];
+  int q = cq[i];
+  double theta = canon_dot(U + u * d, Q + (int64_t)q * d, d);
+  int j = exact_j(theta, fmin[u], delta[u], tau);
+  th[i] = theta;
+  cj[i] = j;
+  nlo[i] = j < tau ? N[u * tau + j] : 0u;
+  nup[i] = j >= 1 ? N[u * tau + j - 1] : top;
+}
+
+// Step-3 estimate (Section 4.3): linear in u.q between (t_j, r_up) and (t_{j+1}, r_low).
+__device__ __forceinline__ double interp_est(double theta, int j, uint32_t nlo, uint32_t nup,
+                                             double fm, double dl, int tau, uint32_t s) {
+  double r_up = __dadd_rn(1.0, __ddiv_rn((double)nup, (double)s));
+  double r_low = __dadd_rn(1.0, __ddiv_rn((double)nlo, (double)s));
+  if (j >= 1 && j <= tau - 1) {
+    double tj = thr_at(fm, dl, j - 1);
+    double tj1 = thr_at(fm, dl, j);
+    double frac = __ddiv_rn(__dsub_rn(theta, tj), __dsub_rn(tj1, tj));
+    return __dsub_rn(r_up, __dmul_rn(__dsub_rn(r_up, r_low), frac));
+  }
+  return r_up;
+}
+
+struct ApproxCand {
+  const int32_t *uid;
+  const uint32_t *nlo, *nup;
+  const double *th;
+  const int32_t *j;
+};
+
+constexpr int kSelThreads = 256;
+
+// One CTA per query: steps 1-3 of Section 4.3 over the query's candidates.
+__global__ void __launch_bounds__(kSelThreads)
+    k_select_approx(int qa, const int64_t *__restrict__ qoff, ApproxCand C,
+                    const int32_t *__restrict__ kq, double c, uint32_t s, int tau,
+                    const double *__restrict__ fmin, const double *__restrict__ delta,
+                    const int64_t *__restrict__ out_off, int32_t *__restrict__ out_users,
+                    uint32_t *__restrict__ out_nlo, uint32_t *__restrict__ out_nup,
+                    double *__restrict__ out_est, int32_t *__restrict__ out_case,
+                    int32_t *__restrict__ out_nc) {
+  extern __shared__ unsigned char sbuf[];
+  SortEnt *ent = (SortEnt *)sbuf;                   // kMaxK entries
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t bc[2];
+  __shared__ unsigned long long cnt_acc;
+  __shared__ int gcount;
+  const int q = qa + blockIdx.x;
+  const int64_t base = qoff[q] - qoff[qa];
+  const int64_t cnt = qoff[q + 1] - qoff[q];
+  const int k = kq[q];
+  const int32_t *uid = C.uid + base;
+  const uint32_t *nlo = C.nlo + base, *nup = C.nup + base;
+  const double *th = C.th + base;
+  const int32_t *cj = C.j + base;
+  auto est_of = [&](int64_t i) {
+    int32_t u = uid[i];
+    return interp_est(th[i], cj[i], nlo[i], nup[i], fmin[u], delta[u], tau, s);
+  };
+  // Step 1: k-th smallest lower and upper bound numerators.
+  uint64_t Rlo = block_kth(cnt, (uint64_t)k, 32,
+                           [&](int64_t i, uint64_t &key) { key = nlo[i]; return true; }, hist, bc);
+  uint64_t Rup = block_kth(cnt, (uint64_t)k, 32,
+                           [&](int64_t i, uint64_t &key) { key = nup[i]; return true; }, hist, bc);
+  const double lhs = c * (double)((uint64_t)s + Rlo);
+  const bool caseA = lhs >= (double)((uint64_t)s + Rup);
+  const int64_t obase = out_off[q];
+  int nc;
+  if (caseA) {
+    // k smallest (r_up, r_low, index): all with nup < Rup, then ties by (nlo, index)
+    int64_t below = block_count(cnt, [&](int64_t i) { return (uint64_t)nup[i] < Rup; }, &cnt_acc);
+    uint64_t kth2 = ~0ull;
+    if (below < k)
+      kth2 = block_kth(cnt, (uint64_t)(k - below), 64,
+                       [&](int64_t i, uint64_t &key) {
+                         key = ((uint64_t)nlo[i] << 32) | (uint32_t)uid[i];
+                         return (uint64_t)nup[i] == Rup;
+                       },
+                       hist, bc);
+    if (threadIdx.x == 0) gcount = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      uint64_t a = nup[i];
+      bool take = a < Rup ||
+                  (a == Rup && (((uint64_t)nlo[i] << 32) | (uint32_t)uid[i]) <= kth2);
+      if (take) {
+        int pos = atomicAdd(&gcount, 1);
+        if (pos < kMaxK) {
+          ent[pos].k1 = ((uint64_t)nup[i] << 32) | nlo[i];
+          ent[pos].k2 = (uint32_t)uid[i];
+          ent[pos].idx = (int32_t)i;
+        }
+      }
+    }
+    __syncthreads();
+    int got = min(gcount, kMaxK);
+    block_sort(ent, got);
+    for (int r = threadIdx.x; r < got && r < k; r += blockDim.x) {
+      int64_t i = ent[r].idx;
+      out_users[obase + r] = uid[i];
+      if (out_nlo) out_nlo[obase + r] = nlo[i];
+      if (out_nup) out_nup[obase + r] = nup[i];
+      if (out_est) out_est[obase + r] = est_of(i);
+    }
+    nc = k;
+  } else {
+    // U_c = {r_up <= c R_low_k}: fewer than k users, (r_up, r_low, index) order
+    auto in_c = [&](int64_t i) { return (double)((uint64_t)s + nup[i]) <= lhs; };
+    if (threadIdx.x == 0) gcount = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      if (in_c(i)) {
+        int pos = atomicAdd(&gcount, 1);
+        if (pos < kMaxK) {
+          ent[pos].k1 = ((uint64_t)nup[i] << 32) | nlo[i];
+          ent[pos].k2 = (uint32_t)uid[i];
+          ent[pos].idx = (int32_t)i;
+        }
+      }
+    }
+    __syncthreads();
+    nc = min(gcount, kMaxK);
+    block_sort(ent, nc);
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+      int64_t i = ent[r].idx;
+      out_users[obase + r] = uid[i];
+      if (out_nlo) out_nlo[obase + r] = nlo[i];
+      if (out_nup) out_nup[obase + r] = nup[i];
+      if (out_est) out_est[obase + r] = est_of(i);
+    }
+    __syncthreads();
+    // Step 3: survivors r_low <= R_up_k outside U_c, smallest (r_hat, index)
+    auto in_t = [&](int64_t i) { return (uint64_t)nlo[i] <= Rup && !in_c(i); };
+    const int need = k - nc;
+    uint64_t ke = block_kth(cnt, (uint64_t)need, 64,
+                            [&](int64_t i, uint64_t &key) {
+                              if (!in_t(i)) return false;
+                              key = dkey(est_of(i));
+                              return true;
+                            },
+                            hist, bc);
+    int64_t below = block_count(cnt, [&](int64_t i) { return in_t(i) && dkey(est_of(i)) < ke; },
+                                &cnt_acc);
+    uint64_t ku = ~0ull;
+    if (below < need)
+      ku = block_kth(cnt, (uint64_t)(need - below), 32,
+                     [&](int64_t i, uint64_t &key) {
+                       if (!in_t(i) || dkey(est_of(i)) != ke) return false;
+                       key = (uint32_t)uid[i];
+                       return true;
+                     },
+                     hist, bc);
+    if (threadIdx.x == 0) gcount = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      if (!in_t(i)) continue;
+      double e = est_of(i);
+      uint64_t ek = dkey(e);
+      if (ek < ke || (ek == ke && (uint64_t)(uint32_t)uid[i] <= ku)) {
+        int pos = atomicAdd(&gcount, 1);
+        if (pos < kMaxK) {
+          ent[pos].k1 = ek;
+          ent[pos].k2 = (uint32_t)uid[i];
+          ent[pos].idx = (int32_t)i;
+        }
+      }
+    }
+    __syncthreads();
+    int got = min(gcount, kMaxK);
+    block_sort(ent, got);
+    for (int r = threadIdx.x; r < got && nc + r < k; r += blockDim.x) {
+      int64_t i = ent[r].idx;
+      out_users[obase + nc + r] = uid[i];
+      if (out_nlo) out_nlo[obase + nc + r] = nlo[i];
+      if (out_nup) out_nup[obase + nc + r] = nup[i];
+      if (out_est) out_est[obase + nc + r] = __longlong_as_double((long long)ent[r].k1);
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (out_case) out_case[q] = caseA ? 1 : 2;
+    if (out_nc) out_nc[q] = nc;
+  }
+}
+
+// -------------------------------------------------------------- exact path
+
+// Canonical u.q of each candidate and its sort key (user, order-preserving u.q).
+__global__ void k_cand_theta(int64_t count, const int32_t *__restrict__ cu,
+                             const int32_t *__restrict__ cq, const float *__restrict__ U,
+                             const float *__restrict__ Q, int d, double *__restrict__ th,
+                             uint64_t *__restrict__ key_hi, uint64_t *__restrict__ key_lo,
+                             int32_t *__restrict__ val, int64_t Np2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Np2) return;
+  if (i >= count) {
+    key_hi[i] = ~0ull;
+    key_lo[i] = ~0ull;
+    val[i] = 0x7fffffff;
+    return;
+  }
+  int64_t u = cu[i];
+  double theta = canon_dot(U + u * d, Q + (int64_t)cq[i] * d, d);
+  th[i] = theta;
+  uint64_t bits = (uint64_t)__double_as_longlong(theta);
+  key_hi[i] = (uint64_t)u;
+  key_lo[i] = (bits >> 63) ? ~bits : (bits | 0x8000000000000000ull);
+  val[i] = (int32_t)i;
+}
+
+// One compare-exchange stage of a bitonic network over ((hi, lo), val).
+__global__ void k_bitonic128(uint64_t *hi, uint64_t *lo, int32_t *val, int64_t N, int64_t j,
+                             int64_t k) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t ixj = i ^ j;
+  if (ixj <= i) return;
+  bool asc = (i & k) == 0;
+  uint64_t ah = hi[i], bh = hi[ixj], al = lo[i], bl = lo[ixj];
+  int32_t va = val[i], vb = val[ixj];
+  bool gt = ah > bh || (ah == bh && (al > bl || (al == bl && va > vb)));
+  if (gt == asc) {
+    hi[i] = bh; hi[ixj] = ah;
+    lo[i] = bl; lo[ixj] = al;
+    val[i] = vb; val[ixj] = va;
+  }
+}
+
+// Segments of equal user in the sorted order: start index and length.
+__global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
+                           unsigned long long *__restrict__ nseg, int64_t *__restrict__ seg_start,
+                           int32_t *__restrict__ seg_len) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  if (i > 0 && key_hi[i] == key_hi[i - 1]) return;
+  int64_t e = i + 1;
+  while (e < count && key_hi[e] == key_hi[i]) ++e;
+  unsigned long long slot = atomicAdd(nseg, 1ull);
+  seg_start[slot] = i;
+  seg_len[slot] = (int32_t)(e - i);
+}
+
+// Exact ranks of grouped candidates.  Thread <-> one user and its block of
+// candidate thresholds theta_0 <= ... < theta_{L-1} (canonical u.q, sorted).
+// For each item the screen gives s in [lo, hi]; pos = #{i : theta_i < s} is
+// decided from the screen when no theta lies in [lo, hi), else from canonical
+// FP64.  hist[pos] += 1; at the end count_i = sum_{pos > i} hist[pos] =
+// #{p : s(u,p) > theta_i}.  Items with hi <= theta_0 exceed no threshold.
+__global__ void __launch_bounds__(128)
+    k_recount_grouped(int64_t nseg, const int64_t *__restrict__ seg_start,
+                      const int32_t *__restrict__ seg_len, const uint64_t *__restrict__ key_hi,
+                      const int32_t *__restrict__ order, const double *__restrict__ th,
+                      const float *__restrict__ U, const float *__restrict__ unrm,
+                      const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int64_t m,
+                      int d, uint32_t *__restrict__ hist, double *__restrict__ ths,
+                      unsigned long long *__restrict__ nties) {
+  extern __shared__ float smem[];
+  float *Us = smem;                    // [d][128]
+  float *Xs = Us + (size_t)d * 128;    // [d][32]
+  const int t = threadIdx.x;
+  const int64_t sg = (int64_t)blockIdx.x * 128 + t;
+  const bool active = sg < nseg;
+  int64_t st0 = 0, uidx = 0;
+  int L = 0;
+  if (active) {
+    st0 = seg_start[sg];
+    L = seg_len[sg];
+    uidx = (int64_t)key_hi[st0];
+  }
+  // users of this CTA's segments, transposed
+  for (int e = t; e < 128 * d; e += blockDim.x) {
+    int tt = e / d, k = e - tt * d;
+    int64_t s2 = (int64_t)blockIdx.x * 128 + tt;
+    float v = 0.0f;
+    if (s2 < nseg) v = U[(int64_t)key_hi[seg_start[s2]] * d + k];
+    Us[k * 128 + tt] = v;
+  }
+  // sorted thresholds of this segment (gathered) and zeroed histogram
+  double *tseg = ths + st0;
+  uint32_t *h = hist + 2 * st0;  // L + 1 slots; segments are disjoint since L >= 1
+  if (active) {
+    for (int i = 0; i < L; ++i) tseg[i] = th[order[st0 + i]];
+    for (int i = 0; i <= L; ++i) h[i] = 0;
+  }
+  const double tmin = active ? tseg[0] : INFINITY;
+  const float tmin_f = __double2float_rd(tmin);  // hi <= tmin_f implies hi <= tmin
+  const float cfac = screen_cfac(d);
+  const float nu = active ? unrm[uidx] : 0.0f;
+  const float *uu = U + uidx * d;
+  uint32_t ties = 0;
+  for (int64_t x0 = 0; x0 < m; x0 += 32) {
+    __syncthreads();
+    load_items_T<32>(Ps, m, d, x0, Xs);
+    __syncthreads();
+    float acc[32];
+    tile_dots<32>(Us, Xs, d, t, acc);
+    if (!active) continue;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      int64_t p = x0 + j;
+      if (p < m) {
+        float b = screen_bound(cfac, nu, pnrm_s[p]);
+        float hi_f = __fadd_ru(acc[j], b);
+        if (hi_f > tmin_f) {
+          double hi = (double)hi_f;
+          double lo = (double)__fsub_rd(acc[j], b);
+          // pa = #{theta < lo}, pb = #{theta < hi}
+          int a0 = 0, a1 = L;
+          while (a0 < a1) { int md = (a0 + a1) >> 1; if (tseg[md] < lo) a0 = md + 1; else a1 = md; }
+          int pa = a0;
+          a1 = L;
+          while (a0 < a1) { int md = (a0 + a1) >> 1; if (tseg[md] < hi) a0 = md + 1; else a1 = md; }
+          int pb = a0, pos = pa;
+          if (pb > pa) {
+            ++ties;
+            double sc = canon_dot_slow(uu, Ps + p * d, d);
+            while (pos < pb && tseg[pos] < sc) ++pos;
+          }
+          h[pos] += 1;
+        }
+      }
+    }
+  }
+  if (!active) return;
+  // suffix sums: h[i] becomes sum_{pos >= i} hist[pos] = count of theta_{i-1}
+  uint32_t run = 0;
+  for (int i = L; i >= 1; --i) {
+    run += h[i];
+    h[i] = run;
+  }
+  if (ties) atomicAdd(nties, (unsigned long long)ties);
+}
+
+// count of candidate order[st0 + i] = hist[2 st0 + i + 1] (see k_recount_grouped).
+__global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_start,
+                                 const int32_t *__restrict__ seg_len,
+                                 const int32_t *__restrict__ order,
+                                 const uint32_t *__restrict__ hist, uint32_t *__restrict__ ccount) {
+  int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (sg >= nseg) return;
+  int64_t st0 = seg_start[sg];
+  int L = seg_len[sg];
+  const uint32_t *h = hist + 2 * st0;
+  for (int i = 0; i < L; ++i) ccount[order[st0 + i]] = h[i + 1];
+}
+
+// One CTA per query: the k smallest (rank, index) among its candidates.
+__global__ void __launch_bounds__(kSelThreads)
+    k_select_exact(int qa, const int64_t *__restrict__ qoff, const int32_t *__restrict__ cuid,
+                   const uint32_t *__restrict__ ccount, const int32_t *__restrict__ kq,
+                   const int64_t *__restrict__ out_off, int32_t *__restrict__ out_users,
+                   int32_t *__restrict__ out_ranks) {
+  extern __shared__ unsigned char sbuf[];
+  SortEnt *ent = (SortEnt *)sbuf;
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t bc[2];
+  __shared__ int gcount;
+  const int q = qa + blockIdx.x;
+  const int64_t base = qoff[q] - qoff[qa];
+  const int64_t cnt = qoff[q + 1] - qoff[q];
+  const int k = kq[q];
+  const int32_t *uid = cuid + base;
+  const uint32_t *cc = ccount + base;
+  uint64_t kth = block_kth(cnt, (uint64_t)k, 64,
+                           [&](int64_t i, uint64_t &key) {
+                             key = ((uint64_t)cc[i] << 32) | (uint32_t)uid[i];
+                             return true;
+                           },
+                           hist, bc);
+  if (threadIdx.x == 0) gcount = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    uint64_t key = ((uint64_t)cc[i] << 32) | (uint32_t)uid[i];
+    if (key <= kth) {
+      int pos = atomicAdd(&gcount, 1);
+      if (pos < kMaxK) {
+        ent[pos].k1 = key;
+        ent[pos].k2 = 0;
+        ent[pos].idx = (int32_t)i;
+      }
+    }
+  }
+  __syncthreads();
+  int got = min(gcount, kMaxK);
+  block_sort(ent, got);
+  const int64_t obase = out_off[q];
+  for (int r = threadIdx.x; r < got && r < k; r += blockDim.x) {
+    out_users[obase + r] = (int32_t)(ent[r].k1 & 0xffffffffu);
+    out_ranks[obase + r] = (int32_t)(ent[r].k1 >> 32) + 1;
+  }
+}
+
+// ------------------------------------------------------------------- host
+
+struct DevBuf {
+  void *p = nullptr;
+  cudaStream_t st = nullptr;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+template <class T>
+static rkr_status tmp_alloc(DevBuf &b, T **out, size_t count, cudaStream_t st) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocAsync(&b.p, count * sizeof(T), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+  }
+  b.st = st;
+  *out = (T *)b.p;
+  return RKR_OK;
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// Shared front half: passes 1 and the cutoff; returns per-query candidate counts.
+struct Plan {
+  std::vector<int64_t> ncand;
+  std::vector<int32_t> lstar;
+};
+
+static size_t theta_smem(int d) {
+  return sizeof(float) * ((size_t)d * 128 + (size_t)d * kQT) + sizeof(int) * 2 * 128 * kLevStride +
+         sizeof(int) * 2 * kQT * 32;
+}
+
+static rkr_status screen_plan(const rkr_index *idx, const float *Qd, const float *qnrm, int nq,
+                              const int32_t *kq_d, const BinFP *bf, const int16_t *JU,
+                              const int16_t *JL, int nlev, cudaStream_t st, int32_t *lstar_d,
+                              int64_t *ncand_d, Plan &plan) {
+  DevBuf bh;
+  uint32_t *hist;
+  RKR_TRY(tmp_alloc(bh, &hist, (size_t)nq * 64, st));
+  RKR_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nq * 64, st));
+  size_t sm = theta_smem(idx->d);
+  RKR_CUDA(cudaFuncSetAttribute(k_theta<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_theta<1><<<(unsigned)((idx->n + 127) / 128), 128, sm, st>>>(
+      idx->U, idx->n, idx->d, idx->unrm, Qd, qnrm, 0, nq, idx->fmin, bf, idx->tau, JU, JL, hist,
+      hist + (size_t)nq * 32, nullptr, nullptr, nullptr, nullptr, nullptr); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  k_cutoff<<<(nq + 127) / 128, 128, 0, st>>>(nq, hist, hist + (size_t)nq * 32, kq_d, nlev,
+                                             lstar_d, ncand_d); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  plan.ncand.resize(nq);
+  plan.lstar.resize(nq);
+  RKR_CUDA(cudaMemcpyAsync(plan.ncand.data(), ncand_d, sizeof(int64_t) * nq,
+                           cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaMemcpyAsync(plan.lstar.data(), lstar_d, sizeof(int32_t) * nq,
+                           cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+// Candidates of queries [qa, qb) into per-query segments.
+static rkr_status emit_candidates(const rkr_index *idx, const float *Qd, const float *qnrm,
+                                  int qa, int qb, const BinFP *bf, const int16_t *JU,
+                                  const int16_t *JL, const int32_t *lstar_d,
+                                  const int64_t *qoff_d, uint32_t *cursor_d, int32_t *cand_u,
+                                  int32_t *cand_q, cudaStream_t st) {
+  size_t sm = theta_smem(idx->d);
+  RKR_CUDA(cudaFuncSetAttribute(k_theta<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_theta<2><<<(unsigned)((idx->n + 127) / 128), 128, sm, st>>>(
+      idx->U, idx->n, idx->d, idx->unrm, Qd, qnrm, qa, qb, idx->fmin, bf, idx->tau, JU, JL,
+      nullptr, nullptr, lstar_d, qoff_d, cursor_d, cand_u, cand_q); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+// Group queries into chunks whose candidate total stays within budget.
+static std::vector<std::pair<int, int>> chunk_queries(const std::vector<int64_t> &ncand,
+                                                      int64_t budget) {
+  std::vector<std::pair<int, int>> out;
+  int nq = (int)ncand.size();
+  int a = 0;
+  while (a < nq) {
+    int64_t tot = 0;
+    int b = a;
+    while (b < nq && (b == a || tot + ncand[b] <= budget)) tot += ncand[b++];
+    out.push_back({a, b});
+    a = b;
+  }
+  return out;
+}
+
+static int64_t candidate_budget() { return (int64_t)1 << 26; }
+
+
+
+// Exact ranks of `cnt` candidates (cu, cq): canonical u.q, sort by (user, u.q),
+// one grouped pass over P per user.  ccount[i] = #{p : s(u_i, p) > u_i.q_i}.
+static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int64_t cnt,
+                                     const int32_t *cu, const int32_t *cq, uint32_t *ccount,
+                                     unsigned long long *ties_d, cudaStream_t st) {
+  int64_t Np2 = 1;
+  while (Np2 < cnt) Np2 <<= 1;
+  DevBuf b1, b2, b3, b4, b5, b6, b7, b8, b9;
+  double *th, *ths;
+  uint64_t *khi, *klo;
+  int32_t *val, *slen;
+  int64_t *sstart;
+  uint32_t *hist;
+  unsigned long long *nseg_d;
+  RKR_TRY(tmp_alloc(b1, &th, cnt, st));
+  RKR_TRY(tmp_alloc(b2, &khi, Np2, st));
+  RKR_TRY(tmp_alloc(b3, &klo, Np2, st));
+  RKR_TRY(tmp_alloc(b4, &val, Np2, st));
+  RKR_TRY(tmp_alloc(b5, &sstart, cnt, st));
+  RKR_TRY(tmp_alloc(b6, &slen, cnt, st));
+  RKR_TRY(tmp_alloc(b7, &hist, 2 * cnt, st));
+  RKR_TRY(tmp_alloc(b8, &ths, cnt, st));
+  RKR_TRY(tmp_alloc(b9, &nseg_d, 1, st));
+  const int bs = 256;
+  k_cand_theta<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(cnt, cu, cq, idx->U, Qd, idx->d,
+                                                                th, khi, klo, val, Np2); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  for (int64_t k = 2; k <= Np2; k <<= 1)
+    for (int64_t j = k >> 1; j > 0; j >>= 1) {
+      k_bitonic128<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(khi, klo, val, Np2, j, k); note_launch();
+    }
+  RKR_CUDA(cudaGetLastError());
+  RKR_CUDA(cudaMemsetAsync(nseg_d, 0, sizeof(unsigned long long), st));
+  k_segments<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, khi, nseg_d, sstart, slen); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  unsigned long long nseg = 0;
+  RKR_CUDA(cudaMemcpyAsync(&nseg, nseg_d, sizeof(nseg), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  size_t sm = sizeof(float) * ((size_t)idx->d * 128 + (size_t)idx->d * 32);
+  RKR_CUDA(cudaFuncSetAttribute(k_recount_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm));
+  k_recount_grouped<<<(unsigned)((nseg + 127) / 128), 128, sm, st>>>(
+      (int64_t)nseg, sstart, slen, khi, val, th, idx->U, idx->unrm, idx->Ps, idx->pnrm_s, idx->m,
+      idx->d, hist, ths, ties_d); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  k_scatter_counts<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
+                                                                   val, hist, ccount); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq, double c,
+                            int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
+                            int32_t *case_d, int32_t *nc_d, rkr_query_stats *stats,
+                            cudaStream_t st) {
+  DevBuf bl, bn;
+  int32_t *lstar_d;
+  int64_t *ncand_d;
+  RKR_TRY(tmp_alloc(bl, &lstar_d, nq, st));
+  RKR_TRY(tmp_alloc(bn, &ncand_d, nq, st));
+  Plan plan;
+  Timer t1(st);
+  RKR_TRY(screen_plan(idx, qc.Qd, qc.qnrm, nq, qc.kq_d, qc.bf, idx->JU, idx->JL, idx->nlev_a, st,
+                      lstar_d, ncand_d, plan));
+  double ms_theta = t1.stop(), ms_res = 0.0, ms_sel = 0.0;
+  int64_t total = 0;
+  int wide = 0;
+  for (int q = 0; q < nq; ++q) {
+    total += plan.ncand[q];
+    wide += plan.lstar[q] >= idx->nlev_a - 1;
+  }
+  std::vector<int64_t> qoff(nq + 1, 0);
+  for (int q = 0; q < nq; ++q) qoff[q + 1] = qoff[q] + plan.ncand[q];
+  DevBuf bo;
+  int64_t *qoff_d;
+  RKR_TRY(tmp_alloc(bo, &qoff_d, nq + 1, st));
+  RKR_CUDA(cudaMemcpyAsync(qoff_d, qoff.data(), sizeof(int64_t) * (nq + 1),
+                           cudaMemcpyHostToDevice, st));
+  for (auto ch : chunk_queries(plan.ncand, candidate_budget())) {
+    int qa = ch.first, qb = ch.second;
+    int64_t cnt = qoff[qb] - qoff[qa];
+    DevBuf b1, b2, b3, b4, b5, b6, b7, b8;
+    int32_t *cu, *cq, *cj;
+    uint32_t *cursor, *nlo, *nup;
+    double *th;
+    int64_t *qoff_rel;
+    RKR_TRY(tmp_alloc(b1, &cu, cnt, st));
+    RKR_TRY(tmp_alloc(b2, &cq, cnt, st));
+    RKR_TRY(tmp_alloc(b3, &cursor, nq, st));
+    RKR_TRY(tmp_alloc(b4, &th, cnt, st));
+    RKR_TRY(tmp_alloc(b5, &cj, cnt, st));
+    RKR_TRY(tmp_alloc(b6, &nlo, cnt, st));
+    RKR_TRY(tmp_alloc(b7, &nup, cnt, st));
+    RKR_TRY(tmp_alloc(b8, &qoff_rel, nq + 1, st));
+    // offsets relative to the chunk start, so candidate arrays hold only this chunk
+    std::vector<int64_t> rel(nq + 1, 0);
+    for (int q = 0; q <= nq; ++q) rel[q] = qoff[q] - qoff[qa];
+    RKR_CUDA(cudaMemcpyAsync(qoff_rel, rel.data(), sizeof(int64_t) * (nq + 1),
+                             cudaMemcpyHostToDevice, st));
+    RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
+    Timer t2(st);
+    RKR_TRY(emit_candidates(idx, qc.Qd, qc.qnrm, qa, qb, qc.bf, idx->JU, idx->JL, lstar_d,
+                            qoff_rel, cursor, cu, cq, st));
+    ms_theta += t2.stop();
+    Timer t3(st);
+    if (cnt > 0) {
+      k_resolve_approx<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
+          cnt, cu, cq, idx->U, qc.Qd, idx->d, idx->fmin, idx->delta, idx->N, idx->tau,
+          (uint32_t)(idx->m * idx->s), th, cj, nlo, nup); note_launch();
+      RKR_CUDA(cudaGetLastError());
+    }
+    ms_res += t3.stop();
+    Timer t4(st);
+    ApproxCand C{cu, nlo, nup, th, cj};
+    size_t sm = sizeof(SortEnt) * kMaxK;
+    RKR_CUDA(cudaFuncSetAttribute(k_select_approx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+    k_select_approx<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, C, qc.kq_d, c,
+                                                      (uint32_t)idx->s, idx->tau, idx->fmin,
+                                                      idx->delta, qc.out_off_d, users_d, nlo_d,
+                                                      nup_d, est_d, case_d, nc_d); note_launch();
+    RKR_CUDA(cudaGetLastError());
+    ms_sel += t4.stop();
+  }
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->pairs = idx->n * (int64_t)nq;
+    stats->candidates = total;
+    stats->fp64_dots = total;
+    stats->near_ties = 0;
+    stats->wide_queries = wide;
+    stats->ms_theta = ms_theta;
+    stats->ms_resolve = ms_res;
+    stats->ms_select = ms_sel;
+  }
+  return RKR_OK;
+}
+
+rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
+                           int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
+                           cudaStream_t st) {
+  DevBuf bl, bn, bt;
+  int32_t *lstar_d;
+  int64_t *ncand_d;
+  unsigned long long *ties_d;
+  RKR_TRY(tmp_alloc(bl, &lstar_d, nq, st));
+  RKR_TRY(tmp_alloc(bn, &ncand_d, nq, st));
+  RKR_TRY(tmp_alloc(bt, &ties_d, 1, st));
+  RKR_CUDA(cudaMemsetAsync(ties_d, 0, sizeof(unsigned long long), st));
+  Plan plan;
+  Timer t1(st);
+  RKR_TRY(screen_plan(idx, qc.Qd, qc.qnrm, nq, qc.kq_d, qc.bf, idx->XJU, idx->XJL, idx->nlev_x,
+                      st, lstar_d, ncand_d, plan));
+  double ms_theta = t1.stop(), ms_res = 0.0, ms_sel = 0.0;
+  int64_t total = 0;
+  int wide = 0;
+  for (int q = 0; q < nq; ++q) {
+    total += plan.ncand[q];
+    wide += plan.lstar[q] >= idx->nlev_x - 1;
+  }
+  std::vector<int64_t> qoff(nq + 1, 0);
+  for (int q = 0; q < nq; ++q) qoff[q + 1] = qoff[q] + plan.ncand[q];
+  for (auto ch : chunk_queries(plan.ncand, candidate_budget())) {
+    int qa = ch.first, qb = ch.second;
+    int64_t cnt = qoff[qb] - qoff[qa];
+    DevBuf b1, b2, b3, b4, b8;
+    int32_t *cu, *cq;
+    uint32_t *cursor, *ccount;
+    int64_t *qoff_rel;
+    RKR_TRY(tmp_alloc(b1, &cu, cnt, st));
+    RKR_TRY(tmp_alloc(b2, &cq, cnt, st));
+    RKR_TRY(tmp_alloc(b3, &cursor, nq, st));
+    RKR_TRY(tmp_alloc(b4, &ccount, cnt, st));
+    RKR_TRY(tmp_alloc(b8, &qoff_rel, nq + 1, st));
+    std::vector<int64_t> rel(nq + 1, 0);
+    for (int q = 0; q <= nq; ++q) rel[q] = qoff[q] - qoff[qa];
+    RKR_CUDA(cudaMemcpyAsync(qoff_rel, rel.data(), sizeof(int64_t) * (nq + 1),
+                             cudaMemcpyHostToDevice, st));
+    RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
+    Timer t2(st);
+    RKR_TRY(emit_candidates(idx, qc.Qd, qc.qnrm, qa, qb, qc.bf, idx->XJU, idx->XJL, lstar_d,
+                            qoff_rel, cursor, cu, cq, st));
+    ms_theta += t2.stop();
+    Timer t3(st);
+    if (cnt > 0) RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu, cq, ccount, ties_d, st));
+    ms_res += t3.stop();
+    Timer t4(st);
+    size_t sm = sizeof(SortEnt) * kMaxK;
+    RKR_CUDA(cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+    k_select_exact<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cu, ccount, qc.kq_d,
+                                                     qc.out_off_d, users_d, ranks_d); note_launch();
+    RKR_CUDA(cudaGetLastError());
+    ms_sel += t4.stop();
+  }
+  unsigned long long ties = 0;
+  RKR_CUDA(cudaMemcpyAsync(&ties, ties_d, sizeof(ties), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->pairs = idx->n * (int64_t)nq;
+    stats->candidates = total;
+    stats->fp64_dots = total + (int64_t)ties;
+    stats->near_ties = (int64_t)ties;
+    stats->wide_queries = wide;
+    stats->ms_theta = ms_theta;
+    stats->ms_resolve = ms_res;
+    stats->ms_select = ms_sel;
+  }
+  return RKR_OK;
+}
+
+}  // namespace rkr
