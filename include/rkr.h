@@ -138,6 +138,17 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
                             double *out_est, int32_t *out_case, int32_t *out_nc,
                             rkr_query_stats *stats, void *stream);
 
+/*
+ * rkr_screen_scores: the tensor-core screen on its own, for validation and for
+ * measuring the screen error.  For every pair (U_i, X_j) writes the screened
+ * score out_s[i * mx + j] (BF16 inputs, FP32 accumulation on tcgen05; split = 1
+ * uses the three-term hi/lo product) and out_b[i * mx + j], the rigorous bound
+ * the library uses for |out_s - s(U_i, X_j)|.  U: n x d, X: mx x d float32.
+ * Meant for small n * mx (the outputs are dense).
+ */
+rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t mx, int32_t d,
+                             int32_t split, float *out_s, float *out_b, void *stream);
+
 /* What rkr_index_export copies out. */
 typedef enum {
   RKR_EXPORT_PERM = 1,      /* int32[m]: original item index of each norm-sorted position */

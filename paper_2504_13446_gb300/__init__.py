@@ -87,6 +87,8 @@ def load() -> ctypes.CDLL:
         lib.rkr_index_timings.argtypes = [V, ctypes.POINTER(ctypes.c_double), I32]
         lib.rkr_kernel_launches.restype = ctypes.c_uint64
         lib.rkr_kernel_launches.argtypes = []
+        lib.rkr_screen_scores.restype = I32
+        lib.rkr_screen_scores.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
         lib.rkr_last_error.restype = ctypes.c_char_p
         lib.rkr_version.restype = ctypes.c_char_p
         _lib = lib
@@ -205,6 +207,20 @@ def rkr_query_approx(index, Q, k, c: float, *, device: bool = False, stream=None
     out["offsets"] = off
     out["stats"] = stats
     return out
+
+
+def rkr_screen_scores(U, X, *, split: bool = False, stream=None):
+    """Tensor-core screened scores and their error bounds for every pair (n x mx each)."""
+    lib = load()
+    n, d = _shape(U)
+    mx, _ = _shape(X)
+    pu, ku = _ptr(U, np.float32)
+    px, kx = _ptr(X, np.float32)
+    s = np.empty((n, mx), dtype=np.float32)
+    b = np.empty((n, mx), dtype=np.float32)
+    _check(lib.rkr_screen_scores(pu, n, px, mx, d, int(split), s.ctypes.data_as(ctypes.c_void_p),
+                                 b.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return s, b
 
 
 @dataclass

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "index.cuh"
+#include "tcops.cuh"
 
 namespace rkr {
 
@@ -328,6 +329,43 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
   RKR_TRY(oes.finish());
   RKR_TRY(oca.finish());
   RKR_TRY(onc.finish());
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t mx, int32_t d,
+                             int32_t split, float *out_s, float *out_b, void *stream) {
+  g_err[0] = 0;
+  if (!U || !X || !out_s || !out_b) return fail(RKR_EINVAL, "null argument");
+  if (n < 1 || mx < 1 || d < 1 || d > kMaxD) return fail(RKR_EINVAL, "bad sizes");
+  if (n * mx > ((int64_t)1 << 31)) return fail(RKR_EINVAL, "n * mx too large");
+  RKR_TRY(check_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  InView vu, vx;
+  RKR_TRY(vu.init(U, sizeof(float) * n * d, st));
+  RKR_TRY(vx.init(X, sizeof(float) * mx * d, st));
+  OutView os, ob;
+  RKR_TRY(os.init(out_s, sizeof(float) * n * mx, st));
+  RKR_TRY(ob.init(out_b, sizeof(float) * n * mx, st));
+  TcSide A, B;
+  struct Guard {
+    TcSide *a, *b;
+    ~Guard() { tc_free(*a); tc_free(*b); }
+  } g{&A, &B};
+  RKR_TRY(tc_stage((const float *)vu.dev, n, d, A, st));
+  RKR_TRY(tc_stage((const float *)vx.dev, mx, d, B, st));
+  int *err;
+  RKR_CUDA(cudaMallocAsync(&err, sizeof(int), st));
+  RKR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  rkr_status r = tc_scores(A, B, split ? 1 : 0, (float *)os.dev, (float *)ob.dev, err, st);
+  int herr = 0;
+  cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(err, st);
+  RKR_CUDA(cudaStreamSynchronize(st));
+  RKR_TRY(r);
+  if (herr) return fail(RKR_ETIMEOUT, "screen kernel wait timed out (code %d)", herr);
+  RKR_TRY(os.finish());
+  RKR_TRY(ob.finish());
   RKR_CUDA(cudaStreamSynchronize(st));
   return RKR_OK;
 }

@@ -1,0 +1,223 @@
+// screen.cu -- BF16 staging, TMA maps, and the tensor-core screens.
+#include <math.h>
+
+#include <algorithm>
+
+#include "index.cuh"
+#include "tcops.cuh"
+
+namespace rkr {
+
+// ---------------------------------------------------------------- staging
+
+// hi = bf16(x), lo = bf16(x - hi) (x - hi and x - hi - lo are exact in FP32),
+// zero padding up to kp, and the bound terms of single and split products
+// (FP64 sums, square roots rounded up to FP32).
+__global__ void k_stage_bf16(const float *__restrict__ X, int64_t rows, int d, int kp,
+                             __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+                             tc::RowBound *__restrict__ rb1, tc::RowBound *__restrict__ rb3) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const float *x = X + i * d;
+  double sx = 0, sh = 0, sl = 0, se1 = 0, se3 = 0, sc = 0;
+  for (int k = 0; k < kp; ++k) {
+    float v = k < d ? x[k] : 0.0f;
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    float hf = __bfloat162float(h);
+    float r1 = v - hf;
+    __nv_bfloat16 l = __float2bfloat16_rn(r1);
+    float lf = __bfloat162float(l);
+    float r3 = r1 - lf;
+    hi[i * kp + k] = h;
+    lo[i * kp + k] = l;
+    sx += (double)v * v;
+    sh += (double)hf * hf;
+    sl += (double)lf * lf;
+    se1 += (double)r1 * r1;
+    se3 += (double)r3 * r3;
+    double c = (double)hf + (double)lf;
+    sc += c * c;
+  }
+  auto up = [](double s) { return __double2float_ru(sqrt(s) * (1.0 + 0x1p-40) + 1e-300); };
+  tc::RowBound a, b;
+  a.a0 = up(se1); a.a1 = up(sh); a.a2 = up(sx); a.a3 = 0.0f; a.a4 = up(sh);
+  b.a0 = up(se3); b.a1 = up(sc); b.a2 = up(sx); b.a3 = up(sl);
+  b.a4 = __fadd_ru(up(sh), up(sl));
+  rb1[i] = a;
+  rb3[i] = b;
+}
+
+rkr_status tc_stage(const float *X, int64_t rows, int d, TcSide &out, cudaStream_t st) {
+  out.rows = rows;
+  out.d = d;
+  out.kp = (d + 15) / 16 * 16;
+  size_t cnt = (size_t)std::max<int64_t>(rows, 1) * out.kp;
+  auto alloc = [&](void **p, size_t bytes) -> rkr_status {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    return RKR_OK;
+  };
+  RKR_TRY(alloc((void **)&out.hi, cnt * 2));
+  RKR_TRY(alloc((void **)&out.lo, cnt * 2));
+  RKR_TRY(alloc((void **)&out.rb1, sizeof(tc::RowBound) * std::max<int64_t>(rows, 1)));
+  RKR_TRY(alloc((void **)&out.rb3, sizeof(tc::RowBound) * std::max<int64_t>(rows, 1)));
+  out.owned = true;
+  if (rows > 0) {
+    k_stage_bf16<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(X, rows, d, out.kp, out.hi,
+                                                                 out.lo, out.rb1, out.rb3);
+    note_launch();
+    RKR_CUDA(cudaGetLastError());
+  }
+  return RKR_OK;
+}
+
+void tc_free(TcSide &s) {
+  if (!s.owned) return;
+  if (s.hi) cudaFree(s.hi);
+  if (s.lo) cudaFree(s.lo);
+  if (s.rb1) cudaFree(s.rb1);
+  if (s.rb3) cudaFree(s.rb3);
+  s.hi = s.lo = nullptr;
+  s.rb1 = s.rb3 = nullptr;
+}
+
+__global__ void k_tile_bounds(const tc::RowBound *__restrict__ rb, int64_t rows, int bn,
+                              int ntiles, tc::RowBound *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  tc::RowBound m{0, 0, 0, 0, 0};
+  for (int64_t i = (int64_t)t * bn; i < std::min<int64_t>(rows, (int64_t)(t + 1) * bn); ++i) {
+    tc::RowBound v = rb[i];
+    m.a0 = fmaxf(m.a0, v.a0); m.a1 = fmaxf(m.a1, v.a1); m.a2 = fmaxf(m.a2, v.a2);
+    m.a3 = fmaxf(m.a3, v.a3); m.a4 = fmaxf(m.a4, v.a4);
+  }
+  out[t] = m;
+}
+
+rkr_status tc_tile_bounds(const TcSide &b, int bn, int split, tc::RowBound **out,
+                          cudaStream_t st) {
+  int ntiles = (int)((b.rows + bn - 1) / bn);
+  cudaError_t e = cudaMallocAsync((void **)out, sizeof(tc::RowBound) * std::max(ntiles, 1), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RKR_ENOMEM, "tile bounds allocation failed");
+  }
+  if (ntiles > 0) {
+    k_tile_bounds<<<(ntiles + 127) / 128, 128, 0, st>>>(split ? b.rb3 : b.rb1, b.rows, bn, ntiles,
+                                                        *out);
+    note_launch();
+    RKR_CUDA(cudaGetLastError());
+  }
+  return RKR_OK;
+}
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached = v > 0 ? v : 1;
+  }
+  return cached;
+}
+
+// ------------------------------------------------------------- TMA maps
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+rkr_status make_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t rows, int kp,
+                    int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(RKR_ECUDA, "cuTensorMapEncodeTiled is not available");
+  if (((uintptr_t)base & 15) != 0 || (kp * 2) % 16 != 0)
+    return fail(RKR_EINTERNAL, "tensor map base or pitch not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)std::max<int64_t>(rows, 1)};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tc::KCH, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(RKR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return RKR_OK;
+}
+
+// --------------------------------------------------------- store epilogue
+
+// Writes every screened score and its bound (validation of the screen).
+struct EpiStore {
+  struct Thread {
+    float b;
+  };
+  static constexpr size_t kSmem = 0;
+  int64_t nrows, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  float gacc, gcan;
+  float *out, *outb;
+  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    int64_t row = (int64_t)rb * tc::BM + r;
+    ts.b = row < nrows ? tc::screen_bound_tc(rowb[row], tileb[ct], gacc, gcan) : 0.0f;
+  }
+  __device__ void chunk(char *, int rb, int ct, int r, int col, const float (&v)[32],
+                        Thread &ts) const {
+    int64_t row = (int64_t)rb * tc::BM + r;
+    if (row >= nrows) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      int64_t c = (int64_t)ct * bn + col + j;
+      if (c < ncols) {
+        out[row * ncols + c] = v[j];
+        outb[row * ncols + c] = ts.b;
+      }
+    }
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+};
+
+rkr_status tc_scores(const TcSide &A, const TcSide &B, int split, float *out, float *outb,
+                     int *err, cudaStream_t st) {
+  constexpr int BN = 256;
+  tc::RowBound *tb = nullptr;
+  RKR_TRY(tc_tile_bounds(B, BN, split, &tb, st));
+  EpiStore e;
+  e.nrows = A.rows;
+  e.ncols = B.rows;
+  e.bn = BN;
+  e.rowb = split ? A.rb3 : A.rb1;
+  e.tileb = tb;
+  e.gacc = tc_gacc(A.kp, split);
+  e.gcan = tc_gcan(A.d);
+  e.out = out;
+  e.outb = outb;
+  rkr_status s =
+      launch_screen<BN, 4>(A, B, split, row_schedule(A.rows, B.rows, BN), e, err, st);
+  cudaFreeAsync(tb, st);
+  return s;
+}
+
+}  // namespace rkr

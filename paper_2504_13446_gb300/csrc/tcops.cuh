@@ -1,0 +1,92 @@
+// tcops.cuh -- BF16 operands of the tensor-core screens and their launch helper.
+#pragma once
+
+#include <cuda.h>
+
+#include "tc_screen.cuh"
+
+namespace rkr {
+
+// One side of a screen: rows of bf16 hi and lo parts (row pitch kp, zero padded
+// beyond d), per-row bound terms for single and split products, and TMA maps.
+struct TcSide {
+  int64_t rows = 0;
+  int d = 0, kp = 0;
+  __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+  tc::RowBound *rb1 = nullptr;   // single product terms
+  tc::RowBound *rb3 = nullptr;   // split product terms
+  bool owned = true;
+};
+
+// Stage float rows into a TcSide (allocates).  rows may be 0.
+rkr_status tc_stage(const float *X, int64_t rows, int d, TcSide &out, cudaStream_t st);
+void tc_free(TcSide &s);
+
+// Per column-tile maxima of the bound terms of a side used as B with tiles of bn rows.
+rkr_status tc_tile_bounds(const TcSide &b, int bn, int split, tc::RowBound **out,
+                          cudaStream_t st);
+
+// Number of SMs of the current device.
+int sm_count();
+
+// Encode a 2-D bf16 tensor map over rows x kp with boxes of 64 x box_rows.
+rkr_status make_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t rows, int kp,
+                    int box_rows);
+
+// Launch the screen kernel over A (users) x B (items or queries).
+template <int BN, int STAGES, class Epi>
+rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::Schedule &sch,
+                         const Epi &epi, int *err_dev, cudaStream_t st) {
+  CUtensorMap mAh, mAl, mBh, mBl;
+  RKR_TRY(make_map(&mAh, A.hi, A.rows, A.kp, tc::BM));
+  RKR_TRY(make_map(&mAl, A.lo, A.rows, A.kp, tc::BM));
+  RKR_TRY(make_map(&mBh, B.hi, B.rows, B.kp, BN));
+  RKR_TRY(make_map(&mBl, B.lo, B.rows, B.kp, BN));
+  tc::Operands op;
+  op.nrows = A.rows;
+  op.ncols = B.rows;
+  op.kchunks = (A.kp + tc::KCH - 1) / tc::KCH;
+  op.ksteps = A.kp / 16;
+  op.split = split;
+  const size_t smem = tc::screen_smem_bytes<BN, STAGES, Epi>();
+  auto kern = tc::k_screen<BN, STAGES, Epi>;
+  RKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int grid = std::min(sch.nunits, sm_count());
+  if (grid < 1) return RKR_OK;
+  kern<<<grid, tc::kThreads, smem, st>>>(mAh, mAl, mBh, mBl, op, sch, epi, err_dev);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+inline tc::Schedule row_schedule(int64_t rows, int64_t cols, int bn) {
+  tc::Schedule s;
+  s.mode = 0;
+  s.nrb = (int)((rows + tc::BM - 1) / tc::BM);
+  s.nct = (int)((cols + bn - 1) / bn);
+  s.parts = 1;
+  s.nunits = s.nrb;
+  return s;
+}
+
+inline tc::Schedule col_schedule(int64_t rows, int64_t cols, int bn, int parts) {
+  tc::Schedule s;
+  s.mode = 1;
+  s.nrb = (int)((rows + tc::BM - 1) / tc::BM);
+  s.nct = (int)((cols + bn - 1) / bn);
+  s.parts = std::max(1, std::min(parts, s.nrb));
+  s.nunits = s.nct * s.parts;
+  return s;
+}
+
+// Accumulation and canonical-rounding factors of the bound for K' products.
+inline float tc_gacc(int kp, int split) {
+  return (float)(2.0 * (double)(kp * (split ? 3 : 1)) * 0x1p-23 * (1.0 + 0x1p-10));
+}
+inline float tc_gcan(int d) { return (float)((double)d * 0x1p-52 * 2.0); }
+
+// Raw screened scores and bounds of every pair (validation of the screen).
+rkr_status tc_scores(const TcSide &A, const TcSide &B, int split, float *out, float *outb,
+                     int *err, cudaStream_t st);
+
+}  // namespace rkr

@@ -1,0 +1,48 @@
+"""The tcgen05 BF16 screen: every screened score lies within its bound of the
+canonical FP64 score, in single (hi.hi) and split (hi.hi + hi.lo + lo.hi) form."""
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+rkr = pytest.importorskip("paper_2504_13446_gb300")
+
+
+def _rows(rng, n, d, sigma=0.7):
+    g = rng.standard_normal((n, d))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    return (g * np.exp(sigma * rng.standard_normal((n, 1)))).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,mx,d", [(300, 700, 32), (129, 257, 100), (260, 513, 200),
+                                    (77, 300, 37), (128, 256, 256)])
+@pytest.mark.parametrize("split", [False, True])
+def test_screen_within_bound(n, mx, d, split):
+    rng = np.random.default_rng(n + mx + d)
+    U, X = _rows(rng, n, d), _rows(rng, mx, d)
+    s, b = rkr.rkr_screen_scores(U, X, split=split)
+    S = oracle.scores(U, X)
+    err = np.abs(s.astype(np.float64) - S)
+    assert np.isfinite(s).all() and (b > 0).all()
+    ratio = err / b
+    assert ratio.max() <= 1.0, f"max error/bound {ratio.max()}"
+    # the bound uses the largest item norm of each 256-column tile
+    xn = np.linalg.norm(X, axis=1)
+    tile_max = np.repeat([xn[i:i + 256].max() for i in range(0, mx, 256)], 256)[:mx]
+    scale = np.linalg.norm(U, axis=1)[:, None] * tile_max[None, :]
+    rel = (b / scale).max()
+    assert rel < (2e-2 if not split else 5e-4), rel
+    # the screen is not trivially loose: typical error far below the bound
+    assert np.median(ratio) < 0.2
+
+
+def test_screen_integer_data_is_exact_when_representable():
+    """Small integers are exact in bf16 and their products sum exactly in FP32."""
+    rng = np.random.default_rng(1)
+    U = rng.integers(-8, 9, size=(140, 48)).astype(np.float32)
+    X = rng.integers(-8, 9, size=(300, 48)).astype(np.float32)
+    s, b = rkr.rkr_screen_scores(U, X)
+    assert (s.astype(np.float64) == oracle.scores(U, X)).all()
