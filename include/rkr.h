@@ -156,16 +156,20 @@ typedef enum {
   RKR_EXPORT_FMAX = 3,      /* double[n] */
   RKR_EXPORT_TABLE = 4,     /* uint32[n * tau]: N[u][j], j = 0..tau-1 */
   RKR_EXPORT_SAMPLES = 5,   /* int32[total samples]: original item index, bucket after bucket */
-  RKR_EXPORT_XLO = 6,       /* uint32[n * tau]: lower bound of #{p : s(u,p) > t_j} */
-  RKR_EXPORT_XHI = 7,       /* uint32[n * tau]: upper bound of the same count */
+  RKR_EXPORT_XCOUNT = 6,    /* uint32[n * G]: #{p : s(u,p) > x_j} on the exact grid (G = 128) */
+  RKR_EXPORT_XGRID = 7,     /* double[n * 2]: (x_0, step) of each user's exact grid,
+                               x_j = x_0 + j * step; x_0 is the threshold t of the sampled
+                               table's last column whose estimated count is >= floor_rank,
+                               x_{G-1} = f_max */
   RKR_EXPORT_PNORM = 8      /* double[m]: FP64 norms of P in original order */
 } rkr_export_what;
 
 /* Copy one internal array to dst (host or device); bytes must equal its size. */
 rkr_status rkr_index_export(const rkr_index *idx, int32_t what, void *dst, int64_t bytes);
 
-/* Sizes of the index: out[0..6] = n, m, d, tau, omega, s, total samples. */
-rkr_status rkr_index_info(const rkr_index *idx, int64_t *out7);
+/* Sizes of the index: out[0..7] = n, m, d, tau, omega, s, total samples,
+ * columns G of the exact grid (0 without exact table). */
+rkr_status rkr_index_info(const rkr_index *idx, int64_t *out8);
 
 /* Device time in ms of the build stages of an index: out[0] items (norms, sort,
  * gather), [1] samples, [2] f_min/f_max, [3] rank table, [4] level tables,

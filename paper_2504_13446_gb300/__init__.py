@@ -29,7 +29,7 @@ __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_ex
 _lock = threading.Lock()
 _lib = None
 
-EXPORTS = dict(perm=1, fmin=2, fmax=3, table=4, samples=5, xlo=6, xhi=7, pnorm=8)
+EXPORTS = dict(perm=1, fmin=2, fmax=3, table=4, samples=5, xcount=6, xgrid=7, pnorm=8)
 _STATUS = {0: "RKR_OK", 1: "RKR_EINVAL", 2: "RKR_ENOMEM", 3: "RKR_ECUDA", 4: "RKR_ETIMEOUT",
            5: "RKR_EUNSUPPORTED", 6: "RKR_EINTERNAL"}
 
@@ -232,6 +232,7 @@ class _Info:
     omega: int
     s: int
     nsamp: int
+    xg: int
 
 
 class Index:
@@ -239,7 +240,7 @@ class Index:
 
     def __init__(self, U, P, **kw):
         self._h: Optional[ctypes.c_void_p] = rkr_build(U, P, **kw)
-        raw = (ctypes.c_int64 * 7)()
+        raw = (ctypes.c_int64 * 8)()
         _check(load().rkr_index_info(self._h, raw))
         self.info = _Info(*[int(v) for v in raw])
 
@@ -253,8 +254,8 @@ class Index:
         i = self.info
         shapes = dict(perm=((i.m,), np.int32), fmin=((i.n,), np.float64),
                       fmax=((i.n,), np.float64), table=((i.n, i.tau), np.uint32),
-                      samples=((i.nsamp,), np.int32), xlo=((i.n, i.tau), np.uint32),
-                      xhi=((i.n, i.tau), np.uint32), pnorm=((i.m,), np.float64))
+                      samples=((i.nsamp,), np.int32), xcount=((i.n, i.xg), np.uint32),
+                      xgrid=((i.n, 2), np.float64), pnorm=((i.m,), np.float64))
         shape, dt = shapes[what]
         a = np.empty(shape, dtype=dt)
         _check(load().rkr_index_export(self._h, EXPORTS[what], a.ctypes.data_as(ctypes.c_void_p),

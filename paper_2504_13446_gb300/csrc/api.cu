@@ -235,12 +235,16 @@ struct QueryStage {
   InView vq, vk;
   float *qnrm = nullptr;
   int64_t *off_d = nullptr;
-  BinFP *bf_own = nullptr;
+  BinFP *bf_own = nullptr, *xbf_own = nullptr;
+  TcSide Qt;
   cudaStream_t st = nullptr;
   ~QueryStage() {
     if (qnrm) cudaFreeAsync(qnrm, st);
     if (off_d) cudaFreeAsync(off_d, st);
     if (bf_own) cudaFreeAsync(bf_own, st);
+    if (xbf_own) cudaFreeAsync(xbf_own, st);
+    cudaStreamSynchronize(st);
+    tc_free(Qt);
   }
 };
 
@@ -266,11 +270,19 @@ static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const in
   qc.kq_d = (int32_t *)qs.vk.dev;
   qc.out_off_d = qs.off_d;
   qc.bf = idx->binfp;
+  qc.xbf = idx->xbin;
   if (qmax > idx->pmax) {  // |u.q| may exceed the range the stored bin bounds assume
     RKR_CUDA(cudaMallocAsync(&qs.bf_own, sizeof(BinFP) * idx->n, st));
     RKR_TRY(make_binfp(idx, qmax, qs.bf_own, st));
     qc.bf = qs.bf_own;
+    if (idx->xbin) {
+      RKR_CUDA(cudaMallocAsync(&qs.xbf_own, sizeof(BinFP) * idx->n, st));
+      RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, idx->xg, qmax, nullptr, qs.xbf_own, st));
+      qc.xbf = qs.xbf_own;
+    }
   }
+  RKR_TRY(tc_stage(qc.Qd, nq, d, qs.Qt, st));
+  qc.Qt = qs.Qt;
   return RKR_OK;
 }
 
@@ -370,8 +382,10 @@ rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t 
   return RKR_OK;
 }
 
-rkr_status rkr_index_info(const rkr_index *idx, int64_t *out7) {
-  if (!idx || !out7) return fail(RKR_EINVAL, "null argument");
+rkr_status rkr_index_info(const rkr_index *idx, int64_t *out8) {
+  if (!idx || !out8) return fail(RKR_EINVAL, "null argument");
+  int64_t *out7 = out8;
+  out8[7] = idx->xg;
   out7[0] = idx->n;
   out7[1] = idx->m;
   out7[2] = idx->d;
@@ -393,8 +407,18 @@ rkr_status rkr_index_export(const rkr_index *idx, int32_t what, void *dst, int64
     case RKR_EXPORT_FMAX: src = idx->fmax; size = 8 * idx->n; break;
     case RKR_EXPORT_TABLE: src = idx->N; size = 4 * idx->n * idx->tau; break;
     case RKR_EXPORT_SAMPLES: src = idx->samp_items; size = 4 * (int64_t)idx->nsamp; break;
-    case RKR_EXPORT_XLO: src = idx->XLO; size = 4 * idx->n * idx->tau; break;
-    case RKR_EXPORT_XHI: src = idx->XHI; size = 4 * idx->n * idx->tau; break;
+    case RKR_EXPORT_XCOUNT: src = idx->XC; size = 4 * idx->n * (int64_t)idx->xg; break;
+    case RKR_EXPORT_XGRID: {
+      if (!idx->xg0) return fail(RKR_EINVAL, "index has no exact table");
+      if (bytes != 16 * idx->n) return fail(RKR_EINVAL, "export %d needs %lld bytes", what,
+                                            (long long)(16 * idx->n));
+      std::vector<double> a(idx->n), b(idx->n), o(2 * idx->n);
+      RKR_CUDA(cudaMemcpy(a.data(), idx->xg0, 8 * idx->n, cudaMemcpyDeviceToHost));
+      RKR_CUDA(cudaMemcpy(b.data(), idx->xdx, 8 * idx->n, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < idx->n; ++i) { o[2 * i] = a[i]; o[2 * i + 1] = b[i]; }
+      RKR_CUDA(cudaMemcpy(dst, o.data(), 16 * idx->n, cudaMemcpyDefault));
+      return RKR_OK;
+    }
     case RKR_EXPORT_PNORM: src = idx->pnorm; size = 8 * idx->m; break;
     default: return fail(RKR_EINVAL, "unknown export %d", what);
   }

@@ -131,19 +131,14 @@ __global__ void k_norm_keys(const double *__restrict__ nrm, int64_t m, int64_t N
   }
 }
 
-// Ps[i] = P[perm[i]], PT[k][i] = Ps[i][k], pnrm_s[i] = pnrm32[perm[i]].
+// Ps[i] = P[perm[i]], pnrm_s[i] = pnrm32[perm[i]].
 __global__ void k_gather_sorted(const float *__restrict__ P, const int32_t *__restrict__ perm,
                                 const float *__restrict__ pn32, int64_t m, int d,
-                                float *__restrict__ Ps, float *__restrict__ PT,
-                                float *__restrict__ pnrm_s) {
+                                float *__restrict__ Ps, float *__restrict__ pnrm_s) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   int64_t src = perm[i];
-  for (int k = 0; k < d; ++k) {
-    float v = P[src * d + k];
-    Ps[i * d + k] = v;
-    PT[(int64_t)k * m + i] = v;
-  }
+  for (int k = 0; k < d; ++k) Ps[i * d + k] = P[src * d + k];
   pnrm_s[i] = pn32[src];
 }
 
@@ -243,6 +238,16 @@ rkr_status make_binfp(const rkr_index *idx, float R, BinFP *out, cudaStream_t st
   k_binfp<<<(unsigned)((idx->n + bs - 1) / bs), bs, 0, st>>>(idx->n, idx->fmin, idx->fmax,
                                                               idx->tau, idx->unrm, R, nullptr,
                                                               out); note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+rkr_status make_binfp_grid(const rkr_index *idx, const double *g0, const double *gmax, int G,
+                           float R, double *delta_out, BinFP *out, cudaStream_t st) {
+  int bs = 256;
+  k_binfp<<<(unsigned)((idx->n + bs - 1) / bs), bs, 0, st>>>(idx->n, g0, gmax, G, idx->unrm, R,
+                                                              delta_out, out);
+  note_launch();
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
 }
@@ -399,92 +404,6 @@ __global__ void k_floor_cols(int64_t n, int tau, const uint32_t *__restrict__ N,
   fl[u] = a > 0 ? a - 1 : 0;
 }
 
-// Warp-per-user exact count table: XLO[j] <= #{p : s(u,p) > t_j} <= XHI[j].
-// Each item's c(s) is known to lie in [clo, chi] from the FP32 screen; items
-// with chi <= floor cannot count for any column >= floor and are skipped.
-constexpr int kXWarps = 8;
-constexpr int kXTile = 64;
-
-__global__ void __launch_bounds__(kXWarps * 32)
-    k_exact_table(const float *__restrict__ U, int64_t n, int d, const float *__restrict__ unrm,
-                  const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int64_t m,
-                  const double *__restrict__ fmin, const BinFP *__restrict__ binfp, int tau,
-                  const int32_t *__restrict__ xfloor, uint32_t *__restrict__ XLO,
-                  uint32_t *__restrict__ XHI) {
-  extern __shared__ float smem[];
-  float *Xs = smem;                                   // [d][kXTile]
-  float *Uw = Xs + (size_t)d * kXTile;                // [warps][d]
-  uint32_t *H = (uint32_t *)(Uw + (size_t)kXWarps * d);  // [warps][2][tau+1]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u = (int64_t)blockIdx.x * kXWarps + warp;
-  const bool active = u < n;
-  uint32_t *Hlo = H + (size_t)warp * 2 * (tau + 1);
-  uint32_t *Hhi = Hlo + (tau + 1);
-  for (int c = lane; c <= tau; c += 32) { Hlo[c] = 0; Hhi[c] = 0; }
-  for (int k = lane; k < d; k += 32) Uw[warp * d + k] = active ? U[u * d + k] : 0.0f;
-  const float cfac = screen_cfac(d);
-  const float nu = active ? unrm[u] : 0.0f;
-  BinFP bf;
-  double fm = 0.0;
-  int fl = 0;
-  if (active) { bf = binfp[u]; fm = fmin[u]; fl = xfloor[u]; }
-  for (int64_t x0 = 0; x0 < m; x0 += kXTile) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < kXTile * d; e += blockDim.x) {
-      int j = e / d, k = e - j * d;
-      int64_t p = x0 + j;
-      Xs[k * kXTile + j] = p < m ? Ps[p * d + k] : 0.0f;
-    }
-    __syncthreads();
-    if (!active) continue;
-    float acc0 = 0.0f, acc1 = 0.0f;
-    const float *uw = Uw + warp * d;
-    for (int k = 0; k < d; ++k) {
-      float uk = uw[k];
-      acc0 = fmaf(uk, Xs[k * kXTile + lane], acc0);
-      acc1 = fmaf(uk, Xs[k * kXTile + lane + 32], acc1);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      int64_t p = x0 + lane + 32 * h;
-      if (p >= m) continue;
-      float sh = h ? acc1 : acc0;
-      float b = screen_bound(cfac, nu, pnrm_s[p]);
-      int clo, chi;
-      bin_interval(bf, fm, tau, __fsub_rd(sh, b), __fadd_ru(sh, b), clo, chi);
-      if (chi <= fl) continue;
-      atomicAdd(&Hlo[max(clo, fl)], 1u);
-      atomicAdd(&Hhi[chi], 1u);
-    }
-  }
-  __syncwarp();
-  if (!active) return;
-  // suffix sums over c, then fill columns below the floor
-  const int chunk = (tau + 1 + 31) / 32;
-  int c0 = lane * chunk, c1 = min(tau + 1, c0 + chunk);
-  uint32_t plo = 0, phi = 0;
-  for (int c = c0; c < c1; ++c) { plo += Hlo[c]; phi += Hhi[c]; }
-  uint32_t ilo = plo, ihi = phi;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t a = __shfl_down_sync(0xffffffffu, ilo, o);
-    uint32_t b2 = __shfl_down_sync(0xffffffffu, ihi, o);
-    if (lane + o < 32) { ilo += a; ihi += b2; }
-  }
-  uint32_t rlo = ilo - plo, rhi = ihi - phi;
-  for (int c = c1 - 1; c >= c0; --c) {
-    rlo += Hlo[c];
-    rhi += Hhi[c];
-    int j = c - 1;
-    if (j >= fl) { XLO[u * tau + j] = rlo; XHI[u * tau + j] = rhi; }
-  }
-  __syncwarp();
-  uint32_t at_floor = XLO[u * tau + fl];
-  for (int j = lane; j < fl; j += 32) {
-    XLO[u * tau + j] = at_floor;
-    XHI[u * tau + j] = (uint32_t)m;
-  }
-}
-
 // ------------------------------------------------------------- sampling
 
 // SplitMix64 (Steele, Lea and Flood, 2014), used only when the caller supplies
@@ -553,12 +472,13 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_TRY(dalloc(&idx->perm, m));
   RKR_CUDA(cudaMemcpyAsync(idx->perm, vals, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
   RKR_TRY(dalloc(&idx->Ps, (size_t)m * d));
-  RKR_TRY(dalloc(&idx->PT, (size_t)m * d));
   RKR_TRY(dalloc(&idx->pnrm_s, m));
   k_gather_sorted<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(P_dev, idx->perm, pn32, m, d,
-                                                               idx->Ps, idx->PT, idx->pnrm_s); note_launch();
+                                                               idx->Ps, idx->pnrm_s); note_launch();
   RKR_CUDA(cudaGetLastError());
   RKR_TRY(max_float(idx->pnrm_s, m, &idx->pmax, st));
+  RKR_TRY(tc_stage(idx->U, n, d, idx->Ut, st));
+  RKR_TRY(tc_stage(idx->Ps, m, d, idx->Pt, st));
   cudaFreeAsync(keys, st);
   cudaFreeAsync(vals, st);
   cudaFreeAsync(pn32, st);
@@ -643,12 +563,20 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_TRY(dalloc(&idx->fmax, n));
   RKR_TRY(dalloc(&idx->delta, n));
   RKR_TRY(dalloc(&idx->binfp, n));
+  bool fb_done = false;
   if (idx->fbounds == 0) {
+    rkr_status fs = tc_fbounds(idx, idx->Ut, idx->Pt, idx->fmin, idx->fmax, st);
+    if (fs == RKR_OK) fb_done = true;
+    else if (fs != RKR_EINTERNAL) return fs;
+    set_error("");
+  }
+  if (idx->fbounds == 0 && !fb_done) {
+    // candidate overflow on the tensor-core path: exact scan on the CUDA cores
     size_t sm = sizeof(float) * ((size_t)d * 128 + (size_t)d * 32);
     RKR_CUDA(cudaFuncSetAttribute(k_fbounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_fbounds<<<(unsigned)((n + 127) / 128), 128, sm, st>>>(idx->U, n, idx->Ps, idx->pnrm_s, m, d,
                                                             idx->unrm, idx->fmin, idx->fmax); note_launch();
-  } else {
+  } else if (idx->fbounds == 1) {
     double pmax64 = 0.0;
     // max FP64 norm: the first item of the sorted order
     int32_t first = 0;
@@ -691,25 +619,20 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_CUDA(cudaEventRecord(ev[5], st));
   // exact count table
   if (idx->has_exact) {
-    RKR_TRY(dalloc(&idx->XLO, (size_t)n * tau));
-    RKR_TRY(dalloc(&idx->XHI, (size_t)n * tau));
+    idx->xg = kXGrid;
     RKR_TRY(dalloc(&idx->xfloor, n));
+    RKR_TRY(dalloc(&idx->xg0, n));
+    RKR_TRY(dalloc(&idx->xdx, n));
+    RKR_TRY(dalloc(&idx->xbin, n));
+    RKR_TRY(dalloc(&idx->XC, (size_t)n * kXGrid));
     k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
                                                                (uint64_t)idx->floor_rank,
                                                                idx->xfloor); note_launch();
-    size_t sm = sizeof(float) * ((size_t)d * kXTile + (size_t)kXWarps * d) +
-                sizeof(uint32_t) * (size_t)kXWarps * 2 * (tau + 1);
-    if (sm > 227 * 1024) return fail(RKR_EINVAL, "tau too large for the exact table kernel");
-    RKR_CUDA(cudaFuncSetAttribute(k_exact_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm));
-    k_exact_table<<<(unsigned)((n + kXWarps - 1) / kXWarps), kXWarps * 32, sm, st>>>(
-        idx->U, n, d, idx->unrm, idx->Ps, idx->pnrm_s, m, idx->fmin, idx->binfp, tau,
-        idx->xfloor, idx->XLO, idx->XHI); note_launch();
-    RKR_CUDA(cudaGetLastError());
+    RKR_TRY(tc_exact_table(idx, idx->Ut, idx->Pt, st, nullptr));
     idx->nlev_x = levels_for((uint64_t)m);
     RKR_TRY(dalloc(&idx->XJU, (size_t)n * kMaxLevels));
     RKR_TRY(dalloc(&idx->XJL, (size_t)n * kMaxLevels));
-    k_levels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, tau, idx->XHI, idx->XLO,
+    k_levels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, kXGrid, idx->XC, idx->XC,
                                                           (uint32_t)m, 1u, idx->nlev_x, idx->XJU,
                                                           idx->XJL); note_launch();
     RKR_CUDA(cudaGetLastError());
@@ -728,12 +651,15 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
 }
 
 void index_release(rkr_index *idx) {
-  void *ptrs[] = {idx->U,      idx->Ps,   idx->PT,   idx->perm, idx->pnorm, idx->unrm,
+  void *ptrs[] = {idx->U,      idx->Ps,   idx->perm, idx->pnorm, idx->unrm,
                   idx->pnrm_s, idx->fmin, idx->fmax, idx->delta, idx->binfp, idx->N,
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
-                  idx->XLO,    idx->XHI,  idx->XJU,  idx->XJL,  idx->xfloor};
+                  idx->xg0,    idx->xdx,  idx->xbin, idx->XC,   idx->XJU,   idx->XJL,
+                  idx->xfloor};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  tc_free(idx->Ut);
+  tc_free(idx->Pt);
 }
 
 }  // namespace rkr

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tcops.cuh"
 
 struct rkr_index {
   // sizes
@@ -18,7 +19,6 @@ struct rkr_index {
   // items and users (device)
   float *U = nullptr;        // n x d, caller order
   float *Ps = nullptr;       // m x d, sorted by (descending norm, index)
-  float *PT = nullptr;       // d x m, transpose of Ps (coalesced item streaming)
   int32_t *perm = nullptr;   // m: original index of sorted position
   double *pnorm = nullptr;   // m: FP64 norm, original order
   float *unrm = nullptr;     // n: FP32 upper bound of ||u||
@@ -36,10 +36,16 @@ struct rkr_index {
   uint32_t *sw = nullptr;      // nsamp weights (|P_l| or s)
   int32_t *samp_items = nullptr;  // nsamp original item index
 
-  // exact count table
-  uint32_t *XLO = nullptr, *XHI = nullptr;  // n x tau
+  // exact count table on the exact grid x_j = xg0 + j * xdx, j = 0 .. xg - 1
+  int xg = 0;
+  double *xg0 = nullptr, *xdx = nullptr;    // n
+  rkr::BinFP *xbin = nullptr;               // n, built with R = pmax
+  uint32_t *XC = nullptr;                   // n x xg: #{p : s(u,p) > x_j}
   int16_t *XJU = nullptr, *XJL = nullptr;   // n x 32
-  int32_t *xfloor = nullptr;                // n
+  int32_t *xfloor = nullptr;                // n: paper column of x_0
+
+  // bf16 operands of the tensor-core screens
+  rkr::TcSide Ut, Pt;
 
   // device time of the build stages (ms): items (norms, sort, gather), samples,
   // f-bounds, rank table, level tables, exact table, total
@@ -56,8 +62,28 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
                        const rkr_build_params *prm, const int32_t *sample_pos_host,
                        cudaStream_t st);
 
-// Per-batch bin parameters for values bounded by ||u|| * R.
+// Per-batch bin parameters for values bounded by ||u|| * R (paper grid).
 rkr_status make_binfp(const rkr_index *idx, float R, BinFP *out, cudaStream_t st);
+
+// Bin parameters of a grid g0 + j * (gmax - g0) / (G - 1), j < G; writes the
+// step to delta_out when it is not null.
+rkr_status make_binfp_grid(const rkr_index *idx, const double *g0, const double *gmax, int G,
+                           float R, double *delta_out, BinFP *out, cudaStream_t st);
+
+// Tensor-core screens (screen_epi.cu).
+rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, double *fmin,
+                      double *fmax, cudaStream_t st);
+rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cudaStream_t st,
+                          int64_t *refined);
+rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
+                         int qa, const BinFP *binfp, const double *fmin, int tau,
+                         const int16_t *JU, const int16_t *JL, uint32_t *hist,
+                         const int32_t *lstar, const int64_t *qoff, uint32_t *qcursor,
+                         int32_t *cand_u, int32_t *cand_q, int split, int *err, cudaStream_t st);
+rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
+                      const int64_t *seg_start, const int32_t *seg_len, const int32_t *seg_user,
+                      const double *ths, uint32_t *hist, cudaStream_t st, int64_t *refined);
+constexpr int kXGrid = 128;
 
 // Row norms: FP64 canonical norms (optional) and FP32 upper bounds.
 rkr_status row_norms(const float *X, int64_t rows, int d, double *nrm64, float *nrm32,
@@ -75,7 +101,9 @@ struct QueryCommon {
   float *qnrm;        // nq FP32 norm bounds
   int32_t *kq_d;      // nq
   int64_t *out_off_d; // nq + 1 output offsets
-  BinFP *bf;          // n bin parameters valid for this batch
+  BinFP *bf;          // n bin parameters of the sampled table's grid, valid for this batch
+  BinFP *xbf;         // n bin parameters of the exact grid, valid for this batch
+  TcSide Qt;          // bf16 operands of the batch
 };
 
 rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq, double c,

@@ -26,98 +26,6 @@
 
 namespace rkr {
 
-constexpr int kQT = 32;     // queries per tile in the screening passes
-constexpr int kLevStride = 33;
-
-// #{L : arr[L] > x} for a non-increasing array of 32 entries ending in -1.
-__device__ __forceinline__ int count_gt(const int *arr, int x) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 16; step > 0; step >>= 1)
-    if (arr[lo + step - 1] > x) lo += step;
-  return lo;
-}
-
-// Screening pass over all (user, query) pairs of queries [qa, qb).
-// PASS 1 accumulates level histograms; PASS 2 writes candidates.
-template <int PASS>
-__global__ void __launch_bounds__(128)
-    k_theta(const float *__restrict__ U, int64_t n, int d, const float *__restrict__ unrm,
-            const float *__restrict__ Q, const float *__restrict__ qnrm, int qa, int qb,
-            const double *__restrict__ fmin, const BinFP *__restrict__ binfp, int tau,
-            const int16_t *__restrict__ JU, const int16_t *__restrict__ JL,
-            uint32_t *__restrict__ hist_up, uint32_t *__restrict__ hist_lo,
-            const int32_t *__restrict__ lstar, const int64_t *__restrict__ qoff,
-            uint32_t *__restrict__ qcursor, int32_t *__restrict__ cand_u,
-            int32_t *__restrict__ cand_q) {
-  extern __shared__ float smem[];
-  float *Us = smem;                                  // [d][128]
-  float *Qs = Us + (size_t)d * 128;                  // [d][kQT]
-  int *Js = (int *)(Qs + (size_t)d * kQT);           // [128][33] JU then [128][33] JL
-  int *Hs = Js + 2 * 128 * kLevStride;               // PASS 1: [kQT][32] up, [kQT][32] lo
-  const int t = threadIdx.x;
-  const int64_t u0 = (int64_t)blockIdx.x * 128;
-  const int64_t u = u0 + t;
-  const bool active = u < n;
-  load_users_T(U, n, d, u0, Us);
-  for (int L = 0; L < 32; ++L) {
-    Js[t * kLevStride + L] = active ? JU[u * kMaxLevels + L] : -1;
-    Js[128 * kLevStride + t * kLevStride + L] = active ? JL[u * kMaxLevels + L] : -1;
-  }
-  if (PASS == 1)
-    for (int i = t; i < 2 * kQT * 32; i += blockDim.x) Hs[i] = 0;
-  const float cfac = screen_cfac(d);
-  const float nu = active ? unrm[u] : 0.0f;
-  BinFP bf = active ? binfp[u] : BinFP{0.f, 1.f, 2e6f, 0.f};
-  const double fm = active ? fmin[u] : 0.0;
-  const int *ju = Js + t * kLevStride;
-  const int *jl = Js + 128 * kLevStride + t * kLevStride;
-  for (int q0 = qa; q0 < qb; q0 += kQT) {
-    __syncthreads();
-    load_items_T<kQT>(Q, qb, d, q0, Qs);
-    __syncthreads();
-    float acc[kQT];
-    tile_dots<kQT>(Us, Qs, d, t, acc);
-    if (active) {
-#pragma unroll
-      for (int j = 0; j < kQT; ++j) {
-        int q = q0 + j;
-        if (q < qb) {
-          float b = screen_bound(cfac, nu, qnrm[q]);
-          int jlo, jhi;
-          bin_interval(bf, fm, tau, __fsub_rd(acc[j], b), __fadd_ru(acc[j], b), jlo, jhi);
-          if (PASS == 1) {
-            int lu = count_gt(ju, jlo);
-            int ll = count_gt(jl, jhi);
-            atomicAdd(&Hs[j * 32 + lu], 1);
-            atomicAdd(&Hs[kQT * 32 + j * 32 + ll], 1);
-          } else {
-            if (jhi >= jl[lstar[q]]) {
-              uint32_t pos = atomicAdd(&qcursor[q], 1u);
-              int64_t at = qoff[q] + pos;
-              cand_u[at] = (int32_t)u;
-              cand_q[at] = q;
-            }
-          }
-        }
-      }
-    }
-    if (PASS == 1) {
-      __syncthreads();
-      for (int i = t; i < kQT * 32; i += blockDim.x) {
-        int j = i >> 5, L = i & 31;
-        int q = q0 + j;
-        int a = Hs[i], b = Hs[kQT * 32 + i];
-        if (q < qb) {
-          if (a) atomicAdd(&hist_up[(int64_t)q * 32 + L], (uint32_t)a);
-          if (b) atomicAdd(&hist_lo[(int64_t)q * 32 + L], (uint32_t)b);
-        }
-        Hs[i] = 0;
-        Hs[kQT * 32 + i] = 0;
-      }
-    }
-  }
-}
 
 // Cutoff level and candidate count of each query.
 __global__ void k_cutoff(int nq, const uint32_t *__restrict__ hist_up,
@@ -392,98 +300,37 @@ __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
   seg_len[slot] = (int32_t)(e - i);
 }
 
-// Exact ranks of grouped candidates.  Thread <-> one user and its block of
-// candidate thresholds theta_0 <= ... < theta_{L-1} (canonical u.q, sorted).
-// For each item the screen gives s in [lo, hi]; pos = #{i : theta_i < s} is
-// decided from the screen when no theta lies in [lo, hi), else from canonical
-// FP64.  hist[pos] += 1; at the end count_i = sum_{pos > i} hist[pos] =
-// #{p : s(u,p) > theta_i}.  Items with hi <= theta_0 exceed no threshold.
-__global__ void __launch_bounds__(128)
-    k_recount_grouped(int64_t nseg, const int64_t *__restrict__ seg_start,
-                      const int32_t *__restrict__ seg_len, const uint64_t *__restrict__ key_hi,
-                      const int32_t *__restrict__ order, const double *__restrict__ th,
-                      const float *__restrict__ U, const float *__restrict__ unrm,
-                      const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int64_t m,
-                      int d, uint32_t *__restrict__ hist, double *__restrict__ ths,
-                      unsigned long long *__restrict__ nties) {
-  extern __shared__ float smem[];
-  float *Us = smem;                    // [d][128]
-  float *Xs = Us + (size_t)d * 128;    // [d][32]
-  const int t = threadIdx.x;
-  const int64_t sg = (int64_t)blockIdx.x * 128 + t;
-  const bool active = sg < nseg;
-  int64_t st0 = 0, uidx = 0;
-  int L = 0;
-  if (active) {
-    st0 = seg_start[sg];
-    L = seg_len[sg];
-    uidx = (int64_t)key_hi[st0];
-  }
-  // users of this CTA's segments, transposed
-  for (int e = t; e < 128 * d; e += blockDim.x) {
-    int tt = e / d, k = e - tt * d;
-    int64_t s2 = (int64_t)blockIdx.x * 128 + tt;
-    float v = 0.0f;
-    if (s2 < nseg) v = U[(int64_t)key_hi[seg_start[s2]] * d + k];
-    Us[k * 128 + tt] = v;
-  }
-  // sorted thresholds of this segment (gathered) and zeroed histogram
-  double *tseg = ths + st0;
-  uint32_t *h = hist + 2 * st0;  // L + 1 slots; segments are disjoint since L >= 1
-  if (active) {
-    for (int i = 0; i < L; ++i) tseg[i] = th[order[st0 + i]];
-    for (int i = 0; i <= L; ++i) h[i] = 0;
-  }
-  const double tmin = active ? tseg[0] : INFINITY;
-  const float tmin_f = __double2float_rd(tmin);  // hi <= tmin_f implies hi <= tmin
-  const float cfac = screen_cfac(d);
-  const float nu = active ? unrm[uidx] : 0.0f;
-  const float *uu = U + uidx * d;
-  uint32_t ties = 0;
-  for (int64_t x0 = 0; x0 < m; x0 += 32) {
-    __syncthreads();
-    load_items_T<32>(Ps, m, d, x0, Xs);
-    __syncthreads();
-    float acc[32];
-    tile_dots<32>(Us, Xs, d, t, acc);
-    if (!active) continue;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      int64_t p = x0 + j;
-      if (p < m) {
-        float b = screen_bound(cfac, nu, pnrm_s[p]);
-        float hi_f = __fadd_ru(acc[j], b);
-        if (hi_f > tmin_f) {
-          double hi = (double)hi_f;
-          double lo = (double)__fsub_rd(acc[j], b);
-          // pa = #{theta < lo}, pb = #{theta < hi}
-          int a0 = 0, a1 = L;
-          while (a0 < a1) { int md = (a0 + a1) >> 1; if (tseg[md] < lo) a0 = md + 1; else a1 = md; }
-          int pa = a0;
-          a1 = L;
-          while (a0 < a1) { int md = (a0 + a1) >> 1; if (tseg[md] < hi) a0 = md + 1; else a1 = md; }
-          int pb = a0, pos = pa;
-          if (pb > pa) {
-            ++ties;
-            double sc = canon_dot_slow(uu, Ps + p * d, d);
-            while (pos < pb && tseg[pos] < sc) ++pos;
-          }
-          h[pos] += 1;
-        }
-      }
-    }
-  }
-  if (!active) return;
-  // suffix sums: h[i] becomes sum_{pos >= i} hist[pos] = count of theta_{i-1}
+// Per segment: its user, its thresholds in sorted order, and a zeroed histogram
+// of L + 1 slots at hist[2 st0] (segments are disjoint since L >= 1).
+__global__ void k_seg_prep(int64_t nseg, const int64_t *__restrict__ seg_start,
+                           const int32_t *__restrict__ seg_len, const uint64_t *__restrict__ key_hi,
+                           const int32_t *__restrict__ order, const double *__restrict__ th,
+                           int32_t *__restrict__ seg_user, double *__restrict__ ths,
+                           uint32_t *__restrict__ hist) {
+  int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (sg >= nseg) return;
+  int64_t st0 = seg_start[sg];
+  int L = seg_len[sg];
+  seg_user[sg] = (int32_t)key_hi[st0];
+  for (int i = 0; i < L; ++i) ths[st0 + i] = th[order[st0 + i]];
+  for (int i = 0; i <= L; ++i) hist[2 * st0 + i] = 0;
+}
+
+// hist[pos] counts items whose score exceeds exactly the first pos thresholds;
+// after the suffix sum h[i] = #{p : s(u,p) > theta_{i-1}}.
+__global__ void k_seg_suffix(int64_t nseg, const int64_t *__restrict__ seg_start,
+                             const int32_t *__restrict__ seg_len, uint32_t *__restrict__ hist) {
+  int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (sg >= nseg) return;
+  uint32_t *h = hist + 2 * seg_start[sg];
   uint32_t run = 0;
-  for (int i = L; i >= 1; --i) {
+  for (int i = seg_len[sg]; i >= 1; --i) {
     run += h[i];
     h[i] = run;
   }
-  if (ties) atomicAdd(nties, (unsigned long long)ties);
 }
 
-// count of candidate order[st0 + i] = hist[2 st0 + i + 1] (see k_recount_grouped).
+// count of candidate order[st0 + i] = hist[2 st0 + i + 1] (see k_seg_suffix).
 __global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_start,
                                  const int32_t *__restrict__ seg_len,
                                  const int32_t *__restrict__ order,
@@ -593,28 +440,42 @@ struct Plan {
   std::vector<int32_t> lstar;
 };
 
-static size_t theta_smem(int d) {
-  return sizeof(float) * ((size_t)d * 128 + (size_t)d * kQT) + sizeof(int) * 2 * 128 * kLevStride +
-         sizeof(int) * 2 * kQT * 32;
+// Grid, bin parameters and level tables one path uses in the screening passes.
+struct Grid {
+  const BinFP *bf;
+  const double *fmin;
+  int tau;
+  const int16_t *JU, *JL;
+  int nlev;
+};
+
+constexpr int kThetaSplit = 1;  // u.q screened with the split (three-term) product
+
+static rkr_status check_flag(int *flag_d, const char *what, cudaStream_t st) {
+  int h = 0;
+  RKR_CUDA(cudaMemcpyAsync(&h, flag_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (h) return fail(RKR_ETIMEOUT, "%s: screen kernel wait timed out (%d)", what, h);
+  return RKR_OK;
 }
 
-static rkr_status screen_plan(const rkr_index *idx, const float *Qd, const float *qnrm, int nq,
-                              const int32_t *kq_d, const BinFP *bf, const int16_t *JU,
-                              const int16_t *JL, int nlev, cudaStream_t st, int32_t *lstar_d,
-                              int64_t *ncand_d, Plan &plan) {
-  DevBuf bh;
+static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int nq,
+                              const Grid &g, cudaStream_t st, int32_t *lstar_d, int64_t *ncand_d,
+                              Plan &plan) {
+  DevBuf bh, bf;
   uint32_t *hist;
+  int *flag;
   RKR_TRY(tmp_alloc(bh, &hist, (size_t)nq * 64, st));
+  RKR_TRY(tmp_alloc(bf, &flag, 1, st));
   RKR_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nq * 64, st));
-  size_t sm = theta_smem(idx->d);
-  RKR_CUDA(cudaFuncSetAttribute(k_theta<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_theta<1><<<(unsigned)((idx->n + 127) / 128), 128, sm, st>>>(
-      idx->U, idx->n, idx->d, idx->unrm, Qd, qnrm, 0, nq, idx->fmin, bf, idx->tau, JU, JL, hist,
-      hist + (size_t)nq * 32, nullptr, nullptr, nullptr, nullptr, nullptr); note_launch();
+  RKR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  RKR_TRY(tc_theta_pass(1, idx, idx->Ut, qc.Qt, 0, g.bf, g.fmin, g.tau, g.JU, g.JL, hist,
+                        nullptr, nullptr, nullptr, nullptr, nullptr, kThetaSplit, flag, st));
+  k_cutoff<<<(nq + 127) / 128, 128, 0, st>>>(nq, hist, hist + (size_t)nq * 32, qc.kq_d, g.nlev,
+                                             lstar_d, ncand_d);
+  note_launch();
   RKR_CUDA(cudaGetLastError());
-  k_cutoff<<<(nq + 127) / 128, 128, 0, st>>>(nq, hist, hist + (size_t)nq * 32, kq_d, nlev,
-                                             lstar_d, ncand_d); note_launch();
-  RKR_CUDA(cudaGetLastError());
+  RKR_TRY(check_flag(flag, "theta pass 1", st));
   plan.ncand.resize(nq);
   plan.lstar.resize(nq);
   RKR_CUDA(cudaMemcpyAsync(plan.ncand.data(), ncand_d, sizeof(int64_t) * nq,
@@ -626,18 +487,24 @@ static rkr_status screen_plan(const rkr_index *idx, const float *Qd, const float
 }
 
 // Candidates of queries [qa, qb) into per-query segments.
-static rkr_status emit_candidates(const rkr_index *idx, const float *Qd, const float *qnrm,
-                                  int qa, int qb, const BinFP *bf, const int16_t *JU,
-                                  const int16_t *JL, const int32_t *lstar_d,
-                                  const int64_t *qoff_d, uint32_t *cursor_d, int32_t *cand_u,
-                                  int32_t *cand_q, cudaStream_t st) {
-  size_t sm = theta_smem(idx->d);
-  RKR_CUDA(cudaFuncSetAttribute(k_theta<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_theta<2><<<(unsigned)((idx->n + 127) / 128), 128, sm, st>>>(
-      idx->U, idx->n, idx->d, idx->unrm, Qd, qnrm, qa, qb, idx->fmin, bf, idx->tau, JU, JL,
-      nullptr, nullptr, lstar_d, qoff_d, cursor_d, cand_u, cand_q); note_launch();
-  RKR_CUDA(cudaGetLastError());
-  return RKR_OK;
+static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, int qa, int qb,
+                                  const Grid &g, const int32_t *lstar_d, const int64_t *qoff_d,
+                                  uint32_t *cursor_d, int32_t *cand_u, int32_t *cand_q,
+                                  cudaStream_t st) {
+  TcSide sub = qc.Qt;
+  sub.owned = false;
+  sub.rows = qb - qa;
+  sub.hi = qc.Qt.hi + (size_t)qa * qc.Qt.kp;
+  sub.lo = qc.Qt.lo + (size_t)qa * qc.Qt.kp;
+  sub.rb1 = qc.Qt.rb1 + qa;
+  sub.rb3 = qc.Qt.rb3 + qa;
+  DevBuf bf;
+  int *flag;
+  RKR_TRY(tmp_alloc(bf, &flag, 1, st));
+  RKR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  RKR_TRY(tc_theta_pass(2, idx, idx->Ut, sub, qa, g.bf, g.fmin, g.tau, g.JU, g.JL, nullptr,
+                        lstar_d, qoff_d, cursor_d, cand_u, cand_q, kThetaSplit, flag, st));
+  return check_flag(flag, "theta pass 2", st);
 }
 
 // Group queries into chunks whose candidate total stays within budget.
@@ -698,13 +565,25 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   unsigned long long nseg = 0;
   RKR_CUDA(cudaMemcpyAsync(&nseg, nseg_d, sizeof(nseg), cudaMemcpyDeviceToHost, st));
   RKR_CUDA(cudaStreamSynchronize(st));
-  size_t sm = sizeof(float) * ((size_t)idx->d * 128 + (size_t)idx->d * 32);
-  RKR_CUDA(cudaFuncSetAttribute(k_recount_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sm));
-  k_recount_grouped<<<(unsigned)((nseg + 127) / 128), 128, sm, st>>>(
-      (int64_t)nseg, sstart, slen, khi, val, th, idx->U, idx->unrm, idx->Ps, idx->pnrm_s, idx->m,
-      idx->d, hist, ths, ties_d); note_launch();
+  DevBuf b10;
+  int32_t *suser;
+  RKR_TRY(tmp_alloc(b10, &suser, nseg, st));
+  k_seg_prep<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen, khi,
+                                                               val, th, suser, ths, hist);
+  note_launch();
   RKR_CUDA(cudaGetLastError());
+  int64_t refined = 0;
+  RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, sstart, slen, suser, ths, hist, st,
+                     &refined));
+  k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
+                                                                 hist);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  if (ties_d) {
+    unsigned long long r = (unsigned long long)refined;
+    RKR_CUDA(cudaMemcpyAsync(ties_d, &r, sizeof(r), cudaMemcpyHostToDevice, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+  }
   k_scatter_counts<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
                                                                    val, hist, ccount); note_launch();
   RKR_CUDA(cudaGetLastError());
@@ -722,8 +601,8 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
   RKR_TRY(tmp_alloc(bn, &ncand_d, nq, st));
   Plan plan;
   Timer t1(st);
-  RKR_TRY(screen_plan(idx, qc.Qd, qc.qnrm, nq, qc.kq_d, qc.bf, idx->JU, idx->JL, idx->nlev_a, st,
-                      lstar_d, ncand_d, plan));
+  const Grid grid{qc.bf, idx->fmin, idx->tau, idx->JU, idx->JL, idx->nlev_a};
+  RKR_TRY(screen_plan(idx, qc, nq, grid, st, lstar_d, ncand_d, plan));
   double ms_theta = t1.stop(), ms_res = 0.0, ms_sel = 0.0;
   int64_t total = 0;
   int wide = 0;
@@ -761,8 +640,7 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
                              cudaMemcpyHostToDevice, st));
     RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
     Timer t2(st);
-    RKR_TRY(emit_candidates(idx, qc.Qd, qc.qnrm, qa, qb, qc.bf, idx->JU, idx->JL, lstar_d,
-                            qoff_rel, cursor, cu, cq, st));
+    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, qoff_rel, cursor, cu, cq, st));
     ms_theta += t2.stop();
     Timer t3(st);
     if (cnt > 0) {
@@ -811,8 +689,8 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
   RKR_CUDA(cudaMemsetAsync(ties_d, 0, sizeof(unsigned long long), st));
   Plan plan;
   Timer t1(st);
-  RKR_TRY(screen_plan(idx, qc.Qd, qc.qnrm, nq, qc.kq_d, qc.bf, idx->XJU, idx->XJL, idx->nlev_x,
-                      st, lstar_d, ncand_d, plan));
+  const Grid grid{qc.xbf, idx->xg0, idx->xg, idx->XJU, idx->XJL, idx->nlev_x};
+  RKR_TRY(screen_plan(idx, qc, nq, grid, st, lstar_d, ncand_d, plan));
   double ms_theta = t1.stop(), ms_res = 0.0, ms_sel = 0.0;
   int64_t total = 0;
   int wide = 0;
@@ -840,8 +718,7 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
                              cudaMemcpyHostToDevice, st));
     RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
     Timer t2(st);
-    RKR_TRY(emit_candidates(idx, qc.Qd, qc.qnrm, qa, qb, qc.bf, idx->XJU, idx->XJL, lstar_d,
-                            qoff_rel, cursor, cu, cq, st));
+    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, qoff_rel, cursor, cu, cq, st));
     ms_theta += t2.stop();
     Timer t3(st);
     if (cnt > 0) RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu, cq, ccount, ties_d, st));

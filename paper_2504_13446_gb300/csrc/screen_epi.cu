@@ -1,0 +1,699 @@
+// screen_epi.cu -- epilogues of the tensor-core screens and their drivers.
+//
+//   f-bounds   U.P^T, two passes: per-user max(s_hat - b) / min(s_hat + b), then
+//              every item that may reach the extreme is evaluated canonically
+//   exact table U.P^T (split product): per user, exact counts #{p : s(u,p) > x_j}
+//              on a grid x_0 < .. < x_{G-1} spanning the upper tail of u's scores
+//   theta      U.Q^T: bin interval of u.q on a grid -> per-query level histograms
+//              (pass 1) or candidate lists (pass 2)
+//   recount    U'.P^T over users with candidates (split product): each score is
+//              located in the user's sorted block of candidate thresholds
+// Undecided cases (bound straddling a boundary) are queued as (row, item) pairs
+// and resolved by canonical FP64 afterwards.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "index.cuh"
+#include "tcops.cuh"
+
+namespace rkr {
+
+namespace {
+
+__device__ __forceinline__ uint64_t dkey_signed(double x) {
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double dkey_inverse(uint64_t k) {
+  uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// Queue of (row, column) pairs with a capacity; overflow raises a flag.
+struct PairQueue {
+  int2 *items;
+  unsigned long long *count;
+  unsigned long long cap;
+  int *overflow;
+  __device__ __forceinline__ void push(int a, int b) const {
+    unsigned long long i = atomicAdd(count, 1ull);
+    if (i < cap) items[i] = make_int2(a, b);
+    else atomicExch(overflow, 1);
+  }
+};
+
+}  // namespace
+
+// ============================================================== f-bounds
+
+struct EpiFbA {
+  struct Thread {
+    float mx, mn, b;
+    float mxlo, mnhi;
+  };
+  static constexpr size_t kSmem = 2 * 128 * sizeof(float);
+  int64_t nrows, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  float gacc, gcan;
+  float *maxlo, *minhi;
+  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &ts) const {
+    ts.mxlo = -INFINITY;
+    ts.mnhi = INFINITY;
+  }
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    int64_t row = (int64_t)rb * tc::BM + r;
+    ts.b = row < nrows ? tc::screen_bound_tc(rowb[row], tileb[ct], gacc, gcan) : 0.0f;
+    ts.mx = -INFINITY;
+    ts.mn = INFINITY;
+  }
+  __device__ void chunk(char *, int, int ct, int, int col, const float (&v)[32],
+                        Thread &ts) const {
+    const int64_t c0 = (int64_t)ct * bn + col;
+    if (c0 + 32 <= ncols) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        ts.mx = fmaxf(ts.mx, v[j]);
+        ts.mn = fminf(ts.mn, v[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < ncols) {
+          ts.mx = fmaxf(ts.mx, v[j]);
+          ts.mn = fminf(ts.mn, v[j]);
+        }
+    }
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &ts) const {
+    ts.mxlo = fmaxf(ts.mxlo, __fsub_rd(ts.mx, ts.b));
+    ts.mnhi = fminf(ts.mnhi, __fadd_ru(ts.mn, ts.b));
+  }
+  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &ts) const {
+    float *sm = (float *)S;
+    const int r = et & 127;  // thread et handles row (quarter, lane) mapping below
+    (void)r;
+    // rows: epilogue thread et -> warp (et>>5)+2, quarter ((et>>5)+2)&3, half (et>>5)>>2
+    const int w = (et >> 5) + 2, lane = et & 31;
+    const int row = (w & 3) * 32 + lane, half = (et >> 5) >> 2;
+    if (half == 1) {
+      sm[row] = ts.mxlo;
+      sm[128 + row] = ts.mnhi;
+    }
+    tc::epi_sync();
+    if (half == 0) {
+      int64_t g = (int64_t)u.rb0 * tc::BM + row;
+      if (g < nrows) {
+        maxlo[g] = fmaxf(ts.mxlo, sm[row]);
+        minhi[g] = fminf(ts.mnhi, sm[128 + row]);
+      }
+    }
+  }
+};
+
+struct EpiFbB {
+  struct Thread {
+    float tmax, tmin;
+    int64_t row;
+  };
+  static constexpr size_t kSmem = 0;
+  int64_t nrows, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  float gacc, gcan;
+  const float *maxlo, *minhi;
+  PairQueue q;
+  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    ts.row = (int64_t)rb * tc::BM + r;
+    if (ts.row < nrows) {
+      float b = tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan);
+      // s_hat >= tmax is implied by s_hat + b >= maxlo (and likewise for the minimum)
+      ts.tmax = __fsub_rd(maxlo[ts.row], b);
+      ts.tmin = __fadd_ru(minhi[ts.row], b);
+    } else {
+      ts.tmax = INFINITY;
+      ts.tmin = -INFINITY;
+    }
+  }
+  __device__ void chunk(char *, int, int ct, int, int col, const float (&v)[32],
+                        Thread &ts) const {
+    const int64_t c0 = (int64_t)ct * bn + col;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if ((v[j] >= ts.tmax || v[j] <= ts.tmin) && c0 + j < ncols) push((int)(c0 + j), ts);
+    }
+  }
+  __device__ __noinline__ void push(int c, const Thread &ts) const { q.push((int)ts.row, c); }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+};
+
+__global__ void k_fb_init(int64_t n, unsigned long long *kmax, unsigned long long *kmin) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  kmax[i] = 0ull;
+  kmin[i] = ~0ull;
+}
+
+__global__ void k_fb_resolve(const int2 *__restrict__ items, const unsigned long long *count,
+                             unsigned long long cap, const float *__restrict__ U,
+                             const float *__restrict__ Ps, int d,
+                             unsigned long long *kmax, unsigned long long *kmin) {
+  unsigned long long c = *count;
+  if (c > cap) c = cap;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    int2 it = items[i];
+    double s = canon_dot(U + (int64_t)it.x * d, Ps + (int64_t)it.y * d, d);
+    uint64_t k = dkey_signed(s);
+    atomicMax(&kmax[it.x], (unsigned long long)k);
+    atomicMin(&kmin[it.x], (unsigned long long)k);
+  }
+}
+
+__global__ void k_fb_finish(int64_t n, const unsigned long long *kmax,
+                            const unsigned long long *kmin, double *fmin, double *fmax,
+                            int *bad) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (kmax[i] == 0ull || kmin[i] == ~0ull) {
+    atomicExch(bad, 1);
+    return;
+  }
+  fmax[i] = dkey_inverse(kmax[i]);
+  fmin[i] = dkey_inverse(kmin[i]);
+}
+
+// Exact canonical f_min / f_max per user from two tensor-core passes.
+// Returns RKR_EINTERNAL (after which the caller uses the CUDA-core scan) when
+// the candidate queue overflows.
+rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, double *fmin,
+                      double *fmax, cudaStream_t st) {
+  constexpr int BN = 256;
+  const int64_t n = idx->n, m = idx->m;
+  tc::RowBound *tb = nullptr;
+  RKR_TRY(tc_tile_bounds(Pt, BN, 0, &tb, st));
+  float *maxlo, *minhi;
+  unsigned long long *kmax, *kmin, *qcount;
+  int2 *qitems;
+  int *flags;  // [0] screen error, [1] overflow, [2] missing extreme
+  const unsigned long long cap = std::max<int64_t>(8 * n, 1 << 16);
+  RKR_CUDA(cudaMallocAsync(&maxlo, sizeof(float) * n, st));
+  RKR_CUDA(cudaMallocAsync(&minhi, sizeof(float) * n, st));
+  RKR_CUDA(cudaMallocAsync(&kmax, sizeof(unsigned long long) * n, st));
+  RKR_CUDA(cudaMallocAsync(&kmin, sizeof(unsigned long long) * n, st));
+  RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
+  RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 4, st));
+  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 4, st));
+  const tc::Schedule sch = row_schedule(n, m, BN);
+  EpiFbA a;
+  a.nrows = n; a.ncols = m; a.bn = BN; a.rowb = Ut.rb1; a.tileb = tb;
+  a.gacc = tc_gacc(Ut.kp, 0); a.gcan = tc_gcan(idx->d);
+  a.maxlo = maxlo; a.minhi = minhi;
+  rkr_status s = launch_screen<BN, 4>(Ut, Pt, 0, sch, a, flags, st);
+  if (s == RKR_OK) {
+    EpiFbB b;
+    b.nrows = n; b.ncols = m; b.bn = BN; b.rowb = Ut.rb1; b.tileb = tb;
+    b.gacc = a.gacc; b.gcan = a.gcan; b.maxlo = maxlo; b.minhi = minhi;
+    b.q = PairQueue{qitems, qcount, cap, flags + 1};
+    s = launch_screen<BN, 4>(Ut, Pt, 0, sch, b, flags, st);
+  }
+  if (s == RKR_OK) {
+    k_fb_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, kmax, kmin);
+    note_launch();
+    k_fb_resolve<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
+                                                  kmax, kmin);
+    note_launch();
+    k_fb_finish<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, kmax, kmin, fmin, fmax,
+                                                             flags + 2);
+    note_launch();
+  }
+  int hf[4] = {0, 0, 0, 0};
+  cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  for (void *p : {(void *)tb, (void *)maxlo, (void *)minhi, (void *)kmax, (void *)kmin,
+                  (void *)qcount, (void *)qitems, (void *)flags})
+    cudaFreeAsync(p, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tc_fbounds");
+  RKR_TRY(s);
+  if (hf[0]) return fail(RKR_ETIMEOUT, "f-bounds screen wait timed out (%d)", hf[0]);
+  if (hf[1] || hf[2]) return fail(RKR_EINTERNAL, "f-bounds candidate queue overflow");
+  return RKR_OK;
+}
+
+// =========================================================== exact table
+
+constexpr int kXG = kXGrid;  // columns of the exact grid
+
+// Exact grid of each user: x_i = g0 + i * dx, i = 0..G-1, dx = (f_max - g0) / (G - 1),
+// where g0 is the paper threshold t_{floor+1} whose estimated count is still at
+// least the floor rank.  The grid spans the upper tail of u's scores.
+__global__ void k_xgrid(int64_t n, const double *__restrict__ fmin,
+                        const double *__restrict__ delta, const int32_t *__restrict__ fl,
+                        double *__restrict__ g0, float *__restrict__ g0f) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  double g = thr_at(fmin[u], delta[u], fl[u]);
+  g0[u] = g;
+  g0f[u] = __double2float_rd(g);
+}
+
+struct EpiXT {
+  struct Thread {
+    float skip, b;
+    BinFP bf;
+    double g0;
+    int64_t row;
+  };
+  static constexpr size_t kSmem = 128 * (kXG + 1) * sizeof(uint32_t);
+  int64_t nrows, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  float gacc, gcan;
+  const BinFP *xbin;
+  const double *xg0;
+  const float *g0f;
+  uint32_t *XC;
+  PairQueue q;
+  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &) const {
+    uint32_t *H = (uint32_t *)S;
+    for (int i = et; i < 128 * (kXG + 1); i += 256) H[i] = 0;
+  }
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    ts.row = (int64_t)rb * tc::BM + r;
+    if (ts.row < nrows) {
+      ts.b = tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan);
+      ts.skip = __fsub_rd(g0f[ts.row], ts.b);  // s_hat <= skip implies s <= x_0
+      ts.bf = xbin[ts.row];
+      ts.g0 = xg0[ts.row];
+    } else {
+      ts.skip = INFINITY;
+    }
+  }
+  __device__ void chunk(char *S, int, int ct, int r, int col, const float (&v)[32],
+                        Thread &ts) const {
+    uint32_t *H = (uint32_t *)S + r * (kXG + 1);
+    const int64_t c0 = (int64_t)ct * bn + col;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (v[j] > ts.skip && c0 + j < ncols) count(H, v[j], (int)(c0 + j), ts);
+  }
+  __device__ __noinline__ void count(uint32_t *H, float v, int c, const Thread &ts) const {
+    int clo, chi;
+    bin_interval(ts.bf, ts.g0, kXG, __fsub_rd(v, ts.b), __fadd_ru(v, ts.b), clo, chi);
+    if (clo == chi) {
+      if (clo > 0) atomicAdd(&H[clo], 1u);
+    } else {
+      q.push((int)ts.row, c);
+    }
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &) const {
+    if (et >= 128) return;
+    int64_t row = (int64_t)u.rb0 * tc::BM + et;
+    if (row >= nrows) return;
+    const uint32_t *H = (const uint32_t *)S + et * (kXG + 1);
+    uint32_t run = 0;
+    for (int c = kXG; c >= 1; --c) {
+      run += H[c];
+      XC[row * kXG + (c - 1)] = run;  // #{p : c(s_p) > c - 1}
+    }
+  }
+};
+
+__global__ void k_xt_refine(const int2 *__restrict__ items, const unsigned long long *count,
+                            unsigned long long cap, const float *__restrict__ U,
+                            const float *__restrict__ Ps, int d, const double *__restrict__ xg0,
+                            const double *__restrict__ xdx, uint32_t *__restrict__ XC) {
+  unsigned long long c = *count;
+  if (c > cap) c = cap;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    int2 it = items[i];
+    double s = canon_dot(U + (int64_t)it.x * d, Ps + (int64_t)it.y * d, d);
+    int cc = exact_c(s, xg0[it.x], xdx[it.x], kXG);
+    for (int j = 0; j < cc; ++j) atomicAdd(&XC[(int64_t)it.x * kXG + j], 1u);
+  }
+}
+
+rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cudaStream_t st,
+                          int64_t *refined) {
+  constexpr int BN = 256;
+  const int64_t n = idx->n, m = idx->m;
+  tc::RowBound *tb = nullptr;
+  RKR_TRY(tc_tile_bounds(Pt, BN, 1, &tb, st));
+  float *g0f;
+  unsigned long long *qcount;
+  int2 *qitems;
+  int *flags;
+  const unsigned long long cap = std::max<int64_t>(64 * n, 1 << 20);
+  RKR_CUDA(cudaMallocAsync(&g0f, sizeof(float) * n, st));
+  RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
+  RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 2, st));
+  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
+  k_xgrid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, idx->fmin, idx->delta, idx->xfloor,
+                                                       idx->xg0, g0f);
+  note_launch();
+  RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, kXG, idx->pmax, idx->xdx, idx->xbin, st));
+  EpiXT e;
+  e.nrows = n; e.ncols = m; e.bn = BN; e.rowb = Ut.rb3; e.tileb = tb;
+  e.gacc = tc_gacc(Ut.kp, 1); e.gcan = tc_gcan(idx->d);
+  e.xbin = idx->xbin; e.xg0 = idx->xg0; e.g0f = g0f; e.XC = idx->XC;
+  e.q = PairQueue{qitems, qcount, cap, flags + 1};
+  rkr_status s = launch_screen<BN, 3>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
+  if (s == RKR_OK) {
+    k_xt_refine<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
+                                                idx->xg0, idx->xdx, idx->XC);
+    note_launch();
+  }
+  int hf[2] = {0, 0};
+  unsigned long long hq = 0;
+  cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&hq, qcount, sizeof(hq), cudaMemcpyDeviceToHost, st);
+  cudaError_t err = cudaStreamSynchronize(st);
+  for (void *p : {(void *)tb, (void *)g0f, (void *)qcount, (void *)qitems, (void *)flags})
+    cudaFreeAsync(p, st);
+  if (err != cudaSuccess) return cuda_fail(err, "tc_exact_table");
+  RKR_TRY(s);
+  if (hf[0]) return fail(RKR_ETIMEOUT, "exact-table screen wait timed out (%d)", hf[0]);
+  if (hf[1]) return fail(RKR_EINTERNAL, "exact-table refinement queue overflow");
+  if (refined) *refined = (int64_t)hq;
+  return RKR_OK;
+}
+
+// ================================================================= theta
+
+constexpr int kThetaBN = 128;
+
+// Pass 1 accumulates, per query, histograms of the rank level of the upper
+// bound (from the low end of the bin interval) and of the lower bound (from
+// its high end).  Pass 2 writes (user, query) when the lower bound may reach
+// the query's cutoff level.
+template <int PASS>
+struct EpiTheta {
+  struct Thread {
+    float b;
+    BinFP bf;
+    double fm;
+    int64_t u;
+  };
+  static constexpr size_t kSmem =
+      sizeof(int) * (2 * 128 * 33 + 2 * kThetaBN * 32 + kThetaBN);
+  int64_t nrows, ncols;
+  int tau;
+  int qa;  // global index of query column 0
+  const tc::RowBound *rowb, *tileb;
+  float gacc, gcan;
+  const BinFP *binfp;
+  const double *fmin;
+  const int16_t *JU, *JL;
+  uint32_t *hist_up, *hist_lo;  // PASS 1: [nq][32], indexed by global query
+  const int32_t *lstar;         // PASS 2: indexed by global query
+  const int64_t *qoff;
+  uint32_t *qcursor;
+  int32_t *cand_u, *cand_q;
+
+  __device__ int *jtab(char *S) const { return (int *)S; }
+  __device__ int *hist(char *S) const { return (int *)S + 2 * 128 * 33; }
+  __device__ int *lst(char *S) const { return hist(S) + 2 * kThetaBN * 32; }
+
+  __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &) const {
+    if (PASS == 1) {
+      int *H = hist(S);
+      for (int i = et; i < 2 * kThetaBN * 32; i += 256) H[i] = 0;
+    } else {
+      int *L = lst(S);
+      for (int i = et; i < kThetaBN; i += 256) {
+        int64_t q = (int64_t)u.ct0 * kThetaBN + i;
+        L[i] = q < ncols ? lstar[qa + q] : 0;
+      }
+    }
+  }
+  __device__ void tile_begin(char *S, int rb, int ct, int r, int h, Thread &ts) const {
+    tc::epi_sync();  // readers of the previous tile are done with the level tables
+    ts.u = (int64_t)rb * tc::BM + r;
+    int *ju = jtab(S) + r * 33, *jl = jtab(S) + 128 * 33 + r * 33;
+    if (ts.u < nrows) {
+      for (int L = h * 16; L < h * 16 + 16; ++L) {
+        ju[L] = JU[ts.u * kMaxLevels + L];
+        jl[L] = JL[ts.u * kMaxLevels + L];
+      }
+      ts.b = tc::screen_bound_tc(rowb[ts.u], tileb[ct], gacc, gcan);
+      ts.bf = binfp[ts.u];
+      ts.fm = fmin[ts.u];
+    }
+    tc::epi_sync();
+  }
+  __device__ void chunk(char *S, int, int ct, int r, int col, const float (&v)[32],
+                        Thread &ts) const {
+    if (ts.u >= nrows) return;
+    const int *ju = jtab(S) + r * 33, *jl = jtab(S) + 128 * 33 + r * 33;
+    int *H = hist(S);
+    const int *Ls = lst(S);
+    const int64_t c0 = (int64_t)ct * kThetaBN + col;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (c0 + j < ncols) {
+        int jlo, jhi;
+        bin_interval(ts.bf, ts.fm, tau, __fsub_rd(v[j], ts.b), __fadd_ru(v[j], ts.b), jlo, jhi);
+        if (PASS == 1) {
+          int lu = 0, ll = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            if (ju[lu + step - 1] > jlo) lu += step;
+            if (jl[ll + step - 1] > jhi) ll += step;
+          }
+          atomicAdd(&H[(col + j) * 32 + lu], 1);
+          atomicAdd(&H[kThetaBN * 32 + (col + j) * 32 + ll], 1);
+        } else if (jhi >= jl[Ls[col + j]]) {
+          emit((int)(c0 + j), ts);
+        }
+      }
+    }
+  }
+  __device__ __noinline__ void emit(int c, const Thread &ts) const {
+    int q = qa + c;
+    uint32_t pos = atomicAdd(&qcursor[q], 1u);
+    int64_t at = qoff[q] + pos;
+    cand_u[at] = (int32_t)ts.u;
+    cand_q[at] = q;
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &) const {
+    if (PASS != 1) return;
+    const int *H = hist(S);
+    for (int i = et; i < kThetaBN * 32; i += 256) {
+      int64_t q = (int64_t)u.ct0 * kThetaBN + (i >> 5);
+      if (q >= ncols) continue;
+      int a = H[i], b = H[kThetaBN * 32 + i];
+      if (a) atomicAdd(&hist_up[(qa + q) * 32 + (i & 31)], (uint32_t)a);
+      if (b) atomicAdd(&hist_lo[(qa + q) * 32 + (i & 31)], (uint32_t)b);
+    }
+  }
+};
+
+// Theta pass over queries [qa, qa + Qt.rows) (Qt holds exactly those rows).
+rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
+                         int qa, const BinFP *binfp, const double *fmin, int tau,
+                         const int16_t *JU, const int16_t *JL, uint32_t *hist,
+                         const int32_t *lstar, const int64_t *qoff, uint32_t *qcursor,
+                         int32_t *cand_u, int32_t *cand_q, int split, int *err, cudaStream_t st) {
+  const int64_t n = idx->n, nq = Qt.rows;
+  tc::RowBound *tb = nullptr;
+  RKR_TRY(tc_tile_bounds(Qt, kThetaBN, split, &tb, st));
+  int nct = (int)((nq + kThetaBN - 1) / kThetaBN);
+  int parts = std::max(1, (2 * sm_count() + nct - 1) / nct);
+  tc::Schedule sch = col_schedule(n, nq, kThetaBN, parts);
+  rkr_status s;
+  if (pass == 1) {
+    EpiTheta<1> e;
+    e.nrows = n; e.ncols = nq; e.tau = tau; e.qa = qa;
+    e.rowb = split ? Ut.rb3 : Ut.rb1; e.tileb = tb;
+    e.gacc = tc_gacc(Ut.kp, split); e.gcan = tc_gcan(idx->d);
+    e.binfp = binfp; e.fmin = fmin; e.JU = JU; e.JL = JL;
+    e.hist_up = hist; e.hist_lo = hist + (size_t)(qa + nq) * 32;
+    e.lstar = nullptr; e.qoff = nullptr; e.qcursor = nullptr; e.cand_u = nullptr; e.cand_q = nullptr;
+    s = launch_screen<kThetaBN, 4>(Ut, Qt, split, sch, e, err, st);
+  } else {
+    EpiTheta<2> e;
+    e.nrows = n; e.ncols = nq; e.tau = tau; e.qa = qa;
+    e.rowb = split ? Ut.rb3 : Ut.rb1; e.tileb = tb;
+    e.gacc = tc_gacc(Ut.kp, split); e.gcan = tc_gcan(idx->d);
+    e.binfp = binfp; e.fmin = fmin; e.JU = JU; e.JL = JL;
+    e.hist_up = nullptr; e.hist_lo = nullptr;
+    e.lstar = lstar; e.qoff = qoff; e.qcursor = qcursor; e.cand_u = cand_u; e.cand_q = cand_q;
+    s = launch_screen<kThetaBN, 4>(Ut, Qt, split, sch, e, err, st);
+  }
+  cudaFreeAsync(tb, st);
+  return s;
+}
+
+// =============================================================== recount
+
+struct EpiRC {
+  struct Thread {
+    float b, tminf;
+    int64_t sg;
+    int L;
+    const double *ts;
+    uint32_t *h;
+  };
+  static constexpr size_t kSmem = 0;
+  int64_t nseg, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  float gacc, gcan;
+  const int64_t *seg_start;
+  const int32_t *seg_len;
+  const double *ths;
+  uint32_t *hist;
+  PairQueue q;
+  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    ts.sg = (int64_t)rb * tc::BM + r;
+    if (ts.sg < nseg) {
+      int64_t st0 = seg_start[ts.sg];
+      ts.L = seg_len[ts.sg];
+      ts.ts = ths + st0;
+      ts.h = hist + 2 * st0;
+      ts.tminf = __double2float_rd(ts.ts[0]);
+      ts.b = tc::screen_bound_tc(rowb[ts.sg], tileb[ct], gacc, gcan);
+    } else {
+      ts.tminf = INFINITY;
+      ts.b = 0.0f;
+    }
+  }
+  __device__ void chunk(char *, int, int ct, int, int col, const float (&v)[32],
+                        Thread &ts) const {
+    const int64_t c0 = (int64_t)ct * bn + col;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float hf = __fadd_ru(v[j], ts.b);
+      if (hf > ts.tminf && c0 + j < ncols) locate(v[j], hf, (int)(c0 + j), ts);
+    }
+  }
+  // Position of one score in the sorted candidate thresholds (rare path).
+  __device__ __noinline__ void locate(float v, float hf, int c, const Thread &ts) const {
+    double hi = (double)hf, lo = (double)__fsub_rd(v, ts.b);
+    int a0 = 0, a1 = ts.L;
+    while (a0 < a1) { int md = (a0 + a1) >> 1; if (ts.ts[md] < lo) a0 = md + 1; else a1 = md; }
+    int pa = a0;
+    a1 = ts.L;
+    while (a0 < a1) { int md = (a0 + a1) >> 1; if (ts.ts[md] < hi) a0 = md + 1; else a1 = md; }
+    if (a0 == pa) atomicAdd(&ts.h[pa], 1u);
+    else q.push((int)ts.sg, c);
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+};
+
+__global__ void k_rc_refine(const int2 *__restrict__ items, const unsigned long long *count,
+                            unsigned long long cap, const int64_t *__restrict__ seg_start,
+                            const int32_t *__restrict__ seg_len,
+                            const int32_t *__restrict__ seg_user, const double *__restrict__ ths,
+                            const float *__restrict__ U, const float *__restrict__ Ps, int d,
+                            uint32_t *__restrict__ hist) {
+  unsigned long long c = *count;
+  if (c > cap) c = cap;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    int2 it = items[i];
+    int64_t st0 = seg_start[it.x];
+    int L = seg_len[it.x];
+    double s = canon_dot(U + (int64_t)seg_user[it.x] * d, Ps + (int64_t)it.y * d, d);
+    const double *t = ths + st0;
+    int a0 = 0, a1 = L;
+    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < s) a0 = md + 1; else a1 = md; }
+    atomicAdd(&hist[2 * st0 + a0], 1u);
+  }
+}
+
+// Gather rows of a side: out row i = side row idx[i].
+__global__ void k_gather_side(const __nv_bfloat16 *__restrict__ hi,
+                              const __nv_bfloat16 *__restrict__ lo,
+                              const tc::RowBound *__restrict__ rb1,
+                              const tc::RowBound *__restrict__ rb3, int kp,
+                              const int32_t *__restrict__ rows, int64_t count,
+                              __nv_bfloat16 *__restrict__ ohi, __nv_bfloat16 *__restrict__ olo,
+                              tc::RowBound *__restrict__ orb1, tc::RowBound *__restrict__ orb3) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
+  if (i >= count) return;
+  int64_t src = rows[i];
+  for (int k = threadIdx.x; k < kp; k += blockDim.x) {
+    ohi[i * kp + k] = hi[src * kp + k];
+    olo[i * kp + k] = lo[src * kp + k];
+  }
+  if (threadIdx.x == 0) {
+    orb1[i] = rb1[src];
+    orb3[i] = rb3[src];
+  }
+}
+
+rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
+                      const int64_t *seg_start, const int32_t *seg_len, const int32_t *seg_user,
+                      const double *ths, uint32_t *hist, cudaStream_t st, int64_t *refined) {
+  constexpr int BN = 256;
+  const int64_t m = idx->m;
+  if (nseg <= 0) return RKR_OK;
+  TcSide A;
+  A.rows = nseg;
+  A.d = Ut.d;
+  A.kp = Ut.kp;
+  A.owned = false;
+  size_t cnt = (size_t)nseg * A.kp;
+  RKR_CUDA(cudaMallocAsync((void **)&A.hi, cnt * 2, st));
+  RKR_CUDA(cudaMallocAsync((void **)&A.lo, cnt * 2, st));
+  RKR_CUDA(cudaMallocAsync((void **)&A.rb1, sizeof(tc::RowBound) * nseg, st));
+  RKR_CUDA(cudaMallocAsync((void **)&A.rb3, sizeof(tc::RowBound) * nseg, st));
+  dim3 blk(32, 8);
+  k_gather_side<<<(unsigned)((nseg + 7) / 8), blk, 0, st>>>(Ut.hi, Ut.lo, Ut.rb1, Ut.rb3, A.kp,
+                                                             seg_user, nseg, A.hi, A.lo, A.rb1,
+                                                             A.rb3);
+  note_launch();
+  tc::RowBound *tb = nullptr;
+  RKR_TRY(tc_tile_bounds(Pt, BN, 1, &tb, st));
+  unsigned long long *qcount;
+  int2 *qitems;
+  int *flags;
+  const unsigned long long cap = std::max<int64_t>(256 * nseg, 1 << 20);
+  RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
+  RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 2, st));
+  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
+  EpiRC e;
+  e.nseg = nseg; e.ncols = m; e.bn = BN; e.rowb = A.rb3; e.tileb = tb;
+  e.gacc = tc_gacc(A.kp, 1); e.gcan = tc_gcan(idx->d);
+  e.seg_start = seg_start; e.seg_len = seg_len; e.ths = ths; e.hist = hist;
+  e.q = PairQueue{qitems, qcount, cap, flags + 1};
+  rkr_status s = launch_screen<BN, 4>(A, Pt, 1, row_schedule(nseg, m, BN), e, flags, st);
+  if (s == RKR_OK) {
+    k_rc_refine<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, seg_start, seg_len,
+                                                seg_user, ths, idx->U, idx->Ps, idx->d, hist);
+    note_launch();
+  }
+  int hf[2] = {0, 0};
+  unsigned long long hq = 0;
+  cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&hq, qcount, sizeof(hq), cudaMemcpyDeviceToHost, st);
+  cudaError_t err = cudaStreamSynchronize(st);
+  for (void *p : {(void *)A.hi, (void *)A.lo, (void *)A.rb1, (void *)A.rb3, (void *)tb,
+                  (void *)qcount, (void *)qitems, (void *)flags})
+    cudaFreeAsync(p, st);
+  if (err != cudaSuccess) return cuda_fail(err, "tc_recount");
+  RKR_TRY(s);
+  if (hf[0]) return fail(RKR_ETIMEOUT, "recount screen wait timed out (%d)", hf[0]);
+  if (hf[1]) return fail(RKR_EINTERNAL, "recount refinement queue overflow");
+  if (refined) *refined = (int64_t)hq;
+  return RKR_OK;
+}
+
+}  // namespace rkr

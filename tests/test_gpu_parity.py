@@ -42,15 +42,27 @@ def check_index(ora, gpu):
     assert len(bad) == 0, f"{len(bad)} table cells differ, first {bad[:5].tolist()}"
 
 
-def check_exact_table(ora, gpu, U, P):
-    """XLO <= #{p : s(u,p) > t_j} <= XHI for every user and column."""
+def check_exact_table(ora, gpu, U, P, floor_rank=0):
+    """The exact count table: #{p : s(u,p) > x_j} on each user's tail grid, where
+    x_0 is the sampled table's threshold at its last column whose estimated count
+    reaches the floor rank and x_{G-1} = f_max (same threshold formula)."""
+    m, s, tau = P.shape[0], ora["s"], ora["tau"]
+    R = floor_rank or max(2048, m // 16)
     S = oracle.scores(U, P)
-    t = oracle.thresholds_all(ora["fmin"], ora["fmax"], ora["tau"])
-    xlo, xhi = gpu.export("xlo"), gpu.export("xhi")
+    grid = gpu.export("xgrid")
+    xc = gpu.export("xcount")
+    G = xc.shape[1]
     for i in range(U.shape[0]):
+        Nrow = ora["N"][i].astype(np.int64)
+        below = np.nonzero(Nrow < s * R)[0]
+        a = below[0] if len(below) else tau
+        fl = a - 1 if a > 0 else 0
+        g0 = oracle.thresholds(ora["fmin"][i], ora["fmax"][i], tau)[fl]
+        x = oracle.thresholds(g0, ora["fmax"][i], G)
+        assert grid[i, 0] == g0 and grid[i, 1] == (ora["fmax"][i] - g0) / float(G - 1), i
         srt = np.sort(S[i])
-        cnt = S.shape[1] - np.searchsorted(srt, t[i], side="right")
-        assert (xlo[i] <= cnt).all() and (cnt <= xhi[i]).all(), i
+        cnt = S.shape[1] - np.searchsorted(srt, x, side="right")
+        assert (xc[i] == cnt).all(), (i, np.nonzero(xc[i] != cnt)[0][:5])
 
 
 def check_exact(U, P, Q, k, gpu):
@@ -105,6 +117,7 @@ def test_approx_workload_shape_scaled():
     w = synth.make_workload("approx", n=12000, m=3000, nq=24)
     ora, gpu = build_pair(w.U, w.P, w.tau, w.omega, w.s, seed=w.seed)
     check_index(ora, gpu)
+    check_exact_table(ora, gpu, w.U, w.P)
     check_approx(w.U, w.Q, w.k, w.c, ora, gpu)
     check_exact(w.U, w.P, w.Q, w.k, gpu)
 
