@@ -156,7 +156,9 @@ typedef enum {
   RKR_EXPORT_FMAX = 3,      /* double[n] */
   RKR_EXPORT_TABLE = 4,     /* uint32[n * tau]: N[u][j], j = 0..tau-1 */
   RKR_EXPORT_SAMPLES = 5,   /* int32[total samples]: original item index, bucket after bucket */
-  RKR_EXPORT_XCOUNT = 6,    /* uint32[n * G]: #{p : s(u,p) > x_j} on the exact grid (G = 128) */
+  RKR_EXPORT_XLO = 6,       /* uint32[n * G]: lower bound of #{p : s(u,p) > x_j} on the
+                               exact grid (G = 128) */
+  RKR_EXPORT_XHI = 9,       /* uint32[n * G]: upper bound of the same count */
   RKR_EXPORT_XGRID = 7,     /* double[n * 2]: (x_0, step) of each user's exact grid,
                                x_j = x_0 + j * step; x_0 is the threshold t of the sampled
                                table's last column whose estimated count is >= floor_rank,

@@ -29,7 +29,7 @@ __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_ex
 _lock = threading.Lock()
 _lib = None
 
-EXPORTS = dict(perm=1, fmin=2, fmax=3, table=4, samples=5, xcount=6, xgrid=7, pnorm=8)
+EXPORTS = dict(perm=1, fmin=2, fmax=3, table=4, samples=5, xlo=6, xgrid=7, pnorm=8, xhi=9)
 _STATUS = {0: "RKR_OK", 1: "RKR_EINVAL", 2: "RKR_ENOMEM", 3: "RKR_ECUDA", 4: "RKR_ETIMEOUT",
            5: "RKR_EUNSUPPORTED", 6: "RKR_EINTERNAL"}
 
@@ -254,7 +254,8 @@ class Index:
         i = self.info
         shapes = dict(perm=((i.m,), np.int32), fmin=((i.n,), np.float64),
                       fmax=((i.n,), np.float64), table=((i.n, i.tau), np.uint32),
-                      samples=((i.nsamp,), np.int32), xcount=((i.n, i.xg), np.uint32),
+                      samples=((i.nsamp,), np.int32), xlo=((i.n, i.xg), np.uint32),
+                      xhi=((i.n, i.xg), np.uint32),
                       xgrid=((i.n, 2), np.float64), pnorm=((i.m,), np.float64))
         shape, dt = shapes[what]
         a = np.empty(shape, dtype=dt)

@@ -407,7 +407,8 @@ rkr_status rkr_index_export(const rkr_index *idx, int32_t what, void *dst, int64
     case RKR_EXPORT_FMAX: src = idx->fmax; size = 8 * idx->n; break;
     case RKR_EXPORT_TABLE: src = idx->N; size = 4 * idx->n * idx->tau; break;
     case RKR_EXPORT_SAMPLES: src = idx->samp_items; size = 4 * (int64_t)idx->nsamp; break;
-    case RKR_EXPORT_XCOUNT: src = idx->XC; size = 4 * idx->n * (int64_t)idx->xg; break;
+    case RKR_EXPORT_XLO: src = idx->XLO; size = 4 * idx->n * (int64_t)idx->xg; break;
+    case RKR_EXPORT_XHI: src = idx->XHI; size = 4 * idx->n * (int64_t)idx->xg; break;
     case RKR_EXPORT_XGRID: {
       if (!idx->xg0) return fail(RKR_EINVAL, "index has no exact table");
       if (bytes != 16 * idx->n) return fail(RKR_EINVAL, "export %d needs %lld bytes", what,

@@ -624,7 +624,8 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     RKR_TRY(dalloc(&idx->xg0, n));
     RKR_TRY(dalloc(&idx->xdx, n));
     RKR_TRY(dalloc(&idx->xbin, n));
-    RKR_TRY(dalloc(&idx->XC, (size_t)n * kXGrid));
+    RKR_TRY(dalloc(&idx->XLO, (size_t)n * kXGrid));
+    RKR_TRY(dalloc(&idx->XHI, (size_t)n * kXGrid));
     k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
                                                                (uint64_t)idx->floor_rank,
                                                                idx->xfloor); note_launch();
@@ -632,7 +633,7 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     idx->nlev_x = levels_for((uint64_t)m);
     RKR_TRY(dalloc(&idx->XJU, (size_t)n * kMaxLevels));
     RKR_TRY(dalloc(&idx->XJL, (size_t)n * kMaxLevels));
-    k_levels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, kXGrid, idx->XC, idx->XC,
+    k_levels<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, kXGrid, idx->XHI, idx->XLO,
                                                           (uint32_t)m, 1u, idx->nlev_x, idx->XJU,
                                                           idx->XJL); note_launch();
     RKR_CUDA(cudaGetLastError());
@@ -654,7 +655,7 @@ void index_release(rkr_index *idx) {
   void *ptrs[] = {idx->U,      idx->Ps,   idx->perm, idx->pnorm, idx->unrm,
                   idx->pnrm_s, idx->fmin, idx->fmax, idx->delta, idx->binfp, idx->N,
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
-                  idx->xg0,    idx->xdx,  idx->xbin, idx->XC,   idx->XJU,   idx->XJL,
+                  idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
                   idx->xfloor};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -40,7 +40,7 @@ struct rkr_index {
   int xg = 0;
   double *xg0 = nullptr, *xdx = nullptr;    // n
   rkr::BinFP *xbin = nullptr;               // n, built with R = pmax
-  uint32_t *XC = nullptr;                   // n x xg: #{p : s(u,p) > x_j}
+  uint32_t *XLO = nullptr, *XHI = nullptr;  // n x xg: bounds of #{p : s(u,p) > x_j}
   int16_t *XJU = nullptr, *XJL = nullptr;   // n x 32
   int32_t *xfloor = nullptr;                // n: paper column of x_0
 
@@ -75,14 +75,30 @@ rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       double *fmax, cudaStream_t st);
 rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cudaStream_t st,
                           int64_t *refined);
+// Arguments of one screening pass over a query batch (see screen_epi.cu).
+struct ThetaArgs {
+  int qa;                       // global index of the first query of the batch slice
+  const BinFP *binfp;
+  const double *fmin;           // grid origin per user
+  int tau;                      // grid columns
+  const int16_t *JU, *JL;       // level tables
+  const uint32_t *thi, *tlo;    // tables behind the upper and lower bounds (n x tau)
+  uint32_t top, scale;          // upper bound below the grid; level scale
+  uint32_t *hist;               // pass 1: [nq][32] upper-bound levels then [nq][32] lower
+  const int32_t *lstar;         // passes 2, 3
+  const uint32_t *cap;          // pass 2
+  uint32_t *fine;               // pass 3: [nq][1024]
+  const int64_t *qoff;          // pass 2
+  uint32_t *qcursor;
+  int32_t *cand_u, *cand_q;
+};
 rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
-                         int qa, const BinFP *binfp, const double *fmin, int tau,
-                         const int16_t *JU, const int16_t *JL, uint32_t *hist,
-                         const int32_t *lstar, const int64_t *qoff, uint32_t *qcursor,
-                         int32_t *cand_u, int32_t *cand_q, int split, int *err, cudaStream_t st);
+                         const ThetaArgs &a, int split, int *err, cudaStream_t st);
+// refined[0] = queued undecided items, refined[1] = of those, canonical FP64 evaluations.
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
-                      const int64_t *seg_start, const int32_t *seg_len, const int32_t *seg_user,
-                      const double *ths, uint32_t *hist, cudaStream_t st, int64_t *refined);
+                      int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
+                      const int32_t *seg_user, const double *ths, uint32_t *hist,
+                      cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
 
 // Row norms: FP64 canonical norms (optional) and FP32 upper bounds.

@@ -27,15 +27,19 @@
 namespace rkr {
 
 
-// Cutoff level and candidate count of each query.
+// Cutoff level of each query: L* = the smallest level holding k upper bounds;
+// below = pairs whose upper bound lies in a lower level; ncand = pairs whose
+// lower bound lies in a level <= L* (an upper bound of the candidate count).
 __global__ void k_cutoff(int nq, const uint32_t *__restrict__ hist_up,
                          const uint32_t *__restrict__ hist_lo, const int32_t *__restrict__ kq,
-                         int nlev, int32_t *__restrict__ lstar, int64_t *__restrict__ ncand) {
+                         int nlev, int32_t *__restrict__ lstar, uint64_t *__restrict__ below,
+                         int64_t *__restrict__ ncand) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
-  uint64_t cum = 0;
+  uint64_t cum = 0, prev = 0;
   int L = nlev - 1;
   for (int l = 0; l < 32; ++l) {
+    prev = cum;
     cum += hist_up[(int64_t)q * 32 + l];
     if (cum >= (uint64_t)kq[q]) { L = l; break; }
   }
@@ -43,7 +47,29 @@ __global__ void k_cutoff(int nq, const uint32_t *__restrict__ hist_up,
   uint64_t c = 0;
   for (int l = 0; l <= L; ++l) c += hist_lo[(int64_t)q * 32 + l];
   lstar[q] = L;
+  below[q] = prev;
   ncand[q] = (int64_t)c;
+}
+
+// Refined cap: the upper edge of the fine bucket of level L* where the running
+// count of upper bounds reaches k; the k-th smallest upper bound is <= cap.
+__global__ void k_cutoff_fine(int nq, const uint32_t *__restrict__ fine,
+                              const uint64_t *__restrict__ below, const int32_t *__restrict__ lstar,
+                              const int32_t *__restrict__ kq, uint32_t scale,
+                              uint32_t *__restrict__ cap) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int L = lstar[q];
+  uint64_t hi = level_bound(L, scale);
+  uint64_t base = L == 0 ? 0 : level_bound(L - 1, scale) + 1;
+  uint64_t width = (hi - base + 1024) / 1024;
+  uint64_t cum = below[q], c = hi;
+  for (int b = 0; b < 1024; ++b) {
+    cum += fine[(int64_t)q * 1024 + b];
+    if (cum >= (uint64_t)kq[q]) { c = base + (uint64_t)(b + 1) * width - 1; break; }
+  }
+  if (c > hi) c = hi;
+  cap[q] = (uint32_t)(c > 0xffffffffull ? 0xffffffffull : c);
 }
 
 // --------------------------------------------------------- approximate path
@@ -59,6 +85,7 @@ __global__ void k_resolve_approx(int64_t count, const int32_t *__restrict__ cu,
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   int64_t u = cu[i];
+  if (u < 0) return;  // unused slot at the end of a query's segment
   int q = cq[i];
   double theta = canon_dot(U + u * d, Q + (int64_t)q * d, d);
   int j = exact_j(theta, fmin[u], delta[u], tau);
@@ -93,13 +120,14 @@ constexpr int kSelThreads = 256;
 
 // One CTA per query: steps 1-3 of Section 4.3 over the query's candidates.
 __global__ void __launch_bounds__(kSelThreads)
-    k_select_approx(int qa, const int64_t *__restrict__ qoff, ApproxCand C,
+    k_select_approx(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
+                    ApproxCand C,
                     const int32_t *__restrict__ kq, double c, uint32_t s, int tau,
                     const double *__restrict__ fmin, const double *__restrict__ delta,
                     const int64_t *__restrict__ out_off, int32_t *__restrict__ out_users,
                     uint32_t *__restrict__ out_nlo, uint32_t *__restrict__ out_nup,
                     double *__restrict__ out_est, int32_t *__restrict__ out_case,
-                    int32_t *__restrict__ out_nc) {
+                    int32_t *__restrict__ out_nc, int *__restrict__ err) {
   extern __shared__ unsigned char sbuf[];
   SortEnt *ent = (SortEnt *)sbuf;                   // kMaxK entries
   __shared__ uint32_t hist[256];
@@ -108,8 +136,12 @@ __global__ void __launch_bounds__(kSelThreads)
   __shared__ int gcount;
   const int q = qa + blockIdx.x;
   const int64_t base = qoff[q] - qoff[qa];
-  const int64_t cnt = qoff[q + 1] - qoff[q];
+  const int64_t cnt = qcount[q];
   const int k = kq[q];
+  if (cnt < k) {  // cannot happen when the screening passes are consistent
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
   const int32_t *uid = C.uid + base;
   const uint32_t *nlo = C.nlo + base, *nup = C.nup + base;
   const double *th = C.th + base;
@@ -253,7 +285,7 @@ __global__ void k_cand_theta(int64_t count, const int32_t *__restrict__ cu,
                              int32_t *__restrict__ val, int64_t Np2) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= Np2) return;
-  if (i >= count) {
+  if (i >= count || cu[i] < 0) {  // padding or an unused slot: sorted to the end
     key_hi[i] = ~0ull;
     key_lo[i] = ~0ull;
     val[i] = 0x7fffffff;
@@ -291,7 +323,7 @@ __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
                            unsigned long long *__restrict__ nseg, int64_t *__restrict__ seg_start,
                            int32_t *__restrict__ seg_len) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= count) return;
+  if (i >= count || key_hi[i] == ~0ull) return;
   if (i > 0 && key_hi[i] == key_hi[i - 1]) return;
   int64_t e = i + 1;
   while (e < count && key_hi[e] == key_hi[i]) ++e;
@@ -345,10 +377,11 @@ __global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_s
 
 // One CTA per query: the k smallest (rank, index) among its candidates.
 __global__ void __launch_bounds__(kSelThreads)
-    k_select_exact(int qa, const int64_t *__restrict__ qoff, const int32_t *__restrict__ cuid,
+    k_select_exact(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
+                   const int32_t *__restrict__ cuid,
                    const uint32_t *__restrict__ ccount, const int32_t *__restrict__ kq,
                    const int64_t *__restrict__ out_off, int32_t *__restrict__ out_users,
-                   int32_t *__restrict__ out_ranks) {
+                   int32_t *__restrict__ out_ranks, int *__restrict__ err) {
   extern __shared__ unsigned char sbuf[];
   SortEnt *ent = (SortEnt *)sbuf;
   __shared__ uint32_t hist[256];
@@ -356,8 +389,12 @@ __global__ void __launch_bounds__(kSelThreads)
   __shared__ int gcount;
   const int q = qa + blockIdx.x;
   const int64_t base = qoff[q] - qoff[qa];
-  const int64_t cnt = qoff[q + 1] - qoff[q];
+  const int64_t cnt = qcount[q];
   const int k = kq[q];
+  if (cnt < k) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
   const int32_t *uid = cuid + base;
   const uint32_t *cc = ccount + base;
   uint64_t kth = block_kth(cnt, (uint64_t)k, 64,
@@ -440,13 +477,15 @@ struct Plan {
   std::vector<int32_t> lstar;
 };
 
-// Grid, bin parameters and level tables one path uses in the screening passes.
+// Grid, bin parameters, level tables and bound tables of one path.
 struct Grid {
   const BinFP *bf;
   const double *fmin;
   int tau;
   const int16_t *JU, *JL;
   int nlev;
+  const uint32_t *thi, *tlo;
+  uint32_t top, scale;
 };
 
 constexpr int kThetaSplit = 1;  // u.q screened with the split (three-term) product
@@ -459,23 +498,52 @@ static rkr_status check_flag(int *flag_d, const char *what, cudaStream_t st) {
   return RKR_OK;
 }
 
+static ThetaArgs theta_args(const Grid &g, int qa) {
+  ThetaArgs a{};
+  a.qa = qa;
+  a.binfp = g.bf;
+  a.fmin = g.fmin;
+  a.tau = g.tau;
+  a.JU = g.JU;
+  a.JL = g.JL;
+  a.thi = g.thi;
+  a.tlo = g.tlo;
+  a.top = g.top;
+  a.scale = g.scale;
+  return a;
+}
+
+// Passes 1 and 3: per-query cutoff level, refined cap, and candidate-count bounds.
 static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int nq,
-                              const Grid &g, cudaStream_t st, int32_t *lstar_d, int64_t *ncand_d,
-                              Plan &plan) {
-  DevBuf bh, bf;
-  uint32_t *hist;
+                              const Grid &g, cudaStream_t st, int32_t *lstar_d, uint32_t *cap_d,
+                              int64_t *ncand_d, Plan &plan) {
+  DevBuf bh, bf, bb, bfi;
+  uint32_t *hist, *fine;
+  uint64_t *below;
   int *flag;
   RKR_TRY(tmp_alloc(bh, &hist, (size_t)nq * 64, st));
+  RKR_TRY(tmp_alloc(bfi, &fine, (size_t)nq * 1024, st));
+  RKR_TRY(tmp_alloc(bb, &below, nq, st));
   RKR_TRY(tmp_alloc(bf, &flag, 1, st));
   RKR_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nq * 64, st));
+  RKR_CUDA(cudaMemsetAsync(fine, 0, sizeof(uint32_t) * (size_t)nq * 1024, st));
   RKR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  RKR_TRY(tc_theta_pass(1, idx, idx->Ut, qc.Qt, 0, g.bf, g.fmin, g.tau, g.JU, g.JL, hist,
-                        nullptr, nullptr, nullptr, nullptr, nullptr, kThetaSplit, flag, st));
+  ThetaArgs a = theta_args(g, 0);
+  a.hist = hist;
+  RKR_TRY(tc_theta_pass(1, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
   k_cutoff<<<(nq + 127) / 128, 128, 0, st>>>(nq, hist, hist + (size_t)nq * 32, qc.kq_d, g.nlev,
-                                             lstar_d, ncand_d);
+                                             lstar_d, below, ncand_d);
   note_launch();
   RKR_CUDA(cudaGetLastError());
-  RKR_TRY(check_flag(flag, "theta pass 1", st));
+  a.hist = nullptr;
+  a.lstar = lstar_d;
+  a.fine = fine;
+  RKR_TRY(tc_theta_pass(3, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
+  k_cutoff_fine<<<(nq + 127) / 128, 128, 0, st>>>(nq, fine, below, lstar_d, qc.kq_d, g.scale,
+                                                  cap_d);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  RKR_TRY(check_flag(flag, "theta passes 1 and 3", st));
   plan.ncand.resize(nq);
   plan.lstar.resize(nq);
   RKR_CUDA(cudaMemcpyAsync(plan.ncand.data(), ncand_d, sizeof(int64_t) * nq,
@@ -486,11 +554,11 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
   return RKR_OK;
 }
 
-// Candidates of queries [qa, qb) into per-query segments.
+// Pass 2: candidates of queries [qa, qb) appended to per-query segments.
 static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, int qa, int qb,
-                                  const Grid &g, const int32_t *lstar_d, const int64_t *qoff_d,
-                                  uint32_t *cursor_d, int32_t *cand_u, int32_t *cand_q,
-                                  cudaStream_t st) {
+                                  const Grid &g, const int32_t *lstar_d, const uint32_t *cap_d,
+                                  const int64_t *qoff_d, uint32_t *cursor_d, int32_t *cand_u,
+                                  int32_t *cand_q, cudaStream_t st) {
   TcSide sub = qc.Qt;
   sub.owned = false;
   sub.rows = qb - qa;
@@ -502,8 +570,14 @@ static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, i
   int *flag;
   RKR_TRY(tmp_alloc(bf, &flag, 1, st));
   RKR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  RKR_TRY(tc_theta_pass(2, idx, idx->Ut, sub, qa, g.bf, g.fmin, g.tau, g.JU, g.JL, nullptr,
-                        lstar_d, qoff_d, cursor_d, cand_u, cand_q, kThetaSplit, flag, st));
+  ThetaArgs a = theta_args(g, qa);
+  a.lstar = lstar_d;
+  a.cap = cap_d;
+  a.qoff = qoff_d;
+  a.qcursor = cursor_d;
+  a.cand_u = cand_u;
+  a.cand_q = cand_q;
+  RKR_TRY(tc_theta_pass(2, idx, idx->Ut, sub, a, kThetaSplit, flag, st));
   return check_flag(flag, "theta pass 2", st);
 }
 
@@ -572,16 +646,20 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
                                                                val, th, suser, ths, hist);
   note_launch();
   RKR_CUDA(cudaGetLastError());
-  int64_t refined = 0;
-  RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, sstart, slen, suser, ths, hist, st,
-                     &refined));
+  int64_t refined[2] = {0, 0};
+  RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, ths, hist,
+                     st, refined));
   k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
                                                                  hist);
   note_launch();
   RKR_CUDA(cudaGetLastError());
-  if (ties_d) {
-    unsigned long long r = (unsigned long long)refined;
-    RKR_CUDA(cudaMemcpyAsync(ties_d, &r, sizeof(r), cudaMemcpyHostToDevice, st));
+  if (ties_d) {  // accumulate over chunks: [0] undecided items, [1] canonical evaluations
+    unsigned long long r[2] = {0, 0};
+    RKR_CUDA(cudaMemcpyAsync(r, ties_d, sizeof(r), cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+    r[0] += (unsigned long long)refined[0];
+    r[1] += (unsigned long long)refined[1];
+    RKR_CUDA(cudaMemcpyAsync(ties_d, r, sizeof(r), cudaMemcpyHostToDevice, st));
     RKR_CUDA(cudaStreamSynchronize(st));
   }
   k_scatter_counts<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
@@ -594,22 +672,26 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
                             int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
                             int32_t *case_d, int32_t *nc_d, rkr_query_stats *stats,
                             cudaStream_t st) {
-  DevBuf bl, bn;
+  DevBuf bl, bn, bcap;
   int32_t *lstar_d;
   int64_t *ncand_d;
+  uint32_t *cap_d;
   RKR_TRY(tmp_alloc(bl, &lstar_d, nq, st));
   RKR_TRY(tmp_alloc(bn, &ncand_d, nq, st));
+  RKR_TRY(tmp_alloc(bcap, &cap_d, nq, st));
+  DevBuf bse;
+  int *sel_err;
+  RKR_TRY(tmp_alloc(bse, &sel_err, 1, st));
+  RKR_CUDA(cudaMemsetAsync(sel_err, 0, sizeof(int), st));
   Plan plan;
   Timer t1(st);
-  const Grid grid{qc.bf, idx->fmin, idx->tau, idx->JU, idx->JL, idx->nlev_a};
-  RKR_TRY(screen_plan(idx, qc, nq, grid, st, lstar_d, ncand_d, plan));
+  const Grid grid{qc.bf,  idx->fmin, idx->tau, idx->JU, idx->JL, idx->nlev_a,
+                  idx->N, idx->N,    (uint32_t)(idx->m * idx->s), (uint32_t)idx->s};
+  RKR_TRY(screen_plan(idx, qc, nq, grid, st, lstar_d, cap_d, ncand_d, plan));
   double ms_theta = t1.stop(), ms_res = 0.0, ms_sel = 0.0;
   int64_t total = 0;
   int wide = 0;
-  for (int q = 0; q < nq; ++q) {
-    total += plan.ncand[q];
-    wide += plan.lstar[q] >= idx->nlev_a - 1;
-  }
+  for (int q = 0; q < nq; ++q) wide += plan.lstar[q] >= idx->nlev_a - 1;
   std::vector<int64_t> qoff(nq + 1, 0);
   for (int q = 0; q < nq; ++q) qoff[q + 1] = qoff[q] + plan.ncand[q];
   DevBuf bo;
@@ -639,9 +721,17 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     RKR_CUDA(cudaMemcpyAsync(qoff_rel, rel.data(), sizeof(int64_t) * (nq + 1),
                              cudaMemcpyHostToDevice, st));
     RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
+    RKR_CUDA(cudaMemsetAsync(cu, 0xff, sizeof(int32_t) * std::max<int64_t>(cnt, 1), st));
     Timer t2(st);
-    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, qoff_rel, cursor, cu, cq, st));
+    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, cap_d, qoff_rel, cursor, cu, cq, st));
     ms_theta += t2.stop();
+    {
+      std::vector<uint32_t> hc(nq);
+      RKR_CUDA(cudaMemcpyAsync(hc.data(), cursor, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost,
+                               st));
+      RKR_CUDA(cudaStreamSynchronize(st));
+      for (int q = qa; q < qb; ++q) total += hc[q];
+    }
     Timer t3(st);
     if (cnt > 0) {
       k_resolve_approx<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
@@ -655,14 +745,20 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     size_t sm = sizeof(SortEnt) * kMaxK;
     RKR_CUDA(cudaFuncSetAttribute(k_select_approx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
-    k_select_approx<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, C, qc.kq_d, c,
+    k_select_approx<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cursor, C, qc.kq_d, c,
                                                       (uint32_t)idx->s, idx->tau, idx->fmin,
                                                       idx->delta, qc.out_off_d, users_d, nlo_d,
-                                                      nup_d, est_d, case_d, nc_d); note_launch();
+                                                      nup_d, est_d, case_d, nc_d, sel_err);
+    note_launch();
     RKR_CUDA(cudaGetLastError());
     ms_sel += t4.stop();
   }
   RKR_CUDA(cudaStreamSynchronize(st));
+  {
+    int h = 0;
+    RKR_CUDA(cudaMemcpy(&h, sel_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return fail(RKR_EINTERNAL, "fewer than k candidates for a query");
+  }
   if (stats) {
     stats->pairs = idx->n * (int64_t)nq;
     stats->candidates = total;
@@ -679,25 +775,29 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
 rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
                            int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
                            cudaStream_t st) {
-  DevBuf bl, bn, bt;
+  DevBuf bl, bn, bt, bcap;
   int32_t *lstar_d;
   int64_t *ncand_d;
+  uint32_t *cap_d;
   unsigned long long *ties_d;
   RKR_TRY(tmp_alloc(bl, &lstar_d, nq, st));
   RKR_TRY(tmp_alloc(bn, &ncand_d, nq, st));
-  RKR_TRY(tmp_alloc(bt, &ties_d, 1, st));
-  RKR_CUDA(cudaMemsetAsync(ties_d, 0, sizeof(unsigned long long), st));
+  RKR_TRY(tmp_alloc(bcap, &cap_d, nq, st));
+  DevBuf bse;
+  int *sel_err;
+  RKR_TRY(tmp_alloc(bse, &sel_err, 1, st));
+  RKR_CUDA(cudaMemsetAsync(sel_err, 0, sizeof(int), st));
+  RKR_TRY(tmp_alloc(bt, &ties_d, 2, st));
+  RKR_CUDA(cudaMemsetAsync(ties_d, 0, 2 * sizeof(unsigned long long), st));
   Plan plan;
   Timer t1(st);
-  const Grid grid{qc.xbf, idx->xg0, idx->xg, idx->XJU, idx->XJL, idx->nlev_x};
-  RKR_TRY(screen_plan(idx, qc, nq, grid, st, lstar_d, ncand_d, plan));
+  const Grid grid{qc.xbf,   idx->xg0, idx->xg,       idx->XJU, idx->XJL, idx->nlev_x,
+                  idx->XHI, idx->XLO, (uint32_t)idx->m, 1u};
+  RKR_TRY(screen_plan(idx, qc, nq, grid, st, lstar_d, cap_d, ncand_d, plan));
   double ms_theta = t1.stop(), ms_res = 0.0, ms_sel = 0.0;
   int64_t total = 0;
   int wide = 0;
-  for (int q = 0; q < nq; ++q) {
-    total += plan.ncand[q];
-    wide += plan.lstar[q] >= idx->nlev_x - 1;
-  }
+  for (int q = 0; q < nq; ++q) wide += plan.lstar[q] >= idx->nlev_x - 1;
   std::vector<int64_t> qoff(nq + 1, 0);
   for (int q = 0; q < nq; ++q) qoff[q + 1] = qoff[q] + plan.ncand[q];
   for (auto ch : chunk_queries(plan.ncand, candidate_budget())) {
@@ -717,9 +817,17 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
     RKR_CUDA(cudaMemcpyAsync(qoff_rel, rel.data(), sizeof(int64_t) * (nq + 1),
                              cudaMemcpyHostToDevice, st));
     RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
+    RKR_CUDA(cudaMemsetAsync(cu, 0xff, sizeof(int32_t) * std::max<int64_t>(cnt, 1), st));
     Timer t2(st);
-    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, qoff_rel, cursor, cu, cq, st));
+    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, cap_d, qoff_rel, cursor, cu, cq, st));
     ms_theta += t2.stop();
+    {
+      std::vector<uint32_t> hc(nq);
+      RKR_CUDA(cudaMemcpyAsync(hc.data(), cursor, sizeof(uint32_t) * nq, cudaMemcpyDeviceToHost,
+                               st));
+      RKR_CUDA(cudaStreamSynchronize(st));
+      for (int q = qa; q < qb; ++q) total += hc[q];
+    }
     Timer t3(st);
     if (cnt > 0) RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu, cq, ccount, ties_d, st));
     ms_res += t3.stop();
@@ -727,19 +835,25 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
     size_t sm = sizeof(SortEnt) * kMaxK;
     RKR_CUDA(cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
-    k_select_exact<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cu, ccount, qc.kq_d,
-                                                     qc.out_off_d, users_d, ranks_d); note_launch();
+    k_select_exact<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cursor, cu, ccount, qc.kq_d,
+                                                     qc.out_off_d, users_d, ranks_d, sel_err);
+    note_launch();
     RKR_CUDA(cudaGetLastError());
     ms_sel += t4.stop();
   }
-  unsigned long long ties = 0;
-  RKR_CUDA(cudaMemcpyAsync(&ties, ties_d, sizeof(ties), cudaMemcpyDeviceToHost, st));
+  unsigned long long tiesv[2] = {0, 0};
+  RKR_CUDA(cudaMemcpyAsync(tiesv, ties_d, sizeof(tiesv), cudaMemcpyDeviceToHost, st));
   RKR_CUDA(cudaStreamSynchronize(st));
+  {
+    int h = 0;
+    RKR_CUDA(cudaMemcpy(&h, sel_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return fail(RKR_EINTERNAL, "fewer than k candidates for a query");
+  }
   if (stats) {
     stats->pairs = idx->n * (int64_t)nq;
     stats->candidates = total;
-    stats->fp64_dots = total + (int64_t)ties;
-    stats->near_ties = (int64_t)ties;
+    stats->fp64_dots = total + (int64_t)tiesv[1];
+    stats->near_ties = (int64_t)tiesv[0];
     stats->wide_queries = wide;
     stats->ms_theta = ms_theta;
     stats->ms_resolve = ms_res;

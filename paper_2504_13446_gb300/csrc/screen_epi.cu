@@ -264,14 +264,21 @@ __global__ void k_xgrid(int64_t n, const double *__restrict__ fmin,
   g0f[u] = __double2float_rd(g);
 }
 
+// Interval counts on the exact grid: an item whose count c(s) = #{j : x_j < s}
+// is known to lie in [clo, chi] adds to Hlo[clo] and Hhi[chi]; then
+// XLO[j] = #{clo > j} <= #{p : s(u,p) > x_j} <= #{chi > j} = XHI[j].
+// Histograms are 16-bit pairs packed in 32-bit words; a row whose tail holds
+// more than 65535 items gets the trivial bounds 0 and m instead.
 struct EpiXT {
   struct Thread {
     float skip, b;
     BinFP bf;
     double g0;
     int64_t row;
+    uint32_t cnt;
   };
-  static constexpr size_t kSmem = 128 * (kXG + 1) * sizeof(uint32_t);
+  static constexpr int kW = (kXG + 2) / 2;  // 32-bit words per histogram row
+  static constexpr size_t kSmem = sizeof(uint32_t) * (2 * 128 * kW + 256);
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
@@ -279,11 +286,12 @@ struct EpiXT {
   const BinFP *xbin;
   const double *xg0;
   const float *g0f;
-  uint32_t *XC;
-  PairQueue q;
-  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &) const {
+  uint32_t *XLO, *XHI;
+  uint32_t mcount;
+  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &ts) const {
     uint32_t *H = (uint32_t *)S;
-    for (int i = et; i < 128 * (kXG + 1); i += 256) H[i] = 0;
+    for (int i = et; i < 2 * 128 * kW; i += 256) H[i] = 0;
+    ts.cnt = 0;
   }
   __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
     ts.row = (int64_t)rb * tc::BM + r;
@@ -298,66 +306,53 @@ struct EpiXT {
   }
   __device__ void chunk(char *S, int, int ct, int r, int col, const float (&v)[32],
                         Thread &ts) const {
-    uint32_t *H = (uint32_t *)S + r * (kXG + 1);
     const int64_t c0 = (int64_t)ct * bn + col;
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      if (v[j] > ts.skip && c0 + j < ncols) count(H, v[j], (int)(c0 + j), ts);
+      if (v[j] > ts.skip && c0 + j < ncols) count((uint32_t *)S, r, v[j], ts);
   }
-  __device__ __noinline__ void count(uint32_t *H, float v, int c, const Thread &ts) const {
+  __device__ __noinline__ void count(uint32_t *S, int r, float v, Thread &ts) const {
     int clo, chi;
     bin_interval(ts.bf, ts.g0, kXG, __fsub_rd(v, ts.b), __fadd_ru(v, ts.b), clo, chi);
-    if (clo == chi) {
-      if (clo > 0) atomicAdd(&H[clo], 1u);
-    } else {
-      q.push((int)ts.row, c);
-    }
+    if (chi == 0) return;
+    uint32_t *Hlo = S + r * kW, *Hhi = S + 128 * kW + r * kW;
+    atomicAdd(&Hlo[clo >> 1], 1u << ((clo & 1) * 16));
+    atomicAdd(&Hhi[chi >> 1], 1u << ((chi & 1) * 16));
+    ++ts.cnt;
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
-  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &) const {
+  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &ts) const {
+    uint32_t *tot = (uint32_t *)S + 2 * 128 * kW;
+    const int w = (et >> 5) + 2, lane = et & 31;
+    const int row = (w & 3) * 32 + lane, half = (et >> 5) >> 2;
+    tot[half * 128 + row] = ts.cnt;
+    tc::epi_sync();
     if (et >= 128) return;
-    int64_t row = (int64_t)u.rb0 * tc::BM + et;
-    if (row >= nrows) return;
-    const uint32_t *H = (const uint32_t *)S + et * (kXG + 1);
-    uint32_t run = 0;
+    int64_t g = (int64_t)u.rb0 * tc::BM + et;
+    if (g >= nrows) return;
+    const uint32_t *Hlo = (const uint32_t *)S + et * kW;
+    const uint32_t *Hhi = (const uint32_t *)S + 128 * kW + et * kW;
+    const bool ok = tot[et] + tot[128 + et] <= 65535u;
+    uint32_t rlo = 0, rhi = 0;
     for (int c = kXG; c >= 1; --c) {
-      run += H[c];
-      XC[row * kXG + (c - 1)] = run;  // #{p : c(s_p) > c - 1}
+      rlo += (Hlo[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
+      rhi += (Hhi[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
+      XLO[g * kXG + (c - 1)] = ok ? rlo : 0u;
+      XHI[g * kXG + (c - 1)] = ok ? rhi : mcount;
     }
   }
 };
 
-__global__ void k_xt_refine(const int2 *__restrict__ items, const unsigned long long *count,
-                            unsigned long long cap, const float *__restrict__ U,
-                            const float *__restrict__ Ps, int d, const double *__restrict__ xg0,
-                            const double *__restrict__ xdx, uint32_t *__restrict__ XC) {
-  unsigned long long c = *count;
-  if (c > cap) c = cap;
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    int2 it = items[i];
-    double s = canon_dot(U + (int64_t)it.x * d, Ps + (int64_t)it.y * d, d);
-    int cc = exact_c(s, xg0[it.x], xdx[it.x], kXG);
-    for (int j = 0; j < cc; ++j) atomicAdd(&XC[(int64_t)it.x * kXG + j], 1u);
-  }
-}
-
 rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cudaStream_t st,
-                          int64_t *refined) {
+                          int64_t *) {
   constexpr int BN = 256;
   const int64_t n = idx->n, m = idx->m;
   tc::RowBound *tb = nullptr;
   RKR_TRY(tc_tile_bounds(Pt, BN, 1, &tb, st));
   float *g0f;
-  unsigned long long *qcount;
-  int2 *qitems;
   int *flags;
-  const unsigned long long cap = std::max<int64_t>(64 * n, 1 << 20);
   RKR_CUDA(cudaMallocAsync(&g0f, sizeof(float) * n, st));
-  RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
-  RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
   RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 2, st));
-  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
   k_xgrid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, idx->fmin, idx->delta, idx->xfloor,
                                                        idx->xg0, g0f);
@@ -366,26 +361,16 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   EpiXT e;
   e.nrows = n; e.ncols = m; e.bn = BN; e.rowb = Ut.rb3; e.tileb = tb;
   e.gacc = tc_gacc(Ut.kp, 1); e.gcan = tc_gcan(idx->d);
-  e.xbin = idx->xbin; e.xg0 = idx->xg0; e.g0f = g0f; e.XC = idx->XC;
-  e.q = PairQueue{qitems, qcount, cap, flags + 1};
+  e.xbin = idx->xbin; e.xg0 = idx->xg0; e.g0f = g0f; e.XLO = idx->XLO; e.XHI = idx->XHI;
+  e.mcount = (uint32_t)m;
   rkr_status s = launch_screen<BN, 3>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
-  if (s == RKR_OK) {
-    k_xt_refine<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
-                                                idx->xg0, idx->xdx, idx->XC);
-    note_launch();
-  }
   int hf[2] = {0, 0};
-  unsigned long long hq = 0;
   cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&hq, qcount, sizeof(hq), cudaMemcpyDeviceToHost, st);
   cudaError_t err = cudaStreamSynchronize(st);
-  for (void *p : {(void *)tb, (void *)g0f, (void *)qcount, (void *)qitems, (void *)flags})
-    cudaFreeAsync(p, st);
+  for (void *p : {(void *)tb, (void *)g0f, (void *)flags}) cudaFreeAsync(p, st);
   if (err != cudaSuccess) return cuda_fail(err, "tc_exact_table");
   RKR_TRY(s);
   if (hf[0]) return fail(RKR_ETIMEOUT, "exact-table screen wait timed out (%d)", hf[0]);
-  if (hf[1]) return fail(RKR_EINTERNAL, "exact-table refinement queue overflow");
-  if (refined) *refined = (int64_t)hq;
   return RKR_OK;
 }
 
@@ -395,8 +380,20 @@ constexpr int kThetaBN = 128;
 
 // Pass 1 accumulates, per query, histograms of the rank level of the upper
 // bound (from the low end of the bin interval) and of the lower bound (from
-// its high end).  Pass 2 writes (user, query) when the lower bound may reach
-// the query's cutoff level.
+// its high end).  Pass 3 refines the cutoff inside the boundary level L*: each
+// pair whose upper bound falls in level L* adds its exact upper-bound value to
+// a 1024-bucket histogram of that level's range.  Pass 2 writes (user, query)
+// when the lower bound may reach the query's cutoff: level test first, then
+// the exact lower-bound value against the refined cap.
+constexpr int kFine = 1024;
+
+__device__ __forceinline__ void level_range(int L, uint32_t scale, uint64_t &base,
+                                            uint64_t &width) {
+  uint64_t hi = level_bound(L, scale);
+  base = L == 0 ? 0 : level_bound(L - 1, scale) + 1;
+  width = (hi - base + kFine) / kFine;  // ceil((hi - base + 1) / kFine)
+}
+
 template <int PASS>
 struct EpiTheta {
   struct Thread {
@@ -406,7 +403,7 @@ struct EpiTheta {
     int64_t u;
   };
   static constexpr size_t kSmem =
-      sizeof(int) * (2 * 128 * 33 + 2 * kThetaBN * 32 + kThetaBN);
+      sizeof(int) * (2 * 128 * 33 + 2 * kThetaBN * 32 + 2 * kThetaBN);
   int64_t nrows, ncols;
   int tau;
   int qa;  // global index of query column 0
@@ -415,8 +412,12 @@ struct EpiTheta {
   const BinFP *binfp;
   const double *fmin;
   const int16_t *JU, *JL;
+  const uint32_t *thi, *tlo;    // tables behind the upper and lower bounds
+  uint32_t top, scale;          // upper bound below the grid; level scale
   uint32_t *hist_up, *hist_lo;  // PASS 1: [nq][32], indexed by global query
-  const int32_t *lstar;         // PASS 2: indexed by global query
+  const int32_t *lstar;         // PASS 2, 3: indexed by global query
+  const uint32_t *cap;          // PASS 2
+  uint32_t *fine;               // PASS 3: [nq][kFine]
   const int64_t *qoff;
   uint32_t *qcursor;
   int32_t *cand_u, *cand_q;
@@ -424,6 +425,7 @@ struct EpiTheta {
   __device__ int *jtab(char *S) const { return (int *)S; }
   __device__ int *hist(char *S) const { return (int *)S + 2 * 128 * 33; }
   __device__ int *lst(char *S) const { return hist(S) + 2 * kThetaBN * 32; }
+  __device__ uint32_t *caps(char *S) const { return (uint32_t *)(lst(S) + kThetaBN); }
 
   __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &) const {
     if (PASS == 1) {
@@ -431,9 +433,11 @@ struct EpiTheta {
       for (int i = et; i < 2 * kThetaBN * 32; i += 256) H[i] = 0;
     } else {
       int *L = lst(S);
+      uint32_t *C = caps(S);
       for (int i = et; i < kThetaBN; i += 256) {
         int64_t q = (int64_t)u.ct0 * kThetaBN + i;
         L[i] = q < ncols ? lstar[qa + q] : 0;
+        if (PASS == 2) C[i] = q < ncols ? cap[qa + q] : 0u;
       }
     }
   }
@@ -473,13 +477,27 @@ struct EpiTheta {
           }
           atomicAdd(&H[(col + j) * 32 + lu], 1);
           atomicAdd(&H[kThetaBN * 32 + (col + j) * 32 + ll], 1);
+        } else if (PASS == 3) {
+          const int Lq = Ls[col + j];
+          // level of the upper bound is L* exactly: above every smaller level's start
+          if (jlo >= ju[Lq] && (Lq == 0 || jlo < ju[Lq - 1])) refine((int)(c0 + j), jlo, Lq, ts);
         } else if (jhi >= jl[Ls[col + j]]) {
-          emit((int)(c0 + j), ts);
+          emit((int)(c0 + j), jhi, caps(S)[col + j], ts);
         }
       }
     }
   }
-  __device__ __noinline__ void emit(int c, const Thread &ts) const {
+  __device__ __noinline__ void refine(int c, int jlo, int Lq, const Thread &ts) const {
+    uint64_t v = jlo >= 1 ? thi[ts.u * tau + jlo - 1] : top;
+    uint64_t base, width;
+    level_range(Lq, scale, base, width);
+    uint64_t bkt = v >= base ? (v - base) / width : 0;
+    if (bkt >= kFine) bkt = kFine - 1;
+    atomicAdd(&fine[(int64_t)(qa + c) * kFine + bkt], 1u);
+  }
+  __device__ __noinline__ void emit(int c, int jhi, uint32_t capq, const Thread &ts) const {
+    uint32_t lb = jhi < tau ? tlo[ts.u * tau + jhi] : 0u;
+    if (lb > capq) return;
     int q = qa + c;
     uint32_t pos = atomicAdd(&qcursor[q], 1u);
     int64_t at = qoff[q] + pos;
@@ -500,40 +518,34 @@ struct EpiTheta {
   }
 };
 
-// Theta pass over queries [qa, qa + Qt.rows) (Qt holds exactly those rows).
-rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
-                         int qa, const BinFP *binfp, const double *fmin, int tau,
-                         const int16_t *JU, const int16_t *JL, uint32_t *hist,
-                         const int32_t *lstar, const int64_t *qoff, uint32_t *qcursor,
-                         int32_t *cand_u, int32_t *cand_q, int split, int *err, cudaStream_t st) {
+template <int PASS>
+static rkr_status theta_launch(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
+                               const ThetaArgs &a, int split, int *err, cudaStream_t st) {
   const int64_t n = idx->n, nq = Qt.rows;
   tc::RowBound *tb = nullptr;
   RKR_TRY(tc_tile_bounds(Qt, kThetaBN, split, &tb, st));
   int nct = (int)((nq + kThetaBN - 1) / kThetaBN);
   int parts = std::max(1, (2 * sm_count() + nct - 1) / nct);
   tc::Schedule sch = col_schedule(n, nq, kThetaBN, parts);
-  rkr_status s;
-  if (pass == 1) {
-    EpiTheta<1> e;
-    e.nrows = n; e.ncols = nq; e.tau = tau; e.qa = qa;
-    e.rowb = split ? Ut.rb3 : Ut.rb1; e.tileb = tb;
-    e.gacc = tc_gacc(Ut.kp, split); e.gcan = tc_gcan(idx->d);
-    e.binfp = binfp; e.fmin = fmin; e.JU = JU; e.JL = JL;
-    e.hist_up = hist; e.hist_lo = hist + (size_t)(qa + nq) * 32;
-    e.lstar = nullptr; e.qoff = nullptr; e.qcursor = nullptr; e.cand_u = nullptr; e.cand_q = nullptr;
-    s = launch_screen<kThetaBN, 4>(Ut, Qt, split, sch, e, err, st);
-  } else {
-    EpiTheta<2> e;
-    e.nrows = n; e.ncols = nq; e.tau = tau; e.qa = qa;
-    e.rowb = split ? Ut.rb3 : Ut.rb1; e.tileb = tb;
-    e.gacc = tc_gacc(Ut.kp, split); e.gcan = tc_gcan(idx->d);
-    e.binfp = binfp; e.fmin = fmin; e.JU = JU; e.JL = JL;
-    e.hist_up = nullptr; e.hist_lo = nullptr;
-    e.lstar = lstar; e.qoff = qoff; e.qcursor = qcursor; e.cand_u = cand_u; e.cand_q = cand_q;
-    s = launch_screen<kThetaBN, 4>(Ut, Qt, split, sch, e, err, st);
-  }
+  EpiTheta<PASS> e;
+  e.nrows = n; e.ncols = nq; e.tau = a.tau; e.qa = a.qa;
+  e.rowb = split ? Ut.rb3 : Ut.rb1; e.tileb = tb;
+  e.gacc = tc_gacc(Ut.kp, split); e.gcan = tc_gcan(idx->d);
+  e.binfp = a.binfp; e.fmin = a.fmin; e.JU = a.JU; e.JL = a.JL;
+  e.thi = a.thi; e.tlo = a.tlo; e.top = a.top; e.scale = a.scale;
+  e.hist_up = a.hist; e.hist_lo = a.hist ? a.hist + (size_t)(a.qa + nq) * 32 : nullptr;
+  e.lstar = a.lstar; e.cap = a.cap; e.fine = a.fine;
+  e.qoff = a.qoff; e.qcursor = a.qcursor; e.cand_u = a.cand_u; e.cand_q = a.cand_q;
+  rkr_status s = launch_screen<kThetaBN, 4>(Ut, Qt, split, sch, e, err, st);
   cudaFreeAsync(tb, st);
   return s;
+}
+
+rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
+                         const ThetaArgs &a, int split, int *err, cudaStream_t st) {
+  if (pass == 1) return theta_launch<1>(idx, Ut, Qt, a, split, err, st);
+  if (pass == 2) return theta_launch<2>(idx, Ut, Qt, a, split, err, st);
+  return theta_launch<3>(idx, Ut, Qt, a, split, err, st);
 }
 
 // =============================================================== recount
@@ -595,24 +607,43 @@ struct EpiRC {
   __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
 };
 
+// Exact position of each queued score among its segment's thresholds.  A
+// CUDA-core FP32 dot product with its bound settles most items; the rest are
+// evaluated canonically.
 __global__ void k_rc_refine(const int2 *__restrict__ items, const unsigned long long *count,
                             unsigned long long cap, const int64_t *__restrict__ seg_start,
                             const int32_t *__restrict__ seg_len,
                             const int32_t *__restrict__ seg_user, const double *__restrict__ ths,
-                            const float *__restrict__ U, const float *__restrict__ Ps, int d,
-                            uint32_t *__restrict__ hist) {
+                            const float *__restrict__ U, const float *__restrict__ unrm,
+                            const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int d,
+                            uint32_t *__restrict__ hist, unsigned long long *nfp64) {
   unsigned long long c = *count;
   if (c > cap) c = cap;
+  const float cfac = screen_cfac(d);
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     int2 it = items[i];
     int64_t st0 = seg_start[it.x];
     int L = seg_len[it.x];
-    double s = canon_dot(U + (int64_t)seg_user[it.x] * d, Ps + (int64_t)it.y * d, d);
+    const int64_t u = seg_user[it.x];
+    const float *uu = U + u * d, *pp = Ps + (int64_t)it.y * d;
+    float acc = 0.0f;
+    for (int k = 0; k < d; ++k) acc = fmaf(uu[k], pp[k], acc);
+    float b = screen_bound(cfac, unrm[u], pnrm_s[it.y]);
+    double lo = (double)__fsub_rd(acc, b), hi = (double)__fadd_ru(acc, b);
     const double *t = ths + st0;
     int a0 = 0, a1 = L;
-    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < s) a0 = md + 1; else a1 = md; }
-    atomicAdd(&hist[2 * st0 + a0], 1u);
+    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < lo) a0 = md + 1; else a1 = md; }
+    int pa = a0;
+    a1 = L;
+    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < hi) a0 = md + 1; else a1 = md; }
+    int pos = pa;
+    if (a0 != pa) {
+      atomicAdd(nfp64, 1ull);
+      double s = canon_dot(uu, pp, d);
+      while (pos < a0 && t[pos] < s) ++pos;
+    }
+    atomicAdd(&hist[2 * st0 + pos], 1u);
   }
 }
 
@@ -638,8 +669,9 @@ __global__ void k_gather_side(const __nv_bfloat16 *__restrict__ hi,
 }
 
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
-                      const int64_t *seg_start, const int32_t *seg_len, const int32_t *seg_user,
-                      const double *ths, uint32_t *hist, cudaStream_t st, int64_t *refined) {
+                      int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
+                      const int32_t *seg_user, const double *ths, uint32_t *hist,
+                      cudaStream_t st, int64_t *refined) {
   constexpr int BN = 256;
   const int64_t m = idx->m;
   if (nseg <= 0) return RKR_OK;
@@ -663,7 +695,10 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   unsigned long long *qcount;
   int2 *qitems;
   int *flags;
-  const unsigned long long cap = std::max<int64_t>(256 * nseg, 1 << 20);
+  const unsigned long long cap = std::max<int64_t>(16 * ncand, 1 << 22);
+  unsigned long long *nfp64;
+  RKR_CUDA(cudaMallocAsync(&nfp64, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(nfp64, 0, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
   RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 2, st));
@@ -676,23 +711,25 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
   rkr_status s = launch_screen<BN, 4>(A, Pt, 1, row_schedule(nseg, m, BN), e, flags, st);
   if (s == RKR_OK) {
-    k_rc_refine<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, seg_start, seg_len,
-                                                seg_user, ths, idx->U, idx->Ps, idx->d, hist);
+    k_rc_refine<<<8 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, seg_start, seg_len,
+                                                seg_user, ths, idx->U, idx->unrm, idx->Ps,
+                                                idx->pnrm_s, idx->d, hist, nfp64);
     note_launch();
   }
   int hf[2] = {0, 0};
-  unsigned long long hq = 0;
+  unsigned long long hq = 0, h64 = 0;
   cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&hq, qcount, sizeof(hq), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&h64, nfp64, sizeof(h64), cudaMemcpyDeviceToHost, st);
   cudaError_t err = cudaStreamSynchronize(st);
   for (void *p : {(void *)A.hi, (void *)A.lo, (void *)A.rb1, (void *)A.rb3, (void *)tb,
-                  (void *)qcount, (void *)qitems, (void *)flags})
+                  (void *)qcount, (void *)qitems, (void *)flags, (void *)nfp64})
     cudaFreeAsync(p, st);
   if (err != cudaSuccess) return cuda_fail(err, "tc_recount");
   RKR_TRY(s);
   if (hf[0]) return fail(RKR_ETIMEOUT, "recount screen wait timed out (%d)", hf[0]);
-  if (hf[1]) return fail(RKR_EINTERNAL, "recount refinement queue overflow");
-  if (refined) *refined = (int64_t)hq;
+  if (hf[1]) return fail(RKR_EINTERNAL, "recount refinement queue overflow (%llu items)", hq);
+  if (refined) { refined[0] = (int64_t)hq; refined[1] = (int64_t)h64; }
   return RKR_OK;
 }
 

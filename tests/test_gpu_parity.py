@@ -43,15 +43,15 @@ def check_index(ora, gpu):
 
 
 def check_exact_table(ora, gpu, U, P, floor_rank=0):
-    """The exact count table: #{p : s(u,p) > x_j} on each user's tail grid, where
+    """The exact count bounds: XLO <= #{p : s(u,p) > x_j} <= XHI on each user's tail grid, where
     x_0 is the sampled table's threshold at its last column whose estimated count
     reaches the floor rank and x_{G-1} = f_max (same threshold formula)."""
     m, s, tau = P.shape[0], ora["s"], ora["tau"]
     R = floor_rank or max(2048, m // 16)
     S = oracle.scores(U, P)
     grid = gpu.export("xgrid")
-    xc = gpu.export("xcount")
-    G = xc.shape[1]
+    xlo, xhi = gpu.export("xlo"), gpu.export("xhi")
+    G = xlo.shape[1]
     for i in range(U.shape[0]):
         Nrow = ora["N"][i].astype(np.int64)
         below = np.nonzero(Nrow < s * R)[0]
@@ -62,7 +62,9 @@ def check_exact_table(ora, gpu, U, P, floor_rank=0):
         assert grid[i, 0] == g0 and grid[i, 1] == (ora["fmax"][i] - g0) / float(G - 1), i
         srt = np.sort(S[i])
         cnt = S.shape[1] - np.searchsorted(srt, x, side="right")
-        assert (xc[i] == cnt).all(), (i, np.nonzero(xc[i] != cnt)[0][:5])
+        assert (xlo[i] <= cnt).all() and (cnt <= xhi[i]).all(), i
+        tight = np.mean(xlo == xhi)
+    assert tight > 0.5, tight   # most counts are decided by the screen alone
 
 
 def check_exact(U, P, Q, k, gpu):
