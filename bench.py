@@ -223,8 +223,9 @@ def bench_ours(args):
             "exact": {kk: qe0[kk] for kk in ("ms_theta", "ms_resolve", "ms_select")},
         },
         "candidates": {"approx": qa0["candidates"], "exact": qe0["candidates"],
-                       "exact_near_ties": qe0["near_ties"], "wide_queries":
-                           [qa0["wide_queries"], qe0["wide_queries"]]},
+                       "exact_recounted": qe0["recounted"],
+                       "exact_near_ties": qe0["near_ties"], "fp64_dots_exact": qe0["fp64_dots"],
+                       "wide_queries": [qa0["wide_queries"], qe0["wide_queries"]]},
         "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                      "peak_source": "FP32 CUDA-core peak from SM count and max SM clock "

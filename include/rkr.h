@@ -87,6 +87,8 @@ typedef struct {
   double ms_theta;          /* device time of the u.q screening passes */
   double ms_resolve;        /* device time of candidate resolution */
   double ms_select;         /* device time of per-query selection */
+  int64_t recounted;        /* exact path: candidates ranked by a re-screen of P (the others
+                               by their user's tail list) */
 } rkr_query_stats;
 
 /*

@@ -626,6 +626,17 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     RKR_TRY(dalloc(&idx->xbin, n));
     RKR_TRY(dalloc(&idx->XLO, (size_t)n * kXGrid));
     RKR_TRY(dalloc(&idx->XHI, (size_t)n * kXGrid));
+    idx->lcap = kListCap;
+    RKR_TRY(dalloc(&idx->xlistcol, n));
+    RKR_TRY(dalloc(&idx->xtop, n));
+    RKR_TRY(dalloc(&idx->xtopf, n));
+    RKR_TRY(dalloc(&idx->xlist, (size_t)n * kListCap));
+    RKR_TRY(dalloc(&idx->xlcnt, n));
+    RKR_TRY(dalloc(&idx->xbmax, n));
+    RKR_TRY(dalloc(&idx->ptile3, (size_t)((m + 255) / 256)));
+    k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(
+        n, tau, idx->N, (uint32_t)s, (uint64_t)std::min(idx->floor_rank, kListRank),
+        idx->xlistcol); note_launch();
     k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
                                                                (uint64_t)idx->floor_rank,
                                                                idx->xfloor); note_launch();
@@ -656,7 +667,8 @@ void index_release(rkr_index *idx) {
                   idx->pnrm_s, idx->fmin, idx->fmax, idx->delta, idx->binfp, idx->N,
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
                   idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
-                  idx->xfloor};
+                  idx->xfloor, idx->xlistcol, idx->xtop, idx->xtopf, idx->xlist, idx->xlcnt,
+                  idx->xbmax, idx->ptile3};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   tc_free(idx->Ut);

@@ -44,6 +44,18 @@ struct rkr_index {
   int16_t *XJU = nullptr, *XJL = nullptr;   // n x 32
   int32_t *xfloor = nullptr;                // n: paper column of x_0
 
+  // tail lists: per user, every item whose score may exceed x_top (the paper
+  // threshold whose estimated count is list_rank), sorted by screened score
+  int lcap = 0;
+  int32_t *xlistcol = nullptr;              // n: paper column of x_top
+  double *xtop = nullptr;                   // n
+  float *xtopf = nullptr;                   // n: x_top rounded down
+  uint2 *xlist = nullptr;                   // n x lcap: (item, float bits of screened score)
+  uint32_t *xlcnt = nullptr;                // n: entries, lcap + 1 = overflow
+  float *xbmax = nullptr;                   // n: largest screen bound of a user's entries
+  rkr::tc::RowBound *ptile3 = nullptr;      // item tile bounds of the split screen
+  int ptile_bn = 0;
+
   // bf16 operands of the tensor-core screens
   rkr::TcSide Ut, Pt;
 
@@ -100,6 +112,9 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       const int32_t *seg_user, const double *ths, uint32_t *hist,
                       cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
+constexpr int kListCap = 1024;
+constexpr int kListRank = 256;
+rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);
 
 // Row norms: FP64 canonical norms (optional) and FP32 upper bounds.
 rkr_status row_norms(const float *X, int64_t rows, int d, double *nrm64, float *nrm32,

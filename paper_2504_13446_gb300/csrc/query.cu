@@ -23,6 +23,7 @@
 #include "index.cuh"
 #include "select.cuh"
 #include "simt.cuh"
+#include "tcops.cuh"
 
 namespace rkr {
 
@@ -373,6 +374,72 @@ __global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_s
   int L = seg_len[sg];
   const uint32_t *h = hist + 2 * st0;
   for (int i = 0; i < L; ++i) ccount[order[st0 + i]] = h[i + 1];
+}
+
+// Exact ranks from the tail lists.  A candidate (u, q) with u.q >= x_top(u)
+// has rank 1 + #{p in list(u) : s(u,p) > u.q}, since every item scoring above
+// x_top is in the list.  Entries are sorted by screened score; those within
+// their bound of u.q are settled by an FP32 dot product with its bound, then
+// canonically.  Candidates below x_top (or with an overflowed list) are
+// passed on, unchanged, in cu_fb for the recount screen; others get -1 there.
+__global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
+                            const int32_t *__restrict__ cq, const float *__restrict__ U,
+                            const float *__restrict__ unrm, const float *__restrict__ Q,
+                            const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int d,
+                            const double *__restrict__ xtop, const uint2 *__restrict__ xlist,
+                            const uint32_t *__restrict__ xlcnt, int lcap,
+                            const float *__restrict__ xbmax, const tc::RowBound *__restrict__ rb3,
+                            const tc::RowBound *__restrict__ ptile, int pbn, float gacc,
+                            float gcan, uint32_t *__restrict__ ccount, int32_t *__restrict__ cu_fb,
+                            unsigned long long *__restrict__ stat) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t u = cu[i];
+  if (u < 0) { cu_fb[i] = -1; return; }
+  const float *uu = U + u * d;
+  const double theta = canon_dot(uu, Q + (int64_t)cq[i] * d, d);
+  const uint32_t L = xlcnt[u];
+  if (L > (uint32_t)lcap || theta < xtop[u]) {
+    cu_fb[i] = (int32_t)u;
+    atomicAdd(&stat[0], 1ull);
+    return;
+  }
+  cu_fb[i] = -1;
+  const uint2 *row = xlist + u * lcap;
+  const double B = (double)xbmax[u];
+  const double above_t = __dadd_ru(theta, B);   // v > above_t  =>  s >= v - b > theta
+  const double below_t = __dsub_rd(theta, B);   // v <= below_t =>  s <= v + b <= theta
+  int a0 = 0, a1 = (int)L;                       // i1 = #{v > above_t} (descending order)
+  while (a0 < a1) {
+    int md = (a0 + a1) >> 1;
+    if ((double)__uint_as_float(row[md].y) > above_t) a0 = md + 1; else a1 = md;
+  }
+  const int i1 = a0;
+  a1 = (int)L;                                   // i2 = #{v > below_t}
+  while (a0 < a1) {
+    int md = (a0 + a1) >> 1;
+    if ((double)__uint_as_float(row[md].y) > below_t) a0 = md + 1; else a1 = md;
+  }
+  const int i2 = a0;
+  uint32_t above = (uint32_t)i1;
+  const tc::RowBound ru = rb3[u];
+  const float cfac = screen_cfac(d);
+  for (int e = i1; e < i2; ++e) {
+    const uint32_t p = row[e].x;
+    const float v = __uint_as_float(row[e].y);
+    const float b = tc::screen_bound_tc(ru, ptile[p / pbn], gacc, gcan);
+    if ((double)__fsub_rd(v, b) > theta) { ++above; continue; }
+    if ((double)__fadd_ru(v, b) <= theta) continue;
+    const float *pp = Ps + (int64_t)p * d;
+    float acc = 0.0f;
+    for (int k = 0; k < d; ++k) acc = fmaf(uu[k], pp[k], acc);
+    const float b32 = screen_bound(cfac, unrm[u], pnrm_s[p]);
+    if ((double)__fsub_rd(acc, b32) > theta) { ++above; continue; }
+    if ((double)__fadd_ru(acc, b32) <= theta) continue;
+    atomicAdd(&stat[1], 1ull);
+    if (canon_dot(uu, pp, d) > theta) ++above;
+  }
+  ccount[i] = above;
 }
 
 // One CTA per query: the k smallest (rank, index) among its candidates.
@@ -789,6 +856,10 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
   RKR_CUDA(cudaMemsetAsync(sel_err, 0, sizeof(int), st));
   RKR_TRY(tmp_alloc(bt, &ties_d, 2, st));
   RKR_CUDA(cudaMemsetAsync(ties_d, 0, 2 * sizeof(unsigned long long), st));
+  DevBuf bls;
+  unsigned long long *lstat;
+  RKR_TRY(tmp_alloc(bls, &lstat, 2, st));
+  int64_t fallback = 0, list_fp64 = 0;
   Plan plan;
   Timer t1(st);
   const Grid grid{qc.xbf,   idx->xg0, idx->xg,       idx->XJU, idx->XJL, idx->nlev_x,
@@ -829,7 +900,24 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
       for (int q = qa; q < qb; ++q) total += hc[q];
     }
     Timer t3(st);
-    if (cnt > 0) RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu, cq, ccount, ties_d, st));
+    if (cnt > 0) {
+      DevBuf bfb;
+      int32_t *cu_fb;
+      RKR_TRY(tmp_alloc(bfb, &cu_fb, cnt, st));
+      RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
+      k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
+          cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d, idx->xtop,
+          idx->xlist, idx->xlcnt, idx->lcap, idx->xbmax, idx->Ut.rb3, idx->ptile3,
+          idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), ccount, cu_fb, lstat);
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+      unsigned long long ls[2] = {0, 0};
+      RKR_CUDA(cudaMemcpyAsync(ls, lstat, sizeof(ls), cudaMemcpyDeviceToHost, st));
+      RKR_CUDA(cudaStreamSynchronize(st));
+      fallback += (int64_t)ls[0];
+      list_fp64 += (int64_t)ls[1];
+      if (ls[0] > 0) RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, ties_d, st));
+    }
     ms_res += t3.stop();
     Timer t4(st);
     size_t sm = sizeof(SortEnt) * kMaxK;
@@ -852,8 +940,9 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
   if (stats) {
     stats->pairs = idx->n * (int64_t)nq;
     stats->candidates = total;
-    stats->fp64_dots = total + (int64_t)tiesv[1];
+    stats->fp64_dots = 2 * total + (int64_t)tiesv[1] + list_fp64;
     stats->near_ties = (int64_t)tiesv[0];
+    stats->recounted = fallback;
     stats->wide_queries = wide;
     stats->ms_theta = ms_theta;
     stats->ms_resolve = ms_res;

@@ -271,14 +271,14 @@ __global__ void k_xgrid(int64_t n, const double *__restrict__ fmin,
 // more than 65535 items gets the trivial bounds 0 and m instead.
 struct EpiXT {
   struct Thread {
-    float skip, b;
+    float skip, b, top;
     BinFP bf;
     double g0;
     int64_t row;
     uint32_t cnt;
   };
   static constexpr int kW = (kXG + 2) / 2;  // 32-bit words per histogram row
-  static constexpr size_t kSmem = sizeof(uint32_t) * (2 * 128 * kW + 256);
+  static constexpr size_t kSmem = sizeof(uint32_t) * (2 * 128 * kW + 256 + 128);
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
@@ -288,9 +288,16 @@ struct EpiXT {
   const float *g0f;
   uint32_t *XLO, *XHI;
   uint32_t mcount;
+  // tail lists: every item whose score may exceed x_top is appended to its user's list
+  const float *topf;   // x_top rounded down to float
+  uint2 *list;         // n x lcap entries (item, screened score bits)
+  uint32_t *lcnt;      // n: entries (lcap + 1 marks an overflow)
+  int lcap;
+  __device__ uint32_t *lslot(char *S) const { return (uint32_t *)S + 2 * 128 * kW + 256; }
   __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &ts) const {
     uint32_t *H = (uint32_t *)S;
     for (int i = et; i < 2 * 128 * kW; i += 256) H[i] = 0;
+    if (et < 128) lslot(S)[et] = 0;
     ts.cnt = 0;
   }
   __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
@@ -298,6 +305,7 @@ struct EpiXT {
     if (ts.row < nrows) {
       ts.b = tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan);
       ts.skip = __fsub_rd(g0f[ts.row], ts.b);  // s_hat <= skip implies s <= x_0
+      ts.top = topf[ts.row];
       ts.bf = xbin[ts.row];
       ts.g0 = xg0[ts.row];
     } else {
@@ -309,9 +317,13 @@ struct EpiXT {
     const int64_t c0 = (int64_t)ct * bn + col;
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      if (v[j] > ts.skip && c0 + j < ncols) count((uint32_t *)S, r, v[j], ts);
+      if (v[j] > ts.skip && c0 + j < ncols) count((uint32_t *)S, r, v[j], (int)(c0 + j), ts);
   }
-  __device__ __noinline__ void count(uint32_t *S, int r, float v, Thread &ts) const {
+  __device__ __noinline__ void count(uint32_t *S, int r, float v, int c, Thread &ts) const {
+    if (__fadd_ru(v, ts.b) > ts.top) {
+      uint32_t pos = atomicAdd(&S[2 * 128 * kW + 256 + r], 1u);
+      if (pos < (uint32_t)lcap) list[ts.row * lcap + pos] = make_uint2((uint32_t)c, __float_as_uint(v));
+    }
     int clo, chi;
     bin_interval(ts.bf, ts.g0, kXG, __fsub_rd(v, ts.b), __fadd_ru(v, ts.b), clo, chi);
     if (chi == 0) return;
@@ -333,6 +345,7 @@ struct EpiXT {
     const uint32_t *Hlo = (const uint32_t *)S + et * kW;
     const uint32_t *Hhi = (const uint32_t *)S + 128 * kW + et * kW;
     const bool ok = tot[et] + tot[128 + et] <= 65535u;
+    lcnt[g] = min(lslot(S)[et], (uint32_t)lcap + 1);
     uint32_t rlo = 0, rhi = 0;
     for (int c = kXG; c >= 1; --c) {
       rlo += (Hlo[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
@@ -342,6 +355,81 @@ struct EpiXT {
     }
   }
 };
+
+// Sort each user's tail list by screened score (descending, ties by item) and
+// record the largest screen bound of its entries.  One warp per user; lists
+// that overflowed are left unsorted and marked unusable by their count.
+constexpr int kListWarps = 4;
+
+__global__ void __launch_bounds__(kListWarps * 32)
+    k_list_sort(int64_t n, int lcap, uint2 *__restrict__ list, const uint32_t *__restrict__ lcnt,
+                const tc::RowBound *__restrict__ rowb, const tc::RowBound *__restrict__ tileb,
+                int bn, float gacc, float gcan, float *__restrict__ bmax) {
+  extern __shared__ uint64_t keys[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = (int64_t)blockIdx.x * kListWarps + warp;
+  if (u >= n) return;
+  uint64_t *k = keys + (size_t)warp * lcap;
+  const uint32_t L = lcnt[u];
+  if (L > (uint32_t)lcap) {
+    if (lane == 0) bmax[u] = INFINITY;
+    return;
+  }
+  int np2 = 1;
+  while (np2 < (int)L) np2 <<= 1;
+  uint2 *row = list + u * lcap;
+  float bm = 0.0f;
+  const tc::RowBound ru = rowb[u];
+  for (int i = lane; i < np2; i += 32) {
+    if (i < (int)L) {
+      uint2 e = row[i];
+      uint32_t fb = e.y;
+      uint32_t ord = (fb >> 31) ? ~fb : (fb | 0x80000000u);  // ascending with the float
+      k[i] = ((uint64_t)(~ord) << 32) | e.x;                 // descending score, then item
+      bm = fmaxf(bm, tc::screen_bound_tc(ru, tileb[e.x / bn], gacc, gcan));
+    } else {
+      k[i] = ~0ull;
+    }
+  }
+  __syncwarp();
+  for (int kk = 2; kk <= np2; kk <<= 1)
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < np2; i += 32) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          bool asc = (i & kk) == 0;
+          uint64_t a = k[i], b = k[ixj];
+          if ((a > b) == asc) { k[i] = b; k[ixj] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  for (int i = lane; i < (int)L; i += 32) {
+    uint64_t key = k[i];
+    uint32_t ord = ~(uint32_t)(key >> 32);
+    uint32_t fb = (ord >> 31) ? (ord & 0x7fffffffu) : ~ord;
+    row[i] = make_uint2((uint32_t)(key & 0xffffffffu), fb);
+  }
+  for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+  if (lane == 0) bmax[u] = bm;
+}
+
+rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st) {
+  // keep the item tile bounds for query-time lookups
+  const int ntiles = (int)((idx->m + bn - 1) / bn);
+  RKR_CUDA(cudaMemcpyAsync(idx->ptile3, tb, sizeof(tc::RowBound) * ntiles,
+                           cudaMemcpyDeviceToDevice, st));
+  idx->ptile_bn = bn;
+  size_t sm = sizeof(uint64_t) * (size_t)kListWarps * idx->lcap;
+  RKR_CUDA(cudaFuncSetAttribute(k_list_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm));
+  k_list_sort<<<(unsigned)((idx->n + kListWarps - 1) / kListWarps), kListWarps * 32, sm, st>>>(
+      idx->n, idx->lcap, idx->xlist, idx->xlcnt, idx->Ut.rb3, idx->ptile3, bn,
+      tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xbmax);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
 
 rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cudaStream_t st,
                           int64_t *) {
@@ -357,13 +445,18 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   k_xgrid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, idx->fmin, idx->delta, idx->xfloor,
                                                        idx->xg0, g0f);
   note_launch();
+  k_xgrid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, idx->fmin, idx->delta, idx->xlistcol,
+                                                       idx->xtop, idx->xtopf);
+  note_launch();
   RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, kXG, idx->pmax, idx->xdx, idx->xbin, st));
   EpiXT e;
   e.nrows = n; e.ncols = m; e.bn = BN; e.rowb = Ut.rb3; e.tileb = tb;
   e.gacc = tc_gacc(Ut.kp, 1); e.gcan = tc_gcan(idx->d);
   e.xbin = idx->xbin; e.xg0 = idx->xg0; e.g0f = g0f; e.XLO = idx->XLO; e.XHI = idx->XHI;
   e.mcount = (uint32_t)m;
+  e.topf = idx->xtopf; e.list = idx->xlist; e.lcnt = idx->xlcnt; e.lcap = idx->lcap;
   rkr_status s = launch_screen<BN, 3>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
+  if (s == RKR_OK) s = tc_sort_lists(idx, tb, BN, st);
   int hf[2] = {0, 0};
   cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
   cudaError_t err = cudaStreamSynchronize(st);
