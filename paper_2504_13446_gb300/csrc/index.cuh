@@ -112,8 +112,8 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       const int32_t *seg_user, const double *ths, uint32_t *hist,
                       cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
-constexpr int kListCap = 1024;
-constexpr int kListRank = 256;
+constexpr int kListCap = 4096;
+constexpr int kListRank = 1024;
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);
 
 // Row norms: FP64 canonical norms (optional) and FP32 upper bounds.

@@ -390,8 +390,11 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             const uint32_t *__restrict__ xlcnt, int lcap,
                             const float *__restrict__ xbmax, const tc::RowBound *__restrict__ rb3,
                             const tc::RowBound *__restrict__ ptile, int pbn, float gacc,
-                            float gcan, uint32_t *__restrict__ ccount, int32_t *__restrict__ cu_fb,
-                            unsigned long long *__restrict__ stat) {
+                            float gcan, const double *__restrict__ xg0,
+                            const double *__restrict__ xdx, int G, const uint32_t *__restrict__ XLO,
+                            const uint32_t *__restrict__ XHI, uint32_t mtop,
+                            uint32_t *__restrict__ ccount, uint32_t *__restrict__ clb,
+                            int32_t *__restrict__ cu_fb, unsigned long long *__restrict__ stat) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int64_t u = cu[i];
@@ -400,6 +403,10 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   const double theta = canon_dot(uu, Q + (int64_t)cq[i] * d, d);
   const uint32_t L = xlcnt[u];
   if (L > (uint32_t)lcap || theta < xtop[u]) {
+    // bounds from the exact count table at the exact bin of u.q
+    const int j = exact_j(theta, xg0[u], xdx[u], G);
+    ccount[i] = j >= 1 ? XHI[u * G + j - 1] : mtop;
+    clb[i] = j < G ? XLO[u * G + j] : 0u;
     cu_fb[i] = (int32_t)u;
     atomicAdd(&stat[0], 1ull);
     return;
@@ -440,6 +447,43 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
     if (canon_dot(uu, pp, d) > theta) ++above;
   }
   ccount[i] = above;
+  clb[i] = above;
+}
+
+// Per query: cap = k-th smallest of (exact count, or upper bound for candidates
+// still to be recounted).  A candidate whose lower bound exceeds the cap cannot
+// be among the k smallest ranks: it is dropped from the recount and given the
+// largest key.
+__global__ void __launch_bounds__(256)
+    k_recount_filter(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
+                     const int32_t *__restrict__ kq, uint32_t *__restrict__ ccount,
+                     const uint32_t *__restrict__ clb, int32_t *__restrict__ cu_fb) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t bc[2];
+  const int q = qa + blockIdx.x;
+  const int64_t base = qoff[q] - qoff[qa];
+  const int64_t cnt = qcount[q];
+  const int k = kq[q];
+  if (cnt < k) return;
+  uint32_t *cc = ccount + base;
+  const uint32_t *lb = clb + base;
+  int32_t *fb = cu_fb + base;
+  const uint64_t cap = block_kth(cnt, (uint64_t)k, 32,
+                                 [&](int64_t i, uint64_t &key) { key = cc[i]; return true; },
+                                 hist, bc);
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
+    if (fb[i] >= 0 && (uint64_t)lb[i] > cap) {
+      fb[i] = -1;
+      cc[i] = 0xffffffffu;
+    }
+}
+
+__global__ void k_count_valid(int64_t n, const int32_t *__restrict__ v,
+                              unsigned long long *__restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long c = (i < n && v[i] >= 0) ? 1ull : 0ull;
+  c = __reduce_add_sync(0xffffffffu, (unsigned)c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
 // One CTA per query: the k smallest (rank, index) among its candidates.
@@ -860,6 +904,7 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
   unsigned long long *lstat;
   RKR_TRY(tmp_alloc(bls, &lstat, 2, st));
   int64_t fallback = 0, list_fp64 = 0;
+  unsigned long long lstat_host_fb = 0;
   Plan plan;
   Timer t1(st);
   const Grid grid{qc.xbf,   idx->xg0, idx->xg,       idx->XJU, idx->XJL, idx->nlev_x,
@@ -901,22 +946,40 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
     }
     Timer t3(st);
     if (cnt > 0) {
-      DevBuf bfb;
+      DevBuf bfb, blb;
       int32_t *cu_fb;
+      uint32_t *clb;
       RKR_TRY(tmp_alloc(bfb, &cu_fb, cnt, st));
+      RKR_TRY(tmp_alloc(blb, &clb, cnt, st));
       RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
       k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
           cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d, idx->xtop,
           idx->xlist, idx->xlcnt, idx->lcap, idx->xbmax, idx->Ut.rb3, idx->ptile3,
-          idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), ccount, cu_fb, lstat);
+          idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
+          idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, lstat);
       note_launch();
       RKR_CUDA(cudaGetLastError());
+      k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+      {  // candidates that still need the recount
+        DevBuf bn2;
+        unsigned long long *nfb;
+        RKR_TRY(tmp_alloc(bn2, &nfb, 1, st));
+        RKR_CUDA(cudaMemsetAsync(nfb, 0, sizeof(unsigned long long), st));
+        k_count_valid<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_fb, nfb);
+        note_launch();
+        RKR_CUDA(cudaMemcpyAsync(&lstat_host_fb, nfb, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        RKR_CUDA(cudaStreamSynchronize(st));
+      }
       unsigned long long ls[2] = {0, 0};
       RKR_CUDA(cudaMemcpyAsync(ls, lstat, sizeof(ls), cudaMemcpyDeviceToHost, st));
       RKR_CUDA(cudaStreamSynchronize(st));
-      fallback += (int64_t)ls[0];
+      fallback += (int64_t)lstat_host_fb;
       list_fp64 += (int64_t)ls[1];
-      if (ls[0] > 0) RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, ties_d, st));
+      if (lstat_host_fb > 0)
+        RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, ties_d, st));
     }
     ms_res += t3.stop();
     Timer t4(st);
