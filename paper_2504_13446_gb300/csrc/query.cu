@@ -389,7 +389,7 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             const double *__restrict__ xtop, const uint2 *__restrict__ xlist,
                             const uint32_t *__restrict__ xlcnt, int lcap,
                             const float *__restrict__ xbmax, const tc::RowBound *__restrict__ rb3,
-                            const tc::RowBound *__restrict__ ptile, int pbn, float gacc,
+                            const tc::RowBound *__restrict__ ptile, int pbn, tc::Gacc gacc,
                             float gcan, const double *__restrict__ xg0,
                             const double *__restrict__ xdx, int G, const uint32_t *__restrict__ XLO,
                             const uint32_t *__restrict__ XHI, uint32_t mtop,

@@ -41,8 +41,7 @@ __global__ void k_stage_bf16(const float *__restrict__ X, int64_t rows, int d, i
   auto up = [](double s) { return __double2float_ru(sqrt(s) * (1.0 + 0x1p-40) + 1e-300); };
   tc::RowBound a, b;
   a.a0 = up(se1); a.a1 = up(sh); a.a2 = up(sx); a.a3 = 0.0f; a.a4 = up(sh);
-  b.a0 = up(se3); b.a1 = up(sc); b.a2 = up(sx); b.a3 = up(sl);
-  b.a4 = __fadd_ru(up(sh), up(sl));
+  b.a0 = up(se3); b.a1 = up(sc); b.a2 = up(sx); b.a3 = up(sl); b.a4 = up(sh);
   rb1[i] = a;
   rb3[i] = b;
 }
@@ -175,7 +174,8 @@ struct EpiStore {
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
-  float gacc, gcan;
+  tc::Gacc gacc;
+  float gcan;
   float *out, *outb;
   __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
   __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {

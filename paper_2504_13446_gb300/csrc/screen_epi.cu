@@ -58,7 +58,8 @@ struct EpiFbA {
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
-  float gacc, gcan;
+  tc::Gacc gacc;
+  float gcan;
   float *maxlo, *minhi;
   __device__ void unit_begin(char *, const tc::Unit &, int, Thread &ts) const {
     ts.mxlo = -INFINITY;
@@ -123,7 +124,8 @@ struct EpiFbB {
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
-  float gacc, gcan;
+  tc::Gacc gacc;
+  float gcan;
   const float *maxlo, *minhi;
   PairQueue q;
   __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
@@ -282,7 +284,8 @@ struct EpiXT {
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
-  float gacc, gcan;
+  tc::Gacc gacc;
+  float gcan;
   const BinFP *xbin;
   const double *xg0;
   const float *g0f;
@@ -364,7 +367,7 @@ constexpr int kListWarps = 4;
 __global__ void __launch_bounds__(kListWarps * 32)
     k_list_sort(int64_t n, int lcap, uint2 *__restrict__ list, const uint32_t *__restrict__ lcnt,
                 const tc::RowBound *__restrict__ rowb, const tc::RowBound *__restrict__ tileb,
-                int bn, float gacc, float gcan, float *__restrict__ bmax) {
+                int bn, tc::Gacc gacc, float gcan, float *__restrict__ bmax) {
   extern __shared__ uint64_t keys[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t u = (int64_t)blockIdx.x * kListWarps + warp;
@@ -489,19 +492,27 @@ __device__ __forceinline__ void level_range(int L, uint32_t scale, uint64_t &bas
 
 template <int PASS>
 struct EpiTheta {
+  static constexpr int kJS = 34;  // int16 row stride of the level tables (conflict-free)
   struct Thread {
     float b;
     BinFP bf;
     double fm;
     int64_t u;
+    int rb1;                 // end of the unit's row blocks (prefetch stays inside)
+    uint4 pju[2], pjl[2];    // prefetched level-table words for the next row block
+    BinFP pbf;
+    double pfm;
+    tc::RowBound prb;
+    bool have_pf;
   };
-  static constexpr size_t kSmem =
-      sizeof(int) * (2 * 128 * 33 + 2 * kThetaBN * 32 + 2 * kThetaBN);
+  static constexpr size_t kSmem = sizeof(int16_t) * 2 * 128 * kJS +
+                                  sizeof(int) * (2 * kThetaBN * 32 + 2 * kThetaBN);
   int64_t nrows, ncols;
   int tau;
   int qa;  // global index of query column 0
   const tc::RowBound *rowb, *tileb;
-  float gacc, gcan;
+  tc::Gacc gacc;
+  float gcan;
   const BinFP *binfp;
   const double *fmin;
   const int16_t *JU, *JL;
@@ -515,12 +526,33 @@ struct EpiTheta {
   uint32_t *qcursor;
   int32_t *cand_u, *cand_q;
 
-  __device__ int *jtab(char *S) const { return (int *)S; }
-  __device__ int *hist(char *S) const { return (int *)S + 2 * 128 * 33; }
+  __device__ int16_t *jtab(char *S) const { return (int16_t *)S; }
+  __device__ int *hist(char *S) const { return (int *)(S + sizeof(int16_t) * 2 * 128 * kJS); }
   __device__ int *lst(char *S) const { return hist(S) + 2 * kThetaBN * 32; }
   __device__ uint32_t *caps(char *S) const { return (uint32_t *)(lst(S) + kThetaBN); }
 
-  __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &) const {
+  // Thread et fetches words [16 et, 16 et + 16) of the 2 x 128 x 32 int16 tables
+  // (JU block then JL block) of row block rb: two uint4 of each table.
+  __device__ void fetch(int rb, int et, Thread &ts) const {
+    const int64_t base = (int64_t)rb * tc::BM * kMaxLevels;  // int16 index of row 0
+    const int64_t lim = nrows * kMaxLevels;
+    for (int h = 0; h < 2; ++h) {
+      int64_t e = base + (int64_t)(et * 2 + h) * 8;  // 8 int16 per uint4
+      ts.pju[h] = e < lim ? *(const uint4 *)(JU + e) : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+      ts.pjl[h] = e < lim ? *(const uint4 *)(JL + e) : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    }
+  }
+  __device__ void fetch_row(int rb, int r, Thread &ts) const {
+    int64_t u = (int64_t)rb * tc::BM + r;
+    if (u < nrows) {
+      ts.pbf = binfp[u];
+      ts.pfm = fmin[u];
+      ts.prb = rowb[u];
+    }
+  }
+  __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &ts) const {
+    ts.rb1 = u.rb1;
+    ts.have_pf = false;
     if (PASS == 1) {
       int *H = hist(S);
       for (int i = et; i < 2 * kThetaBN * 32; i += 256) H[i] = 0;
@@ -535,24 +567,43 @@ struct EpiTheta {
     }
   }
   __device__ void tile_begin(char *S, int rb, int ct, int r, int h, Thread &ts) const {
+    const int w = (threadIdx.x >> 5), et = threadIdx.x - 64;
+    (void)w;
+    if (!ts.have_pf) {
+      fetch(rb, et, ts);
+      fetch_row(rb, r, ts);
+    }
     tc::epi_sync();  // readers of the previous tile are done with the level tables
-    ts.u = (int64_t)rb * tc::BM + r;
-    int *ju = jtab(S) + r * 33, *jl = jtab(S) + 128 * 33 + r * 33;
-    if (ts.u < nrows) {
-      for (int L = h * 16; L < h * 16 + 16; ++L) {
-        ju[L] = JU[ts.u * kMaxLevels + L];
-        jl[L] = JL[ts.u * kMaxLevels + L];
+    // scatter the 32 words this thread holds into padded rows
+    int16_t *J = jtab(S);
+    for (int t2 = 0; t2 < 2; ++t2) {
+      const uint4 *src = t2 ? ts.pjl : ts.pju;
+      for (int hh = 0; hh < 2; ++hh) {
+        int e = (et * 2 + hh) * 8;       // first int16 of this uint4 inside the 128 x 32 block
+        int row = e >> 5, colL = e & 31;
+        const uint32_t wv[4] = {src[hh].x, src[hh].y, src[hh].z, src[hh].w};
+        uint32_t *dst = (uint32_t *)(J + t2 * 128 * kJS + row * kJS + colL);
+        for (int q2 = 0; q2 < 4; ++q2) dst[q2] = wv[q2];
       }
-      ts.b = tc::screen_bound_tc(rowb[ts.u], tileb[ct], gacc, gcan);
-      ts.bf = binfp[ts.u];
-      ts.fm = fmin[ts.u];
+    }
+    ts.u = (int64_t)rb * tc::BM + r;
+    if (ts.u < nrows) {
+      ts.b = tc::screen_bound_tc(ts.prb, tileb[ct], gacc, gcan);
+      ts.bf = ts.pbf;
+      ts.fm = ts.pfm;
     }
     tc::epi_sync();
+    // prefetch the next row block of this unit while this tile is processed
+    ts.have_pf = rb + 1 < ts.rb1;
+    if (ts.have_pf) {
+      fetch(rb + 1, et, ts);
+      fetch_row(rb + 1, r, ts);
+    }
   }
   __device__ void chunk(char *S, int, int ct, int r, int col, const float (&v)[32],
                         Thread &ts) const {
     if (ts.u >= nrows) return;
-    const int *ju = jtab(S) + r * 33, *jl = jtab(S) + 128 * 33 + r * 33;
+    const int16_t *ju = jtab(S) + r * kJS, *jl = jtab(S) + 128 * kJS + r * kJS;
     int *H = hist(S);
     const int *Ls = lst(S);
     const int64_t c0 = (int64_t)ct * kThetaBN + col;
@@ -568,8 +619,13 @@ struct EpiTheta {
             if (ju[lu + step - 1] > jlo) lu += step;
             if (jl[ll + step - 1] > jhi) ll += step;
           }
-          atomicAdd(&H[(col + j) * 32 + lu], 1);
-          atomicAdd(&H[kThetaBN * 32 + (col + j) * 32 + ll], 1);
+          // warp-aggregated: all lanes are on the same query column
+          const unsigned act = __activemask();
+          const unsigned mu = __match_any_sync(act, lu), ml = __match_any_sync(act, ll);
+          const int lane = threadIdx.x & 31;
+          if ((mu & ((1u << lane) - 1)) == 0) atomicAdd(&H[(col + j) * 32 + lu], __popc(mu));
+          if ((ml & ((1u << lane) - 1)) == 0)
+            atomicAdd(&H[kThetaBN * 32 + (col + j) * 32 + ll], __popc(ml));
         } else if (PASS == 3) {
           const int Lq = Ls[col + j];
           // level of the upper bound is L* exactly: above every smaller level's start
@@ -629,6 +685,7 @@ static rkr_status theta_launch(const rkr_index *idx, const TcSide &Ut, const TcS
   e.hist_up = a.hist; e.hist_lo = a.hist ? a.hist + (size_t)(a.qa + nq) * 32 : nullptr;
   e.lstar = a.lstar; e.cap = a.cap; e.fine = a.fine;
   e.qoff = a.qoff; e.qcursor = a.qcursor; e.cand_u = a.cand_u; e.cand_q = a.cand_q;
+  static_assert(tc::screen_smem_bytes<kThetaBN, 4, EpiTheta<1>>() <= 232448, "theta smem");
   rkr_status s = launch_screen<kThetaBN, 4>(Ut, Qt, split, sch, e, err, st);
   cudaFreeAsync(tb, st);
   return s;
@@ -655,7 +712,8 @@ struct EpiRC {
   int64_t nseg, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
-  float gacc, gcan;
+  tc::Gacc gacc;
+  float gcan;
   const int64_t *seg_start;
   const int32_t *seg_len;
   const double *ths;

@@ -5,7 +5,7 @@
 // accumulation in TMEM.  A rows are users, B rows items or queries; both are
 // K-major (rows of K contiguous bf16), staged by TMA with the 128-byte swizzle
 // in 64-element K chunks.  A "split" product sums three segments along K,
-// hi.hi + hi.lo + lo.hi, with hi = bf16(x) and lo = bf16(x - hi).
+// hi.lo + lo.hi + hi.hi (in that order), with hi = bf16(x) and lo = bf16(x - hi).
 //
 // Warp roles (one CTA per SM, persistent):
 //   warp 0      TMA producer (one lane)
@@ -163,7 +163,7 @@ struct Operands {
   int64_t ncols;       // rows of B (items or queries)
   int kchunks;         // 64-wide K chunks per segment
   int ksteps;          // 16-wide MMA steps per segment
-  int split;           // 0: one segment hi.hi; 1: three segments hi.hi, hi.lo, lo.hi
+  int split;           // 0: one segment hi.hi; 1: three segments hi.lo, lo.hi, hi.hi
 };
 
 // Per-row bound terms (FP32 upper bounds), see screen_bound_tc.
@@ -172,18 +172,32 @@ struct RowBound {
   float a1;  // ||xhi + xlo||       (single mode: ||xhi||)
   float a2;  // ||x||
   float a3;  // ||xlo||             (single mode: 0)
-  float a4;  // ||xhi|| + ||xlo||   (single mode: ||xhi||)
+  float a4;  // ||xhi||
+};
+
+// Accumulation factors.  Model: adding a product t to the FP32 accumulator D
+// in the tensor core errs by at most 2^-23 (|D| + |t|) (twice the unit
+// roundoff, so truncating adders are covered).  The split product accumulates
+// its 2 Kp small terms (hi.lo, lo.hi) first and the Kp terms hi.hi last, so
+//   |err| <= 2^-22 (3 Kp L + (Kp + 1) H),  L = sum |lo terms|, H = sum |hi.hi terms|
+// (again a factor 2 of margin); single products: 2^-22 (Kp + 1) H.
+struct Gacc {
+  float h;  // factor of H <= ||u_hi|| ||x_hi||
+  float l;  // factor of L <= ||u_hi|| ||x_lo|| + ||u_lo|| ||x_hi||
 };
 
 // Bound on |s_hat - s(u,x)| for a user row ru and the maxima rt of the
-// item-side terms over a column tile.  gacc = 2 K' 2^-23 covers the FP32
-// accumulation of K' products, gcan = d 2^-52 the canonical sum's own rounding.
+// item-side terms over a column tile.  The representation error is
+// ||u - u~|| ||x|| + ||u~|| ||x - x~|| (+ ||u_lo|| ||x_lo|| for the dropped
+// lo.lo term), by Cauchy-Schwarz; gcan = d 2^-52 covers the canonical sum's
+// own rounding; a tiny absolute term covers flushed subnormals.
 __device__ __forceinline__ float screen_bound_tc(const RowBound &ru, const RowBound &rt,
-                                                 float gacc, float gcan) {
+                                                 const Gacc &g, float gcan) {
   float b = __fmul_ru(ru.a0, rt.a2);
   b = __fadd_ru(b, __fmul_ru(ru.a1, rt.a0));
   b = __fadd_ru(b, __fmul_ru(ru.a3, rt.a3));
-  b = __fadd_ru(b, __fmul_ru(gacc, __fmul_ru(ru.a4, rt.a4)));
+  b = __fadd_ru(b, __fmul_ru(g.h, __fmul_ru(ru.a4, rt.a4)));
+  b = __fadd_ru(b, __fmul_ru(g.l, __fadd_ru(__fmul_ru(ru.a4, rt.a3), __fmul_ru(ru.a3, rt.a4))));
   b = __fadd_ru(b, __fmul_ru(gcan, __fmul_ru(ru.a2, rt.a2)));
   b = __fadd_ru(b, __fmul_ru(0x1p-110f, __fadd_ru(ru.a2, rt.a2)));
   return __fadd_ru(b, 1e-36f);

@@ -119,8 +119,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               unsigned char *sb = sa + L::kA;
               const int g = kc / op.kchunks, c = kc - g * op.kchunks;
               mbar_expect_tx(&full[s], L::kStage);
-              tma_load_2d(sa, g == 2 ? &mAl : &mAh, c * KCH, rb * BM, &full[s]);
-              tma_load_2d(sb, g == 1 ? &mBl : &mBh, c * KCH, ct * BN, &full[s]);
+              // split order: hi.lo, lo.hi, then hi.hi (small terms first)
+              const bool alo = op.split && g == 1, blo = op.split && g == 0;
+              tma_load_2d(sa, alo ? &mAl : &mAh, c * KCH, rb * BM, &full[s]);
+              tma_load_2d(sb, blo ? &mBl : &mBh, c * KCH, ct * BN, &full[s]);
             }
       }
       if (failed) {

@@ -80,8 +80,11 @@ inline tc::Schedule col_schedule(int64_t rows, int64_t cols, int bn, int parts) 
 }
 
 // Accumulation and canonical-rounding factors of the bound for K' products.
-inline float tc_gacc(int kp, int split) {
-  return (float)(2.0 * (double)(kp * (split ? 3 : 1)) * 0x1p-23 * (1.0 + 0x1p-10));
+inline tc::Gacc tc_gacc(int kp, int split) {
+  tc::Gacc g;
+  g.h = (float)((double)(kp + 1) * 0x1p-22 * (1.0 + 0x1p-10));
+  g.l = split ? (float)(3.0 * (double)kp * 0x1p-22 * (1.0 + 0x1p-10)) : 0.0f;
+  return g;
 }
 inline float tc_gcan(int d) { return (float)((double)d * 0x1p-52 * 2.0); }
 

@@ -34,9 +34,9 @@ def test_screen_within_bound(n, mx, d, split):
     tile_max = np.repeat([xn[i:i + 256].max() for i in range(0, mx, 256)], 256)[:mx]
     scale = np.linalg.norm(U, axis=1)[:, None] * tile_max[None, :]
     rel = (b / scale).max()
-    assert rel < (2e-2 if not split else 5e-4), rel
+    assert rel < (2e-2 if not split else 1e-4), rel
     # the screen is not trivially loose: typical error far below the bound
-    assert np.median(ratio) < 0.2
+    assert np.median(ratio) < 0.5
 
 
 def test_screen_integer_data_is_exact_when_representable():
