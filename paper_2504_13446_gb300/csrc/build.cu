@@ -626,11 +626,12 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     RKR_TRY(dalloc(&idx->xbin, n));
     RKR_TRY(dalloc(&idx->XLO, (size_t)n * kXGrid));
     RKR_TRY(dalloc(&idx->XHI, (size_t)n * kXGrid));
-    idx->lcap = kListCap;
+    idx->lcap = m < (1 << 24) ? kListCap : 0;  // list entries park a column in the item's top byte
     RKR_TRY(dalloc(&idx->xlistcol, n));
     RKR_TRY(dalloc(&idx->xtop, n));
     RKR_TRY(dalloc(&idx->xtopf, n));
-    RKR_TRY(dalloc(&idx->xlist, (size_t)n * kListCap));
+    RKR_TRY(dalloc(&idx->xlist, (size_t)n * std::max(idx->lcap, 1)));
+    RKR_TRY(dalloc(&idx->xcoff, (size_t)n * (kXGrid + 2)));
     RKR_TRY(dalloc(&idx->xlcnt, n));
     RKR_TRY(dalloc(&idx->xbmax, n));
     RKR_TRY(dalloc(&idx->ptile3, (size_t)((m + 255) / 256)));
@@ -668,7 +669,7 @@ void index_release(rkr_index *idx) {
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
                   idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
                   idx->xfloor, idx->xlistcol, idx->xtop, idx->xtopf, idx->xlist, idx->xlcnt,
-                  idx->xbmax, idx->ptile3};
+                  idx->xbmax, idx->ptile3, idx->xcoff};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   tc_free(idx->Ut);

@@ -50,7 +50,9 @@ struct rkr_index {
   int32_t *xlistcol = nullptr;              // n: paper column of x_top
   double *xtop = nullptr;                   // n
   float *xtopf = nullptr;                   // n: x_top rounded down
-  uint2 *xlist = nullptr;                   // n x lcap: (item, float bits of screened score)
+  uint2 *xlist = nullptr;                   // n x lcap: (item, float bits of screened score),
+                                            // grouped by exact-grid column
+  uint16_t *xcoff = nullptr;                // n x (xg + 2): start of each column's entries
   uint32_t *xlcnt = nullptr;                // n: entries, lcap + 1 = overflow
   float *xbmax = nullptr;                   // n: largest screen bound of a user's entries
   rkr::tc::RowBound *ptile3 = nullptr;      // item tile bounds of the split screen
@@ -112,7 +114,7 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       const int32_t *seg_user, const double *ths, uint32_t *hist,
                       cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
-constexpr int kListCap = 4096;
+constexpr int kListCap = 4096;  // < 2^16 (column offsets are 16-bit)
 constexpr int kListRank = 1024;
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);
 

@@ -378,15 +378,17 @@ __global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_s
 
 // Exact ranks from the tail lists.  A candidate (u, q) with u.q >= x_top(u)
 // has rank 1 + #{p in list(u) : s(u,p) > u.q}, since every item scoring above
-// x_top is in the list.  Entries are sorted by screened score; those within
-// their bound of u.q are settled by an FP32 dot product with its bound, then
-// canonically.  Candidates below x_top (or with an overflowed list) are
+// x_top is in the list.  Entries are grouped by exact-grid column: whole
+// columns are counted from the column offsets, and the entries of the one or
+// two columns within the screen bound of u.q are settled one by one, by their
+// own bound, an FP32 dot product with its bound, or canonically.  Candidates below x_top (or with an overflowed list) are
 // passed on, unchanged, in cu_fb for the recount screen; others get -1 there.
 __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             const int32_t *__restrict__ cq, const float *__restrict__ U,
                             const float *__restrict__ unrm, const float *__restrict__ Q,
                             const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int d,
                             const double *__restrict__ xtop, const uint2 *__restrict__ xlist,
+                            const uint16_t *__restrict__ xcoff,
                             const uint32_t *__restrict__ xlcnt, int lcap,
                             const float *__restrict__ xbmax, const tc::RowBound *__restrict__ rb3,
                             const tc::RowBound *__restrict__ ptile, int pbn, tc::Gacc gacc,
@@ -412,26 +414,19 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
     return;
   }
   cu_fb[i] = -1;
+  // entries are grouped by column c = #{x_j <= v}: x_{c-1} <= v < x_c
   const uint2 *row = xlist + u * lcap;
+  const uint16_t *co = xcoff + u * (G + 2);
   const double B = (double)xbmax[u];
-  const double above_t = __dadd_ru(theta, B);   // v > above_t  =>  s >= v - b > theta
-  const double below_t = __dsub_rd(theta, B);   // v <= below_t =>  s <= v + b <= theta
-  int a0 = 0, a1 = (int)L;                       // i1 = #{v > above_t} (descending order)
-  while (a0 < a1) {
-    int md = (a0 + a1) >> 1;
-    if ((double)__uint_as_float(row[md].y) > above_t) a0 = md + 1; else a1 = md;
-  }
-  const int i1 = a0;
-  a1 = (int)L;                                   // i2 = #{v > below_t}
-  while (a0 < a1) {
-    int md = (a0 + a1) >> 1;
-    if ((double)__uint_as_float(row[md].y) > below_t) a0 = md + 1; else a1 = md;
-  }
-  const int i2 = a0;
-  uint32_t above = (uint32_t)i1;
+  const double g0 = xg0[u], dx = xdx[u];
+  // columns c >= chi have v >= x_{c-1} > theta + B: every entry is above theta
+  const int chi = exact_j(__dadd_ru(theta, B), g0, dx, G) + 1;
+  // columns c < clo have v < x_c <= theta - B: no entry is above theta
+  const int clo = exact_j(__dsub_rd(theta, B), g0, dx, G);
+  uint32_t above = L - (uint32_t)co[chi];
   const tc::RowBound ru = rb3[u];
   const float cfac = screen_cfac(d);
-  for (int e = i1; e < i2; ++e) {
+  for (int e = co[clo]; e < (int)co[chi]; ++e) {
     const uint32_t p = row[e].x;
     const float v = __uint_as_float(row[e].y);
     const float b = tc::screen_bound_tc(ru, ptile[p / pbn], gacc, gcan);
@@ -954,7 +949,7 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
       RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
       k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
           cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d, idx->xtop,
-          idx->xlist, idx->xlcnt, idx->lcap, idx->xbmax, idx->Ut.rb3, idx->ptile3,
+          idx->xlist, idx->xcoff, idx->xlcnt, idx->lcap, idx->xbmax, idx->Ut.rb3, idx->ptile3,
           idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
           idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, lstat);
       note_launch();

@@ -323,7 +323,7 @@ struct EpiXT {
       if (v[j] > ts.skip && c0 + j < ncols) count((uint32_t *)S, r, v[j], (int)(c0 + j), ts);
   }
   __device__ __noinline__ void count(uint32_t *S, int r, float v, int c, Thread &ts) const {
-    if (__fadd_ru(v, ts.b) > ts.top) {
+    if (lcap > 0 && __fadd_ru(v, ts.b) > ts.top) {
       uint32_t pos = atomicAdd(&S[2 * 128 * kW + 256 + r], 1u);
       if (pos < (uint32_t)lcap) list[ts.row * lcap + pos] = make_uint2((uint32_t)c, __float_as_uint(v));
     }
@@ -359,59 +359,65 @@ struct EpiXT {
   }
 };
 
-// Sort each user's tail list by screened score (descending, ties by item) and
-// record the largest screen bound of its entries.  One warp per user; lists
-// that overflowed are left unsorted and marked unusable by their count.
+// Group each user's tail list by the exact-grid column of the screened score,
+// col(v) = #{j : x_j <= v} in 0..G (counting sort), and record the column
+// offsets and the largest screen bound of the entries.  One warp per user;
+// overflowed lists are left as they are and marked unusable by their count.
 constexpr int kListWarps = 4;
 
 __global__ void __launch_bounds__(kListWarps * 32)
-    k_list_sort(int64_t n, int lcap, uint2 *__restrict__ list, const uint32_t *__restrict__ lcnt,
-                const tc::RowBound *__restrict__ rowb, const tc::RowBound *__restrict__ tileb,
-                int bn, tc::Gacc gacc, float gcan, float *__restrict__ bmax) {
-  extern __shared__ uint64_t keys[];
+    k_list_group(int64_t n, int lcap, uint2 *__restrict__ list, const uint32_t *__restrict__ lcnt,
+                 const BinFP *__restrict__ xbin, const double *__restrict__ xg0,
+                 const double *__restrict__ xdx, int G, const tc::RowBound *__restrict__ rowb,
+                 const tc::RowBound *__restrict__ tileb, int bn, tc::Gacc gacc, float gcan,
+                 uint16_t *__restrict__ coff, float *__restrict__ bmax) {
+  extern __shared__ unsigned char lsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint2 *buf = (uint2 *)lsm + (size_t)warp * lcap;
+  uint32_t *cnt = (uint32_t *)((uint2 *)lsm + (size_t)kListWarps * lcap) + warp * (G + 2);
   const int64_t u = (int64_t)blockIdx.x * kListWarps + warp;
   if (u >= n) return;
-  uint64_t *k = keys + (size_t)warp * lcap;
   const uint32_t L = lcnt[u];
+  uint16_t *co = coff + u * (G + 2);
   if (L > (uint32_t)lcap) {
     if (lane == 0) bmax[u] = INFINITY;
     return;
   }
-  int np2 = 1;
-  while (np2 < (int)L) np2 <<= 1;
+  for (int c = lane; c < G + 2; c += 32) cnt[c] = 0;
+  __syncwarp();
   uint2 *row = list + u * lcap;
-  float bm = 0.0f;
+  const BinFP bf = xbin[u];
+  const double g0 = xg0[u], dx = xdx[u];
   const tc::RowBound ru = rowb[u];
-  for (int i = lane; i < np2; i += 32) {
-    if (i < (int)L) {
-      uint2 e = row[i];
-      uint32_t fb = e.y;
-      uint32_t ord = (fb >> 31) ? ~fb : (fb | 0x80000000u);  // ascending with the float
-      k[i] = ((uint64_t)(~ord) << 32) | e.x;                 // descending score, then item
-      bm = fmaxf(bm, tc::screen_bound_tc(ru, tileb[e.x / bn], gacc, gcan));
-    } else {
-      k[i] = ~0ull;
-    }
+  float bm = 0.0f;
+  for (uint32_t i = lane; i < L; i += 32) {
+    uint2 e = row[i];
+    float v = __uint_as_float(e.y);
+    int jlo, jhi;
+    bin_interval(bf, g0, G, v, v, jlo, jhi);
+    int col = jlo == jhi ? jlo : exact_j((double)v, g0, dx, G);
+    e.x |= (uint32_t)col << 24;  // column parked in the high byte for the scatter below
+    buf[i] = e;
+    atomicAdd(&cnt[col], 1u);
+    bm = fmaxf(bm, tc::screen_bound_tc(ru, tileb[(e.x & 0xffffffu) / bn], gacc, gcan));
   }
   __syncwarp();
-  for (int kk = 2; kk <= np2; kk <<= 1)
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < np2; i += 32) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          bool asc = (i & kk) == 0;
-          uint64_t a = k[i], b = k[ixj];
-          if ((a > b) == asc) { k[i] = b; k[ixj] = a; }
-        }
-      }
-      __syncwarp();
+  if (lane == 0) {  // exclusive prefix over G + 1 columns
+    uint32_t run = 0;
+    for (int c = 0; c <= G; ++c) {
+      uint32_t t = cnt[c];
+      cnt[c] = run;
+      co[c] = (uint16_t)run;
+      run += t;
     }
-  for (int i = lane; i < (int)L; i += 32) {
-    uint64_t key = k[i];
-    uint32_t ord = ~(uint32_t)(key >> 32);
-    uint32_t fb = (ord >> 31) ? (ord & 0x7fffffffu) : ~ord;
-    row[i] = make_uint2((uint32_t)(key & 0xffffffffu), fb);
+    co[G + 1] = (uint16_t)run;
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < L; i += 32) {
+    uint2 e = buf[i];
+    int col = (int)(e.x >> 24);
+    uint32_t pos = atomicAdd(&cnt[col], 1u);
+    row[pos] = make_uint2(e.x & 0xffffffu, e.y);
   }
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
   if (lane == 0) bmax[u] = bm;
@@ -423,12 +429,14 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   RKR_CUDA(cudaMemcpyAsync(idx->ptile3, tb, sizeof(tc::RowBound) * ntiles,
                            cudaMemcpyDeviceToDevice, st));
   idx->ptile_bn = bn;
-  size_t sm = sizeof(uint64_t) * (size_t)kListWarps * idx->lcap;
-  RKR_CUDA(cudaFuncSetAttribute(k_list_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const int G = idx->xg;
+  size_t sm = sizeof(uint2) * (size_t)kListWarps * idx->lcap +
+              sizeof(uint32_t) * (size_t)kListWarps * (G + 2);
+  RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
-  k_list_sort<<<(unsigned)((idx->n + kListWarps - 1) / kListWarps), kListWarps * 32, sm, st>>>(
-      idx->n, idx->lcap, idx->xlist, idx->xlcnt, idx->Ut.rb3, idx->ptile3, bn,
-      tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xbmax);
+  k_list_group<<<(unsigned)((idx->n + kListWarps - 1) / kListWarps), kListWarps * 32, sm, st>>>(
+      idx->n, idx->lcap, idx->xlist, idx->xlcnt, idx->xbin, idx->xg0, idx->xdx, G, idx->Ut.rb3,
+      idx->ptile3, bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff, idx->xbmax);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
@@ -459,7 +467,9 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   e.mcount = (uint32_t)m;
   e.topf = idx->xtopf; e.list = idx->xlist; e.lcnt = idx->xlcnt; e.lcap = idx->lcap;
   rkr_status s = launch_screen<BN, 3>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
-  if (s == RKR_OK) s = tc_sort_lists(idx, tb, BN, st);
+  if (s == RKR_OK && idx->lcap > 0) s = tc_sort_lists(idx, tb, BN, st);
+  if (s == RKR_OK && idx->lcap == 0)
+    RKR_CUDA(cudaMemsetAsync(idx->xlcnt, 0xff, sizeof(uint32_t) * n, st));
   int hf[2] = {0, 0};
   cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
   cudaError_t err = cudaStreamSynchronize(st);
@@ -702,11 +712,12 @@ rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const
 
 struct EpiRC {
   struct Thread {
-    float b, tminf;
+    float b, tminf, tmaxf;
     int64_t sg;
     int L;
     const double *ts;
     uint32_t *h;
+    uint32_t nabove;   // items above every threshold of the segment (pos = L)
   };
   static constexpr size_t kSmem = 0;
   int64_t nseg, ncols;
@@ -719,20 +730,25 @@ struct EpiRC {
   const double *ths;
   uint32_t *hist;
   PairQueue q;
-  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
-  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
-    ts.sg = (int64_t)rb * tc::BM + r;
+  __device__ void unit_begin(char *, const tc::Unit &u, int et, Thread &ts) const {
+    const int w = (et >> 5) + 2, lane = et & 31;
+    const int r = (w & 3) * 32 + lane;
+    ts.sg = (int64_t)u.rb0 * tc::BM + r;
+    ts.nabove = 0;
     if (ts.sg < nseg) {
       int64_t st0 = seg_start[ts.sg];
       ts.L = seg_len[ts.sg];
       ts.ts = ths + st0;
       ts.h = hist + 2 * st0;
       ts.tminf = __double2float_rd(ts.ts[0]);
-      ts.b = tc::screen_bound_tc(rowb[ts.sg], tileb[ct], gacc, gcan);
+      ts.tmaxf = __double2float_ru(ts.ts[ts.L - 1]);
     } else {
       ts.tminf = INFINITY;
-      ts.b = 0.0f;
+      ts.tmaxf = INFINITY;
     }
+  }
+  __device__ void tile_begin(char *, int, int ct, int, int, Thread &ts) const {
+    ts.b = ts.sg < nseg ? tc::screen_bound_tc(rowb[ts.sg], tileb[ct], gacc, gcan) : 0.0f;
   }
   __device__ void chunk(char *, int, int ct, int, int col, const float (&v)[32],
                         Thread &ts) const {
@@ -740,7 +756,10 @@ struct EpiRC {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       float hf = __fadd_ru(v[j], ts.b);
-      if (hf > ts.tminf && c0 + j < ncols) locate(v[j], hf, (int)(c0 + j), ts);
+      if (hf > ts.tminf && c0 + j < ncols) {
+        if (__fsub_rd(v[j], ts.b) > ts.tmaxf) ++ts.nabove;   // above every threshold
+        else locate(v[j], hf, (int)(c0 + j), ts);
+      }
     }
   }
   // Position of one score in the sorted candidate thresholds (rare path).
@@ -755,7 +774,9 @@ struct EpiRC {
     else q.push((int)ts.sg, c);
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
-  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ void unit_end(char *, const tc::Unit &, int, Thread &ts) const {
+    if (ts.sg < nseg && ts.nabove) atomicAdd(&ts.h[ts.L], ts.nabove);
+  }
 };
 
 // Exact position of each queued score among its segment's thresholds.  A
