@@ -146,10 +146,10 @@ struct EpiFbB {
     const int64_t c0 = (int64_t)ct * bn + col;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      if ((v[j] >= ts.tmax || v[j] <= ts.tmin) && c0 + j < ncols) push((int)(c0 + j), ts);
+      if ((v[j] >= ts.tmax || v[j] <= ts.tmin) && c0 + j < ncols) push((int)ts.row, (int)(c0 + j));
     }
   }
-  __device__ __noinline__ void push(int c, const Thread &ts) const { q.push((int)ts.row, c); }
+  __device__ __noinline__ void push(int row, int c) const { q.push(row, c); }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
   __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
 };
@@ -280,7 +280,9 @@ struct EpiXT {
     uint32_t cnt;
   };
   static constexpr int kW = (kXG + 2) / 2;  // 32-bit words per histogram row
-  static constexpr size_t kSmem = sizeof(uint32_t) * (2 * 128 * kW + 256 + 128);
+  // histograms, per-row totals and list cursors, then a 32 x 33 staging tile per warp
+  static constexpr size_t kStageOff = sizeof(uint32_t) * (2 * 128 * kW + 256 + 128);
+  static constexpr size_t kSmem = kStageOff + sizeof(float) * 8 * 32 * 33;
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
@@ -315,14 +317,27 @@ struct EpiXT {
       ts.skip = INFINITY;
     }
   }
+  // Scores above the floor are a few per cent and scattered over lanes: each
+  // lane parks its 32 scores in a shared tile and walks only its own above-floor
+  // ones, so the warp loops max-over-lanes times instead of once per column.
   __device__ void chunk(char *S, int, int ct, int r, int col, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
+    float *tile = (float *)(S + kStageOff) + warp * 32 * 33 + lane * 33;
+    uint32_t mask = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (v[j] > ts.skip && c0 + j < ncols) count((uint32_t *)S, r, v[j], (int)(c0 + j), ts);
+    for (int j = 0; j < 32; ++j) {
+      tile[j] = v[j];
+      if (v[j] > ts.skip && c0 + j < ncols) mask |= 1u << j;
+    }
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      count((uint32_t *)S, r, tile[j], (int)(c0 + j), ts);
+    }
   }
-  __device__ __noinline__ void count(uint32_t *S, int r, float v, int c, Thread &ts) const {
+  __device__ __forceinline__ void count(uint32_t *S, int r, float v, int c, Thread &ts) const {
     if (lcap > 0 && __fadd_ru(v, ts.b) > ts.top) {
       uint32_t pos = atomicAdd(&S[2 * 128 * kW + 256 + r], 1u);
       if (pos < (uint32_t)lcap) list[ts.row * lcap + pos] = make_uint2((uint32_t)c, __float_as_uint(v));
@@ -466,7 +481,8 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   e.xbin = idx->xbin; e.xg0 = idx->xg0; e.g0f = g0f; e.XLO = idx->XLO; e.XHI = idx->XHI;
   e.mcount = (uint32_t)m;
   e.topf = idx->xtopf; e.list = idx->xlist; e.lcnt = idx->xlcnt; e.lcap = idx->lcap;
-  rkr_status s = launch_screen<BN, 3>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
+  static_assert(tc::screen_smem_bytes<BN, 2, EpiXT>() <= 232448, "exact-table smem");
+  rkr_status s = launch_screen<BN, 2>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
   if (s == RKR_OK && idx->lcap > 0) s = tc_sort_lists(idx, tb, BN, st);
   if (s == RKR_OK && idx->lcap == 0)
     RKR_CUDA(cudaMemsetAsync(idx->xlcnt, 0xff, sizeof(uint32_t) * n, st));
@@ -639,28 +655,28 @@ struct EpiTheta {
         } else if (PASS == 3) {
           const int Lq = Ls[col + j];
           // level of the upper bound is L* exactly: above every smaller level's start
-          if (jlo >= ju[Lq] && (Lq == 0 || jlo < ju[Lq - 1])) refine((int)(c0 + j), jlo, Lq, ts);
+          if (jlo >= ju[Lq] && (Lq == 0 || jlo < ju[Lq - 1])) refine((int)(c0 + j), jlo, Lq, ts.u);
         } else if (jhi >= jl[Ls[col + j]]) {
-          emit((int)(c0 + j), jhi, caps(S)[col + j], ts);
+          emit((int)(c0 + j), jhi, caps(S)[col + j], ts.u);
         }
       }
     }
   }
-  __device__ __noinline__ void refine(int c, int jlo, int Lq, const Thread &ts) const {
-    uint64_t v = jlo >= 1 ? thi[ts.u * tau + jlo - 1] : top;
+  __device__ __noinline__ void refine(int c, int jlo, int Lq, int64_t u) const {
+    uint64_t v = jlo >= 1 ? thi[u * tau + jlo - 1] : top;
     uint64_t base, width;
     level_range(Lq, scale, base, width);
     uint64_t bkt = v >= base ? (v - base) / width : 0;
     if (bkt >= kFine) bkt = kFine - 1;
     atomicAdd(&fine[(int64_t)(qa + c) * kFine + bkt], 1u);
   }
-  __device__ __noinline__ void emit(int c, int jhi, uint32_t capq, const Thread &ts) const {
-    uint32_t lb = jhi < tau ? tlo[ts.u * tau + jhi] : 0u;
+  __device__ __noinline__ void emit(int c, int jhi, uint32_t capq, int64_t u) const {
+    uint32_t lb = jhi < tau ? tlo[u * tau + jhi] : 0u;
     if (lb > capq) return;
     int q = qa + c;
     uint32_t pos = atomicAdd(&qcursor[q], 1u);
     int64_t at = qoff[q] + pos;
-    cand_u[at] = (int32_t)ts.u;
+    cand_u[at] = (int32_t)u;
     cand_q[at] = q;
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
@@ -711,13 +727,15 @@ rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const
 // =============================================================== recount
 
 struct EpiRC {
+  static constexpr int kR = 8;   // thresholds kept in registers
   struct Thread {
     float b, tminf, tmaxf;
     int64_t sg;
     int L;
     const double *ts;
     uint32_t *h;
-    uint32_t nabove;   // items above every threshold of the segment (pos = L)
+    float tdn[kR], tup[kR];      // thresholds rounded down / up to float (L <= kR)
+    uint32_t cnt[kR + 1];        // register histogram of positions (L <= kR)
   };
   static constexpr size_t kSmem = 0;
   int64_t nseg, ncols;
@@ -734,7 +752,8 @@ struct EpiRC {
     const int w = (et >> 5) + 2, lane = et & 31;
     const int r = (w & 3) * 32 + lane;
     ts.sg = (int64_t)u.rb0 * tc::BM + r;
-    ts.nabove = 0;
+#pragma unroll
+    for (int i = 0; i <= kR; ++i) ts.cnt[i] = 0;
     if (ts.sg < nseg) {
       int64_t st0 = seg_start[ts.sg];
       ts.L = seg_len[ts.sg];
@@ -742,7 +761,14 @@ struct EpiRC {
       ts.h = hist + 2 * st0;
       ts.tminf = __double2float_rd(ts.ts[0]);
       ts.tmaxf = __double2float_ru(ts.ts[ts.L - 1]);
+#pragma unroll
+      for (int i = 0; i < kR; ++i) {
+        double t = i < ts.L ? ts.ts[i] : INFINITY;
+        ts.tdn[i] = __double2float_rd(t);
+        ts.tup[i] = __double2float_ru(t);
+      }
     } else {
+      ts.L = 0;
       ts.tminf = INFINITY;
       ts.tmaxf = INFINITY;
     }
@@ -757,25 +783,50 @@ struct EpiRC {
     for (int j = 0; j < 32; ++j) {
       float hf = __fadd_ru(v[j], ts.b);
       if (hf > ts.tminf && c0 + j < ncols) {
-        if (__fsub_rd(v[j], ts.b) > ts.tmaxf) ++ts.nabove;   // above every threshold
-        else locate(v[j], hf, (int)(c0 + j), ts);
+        const float lf = __fsub_rd(v[j], ts.b);
+        if (lf > ts.tmaxf) {
+          ++ts.cnt[kR];                      // above every threshold: position L
+        } else if (ts.L <= kR) {
+          // pos = #{t < s}: t_i < lf certainly if tup_i < lf; t_i >= hf certainly
+          // if tdn_i >= hf; anything else is undecided
+          int plo = 0, phi = 0;
+#pragma unroll
+          for (int i = 0; i < kR; ++i) {
+            plo += ts.tup[i] < lf;
+            phi += ts.tdn[i] < hf;
+          }
+          if (plo == phi) {
+#pragma unroll
+            for (int i = 0; i < kR; ++i) ts.cnt[i] += plo == i;
+          } else {
+            push_undecided((int)ts.sg, (int)(c0 + j));
+          }
+        } else {
+          locate(v[j], hf, ts.b, (int)(c0 + j), (int)ts.sg, ts.L, ts.ts, ts.h);
+        }
       }
     }
   }
-  // Position of one score in the sorted candidate thresholds (rare path).
-  __device__ __noinline__ void locate(float v, float hf, int c, const Thread &ts) const {
-    double hi = (double)hf, lo = (double)__fsub_rd(v, ts.b);
-    int a0 = 0, a1 = ts.L;
-    while (a0 < a1) { int md = (a0 + a1) >> 1; if (ts.ts[md] < lo) a0 = md + 1; else a1 = md; }
+  __device__ __noinline__ void push_undecided(int sg, int c) const { q.push(sg, c); }
+  // Position of one score in the sorted candidate thresholds (long blocks).
+  __device__ __noinline__ void locate(float v, float hf, float b, int c, int sg, int L,
+                                      const double *t, uint32_t *h) const {
+    double hi = (double)hf, lo = (double)__fsub_rd(v, b);
+    int a0 = 0, a1 = L;
+    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < lo) a0 = md + 1; else a1 = md; }
     int pa = a0;
-    a1 = ts.L;
-    while (a0 < a1) { int md = (a0 + a1) >> 1; if (ts.ts[md] < hi) a0 = md + 1; else a1 = md; }
-    if (a0 == pa) atomicAdd(&ts.h[pa], 1u);
-    else q.push((int)ts.sg, c);
+    a1 = L;
+    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < hi) a0 = md + 1; else a1 = md; }
+    if (a0 == pa) atomicAdd(&h[pa], 1u);
+    else q.push(sg, c);
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
   __device__ void unit_end(char *, const tc::Unit &, int, Thread &ts) const {
-    if (ts.sg < nseg && ts.nabove) atomicAdd(&ts.h[ts.L], ts.nabove);
+    if (ts.sg >= nseg) return;
+    if (ts.cnt[kR]) atomicAdd(&ts.h[ts.L], ts.cnt[kR]);
+#pragma unroll
+    for (int i = 0; i < kR; ++i)
+      if (ts.cnt[i]) atomicAdd(&ts.h[i], ts.cnt[i]);   // only i < L can be nonzero
   }
 };
 
