@@ -68,7 +68,7 @@ typedef struct {
   int32_t exact_table;      /* 1: also build the exact count table rkr_query_exact needs */
   int32_t floor_rank;       /* exact table: counts are kept exact only above the
                                threshold whose estimated rank is floor_rank; 0 = default
-                               max(2048, m / 32).  Only speed depends on it. */
+                               max(2048, m / 16).  Only speed depends on it. */
   const int32_t *sample_pos;/* omega x s positions inside each bucket of the norm-sorted
                                items, -1 = unused; a bucket of at most s items must list
                                0..|P_l|-1.  Host or device.  NULL = draw them from `seed`

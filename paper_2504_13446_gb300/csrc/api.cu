@@ -197,7 +197,7 @@ rkr_status rkr_build(const float *U, int64_t n, const float *P, int64_t m, int32
   idx->s = p.s;
   idx->fbounds = p.fbounds;
   idx->has_exact = p.exact_table ? 1 : 0;
-  idx->floor_rank = p.floor_rank ? p.floor_rank : (int)(m / 32 > 2048 ? m / 32 : 2048);
+  idx->floor_rank = p.floor_rank ? p.floor_rank : (int)(m / 16 > 2048 ? m / 16 : 2048);
   rkr_status stt = build_index(idx, (const float *)vu.dev, (const float *)vp.dev, &p,
                                p.sample_pos ? spos.data() : nullptr, st);
   if (stt != RKR_OK) {

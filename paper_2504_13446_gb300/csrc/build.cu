@@ -404,6 +404,19 @@ __global__ void k_floor_cols(int64_t n, int tau, const uint32_t *__restrict__ N,
   fl[u] = a > 0 ? a - 1 : 0;
 }
 
+// Capacity of each user's tail list: 1.5 times the sampled table's estimate of
+// the count above the floor threshold, plus 256, at most kListCapMax (0 when
+// lists are disabled).  Lists that overflow are detected and not used.
+__global__ void k_list_caps(int64_t n, int tau, const uint32_t *__restrict__ N, uint32_t s,
+                            const int32_t *__restrict__ fl, int enabled, uint32_t *__restrict__ cap) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  if (!enabled) { cap[u] = 0; return; }
+  uint64_t est = (uint64_t)N[u * tau + fl[u]] / s;
+  uint64_t c = est + est / 2 + 256;
+  cap[u] = (uint32_t)(c < (uint64_t)kListCapMax ? c : kListCapMax);
+}
+
 // ------------------------------------------------------------- sampling
 
 // SplitMix64 (Steele, Lea and Flood, 2014), used only when the caller supplies
@@ -626,21 +639,32 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     RKR_TRY(dalloc(&idx->xbin, n));
     RKR_TRY(dalloc(&idx->XLO, (size_t)n * kXGrid));
     RKR_TRY(dalloc(&idx->XHI, (size_t)n * kXGrid));
-    idx->lcap = m < (1 << 24) ? kListCap : 0;  // list entries park a column in the item's top byte
-    RKR_TRY(dalloc(&idx->xlistcol, n));
-    RKR_TRY(dalloc(&idx->xtop, n));
-    RKR_TRY(dalloc(&idx->xtopf, n));
-    RKR_TRY(dalloc(&idx->xlist, (size_t)n * std::max(idx->lcap, 1)));
-    RKR_TRY(dalloc(&idx->xcoff, (size_t)n * (kXGrid + 2)));
     RKR_TRY(dalloc(&idx->xlcnt, n));
+    RKR_TRY(dalloc(&idx->xcoff, (size_t)n * (kXGrid + 2)));
     RKR_TRY(dalloc(&idx->xbmax, n));
     RKR_TRY(dalloc(&idx->ptile3, (size_t)((m + 255) / 256)));
-    k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(
-        n, tau, idx->N, (uint32_t)s, (uint64_t)std::min(idx->floor_rank, kListRank),
-        idx->xlistcol); note_launch();
+    RKR_TRY(dalloc(&idx->xlcap, n));
+    RKR_TRY(dalloc(&idx->xloff, n + 1));
     k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
                                                                (uint64_t)idx->floor_rank,
                                                                idx->xfloor); note_launch();
+    // list entries park a grid column in the item index's top byte
+    idx->lists = m < (1 << 24);
+    k_list_caps<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
+                                                              idx->xfloor, idx->lists,
+                                                              idx->xlcap); note_launch();
+    {
+      std::vector<uint32_t> cap(n);
+      std::vector<int64_t> off(n + 1, 0);
+      RKR_CUDA(cudaMemcpyAsync(cap.data(), idx->xlcap, sizeof(uint32_t) * n,
+                               cudaMemcpyDeviceToHost, st));
+      RKR_CUDA(cudaStreamSynchronize(st));
+      for (int64_t u = 0; u < n; ++u) off[u + 1] = off[u] + cap[u];
+      RKR_TRY(dalloc(&idx->xlist, (size_t)std::max<int64_t>(off[n], 1)));
+      RKR_CUDA(cudaMemcpyAsync(idx->xloff, off.data(), sizeof(int64_t) * (n + 1),
+                               cudaMemcpyHostToDevice, st));
+      RKR_CUDA(cudaStreamSynchronize(st));
+    }
     RKR_TRY(tc_exact_table(idx, idx->Ut, idx->Pt, st, nullptr));
     idx->nlev_x = levels_for((uint64_t)m);
     RKR_TRY(dalloc(&idx->XJU, (size_t)n * kMaxLevels));
@@ -668,7 +692,7 @@ void index_release(rkr_index *idx) {
                   idx->pnrm_s, idx->fmin, idx->fmax, idx->delta, idx->binfp, idx->N,
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
                   idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
-                  idx->xfloor, idx->xlistcol, idx->xtop, idx->xtopf, idx->xlist, idx->xlcnt,
+                  idx->xfloor, idx->xloff, idx->xlcap, idx->xlist, idx->xlcnt,
                   idx->xbmax, idx->ptile3, idx->xcoff};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -44,16 +44,15 @@ struct rkr_index {
   int16_t *XJU = nullptr, *XJL = nullptr;   // n x 32
   int32_t *xfloor = nullptr;                // n: paper column of x_0
 
-  // tail lists: per user, every item whose score may exceed x_top (the paper
-  // threshold whose estimated count is list_rank), sorted by screened score
-  int lcap = 0;
-  int32_t *xlistcol = nullptr;              // n: paper column of x_top
-  double *xtop = nullptr;                   // n
-  float *xtopf = nullptr;                   // n: x_top rounded down
-  uint2 *xlist = nullptr;                   // n x lcap: (item, float bits of screened score),
-                                            // grouped by exact-grid column
+  // tail lists: per user, every item whose screened score may exceed x_0 (the
+  // exact grid's floor), grouped by exact-grid column; user u's entries are
+  // xlist[xloff[u] .. xloff[u] + xlcnt[u]) within a capacity xlcap[u]
+  int lists = 0;
+  int64_t *xloff = nullptr;                 // n + 1
+  uint32_t *xlcap = nullptr;                // n
+  uint2 *xlist = nullptr;                   // (item, float bits of screened score)
+  uint32_t *xlcnt = nullptr;                // n: entries, > xlcap[u] marks an overflow
   uint16_t *xcoff = nullptr;                // n x (xg + 2): start of each column's entries
-  uint32_t *xlcnt = nullptr;                // n: entries, lcap + 1 = overflow
   float *xbmax = nullptr;                   // n: largest screen bound of a user's entries
   rkr::tc::RowBound *ptile3 = nullptr;      // item tile bounds of the split screen
   int ptile_bn = 0;
@@ -114,8 +113,7 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       const int32_t *seg_user, const double *ths, uint32_t *hist,
                       cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
-constexpr int kListCap = 4096;  // < 2^16 (column offsets are 16-bit)
-constexpr int kListRank = 1024;
+constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);
 
 // Row norms: FP64 canonical norms (optional) and FP32 upper bounds.

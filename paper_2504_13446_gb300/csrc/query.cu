@@ -376,20 +376,21 @@ __global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_s
   for (int i = 0; i < L; ++i) ccount[order[st0 + i]] = h[i + 1];
 }
 
-// Exact ranks from the tail lists.  A candidate (u, q) with u.q >= x_top(u)
+// Exact ranks from the tail lists.  A candidate (u, q) with u.q >= x_0(u)
 // has rank 1 + #{p in list(u) : s(u,p) > u.q}, since every item scoring above
-// x_top is in the list.  Entries are grouped by exact-grid column: whole
+// x_0 is in the list.  Entries are grouped by exact-grid column: whole
 // columns are counted from the column offsets, and the entries of the one or
 // two columns within the screen bound of u.q are settled one by one, by their
-// own bound, an FP32 dot product with its bound, or canonically.  Candidates below x_top (or with an overflowed list) are
+// own bound, an FP32 dot product with its bound, or canonically.  Candidates below x_0 (or with an overflowed list) are
 // passed on, unchanged, in cu_fb for the recount screen; others get -1 there.
 __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             const int32_t *__restrict__ cq, const float *__restrict__ U,
                             const float *__restrict__ unrm, const float *__restrict__ Q,
                             const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int d,
-                            const double *__restrict__ xtop, const uint2 *__restrict__ xlist,
+                            const uint2 *__restrict__ xlist,
+                            const int64_t *__restrict__ xloff, const uint32_t *__restrict__ xlcap,
                             const uint16_t *__restrict__ xcoff,
-                            const uint32_t *__restrict__ xlcnt, int lcap,
+                            const uint32_t *__restrict__ xlcnt,
                             const float *__restrict__ xbmax, const tc::RowBound *__restrict__ rb3,
                             const tc::RowBound *__restrict__ ptile, int pbn, tc::Gacc gacc,
                             float gcan, const double *__restrict__ xg0,
@@ -404,7 +405,7 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   const float *uu = U + u * d;
   const double theta = canon_dot(uu, Q + (int64_t)cq[i] * d, d);
   const uint32_t L = xlcnt[u];
-  if (L > (uint32_t)lcap || theta < xtop[u]) {
+  if (L > xlcap[u] || theta < xg0[u]) {
     // bounds from the exact count table at the exact bin of u.q
     const int j = exact_j(theta, xg0[u], xdx[u], G);
     ccount[i] = j >= 1 ? XHI[u * G + j - 1] : mtop;
@@ -415,7 +416,7 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   }
   cu_fb[i] = -1;
   // entries are grouped by column c = #{x_j <= v}: x_{c-1} <= v < x_c
-  const uint2 *row = xlist + u * lcap;
+  const uint2 *row = xlist + xloff[u];
   const uint16_t *co = xcoff + u * (G + 2);
   const double B = (double)xbmax[u];
   const double g0 = xg0[u], dx = xdx[u];
@@ -948,8 +949,8 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
       RKR_TRY(tmp_alloc(blb, &clb, cnt, st));
       RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
       k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
-          cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d, idx->xtop,
-          idx->xlist, idx->xcoff, idx->xlcnt, idx->lcap, idx->xbmax, idx->Ut.rb3, idx->ptile3,
+          cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d,
+          idx->xlist, idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
           idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
           idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, lstat);
       note_launch();

@@ -273,11 +273,13 @@ __global__ void k_xgrid(int64_t n, const double *__restrict__ fmin,
 // more than 65535 items gets the trivial bounds 0 and m instead.
 struct EpiXT {
   struct Thread {
-    float skip, b, top;
+    float skip, b;
     BinFP bf;
     double g0;
     int64_t row;
     uint32_t cnt;
+    int64_t off;
+    uint32_t cap;
   };
   static constexpr int kW = (kXG + 2) / 2;  // 32-bit words per histogram row
   // histograms, per-row totals and list cursors, then a 32 x 33 staging tile per warp
@@ -293,11 +295,11 @@ struct EpiXT {
   const float *g0f;
   uint32_t *XLO, *XHI;
   uint32_t mcount;
-  // tail lists: every item whose score may exceed x_top is appended to its user's list
-  const float *topf;   // x_top rounded down to float
-  uint2 *list;         // n x lcap entries (item, screened score bits)
-  uint32_t *lcnt;      // n: entries (lcap + 1 marks an overflow)
-  int lcap;
+  // tail lists: every above-floor item is appended to its user's list
+  uint2 *list;
+  const int64_t *loff;
+  const uint32_t *lcapv;
+  uint32_t *lcnt;      // n: entries (> capacity marks an overflow)
   __device__ uint32_t *lslot(char *S) const { return (uint32_t *)S + 2 * 128 * kW + 256; }
   __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &ts) const {
     uint32_t *H = (uint32_t *)S;
@@ -310,7 +312,8 @@ struct EpiXT {
     if (ts.row < nrows) {
       ts.b = tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan);
       ts.skip = __fsub_rd(g0f[ts.row], ts.b);  // s_hat <= skip implies s <= x_0
-      ts.top = topf[ts.row];
+      ts.off = loff[ts.row];
+      ts.cap = lcapv[ts.row];
       ts.bf = xbin[ts.row];
       ts.g0 = xg0[ts.row];
     } else {
@@ -338,9 +341,9 @@ struct EpiXT {
     }
   }
   __device__ __forceinline__ void count(uint32_t *S, int r, float v, int c, Thread &ts) const {
-    if (lcap > 0 && __fadd_ru(v, ts.b) > ts.top) {
+    {  // every above-floor item goes to the list: it is complete above x_0
       uint32_t pos = atomicAdd(&S[2 * 128 * kW + 256 + r], 1u);
-      if (pos < (uint32_t)lcap) list[ts.row * lcap + pos] = make_uint2((uint32_t)c, __float_as_uint(v));
+      if (pos < ts.cap) list[ts.off + pos] = make_uint2((uint32_t)c, __float_as_uint(v));
     }
     int clo, chi;
     bin_interval(ts.bf, ts.g0, kXG, __fsub_rd(v, ts.b), __fadd_ru(v, ts.b), clo, chi);
@@ -363,7 +366,7 @@ struct EpiXT {
     const uint32_t *Hlo = (const uint32_t *)S + et * kW;
     const uint32_t *Hhi = (const uint32_t *)S + 128 * kW + et * kW;
     const bool ok = tot[et] + tot[128 + et] <= 65535u;
-    lcnt[g] = min(lslot(S)[et], (uint32_t)lcap + 1);
+    lcnt[g] = lslot(S)[et];
     uint32_t rlo = 0, rhi = 0;
     for (int c = kXG; c >= 1; --c) {
       rlo += (Hlo[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
@@ -376,36 +379,36 @@ struct EpiXT {
 
 // Group each user's tail list by the exact-grid column of the screened score,
 // col(v) = #{j : x_j <= v} in 0..G (counting sort), and record the column
-// offsets and the largest screen bound of the entries.  One warp per user;
-// overflowed lists are left as they are and marked unusable by their count.
-constexpr int kListWarps = 4;
+// offsets and the largest screen bound of the entries.  One CTA per user;
+// overflowed lists are left as they are and marked unusable.
+constexpr int kGroupThreads = 256;
 
-__global__ void __launch_bounds__(kListWarps * 32)
-    k_list_group(int64_t n, int lcap, uint2 *__restrict__ list, const uint32_t *__restrict__ lcnt,
+__global__ void __launch_bounds__(kGroupThreads)
+    k_list_group(int64_t n, uint2 *__restrict__ list, const int64_t *__restrict__ loff,
+                 const uint32_t *__restrict__ lcap, const uint32_t *__restrict__ lcnt,
                  const BinFP *__restrict__ xbin, const double *__restrict__ xg0,
                  const double *__restrict__ xdx, int G, const tc::RowBound *__restrict__ rowb,
                  const tc::RowBound *__restrict__ tileb, int bn, tc::Gacc gacc, float gcan,
                  uint16_t *__restrict__ coff, float *__restrict__ bmax) {
   extern __shared__ unsigned char lsm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint2 *buf = (uint2 *)lsm + (size_t)warp * lcap;
-  uint32_t *cnt = (uint32_t *)((uint2 *)lsm + (size_t)kListWarps * lcap) + warp * (G + 2);
-  const int64_t u = (int64_t)blockIdx.x * kListWarps + warp;
-  if (u >= n) return;
+  uint2 *buf = (uint2 *)lsm;                                  // kListCapMax
+  uint32_t *cnt = (uint32_t *)(buf + kListCapMax);            // G + 2
+  float *red = (float *)(cnt + G + 2);                        // kGroupThreads / 32
+  const int64_t u = blockIdx.x;
   const uint32_t L = lcnt[u];
   uint16_t *co = coff + u * (G + 2);
-  if (L > (uint32_t)lcap) {
-    if (lane == 0) bmax[u] = INFINITY;
+  if (L > lcap[u]) {  // overflow (or lists disabled with L > 0)
+    if (threadIdx.x == 0) bmax[u] = INFINITY;
     return;
   }
-  for (int c = lane; c < G + 2; c += 32) cnt[c] = 0;
-  __syncwarp();
-  uint2 *row = list + u * lcap;
+  for (int c = threadIdx.x; c < G + 2; c += blockDim.x) cnt[c] = 0;
+  __syncthreads();
+  uint2 *row = list + loff[u];
   const BinFP bf = xbin[u];
   const double g0 = xg0[u], dx = xdx[u];
   const tc::RowBound ru = rowb[u];
   float bm = 0.0f;
-  for (uint32_t i = lane; i < L; i += 32) {
+  for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
     uint2 e = row[i];
     float v = __uint_as_float(e.y);
     int jlo, jhi;
@@ -416,8 +419,10 @@ __global__ void __launch_bounds__(kListWarps * 32)
     atomicAdd(&cnt[col], 1u);
     bm = fmaxf(bm, tc::screen_bound_tc(ru, tileb[(e.x & 0xffffffu) / bn], gacc, gcan));
   }
-  __syncwarp();
-  if (lane == 0) {  // exclusive prefix over G + 1 columns
+  for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bm;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive prefix over G + 1 columns
     uint32_t run = 0;
     for (int c = 0; c <= G; ++c) {
       uint32_t t = cnt[c];
@@ -426,16 +431,17 @@ __global__ void __launch_bounds__(kListWarps * 32)
       run += t;
     }
     co[G + 1] = (uint16_t)run;
+    float m2 = 0.0f;
+    for (int w = 0; w < kGroupThreads / 32; ++w) m2 = fmaxf(m2, red[w]);
+    bmax[u] = m2;
   }
-  __syncwarp();
-  for (uint32_t i = lane; i < L; i += 32) {
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
     uint2 e = buf[i];
     int col = (int)(e.x >> 24);
     uint32_t pos = atomicAdd(&cnt[col], 1u);
     row[pos] = make_uint2(e.x & 0xffffffu, e.y);
   }
-  for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-  if (lane == 0) bmax[u] = bm;
 }
 
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st) {
@@ -445,13 +451,14 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
                            cudaMemcpyDeviceToDevice, st));
   idx->ptile_bn = bn;
   const int G = idx->xg;
-  size_t sm = sizeof(uint2) * (size_t)kListWarps * idx->lcap +
-              sizeof(uint32_t) * (size_t)kListWarps * (G + 2);
+  size_t sm = sizeof(uint2) * kListCapMax + sizeof(uint32_t) * (G + 2) +
+              sizeof(float) * (kGroupThreads / 32);
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
-  k_list_group<<<(unsigned)((idx->n + kListWarps - 1) / kListWarps), kListWarps * 32, sm, st>>>(
-      idx->n, idx->lcap, idx->xlist, idx->xlcnt, idx->xbin, idx->xg0, idx->xdx, G, idx->Ut.rb3,
-      idx->ptile3, bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff, idx->xbmax);
+  k_list_group<<<(unsigned)idx->n, kGroupThreads, sm, st>>>(
+      idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->xbin, idx->xg0, idx->xdx, G,
+      idx->Ut.rb3, idx->ptile3, bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff,
+      idx->xbmax);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
@@ -471,21 +478,17 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   k_xgrid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, idx->fmin, idx->delta, idx->xfloor,
                                                        idx->xg0, g0f);
   note_launch();
-  k_xgrid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, idx->fmin, idx->delta, idx->xlistcol,
-                                                       idx->xtop, idx->xtopf);
-  note_launch();
+
   RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, kXG, idx->pmax, idx->xdx, idx->xbin, st));
   EpiXT e;
   e.nrows = n; e.ncols = m; e.bn = BN; e.rowb = Ut.rb3; e.tileb = tb;
   e.gacc = tc_gacc(Ut.kp, 1); e.gcan = tc_gcan(idx->d);
   e.xbin = idx->xbin; e.xg0 = idx->xg0; e.g0f = g0f; e.XLO = idx->XLO; e.XHI = idx->XHI;
   e.mcount = (uint32_t)m;
-  e.topf = idx->xtopf; e.list = idx->xlist; e.lcnt = idx->xlcnt; e.lcap = idx->lcap;
+  e.list = idx->xlist; e.loff = idx->xloff; e.lcapv = idx->xlcap; e.lcnt = idx->xlcnt;
   static_assert(tc::screen_smem_bytes<BN, 2, EpiXT>() <= 232448, "exact-table smem");
   rkr_status s = launch_screen<BN, 2>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
-  if (s == RKR_OK && idx->lcap > 0) s = tc_sort_lists(idx, tb, BN, st);
-  if (s == RKR_OK && idx->lcap == 0)
-    RKR_CUDA(cudaMemsetAsync(idx->xlcnt, 0xff, sizeof(uint32_t) * n, st));
+  if (s == RKR_OK) s = tc_sort_lists(idx, tb, BN, st);
   int hf[2] = {0, 0};
   cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
   cudaError_t err = cudaStreamSynchronize(st);

@@ -47,7 +47,7 @@ def check_exact_table(ora, gpu, U, P, floor_rank=0):
     x_0 is the sampled table's threshold at its last column whose estimated count
     reaches the floor rank and x_{G-1} = f_max (same threshold formula)."""
     m, s, tau = P.shape[0], ora["s"], ora["tau"]
-    R = floor_rank or max(2048, m // 32)
+    R = floor_rank or max(2048, m // 16)
     S = oracle.scores(U, P)
     grid = gpu.export("xgrid")
     xlo, xhi = gpu.export("xlo"), gpu.export("xhi")
