@@ -710,9 +710,50 @@ static int64_t candidate_budget() { return (int64_t)1 << 26; }
 
 // Exact ranks of `cnt` candidates (cu, cq): canonical u.q, sort by (user, u.q),
 // one grouped pass over P per user.  ccount[i] = #{p : s(u_i, p) > u_i.q_i}.
-static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int64_t cnt,
-                                     const int32_t *cu, const int32_t *cq, uint32_t *ccount,
-                                     unsigned long long *ties_d, cudaStream_t st) {
+__global__ void k_compact(int64_t n, const int32_t *__restrict__ cu, const int32_t *__restrict__ cq,
+                          unsigned long long *__restrict__ cursor, int32_t *__restrict__ ou,
+                          int32_t *__restrict__ oq, int32_t *__restrict__ oi) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n || cu[i] < 0) return;
+  unsigned long long p = atomicAdd(cursor, 1ull);
+  ou[p] = cu[i];
+  oq[p] = cq[i];
+  oi[p] = (int32_t)i;
+}
+
+__global__ void k_scatter_back(int64_t n, const int32_t *__restrict__ oi,
+                               const uint32_t *__restrict__ c2, uint32_t *__restrict__ ccount) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ccount[oi[i]] = c2[i];
+}
+
+// Exact ranks of the candidates whose cu entry is valid (the others keep their
+// ccount): compact them, canonical u.q, sort by (user, u.q), one grouped
+// tensor-core pass over P per user.  ccount[i] = #{p : s(u_i, p) > u_i.q_i}.
+static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int64_t total,
+                                     const int32_t *cu_all, const int32_t *cq_all,
+                                     uint32_t *ccount_all, unsigned long long *ties_d,
+                                     cudaStream_t st) {
+  const int bs = 256;
+  DevBuf bcu, bcq, bci, bcc, bcur;
+  int32_t *cu, *cq, *ci;
+  uint32_t *ccount;
+  unsigned long long *cur;
+  RKR_TRY(tmp_alloc(bcur, &cur, 1, st));
+  RKR_CUDA(cudaMemsetAsync(cur, 0, sizeof(unsigned long long), st));
+  RKR_TRY(tmp_alloc(bcu, &cu, total, st));
+  RKR_TRY(tmp_alloc(bcq, &cq, total, st));
+  RKR_TRY(tmp_alloc(bci, &ci, total, st));
+  k_compact<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(total, cu_all, cq_all, cur, cu, cq,
+                                                               ci);
+  note_launch();
+  unsigned long long hc = 0;
+  RKR_CUDA(cudaMemcpyAsync(&hc, cur, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  const int64_t cnt = (int64_t)hc;
+  if (cnt == 0) return RKR_OK;
+  RKR_TRY(tmp_alloc(bcc, &ccount, cnt, st));
   int64_t Np2 = 1;
   while (Np2 < cnt) Np2 <<= 1;
   DevBuf b1, b2, b3, b4, b5, b6, b7, b8, b9;
@@ -731,17 +772,19 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   RKR_TRY(tmp_alloc(b7, &hist, 2 * cnt, st));
   RKR_TRY(tmp_alloc(b8, &ths, cnt, st));
   RKR_TRY(tmp_alloc(b9, &nseg_d, 1, st));
-  const int bs = 256;
   k_cand_theta<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(cnt, cu, cq, idx->U, Qd, idx->d,
-                                                                th, khi, klo, val, Np2); note_launch();
+                                                                th, khi, klo, val, Np2);
+  note_launch();
   RKR_CUDA(cudaGetLastError());
   for (int64_t k = 2; k <= Np2; k <<= 1)
     for (int64_t j = k >> 1; j > 0; j >>= 1) {
-      k_bitonic128<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(khi, klo, val, Np2, j, k); note_launch();
+      k_bitonic128<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(khi, klo, val, Np2, j, k);
+      note_launch();
     }
   RKR_CUDA(cudaGetLastError());
   RKR_CUDA(cudaMemsetAsync(nseg_d, 0, sizeof(unsigned long long), st));
-  k_segments<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, khi, nseg_d, sstart, slen); note_launch();
+  k_segments<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, khi, nseg_d, sstart, slen);
+  note_launch();
   RKR_CUDA(cudaGetLastError());
   unsigned long long nseg = 0;
   RKR_CUDA(cudaMemcpyAsync(&nseg, nseg_d, sizeof(nseg), cudaMemcpyDeviceToHost, st));
@@ -770,7 +813,10 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     RKR_CUDA(cudaStreamSynchronize(st));
   }
   k_scatter_counts<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
-                                                                   val, hist, ccount); note_launch();
+                                                                   val, hist, ccount);
+  note_launch();
+  k_scatter_back<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, ci, ccount, ccount_all);
+  note_launch();
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
 }
