@@ -921,7 +921,8 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   unsigned long long *qcount;
   int2 *qitems;
   int *flags;
-  const unsigned long long cap = std::max<int64_t>(16 * ncand, 1 << 22);
+  const unsigned long long cap =
+      std::min<int64_t>(std::max<int64_t>(128 * ncand, 1 << 24), (int64_t)1 << 30);
   unsigned long long *nfp64;
   RKR_CUDA(cudaMallocAsync(&nfp64, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(nfp64, 0, sizeof(unsigned long long), st));
