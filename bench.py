@@ -225,7 +225,8 @@ def bench_ours(args):
         "candidates": {"approx": qa0["candidates"], "exact": qe0["candidates"],
                        "exact_recounted": qe0["recounted"],
                        "exact_near_ties": qe0["near_ties"], "fp64_dots_exact": qe0["fp64_dots"],
-                       "wide_queries": [qa0["wide_queries"], qe0["wide_queries"]]},
+                       "wide_queries": [qa0["wide_queries"], qe0["wide_queries"]],
+                       "deep_queries": [qa0["deep_queries"], qe0["deep_queries"]]},
         "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                      "peak_source": "FP32 CUDA-core peak from SM count and max SM clock "

@@ -89,6 +89,11 @@ typedef struct {
   double ms_select;         /* device time of per-query selection */
   int64_t recounted;        /* exact path: candidates ranked by a re-screen of P (the others
                                by their user's tail list) */
+  int32_t deep_queries;     /* queries whose cutoff lies above the skip level: screened
+                               again without the one-compare skip of deep pairs.  The skip
+                               level is the smallest L with 2^L - 1 >= m / 128, or the
+                               value of the environment variable RKR_SKIP_LEVEL; results
+                               do not depend on it. */
 } rkr_query_stats;
 
 /*

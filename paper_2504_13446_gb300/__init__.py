@@ -52,7 +52,8 @@ class QueryStats(ctypes.Structure):
                 ("fp64_dots", ctypes.c_int64), ("near_ties", ctypes.c_int64),
                 ("wide_queries", ctypes.c_int32), ("max_rel_screen_err", ctypes.c_double),
                 ("ms_theta", ctypes.c_double), ("ms_resolve", ctypes.c_double),
-                ("ms_select", ctypes.c_double), ("recounted", ctypes.c_int64)]
+                ("ms_select", ctypes.c_double), ("recounted", ctypes.c_int64),
+                ("deep_queries", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -640,7 +640,9 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     RKR_TRY(dalloc(&idx->XLO, (size_t)n * kXGrid));
     RKR_TRY(dalloc(&idx->XHI, (size_t)n * kXGrid));
     RKR_TRY(dalloc(&idx->xlcnt, n));
-    RKR_TRY(dalloc(&idx->xcoff, (size_t)n * (kXGrid + 2)));
+    RKR_TRY(dalloc(&idx->xcoff, (size_t)n * (kListG + 2)));
+    RKR_TRY(dalloc(&idx->ldx, n));
+    RKR_TRY(dalloc(&idx->lbin, n));
     RKR_TRY(dalloc(&idx->xbmax, n));
     RKR_TRY(dalloc(&idx->ptile3, (size_t)((m + 255) / 256)));
     RKR_TRY(dalloc(&idx->xlcap, n));
@@ -648,8 +650,7 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
                                                                (uint64_t)idx->floor_rank,
                                                                idx->xfloor); note_launch();
-    // list entries park a grid column in the item index's top byte
-    idx->lists = m < (1 << 24);
+    idx->lists = 1;
     k_list_caps<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, tau, idx->N, (uint32_t)s,
                                                               idx->xfloor, idx->lists,
                                                               idx->xlcap); note_launch();
@@ -693,7 +694,7 @@ void index_release(rkr_index *idx) {
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
                   idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
                   idx->xfloor, idx->xloff, idx->xlcap, idx->xlist, idx->xlcnt,
-                  idx->xbmax, idx->ptile3, idx->xcoff};
+                  idx->xbmax, idx->ptile3, idx->xcoff, idx->ldx, idx->lbin};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   tc_free(idx->Ut);

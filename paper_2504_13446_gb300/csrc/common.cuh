@@ -103,11 +103,16 @@ struct BinFP {
   float pad;
 };
 
+// Upper bound of the bin coordinate of x (non-decreasing in x where it is not NaN).
+__device__ __forceinline__ float bin_vhi(const BinFP &b, float x) {
+  return __fadd_ru(__fmul_ru(__fsub_ru(x, b.fmin32), b.invd32), b.err);
+}
+
 // FP32 bin coordinate lower/upper bounds for x in [xlo, xhi].
 __device__ __forceinline__ void bin_coord(const BinFP &b, float xlo, float xhi, float &vlo,
                                           float &vhi) {
   vlo = __fsub_rd(__fmul_rd(__fsub_rd(xlo, b.fmin32), b.invd32), b.err);
-  vhi = __fadd_ru(__fmul_ru(__fsub_ru(xhi, b.fmin32), b.invd32), b.err);
+  vhi = bin_vhi(b, xhi);
 }
 
 // Lower end: ceil(v) clamped into [0, tau] (a lower bound of both c and j).

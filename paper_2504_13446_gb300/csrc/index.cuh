@@ -52,7 +52,9 @@ struct rkr_index {
   uint32_t *xlcap = nullptr;                // n
   uint2 *xlist = nullptr;                   // (item, float bits of screened score)
   uint32_t *xlcnt = nullptr;                // n: entries, > xlcap[u] marks an overflow
-  uint16_t *xcoff = nullptr;                // n x (xg + 2): start of each column's entries
+  uint16_t *xcoff = nullptr;                // n x (kListG + 2): start of each list column
+  double *ldx = nullptr;                    // n: step of the list grid x_0 + j ldx, j < kListG
+  rkr::BinFP *lbin = nullptr;               // n: bin parameters of the list grid
   float *xbmax = nullptr;                   // n: largest screen bound of a user's entries
   rkr::tc::RowBound *ptile3 = nullptr;      // item tile bounds of the split screen
   int ptile_bn = 0;
@@ -104,6 +106,11 @@ struct ThetaArgs {
   const int64_t *qoff;          // pass 2
   uint32_t *qcursor;
   int32_t *cand_u, *cand_q;
+  int nq_all;                   // queries of the whole batch (pass 1 histogram pitch)
+  const float *xs;              // per-user skip scores (null: every pair is screened)
+  const int32_t *qmap;          // global query of each column (null: qa + column)
+  int lskip;                    // passes 2, 3: leave out queries with L* above this
+  int *ovf;                     // pass 2: overflow flag of the candidate segments
 };
 rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
                          const ThetaArgs &a, int split, int *err, cudaStream_t st);
@@ -114,6 +121,7 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
 constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)
+constexpr int kListG = 1024;        // columns of the list grid (finer than the count grid)
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);
 
 // Row norms: FP64 canonical norms (optional) and FP32 upper bounds.

@@ -16,7 +16,10 @@
 //   select  one CTA per query: Section 4.3 steps 1-3 (approximate) or the k
 //           smallest (rank, index) (exact) over the candidates.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include <vector>
 
@@ -31,18 +34,29 @@ namespace rkr {
 // Cutoff level of each query: L* = the smallest level holding k upper bounds;
 // below = pairs whose upper bound lies in a lower level; ncand = pairs whose
 // lower bound lies in a level <= L* (an upper bound of the candidate count).
+// Only levels <= lcap are complete in the histograms; a query that does not
+// reach k there gets L* = kDeep and is screened again without skipping.
+constexpr int kDeep = kMaxLevels;
+
 __global__ void k_cutoff(int nq, const uint32_t *__restrict__ hist_up,
                          const uint32_t *__restrict__ hist_lo, const int32_t *__restrict__ kq,
-                         int nlev, int32_t *__restrict__ lstar, uint64_t *__restrict__ below,
-                         int64_t *__restrict__ ncand) {
+                         int nlev, int lcap, int32_t *__restrict__ lstar,
+                         uint64_t *__restrict__ below, int64_t *__restrict__ ncand) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
   uint64_t cum = 0, prev = 0;
-  int L = nlev - 1;
-  for (int l = 0; l < 32; ++l) {
+  int L = lcap >= nlev - 1 ? nlev - 1 : kDeep;
+  const int lend = lcap < 31 ? lcap : 31;
+  for (int l = 0; l <= lend; ++l) {
     prev = cum;
     cum += hist_up[(int64_t)q * 32 + l];
     if (cum >= (uint64_t)kq[q]) { L = l; break; }
+  }
+  if (L == kDeep) {
+    lstar[q] = kDeep;
+    below[q] = 0;
+    ncand[q] = 0;
+    return;
   }
   if (L > nlev - 1) L = nlev - 1;
   uint64_t c = 0;
@@ -50,6 +64,53 @@ __global__ void k_cutoff(int nq, const uint32_t *__restrict__ hist_up,
   lstar[q] = L;
   below[q] = prev;
   ncand[q] = (int64_t)c;
+}
+
+// Skip score of each user for skip level LS: the largest float x such that every
+// screened upper end x_hi <= x gives a bin upper bound j_hi < JL[LS], so the
+// pair's lower bound lies above level LS.  -inf when no such x is found.
+__global__ void k_skip_scores(int64_t n, const BinFP *__restrict__ bf,
+                              const int16_t *__restrict__ JL, int LS, float *__restrict__ xs) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const int J = JL[u * kMaxLevels + LS];
+  const BinFP b = bf[u];
+  float x = -INFINITY;
+  if (J >= 1 && b.invd32 > 0.0f && !(b.err > 1e6f)) {
+    // bin_vhi(x) < J - 1 gives floor(v) + 1 <= J - 1
+    const float target = (float)(J - 1);
+    double x0 = (double)b.fmin32 + ((double)target - (double)b.err - 1.0) / (double)b.invd32;
+    float c = __double2float_rd(x0);
+    for (int it = 0; it < 64 && !(bin_vhi(b, c) < target); ++it) c = nextafterf(c, -INFINITY);
+    if (bin_vhi(b, c) < target) x = c;
+  }
+  xs[u] = x;
+}
+
+// Rows of the deep queries, gathered for their own screening launches.
+__global__ void k_gather_qrows(int nd, const int32_t *__restrict__ rows, int kp,
+                               const __nv_bfloat16 *__restrict__ hi,
+                               const __nv_bfloat16 *__restrict__ lo,
+                               const tc::RowBound *__restrict__ rb1,
+                               const tc::RowBound *__restrict__ rb3,
+                               __nv_bfloat16 *__restrict__ ohi, __nv_bfloat16 *__restrict__ olo,
+                               tc::RowBound *__restrict__ orb1, tc::RowBound *__restrict__ orb3,
+                               uint32_t *__restrict__ hist, int nq) {
+  const int i = blockIdx.x;
+  if (i >= nd) return;
+  const int64_t r = rows[i];
+  for (int k = threadIdx.x; k < kp; k += blockDim.x) {
+    ohi[(int64_t)i * kp + k] = hi[r * kp + k];
+    olo[(int64_t)i * kp + k] = lo[r * kp + k];
+  }
+  if (threadIdx.x < 32) {  // the histograms of the skipping pass are incomplete
+    hist[r * 32 + threadIdx.x] = 0;
+    hist[((int64_t)nq + r) * 32 + threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) {
+    orb1[i] = rb1[r];
+    orb3[i] = rb3[r];
+  }
 }
 
 // Refined cap: the upper edge of the fine bucket of level L* where the running
@@ -394,7 +455,8 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             const float *__restrict__ xbmax, const tc::RowBound *__restrict__ rb3,
                             const tc::RowBound *__restrict__ ptile, int pbn, tc::Gacc gacc,
                             float gcan, const double *__restrict__ xg0,
-                            const double *__restrict__ xdx, int G, const uint32_t *__restrict__ XLO,
+                            const double *__restrict__ xdx, int GX, const double *__restrict__ ldx,
+                            int G, const uint32_t *__restrict__ XLO,
                             const uint32_t *__restrict__ XHI, uint32_t mtop,
                             uint32_t *__restrict__ ccount, uint32_t *__restrict__ clb,
                             int32_t *__restrict__ cu_fb, unsigned long long *__restrict__ stat) {
@@ -407,9 +469,9 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   const uint32_t L = xlcnt[u];
   if (L > xlcap[u] || theta < xg0[u]) {
     // bounds from the exact count table at the exact bin of u.q
-    const int j = exact_j(theta, xg0[u], xdx[u], G);
-    ccount[i] = j >= 1 ? XHI[u * G + j - 1] : mtop;
-    clb[i] = j < G ? XLO[u * G + j] : 0u;
+    const int j = exact_j(theta, xg0[u], xdx[u], GX);
+    ccount[i] = j >= 1 ? XHI[u * GX + j - 1] : mtop;
+    clb[i] = j < GX ? XLO[u * GX + j] : 0u;
     cu_fb[i] = (int32_t)u;
     atomicAdd(&stat[0], 1ull);
     return;
@@ -419,7 +481,7 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   const uint2 *row = xlist + xloff[u];
   const uint16_t *co = xcoff + u * (G + 2);
   const double B = (double)xbmax[u];
-  const double g0 = xg0[u], dx = xdx[u];
+  const double g0 = xg0[u], dx = ldx[u];
   // columns c >= chi have v >= x_{c-1} > theta + B: every entry is above theta
   const int chi = exact_j(__dadd_ru(theta, B), g0, dx, G) + 1;
   // columns c < clo have v < x_c <= theta - B: no entry is above theta
@@ -578,11 +640,31 @@ struct Timer {
   }
 };
 
-// Shared front half: passes 1 and the cutoff; returns per-query candidate counts.
+// Shared front half: passes 1 and 3 and the cutoffs; per-query candidate counts.
+// Pairs whose lower bound lies above the skip level are left out by a single
+// compare of the screened score; queries whose cutoff lies above it ("deep")
+// are gathered and screened again in full by launches of their own.
 struct Plan {
   std::vector<int64_t> ncand;
   std::vector<int32_t> lstar;
+  int lskip = 1 << 30;          // skip level (no skipping: every level)
+  DevBuf bxs;
+  float *xs = nullptr;          // per-user skip scores
+  std::vector<int32_t> deep;    // deep queries, ascending
+  DevBuf bdeep, bdhi, bdlo, bdr1, bdr3;
+  int32_t *deep_d = nullptr;
+  TcSide dside;                 // their bf16 rows (views of the buffers above)
 };
+
+// Skip level: the smallest level whose ranks reach m / 128.
+static int skip_level(const rkr_index *idx) {
+  const char *env = getenv("RKR_SKIP_LEVEL");
+  if (env && *env) return atoi(env);
+  int64_t r = idx->m / 128;
+  int L = 0;
+  while (L < 31 && (((int64_t)1 << L) - 1) < r) ++L;
+  return L;
+}
 
 // Grid, bin parameters, level tables and bound tables of one path.
 struct Grid {
@@ -608,6 +690,7 @@ static rkr_status check_flag(int *flag_d, const char *what, cudaStream_t st) {
 static ThetaArgs theta_args(const Grid &g, int qa) {
   ThetaArgs a{};
   a.qa = qa;
+  a.lskip = 1 << 30;
   a.binfp = g.bf;
   a.fmin = g.fmin;
   a.tau = g.tau;
@@ -635,17 +718,73 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
   RKR_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)nq * 64, st));
   RKR_CUDA(cudaMemsetAsync(fine, 0, sizeof(uint32_t) * (size_t)nq * 1024, st));
   RKR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  const int LS = skip_level(idx);
+  const bool skip = LS >= 0 && LS < g.nlev - 1;
+  if (skip) {
+    RKR_TRY(tmp_alloc(plan.bxs, &plan.xs, idx->n, st));
+    k_skip_scores<<<(unsigned)((idx->n + 255) / 256), 256, 0, st>>>(idx->n, g.bf, g.JL, LS,
+                                                                     plan.xs);
+    note_launch();
+    RKR_CUDA(cudaGetLastError());
+    plan.lskip = LS;
+  }
   ThetaArgs a = theta_args(g, 0);
+  a.nq_all = nq;
   a.hist = hist;
+  a.xs = plan.xs;
+  a.lskip = plan.lskip;
   RKR_TRY(tc_theta_pass(1, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
   k_cutoff<<<(nq + 127) / 128, 128, 0, st>>>(nq, hist, hist + (size_t)nq * 32, qc.kq_d, g.nlev,
-                                             lstar_d, below, ncand_d);
+                                             skip ? LS : 31, lstar_d, below, ncand_d);
   note_launch();
   RKR_CUDA(cudaGetLastError());
+  ThetaArgs ad = a;  // deep queries: own rows, every pair screened
+  ad.xs = nullptr;
+  ad.lskip = 1 << 30;
+  if (skip) {
+    std::vector<int32_t> ls(nq);
+    RKR_CUDA(cudaMemcpyAsync(ls.data(), lstar_d, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost,
+                             st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < nq; ++q)
+      if (ls[q] == kDeep) plan.deep.push_back(q);
+  }
+  const int nd = (int)plan.deep.size();
+  if (nd > 0) {
+    const int kp = qc.Qt.kp;
+    TcSide &D = plan.dside;
+    RKR_TRY(tmp_alloc(plan.bdeep, &plan.deep_d, nd, st));
+    RKR_TRY(tmp_alloc(plan.bdhi, &D.hi, (size_t)nd * kp, st));
+    RKR_TRY(tmp_alloc(plan.bdlo, &D.lo, (size_t)nd * kp, st));
+    RKR_TRY(tmp_alloc(plan.bdr1, &D.rb1, nd, st));
+    RKR_TRY(tmp_alloc(plan.bdr3, &D.rb3, nd, st));
+    D.rows = nd;
+    D.d = qc.Qt.d;
+    D.kp = kp;
+    D.owned = false;
+    RKR_CUDA(cudaMemcpyAsync(plan.deep_d, plan.deep.data(), sizeof(int32_t) * nd,
+                             cudaMemcpyHostToDevice, st));
+    k_gather_qrows<<<nd, 128, 0, st>>>(nd, plan.deep_d, kp, qc.Qt.hi, qc.Qt.lo, qc.Qt.rb1,
+                                       qc.Qt.rb3, D.hi, D.lo, D.rb1, D.rb3, hist, nq);
+    note_launch();
+    RKR_CUDA(cudaGetLastError());
+    ad.qmap = plan.deep_d;
+    RKR_TRY(tc_theta_pass(1, idx, idx->Ut, D, ad, kThetaSplit, flag, st));
+    k_cutoff<<<(nq + 127) / 128, 128, 0, st>>>(nq, hist, hist + (size_t)nq * 32, qc.kq_d,
+                                               g.nlev, 31, lstar_d, below, ncand_d);
+    note_launch();
+    RKR_CUDA(cudaGetLastError());
+  }
   a.hist = nullptr;
   a.lstar = lstar_d;
   a.fine = fine;
   RKR_TRY(tc_theta_pass(3, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
+  if (nd > 0) {
+    ad.hist = nullptr;
+    ad.lstar = lstar_d;
+    ad.fine = fine;
+    RKR_TRY(tc_theta_pass(3, idx, idx->Ut, plan.dside, ad, kThetaSplit, flag, st));
+  }
   k_cutoff_fine<<<(nq + 127) / 128, 128, 0, st>>>(nq, fine, below, lstar_d, qc.kq_d, g.scale,
                                                   cap_d);
   note_launch();
@@ -663,9 +802,9 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
 
 // Pass 2: candidates of queries [qa, qb) appended to per-query segments.
 static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, int qa, int qb,
-                                  const Grid &g, const int32_t *lstar_d, const uint32_t *cap_d,
-                                  const int64_t *qoff_d, uint32_t *cursor_d, int32_t *cand_u,
-                                  int32_t *cand_q, cudaStream_t st) {
+                                  const Grid &g, const Plan &plan, const int32_t *lstar_d,
+                                  const uint32_t *cap_d, const int64_t *qoff_d, uint32_t *cursor_d,
+                                  int32_t *cand_u, int32_t *cand_q, cudaStream_t st) {
   TcSide sub = qc.Qt;
   sub.owned = false;
   sub.rows = qb - qa;
@@ -675,17 +814,42 @@ static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, i
   sub.rb3 = qc.Qt.rb3 + qa;
   DevBuf bf;
   int *flag;
-  RKR_TRY(tmp_alloc(bf, &flag, 1, st));
-  RKR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  RKR_TRY(tmp_alloc(bf, &flag, 2, st));
+  RKR_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
   ThetaArgs a = theta_args(g, qa);
+  a.nq_all = qc.Qt.rows;
+  a.ovf = flag + 1;
   a.lstar = lstar_d;
   a.cap = cap_d;
   a.qoff = qoff_d;
   a.qcursor = cursor_d;
   a.cand_u = cand_u;
   a.cand_q = cand_q;
+  a.xs = plan.xs;
+  a.lskip = plan.lskip;
   RKR_TRY(tc_theta_pass(2, idx, idx->Ut, sub, a, kThetaSplit, flag, st));
-  return check_flag(flag, "theta pass 2", st);
+  // deep queries of [qa, qb): a contiguous slice of the gathered rows
+  const int da = (int)(std::lower_bound(plan.deep.begin(), plan.deep.end(), qa) - plan.deep.begin());
+  const int db = (int)(std::lower_bound(plan.deep.begin(), plan.deep.end(), qb) - plan.deep.begin());
+  if (db > da) {
+    TcSide ds = plan.dside;
+    ds.owned = false;
+    ds.rows = db - da;
+    ds.hi = plan.dside.hi + (size_t)da * ds.kp;
+    ds.lo = plan.dside.lo + (size_t)da * ds.kp;
+    ds.rb1 = plan.dside.rb1 + da;
+    ds.rb3 = plan.dside.rb3 + da;
+    ThetaArgs ad = a;
+    ad.qmap = plan.deep_d + da;
+    ad.xs = nullptr;
+    ad.lskip = 1 << 30;
+    RKR_TRY(tc_theta_pass(2, idx, idx->Ut, ds, ad, kThetaSplit, flag, st));
+  }
+  RKR_TRY(check_flag(flag, "theta pass 2", st));
+  int ovf = 0;
+  RKR_CUDA(cudaMemcpy(&ovf, flag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (ovf) return fail(RKR_EINTERNAL, "candidate segment overflow in theta pass 2");
+  return RKR_OK;
 }
 
 // Group queries into chunks whose candidate total stays within budget.
@@ -876,7 +1040,8 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
     RKR_CUDA(cudaMemsetAsync(cu, 0xff, sizeof(int32_t) * std::max<int64_t>(cnt, 1), st));
     Timer t2(st);
-    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, cap_d, qoff_rel, cursor, cu, cq, st));
+    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, plan, lstar_d, cap_d, qoff_rel, cursor, cu, cq,
+                            st));
     ms_theta += t2.stop();
     {
       std::vector<uint32_t> hc(nq);
@@ -918,6 +1083,7 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     stats->fp64_dots = total;
     stats->near_ties = 0;
     stats->wide_queries = wide;
+    stats->deep_queries = (int32_t)plan.deep.size();
     stats->ms_theta = ms_theta;
     stats->ms_resolve = ms_res;
     stats->ms_select = ms_sel;
@@ -977,7 +1143,8 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
     RKR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, st));
     RKR_CUDA(cudaMemsetAsync(cu, 0xff, sizeof(int32_t) * std::max<int64_t>(cnt, 1), st));
     Timer t2(st);
-    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, lstar_d, cap_d, qoff_rel, cursor, cu, cq, st));
+    RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, plan, lstar_d, cap_d, qoff_rel, cursor, cu, cq,
+                            st));
     ms_theta += t2.stop();
     {
       std::vector<uint32_t> hc(nq);
@@ -998,6 +1165,7 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
           cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d,
           idx->xlist, idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
           idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
+          idx->ldx, kListG,
           idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, lstat);
       note_launch();
       RKR_CUDA(cudaGetLastError());
@@ -1049,6 +1217,7 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
     stats->near_ties = (int64_t)tiesv[0];
     stats->recounted = fallback;
     stats->wide_queries = wide;
+    stats->deep_queries = (int32_t)plan.deep.size();
     stats->ms_theta = ms_theta;
     stats->ms_resolve = ms_res;
     stats->ms_select = ms_sel;

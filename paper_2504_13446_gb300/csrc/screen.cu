@@ -182,7 +182,7 @@ struct EpiStore {
     int64_t row = (int64_t)rb * tc::BM + r;
     ts.b = row < nrows ? tc::screen_bound_tc(rowb[row], tileb[ct], gacc, gcan) : 0.0f;
   }
-  __device__ void chunk(char *, int rb, int ct, int r, int col, const float (&v)[32],
+  __device__ void chunk(char *, int rb, int ct, int r, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     int64_t row = (int64_t)rb * tc::BM + r;
     if (row >= nrows) return;

@@ -71,7 +71,7 @@ struct EpiFbA {
     ts.mx = -INFINITY;
     ts.mn = INFINITY;
   }
-  __device__ void chunk(char *, int, int ct, int, int col, const float (&v)[32],
+  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
     if (c0 + 32 <= ncols) {
@@ -141,7 +141,7 @@ struct EpiFbB {
       ts.tmin = -INFINITY;
     }
   }
-  __device__ void chunk(char *, int, int ct, int, int col, const float (&v)[32],
+  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
 #pragma unroll
@@ -323,7 +323,7 @@ struct EpiXT {
   // Scores above the floor are a few per cent and scattered over lanes: each
   // lane parks its 32 scores in a shared tile and walks only its own above-floor
   // ones, so the warp loops max-over-lanes times instead of once per column.
-  __device__ void chunk(char *S, int, int ct, int r, int col, const float (&v)[32],
+  __device__ void chunk(char *S, int, int ct, int r, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
     const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(kGroupThreads)
   uint2 *buf = (uint2 *)lsm;                                  // kListCapMax
   uint32_t *cnt = (uint32_t *)(buf + kListCapMax);            // G + 2
   float *red = (float *)(cnt + G + 2);                        // kGroupThreads / 32
+  uint16_t *cols = (uint16_t *)(red + kGroupThreads / 32);    // kListCapMax
   const int64_t u = blockIdx.x;
   const uint32_t L = lcnt[u];
   uint16_t *co = coff + u * (G + 2);
@@ -414,10 +415,10 @@ __global__ void __launch_bounds__(kGroupThreads)
     int jlo, jhi;
     bin_interval(bf, g0, G, v, v, jlo, jhi);
     int col = jlo == jhi ? jlo : exact_j((double)v, g0, dx, G);
-    e.x |= (uint32_t)col << 24;  // column parked in the high byte for the scatter below
     buf[i] = e;
+    cols[i] = (uint16_t)col;
     atomicAdd(&cnt[col], 1u);
-    bm = fmaxf(bm, tc::screen_bound_tc(ru, tileb[(e.x & 0xffffffu) / bn], gacc, gcan));
+    bm = fmaxf(bm, tc::screen_bound_tc(ru, tileb[e.x / bn], gacc, gcan));
   }
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bm;
@@ -437,10 +438,8 @@ __global__ void __launch_bounds__(kGroupThreads)
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-    uint2 e = buf[i];
-    int col = (int)(e.x >> 24);
-    uint32_t pos = atomicAdd(&cnt[col], 1u);
-    row[pos] = make_uint2(e.x & 0xffffffu, e.y);
+    uint32_t pos = atomicAdd(&cnt[cols[i]], 1u);
+    row[pos] = buf[i];
   }
 }
 
@@ -450,13 +449,14 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   RKR_CUDA(cudaMemcpyAsync(idx->ptile3, tb, sizeof(tc::RowBound) * ntiles,
                            cudaMemcpyDeviceToDevice, st));
   idx->ptile_bn = bn;
-  const int G = idx->xg;
+  const int G = kListG;
+  RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, G, idx->pmax, idx->ldx, idx->lbin, st));
   size_t sm = sizeof(uint2) * kListCapMax + sizeof(uint32_t) * (G + 2) +
-              sizeof(float) * (kGroupThreads / 32);
+              sizeof(float) * (kGroupThreads / 32) + sizeof(uint16_t) * kListCapMax;
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
   k_list_group<<<(unsigned)idx->n, kGroupThreads, sm, st>>>(
-      idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->xbin, idx->xg0, idx->xdx, G,
+      idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->lbin, idx->xg0, idx->ldx, G,
       idx->Ut.rb3, idx->ptile3, bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff,
       idx->xbmax);
   note_launch();
@@ -531,15 +531,18 @@ struct EpiTheta {
     uint4 pju[2], pjl[2];    // prefetched level-table words for the next row block
     BinFP pbf;
     double pfm;
-    tc::RowBound prb;
+    tc::RowBound prb, rb;
+    float xsb, pxs;          // skip pairs with screened score <= xsb
     bool have_pf;
   };
   static constexpr size_t kSmem = sizeof(int16_t) * 2 * 128 * kJS +
-                                  sizeof(int) * (2 * kThetaBN * 32 + 2 * kThetaBN);
+                                  sizeof(int) * (2 * kThetaBN * 32 + 3 * kThetaBN) +
+                                  sizeof(tc::RowBound) * kThetaBN;
   int64_t nrows, ncols;
   int tau;
   int qa;  // global index of query column 0
   const tc::RowBound *rowb, *tileb;
+  const tc::RowBound *colb;     // per-column (query) bound terms, local column index
   tc::Gacc gacc;
   float gcan;
   const BinFP *binfp;
@@ -554,11 +557,17 @@ struct EpiTheta {
   const int64_t *qoff;
   uint32_t *qcursor;
   int32_t *cand_u, *cand_q;
+  int *ovf;                     // PASS 2: set when a query's segment would overflow
+  const float *xs;              // per user: pairs scoring <= xs[u] - b are skipped (or null)
+  const int32_t *qmap;          // global query of each column (null: qa + column)
+  int lskip;                    // passes 2, 3: columns whose L* exceeds this are left out
 
   __device__ int16_t *jtab(char *S) const { return (int16_t *)S; }
   __device__ int *hist(char *S) const { return (int *)(S + sizeof(int16_t) * 2 * 128 * kJS); }
   __device__ int *lst(char *S) const { return hist(S) + 2 * kThetaBN * 32; }
   __device__ uint32_t *caps(char *S) const { return (uint32_t *)(lst(S) + kThetaBN); }
+  __device__ int *qglob(char *S) const { return (int *)(caps(S) + kThetaBN); }
+  __device__ tc::RowBound *qbnd(char *S) const { return (tc::RowBound *)(qglob(S) + kThetaBN); }
 
   // Thread et fetches words [16 et, 16 et + 16) of the 2 x 128 x 32 int16 tables
   // (JU block then JL block) of row block rb: two uint4 of each table.
@@ -577,11 +586,19 @@ struct EpiTheta {
       ts.pbf = binfp[u];
       ts.pfm = fmin[u];
       ts.prb = rowb[u];
+      ts.pxs = xs ? xs[u] : -INFINITY;
     }
   }
   __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &ts) const {
     ts.rb1 = u.rb1;
     ts.have_pf = false;
+    int *QG = qglob(S);
+    tc::RowBound *QB = qbnd(S);
+    for (int i = et; i < kThetaBN; i += 256) {
+      int64_t q = (int64_t)u.ct0 * kThetaBN + i;
+      QG[i] = q < ncols ? (qmap ? qmap[q] : qa + (int)q) : 0;
+      QB[i] = q < ncols ? colb[q] : tc::RowBound{0, 0, 0, 0, 0};
+    }
     if (PASS == 1) {
       int *H = hist(S);
       for (int i = et; i < 2 * kThetaBN * 32; i += 256) H[i] = 0;
@@ -590,8 +607,9 @@ struct EpiTheta {
       uint32_t *C = caps(S);
       for (int i = et; i < kThetaBN; i += 256) {
         int64_t q = (int64_t)u.ct0 * kThetaBN + i;
-        L[i] = q < ncols ? lstar[qa + q] : 0;
-        if (PASS == 2) C[i] = q < ncols ? cap[qa + q] : 0u;
+        const int g = q < ncols ? (qmap ? qmap[q] : qa + (int)q) : 0;
+        L[i] = q < ncols ? lstar[g] : 0;
+        if (PASS == 2) C[i] = q < ncols ? cap[g] : 0u;
       }
     }
   }
@@ -618,8 +636,10 @@ struct EpiTheta {
     ts.u = (int64_t)rb * tc::BM + r;
     if (ts.u < nrows) {
       ts.b = tc::screen_bound_tc(ts.prb, tileb[ct], gacc, gcan);
+      ts.rb = ts.prb;
       ts.bf = ts.pbf;
       ts.fm = ts.pfm;
+      ts.xsb = __fsub_rd(ts.pxs, ts.b);
     }
     tc::epi_sync();
     // prefetch the next row block of this unit while this tile is processed
@@ -629,56 +649,105 @@ struct EpiTheta {
       fetch_row(rb + 1, r, ts);
     }
   }
-  __device__ void chunk(char *S, int, int ct, int r, int col, const float (&v)[32],
+  // The chunk's 32 columns are first tested with one compare each; the warp then
+  // walks the union of its lanes' surviving columns four at a time, reloading
+  // those accumulator columns together so that the four bin and level
+  // computations are independent.
+  __device__ void chunk(char *S, int, int ct, int r, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
-    if (ts.u >= nrows) return;
-    const int16_t *ju = jtab(S) + r * kJS, *jl = jtab(S) + 128 * kJS + r * kJS;
-    int *H = hist(S);
-    const int *Ls = lst(S);
     const int64_t c0 = (int64_t)ct * kThetaBN + col;
+    uint32_t pm = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (c0 + j < ncols) {
-        int jlo, jhi;
-        bin_interval(ts.bf, ts.fm, tau, __fsub_rd(v[j], ts.b), __fadd_ru(v[j], ts.b), jlo, jhi);
-        if (PASS == 1) {
-          int lu = 0, ll = 0;
+    for (int j = 0; j < 32; ++j)  // v <= xsb: lower bound above the skip level (NaN kept)
+      pm |= (v[j] <= ts.xsb ? 0u : 1u) << j;
+    const int64_t left = ncols - c0;
+    if (left < 32) pm &= left <= 0 ? 0u : (1u << left) - 1u;
+    if (ts.u >= nrows) pm = 0;
+    uint32_t any = __reduce_or_sync(0xffffffffu, pm);
+    while (any) {
+      int jj[4];
 #pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            if (ju[lu + step - 1] > jlo) lu += step;
-            if (jl[ll + step - 1] > jhi) ll += step;
+      for (int i = 0; i < 4; ++i) {
+        jj[i] = any ? __ffs(any) - 1 : -1;
+        any &= any - 1u;
+      }
+      float x[4];
+      tc::tmem_ld1x4(tm + (uint32_t)jj[0], tm + (uint32_t)(jj[1] < 0 ? jj[0] : jj[1]),
+                     tm + (uint32_t)(jj[2] < 0 ? jj[0] : jj[2]),
+                     tm + (uint32_t)(jj[3] < 0 ? jj[0] : jj[3]), x);
+      bool on[4];
+      int cl[4], jlo[4], jhi[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        on[i] = jj[i] >= 0 && ((pm >> (jj[i] & 31)) & 1u);
+        cl[i] = col + (jj[i] < 0 ? jj[0] : jj[i]);
+        // the pair's own bound (the tile's maximum only decides the skip), so that a
+        // pair's bin interval does not depend on which queries share its tile
+        const float b = tc::screen_bound_tc(ts.rb, qbnd(S)[cl[i]], gacc, gcan);
+        bin_interval(ts.bf, ts.fm, tau, __fsub_rd(x[i], b), __fadd_ru(x[i], b), jlo[i], jhi[i]);
+      }
+      const int16_t *ju = jtab(S) + r * kJS, *jl = jtab(S) + 128 * kJS + r * kJS;
+      if (PASS == 1) {
+        int lu[4], ll[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { lu[i] = 0; ll[i] = 0; }
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (ju[lu[i] + step - 1] > jlo[i]) lu[i] += step;
+            if (jl[ll[i] + step - 1] > jhi[i]) ll[i] += step;
           }
-          // warp-aggregated: all lanes are on the same query column
-          const unsigned act = __activemask();
-          const unsigned mu = __match_any_sync(act, lu), ml = __match_any_sync(act, ll);
-          const int lane = threadIdx.x & 31;
-          if ((mu & ((1u << lane) - 1)) == 0) atomicAdd(&H[(col + j) * 32 + lu], __popc(mu));
-          if ((ml & ((1u << lane) - 1)) == 0)
-            atomicAdd(&H[kThetaBN * 32 + (col + j) * 32 + ll], __popc(ml));
-        } else if (PASS == 3) {
-          const int Lq = Ls[col + j];
-          // level of the upper bound is L* exactly: above every smaller level's start
-          if (jlo >= ju[Lq] && (Lq == 0 || jlo < ju[Lq - 1])) refine((int)(c0 + j), jlo, Lq, ts.u);
-        } else if (jhi >= jl[Ls[col + j]]) {
-          emit((int)(c0 + j), jhi, caps(S)[col + j], ts.u);
         }
+        int *H = hist(S);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (on[i]) {
+            atomicAdd(&H[cl[i] * 32 + lu[i]], 1);
+            atomicAdd(&H[kThetaBN * 32 + cl[i] * 32 + ll[i]], 1);
+          }
+      } else if (PASS == 3) {
+        // level of the upper bound is L* exactly: above every smaller level's start
+        uint32_t val[4];
+        int Lq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          Lq[i] = lst(S)[cl[i]];
+          on[i] = on[i] && Lq[i] <= lskip && jlo[i] >= ju[Lq[i]] &&
+                  (Lq[i] == 0 || jlo[i] < ju[Lq[i] - 1]);
+          val[i] = on[i] ? (jlo[i] >= 1 ? thi[ts.u * tau + jlo[i] - 1] : top) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (on[i]) refine(qglob(S)[cl[i]], val[i], Lq[i]);
+      } else {
+        uint32_t lb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int Lq = lst(S)[cl[i]];
+          on[i] = on[i] && Lq <= lskip && jhi[i] >= jl[Lq];
+          lb[i] = on[i] ? (jhi[i] < tau ? tlo[ts.u * tau + jhi[i]] : 0u) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (on[i] && lb[i] <= caps(S)[cl[i]]) emit(qglob(S)[cl[i]], ts.u);
       }
     }
   }
-  __device__ __noinline__ void refine(int c, int jlo, int Lq, int64_t u) const {
-    uint64_t v = jlo >= 1 ? thi[u * tau + jlo - 1] : top;
+  __device__ void refine(int q, uint64_t v, int Lq) const {
     uint64_t base, width;
     level_range(Lq, scale, base, width);
     uint64_t bkt = v >= base ? (v - base) / width : 0;
     if (bkt >= kFine) bkt = kFine - 1;
-    atomicAdd(&fine[(int64_t)(qa + c) * kFine + bkt], 1u);
+    atomicAdd(&fine[(int64_t)q * kFine + bkt], 1u);
   }
-  __device__ __noinline__ void emit(int c, int jhi, uint32_t capq, int64_t u) const {
-    uint32_t lb = jhi < tau ? tlo[u * tau + jhi] : 0u;
-    if (lb > capq) return;
-    int q = qa + c;
+  __device__ void emit(int q, int64_t u) const {
     uint32_t pos = atomicAdd(&qcursor[q], 1u);
     int64_t at = qoff[q] + pos;
+    if (at >= qoff[q + 1]) {  // more than the pass-1 count: never written out of the segment
+      atomicExch(ovf, 1);
+      return;
+    }
     cand_u[at] = (int32_t)u;
     cand_q[at] = q;
   }
@@ -686,12 +755,14 @@ struct EpiTheta {
   __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &) const {
     if (PASS != 1) return;
     const int *H = hist(S);
+    const int *QG = qglob(S);
     for (int i = et; i < kThetaBN * 32; i += 256) {
       int64_t q = (int64_t)u.ct0 * kThetaBN + (i >> 5);
       if (q >= ncols) continue;
+      const int64_t g = QG[i >> 5];
       int a = H[i], b = H[kThetaBN * 32 + i];
-      if (a) atomicAdd(&hist_up[(qa + q) * 32 + (i & 31)], (uint32_t)a);
-      if (b) atomicAdd(&hist_lo[(qa + q) * 32 + (i & 31)], (uint32_t)b);
+      if (a) atomicAdd(&hist_up[g * 32 + (i & 31)], (uint32_t)a);
+      if (b) atomicAdd(&hist_lo[g * 32 + (i & 31)], (uint32_t)b);
     }
   }
 };
@@ -708,10 +779,12 @@ static rkr_status theta_launch(const rkr_index *idx, const TcSide &Ut, const TcS
   EpiTheta<PASS> e;
   e.nrows = n; e.ncols = nq; e.tau = a.tau; e.qa = a.qa;
   e.rowb = split ? Ut.rb3 : Ut.rb1; e.tileb = tb;
+  e.colb = split ? Qt.rb3 : Qt.rb1;
   e.gacc = tc_gacc(Ut.kp, split); e.gcan = tc_gcan(idx->d);
   e.binfp = a.binfp; e.fmin = a.fmin; e.JU = a.JU; e.JL = a.JL;
   e.thi = a.thi; e.tlo = a.tlo; e.top = a.top; e.scale = a.scale;
-  e.hist_up = a.hist; e.hist_lo = a.hist ? a.hist + (size_t)(a.qa + nq) * 32 : nullptr;
+  e.hist_up = a.hist; e.hist_lo = a.hist ? a.hist + (size_t)a.nq_all * 32 : nullptr;
+  e.xs = a.xs; e.qmap = a.qmap; e.lskip = a.lskip; e.ovf = a.ovf;
   e.lstar = a.lstar; e.cap = a.cap; e.fine = a.fine;
   e.qoff = a.qoff; e.qcursor = a.qcursor; e.cand_u = a.cand_u; e.cand_q = a.cand_q;
   static_assert(tc::screen_smem_bytes<kThetaBN, 4, EpiTheta<1>>() <= 232448, "theta smem");
@@ -779,7 +852,7 @@ struct EpiRC {
   __device__ void tile_begin(char *, int, int ct, int, int, Thread &ts) const {
     ts.b = ts.sg < nseg ? tc::screen_bound_tc(rowb[ts.sg], tileb[ct], gacc, gcan) : 0.0f;
   }
-  __device__ void chunk(char *, int, int ct, int, int col, const float (&v)[32],
+  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
 #pragma unroll

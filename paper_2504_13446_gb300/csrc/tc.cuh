@@ -156,6 +156,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// One accumulator column of the warp's 32 lanes (warp-convergent).
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  return __uint_as_float(r);
+}
+
+// Four accumulator columns of the warp's 32 lanes, loaded together (warp-convergent).
+__device__ __forceinline__ void tmem_ld1x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                           float (&x)[4]) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r0) : "r"(a0));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r1) : "r"(a1));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r2) : "r"(a2));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r3) : "r"(a3));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  x[0] = __uint_as_float(r0);
+  x[1] = __uint_as_float(r1);
+  x[2] = __uint_as_float(r2);
+  x[3] = __uint_as_float(r3);
+}
+
 // Operands of one screen: row maps (A) and column maps (B) for the hi and lo
 // parts; ncol_rows = rows of B.  ksteps = K / 16 per segment (K padded to 16).
 struct Operands {

@@ -11,7 +11,7 @@
 //   static constexpr size_t kSmem;                    bytes of epilogue scratch
 //   void unit_begin(char *S, const Unit &u, int et, Thread &)   et = 0..255
 //   void tile_begin(char *S, int rb, int ct, int r, int h, Thread &)
-//   void chunk(char *S, int rb, int ct, int r, int col, const float (&v)[32], Thread &)
+//   void chunk(char *S, int rb, int ct, int r, int col, uint32_t tm, const float (&v)[32], Thread &)
 //   void tile_end(char *S, int rb, int ct, int r, int h, Thread &)
 //   void unit_end(char *S, const Unit &u, int et, Thread &)
 // r is the accumulator row (0..127), h the column half, col the first of the
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int col = half * (BN / 2) + cc * 32;
             float v[32];
             tmem_ld32(trow + col, v);
-            epi.chunk(escratch, rb, ct, r, col, v, ts);
+            epi.chunk(escratch, rb, ct, r, col, trow + (uint32_t)col, v, ts);
           }
           epi.tile_end(escratch, rb, ct, r, half, ts);
           tc_fence_before();

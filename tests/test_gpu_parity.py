@@ -202,3 +202,19 @@ def test_invalid_arguments_return_status():
         rkr.Index(U, P, tau=8, omega=31, s=5)
     # the index stays usable after errors
     check_exact(U, P, Q, 4, gpu)
+
+
+@pytest.mark.parametrize("level", ["0", "3", "40"])
+def test_skip_level_leaves_results_unchanged(monkeypatch, level):
+    """Pairs whose lower rank bound lies above the skip level are left out by one compare;
+    queries whose cutoff lies above it are screened again in full.  Level 0 makes almost
+    every query deep, 40 turns skipping off: the answers stay those of the oracle."""
+    monkeypatch.setenv("RKR_SKIP_LEVEL", level)
+    w = synth.make_workload("approx", n=12000, m=3000, nq=40)
+    ora, gpu = build_pair(w.U, w.P, w.tau, w.omega, w.s, seed=w.seed)
+    out = check_approx(w.U, w.Q, w.k, w.c, ora, gpu)
+    st = check_exact(w.U, w.P, w.Q, w.k, gpu)
+    if level == "40":
+        assert out["stats"].deep_queries == 0 and st.deep_queries == 0
+    if level == "0":
+        assert out["stats"].deep_queries > 0 and st.deep_queries > 0
