@@ -114,6 +114,20 @@ struct ThetaArgs {
 };
 rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
                          const ThetaArgs &a, int split, int *err, cudaStream_t st);
+// Entries (user, query, screened score) recorded by the skim screen: region r
+// (one per CTA of the launch) holds cnt[r] entries from r * rcap on; a count
+// above rcap means the region overflowed and dropped the excess.
+struct SkimList {
+  int32_t *u, *q;
+  float *x;
+  uint32_t *cnt;
+  int64_t rcap;
+  int regions;
+};
+// CTAs (= list regions) of the skim launch for n users and nq queries.
+int skim_regions(int64_t n, int64_t nq);
+rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, const float *xs,
+                   const SkimList &list, int *err, cudaStream_t st);
 // refined[0] = queued undecided items, refined[1] = of those, canonical FP64 evaluations.
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,

@@ -640,6 +640,99 @@ struct Timer {
   }
 };
 
+// ------------------------------------------------------------ skim list
+
+// Entry e of region blockIdx.y (thread index within the region's count).
+__device__ __forceinline__ bool list_entry(const SkimList &L, int64_t &e) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const uint32_t c = L.cnt[blockIdx.y];
+  if (i >= (int64_t)(c < L.rcap ? c : L.rcap)) return false;
+  e = (int64_t)blockIdx.y * L.rcap + i;
+  return true;
+}
+
+// Pass 1 on the list: bin interval of each entry's u.q from its screened score
+// and the pair's own bound, the levels of its upper and lower rank bounds
+// (histograms per query), and both kept for the later passes.
+__global__ void k_list_levels(SkimList L, const tc::RowBound *__restrict__ urb,
+                              const tc::RowBound *__restrict__ qrb, tc::Gacc gacc, float gcan,
+                              const BinFP *__restrict__ bf, const double *__restrict__ fmin,
+                              int tau, const int16_t *__restrict__ JU,
+                              const int16_t *__restrict__ JL, uint32_t *__restrict__ hist_up,
+                              uint32_t *__restrict__ hist_lo, uint32_t *__restrict__ jj,
+                              uint32_t *__restrict__ lv) {
+  int64_t e;
+  if (!list_entry(L, e)) return;
+  const int64_t u = L.u[e];
+  const int q = L.q[e];
+  const float x = L.x[e];
+  const float b = tc::screen_bound_tc(urb[u], qrb[q], gacc, gcan);
+  int jlo, jhi;
+  bin_interval(bf[u], fmin[u], tau, __fsub_rd(x, b), __fadd_ru(x, b), jlo, jhi);
+  const int16_t *ju = JU + u * kMaxLevels, *jl = JL + u * kMaxLevels;
+  int lu = 0, ll = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    if (ju[lu + step - 1] > jlo) lu += step;
+    if (jl[ll + step - 1] > jhi) ll += step;
+  }
+  atomicAdd(&hist_up[(int64_t)q * 32 + lu], 1u);
+  atomicAdd(&hist_lo[(int64_t)q * 32 + ll], 1u);
+  jj[e] = (uint32_t)jlo | ((uint32_t)jhi << 16);
+  lv[e] = (uint32_t)lu | ((uint32_t)ll << 8);
+}
+
+// Pass 3 on the list: entries whose upper bound lies exactly at their query's
+// level L* add that bound to the query's fine histogram of the level.
+__global__ void k_list_fine(SkimList L, const uint32_t *__restrict__ jj,
+                            const uint32_t *__restrict__ lv, const int32_t *__restrict__ lstar,
+                            int lskip, const uint32_t *__restrict__ thi, int tau, uint32_t top,
+                            uint32_t scale, uint32_t *__restrict__ fine) {
+  int64_t e;
+  if (!list_entry(L, e)) return;
+  const int q = L.q[e];
+  const int Lq = lstar[q];
+  if (Lq > lskip || (int)(lv[e] & 0xff) != Lq) return;
+  const int64_t u = L.u[e];
+  const int jlo = (int)(jj[e] & 0xffff);
+  const uint64_t v = jlo >= 1 ? thi[u * tau + jlo - 1] : top;
+  const uint64_t hi = level_bound(Lq, scale);
+  const uint64_t base = Lq == 0 ? 0 : level_bound(Lq - 1, scale) + 1;
+  const uint64_t width = (hi - base + 1024) / 1024;
+  uint64_t bkt = v >= base ? (v - base) / width : 0;
+  if (bkt >= 1024) bkt = 1023;
+  atomicAdd(&fine[(int64_t)q * 1024 + bkt], 1u);
+}
+
+// Pass 2 on the list: entries of queries [qa, qb) whose lower bound may reach
+// the query's refined cap, appended to the query's candidate segment.
+__global__ void k_list_emit(SkimList L, const uint32_t *__restrict__ jj,
+                            const uint32_t *__restrict__ lv, int qa, int qb,
+                            const int32_t *__restrict__ lstar, int lskip,
+                            const uint32_t *__restrict__ cap, const uint32_t *__restrict__ tlo,
+                            int tau, const int64_t *__restrict__ qoff,
+                            uint32_t *__restrict__ qcursor, int32_t *__restrict__ cand_u,
+                            int32_t *__restrict__ cand_q, int *__restrict__ ovf) {
+  int64_t e;
+  if (!list_entry(L, e)) return;
+  const int q = L.q[e];
+  if (q < qa || q >= qb) return;
+  const int Lq = lstar[q];
+  if (Lq > lskip || (int)((lv[e] >> 8) & 0xff) > Lq) return;
+  const int64_t u = L.u[e];
+  const int jhi = (int)(jj[e] >> 16);
+  const uint32_t lb = jhi < tau ? tlo[u * tau + jhi] : 0u;
+  if (lb > cap[q]) return;
+  const uint32_t pos = atomicAdd(&qcursor[q], 1u);
+  const int64_t at = qoff[q] + pos;
+  if (at >= qoff[q + 1]) {
+    atomicExch(ovf, 1);
+    return;
+  }
+  cand_u[at] = (int32_t)u;
+  cand_q[at] = q;
+}
+
 // Shared front half: passes 1 and 3 and the cutoffs; per-query candidate counts.
 // Pairs whose lower bound lies above the skip level are left out by a single
 // compare of the screened score; queries whose cutoff lies above it ("deep")
@@ -654,7 +747,66 @@ struct Plan {
   DevBuf bdeep, bdhi, bdlo, bdr1, bdr3;
   int32_t *deep_d = nullptr;
   TcSide dside;                 // their bf16 rows (views of the buffers above)
+  bool listed = false;          // passes 1-3 of the other queries run on the skim list
+  SkimList list{};
+  uint32_t maxcnt = 0;          // largest region count (launch width of list kernels)
+  DevBuf blu, blq, blx, blc, bjj, blv;
+  uint32_t *jj = nullptr, *lv = nullptr;
 };
+
+static rkr_status check_flag(int *flag_d, const char *what, cudaStream_t st);
+
+// Capacity of the skim list: entries of every region together.
+static int64_t skim_capacity(int64_t n, int64_t nq) {
+  int64_t want = n * nq / 16;
+  return std::max<int64_t>((int64_t)1 << 20, std::min<int64_t>(want, (int64_t)1 << 29));
+}
+
+static dim3 list_grid(const Plan &plan) {
+  return dim3((unsigned)std::max<uint32_t>(1, (plan.maxcnt + 255) / 256),
+              (unsigned)plan.list.regions);
+}
+
+// Skim screen of all queries into plan.list; plan.listed stays false when the
+// list cannot be allocated or a region overflowed (the passes then screen again).
+static rkr_status skim_queries(const rkr_index *idx, const QueryCommon &qc, int nq, Plan &plan,
+                               int *flag, cudaStream_t st) {
+  const int regions = skim_regions(idx->n, nq);
+  const int64_t cap = skim_capacity(idx->n, nq);
+  SkimList &L = plan.list;
+  L.regions = regions;
+  L.rcap = cap / regions;
+  const size_t ent = (size_t)L.rcap * regions;
+  auto try_alloc = [&](DevBuf &b, auto **p, size_t count) -> bool {
+    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(**p), st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    b.p = (void *)*p;
+    b.st = st;
+    return true;
+  };
+  if (!try_alloc(plan.blu, &L.u, ent) || !try_alloc(plan.blq, &L.q, ent) ||
+      !try_alloc(plan.blx, &L.x, ent) || !try_alloc(plan.blc, &L.cnt, regions) ||
+      !try_alloc(plan.bjj, &plan.jj, ent) || !try_alloc(plan.blv, &plan.lv, ent))
+    return RKR_OK;
+  RKR_CUDA(cudaMemsetAsync(L.cnt, 0, sizeof(uint32_t) * regions, st));
+  RKR_TRY(tc_skim(idx, idx->Ut, qc.Qt, plan.xs, L, flag, st));
+  std::vector<uint32_t> cnt(regions);
+  RKR_CUDA(cudaMemcpyAsync(cnt.data(), L.cnt, sizeof(uint32_t) * regions, cudaMemcpyDeviceToHost,
+                           st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  RKR_TRY(check_flag(flag, "skim screen", st));
+  uint32_t mx = 0;
+  for (uint32_t c : cnt) {
+    if ((int64_t)c > L.rcap) return RKR_OK;  // overflow: not listed
+    mx = std::max(mx, c);
+  }
+  plan.maxcnt = mx;
+  plan.listed = true;
+  return RKR_OK;
+}
 
 // Skip level: the smallest level whose ranks reach m / 128.
 static int skip_level(const rkr_index *idx) {
@@ -733,7 +885,18 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
   a.hist = hist;
   a.xs = plan.xs;
   a.lskip = plan.lskip;
-  RKR_TRY(tc_theta_pass(1, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
+  if (skip) RKR_TRY(skim_queries(idx, qc, nq, plan, flag, st));
+  if (plan.listed) {
+    if (plan.maxcnt > 0) {
+      k_list_levels<<<list_grid(plan), 256, 0, st>>>(
+          plan.list, idx->Ut.rb3, qc.Qt.rb3, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), g.bf,
+          g.fmin, g.tau, g.JU, g.JL, hist, hist + (size_t)nq * 32, plan.jj, plan.lv);
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+    }
+  } else {
+    RKR_TRY(tc_theta_pass(1, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
+  }
   k_cutoff<<<(nq + 127) / 128, 128, 0, st>>>(nq, hist, hist + (size_t)nq * 32, qc.kq_d, g.nlev,
                                              skip ? LS : 31, lstar_d, below, ncand_d);
   note_launch();
@@ -778,7 +941,17 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
   a.hist = nullptr;
   a.lstar = lstar_d;
   a.fine = fine;
-  RKR_TRY(tc_theta_pass(3, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
+  if (plan.listed) {
+    if (plan.maxcnt > 0) {
+      k_list_fine<<<list_grid(plan), 256, 0, st>>>(plan.list, plan.jj, plan.lv, lstar_d,
+                                                   plan.lskip, g.thi, g.tau, g.top, g.scale,
+                                                   fine);
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+    }
+  } else {
+    RKR_TRY(tc_theta_pass(3, idx, idx->Ut, qc.Qt, a, kThetaSplit, flag, st));
+  }
   if (nd > 0) {
     ad.hist = nullptr;
     ad.lstar = lstar_d;
@@ -827,7 +1000,17 @@ static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, i
   a.cand_q = cand_q;
   a.xs = plan.xs;
   a.lskip = plan.lskip;
-  RKR_TRY(tc_theta_pass(2, idx, idx->Ut, sub, a, kThetaSplit, flag, st));
+  if (plan.listed) {
+    if (plan.maxcnt > 0) {
+      k_list_emit<<<list_grid(plan), 256, 0, st>>>(plan.list, plan.jj, plan.lv, qa, qb, lstar_d,
+                                                   plan.lskip, cap_d, g.tlo, g.tau, qoff_d,
+                                                   cursor_d, cand_u, cand_q, flag + 1);
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+    }
+  } else {
+    RKR_TRY(tc_theta_pass(2, idx, idx->Ut, sub, a, kThetaSplit, flag, st));
+  }
   // deep queries of [qa, qb): a contiguous slice of the gathered rows
   const int da = (int)(std::lower_bound(plan.deep.begin(), plan.deep.end(), qa) - plan.deep.begin());
   const int db = (int)(std::lower_bound(plan.deep.begin(), plan.deep.end(), qb) - plan.deep.begin());

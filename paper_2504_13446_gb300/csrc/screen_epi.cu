@@ -800,6 +800,141 @@ rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const
   return theta_launch<3>(idx, Ut, Qt, a, split, err, st);
 }
 
+// ================================================================== skim
+
+// One screening pass that only records: every pair whose screened score passes
+// the skip test (its lower rank bound may lie at or below the skip level) is
+// appended as (user, query, screened score) to the list region of the CTA that
+// screened it.  Levels, cutoffs, refinement and emission then run on the list
+// with plain CUDA-core kernels, one thread per entry, instead of inside the
+// warp-synchronous epilogue.
+constexpr int kSkimBN = 256;
+
+struct EpiSkim {
+  struct Thread {
+    float b, xsb, pxs;
+    int64_t u;
+    int rb1;
+    tc::RowBound prb;
+    bool have_pf;
+  };
+  static constexpr size_t kSmem = 0;
+  int64_t nrows, ncols;
+  const tc::RowBound *rowb, *tileb;
+  tc::Gacc gacc;
+  float gcan;
+  const float *xs;
+  SkimList L;
+
+  __device__ void fetch_row(int rb, int r, Thread &ts) const {
+    const int64_t u = (int64_t)rb * tc::BM + r;
+    if (u < nrows) {
+      ts.prb = rowb[u];
+      ts.pxs = xs[u];
+    }
+  }
+  __device__ void unit_begin(char *, const tc::Unit &u, int, Thread &ts) const {
+    ts.rb1 = u.rb1;
+    ts.have_pf = false;
+  }
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    if (!ts.have_pf) fetch_row(rb, r, ts);
+    ts.u = (int64_t)rb * tc::BM + r;
+    if (ts.u < nrows) {
+      ts.b = tc::screen_bound_tc(ts.prb, tileb[ct], gacc, gcan);
+      ts.xsb = __fsub_rd(ts.pxs, ts.b);
+    }
+    ts.have_pf = rb + 1 < ts.rb1;
+    if (ts.have_pf) fetch_row(rb + 1, r, ts);
+  }
+  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
+                        Thread &ts) const {
+    const int64_t c0 = (int64_t)ct * kSkimBN + col;
+    uint32_t pm = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)  // v <= xsb: lower bound above the skip level (NaN kept)
+      pm |= (v[j] <= ts.xsb ? 0u : 1u) << j;
+    const int64_t left = ncols - c0;
+    if (left < 32) pm &= left <= 0 ? 0u : (1u << left) - 1u;
+    if (ts.u >= nrows) pm = 0;
+    // warp-aggregated reservation of this warp's entries in the CTA's region
+    const int lane = threadIdx.x & 31;
+    const int n = __popc(pm);
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&L.cnt[blockIdx.x], (uint32_t)total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    int64_t pos = (int64_t)base + incl - n;
+    const int64_t rbase = (int64_t)blockIdx.x * L.rcap;
+    uint32_t any = __reduce_or_sync(0xffffffffu, pm);
+    while (any) {
+      int jj[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        jj[i] = any ? __ffs(any) - 1 : -1;
+        any &= any - 1u;
+      }
+      float x[4];
+      tc::tmem_ld1x4(tm + (uint32_t)jj[0], tm + (uint32_t)(jj[1] < 0 ? jj[0] : jj[1]),
+                     tm + (uint32_t)(jj[2] < 0 ? jj[0] : jj[2]),
+                     tm + (uint32_t)(jj[3] < 0 ? jj[0] : jj[3]), x);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (jj[i] >= 0 && ((pm >> (jj[i] & 31)) & 1u)) {
+          if (pos < L.rcap) {  // entries past the region are dropped; cnt records them
+            L.u[rbase + pos] = (int32_t)ts.u;
+            L.q[rbase + pos] = (int32_t)(c0 + jj[i]);
+            L.x[rbase + pos] = x[i];
+          }
+          ++pos;
+        }
+      }
+    }
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+};
+
+int skim_regions(int64_t n, int64_t nq) {
+  const int nct = (int)((nq + kSkimBN - 1) / kSkimBN);
+  const int nrb = (int)((n + tc::BM - 1) / tc::BM);
+  const int parts = std::max(1, std::min((2 * sm_count() + nct - 1) / nct, nrb));
+  return std::max(1, std::min(nct * parts, sm_count()));
+}
+
+rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, const float *xs,
+                   const SkimList &list, int *err, cudaStream_t st) {
+  const int64_t n = idx->n, nq = Qt.rows;
+  tc::RowBound *tb = nullptr;
+  RKR_TRY(tc_tile_bounds(Qt, kSkimBN, 1, &tb, st));
+  const int nct = (int)((nq + kSkimBN - 1) / kSkimBN);
+  tc::Schedule sch = col_schedule(n, nq, kSkimBN, (2 * sm_count() + nct - 1) / nct);
+  if (std::min(sch.nunits, sm_count()) != list.regions) {
+    cudaFreeAsync(tb, st);
+    return fail(RKR_EINTERNAL, "skim list regions do not match the launch");
+  }
+  EpiSkim e;
+  e.nrows = n;
+  e.ncols = nq;
+  e.rowb = Ut.rb3;
+  e.tileb = tb;
+  e.gacc = tc_gacc(Ut.kp, 1);
+  e.gcan = tc_gcan(idx->d);
+  e.xs = xs;
+  e.L = list;
+  static_assert(tc::screen_smem_bytes<kSkimBN, 4, EpiSkim>() <= 232448, "skim smem");
+  rkr_status s = launch_screen<kSkimBN, 4>(Ut, Qt, 1, sch, e, err, st);
+  cudaFreeAsync(tb, st);
+  return s;
+}
+
 // =============================================================== recount
 
 struct EpiRC {
