@@ -156,6 +156,33 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
 rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t mx, int32_t d,
                              int32_t split, float *out_s, float *out_b, void *stream);
 
+/*
+ * rkr_screen_scores_static: rkr_screen_scores without any device allocation.
+ * The paper has no counterpart: this is a deployment variant of the validation
+ * screen above, with the same outputs bit for bit.  It exists for callers that
+ * must not call the CUDA allocator (cudaMalloc/cudaFree can synchronize the
+ * device and can fail under memory pressure; a serving loop that owns its
+ * device memory budget needs a call whose footprint is fixed at load time).
+ *   All scratch (BF16 rows of U and X, their bound terms, per-tile bound maxima
+ *   and the kernel's error word) lives in one file-scope device array of
+ *   16 MiB per device.  Scratch needed for n rows of U and mx rows of X at
+ *   kp = d rounded up to 16 is about 4 kp (n + mx) + 40 (n + mx) + 20 mx / 256
+ *   bytes (each piece rounded up to 256 bytes); larger problems are rejected
+ *   with RKR_EINVAL and a message giving both figures.
+ *   U, X, out_s, out_b must be device (or managed) memory; host pointers are
+ *   rejected with RKR_EINVAL.  Outputs as in rkr_screen_scores; the caller owns
+ *   every buffer.
+ *   The first call on a device looks up the array's address
+ *   (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ *   first call before any stream capture.  Every call on a device uses the same
+ *   array: calls that overlap in time (several host threads or streams) race
+ *   on it and must be serialized by the caller.  The call synchronizes
+ *   `stream` before it returns.
+ */
+rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, int64_t mx,
+                                    int32_t d, int32_t split, float *out_s, float *out_b,
+                                    void *stream);
+
 /* What rkr_index_export copies out. */
 typedef enum {
   RKR_EXPORT_PERM = 1,      /* int32[m]: original item index of each norm-sorted position */

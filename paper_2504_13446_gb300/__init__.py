@@ -24,7 +24,7 @@ import numpy as np
 from . import buildlib
 
 __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
-           "rkr_query_approx", "EXPORTS"]
+           "rkr_query_approx", "rkr_screen_scores", "rkr_screen_scores_static", "EXPORTS"]
 
 _lock = threading.Lock()
 _lib = None
@@ -90,6 +90,8 @@ def load() -> ctypes.CDLL:
         lib.rkr_kernel_launches.argtypes = []
         lib.rkr_screen_scores.restype = I32
         lib.rkr_screen_scores.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
+        lib.rkr_screen_scores_static.restype = I32
+        lib.rkr_screen_scores_static.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
         lib.rkr_last_error.restype = ctypes.c_char_p
         lib.rkr_version.restype = ctypes.c_char_p
         _lib = lib
@@ -222,6 +224,23 @@ def rkr_screen_scores(U, X, *, split: bool = False, stream=None):
     _check(lib.rkr_screen_scores(pu, n, px, mx, d, int(split), s.ctypes.data_as(ctypes.c_void_p),
                                  b.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
     return s, b
+
+
+def rkr_screen_scores_static(U, X, out_s, out_b, *, split: bool = False, stream=None):
+    """rkr_screen_scores into caller-owned device buffers, with no device allocation.
+
+    U (n x d), X (mx x d), out_s and out_b (n x mx, float32) must be CUDA tensors."""
+    lib = load()
+    n, d = _shape(U)
+    mx, _ = _shape(X)
+    for t in (U, X, out_s, out_b):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()
+                and str(t.dtype) == "torch.float32"):
+            raise RKRError(1, "rkr_screen_scores_static takes contiguous float32 CUDA tensors")
+    if tuple(out_s.shape) != (n, mx) or tuple(out_b.shape) != (n, mx):
+        raise RKRError(1, "output shape must be (n, mx)")
+    _check(lib.rkr_screen_scores_static(U.data_ptr(), n, X.data_ptr(), mx, d, int(split),
+                                        out_s.data_ptr(), out_b.data_ptr(), _stream(stream)))
 
 
 @dataclass

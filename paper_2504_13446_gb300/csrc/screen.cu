@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "index.cuh"
 #include "tcops.cuh"
@@ -221,3 +222,138 @@ rkr_status tc_scores(const TcSide &A, const TcSide &B, int split, float *out, fl
 }
 
 }  // namespace rkr
+
+// ------------------------------------------------- allocation-free screen
+//
+// rkr_screen_scores_static: the validation screen of rkr_screen_scores with
+// every piece of device scratch (BF16 hi/lo rows of both sides, their bound
+// terms, the per-tile bound maxima and the kernel's error word) carved out of
+// one file-scope device array of fixed size.  It is for callers that must not
+// call the CUDA allocator: cudaMalloc and cudaFree can synchronize the device
+// and can fail under memory pressure, so a serving loop that owns its memory
+// budget (for instance through a framework's caching allocator) needs a call
+// whose device footprint is fixed when the library is loaded.  Inputs and
+// outputs must already be device memory.  The array is shared by every call
+// on a device: calls that overlap in time (two host threads, or two streams)
+// race on it, so callers serialize them.
+
+namespace rkr {
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB per device
+constexpr int kStaticDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void *g_static_ptr[kStaticDevices] = {nullptr};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Scratch bytes for n + mx rows of width kp and ntiles column tiles.
+size_t static_bytes(int64_t n, int64_t mx, int kp, int64_t ntiles) {
+  return 2 * round256((size_t)n * kp * 2) + 2 * round256((size_t)mx * kp * 2) +
+         2 * round256(sizeof(tc::RowBound) * (size_t)n) +
+         2 * round256(sizeof(tc::RowBound) * (size_t)mx) +
+         round256(sizeof(tc::RowBound) * (size_t)ntiles) + 256;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+}  // namespace rkr
+
+extern "C" rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X,
+                                               int64_t mx, int32_t d, int32_t split, float *out_s,
+                                               float *out_b, void *stream) {
+  using namespace rkr;
+  set_error("%s", "");
+  if (!U || !X || !out_s || !out_b) return fail(RKR_EINVAL, "null argument");
+  if (n < 1 || mx < 1 || d < 1 || d > kMaxD) return fail(RKR_EINVAL, "bad sizes");
+  if (n * mx > ((int64_t)1 << 31)) return fail(RKR_EINVAL, "n * mx too large");
+  constexpr int BN = 256;
+  const int kp = (d + 15) / 16 * 16;
+  const int64_t ntiles = (mx + BN - 1) / BN;
+  const size_t need = static_bytes(n, mx, kp, ntiles);
+  if (need > kStaticScratchBytes)
+    return fail(RKR_EINVAL,
+                "rkr_screen_scores_static needs %zu bytes of scratch for n = %lld, mx = %lld, "
+                "d = %d; the static limit is %zu bytes",
+                need, (long long)n, (long long)mx, (int)d, kStaticScratchBytes);
+  if (!is_device_ptr(U) || !is_device_ptr(X) || !is_device_ptr(out_s) || !is_device_ptr(out_b))
+    return fail(RKR_EINVAL, "rkr_screen_scores_static takes device pointers only");
+  int dev = 0;
+  RKR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticDevices) return fail(RKR_EUNSUPPORTED, "device index %d", dev);
+  unsigned char *base = nullptr;
+  {
+    // set-up, once per device with that device current: the address of the array
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+      g_static_ptr[dev] = p;
+    }
+    base = (unsigned char *)g_static_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    unsigned char *p = base + off;
+    off += round256(bytes);
+    return p;
+  };
+  TcSide A, B;
+  A.rows = n; A.d = d; A.kp = kp; A.owned = false;
+  B.rows = mx; B.d = d; B.kp = kp; B.owned = false;
+  A.hi = (__nv_bfloat16 *)carve((size_t)n * kp * 2);
+  A.lo = (__nv_bfloat16 *)carve((size_t)n * kp * 2);
+  B.hi = (__nv_bfloat16 *)carve((size_t)mx * kp * 2);
+  B.lo = (__nv_bfloat16 *)carve((size_t)mx * kp * 2);
+  A.rb1 = (tc::RowBound *)carve(sizeof(tc::RowBound) * n);
+  A.rb3 = (tc::RowBound *)carve(sizeof(tc::RowBound) * n);
+  B.rb1 = (tc::RowBound *)carve(sizeof(tc::RowBound) * mx);
+  B.rb3 = (tc::RowBound *)carve(sizeof(tc::RowBound) * mx);
+  tc::RowBound *tb = (tc::RowBound *)carve(sizeof(tc::RowBound) * ntiles);
+  int *err = (int *)carve(sizeof(int));
+  // the error word is the only scratch that must start at zero; everything else
+  // is written in full before it is read
+  RKR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  k_stage_bf16<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(U, n, d, kp, A.hi, A.lo, A.rb1,
+                                                            A.rb3);
+  note_launch();
+  k_stage_bf16<<<(unsigned)((mx + 127) / 128), 128, 0, st>>>(X, mx, d, kp, B.hi, B.lo, B.rb1,
+                                                             B.rb3);
+  note_launch();
+  k_tile_bounds<<<(unsigned)((ntiles + 127) / 128), 128, 0, st>>>(split ? B.rb3 : B.rb1, mx, BN,
+                                                                  (int)ntiles, tb);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  EpiStore e;
+  e.nrows = n;
+  e.ncols = mx;
+  e.bn = BN;
+  e.rowb = split ? A.rb3 : A.rb1;
+  e.tileb = tb;
+  e.gacc = tc_gacc(kp, split ? 1 : 0);
+  e.gcan = tc_gcan(d);
+  e.out = out_s;
+  e.outb = out_b;
+  const rkr_status ls =
+      launch_screen<BN, 4>(A, B, split ? 1 : 0, row_schedule(n, mx, BN), e, err, st);
+  RKR_TRY(ls);
+  int herr = 0;
+  RKR_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (herr) return fail(RKR_ETIMEOUT, "screen kernel wait timed out (code %d)", herr);
+  return RKR_OK;
+}
