@@ -183,6 +183,21 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
                                     int32_t d, int32_t split, float *out_s, float *out_b,
                                     void *stream);
 
+/*
+ * rkr_profile_start / rkr_profile_stop: per-kernel device time of the library's
+ * launches between the two calls (not part of the paper).  While on, the main
+ * kernels are bracketed by CUDA events recorded on the stream they are launched
+ * on.  rkr_profile_stop synchronizes those events and writes one text line per
+ * kernel, "name launches total_ms work", into report (len bytes including the
+ * terminating NUL; RKR_EINVAL if it does not fit).  work is the summed
+ * algorithmic work of the launches: 2 * rows * cols * K' * products flops for a
+ * tensor-core screen (K' = d rounded up to 16, products = 3 for the split
+ * product), 0 where none is stated.  Not thread-safe against concurrent queries
+ * on other threads beyond what the shared event list allows.
+ */
+rkr_status rkr_profile_start(void);
+rkr_status rkr_profile_stop(char *report, int64_t len);
+
 /* What rkr_index_export copies out. */
 typedef enum {
   RKR_EXPORT_PERM = 1,      /* int32[m]: original item index of each norm-sorted position */

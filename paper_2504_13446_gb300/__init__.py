@@ -24,7 +24,8 @@ import numpy as np
 from . import buildlib
 
 __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
-           "rkr_query_approx", "rkr_screen_scores", "rkr_screen_scores_static", "EXPORTS"]
+           "rkr_query_approx", "rkr_screen_scores", "rkr_screen_scores_static",
+           "rkr_profile_start", "rkr_profile_stop", "EXPORTS"]
 
 _lock = threading.Lock()
 _lib = None
@@ -90,12 +91,32 @@ def load() -> ctypes.CDLL:
         lib.rkr_kernel_launches.argtypes = []
         lib.rkr_screen_scores.restype = I32
         lib.rkr_screen_scores.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
+        lib.rkr_profile_start.restype = I32
+        lib.rkr_profile_start.argtypes = []
+        lib.rkr_profile_stop.restype = I32
+        lib.rkr_profile_stop.argtypes = [ctypes.c_char_p, I64]
         lib.rkr_screen_scores_static.restype = I32
         lib.rkr_screen_scores_static.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
         lib.rkr_last_error.restype = ctypes.c_char_p
         lib.rkr_version.restype = ctypes.c_char_p
         _lib = lib
         return lib
+
+
+def rkr_profile_start() -> None:
+    """Start per-kernel device-time accounting (CUDA events on the launching stream)."""
+    _check(load().rkr_profile_start())
+
+
+def rkr_profile_stop() -> dict:
+    """Stop accounting; {kernel: (launches, total_ms, algorithmic work)}."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().rkr_profile_stop(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms, work = line.split()
+        out[name] = (int(n), float(ms), float(work))
+    return out
 
 
 def kernel_launches() -> int:

@@ -8,7 +8,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "index.cuh"
@@ -20,6 +22,44 @@ static thread_local char g_err[512] = "";
 static std::atomic<uint64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct ProfRec {
+  const char *name;
+  cudaEvent_t a, b;
+  double work;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+
+int prof_begin(const char *name, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return -1;
+  ProfRec r{name, nullptr, nullptr, 0.0};
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  cudaEventRecord(r.a, st);
+  g_prof.push_back(r);
+  return (int)g_prof.size() - 1;
+}
+
+void prof_end(int slot, cudaStream_t st, double work) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot >= (int)g_prof.size()) return;
+  cudaEventRecord(g_prof[slot].b, st);
+  g_prof[slot].work = work;
+}
+
+static void prof_clear() {
+  for (auto &r : g_prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+}
 
 void set_error(const char *fmt, ...) {
   va_list ap;
@@ -434,6 +474,58 @@ void rkr_index_free(rkr_index *idx) {
   cudaDeviceSynchronize();
   index_release(idx);
   delete idx;
+}
+
+rkr_status rkr_profile_start(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_clear();
+  g_prof_on = true;
+  return RKR_OK;
+}
+
+rkr_status rkr_profile_stop(char *report, int64_t len) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = false;
+  struct Agg {
+    std::string name;
+    int64_t launches = 0;
+    double ms = 0.0, work = 0.0;
+  };
+  std::vector<Agg> agg;
+  rkr_status st = RKR_OK;
+  for (auto &r : g_prof) {
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "rkr_profile_stop");
+      continue;
+    }
+    Agg *a = nullptr;
+    for (auto &x : agg)
+      if (x.name == r.name) a = &x;
+    if (!a) {
+      agg.push_back(Agg{r.name});
+      a = &agg.back();
+    }
+    a->launches += 1;
+    a->ms += ms;
+    a->work += r.work;
+  }
+  prof_clear();
+  if (report && len > 0) {
+    std::string out;
+    char line[256];
+    for (auto &a : agg) {
+      snprintf(line, sizeof(line), "%s %lld %.6f %.6e\n", a.name.c_str(), (long long)a.launches,
+               a.ms, a.work);
+      out += line;
+    }
+    if ((int64_t)out.size() + 1 > len) return fail(RKR_EINVAL, "report needs %zu bytes",
+                                                   out.size() + 1);
+    memcpy(report, out.c_str(), out.size() + 1);
+  }
+  return st;
 }
 
 }  // extern "C"

@@ -37,7 +37,12 @@ rkr_status row_norms(const float *X, int64_t rows, int d, double *nrm64, float *
                      cudaStream_t st) {
   if (rows <= 0) return RKR_OK;
   int bs = 128;
-  k_row_norms<<<(unsigned)((rows + bs - 1) / bs), bs, 0, st>>>(X, rows, d, nrm64, nrm32); note_launch();
+  {
+    const int prof_slot = prof_begin("k_row_norms", st);
+    k_row_norms<<<(unsigned)((rows + bs - 1) / bs), bs, 0, st>>>(X, rows, d, nrm64, nrm32);
+    prof_end(prof_slot, st, 0.0);
+    note_launch();
+  }
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
 }
@@ -111,7 +116,12 @@ rkr_status sort_pairs(uint64_t *key, int32_t *val, int64_t N_pow2, cudaStream_t 
   unsigned grid = (unsigned)((N_pow2 + bs - 1) / bs);
   for (int64_t k = 2; k <= N_pow2; k <<= 1)
     for (int64_t j = k >> 1; j > 0; j >>= 1) {
-      k_bitonic<<<grid, bs, 0, st>>>(key, val, N_pow2, j, k); note_launch();
+      {
+        const int prof_slot = prof_begin("k_bitonic", st);
+        k_bitonic<<<grid, bs, 0, st>>>(key, val, N_pow2, j, k);
+        prof_end(prof_slot, st, 0.0);
+        note_launch();
+      }
     }
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
@@ -486,8 +496,13 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_CUDA(cudaMemcpyAsync(idx->perm, vals, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
   RKR_TRY(dalloc(&idx->Ps, (size_t)m * d));
   RKR_TRY(dalloc(&idx->pnrm_s, m));
-  k_gather_sorted<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(P_dev, idx->perm, pn32, m, d,
-                                                               idx->Ps, idx->pnrm_s); note_launch();
+  {
+    const int prof_slot = prof_begin("k_gather_sorted", st);
+    k_gather_sorted<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(P_dev, idx->perm, pn32, m, d,
+                                                                 idx->Ps, idx->pnrm_s);
+    prof_end(prof_slot, st, 0.0);
+    note_launch();
+  }
   RKR_CUDA(cudaGetLastError());
   RKR_TRY(max_float(idx->pnrm_s, m, &idx->pmax, st));
   RKR_TRY(tc_stage(idx->U, n, d, idx->Ut, st));
@@ -587,8 +602,13 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     // candidate overflow on the tensor-core path: exact scan on the CUDA cores
     size_t sm = sizeof(float) * ((size_t)d * 128 + (size_t)d * 32);
     RKR_CUDA(cudaFuncSetAttribute(k_fbounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_fbounds<<<(unsigned)((n + 127) / 128), 128, sm, st>>>(idx->U, n, idx->Ps, idx->pnrm_s, m, d,
-                                                            idx->unrm, idx->fmin, idx->fmax); note_launch();
+    {
+      const int prof_slot = prof_begin("k_fbounds", st);
+      k_fbounds<<<(unsigned)((n + 127) / 128), 128, sm, st>>>(idx->U, n, idx->Ps, idx->pnrm_s, m, d,
+                                                              idx->unrm, idx->fmin, idx->fmax);
+      prof_end(prof_slot, st, 0.0);
+      note_launch();
+    }
   } else if (idx->fbounds == 1) {
     double pmax64 = 0.0;
     // max FP64 norm: the first item of the sorted order
@@ -615,9 +635,14 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
     if (sm > 227 * 1024) return fail(RKR_EINVAL, "tau too large for the table kernel");
     RKR_CUDA(cudaFuncSetAttribute(k_rank_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
-    k_rank_table<<<(unsigned)((n + kTableWarps - 1) / kTableWarps), kTableWarps * 32, sm, st>>>(
-        idx->U, n, d, idx->unrm, idx->S, idx->snrm, idx->sw, idx->nsamp, idx->fmin, idx->delta,
-        idx->binfp, tau, idx->N); note_launch();
+    {
+      const int prof_slot = prof_begin("k_rank_table", st);
+      k_rank_table<<<(unsigned)((n + kTableWarps - 1) / kTableWarps), kTableWarps * 32, sm, st>>>(
+          idx->U, n, d, idx->unrm, idx->S, idx->snrm, idx->sw, idx->nsamp, idx->fmin, idx->delta,
+          idx->binfp, tau, idx->N);
+      prof_end(prof_slot, st, 0.0);
+      note_launch();
+    }
     RKR_CUDA(cudaGetLastError());
   }
   RKR_CUDA(cudaEventRecord(ev[4], st));

@@ -28,6 +28,20 @@ rkr_status cuda_fail(cudaError_t e, const char *what);
 // Count of kernels this library has launched (reported by rkr_kernel_launches).
 void note_launch();
 
+// Per-kernel device-time accounting, on while rkr_profile_start is in effect:
+// CUDA events recorded on the launching stream around a launch.  `work` is the
+// launch's algorithmic work (flops of a screen; 0 when not stated).
+int prof_begin(const char *name, cudaStream_t st);
+void prof_end(int slot, cudaStream_t st, double work);
+struct ProfScope {
+  int slot;
+  cudaStream_t st;
+  double work;
+  ProfScope(const char *name, cudaStream_t s, double w = 0.0)
+      : slot(prof_begin(name, s)), st(s), work(w) {}
+  ~ProfScope() { prof_end(slot, st, work); }
+};
+
 #define RKR_CUDA(expr)                                            \
   do {                                                            \
     cudaError_t _e = (expr);                                      \

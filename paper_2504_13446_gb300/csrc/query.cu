@@ -888,9 +888,13 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
   if (skip) RKR_TRY(skim_queries(idx, qc, nq, plan, flag, st));
   if (plan.listed) {
     if (plan.maxcnt > 0) {
-      k_list_levels<<<list_grid(plan), 256, 0, st>>>(
-          plan.list, idx->Ut.rb3, qc.Qt.rb3, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), g.bf,
-          g.fmin, g.tau, g.JU, g.JL, hist, hist + (size_t)nq * 32, plan.jj, plan.lv);
+      {
+        const int prof_slot = prof_begin("k_list_levels", st);
+        k_list_levels<<<list_grid(plan), 256, 0, st>>>(
+            plan.list, idx->Ut.rb3, qc.Qt.rb3, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), g.bf,
+            g.fmin, g.tau, g.JU, g.JL, hist, hist + (size_t)nq * 32, plan.jj, plan.lv);
+        prof_end(prof_slot, st, 0.0);
+      }
       note_launch();
       RKR_CUDA(cudaGetLastError());
     }
@@ -927,8 +931,12 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
     D.owned = false;
     RKR_CUDA(cudaMemcpyAsync(plan.deep_d, plan.deep.data(), sizeof(int32_t) * nd,
                              cudaMemcpyHostToDevice, st));
-    k_gather_qrows<<<nd, 128, 0, st>>>(nd, plan.deep_d, kp, qc.Qt.hi, qc.Qt.lo, qc.Qt.rb1,
-                                       qc.Qt.rb3, D.hi, D.lo, D.rb1, D.rb3, hist, nq);
+    {
+      const int prof_slot = prof_begin("k_gather_qrows", st);
+      k_gather_qrows<<<nd, 128, 0, st>>>(nd, plan.deep_d, kp, qc.Qt.hi, qc.Qt.lo, qc.Qt.rb1,
+                                         qc.Qt.rb3, D.hi, D.lo, D.rb1, D.rb3, hist, nq);
+      prof_end(prof_slot, st, 0.0);
+    }
     note_launch();
     RKR_CUDA(cudaGetLastError());
     ad.qmap = plan.deep_d;
@@ -943,9 +951,13 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
   a.fine = fine;
   if (plan.listed) {
     if (plan.maxcnt > 0) {
-      k_list_fine<<<list_grid(plan), 256, 0, st>>>(plan.list, plan.jj, plan.lv, lstar_d,
-                                                   plan.lskip, g.thi, g.tau, g.top, g.scale,
-                                                   fine);
+      {
+        const int prof_slot = prof_begin("k_list_fine", st);
+        k_list_fine<<<list_grid(plan), 256, 0, st>>>(plan.list, plan.jj, plan.lv, lstar_d,
+                                                     plan.lskip, g.thi, g.tau, g.top, g.scale,
+                                                     fine);
+        prof_end(prof_slot, st, 0.0);
+      }
       note_launch();
       RKR_CUDA(cudaGetLastError());
     }
@@ -1002,9 +1014,13 @@ static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, i
   a.lskip = plan.lskip;
   if (plan.listed) {
     if (plan.maxcnt > 0) {
-      k_list_emit<<<list_grid(plan), 256, 0, st>>>(plan.list, plan.jj, plan.lv, qa, qb, lstar_d,
-                                                   plan.lskip, cap_d, g.tlo, g.tau, qoff_d,
-                                                   cursor_d, cand_u, cand_q, flag + 1);
+      {
+        const int prof_slot = prof_begin("k_list_emit", st);
+        k_list_emit<<<list_grid(plan), 256, 0, st>>>(plan.list, plan.jj, plan.lv, qa, qb, lstar_d,
+                                                     plan.lskip, cap_d, g.tlo, g.tau, qoff_d,
+                                                     cursor_d, cand_u, cand_q, flag + 1);
+        prof_end(prof_slot, st, 0.0);
+      }
       note_launch();
       RKR_CUDA(cudaGetLastError());
     }
@@ -1092,8 +1108,12 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   RKR_TRY(tmp_alloc(bcu, &cu, total, st));
   RKR_TRY(tmp_alloc(bcq, &cq, total, st));
   RKR_TRY(tmp_alloc(bci, &ci, total, st));
-  k_compact<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(total, cu_all, cq_all, cur, cu, cq,
-                                                               ci);
+  {
+    const int prof_slot = prof_begin("k_compact", st);
+    k_compact<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(total, cu_all, cq_all, cur, cu, cq,
+                                                                 ci);
+    prof_end(prof_slot, st, 0.0);
+  }
   note_launch();
   unsigned long long hc = 0;
   RKR_CUDA(cudaMemcpyAsync(&hc, cur, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -1119,13 +1139,21 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   RKR_TRY(tmp_alloc(b7, &hist, 2 * cnt, st));
   RKR_TRY(tmp_alloc(b8, &ths, cnt, st));
   RKR_TRY(tmp_alloc(b9, &nseg_d, 1, st));
-  k_cand_theta<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(cnt, cu, cq, idx->U, Qd, idx->d,
-                                                                th, khi, klo, val, Np2);
+  {
+    const int prof_slot = prof_begin("k_cand_theta", st);
+    k_cand_theta<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(cnt, cu, cq, idx->U, Qd, idx->d,
+                                                                  th, khi, klo, val, Np2);
+    prof_end(prof_slot, st, 0.0);
+  }
   note_launch();
   RKR_CUDA(cudaGetLastError());
   for (int64_t k = 2; k <= Np2; k <<= 1)
     for (int64_t j = k >> 1; j > 0; j >>= 1) {
-      k_bitonic128<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(khi, klo, val, Np2, j, k);
+      {
+        const int prof_slot = prof_begin("k_bitonic128", st);
+        k_bitonic128<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(khi, klo, val, Np2, j, k);
+        prof_end(prof_slot, st, 0.0);
+      }
       note_launch();
     }
   RKR_CUDA(cudaGetLastError());
@@ -1146,8 +1174,12 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   int64_t refined[2] = {0, 0};
   RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, ths, hist,
                      st, refined));
-  k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
-                                                                 hist);
+  {
+    const int prof_slot = prof_begin("k_seg_suffix", st);
+    k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
+                                                                   hist);
+    prof_end(prof_slot, st, 0.0);
+  }
   note_launch();
   RKR_CUDA(cudaGetLastError());
   if (ties_d) {  // accumulate over chunks: [0] undecided items, [1] canonical evaluations
@@ -1159,8 +1191,12 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     RKR_CUDA(cudaMemcpyAsync(ties_d, r, sizeof(r), cudaMemcpyHostToDevice, st));
     RKR_CUDA(cudaStreamSynchronize(st));
   }
-  k_scatter_counts<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
-                                                                   val, hist, ccount);
+  {
+    const int prof_slot = prof_begin("k_scatter_counts", st);
+    k_scatter_counts<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
+                                                                     val, hist, ccount);
+    prof_end(prof_slot, st, 0.0);
+  }
   note_launch();
   k_scatter_back<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, ci, ccount, ccount_all);
   note_launch();
@@ -1235,9 +1271,14 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     }
     Timer t3(st);
     if (cnt > 0) {
-      k_resolve_approx<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
-          cnt, cu, cq, idx->U, qc.Qd, idx->d, idx->fmin, idx->delta, idx->N, idx->tau,
-          (uint32_t)(idx->m * idx->s), th, cj, nlo, nup); note_launch();
+      {
+        const int prof_slot = prof_begin("k_resolve_approx", st);
+        k_resolve_approx<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
+            cnt, cu, cq, idx->U, qc.Qd, idx->d, idx->fmin, idx->delta, idx->N, idx->tau,
+            (uint32_t)(idx->m * idx->s), th, cj, nlo, nup);
+        prof_end(prof_slot, st, 0.0);
+        note_launch();
+      }
       RKR_CUDA(cudaGetLastError());
     }
     ms_res += t3.stop();
@@ -1246,10 +1287,14 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     size_t sm = sizeof(SortEnt) * kMaxK;
     RKR_CUDA(cudaFuncSetAttribute(k_select_approx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
-    k_select_approx<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cursor, C, qc.kq_d, c,
-                                                      (uint32_t)idx->s, idx->tau, idx->fmin,
-                                                      idx->delta, qc.out_off_d, users_d, nlo_d,
-                                                      nup_d, est_d, case_d, nc_d, sel_err);
+    {
+      const int prof_slot = prof_begin("k_select_approx", st);
+      k_select_approx<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cursor, C, qc.kq_d, c,
+                                                        (uint32_t)idx->s, idx->tau, idx->fmin,
+                                                        idx->delta, qc.out_off_d, users_d, nlo_d,
+                                                        nup_d, est_d, case_d, nc_d, sel_err);
+      prof_end(prof_slot, st, 0.0);
+    }
     note_launch();
     RKR_CUDA(cudaGetLastError());
     ms_sel += t4.stop();
@@ -1344,15 +1389,23 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
       RKR_TRY(tmp_alloc(bfb, &cu_fb, cnt, st));
       RKR_TRY(tmp_alloc(blb, &clb, cnt, st));
       RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
-      k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
-          cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d,
-          idx->xlist, idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
-          idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
-          idx->ldx, kListG,
-          idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, lstat);
+      {
+        const int prof_slot = prof_begin("k_list_rank", st);
+        k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
+            cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d,
+            idx->xlist, idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
+            idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
+            idx->ldx, kListG,
+            idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, lstat);
+        prof_end(prof_slot, st, 0.0);
+      }
       note_launch();
       RKR_CUDA(cudaGetLastError());
-      k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
+      {
+        const int prof_slot = prof_begin("k_recount_filter", st);
+        k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
+        prof_end(prof_slot, st, 0.0);
+      }
       note_launch();
       RKR_CUDA(cudaGetLastError());
       {  // candidates that still need the recount
@@ -1379,8 +1432,12 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
     size_t sm = sizeof(SortEnt) * kMaxK;
     RKR_CUDA(cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
-    k_select_exact<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cursor, cu, ccount, qc.kq_d,
-                                                     qc.out_off_d, users_d, ranks_d, sel_err);
+    {
+      const int prof_slot = prof_begin("k_select_exact", st);
+      k_select_exact<<<qb - qa, kSelThreads, sm, st>>>(qa, qoff_rel, cursor, cu, ccount, qc.kq_d,
+                                                       qc.out_off_d, users_d, ranks_d, sel_err);
+      prof_end(prof_slot, st, 0.0);
+    }
     note_launch();
     RKR_CUDA(cudaGetLastError());
     ms_sel += t4.stop();

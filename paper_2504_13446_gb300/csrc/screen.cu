@@ -168,6 +168,7 @@ rkr_status make_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t rows, i
 
 // Writes every screened score and its bound (validation of the screen).
 struct EpiStore {
+  static const char *name() { return "k_screen<EpiStore>"; }
   struct Thread {
     float b;
   };

@@ -50,6 +50,7 @@ struct PairQueue {
 // ============================================================== f-bounds
 
 struct EpiFbA {
+  static const char *name() { return "k_screen<EpiFbA>"; }
   struct Thread {
     float mx, mn, b;
     float mxlo, mnhi;
@@ -116,6 +117,7 @@ struct EpiFbA {
 };
 
 struct EpiFbB {
+  static const char *name() { return "k_screen<EpiFbB>"; }
   struct Thread {
     float tmax, tmin;
     int64_t row;
@@ -229,8 +231,12 @@ rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   if (s == RKR_OK) {
     k_fb_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, kmax, kmin);
     note_launch();
-    k_fb_resolve<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
-                                                  kmax, kmin);
+    {
+      const int prof_slot = prof_begin("k_fb_resolve", st);
+      k_fb_resolve<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
+                                                    kmax, kmin);
+      prof_end(prof_slot, st, 0.0);
+    }
     note_launch();
     k_fb_finish<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, kmax, kmin, fmin, fmax,
                                                              flags + 2);
@@ -272,6 +278,7 @@ __global__ void k_xgrid(int64_t n, const double *__restrict__ fmin,
 // Histograms are 16-bit pairs packed in 32-bit words; a row whose tail holds
 // more than 65535 items gets the trivial bounds 0 and m instead.
 struct EpiXT {
+  static const char *name() { return "k_screen<EpiXT>"; }
   struct Thread {
     float skip, b;
     BinFP bf;
@@ -455,10 +462,14 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
               sizeof(float) * (kGroupThreads / 32) + sizeof(uint16_t) * kListCapMax;
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
-  k_list_group<<<(unsigned)idx->n, kGroupThreads, sm, st>>>(
-      idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->lbin, idx->xg0, idx->ldx, G,
-      idx->Ut.rb3, idx->ptile3, bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff,
-      idx->xbmax);
+  {
+    const int prof_slot = prof_begin("k_list_group", st);
+    k_list_group<<<(unsigned)idx->n, kGroupThreads, sm, st>>>(
+        idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->lbin, idx->xg0, idx->ldx, G,
+        idx->Ut.rb3, idx->ptile3, bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff,
+        idx->xbmax);
+    prof_end(prof_slot, st, 0.0);
+  }
   note_launch();
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
@@ -521,6 +532,9 @@ __device__ __forceinline__ void level_range(int L, uint32_t scale, uint64_t &bas
 
 template <int PASS>
 struct EpiTheta {
+  static const char *name() {
+    return PASS == 1 ? "k_screen<EpiTheta1>" : PASS == 2 ? "k_screen<EpiTheta2>" : "k_screen<EpiTheta3>";
+  }
   static constexpr int kJS = 34;  // int16 row stride of the level tables (conflict-free)
   struct Thread {
     float b;
@@ -811,6 +825,7 @@ rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const
 constexpr int kSkimBN = 256;
 
 struct EpiSkim {
+  static const char *name() { return "k_screen<EpiSkim>"; }
   struct Thread {
     float b, xsb, pxs;
     int64_t u;
@@ -938,6 +953,7 @@ rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, con
 // =============================================================== recount
 
 struct EpiRC {
+  static const char *name() { return "k_screen<EpiRC>"; }
   static constexpr int kR = 8;   // thresholds kept in registers
   struct Thread {
     float b, tminf, tmaxf;
@@ -1120,9 +1136,13 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   RKR_CUDA(cudaMallocAsync((void **)&A.rb1, sizeof(tc::RowBound) * nseg, st));
   RKR_CUDA(cudaMallocAsync((void **)&A.rb3, sizeof(tc::RowBound) * nseg, st));
   dim3 blk(32, 8);
-  k_gather_side<<<(unsigned)((nseg + 7) / 8), blk, 0, st>>>(Ut.hi, Ut.lo, Ut.rb1, Ut.rb3, A.kp,
-                                                             seg_user, nseg, A.hi, A.lo, A.rb1,
-                                                             A.rb3);
+  {
+    const int prof_slot = prof_begin("k_gather_side", st);
+    k_gather_side<<<(unsigned)((nseg + 7) / 8), blk, 0, st>>>(Ut.hi, Ut.lo, Ut.rb1, Ut.rb3, A.kp,
+                                                               seg_user, nseg, A.hi, A.lo, A.rb1,
+                                                               A.rb3);
+    prof_end(prof_slot, st, 0.0);
+  }
   note_launch();
   tc::RowBound *tb = nullptr;
   RKR_TRY(tc_tile_bounds(Pt, BN, 1, &tb, st));
@@ -1146,9 +1166,13 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
   rkr_status s = launch_screen<BN, 4>(A, Pt, 1, row_schedule(nseg, m, BN), e, flags, st);
   if (s == RKR_OK) {
-    k_rc_refine<<<8 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, seg_start, seg_len,
-                                                seg_user, ths, idx->U, idx->unrm, idx->Ps,
-                                                idx->pnrm_s, idx->d, hist, nfp64);
+    {
+      const int prof_slot = prof_begin("k_rc_refine", st);
+      k_rc_refine<<<8 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, seg_start, seg_len,
+                                                  seg_user, ths, idx->U, idx->unrm, idx->Ps,
+                                                  idx->pnrm_s, idx->d, hist, nfp64);
+      prof_end(prof_slot, st, 0.0);
+    }
     note_launch();
   }
   int hf[2] = {0, 0};

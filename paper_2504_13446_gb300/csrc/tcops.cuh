@@ -53,6 +53,8 @@ rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::
   RKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = std::min(sch.nunits, sm_count());
   if (grid < 1) return RKR_OK;
+  ProfScope prof(Epi::name(), st,
+                 2.0 * (double)A.rows * (double)B.rows * (double)A.kp * (split ? 3.0 : 1.0));
   kern<<<grid, tc::kThreads, smem, st>>>(mAh, mAl, mBh, mBl, op, sch, epi, err_dev);
   note_launch();
   RKR_CUDA(cudaGetLastError());
