@@ -129,10 +129,11 @@ int skim_regions(int64_t n, int64_t nq);
 rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, const float *xs,
                    const SkimList &list, int *err, cudaStream_t st);
 // refined[0] = queued undecided items, refined[1] = of those, canonical FP64 evaluations.
+// With hist_hi (bounds mode) nothing is queued: undecided items give count intervals.
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
                       const int32_t *seg_user, const double *ths, uint32_t *hist,
-                      cudaStream_t st, int64_t *refined);
+                      uint32_t *hist_hi, cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
 constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)
 constexpr int kListG = 1024;        // columns of the list grid (finer than the count grid)

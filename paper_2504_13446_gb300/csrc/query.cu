@@ -1094,10 +1094,12 @@ __global__ void k_scatter_back(int64_t n, const int32_t *__restrict__ oi,
 // Exact ranks of the candidates whose cu entry is valid (the others keep their
 // ccount): compact them, canonical u.q, sort by (user, u.q), one grouped
 // tensor-core pass over P per user.  ccount[i] = #{p : s(u_i, p) > u_i.q_i}.
+// With clb_all (bounds mode) items the screen cannot place are not resolved:
+// ccount gets an upper and clb a lower bound of the count instead.
 static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int64_t total,
                                      const int32_t *cu_all, const int32_t *cq_all,
-                                     uint32_t *ccount_all, unsigned long long *ties_d,
-                                     cudaStream_t st) {
+                                     uint32_t *ccount_all, uint32_t *clb_all,
+                                     unsigned long long *ties_d, cudaStream_t st) {
   const int bs = 256;
   DevBuf bcu, bcq, bci, bcc, bcur;
   int32_t *cu, *cq, *ci;
@@ -1172,8 +1174,14 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   note_launch();
   RKR_CUDA(cudaGetLastError());
   int64_t refined[2] = {0, 0};
+  DevBuf bhh;
+  uint32_t *hist_hi = nullptr;
+  if (clb_all) {
+    RKR_TRY(tmp_alloc(bhh, &hist_hi, 2 * cnt, st));
+    RKR_CUDA(cudaMemsetAsync(hist_hi, 0, sizeof(uint32_t) * 2 * cnt, st));
+  }
   RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, ths, hist,
-                     st, refined));
+                     hist_hi, st, refined));
   {
     const int prof_slot = prof_begin("k_seg_suffix", st);
     k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
@@ -1198,10 +1206,27 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     prof_end(prof_slot, st, 0.0);
   }
   note_launch();
+  if (clb_all) {  // lower ends into clb, upper ends (below) into ccount
+    k_scatter_back<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, ci, ccount, clb_all);
+    note_launch();
+    k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,
+                                                                   hist_hi);
+    note_launch();
+    k_scatter_counts<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart,
+                                                                     slen, val, hist_hi, ccount);
+    note_launch();
+  }
   k_scatter_back<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, ci, ccount, ccount_all);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
+}
+
+// Candidates whose count interval has closed (lower == upper) need no recount.
+__global__ void k_drop_decided(int64_t n, const uint32_t *__restrict__ ccount,
+                               const uint32_t *__restrict__ clb, int32_t *__restrict__ cu_fb) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && cu_fb[i] >= 0 && ccount[i] == clb[i]) cu_fb[i] = -1;
 }
 
 rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq, double c,
@@ -1424,8 +1449,32 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
       RKR_CUDA(cudaStreamSynchronize(st));
       fallback += (int64_t)lstat_host_fb;
       list_fp64 += (int64_t)ls[1];
-      if (lstat_host_fb > 0)
-        RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, ties_d, st));
+      if (lstat_host_fb > 0) {
+        // count intervals for every remaining candidate, then the cap again; only
+        // candidates that can still make the k smallest and whose interval is
+        // open get their undecided items resolved
+        RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, clb, nullptr, st));
+        {
+          const int prof_slot = prof_begin("k_recount_filter", st);
+          k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
+                                                   cu_fb);
+          prof_end(prof_slot, st, 0.0);
+        }
+        note_launch();
+        k_drop_decided<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, ccount, clb, cu_fb);
+        note_launch();
+        RKR_CUDA(cudaGetLastError());
+        DevBuf bn3;
+        unsigned long long *nfb2, h2 = 0;
+        RKR_TRY(tmp_alloc(bn3, &nfb2, 1, st));
+        RKR_CUDA(cudaMemsetAsync(nfb2, 0, sizeof(unsigned long long), st));
+        k_count_valid<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_fb, nfb2);
+        note_launch();
+        RKR_CUDA(cudaMemcpyAsync(&h2, nfb2, sizeof(h2), cudaMemcpyDeviceToHost, st));
+        RKR_CUDA(cudaStreamSynchronize(st));
+        if (h2 > 0)
+          RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, nullptr, ties_d, st));
+      }
     }
     ms_res += t3.stop();
     Timer t4(st);

@@ -960,9 +960,10 @@ struct EpiRC {
     int64_t sg;
     int L;
     const double *ts;
-    uint32_t *h;
+    uint32_t *h, *hh;
     float tdn[kR], tup[kR];      // thresholds rounded down / up to float (L <= kR)
     uint32_t cnt[kR + 1];        // register histogram of positions (L <= kR)
+    int32_t dhi[kR + 1];         // bounds mode: upper-end minus lower-end positions
   };
   static constexpr size_t kSmem = 0;
   int64_t nseg, ncols;
@@ -974,18 +975,26 @@ struct EpiRC {
   const int32_t *seg_len;
   const double *ths;
   uint32_t *hist;
+  // Bounds mode (hist_hi not null): an item the screen cannot place among the
+  // thresholds adds its lower-end position to hist and its upper-end position
+  // to hist_hi, so each threshold gets a count interval; exact mode queues it.
+  uint32_t *hist_hi;
   PairQueue q;
   __device__ void unit_begin(char *, const tc::Unit &u, int et, Thread &ts) const {
     const int w = (et >> 5) + 2, lane = et & 31;
     const int r = (w & 3) * 32 + lane;
     ts.sg = (int64_t)u.rb0 * tc::BM + r;
 #pragma unroll
-    for (int i = 0; i <= kR; ++i) ts.cnt[i] = 0;
+    for (int i = 0; i <= kR; ++i) {
+      ts.cnt[i] = 0;
+      ts.dhi[i] = 0;
+    }
     if (ts.sg < nseg) {
       int64_t st0 = seg_start[ts.sg];
       ts.L = seg_len[ts.sg];
       ts.ts = ths + st0;
       ts.h = hist + 2 * st0;
+      ts.hh = hist_hi ? hist_hi + 2 * st0 : nullptr;
       ts.tminf = __double2float_rd(ts.ts[0]);
       ts.tmaxf = __double2float_ru(ts.ts[ts.L - 1]);
 #pragma unroll
@@ -1025,11 +1034,17 @@ struct EpiRC {
           if (plo == phi) {
 #pragma unroll
             for (int i = 0; i < kR; ++i) ts.cnt[i] += plo == i;
+          } else if (hist_hi) {
+#pragma unroll
+            for (int i = 0; i <= kR; ++i) {
+              ts.cnt[i] += plo == i;
+              ts.dhi[i] += (phi == i) - (plo == i);
+            }
           } else {
             push_undecided((int)ts.sg, (int)(c0 + j));
           }
         } else {
-          locate(v[j], hf, ts.b, (int)(c0 + j), (int)ts.sg, ts.L, ts.ts, ts.h);
+          locate(v[j], hf, ts.b, (int)(c0 + j), (int)ts.sg, ts.L, ts.ts, ts.h, ts.hh);
         }
       }
     }
@@ -1037,15 +1052,22 @@ struct EpiRC {
   __device__ __noinline__ void push_undecided(int sg, int c) const { q.push(sg, c); }
   // Position of one score in the sorted candidate thresholds (long blocks).
   __device__ __noinline__ void locate(float v, float hf, float b, int c, int sg, int L,
-                                      const double *t, uint32_t *h) const {
+                                      const double *t, uint32_t *h, uint32_t *hh) const {
     double hi = (double)hf, lo = (double)__fsub_rd(v, b);
     int a0 = 0, a1 = L;
     while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < lo) a0 = md + 1; else a1 = md; }
     int pa = a0;
     a1 = L;
     while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < hi) a0 = md + 1; else a1 = md; }
-    if (a0 == pa) atomicAdd(&h[pa], 1u);
-    else q.push(sg, c);
+    if (a0 == pa) {
+      atomicAdd(&h[pa], 1u);
+      if (hh) atomicAdd(&hh[pa], 1u);
+    } else if (hh) {
+      atomicAdd(&h[pa], 1u);
+      atomicAdd(&hh[a0], 1u);
+    } else {
+      q.push(sg, c);
+    }
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
   __device__ void unit_end(char *, const tc::Unit &, int, Thread &ts) const {
@@ -1054,6 +1076,15 @@ struct EpiRC {
 #pragma unroll
     for (int i = 0; i < kR; ++i)
       if (ts.cnt[i]) atomicAdd(&ts.h[i], ts.cnt[i]);   // only i < L can be nonzero
+    if (ts.hh) {
+      const uint32_t top = ts.cnt[kR] + (uint32_t)ts.dhi[kR];
+      if (top) atomicAdd(&ts.hh[ts.L], top);
+#pragma unroll
+      for (int i = 0; i < kR; ++i) {
+        const uint32_t c = ts.cnt[i] + (uint32_t)ts.dhi[i];
+        if (c) atomicAdd(&ts.hh[i], c);
+      }
+    }
   }
 };
 
@@ -1121,7 +1152,7 @@ __global__ void k_gather_side(const __nv_bfloat16 *__restrict__ hi,
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
                       const int32_t *seg_user, const double *ths, uint32_t *hist,
-                      cudaStream_t st, int64_t *refined) {
+                      uint32_t *hist_hi, cudaStream_t st, int64_t *refined) {
   constexpr int BN = 256;
   const int64_t m = idx->m;
   if (nseg <= 0) return RKR_OK;
@@ -1150,7 +1181,9 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   int2 *qitems;
   int *flags;
   const unsigned long long cap =
-      std::min<int64_t>(std::max<int64_t>(128 * ncand, 1 << 24), (int64_t)1 << 30);
+      hist_hi ? 1ull
+              : (unsigned long long)std::min<int64_t>(std::max<int64_t>(128 * ncand, 1 << 24),
+                                                      (int64_t)1 << 30);
   unsigned long long *nfp64;
   RKR_CUDA(cudaMallocAsync(&nfp64, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(nfp64, 0, sizeof(unsigned long long), st));
@@ -1163,9 +1196,10 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   e.nseg = nseg; e.ncols = m; e.bn = BN; e.rowb = A.rb3; e.tileb = tb;
   e.gacc = tc_gacc(A.kp, 1); e.gcan = tc_gcan(idx->d);
   e.seg_start = seg_start; e.seg_len = seg_len; e.ths = ths; e.hist = hist;
+  e.hist_hi = hist_hi;
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
   rkr_status s = launch_screen<BN, 4>(A, Pt, 1, row_schedule(nseg, m, BN), e, flags, st);
-  if (s == RKR_OK) {
+  if (s == RKR_OK && !hist_hi) {
     {
       const int prof_slot = prof_begin("k_rc_refine", st);
       k_rc_refine<<<8 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, seg_start, seg_len,

@@ -218,3 +218,19 @@ def test_skip_level_leaves_results_unchanged(monkeypatch, level):
         assert out["stats"].deep_queries == 0 and st.deep_queries == 0
     if level == "0":
         assert out["stats"].deep_queries > 0 and st.deep_queries > 0
+
+
+@pytest.mark.parametrize("floor_rank", [8, 40])
+def test_recount_below_the_tail_lists(floor_rank):
+    """A low floor rank leaves most candidates below their user's tail list, and
+    tiny-norm queries put u.q near the middle of every user's scores, so the
+    cutoff is wide open: ranks come from the count-interval recount and the
+    resolution of its survivors."""
+    rng = np.random.default_rng(floor_rank)
+    U, P = _rows(rng, 3000, 48), _rows(rng, 4000, 48)
+    Q = np.vstack([P[:6], 1e-3 * P[6:9], _rows(rng, 3, 48), np.zeros((1, 48), np.float32)])
+    k = np.array([1, 5, 20, 60, 7, 13, 30, 2, 50, 9, 25, 3, 11], dtype=np.int32)
+    ora, gpu = build_pair(U, P, 40, 6, 30, floor_rank=floor_rank)
+    check_exact_table(ora, gpu, U, P, floor_rank=floor_rank)
+    st = check_exact(U, P, Q, k, gpu)
+    assert st.recounted > 0 and st.wide_queries > 0
