@@ -282,9 +282,12 @@ __global__ void k_gather_samples(const float *__restrict__ Ps, const float *__re
 // Warp-per-user rank-table fill (Alg. 1 step 3, Eq. 1).  For each sampled row
 // the number of thresholds it exceeds, c = #{j : s(u,p) > t_j}, is decided by
 // the FP32 screen when its bin interval is a single value and by canonical
-// FP64 otherwise; W[c] += w.  Then N[j] = sum_{c > j} W[c].
+// FP64 otherwise; W[c] += w.  Then N[j] = sum_{c > j} W[c].  Undecided samples
+// are queued per warp and evaluated after the screen one per lane, so the
+// canonical FP64 dot products run in full warps.
 constexpr int kTableWarps = 8;
 constexpr int kTableTile = 64;
+constexpr int kTableQueue = 128;  // undecided samples queued per warp
 
 __global__ void __launch_bounds__(kTableWarps * 32)
     k_rank_table(const float *__restrict__ U, int64_t n, int d, const float *__restrict__ unrm,
@@ -296,11 +299,15 @@ __global__ void __launch_bounds__(kTableWarps * 32)
   float *Xs = smem;                                   // [d][kTableTile]
   float *Uw = Xs + (size_t)d * kTableTile;            // [warps][d]
   uint32_t *W = (uint32_t *)(Uw + (size_t)kTableWarps * d);  // [warps][tau+1]
+  int32_t *Qs = (int32_t *)(W + (size_t)kTableWarps * (tau + 1));  // [warps][kTableQueue]
+  __shared__ int qn[kTableWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t u = (int64_t)blockIdx.x * kTableWarps + warp;
   const bool active = u < n;
   uint32_t *Wu = W + (size_t)warp * (tau + 1);
+  int32_t *Qw = Qs + warp * kTableQueue;
   for (int c = lane; c <= tau; c += 32) Wu[c] = 0;
+  if (lane == 0) qn[warp] = 0;
   for (int k = lane; k < d; k += 32) Uw[warp * d + k] = active ? U[u * d + k] : 0.0f;
   const float cfac = screen_cfac(d);
   const float nu = active ? unrm[u] : 0.0f;
@@ -331,16 +338,28 @@ __global__ void __launch_bounds__(kTableWarps * 32)
       float b = screen_bound(cfac, nu, snrm[p]);
       int jlo, jhi;
       bin_interval(bf, fm, tau, __fsub_rd(sh, b), __fadd_ru(sh, b), jlo, jhi);
-      int c = jlo;
-      if (jlo != jhi) {
-        double sc = canon_dot_slow(U + u * d, S + (int64_t)p * d, d);
-        c = exact_c(sc, fm, dl, tau);
+      if (jlo == jhi) {
+        atomicAdd(&Wu[jlo], sw[p]);
+      } else {
+        const int slot = atomicAdd(&qn[warp], 1);
+        if (slot < kTableQueue) {
+          Qw[slot] = p;
+        } else {  // queue full: evaluate here
+          double sc = canon_dot_slow(U + u * d, S + (int64_t)p * d, d);
+          atomicAdd(&Wu[exact_c(sc, fm, dl, tau)], sw[p]);
+        }
       }
-      atomicAdd(&Wu[c], sw[p]);
     }
   }
   __syncwarp();
   if (!active) return;
+  const int nqd = min(qn[warp], kTableQueue);
+  for (int i = lane; i < nqd; i += 32) {
+    const int p = Qw[i];
+    double sc = canon_dot(U + u * d, S + (int64_t)p * d, d);
+    atomicAdd(&Wu[exact_c(sc, fm, dl, tau)], sw[p]);
+  }
+  __syncwarp();
   // suffix sums: N[j] = sum_{c = j+1 .. tau} W[c]; lanes own contiguous chunks
   const int chunk = (tau + 1 + 31) / 32;
   int c0 = lane * chunk, c1 = min(tau + 1, c0 + chunk);
@@ -631,7 +650,8 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_TRY(dalloc(&idx->N, (size_t)n * tau));
   {
     size_t sm = sizeof(float) * ((size_t)d * kTableTile + (size_t)kTableWarps * d) +
-                sizeof(uint32_t) * (size_t)kTableWarps * (tau + 1);
+                sizeof(uint32_t) * (size_t)kTableWarps * (tau + 1) +
+                sizeof(int32_t) * kTableWarps * kTableQueue;
     if (sm > 227 * 1024) return fail(RKR_EINVAL, "tau too large for the table kernel");
     RKR_CUDA(cudaFuncSetAttribute(k_rank_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));

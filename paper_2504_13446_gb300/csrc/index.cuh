@@ -135,6 +135,7 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       const int32_t *seg_user, const double *ths, uint32_t *hist,
                       uint32_t *hist_hi, cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
+constexpr int kRecountSeg = 1;      // thresholds per recount segment (one per screen row)
 constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)
 constexpr int kListG = 1024;        // columns of the list grid (finer than the count grid)
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);

@@ -380,7 +380,8 @@ __global__ void k_bitonic128(uint64_t *hi, uint64_t *lo, int32_t *val, int64_t N
   }
 }
 
-// Segments of equal user in the sorted order: start index and length.
+// Segments of equal user in the sorted order: start index and length (runs
+// longer than kRecountSeg are cut).
 __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
                            unsigned long long *__restrict__ nseg, int64_t *__restrict__ seg_start,
                            int32_t *__restrict__ seg_len) {
@@ -389,9 +390,13 @@ __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
   if (i > 0 && key_hi[i] == key_hi[i - 1]) return;
   int64_t e = i + 1;
   while (e < count && key_hi[e] == key_hi[i]) ++e;
-  unsigned long long slot = atomicAdd(nseg, 1ull);
-  seg_start[slot] = i;
-  seg_len[slot] = (int32_t)(e - i);
+  // a user's run is cut into segments of at most kRecountSeg thresholds, which
+  // the recount screen keeps in registers
+  for (int64_t a = i; a < e; a += kRecountSeg) {
+    unsigned long long slot = atomicAdd(nseg, 1ull);
+    seg_start[slot] = a;
+    seg_len[slot] = (int32_t)(e - a < kRecountSeg ? e - a : kRecountSeg);
+  }
 }
 
 // Per segment: its user, its thresholds in sorted order, and a zeroed histogram
@@ -1180,8 +1185,11 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     RKR_TRY(tmp_alloc(bhh, &hist_hi, 2 * cnt, st));
     RKR_CUDA(cudaMemsetAsync(hist_hi, 0, sizeof(uint32_t) * 2 * cnt, st));
   }
-  RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, ths, hist,
-                     hist_hi, st, refined));
+  {
+    ProfScope prof(clb_all ? "recount(bounds)" : "recount(exact)", st, (double)nseg);
+    RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, ths,
+                       hist, hist_hi, st, refined));
+  }
   {
     const int prof_slot = prof_begin("k_seg_suffix", st);
     k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,

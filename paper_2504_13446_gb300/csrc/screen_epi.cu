@@ -151,7 +151,7 @@ struct EpiFbB {
       if ((v[j] >= ts.tmax || v[j] <= ts.tmin) && c0 + j < ncols) push((int)ts.row, (int)(c0 + j));
     }
   }
-  __device__ __noinline__ void push(int row, int c) const { q.push(row, c); }
+  __device__ __forceinline__ void push(int row, int c) const { q.push(row, c); }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
   __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
 };
@@ -954,16 +954,13 @@ rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, con
 
 struct EpiRC {
   static const char *name() { return "k_screen<EpiRC>"; }
-  static constexpr int kR = 8;   // thresholds kept in registers
+  // One threshold per row (segments of one candidate): an item is certainly above
+  // u.q when its lower end exceeds u.q, possibly above when its upper end does.
   struct Thread {
-    float b, tminf, tmaxf;
+    float b, tdn, tup;           // bound; u.q rounded down / up to float
     int64_t sg;
-    int L;
-    const double *ts;
     uint32_t *h, *hh;
-    float tdn[kR], tup[kR];      // thresholds rounded down / up to float (L <= kR)
-    uint32_t cnt[kR + 1];        // register histogram of positions (L <= kR)
-    int32_t dhi[kR + 1];         // bounds mode: upper-end minus lower-end positions
+    uint32_t clo, chi;           // items certainly / possibly above u.q
   };
   static constexpr size_t kSmem = 0;
   int64_t nseg, ncols;
@@ -975,118 +972,66 @@ struct EpiRC {
   const int32_t *seg_len;
   const double *ths;
   uint32_t *hist;
-  // Bounds mode (hist_hi not null): an item the screen cannot place among the
-  // thresholds adds its lower-end position to hist and its upper-end position
-  // to hist_hi, so each threshold gets a count interval; exact mode queues it.
+  // Bounds mode (hist_hi not null): the possibly-above count goes to hist_hi and
+  // nothing is queued; exact mode queues the items between the two ends.
   uint32_t *hist_hi;
   PairQueue q;
-  __device__ void unit_begin(char *, const tc::Unit &u, int et, Thread &ts) const {
+  __device__ __forceinline__ void unit_begin(char *, const tc::Unit &u, int et,
+                                             Thread &ts) const {
     const int w = (et >> 5) + 2, lane = et & 31;
     const int r = (w & 3) * 32 + lane;
     ts.sg = (int64_t)u.rb0 * tc::BM + r;
-#pragma unroll
-    for (int i = 0; i <= kR; ++i) {
-      ts.cnt[i] = 0;
-      ts.dhi[i] = 0;
-    }
+    ts.clo = 0;
+    ts.chi = 0;
     if (ts.sg < nseg) {
-      int64_t st0 = seg_start[ts.sg];
-      ts.L = seg_len[ts.sg];
-      ts.ts = ths + st0;
+      const int64_t st0 = seg_start[ts.sg];
+      const double t = ths[st0];
       ts.h = hist + 2 * st0;
       ts.hh = hist_hi ? hist_hi + 2 * st0 : nullptr;
-      ts.tminf = __double2float_rd(ts.ts[0]);
-      ts.tmaxf = __double2float_ru(ts.ts[ts.L - 1]);
-#pragma unroll
-      for (int i = 0; i < kR; ++i) {
-        double t = i < ts.L ? ts.ts[i] : INFINITY;
-        ts.tdn[i] = __double2float_rd(t);
-        ts.tup[i] = __double2float_ru(t);
-      }
+      ts.tdn = __double2float_rd(t);
+      ts.tup = __double2float_ru(t);
     } else {
-      ts.L = 0;
-      ts.tminf = INFINITY;
-      ts.tmaxf = INFINITY;
+      ts.tdn = INFINITY;
+      ts.tup = INFINITY;
     }
   }
-  __device__ void tile_begin(char *, int, int ct, int, int, Thread &ts) const {
+  __device__ __forceinline__ void tile_begin(char *, int, int ct, int, int, Thread &ts) const {
     ts.b = ts.sg < nseg ? tc::screen_bound_tc(rowb[ts.sg], tileb[ct], gacc, gcan) : 0.0f;
   }
-  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
-                        Thread &ts) const {
+  __device__ __forceinline__ void chunk(char *, int, int ct, int, int col, uint32_t,
+                                        const float (&v)[32], Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
+    uint32_t mlo = 0, mhi = 0;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      float hf = __fadd_ru(v[j], ts.b);
-      if (hf > ts.tminf && c0 + j < ncols) {
-        const float lf = __fsub_rd(v[j], ts.b);
-        if (lf > ts.tmaxf) {
-          ++ts.cnt[kR];                      // above every threshold: position L
-        } else if (ts.L <= kR) {
-          // pos = #{t < s}: t_i < lf certainly if tup_i < lf; t_i >= hf certainly
-          // if tdn_i >= hf; anything else is undecided
-          int plo = 0, phi = 0;
-#pragma unroll
-          for (int i = 0; i < kR; ++i) {
-            plo += ts.tup[i] < lf;
-            phi += ts.tdn[i] < hf;
-          }
-          if (plo == phi) {
-#pragma unroll
-            for (int i = 0; i < kR; ++i) ts.cnt[i] += plo == i;
-          } else if (hist_hi) {
-#pragma unroll
-            for (int i = 0; i <= kR; ++i) {
-              ts.cnt[i] += plo == i;
-              ts.dhi[i] += (phi == i) - (plo == i);
-            }
-          } else {
-            push_undecided((int)ts.sg, (int)(c0 + j));
-          }
-        } else {
-          locate(v[j], hf, ts.b, (int)(c0 + j), (int)ts.sg, ts.L, ts.ts, ts.h, ts.hh);
-        }
+      mlo |= (__fsub_rd(v[j], ts.b) > ts.tup ? 1u : 0u) << j;
+      mhi |= (__fadd_ru(v[j], ts.b) > ts.tdn ? 1u : 0u) << j;
+    }
+    const int64_t left = ncols - c0;
+    if (left < 32) {
+      const uint32_t keep = left <= 0 ? 0u : (1u << left) - 1u;
+      mlo &= keep;
+      mhi &= keep;
+    }
+    ts.clo += __popc(mlo);
+    ts.chi += __popc(mhi);
+    if (!hist_hi) {
+      uint32_t und = mhi & ~mlo;
+      while (und) {
+        const int j = __ffs(und) - 1;
+        und &= und - 1u;
+        q.push((int)ts.sg, (int)(c0 + j));
       }
     }
   }
-  __device__ __noinline__ void push_undecided(int sg, int c) const { q.push(sg, c); }
-  // Position of one score in the sorted candidate thresholds (long blocks).
-  __device__ __noinline__ void locate(float v, float hf, float b, int c, int sg, int L,
-                                      const double *t, uint32_t *h, uint32_t *hh) const {
-    double hi = (double)hf, lo = (double)__fsub_rd(v, b);
-    int a0 = 0, a1 = L;
-    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < lo) a0 = md + 1; else a1 = md; }
-    int pa = a0;
-    a1 = L;
-    while (a0 < a1) { int md = (a0 + a1) >> 1; if (t[md] < hi) a0 = md + 1; else a1 = md; }
-    if (a0 == pa) {
-      atomicAdd(&h[pa], 1u);
-      if (hh) atomicAdd(&hh[pa], 1u);
-    } else if (hh) {
-      atomicAdd(&h[pa], 1u);
-      atomicAdd(&hh[a0], 1u);
-    } else {
-      q.push(sg, c);
-    }
-  }
-  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
-  __device__ void unit_end(char *, const tc::Unit &, int, Thread &ts) const {
+  __device__ __forceinline__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ __forceinline__ void unit_end(char *, const tc::Unit &, int, Thread &ts) const {
     if (ts.sg >= nseg) return;
-    if (ts.cnt[kR]) atomicAdd(&ts.h[ts.L], ts.cnt[kR]);
-#pragma unroll
-    for (int i = 0; i < kR; ++i)
-      if (ts.cnt[i]) atomicAdd(&ts.h[i], ts.cnt[i]);   // only i < L can be nonzero
-    if (ts.hh) {
-      const uint32_t top = ts.cnt[kR] + (uint32_t)ts.dhi[kR];
-      if (top) atomicAdd(&ts.hh[ts.L], top);
-#pragma unroll
-      for (int i = 0; i < kR; ++i) {
-        const uint32_t c = ts.cnt[i] + (uint32_t)ts.dhi[i];
-        if (c) atomicAdd(&ts.hh[i], c);
-      }
-    }
+    if (ts.clo) atomicAdd(&ts.h[1], ts.clo);      // position 1: above the one threshold
+    if (ts.hh && ts.chi) atomicAdd(&ts.hh[1], ts.chi);
   }
 };
+
 
 // Exact position of each queued score among its segment's thresholds.  A
 // CUDA-core FP32 dot product with its bound settles most items; the rest are
