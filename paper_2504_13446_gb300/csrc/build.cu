@@ -111,6 +111,66 @@ __global__ void k_bitonic(uint64_t *key, int32_t *val, int64_t N, int64_t j, int
   }
 }
 
+// FNV-1a over the 32-bit patterns of a row.
+__device__ __forceinline__ uint64_t row_hash(const float *x, int d) {
+  uint64_t h = 1469598103934665603ull;
+  for (int k = 0; k < d; ++k) {
+    h ^= (uint64_t)__float_as_uint(x[k]);
+    h *= 1099511628211ull;
+  }
+  return h == ~0ull ? h - 1 : h;  // ~0 marks padding
+}
+
+__global__ void k_row_hashes(const float *__restrict__ X, int64_t rows, int d, int64_t Np2,
+                             uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Np2) return;
+  keys[i] = i < rows ? row_hash(X + i * d, d) : ~0ull;
+  vals[i] = (int32_t)i;
+}
+
+rkr_status row_hashes(const float *X, int64_t rows, int d, int64_t Np2, uint64_t *keys,
+                      int32_t *vals, cudaStream_t st) {
+  k_row_hashes<<<(unsigned)((Np2 + 255) / 256), 256, 0, st>>>(X, rows, d, Np2, keys, vals);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+// Sorted-item position of an item row bitwise equal to each query row, or -1.
+__global__ void k_query_self(int nq, const float *__restrict__ Q, int d,
+                             const uint64_t *__restrict__ phk, const int32_t *__restrict__ phv,
+                             int64_t phn, const float *__restrict__ Ps,
+                             int32_t *__restrict__ qself) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const float *x = Q + (int64_t)q * d;
+  const uint64_t h = row_hash(x, d);
+  int64_t a = 0, b = phn;
+  while (a < b) {
+    int64_t md = (a + b) >> 1;
+    if (phk[md] < h) a = md + 1; else b = md;
+  }
+  int32_t found = -1;
+  for (; a < phn && phk[a] == h && found < 0; ++a) {
+    const float *y = Ps + (int64_t)phv[a] * d;
+    bool eq = true;
+    for (int k = 0; k < d && eq; ++k) eq = __float_as_uint(x[k]) == __float_as_uint(y[k]);
+    if (eq) found = phv[a];
+  }
+  qself[q] = found;
+}
+
+rkr_status query_self(const rkr_index *idx, const float *Q, int nq, int32_t *qself,
+                      cudaStream_t st) {
+  if (nq <= 0) return RKR_OK;
+  k_query_self<<<(nq + 127) / 128, 128, 0, st>>>(nq, Q, idx->d, idx->phk, idx->phv, idx->phn,
+                                                 idx->Ps, qself);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
 rkr_status sort_pairs(uint64_t *key, int32_t *val, int64_t N_pow2, cudaStream_t st) {
   int bs = 256;
   unsigned grid = (unsigned)((N_pow2 + bs - 1) / bs);
@@ -526,6 +586,12 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_TRY(max_float(idx->pnrm_s, m, &idx->pmax, st));
   RKR_TRY(tc_stage(idx->U, n, d, idx->Ut, st));
   RKR_TRY(tc_stage(idx->Ps, m, d, idx->Pt, st));
+  // hash table of the sorted item rows (a query equal to an item ties with it exactly)
+  idx->phn = Np2;
+  RKR_TRY(dalloc(&idx->phk, Np2));
+  RKR_TRY(dalloc(&idx->phv, Np2));
+  RKR_TRY(row_hashes(idx->Ps, m, d, Np2, idx->phk, idx->phv, st));
+  RKR_TRY(sort_pairs(idx->phk, idx->phv, Np2, st));
   cudaFreeAsync(keys, st);
   cudaFreeAsync(vals, st);
   cudaFreeAsync(pn32, st);
@@ -739,7 +805,7 @@ void index_release(rkr_index *idx) {
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
                   idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
                   idx->xfloor, idx->xloff, idx->xlcap, idx->xlist, idx->xlcnt,
-                  idx->xbmax, idx->ptile3, idx->xcoff, idx->ldx, idx->lbin};
+                  idx->xbmax, idx->ptile3, idx->xcoff, idx->ldx, idx->lbin, idx->phk, idx->phv};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   tc_free(idx->Ut);

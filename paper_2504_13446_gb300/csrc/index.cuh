@@ -56,6 +56,9 @@ struct rkr_index {
   double *ldx = nullptr;                    // n: step of the list grid x_0 + j ldx, j < kListG
   rkr::BinFP *lbin = nullptr;               // n: bin parameters of the list grid
   float *xbmax = nullptr;                   // n: largest screen bound of a user's entries
+  uint64_t *phk = nullptr;                  // hashes of the sorted item rows, ascending (phn)
+  int32_t *phv = nullptr;                   // sorted-item position of each hash
+  int64_t phn = 0;
   rkr::tc::RowBound *ptile3 = nullptr;      // item tile bounds of the split screen
   int ptile_bn = 0;
 
@@ -132,13 +135,22 @@ rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, con
 // With hist_hi (bounds mode) nothing is queued: undecided items give count intervals.
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
-                      const int32_t *seg_user, const double *ths, uint32_t *hist,
-                      uint32_t *hist_hi, cudaStream_t st, int64_t *refined);
+                      const int32_t *seg_user, const int32_t *seg_self, const double *ths,
+                      uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined);
 constexpr int kXGrid = 128;
 constexpr int kRecountSeg = 1;      // thresholds per recount segment (one per screen row)
 constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)
 constexpr int kListG = 1024;        // columns of the list grid (finer than the count grid)
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);
+
+// Hash of each row's float bit patterns; rows past `rows` (up to Np2) get ~0.
+rkr_status row_hashes(const float *X, int64_t rows, int d, int64_t Np2, uint64_t *keys,
+                      int32_t *vals, cudaStream_t st);
+rkr_status sort_pairs(uint64_t *key, int32_t *val, int64_t N_pow2, cudaStream_t st);
+// qself[q] = sorted position of an item bitwise equal to query q (its score ties
+// with u.q exactly for every user), or -1.
+rkr_status query_self(const rkr_index *idx, const float *Q, int nq, int32_t *qself,
+                      cudaStream_t st);
 
 // Row norms: FP64 canonical norms (optional) and FP32 upper bounds.
 rkr_status row_norms(const float *X, int64_t rows, int d, double *nrm64, float *nrm32,

@@ -404,13 +404,16 @@ __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
 __global__ void k_seg_prep(int64_t nseg, const int64_t *__restrict__ seg_start,
                            const int32_t *__restrict__ seg_len, const uint64_t *__restrict__ key_hi,
                            const int32_t *__restrict__ order, const double *__restrict__ th,
-                           int32_t *__restrict__ seg_user, double *__restrict__ ths,
-                           uint32_t *__restrict__ hist) {
+                           const int32_t *__restrict__ cq, const int32_t *__restrict__ qself,
+                           int32_t *__restrict__ seg_user, int32_t *__restrict__ seg_self,
+                           double *__restrict__ ths, uint32_t *__restrict__ hist) {
   int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (sg >= nseg) return;
   int64_t st0 = seg_start[sg];
   int L = seg_len[sg];
   seg_user[sg] = (int32_t)key_hi[st0];
+  // one-threshold segments: the item tying exactly with that candidate's u.q
+  seg_self[sg] = L == 1 ? qself[cq[order[st0]]] : -1;
   for (int i = 0; i < L; ++i) ths[st0 + i] = th[order[st0 + i]];
   for (int i = 0; i <= L; ++i) hist[2 * st0 + i] = 0;
 }
@@ -464,7 +467,8 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             int G, const uint32_t *__restrict__ XLO,
                             const uint32_t *__restrict__ XHI, uint32_t mtop,
                             uint32_t *__restrict__ ccount, uint32_t *__restrict__ clb,
-                            int32_t *__restrict__ cu_fb, unsigned long long *__restrict__ stat) {
+                            int32_t *__restrict__ cu_fb, const int32_t *__restrict__ qself,
+                            unsigned long long *__restrict__ stat) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int64_t u = cu[i];
@@ -494,8 +498,10 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   uint32_t above = L - (uint32_t)co[chi];
   const tc::RowBound ru = rb3[u];
   const float cfac = screen_cfac(d);
+  const int32_t self = qself[cq[i]];
   for (int e = co[clo]; e < (int)co[chi]; ++e) {
     const uint32_t p = row[e].x;
+    if ((int32_t)p == self) continue;  // the query's own item: s(u,p) = u.q, not above
     const float v = __uint_as_float(row[e].y);
     const float b = tc::screen_bound_tc(ru, ptile[p / pbn], gacc, gcan);
     if ((double)__fsub_rd(v, b) > theta) { ++above; continue; }
@@ -1103,8 +1109,9 @@ __global__ void k_scatter_back(int64_t n, const int32_t *__restrict__ oi,
 // ccount gets an upper and clb a lower bound of the count instead.
 static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int64_t total,
                                      const int32_t *cu_all, const int32_t *cq_all,
-                                     uint32_t *ccount_all, uint32_t *clb_all,
-                                     unsigned long long *ties_d, cudaStream_t st) {
+                                     const int32_t *qself, uint32_t *ccount_all,
+                                     uint32_t *clb_all, unsigned long long *ties_d,
+                                     cudaStream_t st) {
   const int bs = 256;
   DevBuf bcu, bcq, bci, bcc, bcur;
   int32_t *cu, *cq, *ci;
@@ -1171,11 +1178,12 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   unsigned long long nseg = 0;
   RKR_CUDA(cudaMemcpyAsync(&nseg, nseg_d, sizeof(nseg), cudaMemcpyDeviceToHost, st));
   RKR_CUDA(cudaStreamSynchronize(st));
-  DevBuf b10;
-  int32_t *suser;
+  DevBuf b10, b11;
+  int32_t *suser, *sself;
   RKR_TRY(tmp_alloc(b10, &suser, nseg, st));
-  k_seg_prep<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen, khi,
-                                                               val, th, suser, ths, hist);
+  RKR_TRY(tmp_alloc(b11, &sself, nseg, st));
+  k_seg_prep<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>(
+      (int64_t)nseg, sstart, slen, khi, val, th, cq, qself, suser, sself, ths, hist);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   int64_t refined[2] = {0, 0};
@@ -1187,8 +1195,8 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   }
   {
     ProfScope prof(clb_all ? "recount(bounds)" : "recount(exact)", st, (double)nseg);
-    RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, ths,
-                       hist, hist_hi, st, refined));
+    RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, sself,
+                       ths, hist, hist_hi, st, refined));
   }
   {
     const int prof_slot = prof_begin("k_seg_suffix", st);
@@ -1372,6 +1380,10 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
   DevBuf bls;
   unsigned long long *lstat;
   RKR_TRY(tmp_alloc(bls, &lstat, 2, st));
+  DevBuf bqs;
+  int32_t *qself;
+  RKR_TRY(tmp_alloc(bqs, &qself, nq, st));
+  RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
   int64_t fallback = 0, list_fp64 = 0;
   unsigned long long lstat_host_fb = 0;
   Plan plan;
@@ -1429,7 +1441,7 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
             idx->xlist, idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
             idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
             idx->ldx, kListG,
-            idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, lstat);
+            idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, qself, lstat);
         prof_end(prof_slot, st, 0.0);
       }
       note_launch();
@@ -1461,7 +1473,8 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
         // count intervals for every remaining candidate, then the cap again; only
         // candidates that can still make the k smallest and whose interval is
         // open get their undecided items resolved
-        RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, clb, nullptr, st));
+        RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr,
+                                   st));
         {
           const int prof_slot = prof_begin("k_recount_filter", st);
           k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
@@ -1481,7 +1494,8 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
         RKR_CUDA(cudaMemcpyAsync(&h2, nfb2, sizeof(h2), cudaMemcpyDeviceToHost, st));
         RKR_CUDA(cudaStreamSynchronize(st));
         if (h2 > 0)
-          RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, ccount, nullptr, ties_d, st));
+          RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, nullptr, ties_d,
+                                     st));
       }
     }
     ms_res += t3.stop();

@@ -959,6 +959,7 @@ struct EpiRC {
   struct Thread {
     float b, tdn, tup;           // bound; u.q rounded down / up to float
     int64_t sg;
+    int64_t self;                // item tying exactly with u.q (never above), or -1
     uint32_t *h, *hh;
     uint32_t clo, chi;           // items certainly / possibly above u.q
   };
@@ -971,6 +972,7 @@ struct EpiRC {
   const int64_t *seg_start;
   const int32_t *seg_len;
   const double *ths;
+  const int32_t *seg_self;
   uint32_t *hist;
   // Bounds mode (hist_hi not null): the possibly-above count goes to hist_hi and
   // nothing is queued; exact mode queues the items between the two ends.
@@ -990,7 +992,9 @@ struct EpiRC {
       ts.hh = hist_hi ? hist_hi + 2 * st0 : nullptr;
       ts.tdn = __double2float_rd(t);
       ts.tup = __double2float_ru(t);
+      ts.self = seg_self[ts.sg];
     } else {
+      ts.self = -1;
       ts.tdn = INFINITY;
       ts.tup = INFINITY;
     }
@@ -1013,6 +1017,7 @@ struct EpiRC {
       mlo &= keep;
       mhi &= keep;
     }
+    if (ts.self >= c0 && ts.self < c0 + 32) mhi &= ~(1u << (int)(ts.self - c0));
     ts.clo += __popc(mlo);
     ts.chi += __popc(mhi);
     if (!hist_hi) {
@@ -1096,8 +1101,8 @@ __global__ void k_gather_side(const __nv_bfloat16 *__restrict__ hi,
 
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
-                      const int32_t *seg_user, const double *ths, uint32_t *hist,
-                      uint32_t *hist_hi, cudaStream_t st, int64_t *refined) {
+                      const int32_t *seg_user, const int32_t *seg_self, const double *ths,
+                      uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined) {
   constexpr int BN = 256;
   const int64_t m = idx->m;
   if (nseg <= 0) return RKR_OK;
@@ -1141,7 +1146,7 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   e.nseg = nseg; e.ncols = m; e.bn = BN; e.rowb = A.rb3; e.tileb = tb;
   e.gacc = tc_gacc(A.kp, 1); e.gcan = tc_gcan(idx->d);
   e.seg_start = seg_start; e.seg_len = seg_len; e.ths = ths; e.hist = hist;
-  e.hist_hi = hist_hi;
+  e.hist_hi = hist_hi; e.seg_self = seg_self;
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
   rkr_status s = launch_screen<BN, 4>(A, Pt, 1, row_schedule(nseg, m, BN), e, flags, st);
   if (s == RKR_OK && !hist_hi) {
