@@ -356,8 +356,8 @@ __global__ void __launch_bounds__(kTableWarps * 32)
                  const double *__restrict__ delta, const BinFP *__restrict__ binfp, int tau,
                  uint32_t *__restrict__ N) {
   extern __shared__ float smem[];
-  float *Xs = smem;                                   // [d][kTableTile]
-  float *Uw = Xs + (size_t)d * kTableTile;            // [warps][d]
+  float *Xs = smem;                                   // [d][kTableTile + 1]
+  float *Uw = Xs + (size_t)d * (kTableTile + 1);      // [warps][d]
   uint32_t *W = (uint32_t *)(Uw + (size_t)kTableWarps * d);  // [warps][tau+1]
   int32_t *Qs = (int32_t *)(W + (size_t)kTableWarps * (tau + 1));  // [warps][kTableQueue]
   __shared__ int qn[kTableWarps];
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kTableWarps * 32)
     for (int e = threadIdx.x; e < kTableTile * d; e += blockDim.x) {
       int j = e / d, k = e - j * d;
       int p = x0 + j;
-      Xs[k * kTableTile + j] = p < nsamp ? S[(int64_t)p * d + k] : 0.0f;
+      Xs[k * (kTableTile + 1) + j] = p < nsamp ? S[(int64_t)p * d + k] : 0.0f;
     }
     __syncthreads();
     if (!active) continue;
@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(kTableWarps * 32)
     const float *uw = Uw + warp * d;
     for (int k = 0; k < d; ++k) {
       float uk = uw[k];
-      acc0 = fmaf(uk, Xs[k * kTableTile + lane], acc0);
-      acc1 = fmaf(uk, Xs[k * kTableTile + lane + 32], acc1);
+      acc0 = fmaf(uk, Xs[k * (kTableTile + 1) + lane], acc0);
+      acc1 = fmaf(uk, Xs[k * (kTableTile + 1) + lane + 32], acc1);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -715,7 +715,7 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   // sampled rank table
   RKR_TRY(dalloc(&idx->N, (size_t)n * tau));
   {
-    size_t sm = sizeof(float) * ((size_t)d * kTableTile + (size_t)kTableWarps * d) +
+    size_t sm = sizeof(float) * ((size_t)d * (kTableTile + 1) + (size_t)kTableWarps * d) +
                 sizeof(uint32_t) * (size_t)kTableWarps * (tau + 1) +
                 sizeof(int32_t) * kTableWarps * kTableQueue;
     if (sm > 227 * 1024) return fail(RKR_EINVAL, "tau too large for the table kernel");

@@ -146,9 +146,15 @@ struct EpiFbB {
   __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
+    uint32_t mask = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if ((v[j] >= ts.tmax || v[j] <= ts.tmin) && c0 + j < ncols) push((int)ts.row, (int)(c0 + j));
+    for (int j = 0; j < 32; ++j) mask |= (v[j] >= ts.tmax || v[j] <= ts.tmin ? 1u : 0u) << j;
+    const int64_t left = ncols - c0;
+    if (left < 32) mask &= left <= 0 ? 0u : (1u << left) - 1u;
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      push((int)ts.row, (int)(c0 + j));
     }
   }
   __device__ __forceinline__ void push(int row, int c) const { q.push(row, c); }
@@ -281,38 +287,28 @@ struct EpiXT {
   static const char *name() { return "k_screen<EpiXT>"; }
   struct Thread {
     float skip, b;
-    BinFP bf;
-    double g0;
     int64_t row;
-    uint32_t cnt;
     int64_t off;
     uint32_t cap;
   };
-  static constexpr int kW = (kXG + 2) / 2;  // 32-bit words per histogram row
-  // histograms, per-row totals and list cursors, then a 32 x 33 staging tile per warp
-  static constexpr size_t kStageOff = sizeof(uint32_t) * (2 * 128 * kW + 256 + 128);
+  // list cursors of the block's 128 rows, then a 32 x 33 staging tile per warp
+  static constexpr size_t kStageOff = sizeof(uint32_t) * 128;
   static constexpr size_t kSmem = kStageOff + sizeof(float) * 8 * 32 * 33;
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
   tc::Gacc gacc;
   float gcan;
-  const BinFP *xbin;
-  const double *xg0;
   const float *g0f;
-  uint32_t *XLO, *XHI;
-  uint32_t mcount;
-  // tail lists: every above-floor item is appended to its user's list
+  // tail lists: every above-floor item is appended to its user's list; the
+  // count table is derived from the lists when they are grouped
   uint2 *list;
   const int64_t *loff;
   const uint32_t *lcapv;
   uint32_t *lcnt;      // n: entries (> capacity marks an overflow)
-  __device__ uint32_t *lslot(char *S) const { return (uint32_t *)S + 2 * 128 * kW + 256; }
-  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &ts) const {
-    uint32_t *H = (uint32_t *)S;
-    for (int i = et; i < 2 * 128 * kW; i += 256) H[i] = 0;
+  __device__ uint32_t *lslot(char *S) const { return (uint32_t *)S; }
+  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &) const {
     if (et < 128) lslot(S)[et] = 0;
-    ts.cnt = 0;
   }
   __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
     ts.row = (int64_t)rb * tc::BM + r;
@@ -321,16 +317,14 @@ struct EpiXT {
       ts.skip = __fsub_rd(g0f[ts.row], ts.b);  // s_hat <= skip implies s <= x_0
       ts.off = loff[ts.row];
       ts.cap = lcapv[ts.row];
-      ts.bf = xbin[ts.row];
-      ts.g0 = xg0[ts.row];
     } else {
       ts.skip = INFINITY;
     }
   }
   // Scores above the floor are a few per cent and scattered over lanes: each
-  // lane parks its 32 scores in a shared tile and walks only its own above-floor
-  // ones, so the warp loops max-over-lanes times instead of once per column.
-  __device__ void chunk(char *S, int, int ct, int r, int col, uint32_t tm, const float (&v)[32],
+  // lane parks its 32 scores in a shared tile, reserves its slots with one
+  // atomic and walks only its own above-floor ones.
+  __device__ void chunk(char *S, int, int ct, int r, int col, uint32_t, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
     const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
@@ -339,50 +333,28 @@ struct EpiXT {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       tile[j] = v[j];
-      if (v[j] > ts.skip && c0 + j < ncols) mask |= 1u << j;
+      mask |= (v[j] > ts.skip ? 1u : 0u) << j;
     }
+    const int64_t left = ncols - c0;
+    if (left < 32) mask &= left <= 0 ? 0u : (1u << left) - 1u;
+    if (!mask) return;
+    uint32_t pos = atomicAdd(&lslot(S)[r], (uint32_t)__popc(mask));
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      count((uint32_t *)S, r, tile[j], (int)(c0 + j), ts);
+      if (pos < ts.cap) list[ts.off + pos] = make_uint2((uint32_t)(c0 + j), __float_as_uint(tile[j]));
+      ++pos;
     }
-  }
-  __device__ __forceinline__ void count(uint32_t *S, int r, float v, int c, Thread &ts) const {
-    {  // every above-floor item goes to the list: it is complete above x_0
-      uint32_t pos = atomicAdd(&S[2 * 128 * kW + 256 + r], 1u);
-      if (pos < ts.cap) list[ts.off + pos] = make_uint2((uint32_t)c, __float_as_uint(v));
-    }
-    int clo, chi;
-    bin_interval(ts.bf, ts.g0, kXG, __fsub_rd(v, ts.b), __fadd_ru(v, ts.b), clo, chi);
-    if (chi == 0) return;
-    uint32_t *Hlo = S + r * kW, *Hhi = S + 128 * kW + r * kW;
-    atomicAdd(&Hlo[clo >> 1], 1u << ((clo & 1) * 16));
-    atomicAdd(&Hhi[chi >> 1], 1u << ((chi & 1) * 16));
-    ++ts.cnt;
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
-  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &ts) const {
-    uint32_t *tot = (uint32_t *)S + 2 * 128 * kW;
-    const int w = (et >> 5) + 2, lane = et & 31;
-    const int row = (w & 3) * 32 + lane, half = (et >> 5) >> 2;
-    tot[half * 128 + row] = ts.cnt;
+  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &) const {
     tc::epi_sync();
     if (et >= 128) return;
-    int64_t g = (int64_t)u.rb0 * tc::BM + et;
-    if (g >= nrows) return;
-    const uint32_t *Hlo = (const uint32_t *)S + et * kW;
-    const uint32_t *Hhi = (const uint32_t *)S + 128 * kW + et * kW;
-    const bool ok = tot[et] + tot[128 + et] <= 65535u;
-    lcnt[g] = lslot(S)[et];
-    uint32_t rlo = 0, rhi = 0;
-    for (int c = kXG; c >= 1; --c) {
-      rlo += (Hlo[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
-      rhi += (Hhi[c >> 1] >> ((c & 1) * 16)) & 0xffffu;
-      XLO[g * kXG + (c - 1)] = ok ? rlo : 0u;
-      XHI[g * kXG + (c - 1)] = ok ? rhi : mcount;
-    }
+    const int64_t g = (int64_t)u.rb0 * tc::BM + et;
+    if (g < nrows) lcnt[g] = lslot(S)[et];
   }
 };
+
 
 // Group each user's tail list by the exact-grid column of the screened score,
 // col(v) = #{j : x_j <= v} in 0..G (counting sort), and record the column
@@ -390,59 +362,131 @@ struct EpiXT {
 // overflowed lists are left as they are and marked unusable.
 constexpr int kGroupThreads = 256;
 
+// j(theta) = #{i < tau : t_i <= theta} when it is known to lie in [jlo, jhi]:
+// the thresholds inside the bracket are compared in FP64 (no division).
+__device__ __forceinline__ int exact_j_near(double theta, double fmin, double delta, int jlo,
+                                           int jhi) {
+  int g = jlo;
+  while (g < jhi && thr_at(fmin, delta, g) <= theta) ++g;
+  return g;
+}
+
+// One block per user: (1) the exact count table XLO/XHI on the kXG-column grid
+// from the user's list (every item above x_0 is in it; each entry's interval
+// uses the screen bound of its item tile), (2) the list grouped by the
+// kListG-column list grid with column offsets, (3) the largest entry bound.
+// An overflowed list gives the trivial table XLO = 0, XHI = m.
 __global__ void __launch_bounds__(kGroupThreads)
     k_list_group(int64_t n, uint2 *__restrict__ list, const int64_t *__restrict__ loff,
                  const uint32_t *__restrict__ lcap, const uint32_t *__restrict__ lcnt,
+                 const BinFP *__restrict__ lbin, const double *__restrict__ ldx, int G,
                  const BinFP *__restrict__ xbin, const double *__restrict__ xg0,
-                 const double *__restrict__ xdx, int G, const tc::RowBound *__restrict__ rowb,
-                 const tc::RowBound *__restrict__ tileb, int bn, tc::Gacc gacc, float gcan,
-                 uint16_t *__restrict__ coff, float *__restrict__ bmax) {
+                 uint32_t *__restrict__ XLO, uint32_t *__restrict__ XHI, uint32_t mcount,
+                 const tc::RowBound *__restrict__ rowb, const tc::RowBound *__restrict__ tileb,
+                 int bn, tc::Gacc gacc, float gcan, uint16_t *__restrict__ coff,
+                 float *__restrict__ bmax) {
   extern __shared__ unsigned char lsm[];
   uint2 *buf = (uint2 *)lsm;                                  // kListCapMax
   uint32_t *cnt = (uint32_t *)(buf + kListCapMax);            // G + 2
-  float *red = (float *)(cnt + G + 2);                        // kGroupThreads / 32
+  uint32_t *hlo = cnt + G + 2;                                // kXG + 1
+  uint32_t *hhi = hlo + kXG + 1;                              // kXG + 1
+  uint32_t *wsum = hhi + kXG + 1;                             // kGroupThreads / 32
+  float *red = (float *)(wsum + kGroupThreads / 32);          // kGroupThreads / 32
   uint16_t *cols = (uint16_t *)(red + kGroupThreads / 32);    // kListCapMax
   const int64_t u = blockIdx.x;
   const uint32_t L = lcnt[u];
   uint16_t *co = coff + u * (G + 2);
-  if (L > lcap[u]) {  // overflow (or lists disabled with L > 0)
+  if (L > lcap[u]) {  // overflow: the list is incomplete
     if (threadIdx.x == 0) bmax[u] = INFINITY;
+    for (int c = threadIdx.x; c < kXG; c += blockDim.x) {
+      XLO[u * kXG + c] = 0u;
+      XHI[u * kXG + c] = mcount;
+    }
     return;
   }
   for (int c = threadIdx.x; c < G + 2; c += blockDim.x) cnt[c] = 0;
+  for (int c = threadIdx.x; c <= kXG; c += blockDim.x) {
+    hlo[c] = 0;
+    hhi[c] = 0;
+  }
   __syncthreads();
   uint2 *row = list + loff[u];
-  const BinFP bf = xbin[u];
-  const double g0 = xg0[u], dx = xdx[u];
+  const BinFP lb = lbin[u], xb = xbin[u];
+  const double g0 = xg0[u], dx = ldx[u];
   const tc::RowBound ru = rowb[u];
   float bm = 0.0f;
   for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-    uint2 e = row[i];
-    float v = __uint_as_float(e.y);
+    const uint2 e = row[i];
+    const float v = __uint_as_float(e.y);
+    const float b = tc::screen_bound_tc(ru, tileb[e.x / bn], gacc, gcan);
+    bm = fmaxf(bm, b);
+    int clo, chi;
+    bin_interval(xb, g0, kXG, __fsub_rd(v, b), __fadd_ru(v, b), clo, chi);
+    if (chi > 0) {
+      atomicAdd(&hlo[clo], 1u);
+      atomicAdd(&hhi[chi], 1u);
+    }
     int jlo, jhi;
-    bin_interval(bf, g0, G, v, v, jlo, jhi);
-    int col = jlo == jhi ? jlo : exact_j((double)v, g0, dx, G);
+    bin_interval(lb, g0, G, v, v, jlo, jhi);
+    const int col = jlo == jhi ? jlo : exact_j_near((double)v, g0, dx, jlo, jhi);
     buf[i] = e;
     cols[i] = (uint16_t)col;
     atomicAdd(&cnt[col], 1u);
-    bm = fmaxf(bm, tc::screen_bound_tc(ru, tileb[e.x / bn], gacc, gcan));
   }
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bm;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = bm;
   __syncthreads();
-  if (threadIdx.x == 0) {  // exclusive prefix over G + 1 columns
-    uint32_t run = 0;
-    for (int c = 0; c <= G; ++c) {
-      uint32_t t = cnt[c];
-      cnt[c] = run;
-      co[c] = (uint16_t)run;
-      run += t;
+  if (wid == 0) {
+    // count table: XLO[c-1] = sum_{c' >= c} hlo[c'], c = 1..kXG (4 columns per lane)
+    constexpr int kPer = kXG / 32;
+    uint32_t sl = 0, sh = 0;
+    for (int t = 0; t < kPer; ++t) {
+      sl += hlo[1 + lane * kPer + t];
+      sh += hhi[1 + lane * kPer + t];
     }
-    co[G + 1] = (uint16_t)run;
-    float m2 = 0.0f;
-    for (int w = 0; w < kGroupThreads / 32; ++w) m2 = fmaxf(m2, red[w]);
-    bmax[u] = m2;
+    uint32_t al = sl, ah = sh;  // inclusive suffix over lanes >= lane
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t xl = __shfl_down_sync(0xffffffffu, al, o);
+      const uint32_t xh = __shfl_down_sync(0xffffffffu, ah, o);
+      if (lane + o < 32) { al += xl; ah += xh; }
+    }
+    uint32_t rl = al - sl, rh = ah - sh;  // sums over columns above this lane's block
+    for (int t = kPer - 1; t >= 0; --t) {
+      const int c = 1 + lane * kPer + t;
+      rl += hlo[c];
+      rh += hhi[c];
+      XLO[u * kXG + (c - 1)] = rl;
+      XHI[u * kXG + (c - 1)] = rh;
+    }
+    if (lane == 0) {
+      float m2 = 0.0f;
+      for (int w = 0; w < kGroupThreads / 32; ++w) m2 = fmaxf(m2, red[w]);
+      bmax[u] = m2;
+    }
   }
+  // list grid: exclusive prefix over the G + 1 columns, a contiguous run per thread
+  const int per = (G + 1 + kGroupThreads - 1) / kGroupThreads;
+  const int c0 = threadIdx.x * per, c1 = min(G + 1, c0 + per);
+  uint32_t part = 0;
+  for (int c = c0; c < c1; ++c) part += cnt[c];
+  uint32_t incl = part;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  uint32_t base = 0;
+  for (int w = 0; w < wid; ++w) base += wsum[w];
+  uint32_t run = base + incl - part;
+  for (int c = c0; c < c1; ++c) {
+    const uint32_t t = cnt[c];
+    cnt[c] = run;
+    co[c] = (uint16_t)run;
+    run += t;
+  }
+  if (threadIdx.x == kGroupThreads - 1) co[G + 1] = (uint16_t)run;
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
     uint32_t pos = atomicAdd(&cnt[cols[i]], 1u);
@@ -458,16 +502,17 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   idx->ptile_bn = bn;
   const int G = kListG;
   RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, G, idx->pmax, idx->ldx, idx->lbin, st));
-  size_t sm = sizeof(uint2) * kListCapMax + sizeof(uint32_t) * (G + 2) +
-              sizeof(float) * (kGroupThreads / 32) + sizeof(uint16_t) * kListCapMax;
+  size_t sm = sizeof(uint2) * kListCapMax + sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) +
+              sizeof(uint32_t) * (kGroupThreads / 32) + sizeof(float) * (kGroupThreads / 32) +
+              sizeof(uint16_t) * kListCapMax;
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
   {
     const int prof_slot = prof_begin("k_list_group", st);
     k_list_group<<<(unsigned)idx->n, kGroupThreads, sm, st>>>(
-        idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->lbin, idx->xg0, idx->ldx, G,
-        idx->Ut.rb3, idx->ptile3, bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff,
-        idx->xbmax);
+        idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->lbin, idx->ldx, G,
+        idx->xbin, idx->xg0, idx->XLO, idx->XHI, (uint32_t)idx->m, idx->Ut.rb3, idx->ptile3, bn,
+        tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff, idx->xbmax);
     prof_end(prof_slot, st, 0.0);
   }
   note_launch();
@@ -494,8 +539,7 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   EpiXT e;
   e.nrows = n; e.ncols = m; e.bn = BN; e.rowb = Ut.rb3; e.tileb = tb;
   e.gacc = tc_gacc(Ut.kp, 1); e.gcan = tc_gcan(idx->d);
-  e.xbin = idx->xbin; e.xg0 = idx->xg0; e.g0f = g0f; e.XLO = idx->XLO; e.XHI = idx->XHI;
-  e.mcount = (uint32_t)m;
+  e.g0f = g0f;
   e.list = idx->xlist; e.loff = idx->xloff; e.lcapv = idx->xlcap; e.lcnt = idx->xlcnt;
   static_assert(tc::screen_smem_bytes<BN, 2, EpiXT>() <= 232448, "exact-table smem");
   rkr_status s = launch_screen<BN, 2>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
