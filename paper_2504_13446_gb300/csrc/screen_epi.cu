@@ -360,7 +360,7 @@ struct EpiXT {
 // col(v) = #{j : x_j <= v} in 0..G (counting sort), and record the column
 // offsets and the largest screen bound of the entries.  One CTA per user;
 // overflowed lists are left as they are and marked unusable.
-constexpr int kGroupThreads = 256;
+constexpr int kGroupThreads = 1024;
 
 // j(theta) = #{i < tau : t_i <= theta} when it is known to lie in [jlo, jhi]:
 // the thresholds inside the bracket are compared in FP64 (no division).
@@ -541,8 +541,8 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   e.gacc = tc_gacc(Ut.kp, 1); e.gcan = tc_gcan(idx->d);
   e.g0f = g0f;
   e.list = idx->xlist; e.loff = idx->xloff; e.lcapv = idx->xlcap; e.lcnt = idx->xlcnt;
-  static_assert(tc::screen_smem_bytes<BN, 2, EpiXT>() <= 232448, "exact-table smem");
-  rkr_status s = launch_screen<BN, 2>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
+  static_assert(tc::screen_smem_bytes<BN, 4, EpiXT>() <= 232448, "exact-table smem");
+  rkr_status s = launch_screen<BN, 4>(Ut, Pt, 1, row_schedule(n, m, BN), e, flags, st);
   if (s == RKR_OK) s = tc_sort_lists(idx, tb, BN, st);
   int hf[2] = {0, 0};
   cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
