@@ -714,7 +714,9 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_CUDA(cudaEventRecord(ev[3], st));
   // sampled rank table
   RKR_TRY(dalloc(&idx->N, (size_t)n * tau));
-  {
+  bool table_done = false;
+  RKR_TRY(tc_rank_table(idx, idx->Ut, st, &table_done));
+  if (!table_done) {
     size_t sm = sizeof(float) * ((size_t)d * (kTableTile + 1) + (size_t)kTableWarps * d) +
                 sizeof(uint32_t) * (size_t)kTableWarps * (tau + 1) +
                 sizeof(int32_t) * kTableWarps * kTableQueue;

@@ -70,6 +70,39 @@ static __device__ __noinline__ double canon_dot_slow(const float *__restrict__ a
   return canon_dot(a, b, d);
 }
 
+// Interval [lo, hi] that holds the canonical score s(a, b).  A compensated FP32
+// dot product (Ogita, Rump and Oishi's Dot2: each product split exactly by an
+// FMA, each addition by an error-free two-sum, the low parts summed apart)
+// satisfies |(p + s) - a.b| <= gamma_d^2 sum|a_k b_k| (gamma_d = d u / (1 - d u),
+// u = 2^-24); the final p + s is formed in FP64 (error <= 2^-53 |p + s|) and the
+// canonical sum differs from a.b by at most gamma'_d sum|a_k b_k| with the FP64
+// unit 2^-53.  Intrinsics keep the compiler from fusing or reordering the steps.
+// A tiny absolute term covers products in the subnormal range.
+__device__ __forceinline__ void dot2_interval(const float *__restrict__ a,
+                                              const float *__restrict__ b, int d, double &lo,
+                                              double &hi) {
+  float p = 0.0f, s = 0.0f, asum = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    const float x = a[k], y = b[k];
+    const float h = __fmul_rn(x, y);
+    const float r = __fmaf_rn(x, y, -h);
+    const float t = __fadd_rn(p, h);
+    const float z = __fsub_rn(t, p);
+    const float e = __fadd_rn(__fsub_rn(p, __fsub_rn(t, z)), __fsub_rn(h, z));
+    p = t;
+    s = __fadd_rn(s, __fadd_rn(e, r));
+    asum = __fadd_ru(asum, fabsf(h));
+  }
+  const double res = (double)p + (double)s;
+  const double g = (double)d * 0x1p-24;
+  const double gam = g / (1.0 - g);
+  const double gc = (double)d * 0x1p-53 / (1.0 - (double)d * 0x1p-53);
+  const double E = ((gam * gam + gc) * (double)asum * (1.0 + 0x1p-20) + fabs(res) * 0x1p-52 +
+                    (double)d * 0x1p-140) * (1.0 + 0x1p-20);
+  lo = res - E;
+  hi = res + E;
+}
+
 // Threshold t_{j+1} (0-based i = j): f_min + i * delta, delta = (f_max - f_min) / (tau - 1),
 // each operation rounded to double in that order (Section 4.2, step 2).
 __device__ __forceinline__ double thr_at(double fmin, double delta, int i) {

@@ -117,6 +117,10 @@ struct ThetaArgs {
 };
 rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
                          const ThetaArgs &a, int split, int *err, cudaStream_t st);
+// Rank table (Alg. 1 step 3, Eq. 1) on the tensor cores; *done stays false when the
+// scratch could not be allocated or its queue overflowed (the caller then runs the
+// CUDA-core kernel).
+rkr_status tc_rank_table(const rkr_index *idx, const TcSide &Ut, cudaStream_t st, bool *done);
 // Entries (user, query, screened score) recorded by the skim screen: region r
 // (one per CTA of the launch) holds cnt[r] entries from r * rcap on; a count
 // above rcap means the region overflowed and dropped the excess.

@@ -474,13 +474,24 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   const int64_t u = cu[i];
   if (u < 0) { cu_fb[i] = -1; return; }
   const float *uu = U + u * d;
-  const double theta = canon_dot(uu, Q + (int64_t)cq[i] * d, d);
+  const float *qq = Q + (int64_t)cq[i] * d;
+  // u.q as an interval [tlo, thi] from the compensated product; the canonical
+  // value is formed only where the interval cannot settle a comparison
+  double tlo, thi;
+  dot2_interval(uu, qq, d, tlo, thi);
+  double theta = 0.0;
+  bool exact = false;
   const uint32_t L = xlcnt[u];
-  if (L > xlcap[u] || theta < xg0[u]) {
-    // bounds from the exact count table at the exact bin of u.q
-    const int j = exact_j(theta, xg0[u], xdx[u], GX);
-    ccount[i] = j >= 1 ? XHI[u * GX + j - 1] : mtop;
-    clb[i] = j < GX ? XLO[u * GX + j] : 0u;
+  if (L <= xlcap[u] && tlo < xg0[u] && thi >= xg0[u]) {
+    theta = canon_dot(uu, qq, d);
+    tlo = thi = theta;
+    exact = true;
+  }
+  if (L > xlcap[u] || thi < xg0[u]) {
+    // bounds from the exact count table at the bins of both ends of u.q
+    const int jl = exact_j(tlo, xg0[u], xdx[u], GX), jh = exact_j(thi, xg0[u], xdx[u], GX);
+    ccount[i] = jl >= 1 ? XHI[u * GX + jl - 1] : mtop;
+    clb[i] = jh < GX ? XLO[u * GX + jh] : 0u;
     cu_fb[i] = (int32_t)u;
     atomicAdd(&stat[0], 1ull);
     return;
@@ -491,28 +502,31 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   const uint16_t *co = xcoff + u * (G + 2);
   const double B = (double)xbmax[u];
   const double g0 = xg0[u], dx = ldx[u];
-  // columns c >= chi have v >= x_{c-1} > theta + B: every entry is above theta
-  const int chi = exact_j(__dadd_ru(theta, B), g0, dx, G) + 1;
-  // columns c < clo have v < x_c <= theta - B: no entry is above theta
-  const int clo = exact_j(__dsub_rd(theta, B), g0, dx, G);
+  // columns c >= chi have v >= x_{c-1} > u.q + B: every entry is above u.q
+  const int chi = exact_j(__dadd_ru(thi, B), g0, dx, G) + 1;
+  // columns c < clo have v < x_c <= u.q - B: no entry is above u.q
+  const int clo = exact_j(__dsub_rd(tlo, B), g0, dx, G);
   uint32_t above = L - (uint32_t)co[chi];
   const tc::RowBound ru = rb3[u];
-  const float cfac = screen_cfac(d);
   const int32_t self = qself[cq[i]];
   for (int e = co[clo]; e < (int)co[chi]; ++e) {
     const uint32_t p = row[e].x;
     if ((int32_t)p == self) continue;  // the query's own item: s(u,p) = u.q, not above
     const float v = __uint_as_float(row[e].y);
     const float b = tc::screen_bound_tc(ru, ptile[p / pbn], gacc, gcan);
-    if ((double)__fsub_rd(v, b) > theta) { ++above; continue; }
-    if ((double)__fadd_ru(v, b) <= theta) continue;
+    if ((double)__fsub_rd(v, b) > thi) { ++above; continue; }
+    if ((double)__fadd_ru(v, b) <= tlo) continue;
     const float *pp = Ps + (int64_t)p * d;
-    float acc = 0.0f;
-    for (int k = 0; k < d; ++k) acc = fmaf(uu[k], pp[k], acc);
-    const float b32 = screen_bound(cfac, unrm[u], pnrm_s[p]);
-    if ((double)__fsub_rd(acc, b32) > theta) { ++above; continue; }
-    if ((double)__fadd_ru(acc, b32) <= theta) continue;
+    double slo, shi;
+    dot2_interval(uu, pp, d, slo, shi);
+    if (slo > thi) { ++above; continue; }
+    if (shi <= tlo) continue;
     atomicAdd(&stat[1], 1ull);
+    if (!exact) {
+      theta = canon_dot(uu, qq, d);
+      tlo = thi = theta;
+      exact = true;
+    }
     if (canon_dot(uu, pp, d) > theta) ++above;
   }
   ccount[i] = above;

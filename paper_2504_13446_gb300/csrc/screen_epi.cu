@@ -43,6 +43,17 @@ struct PairQueue {
     if (i < cap) items[i] = make_int2(a, b);
     else atomicExch(overflow, 1);
   }
+  // push from every lane active at this point with one atomic per group
+  __device__ __forceinline__ void push_agg(int a, int b) const {
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    const unsigned long long i = base + __popc(act & ((1u << lane) - 1u));
+    if (i < cap) items[i] = make_int2(a, b);
+    else atomicExch(overflow, 1);
+  }
 };
 
 }  // namespace
@@ -856,6 +867,178 @@ rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const
   if (pass == 1) return theta_launch<1>(idx, Ut, Qt, a, split, err, st);
   if (pass == 2) return theta_launch<2>(idx, Ut, Qt, a, split, err, st);
   return theta_launch<3>(idx, Ut, Qt, a, split, err, st);
+}
+
+// ============================================================ rank table
+
+// Alg. 1 step 3 / Eq. 1 on the tensor cores: for every (user, sampled row) the
+// number of thresholds the score exceeds, c = #{j : s(u,p) > t_j}, decided by
+// the split screen with the pair's own bound when its bin interval is a single
+// value; W[u][c] += weight of the sample with a global reduction.  Undecided
+// pairs are queued for the canonical FP64 evaluation.
+struct EpiTable {
+  static const char *name() { return "k_screen<EpiTable>"; }
+  struct Thread {
+    int64_t u;
+    tc::RowBound ru;
+    BinFP bf;
+    double fm;
+  };
+  static constexpr size_t kSmem = 0;
+  int64_t nrows, ncols;
+  int tau;
+  const tc::RowBound *rowb, *colb;
+  tc::Gacc gacc;
+  float gcan;
+  const BinFP *binfp;
+  const double *fmin;
+  const uint32_t *w;        // weight of each sampled row
+  uint32_t *W;              // n x (tau + 1)
+  PairQueue q;
+  __device__ __forceinline__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ __forceinline__ void tile_begin(char *, int rb, int, int r, int, Thread &ts) const {
+    ts.u = (int64_t)rb * tc::BM + r;
+    if (ts.u < nrows) {
+      ts.ru = rowb[ts.u];
+      ts.bf = binfp[ts.u];
+      ts.fm = fmin[ts.u];
+    }
+  }
+  __device__ __forceinline__ void chunk(char *, int, int ct, int, int col, uint32_t,
+                                        const float (&v)[32], Thread &ts) const {
+    if (ts.u >= nrows) return;
+    const int64_t c0 = (int64_t)ct * kTableBN + col;
+    uint32_t *Wu = W + ts.u * (tau + 1);
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      const int64_t p = c0 + j;
+      if (p >= ncols) break;
+      const float b = tc::screen_bound_tc(ts.ru, colb[p], gacc, gcan);
+      int jlo, jhi;
+      bin_interval(ts.bf, ts.fm, tau, __fsub_rd(v[j], b), __fadd_ru(v[j], b), jlo, jhi);
+      if (jlo == jhi) atomicAdd(&Wu[jlo], w[p]);
+      else q.push_agg((int)ts.u, (int)p);
+    }
+  }
+  __device__ __forceinline__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ __forceinline__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+  static constexpr int kTableBN = 256;
+};
+
+// Queued pairs: canonical score, its threshold count, weighted add.
+__global__ void k_table_resolve(const int2 *__restrict__ items,
+                                const unsigned long long *__restrict__ count,
+                                unsigned long long cap, const float *__restrict__ U,
+                                const float *__restrict__ S, int d,
+                                const double *__restrict__ fmin, const double *__restrict__ delta,
+                                int tau, const uint32_t *__restrict__ w, uint32_t *__restrict__ W) {
+  // c(s) = #{t_j < s} is non-decreasing in s: equal at both ends of an interval
+  // holding s(u,p) means it is decided
+  unsigned long long c = *count;
+  if (c > cap) c = cap;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int2 it = items[i];
+    const int64_t u = it.x;
+    const float *uu = U + u * d, *pp = S + (int64_t)it.y * d;
+    // the compensated interval decides almost every pair; canonical FP64 otherwise
+    double lo, hi;
+    dot2_interval(uu, pp, d, lo, hi);
+    int c;
+    const int clo = exact_c(lo, fmin[u], delta[u], tau), chi = exact_c(hi, fmin[u], delta[u], tau);
+    if (clo == chi) {
+      c = clo;
+    } else {
+      c = exact_c(canon_dot(uu, pp, d), fmin[u], delta[u], tau);
+    }
+    atomicAdd(&W[u * (tau + 1) + c], w[it.y]);
+  }
+}
+
+// N[u][j] = sum_{c > j} W[u][c], j < tau: one warp per user.
+__global__ void k_table_suffix(int64_t n, int tau, const uint32_t *__restrict__ W,
+                               uint32_t *__restrict__ N) {
+  const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (u >= n) return;
+  const uint32_t *Wu = W + u * (tau + 1);
+  const int chunk = (tau + 1 + 31) / 32;
+  const int c0 = lane * chunk, c1 = min(tau + 1, c0 + chunk);
+  uint32_t part = 0;
+  for (int c = c0; c < c1; ++c) part += Wu[c];
+  uint32_t incl = part;  // inclusive suffix over lanes >= lane
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_down_sync(0xffffffffu, incl, o);
+    if (lane + o < 32) incl += x;
+  }
+  uint32_t run = incl - part;
+  for (int c = c1 - 1; c >= c0; --c) {
+    run += Wu[c];
+    if (c >= 1) N[u * tau + (c - 1)] = run;
+  }
+}
+
+rkr_status tc_rank_table(const rkr_index *idx, const TcSide &Ut, cudaStream_t st, bool *done) {
+  *done = false;
+  const int64_t n = idx->n;
+  const int tau = idx->tau, nsamp = idx->nsamp;
+  TcSide St;
+  struct Guard {
+    TcSide *s;
+    ~Guard() { tc_free(*s); }
+  } g{&St};
+  RKR_TRY(tc_stage(idx->S, nsamp, idx->d, St, st));
+  uint32_t *W = nullptr;
+  int2 *qitems = nullptr;
+  unsigned long long *qcount = nullptr;
+  int *flags = nullptr;
+  const unsigned long long cap =
+      (unsigned long long)std::max<int64_t>(n * (int64_t)nsamp / 32, 1 << 16);
+  auto cleanup = [&]() {
+    for (void *p : {(void *)W, (void *)qitems, (void *)qcount, (void *)flags})
+      if (p) cudaFreeAsync(p, st);
+  };
+  if (cudaMallocAsync((void **)&W, sizeof(uint32_t) * (size_t)n * (tau + 1), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&qitems, sizeof(int2) * cap, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&qcount, sizeof(unsigned long long), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&flags, sizeof(int) * 2, st) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return RKR_OK;  // not enough memory for the scratch: the CUDA-core kernel runs instead
+  }
+  RKR_CUDA(cudaMemsetAsync(W, 0, sizeof(uint32_t) * (size_t)n * (tau + 1), st));
+  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
+  EpiTable e;
+  e.nrows = n; e.ncols = nsamp; e.tau = tau;
+  e.rowb = Ut.rb3; e.colb = St.rb3;
+  e.gacc = tc_gacc(Ut.kp, 1); e.gcan = tc_gcan(idx->d);
+  e.binfp = idx->binfp; e.fmin = idx->fmin; e.w = idx->sw; e.W = W;
+  e.q = PairQueue{qitems, qcount, cap, flags + 1};
+  constexpr int BN = EpiTable::kTableBN;
+  rkr_status s = launch_screen<BN, 4>(Ut, St, 1, row_schedule(n, nsamp, BN), e, flags, st);
+  if (s == RKR_OK) {
+    {
+      ProfScope prof("k_table_resolve", st);
+      k_table_resolve<<<8 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->S, idx->d,
+                                                      idx->fmin, idx->delta, tau, idx->sw, W);
+    }
+    note_launch();
+    {
+      ProfScope prof("k_table_suffix", st);
+      k_table_suffix<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(n, tau, W, idx->N);
+    }
+    note_launch();
+  }
+  int hf[2] = {0, 0};
+  cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
+  cudaError_t err = cudaStreamSynchronize(st);
+  cleanup();
+  if (err != cudaSuccess) return cuda_fail(err, "tc_rank_table");
+  RKR_TRY(s);
+  if (hf[0]) return fail(RKR_ETIMEOUT, "rank-table screen wait timed out (%d)", hf[0]);
+  *done = hf[1] == 0;  // a queue overflow leaves the table to the CUDA-core kernel
+  return RKR_OK;
 }
 
 // ================================================================== skim
