@@ -108,8 +108,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs():
-    w = synth.make_workload(WORKLOAD)
+def make_inputs(case="full"):
+    if case == "small":
+        # profiling case: 40k users, all 100k items, 2,000 queries; two of them shrunk to a
+        # tiny norm so that u.q lies mid-range for every user and the recount screen runs
+        w = synth.make_workload(WORKLOAD, n=40_000, nq=2000)
+        w.Q[:2] *= np.float32(1e-3)
+    else:
+        w = synth.make_workload(WORKLOAD)
     sizes = np.array([w.m // w.omega + (1 if l < w.m % w.omega else 0) for l in range(w.omega)])
     pos = synth.sample_positions(w.seed, sizes, w.s)
     return w, pos
@@ -132,7 +138,7 @@ def bench_ours(args):
     dist, rank, ws = _dist()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     peaks, peak_src = _load_peaks()
-    w, pos = make_inputs()
+    w, pos = make_inputs(args.case)
     U = torch.from_numpy(w.U).cuda()
     P = torch.from_numpy(w.P).cuda()
     Q = torch.from_numpy(w.Q).cuda()
@@ -170,6 +176,12 @@ def bench_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
 
+    if args.case == "small":
+        if rank == 0:
+            print(json.dumps({"case": "small (profiling)", "ms_per_step": ms,
+                              "kernels_ms_per_step": {kk: round(v[1] / args.steps, 3)
+                                                      for kk, v in kernels.items()}}))
+        return
     # end to end through the C ABI with host buffers
     t0 = time.perf_counter()
     a_h, e_h, _ = run_step(rkr, w.U, w.P, w.Q, w.k.astype(np.int32), pos, w, device=False)
@@ -305,6 +317,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: a 40k-user profiling case (no CPU baseline, no e2e)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
