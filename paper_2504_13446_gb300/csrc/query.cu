@@ -140,7 +140,8 @@ __global__ void k_resolve_approx(int64_t count, const int32_t *__restrict__ cu,
                                  const int32_t *__restrict__ cq, const float *__restrict__ U,
                                  const float *__restrict__ Q, int d,
                                  const double *__restrict__ fmin,
-                                 const double *__restrict__ delta, const uint32_t *__restrict__ N,
+                                 const double *__restrict__ delta, const BinFP *__restrict__ bf,
+                                 const uint32_t *__restrict__ N,
                                  int tau, uint32_t top, double *__restrict__ th,
                                  int32_t *__restrict__ cj, uint32_t *__restrict__ nlo,
                                  uint32_t *__restrict__ nup) {
@@ -149,9 +150,23 @@ __global__ void k_resolve_approx(int64_t count, const int32_t *__restrict__ cu,
   int64_t u = cu[i];
   if (u < 0) return;  // unused slot at the end of a query's segment
   int q = cq[i];
-  double theta = canon_dot(U + u * d, Q + (int64_t)q * d, d);
-  int j = exact_j(theta, fmin[u], delta[u], tau);
-  th[i] = theta;
+  const float *uu = U + u * d, *qq = Q + (int64_t)q * d;
+  // j from the compensated interval of u.q when both ends fall in one bin; the
+  // canonical u.q otherwise.  u.q itself is formed later, only for the users
+  // whose step-3 estimate is needed (NaN marks it as not yet formed).
+  double tlo, thi;
+  dot2_interval(uu, qq, d, tlo, thi);
+  int jlo, jhi;
+  bin_interval(bf[u], fmin[u], tau, __double2float_rd(tlo), __double2float_ru(thi), jlo, jhi);
+  int j;
+  if (jlo == jhi) {
+    j = jlo;
+    th[i] = __longlong_as_double(0x7ff8000000000000ll);
+  } else {
+    const double theta = canon_dot(uu, qq, d);
+    j = exact_j(theta, fmin[u], delta[u], tau);
+    th[i] = theta;
+  }
   cj[i] = j;
   nlo[i] = j < tau ? N[u * tau + j] : 0u;
   nup[i] = j >= 1 ? N[u * tau + j - 1] : top;
@@ -174,8 +189,10 @@ __device__ __forceinline__ double interp_est(double theta, int j, uint32_t nlo, 
 struct ApproxCand {
   const int32_t *uid;
   const uint32_t *nlo, *nup;
-  const double *th;
+  double *th;          // canonical u.q, NaN until formed
   const int32_t *j;
+  const float *U, *Q;  // rows, for forming u.q on demand
+  int d;
 };
 
 constexpr int kSelThreads = 256;
@@ -206,11 +223,17 @@ __global__ void __launch_bounds__(kSelThreads)
   }
   const int32_t *uid = C.uid + base;
   const uint32_t *nlo = C.nlo + base, *nup = C.nup + base;
-  const double *th = C.th + base;
+  double *th = C.th + base;
   const int32_t *cj = C.j + base;
+  const float *qrow = C.Q + (int64_t)q * C.d;
   auto est_of = [&](int64_t i) {
     int32_t u = uid[i];
-    return interp_est(th[i], cj[i], nlo[i], nup[i], fmin[u], delta[u], tau, s);
+    double t = th[i];
+    if (t != t) {  // not formed yet: the canonical u.q, kept for later calls
+      t = canon_dot(C.U + (int64_t)u * C.d, qrow, C.d);
+      th[i] = t;
+    }
+    return interp_est(t, cj[i], nlo[i], nup[i], fmin[u], delta[u], tau, s);
   };
   // Step 1: k-th smallest lower and upper bound numerators.
   uint64_t Rlo = block_kth(cnt, (uint64_t)k, 32,
@@ -1329,7 +1352,7 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
       {
         const int prof_slot = prof_begin("k_resolve_approx", st);
         k_resolve_approx<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
-            cnt, cu, cq, idx->U, qc.Qd, idx->d, idx->fmin, idx->delta, idx->N, idx->tau,
+            cnt, cu, cq, idx->U, qc.Qd, idx->d, idx->fmin, idx->delta, qc.bf, idx->N, idx->tau,
             (uint32_t)(idx->m * idx->s), th, cj, nlo, nup);
         prof_end(prof_slot, st, 0.0);
         note_launch();
@@ -1338,7 +1361,7 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     }
     ms_res += t3.stop();
     Timer t4(st);
-    ApproxCand C{cu, nlo, nup, th, cj};
+    ApproxCand C{cu, nlo, nup, th, cj, idx->U, qc.Qd, idx->d};
     size_t sm = sizeof(SortEnt) * kMaxK;
     RKR_CUDA(cudaFuncSetAttribute(k_select_approx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));

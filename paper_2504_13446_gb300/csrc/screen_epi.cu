@@ -60,77 +60,18 @@ struct PairQueue {
 
 // ============================================================== f-bounds
 
-struct EpiFbA {
-  static const char *name() { return "k_screen<EpiFbA>"; }
+// f_min / f_max in one single-product pass.  Each thread keeps, over the
+// columns it has seen, the largest lower end (mxlo) and the smallest upper end
+// (mnhi) of the screened scores; an item is queued when its upper end reaches
+// mxlo or its lower end reaches mnhi after the chunk is folded in.  The item
+// holding the exact maximum is always queued: when it is seen, mxlo is at most
+// the maximum, which is at most its upper end (and likewise for the minimum).
+// A short seeding launch over the first (largest-norm) columns starts every
+// thread at near-final extremes, so few items are queued.
+struct EpiFb {
+  static const char *name() { return "k_screen<EpiFb>"; }
   struct Thread {
-    float mx, mn, b;
-    float mxlo, mnhi;
-  };
-  static constexpr size_t kSmem = 2 * 128 * sizeof(float);
-  int64_t nrows, ncols;
-  int bn;
-  const tc::RowBound *rowb, *tileb;
-  tc::Gacc gacc;
-  float gcan;
-  float *maxlo, *minhi;
-  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &ts) const {
-    ts.mxlo = -INFINITY;
-    ts.mnhi = INFINITY;
-  }
-  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
-    int64_t row = (int64_t)rb * tc::BM + r;
-    ts.b = row < nrows ? tc::screen_bound_tc(rowb[row], tileb[ct], gacc, gcan) : 0.0f;
-    ts.mx = -INFINITY;
-    ts.mn = INFINITY;
-  }
-  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
-                        Thread &ts) const {
-    const int64_t c0 = (int64_t)ct * bn + col;
-    if (c0 + 32 <= ncols) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        ts.mx = fmaxf(ts.mx, v[j]);
-        ts.mn = fminf(ts.mn, v[j]);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < ncols) {
-          ts.mx = fmaxf(ts.mx, v[j]);
-          ts.mn = fminf(ts.mn, v[j]);
-        }
-    }
-  }
-  __device__ void tile_end(char *, int, int, int, int, Thread &ts) const {
-    ts.mxlo = fmaxf(ts.mxlo, __fsub_rd(ts.mx, ts.b));
-    ts.mnhi = fminf(ts.mnhi, __fadd_ru(ts.mn, ts.b));
-  }
-  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &ts) const {
-    float *sm = (float *)S;
-    const int r = et & 127;  // thread et handles row (quarter, lane) mapping below
-    (void)r;
-    // rows: epilogue thread et -> warp (et>>5)+2, quarter ((et>>5)+2)&3, half (et>>5)>>2
-    const int w = (et >> 5) + 2, lane = et & 31;
-    const int row = (w & 3) * 32 + lane, half = (et >> 5) >> 2;
-    if (half == 1) {
-      sm[row] = ts.mxlo;
-      sm[128 + row] = ts.mnhi;
-    }
-    tc::epi_sync();
-    if (half == 0) {
-      int64_t g = (int64_t)u.rb0 * tc::BM + row;
-      if (g < nrows) {
-        maxlo[g] = fmaxf(ts.mxlo, sm[row]);
-        minhi[g] = fminf(ts.mnhi, sm[128 + row]);
-      }
-    }
-  }
-};
-
-struct EpiFbB {
-  static const char *name() { return "k_screen<EpiFbB>"; }
-  struct Thread {
-    float tmax, tmin;
+    float b, mxlo, mnhi;
     int64_t row;
   };
   static constexpr size_t kSmem = 0;
@@ -139,38 +80,80 @@ struct EpiFbB {
   const tc::RowBound *rowb, *tileb;
   tc::Gacc gacc;
   float gcan;
-  const float *maxlo, *minhi;
   PairQueue q;
-  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
-  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
-    ts.row = (int64_t)rb * tc::BM + r;
-    if (ts.row < nrows) {
-      float b = tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan);
-      // s_hat >= tmax is implied by s_hat + b >= maxlo (and likewise for the minimum)
-      ts.tmax = __fsub_rd(maxlo[ts.row], b);
-      ts.tmin = __fadd_ru(minhi[ts.row], b);
-    } else {
-      ts.tmax = INFINITY;
-      ts.tmin = -INFINITY;
+  const float2 *seed;   // per row: (largest lower end, smallest upper end) to start from, or null
+  float2 *seed_out;     // seeding launch: per (row, column half) extremes, no queue
+  __device__ __forceinline__ void unit_begin(char *, const tc::Unit &u, int et,
+                                             Thread &ts) const {
+    ts.mxlo = -INFINITY;
+    ts.mnhi = INFINITY;
+    if (seed) {
+      const int w = (et >> 5) + 2, lane = et & 31;
+      const int64_t row = (int64_t)u.rb0 * tc::BM + (w & 3) * 32 + lane;
+      if (row < nrows) {
+        const float2 a = seed[2 * row], b = seed[2 * row + 1];
+        ts.mxlo = fmaxf(a.x, b.x);
+        ts.mnhi = fminf(a.y, b.y);
+      }
     }
   }
-  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
-                        Thread &ts) const {
+  __device__ __forceinline__ void tile_begin(char *, int rb, int ct, int r, int,
+                                             Thread &ts) const {
+    ts.row = (int64_t)rb * tc::BM + r;
+    ts.b = ts.row < nrows ? tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan) : 0.0f;
+  }
+  __device__ __forceinline__ void chunk(char *, int, int ct, int, int col, uint32_t,
+                                        const float (&v)[32], Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
+    const int64_t left = ncols - c0;
+    uint32_t keep = left >= 32 ? 0xffffffffu : left <= 0 ? 0u : (1u << left) - 1u;
+    if (ts.row >= nrows) keep = 0;  // the warp stays together for the reservation below
+    float mx = -INFINITY, mn = INFINITY;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const bool in = (keep >> j) & 1u;
+      mx = fmaxf(mx, in ? v[j] : -INFINITY);
+      mn = fminf(mn, in ? v[j] : INFINITY);
+    }
+    ts.mxlo = fmaxf(ts.mxlo, __fsub_rd(mx, ts.b));
+    ts.mnhi = fminf(ts.mnhi, __fadd_ru(mn, ts.b));
+    if (seed_out) return;
+    // v + b >= mxlo  <=  v >= mxlo - b rounded down (and likewise for the minimum)
+    const float tmax = __fsub_rd(ts.mxlo, ts.b), tmin = __fadd_ru(ts.mnhi, ts.b);
     uint32_t mask = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) mask |= (v[j] >= ts.tmax || v[j] <= ts.tmin ? 1u : 0u) << j;
-    const int64_t left = ncols - c0;
-    if (left < 32) mask &= left <= 0 ? 0u : (1u << left) - 1u;
+    for (int j = 0; j < 32; ++j) mask |= (v[j] >= tmax || v[j] <= tmin ? 1u : 0u) << j;
+    mask &= keep;
+    if (!__any_sync(0xffffffffu, mask != 0u)) return;
+    // one queue reservation per warp and chunk
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(q.count, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)(incl - cnt);
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      push((int)ts.row, (int)(c0 + j));
+      if (base < q.cap) q.items[base] = make_int2((int)ts.row, (int)(c0 + j));
+      else atomicExch(q.overflow, 1);
+      ++base;
     }
   }
-  __device__ __forceinline__ void push(int row, int c) const { q.push(row, c); }
-  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
-  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ __forceinline__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ __forceinline__ void unit_end(char *, const tc::Unit &u, int et, Thread &ts) const {
+    if (!seed_out) return;
+    const int w = (et >> 5) + 2, lane = et & 31;
+    const int64_t row = (int64_t)u.rb0 * tc::BM + (w & 3) * 32 + lane;
+    if (row < nrows) seed_out[2 * row + ((et >> 5) >> 2)] = make_float2(ts.mxlo, ts.mnhi);
+  }
 };
 
 __global__ void k_fb_init(int64_t n, unsigned long long *kmax, unsigned long long *kmin) {
@@ -180,19 +163,48 @@ __global__ void k_fb_init(int64_t n, unsigned long long *kmax, unsigned long lon
   kmin[i] = ~0ull;
 }
 
-__global__ void k_fb_resolve(const int2 *__restrict__ items, const unsigned long long *count,
+// Queued items, first pass: per user the largest lower end and the smallest
+// upper end of the compensated intervals holding the canonical scores.
+__global__ void k_fb_bracket(const int2 *__restrict__ items, const unsigned long long *count,
                              unsigned long long cap, const float *__restrict__ U,
                              const float *__restrict__ Ps, int d,
-                             unsigned long long *kmax, unsigned long long *kmin) {
+                             unsigned long long *__restrict__ kmaxlo,
+                             unsigned long long *__restrict__ kminhi,
+                             double2 *__restrict__ ival) {
   unsigned long long c = *count;
   if (c > cap) c = cap;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    int2 it = items[i];
-    double s = canon_dot(U + (int64_t)it.x * d, Ps + (int64_t)it.y * d, d);
-    uint64_t k = dkey_signed(s);
-    atomicMax(&kmax[it.x], (unsigned long long)k);
-    atomicMin(&kmin[it.x], (unsigned long long)k);
+    const int2 it = items[i];
+    double lo, hi;
+    dot2_interval(U + (int64_t)it.x * d, Ps + (int64_t)it.y * d, d, lo, hi);
+    ival[i] = make_double2(lo, hi);
+    atomicMax(&kmaxlo[it.x], (unsigned long long)dkey_signed(lo));
+    atomicMin(&kminhi[it.x], (unsigned long long)dkey_signed(hi));
+  }
+}
+
+// Second pass: only items whose interval reaches the bracket can hold an
+// extreme; those get the canonical score.
+__global__ void k_fb_resolve(const int2 *__restrict__ items, const unsigned long long *count,
+                             unsigned long long cap, const float *__restrict__ U,
+                             const float *__restrict__ Ps, int d,
+                             const unsigned long long *__restrict__ kmaxlo,
+                             const unsigned long long *__restrict__ kminhi,
+                             const double2 *__restrict__ ival, unsigned long long *kmax,
+                             unsigned long long *kmin) {
+  unsigned long long c = *count;
+  if (c > cap) c = cap;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < c;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int2 it = items[i];
+    const float *uu = U + (int64_t)it.x * d, *pp = Ps + (int64_t)it.y * d;
+    const double lo = ival[i].x, hi = ival[i].y;
+    const bool maxc = dkey_signed(hi) >= kmaxlo[it.x], minc = dkey_signed(lo) <= kminhi[it.x];
+    if (!maxc && !minc) continue;
+    const uint64_t k = dkey_signed(canon_dot(uu, pp, d));
+    if (maxc) atomicMax(&kmax[it.x], (unsigned long long)k);
+    if (minc) atomicMin(&kmin[it.x], (unsigned long long)k);
   }
 }
 
@@ -209,7 +221,7 @@ __global__ void k_fb_finish(int64_t n, const unsigned long long *kmax,
   fmin[i] = dkey_inverse(kmin[i]);
 }
 
-// Exact canonical f_min / f_max per user from two tensor-core passes.
+// Exact canonical f_min / f_max per user from one tensor-core pass.
 // Returns RKR_EINTERNAL (after which the caller uses the CUDA-core scan) when
 // the candidate queue overflows.
 rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, double *fmin,
@@ -218,41 +230,56 @@ rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   const int64_t n = idx->n, m = idx->m;
   tc::RowBound *tb = nullptr;
   RKR_TRY(tc_tile_bounds(Pt, BN, 0, &tb, st));
-  float *maxlo, *minhi;
-  unsigned long long *kmax, *kmin, *qcount;
+  unsigned long long *kmax, *kmin, *kmaxlo, *kminhi, *qcount;
   int2 *qitems;
   int *flags;  // [0] screen error, [1] overflow, [2] missing extreme
-  const unsigned long long cap = std::max<int64_t>(8 * n, 1 << 16);
-  RKR_CUDA(cudaMallocAsync(&maxlo, sizeof(float) * n, st));
-  RKR_CUDA(cudaMallocAsync(&minhi, sizeof(float) * n, st));
+  const unsigned long long cap = std::max<int64_t>(64 * n, 1 << 16);
+  RKR_CUDA(cudaMallocAsync(&kmaxlo, sizeof(unsigned long long) * n, st));
+  RKR_CUDA(cudaMallocAsync(&kminhi, sizeof(unsigned long long) * n, st));
   RKR_CUDA(cudaMallocAsync(&kmax, sizeof(unsigned long long) * n, st));
   RKR_CUDA(cudaMallocAsync(&kmin, sizeof(unsigned long long) * n, st));
   RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
+  double2 *ival;
+  RKR_CUDA(cudaMallocAsync(&ival, sizeof(double2) * cap, st));
   RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 4, st));
   RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 4, st));
   const tc::Schedule sch = row_schedule(n, m, BN);
-  EpiFbA a;
+  EpiFb a;
   a.nrows = n; a.ncols = m; a.bn = BN; a.rowb = Ut.rb1; a.tileb = tb;
   a.gacc = tc_gacc(Ut.kp, 0); a.gcan = tc_gcan(idx->d);
-  a.maxlo = maxlo; a.minhi = minhi;
-  rkr_status s = launch_screen<BN, 4>(Ut, Pt, 0, sch, a, flags, st);
+  a.q = PairQueue{qitems, qcount, cap, flags + 1};
+  // seeding launch over the first columns (the largest norms), then the full pass
+  float2 *seed;
+  RKR_CUDA(cudaMallocAsync(&seed, sizeof(float2) * 2 * n, st));
+  TcSide head = Pt;
+  head.owned = false;
+  head.rows = std::min<int64_t>(m, 4 * BN);
+  EpiFb a0 = a;
+  a0.seed = nullptr;
+  a0.seed_out = seed;
+  a0.ncols = head.rows;
+  rkr_status s = launch_screen<BN, 4>(Ut, head, 0, row_schedule(n, head.rows, BN), a0, flags, st);
+  a.seed = seed;
+  a.seed_out = nullptr;
+  if (s == RKR_OK) s = launch_screen<BN, 4>(Ut, Pt, 0, sch, a, flags, st);
+  cudaFreeAsync(seed, st);
   if (s == RKR_OK) {
-    EpiFbB b;
-    b.nrows = n; b.ncols = m; b.bn = BN; b.rowb = Ut.rb1; b.tileb = tb;
-    b.gacc = a.gacc; b.gcan = a.gcan; b.maxlo = maxlo; b.minhi = minhi;
-    b.q = PairQueue{qitems, qcount, cap, flags + 1};
-    s = launch_screen<BN, 4>(Ut, Pt, 0, sch, b, flags, st);
-  }
-  if (s == RKR_OK) {
+    k_fb_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, kmaxlo, kminhi);
+    note_launch();
     k_fb_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, kmax, kmin);
     note_launch();
     {
-      const int prof_slot = prof_begin("k_fb_resolve", st);
-      k_fb_resolve<<<4 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
-                                                    kmax, kmin);
-      prof_end(prof_slot, st, 0.0);
+      ProfScope prof("k_fb_bracket", st);
+      k_fb_bracket<<<8 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
+                                                   kmaxlo, kminhi, ival);
+    }
+    note_launch();
+    {
+      ProfScope prof("k_fb_resolve", st);
+      k_fb_resolve<<<8 * sm_count(), 256, 0, st>>>(qitems, qcount, cap, idx->U, idx->Ps, idx->d,
+                                                   kmaxlo, kminhi, ival, kmax, kmin);
     }
     note_launch();
     k_fb_finish<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, kmax, kmin, fmin, fmax,
@@ -262,8 +289,8 @@ rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   int hf[4] = {0, 0, 0, 0};
   cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
-  for (void *p : {(void *)tb, (void *)maxlo, (void *)minhi, (void *)kmax, (void *)kmin,
-                  (void *)qcount, (void *)qitems, (void *)flags})
+  for (void *p : {(void *)tb, (void *)kmax, (void *)kmin, (void *)kmaxlo, (void *)kminhi,
+                  (void *)qcount, (void *)qitems, (void *)ival, (void *)flags})
     cudaFreeAsync(p, st);
   if (e != cudaSuccess) return cuda_fail(e, "tc_fbounds");
   RKR_TRY(s);
