@@ -146,6 +146,30 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
                             rkr_query_stats *stats, void *stream);
 
 /*
+ * rkr_query_exact_subsets / rkr_query_approx_subsets: the same queries with a
+ * user subset per query (a batched deployment form; the paper's queries use
+ * all of U).  For query i only users in
+ * subset_users[subset_offs[i] .. subset_offs[i+1]) are eligible; ranks are
+ * still taken over all of P (Def. 1), and R_low_k, R_up_k, U_c and the
+ * interpolation of Section 4.3 run over the subset.
+ *   subset_offs: nq + 1 int64, subset_offs[0] = 0, non-decreasing.
+ *   subset_users: int32 user indices in [0, n), in any order (duplicates allowed).
+ *   k[i] must not exceed the size of subset i (RKR_EINVAL otherwise).
+ *   Host or device arrays.  The subsets are held as one bitmap of n bits per
+ *   query on the device for the duration of the call.
+ */
+rkr_status rkr_query_exact_subsets(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   const int64_t *subset_offs, const int32_t *subset_users,
+                                   int32_t *out_users, int32_t *out_ranks,
+                                   rkr_query_stats *stats, void *stream);
+rkr_status rkr_query_approx_subsets(rkr_index *idx, const float *Q, int32_t nq,
+                                    const int32_t *k, const int64_t *subset_offs,
+                                    const int32_t *subset_users, double c, int32_t *out_users,
+                                    uint32_t *out_nlow, uint32_t *out_nup, double *out_est,
+                                    int32_t *out_case, int32_t *out_nc, rkr_query_stats *stats,
+                                    void *stream);
+
+/*
  * rkr_screen_scores: the tensor-core screen on its own, for validation and for
  * measuring the screen error.  For every pair (U_i, X_j) writes the screened
  * score out_s[i * mx + j] (BF16 inputs, FP32 accumulation on tcgen05; split = 1

@@ -24,7 +24,8 @@ import numpy as np
 from . import buildlib
 
 __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
-           "rkr_query_approx", "rkr_screen_scores", "rkr_screen_scores_static",
+           "rkr_query_approx", "rkr_query_exact_subsets", "rkr_query_approx_subsets",
+           "rkr_screen_scores", "rkr_screen_scores_static",
            "rkr_profile_start", "rkr_profile_stop", "EXPORTS"]
 
 _lock = threading.Lock()
@@ -79,6 +80,12 @@ def load() -> ctypes.CDLL:
         lib.rkr_query_approx.restype = I32
         lib.rkr_query_approx.argtypes = [V, V, I32, V, ctypes.c_double, V, V, V, V, V, V,
                                          ctypes.POINTER(QueryStats), V]
+        lib.rkr_query_exact_subsets.restype = I32
+        lib.rkr_query_exact_subsets.argtypes = [V, V, I32, V, V, V, V, V,
+                                                ctypes.POINTER(QueryStats), V]
+        lib.rkr_query_approx_subsets.restype = I32
+        lib.rkr_query_approx_subsets.argtypes = [V, V, I32, V, V, V, ctypes.c_double, V, V, V,
+                                                 V, V, V, ctypes.POINTER(QueryStats), V]
         lib.rkr_index_export.restype = I32
         lib.rkr_index_export.argtypes = [V, I32, V, I64]
         lib.rkr_index_info.restype = I32
@@ -193,8 +200,21 @@ def rkr_build(U, P, *, tau: int = 500, omega: int = 10, s: int = 100, fbounds: s
     return h
 
 
-def rkr_query_exact(index, Q, k, *, device: bool = False, stream=None):
-    """Exact reverse k-ranks: (users, ranks, offsets, stats) with per-query segments."""
+def _subsets_csr(subsets, nq):
+    """(offsets int64, users int32) from a list of nq per-query user-id arrays."""
+    if len(subsets) != nq:
+        raise ValueError("one subset per query")
+    off = np.zeros(nq + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(s_) for s_ in subsets])
+    users = (np.concatenate([np.asarray(s_, dtype=np.int32) for s_ in subsets])
+             if off[-1] else np.zeros(1, np.int32))
+    return off, np.ascontiguousarray(users)
+
+
+def rkr_query_exact(index, Q, k, *, subsets=None, device: bool = False, stream=None):
+    """Exact reverse k-ranks: (users, ranks, offsets, stats) with per-query segments.
+
+    subsets: optional list of per-query user-id arrays (rkr_query_exact_subsets)."""
     lib = load()
     nq, _ = _shape(Q)
     kk = np.broadcast_to(np.asarray(k if not _is_torch(k) else k.cpu().numpy(), np.int32), (nq,))
@@ -206,12 +226,20 @@ def rkr_query_exact(index, Q, k, *, device: bool = False, stream=None):
     pu, _ = _ptr(users, np.int32)
     pr, _ = _ptr(ranks, np.int32)
     stats = QueryStats()
-    _check(lib.rkr_query_exact(index, pq, nq, pk, pu, pr, ctypes.byref(stats), _stream(stream)))
+    if subsets is None:
+        _check(lib.rkr_query_exact(index, pq, nq, pk, pu, pr, ctypes.byref(stats),
+                                   _stream(stream)))
+    else:
+        so, su = _subsets_csr(subsets, nq)
+        _check(lib.rkr_query_exact_subsets(index, pq, nq, pk, so.ctypes.data, su.ctypes.data, pu,
+                                           pr, ctypes.byref(stats), _stream(stream)))
     return users, ranks, off, stats
 
 
-def rkr_query_approx(index, Q, k, c: float, *, device: bool = False, stream=None):
-    """c-approximate reverse k-ranks (Section 4.3): dict of per-user and per-query outputs."""
+def rkr_query_approx(index, Q, k, c: float, *, subsets=None, device: bool = False, stream=None):
+    """c-approximate reverse k-ranks (Section 4.3): dict of per-user and per-query outputs.
+
+    subsets: optional list of per-query user-id arrays (rkr_query_approx_subsets)."""
     lib = load()
     nq, _ = _shape(Q)
     kk = np.broadcast_to(np.asarray(k if not _is_torch(k) else k.cpu().numpy(), np.int32), (nq,))
@@ -226,11 +254,27 @@ def rkr_query_approx(index, Q, k, c: float, *, device: bool = False, stream=None
             (("users", np.int32), ("n_low", np.uint32), ("n_up", np.uint32),
              ("est", np.float64), ("case", np.int32), ("nc", np.int32))]
     stats = QueryStats()
-    _check(lib.rkr_query_approx(index, pq, nq, pk, ctypes.c_double(c), *ptrs,
-                                ctypes.byref(stats), _stream(stream)))
+    if subsets is None:
+        _check(lib.rkr_query_approx(index, pq, nq, pk, ctypes.c_double(c), *ptrs,
+                                    ctypes.byref(stats), _stream(stream)))
+    else:
+        so, su = _subsets_csr(subsets, nq)
+        _check(lib.rkr_query_approx_subsets(index, pq, nq, pk, so.ctypes.data, su.ctypes.data,
+                                            ctypes.c_double(c), *ptrs, ctypes.byref(stats),
+                                            _stream(stream)))
     out["offsets"] = off
     out["stats"] = stats
     return out
+
+
+def rkr_query_exact_subsets(index, Q, k, subsets, **kw):
+    """rkr_query_exact restricted to one user subset per query."""
+    return rkr_query_exact(index, Q, k, subsets=subsets, **kw)
+
+
+def rkr_query_approx_subsets(index, Q, k, subsets, c: float, **kw):
+    """rkr_query_approx restricted to one user subset per query."""
+    return rkr_query_approx(index, Q, k, c, subsets=subsets, **kw)
 
 
 def rkr_screen_scores(U, X, *, split: bool = False, stream=None):
@@ -256,7 +300,7 @@ def rkr_screen_scores_static(U, X, out_s, out_b, *, split: bool = False, stream=
     mx, _ = _shape(X)
     for t in (U, X, out_s, out_b):
         if not (_is_torch(t) and t.is_cuda and t.is_contiguous()
-                and str(t.dtype) == "torch.float32"):
+                and str(t.dtype) == "torch.float32"):  # noqa: E129
             raise RKRError(1, "rkr_screen_scores_static takes contiguous float32 CUDA tensors")
     if tuple(out_s.shape) != (n, mx) or tuple(out_b.shape) != (n, mx):
         raise RKRError(1, "output shape must be (n, mx)")

@@ -250,6 +250,21 @@ rkr_status rkr_build(const float *U, int64_t n, const float *P, int64_t m, int32
   return RKR_OK;
 }
 
+// Subset bitmaps: block q sets the bits of query q's users; out-of-range ids flag bad.
+__global__ void k_subset_bitmap(const int64_t *__restrict__ soff,
+                                const int32_t *__restrict__ users, int64_t n, int64_t words,
+                                uint32_t *__restrict__ member, int *__restrict__ bad) {
+  const int64_t q = blockIdx.x;
+  for (int64_t e = soff[q] + threadIdx.x; e < soff[q + 1]; e += blockDim.x) {
+    const int64_t u = users[e];
+    if (u < 0 || u >= n) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    atomicOr(&member[q * words + (u >> 5)], 1u << (u & 31));
+  }
+}
+
 static rkr_status query_prologue(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
                                  cudaStream_t st, std::vector<int32_t> &kh,
                                  std::vector<int64_t> &off) {
@@ -272,7 +287,9 @@ static rkr_status query_prologue(rkr_index *idx, const float *Q, int32_t nq, con
 }
 
 struct QueryStage {
-  InView vq, vk;
+  InView vq, vk, vsu;
+  uint32_t *member = nullptr;
+  int64_t *soff = nullptr;
   float *qnrm = nullptr;
   int64_t *off_d = nullptr;
   BinFP *bf_own = nullptr, *xbf_own = nullptr;
@@ -283,10 +300,55 @@ struct QueryStage {
     if (off_d) cudaFreeAsync(off_d, st);
     if (bf_own) cudaFreeAsync(bf_own, st);
     if (xbf_own) cudaFreeAsync(xbf_own, st);
+    if (member) cudaFreeAsync(member, st);
+    if (soff) cudaFreeAsync(soff, st);
     cudaStreamSynchronize(st);
     tc_free(Qt);
   }
 };
+
+// Validate the CSR subsets (host or device arrays) against k and build the bitmaps.
+static rkr_status stage_subsets(rkr_index *idx, int32_t nq, const std::vector<int32_t> &kh,
+                                const int64_t *subset_offs, const int32_t *subset_users,
+                                cudaStream_t st, QueryStage &qs, QueryCommon &qc) {
+  if (!subset_offs || !subset_users) return fail(RKR_EINVAL, "null subset argument");
+  std::vector<int64_t> so(nq + 1);
+  if (is_device(subset_offs)) {
+    RKR_CUDA(cudaMemcpyAsync(so.data(), subset_offs, sizeof(int64_t) * (nq + 1),
+                             cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+  } else {
+    memcpy(so.data(), subset_offs, sizeof(int64_t) * (nq + 1));
+  }
+  if (so[0] != 0) return fail(RKR_EINVAL, "subset_offs[0] must be 0");
+  for (int q = 0; q < nq; ++q) {
+    if (so[q + 1] < so[q]) return fail(RKR_EINVAL, "subset_offs must be non-decreasing");
+    if (kh[q] > so[q + 1] - so[q])
+      return fail(RKR_EINVAL, "k[%d] = %d exceeds the subset size %lld", q, kh[q],
+                  (long long)(so[q + 1] - so[q]));
+  }
+  const int64_t total = so[nq];
+  RKR_TRY(qs.vsu.init(subset_users, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1), st));
+  const int64_t words = (idx->n + 31) / 32;
+  RKR_CUDA(cudaMallocAsync(&qs.member, sizeof(uint32_t) * (size_t)words * nq, st));
+  RKR_CUDA(cudaMemsetAsync(qs.member, 0, sizeof(uint32_t) * (size_t)words * nq, st));
+  RKR_CUDA(cudaMallocAsync(&qs.soff, sizeof(int64_t) * (nq + 2), st));
+  int *bad = (int *)(qs.soff + nq + 1);
+  RKR_CUDA(cudaMemcpyAsync(qs.soff, so.data(), sizeof(int64_t) * (nq + 1),
+                           cudaMemcpyHostToDevice, st));
+  RKR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  k_subset_bitmap<<<nq, 256, 0, st>>>(qs.soff, (const int32_t *)qs.vsu.dev, idx->n, words,
+                                      qs.member, bad);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  int hb = 0;
+  RKR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (hb) return fail(RKR_EINVAL, "subset user ids must lie in [0, n)");
+  qc.member = qs.member;
+  qc.mwords = words;
+  return RKR_OK;
+}
 
 static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const int32_t *k,
                                 const std::vector<int64_t> &off, cudaStream_t st,
@@ -326,9 +388,10 @@ static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const in
   return RKR_OK;
 }
 
-rkr_status rkr_query_exact(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
-                           int32_t *out_users, int32_t *out_ranks, rkr_query_stats *stats,
-                           void *stream) {
+static rkr_status query_exact_impl(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   const int64_t *subset_offs, const int32_t *subset_users,
+                                   bool subsets, int32_t *out_users, int32_t *out_ranks,
+                                   rkr_query_stats *stats, void *stream) {
   g_err[0] = 0;
   if (!out_users || !out_ranks) return fail(RKR_EINVAL, "null output");
   cudaStream_t st = (cudaStream_t)stream;
@@ -338,6 +401,7 @@ rkr_status rkr_query_exact(rkr_index *idx, const float *Q, int32_t nq, const int
   if (!idx->has_exact) return fail(RKR_EINVAL, "index was built without exact_table");
   QueryStage qs;
   QueryCommon qc;
+  if (subsets) RKR_TRY(stage_subsets(idx, nq, kh, subset_offs, subset_users, st, qs, qc));
   RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
   OutView ou, orr;
   size_t tot = (size_t)off[nq];
@@ -350,10 +414,12 @@ rkr_status rkr_query_exact(rkr_index *idx, const float *Q, int32_t nq, const int
   return RKR_OK;
 }
 
-rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
-                            double c, int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
-                            double *out_est, int32_t *out_case, int32_t *out_nc,
-                            rkr_query_stats *stats, void *stream) {
+static rkr_status query_approx_impl(rkr_index *idx, const float *Q, int32_t nq,
+                                    const int32_t *k, const int64_t *subset_offs,
+                                    const int32_t *subset_users, bool subsets, double c,
+                                    int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
+                                    double *out_est, int32_t *out_case, int32_t *out_nc,
+                                    rkr_query_stats *stats, void *stream) {
   g_err[0] = 0;
   if (!out_users) return fail(RKR_EINVAL, "null output");
   if (!(c >= 1.0) || !isfinite(c)) return fail(RKR_EINVAL, "c must be a finite value >= 1");
@@ -363,6 +429,7 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
   RKR_TRY(query_prologue(idx, Q, nq, k, st, kh, off));
   QueryStage qs;
   QueryCommon qc;
+  if (subsets) RKR_TRY(stage_subsets(idx, nq, kh, subset_offs, subset_users, st, qs, qc));
   RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
   size_t tot = (size_t)off[nq];
   OutView ou, olo, oup, oes, oca, onc;
@@ -383,6 +450,39 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
   RKR_TRY(onc.finish());
   RKR_CUDA(cudaStreamSynchronize(st));
   return RKR_OK;
+}
+
+rkr_status rkr_query_exact(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                           int32_t *out_users, int32_t *out_ranks, rkr_query_stats *stats,
+                           void *stream) {
+  return query_exact_impl(idx, Q, nq, k, nullptr, nullptr, false, out_users, out_ranks, stats,
+                          stream);
+}
+
+rkr_status rkr_query_exact_subsets(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   const int64_t *subset_offs, const int32_t *subset_users,
+                                   int32_t *out_users, int32_t *out_ranks,
+                                   rkr_query_stats *stats, void *stream) {
+  return query_exact_impl(idx, Q, nq, k, subset_offs, subset_users, true, out_users, out_ranks,
+                          stats, stream);
+}
+
+rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                            double c, int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
+                            double *out_est, int32_t *out_case, int32_t *out_nc,
+                            rkr_query_stats *stats, void *stream) {
+  return query_approx_impl(idx, Q, nq, k, nullptr, nullptr, false, c, out_users, out_nlow,
+                           out_nup, out_est, out_case, out_nc, stats, stream);
+}
+
+rkr_status rkr_query_approx_subsets(rkr_index *idx, const float *Q, int32_t nq,
+                                    const int32_t *k, const int64_t *subset_offs,
+                                    const int32_t *subset_users, double c, int32_t *out_users,
+                                    uint32_t *out_nlow, uint32_t *out_nup, double *out_est,
+                                    int32_t *out_case, int32_t *out_nc, rkr_query_stats *stats,
+                                    void *stream) {
+  return query_approx_impl(idx, Q, nq, k, subset_offs, subset_users, true, c, out_users,
+                           out_nlow, out_nup, out_est, out_case, out_nc, stats, stream);
 }
 
 rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t mx, int32_t d,

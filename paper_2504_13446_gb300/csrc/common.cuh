@@ -207,6 +207,13 @@ __device__ __forceinline__ float screen_bound(float cfac, float nu, float nx) {
   return __fadd_ru(__fmul_ru(__fmul_ru(cfac, nu), nx), 1e-30f);
 }
 
+// Per-query user subsets as bitmaps: word q * words + u / 32, bit u % 32.  A null
+// bitmap means every user belongs to every query.
+__device__ __forceinline__ bool in_subset(const uint32_t *__restrict__ member, int64_t words,
+                                          int64_t q, int64_t u) {
+  return !member || ((member[q * words + (u >> 5)] >> (u & 31)) & 1u);
+}
+
 // Level boundaries: level L holds counts N <= B_L = scale * (2^L - 1).
 __host__ __device__ __forceinline__ uint64_t level_bound(int L, uint32_t scale) {
   return (uint64_t)scale * (((uint64_t)1 << L) - 1);

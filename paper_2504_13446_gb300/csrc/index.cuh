@@ -114,6 +114,8 @@ struct ThetaArgs {
   const int32_t *qmap;          // global query of each column (null: qa + column)
   int lskip;                    // passes 2, 3: leave out queries with L* above this
   int *ovf;                     // pass 2: overflow flag of the candidate segments
+  const uint32_t *member;       // per-query user subsets, or null
+  int64_t mwords;
 };
 rkr_status tc_theta_pass(int pass, const rkr_index *idx, const TcSide &Ut, const TcSide &Qt,
                          const ThetaArgs &a, int split, int *err, cudaStream_t st);
@@ -175,6 +177,8 @@ struct QueryCommon {
   BinFP *bf;          // n bin parameters of the sampled table's grid, valid for this batch
   BinFP *xbf;         // n bin parameters of the exact grid, valid for this batch
   TcSide Qt;          // bf16 operands of the batch
+  const uint32_t *member = nullptr;  // per-query user subsets (bitmaps), or null
+  int64_t mwords = 0;                // 32-bit words per query in member
 };
 
 rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq, double c,

@@ -708,11 +708,17 @@ __global__ void k_list_levels(SkimList L, const tc::RowBound *__restrict__ urb,
                               int tau, const int16_t *__restrict__ JU,
                               const int16_t *__restrict__ JL, uint32_t *__restrict__ hist_up,
                               uint32_t *__restrict__ hist_lo, uint32_t *__restrict__ jj,
-                              uint32_t *__restrict__ lv) {
+                              uint32_t *__restrict__ lv, const uint32_t *__restrict__ member,
+                              int64_t mwords) {
   int64_t e;
   if (!list_entry(L, e)) return;
   const int64_t u = L.u[e];
   const int q = L.q[e];
+  if (!in_subset(member, mwords, q, u)) {  // outside the query's subset: never counted
+    jj[e] = 0;
+    lv[e] = 0xffffu;
+    return;
+  }
   const float x = L.x[e];
   const float b = tc::screen_bound_tc(urb[u], qrb[q], gacc, gcan);
   int jlo, jhi;
@@ -887,10 +893,12 @@ static rkr_status check_flag(int *flag_d, const char *what, cudaStream_t st) {
   return RKR_OK;
 }
 
-static ThetaArgs theta_args(const Grid &g, int qa) {
+static ThetaArgs theta_args(const Grid &g, int qa, const QueryCommon &qc) {
   ThetaArgs a{};
   a.qa = qa;
   a.lskip = 1 << 30;
+  a.member = qc.member;
+  a.mwords = qc.mwords;
   a.binfp = g.bf;
   a.fmin = g.fmin;
   a.tau = g.tau;
@@ -928,7 +936,7 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
     RKR_CUDA(cudaGetLastError());
     plan.lskip = LS;
   }
-  ThetaArgs a = theta_args(g, 0);
+  ThetaArgs a = theta_args(g, 0, qc);
   a.nq_all = nq;
   a.hist = hist;
   a.xs = plan.xs;
@@ -940,7 +948,8 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
         const int prof_slot = prof_begin("k_list_levels", st);
         k_list_levels<<<list_grid(plan), 256, 0, st>>>(
             plan.list, idx->Ut.rb3, qc.Qt.rb3, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), g.bf,
-            g.fmin, g.tau, g.JU, g.JL, hist, hist + (size_t)nq * 32, plan.jj, plan.lv);
+            g.fmin, g.tau, g.JU, g.JL, hist, hist + (size_t)nq * 32, plan.jj, plan.lv, qc.member,
+          qc.mwords);
         prof_end(prof_slot, st, 0.0);
       }
       note_launch();
@@ -1049,7 +1058,7 @@ static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, i
   int *flag;
   RKR_TRY(tmp_alloc(bf, &flag, 2, st));
   RKR_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
-  ThetaArgs a = theta_args(g, qa);
+  ThetaArgs a = theta_args(g, qa, qc);
   a.nq_all = qc.Qt.rows;
   a.ovf = flag + 1;
   a.lstar = lstar_d;

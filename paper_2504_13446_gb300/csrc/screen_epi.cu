@@ -655,6 +655,8 @@ struct EpiTheta {
   int32_t *cand_u, *cand_q;
   int *ovf;                     // PASS 2: set when a query's segment would overflow
   const float *xs;              // per user: pairs scoring <= xs[u] - b are skipped (or null)
+  const uint32_t *member;       // per-query user subsets (bitmaps), or null
+  int64_t mwords;
   const int32_t *qmap;          // global query of each column (null: qa + column)
   int lskip;                    // passes 2, 3: columns whose L* exceeds this are left out
 
@@ -777,6 +779,7 @@ struct EpiTheta {
       for (int i = 0; i < 4; ++i) {
         on[i] = jj[i] >= 0 && ((pm >> (jj[i] & 31)) & 1u);
         cl[i] = col + (jj[i] < 0 ? jj[0] : jj[i]);
+        on[i] = on[i] && in_subset(member, mwords, qglob(S)[cl[i]], ts.u);
         // the pair's own bound (the tile's maximum only decides the skip), so that a
         // pair's bin interval does not depend on which queries share its tile
         const float b = tc::screen_bound_tc(ts.rb, qbnd(S)[cl[i]], gacc, gcan);
@@ -881,6 +884,7 @@ static rkr_status theta_launch(const rkr_index *idx, const TcSide &Ut, const TcS
   e.thi = a.thi; e.tlo = a.tlo; e.top = a.top; e.scale = a.scale;
   e.hist_up = a.hist; e.hist_lo = a.hist ? a.hist + (size_t)a.nq_all * 32 : nullptr;
   e.xs = a.xs; e.qmap = a.qmap; e.lskip = a.lskip; e.ovf = a.ovf;
+  e.member = a.member; e.mwords = a.mwords;
   e.lstar = a.lstar; e.cap = a.cap; e.fine = a.fine;
   e.qoff = a.qoff; e.qcursor = a.qcursor; e.cand_u = a.cand_u; e.cand_q = a.cand_q;
   static_assert(tc::screen_smem_bytes<kThetaBN, 4, EpiTheta<1>>() <= 232448, "theta smem");
