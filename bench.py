@@ -56,6 +56,22 @@ def _dist():
     return None, 0, 1
 
 
+def job_ms(ms_local: float, dist) -> float:
+    """The job's step time: the maximum over ranks (each rank runs its own replica)."""
+    if not dist:
+        return ms_local
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size: int, queries_per_rank: int, ms: float) -> float:
+    """Whole-job throughput: queries processed by all ranks per second of the slowest rank."""
+    return world_size * queries_per_rank / (ms / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle samples while the timed region runs."""
 
@@ -170,11 +186,7 @@ def bench_ours(args):
     launches = rkr.kernel_launches() - launches0
     kernels = rkr.rkr_profile_stop()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = job_ms(ev0.elapsed_time(ev1) / args.steps, dist)
 
     if args.case == "small":
         if rank == 0:
@@ -193,7 +205,7 @@ def bench_ours(args):
     if rank != 0:
         return
     nq = w.Q.shape[0]
-    value = ws * nq / (ms / 1000.0)
+    value = job_value(ws, nq, ms)
     mean = lambda key: float(np.mean([s[key] for s in stage]))  # noqa: E731
     # dominant kernel: the largest device time of the timed region, with its algorithmic
     # flops (2 * rows * cols * K' * products for a tensor-core screen)
