@@ -173,7 +173,8 @@ rkr_status rkr_query_approx_subsets(rkr_index *idx, const float *Q, int32_t nq,
  * rkr_screen_scores: the tensor-core screen on its own, for validation and for
  * measuring the screen error.  For every pair (U_i, X_j) writes the screened
  * score out_s[i * mx + j] (BF16 inputs, FP32 accumulation on tcgen05; split = 1
- * uses the three-term hi/lo product) and out_b[i * mx + j], the rigorous bound
+ * uses the three-term hi/lo product; split = 2 uses one E4M3 product (kind::f8f6f4) of
+ * rows scaled by powers of two so that max|x| <= 448) and out_b[i * mx + j], the rigorous bound
  * the library uses for |out_s - s(U_i, X_j)|.  U: n x d, X: mx x d float32.
  * Meant for small n * mx (the outputs are dense).
  */

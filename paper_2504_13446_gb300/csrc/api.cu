@@ -499,17 +499,24 @@ rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t 
   OutView os, ob;
   RKR_TRY(os.init(out_s, sizeof(float) * n * mx, st));
   RKR_TRY(ob.init(out_b, sizeof(float) * n * mx, st));
+  if (split < 0 || split > 2) return fail(RKR_EINVAL, "split must be 0, 1 or 2");
   TcSide A, B;
   struct Guard {
     TcSide *a, *b;
     ~Guard() { tc_free(*a); tc_free(*b); }
   } g{&A, &B};
-  RKR_TRY(tc_stage((const float *)vu.dev, n, d, A, st));
-  RKR_TRY(tc_stage((const float *)vx.dev, mx, d, B, st));
   int *err;
   RKR_CUDA(cudaMallocAsync(&err, sizeof(int), st));
   RKR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  rkr_status r = tc_scores(A, B, split ? 1 : 0, (float *)os.dev, (float *)ob.dev, err, st);
+  rkr_status r;
+  if (split == 2) {
+    r = tc_scores_e4m3((const float *)vu.dev, n, (const float *)vx.dev, mx, d, (float *)os.dev,
+                       (float *)ob.dev, err, st);
+  } else {
+    RKR_TRY(tc_stage((const float *)vu.dev, n, d, A, st));
+    RKR_TRY(tc_stage((const float *)vx.dev, mx, d, B, st));
+    r = tc_scores(A, B, split, (float *)os.dev, (float *)ob.dev, err, st);
+  }
   int herr = 0;
   cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(err, st);

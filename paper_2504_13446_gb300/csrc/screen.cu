@@ -4,6 +4,9 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "index.cuh"
 #include "tcops.cuh"
 
@@ -219,6 +222,173 @@ rkr_status tc_scores(const TcSide &A, const TcSide &B, int split, float *out, fl
   rkr_status s =
       launch_screen<BN, 4>(A, B, split, row_schedule(A.rows, B.rows, BN), e, err, st);
   cudaFreeAsync(tb, st);
+  return s;
+}
+
+}  // namespace rkr
+
+namespace rkr {
+
+// ------------------------------------------------------ FP8 E4M3 screen
+
+// Per-row E4M3 staging: scale 2^e with e the smallest integer such that
+// max|x| / 2^e <= 448 (the largest E4M3 value), q = e4m3_rn(x / 2^e), K padded
+// with zeros to kp (a multiple of 32).  The bound terms use the dequantised row
+// x~ = 2^e * q: a0 = ||x - x~||, a1 = a4 = ||x~||, a2 = ||x||, a3 = 0 (FP64 sums,
+// square roots rounded up).
+__global__ void k_stage_e4m3(const float *__restrict__ X, int64_t rows, int d, int kp,
+                             uint8_t *__restrict__ q, float *__restrict__ scale,
+                             tc::RowBound *__restrict__ rb) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const float *x = X + i * d;
+  float mx = 0.0f;
+  for (int k = 0; k < d; ++k) mx = fmaxf(mx, fabsf(x[k]));
+  int e = 0;
+  if (mx > 0.0f) {
+    frexpf(mx / 448.0f, &e);                 // mx / 448 = f * 2^e with f in [0.5, 1)
+    while (ldexpf(448.0f, e) < mx) ++e;      // guard against the division's rounding
+    while (e > -149 && ldexpf(448.0f, e - 1) >= mx) --e;
+  }
+  const float sc = ldexpf(1.0f, e);
+  double sx = 0, sd = 0, se = 0;
+  for (int k = 0; k < kp; ++k) {
+    const float v = k < d ? x[k] : 0.0f;
+    const __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
+    const float dq = __half2float(__half(__nv_cvt_fp8_to_halfraw(b, __NV_E4M3))) * sc;
+    q[i * kp + k] = (uint8_t)b;
+    sx += (double)v * v;
+    sd += (double)dq * dq;
+    se += ((double)v - dq) * ((double)v - dq);
+  }
+  auto up = [](double t) { return __double2float_ru(sqrt(t) * (1.0 + 0x1p-40) + 1e-300); };
+  tc::RowBound r;
+  r.a0 = up(se); r.a1 = up(sd); r.a2 = up(sx); r.a3 = 0.0f; r.a4 = up(sd);
+  rb[i] = r;
+  scale[i] = sc;
+}
+
+static rkr_status make_map8(CUtensorMap *map, const uint8_t *base, int64_t rows, int kp,
+                            int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(RKR_ECUDA, "cuTensorMapEncodeTiled is not available");
+  if (((uintptr_t)base & 15) != 0 || kp % 16 != 0)
+    return fail(RKR_EINTERNAL, "tensor map base or pitch not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)std::max<int64_t>(rows, 1)};
+  cuuint64_t strides[1] = {(cuuint64_t)kp};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * tc::KCH), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(RKR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return RKR_OK;
+}
+
+// Scaled screened scores and their bounds.  The tensor core forms the sum of
+// exact E4M3 products in FP32; the accumulation factor used for that sum is
+// 2^-12 (K' + 1) per unit of ||q_u~|| ||q_x~|| (a conservative model, checked by the
+// screen tests), and the power-of-two scales multiply exactly.
+struct EpiStore8 {
+  static const char *name() { return "k_screen<EpiStore8>"; }
+  struct Thread {
+    float b, su;
+  };
+  static constexpr size_t kSmem = 0;
+  int64_t nrows, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  const float *su, *sx;
+  tc::Gacc gacc;
+  float gcan;
+  float *out, *outb;
+  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    int64_t row = (int64_t)rb * tc::BM + r;
+    ts.b = row < nrows ? tc::screen_bound_tc(rowb[row], tileb[ct], gacc, gcan) : 0.0f;
+    ts.su = row < nrows ? su[row] : 0.0f;
+  }
+  __device__ void chunk(char *, int rb, int ct, int r, int col, uint32_t, const float (&v)[32],
+                        Thread &ts) const {
+    int64_t row = (int64_t)rb * tc::BM + r;
+    if (row >= nrows) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      int64_t c = (int64_t)ct * bn + col + j;
+      if (c < ncols) {
+        out[row * ncols + c] = v[j] * ts.su * sx[c];
+        outb[row * ncols + c] = ts.b;
+      }
+    }
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+};
+
+rkr_status tc_scores_e4m3(const float *U, int64_t n, const float *X, int64_t mx, int d,
+                          float *out, float *outb, int *err, cudaStream_t st) {
+  constexpr int BN = 256;
+  const int kp = (d + 31) / 32 * 32;
+  uint8_t *qa = nullptr, *qb = nullptr;
+  float *sa = nullptr, *sb = nullptr;
+  tc::RowBound *ra = nullptr, *rb = nullptr, *tb = nullptr;
+  const int64_t ntiles = (mx + BN - 1) / BN;
+  auto cleanup = [&]() {
+    for (void *p : {(void *)qa, (void *)qb, (void *)sa, (void *)sb, (void *)ra, (void *)rb,
+                    (void *)tb})
+      if (p) cudaFreeAsync(p, st);
+  };
+  if (cudaMallocAsync((void **)&qa, (size_t)n * kp, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&qb, (size_t)mx * kp, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&sa, sizeof(float) * n, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&sb, sizeof(float) * mx, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&ra, sizeof(tc::RowBound) * n, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&rb, sizeof(tc::RowBound) * mx, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&tb, sizeof(tc::RowBound) * ntiles, st) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(RKR_ENOMEM, "FP8 screen scratch allocation failed");
+  }
+  k_stage_e4m3<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(U, n, d, kp, qa, sa, ra);
+  note_launch();
+  k_stage_e4m3<<<(unsigned)((mx + 127) / 128), 128, 0, st>>>(X, mx, d, kp, qb, sb, rb);
+  note_launch();
+  k_tile_bounds<<<(unsigned)((ntiles + 127) / 128), 128, 0, st>>>(rb, mx, BN, (int)ntiles, tb);
+  note_launch();
+  CUtensorMap mA, mB;
+  rkr_status s = make_map8(&mA, qa, n, kp, tc::BM);
+  if (s == RKR_OK) s = make_map8(&mB, qb, mx, kp, BN);
+  if (s == RKR_OK) {
+    tc::Operands op;
+    op.nrows = n;
+    op.ncols = mx;
+    op.kchunks = (kp + 2 * tc::KCH - 1) / (2 * tc::KCH);
+    op.ksteps = kp / 32;
+    op.split = 0;
+    op.fp8 = 1;
+    EpiStore8 e;
+    e.nrows = n; e.ncols = mx; e.bn = BN; e.rowb = ra; e.tileb = tb; e.su = sa; e.sx = sb;
+    e.gacc.h = (float)((double)(kp + 1) * 0x1p-12 * (1.0 + 0x1p-10));
+    e.gacc.l = 0.0f;
+    e.gcan = tc_gcan(d);
+    e.out = out;
+    e.outb = outb;
+    const tc::Schedule sch = row_schedule(n, mx, BN);
+    const size_t smem = tc::screen_smem_bytes<BN, 4, EpiStore8>();
+    auto kern = tc::k_screen<BN, 4, EpiStore8>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
+    if (ce != cudaSuccess) s = cuda_fail(ce, "cudaFuncSetAttribute");
+    const int grid = std::min(sch.nunits, sm_count());
+    if (s == RKR_OK && grid > 0) {
+      ProfScope prof(EpiStore8::name(), st, 2.0 * (double)n * (double)mx * (double)kp);
+      kern<<<grid, tc::kThreads, smem, st>>>(mA, mA, mB, mB, op, sch, e, err);
+      note_launch();
+      ce = cudaGetLastError();
+      if (ce != cudaSuccess) s = cuda_fail(ce, "FP8 screen launch");
+    }
+  }
+  cleanup();
   return s;
 }
 

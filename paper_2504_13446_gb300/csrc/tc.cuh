@@ -95,6 +95,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// Instruction descriptor: E4M3 x E4M3 -> FP32 (kind::f8f6f4), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_e4m3(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
 // Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -184,9 +197,10 @@ __device__ __forceinline__ void tmem_ld1x4(uint32_t a0, uint32_t a1, uint32_t a2
 struct Operands {
   int64_t nrows;       // rows of A (users)
   int64_t ncols;       // rows of B (items or queries)
-  int kchunks;         // 64-wide K chunks per segment
-  int ksteps;          // 16-wide MMA steps per segment
+  int kchunks;         // 128-byte K chunks per segment
+  int ksteps;          // MMA steps per segment (32 bytes of K each)
   int split;           // 0: one segment hi.hi; 1: three segments hi.lo, lo.hi, hi.hi
+  int fp8 = 0;         // 1: E4M3 operands (kind::f8f6f4, 128 elements per chunk)
 };
 
 // Per-row bound terms (FP32 upper bounds), see screen_bound_tc.

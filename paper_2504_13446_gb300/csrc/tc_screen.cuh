@@ -121,8 +121,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               mbar_expect_tx(&full[s], L::kStage);
               // split order: hi.lo, lo.hi, then hi.hi (small terms first)
               const bool alo = op.split && g == 1, blo = op.split && g == 0;
-              tma_load_2d(sa, alo ? &mAl : &mAh, c * KCH, rb * BM, &full[s]);
-              tma_load_2d(sb, blo ? &mBl : &mBh, c * KCH, ct * BN, &full[s]);
+              const int kx = c * (op.fp8 ? 2 * KCH : KCH);  // elements of 128 bytes
+              tma_load_2d(sa, alo ? &mAl : &mAh, kx, rb * BM, &full[s]);
+              tma_load_2d(sb, blo ? &mBl : &mBh, kx, ct * BN, &full[s]);
             }
       }
       if (failed) {
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(BM, BN);
+      const uint32_t idesc = op.fp8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
       uint32_t it = 0, t = 0;
       for (int ui = blockIdx.x; ui < sch.nunits && !failed; ui += gridDim.x) {
         Unit u = unit_of(sch, ui);
@@ -155,9 +156,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t sb = sa + L::kA;
               const int c = kc % op.kchunks;
               const int steps = min(4, op.ksteps - c * 4);
-              for (int k = 0; k < steps; ++k)
-                umma_bf16(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc,
-                          (kc > 0 || k > 0) ? 1u : 0u);
+              for (int k = 0; k < steps; ++k) {
+                if (op.fp8)
+                  umma_e4m3(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc,
+                            (kc > 0 || k > 0) ? 1u : 0u);
+                else
+                  umma_bf16(dt, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc,
+                            (kc > 0 || k > 0) ? 1u : 0u);
+              }
               umma_commit(&empty[s]);
             }
             if (failed) break;

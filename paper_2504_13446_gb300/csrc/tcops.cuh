@@ -90,6 +90,11 @@ inline tc::Gacc tc_gacc(int kp, int split) {
 }
 inline float tc_gcan(int d) { return (float)((double)d * 0x1p-52 * 2.0); }
 
+// FP8 E4M3 screen with per-row power-of-two scales (single product): scores and
+// bounds of every pair, from FP32 rows on the device.
+rkr_status tc_scores_e4m3(const float *U, int64_t n, const float *X, int64_t mx, int d,
+                          float *out, float *outb, int *err, cudaStream_t st);
+
 // Raw screened scores and bounds of every pair (validation of the screen).
 rkr_status tc_scores(const TcSide &A, const TcSide &B, int split, float *out, float *outb,
                      int *err, cudaStream_t st);

@@ -46,3 +46,28 @@ def test_screen_integer_data_is_exact_when_representable():
     X = rng.integers(-8, 9, size=(300, 48)).astype(np.float32)
     s, b = rkr.rkr_screen_scores(U, X)
     assert (s.astype(np.float64) == oracle.scores(U, X)).all()
+
+
+@pytest.mark.parametrize("n,mx,d", [(300, 700, 32), (129, 257, 100), (128, 512, 128),
+                                    (77, 300, 37), (260, 513, 200)])
+def test_fp8_screen_within_bound(n, mx, d):
+    """E4M3 operands with per-row power-of-two scales (one product, kind::f8f6f4): every
+    scaled score lies within its bound of the canonical score; the bound is of the order
+    of the E4M3 unit roundoff (2^-4) times the norms, far looser than the BF16 forms."""
+    rng = np.random.default_rng(n * 7 + mx + d)
+    U, X = _rows(rng, n, d), _rows(rng, mx, d)
+    s, b = rkr.rkr_screen_scores(U, X, split=2)
+    S = oracle.scores(U, X)
+    err = np.abs(s.astype(np.float64) - S)
+    assert np.isfinite(s).all() and (b > 0).all()
+    ratio = err / b
+    assert ratio.max() <= 1.0, f"max error/bound {ratio.max()}"
+    xn = np.linalg.norm(X, axis=1)
+    tile_max = np.repeat([xn[i:i + 256].max() for i in range(0, mx, 256)], 256)[:mx]
+    rel = (b / (np.linalg.norm(U, axis=1)[:, None] * tile_max[None, :])).max()
+    assert rel < 0.5, rel
+    # the FP8 product tracks the score: typical error well below the bound
+    assert np.median(ratio) < 0.5
+    # ... and is much coarser than the split BF16 product
+    s3, b3 = rkr.rkr_screen_scores(U, X, split=True)
+    assert np.median(b) > 10 * np.median(b3)
