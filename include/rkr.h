@@ -220,6 +220,42 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  * product), 0 where none is stated.  Not thread-safe against concurrent queries
  * on other threads beyond what the shared event list allows.
  */
+/*
+ * Learned pruner (not in the paper): a monotone rank regressor
+ *   h1 = relu(W1 x - softplus(A) t + b1), h2 = relu(softplus(V2) h1 + b2),
+ *   y = softplus(v3) . h2 + b3  ~  log r(q, u, P),
+ * with x the F non-monotone features of the user and t = u.q / ||u||.  Every
+ * path from t has a non-positive weight product through non-decreasing
+ * activations, so y never increases with t (as the rank of Def. 1 cannot).
+ * Trained and run on the GPU with hand-written kernels: BF16 operands, FP32
+ * accumulation, FP32 master weights, Adam.  Loss 0.5 * mean((y - target)^2).
+ * Flat parameter order: W1 (H x F, row-major), A (H), b1 (H), V2 (H x H),
+ * b2 (H), v3 (H), b3 (1); rkr_pruner_nparams gives the count.
+ *   rkr_pruner_create: F, H in [1, 1024]; weights drawn from `seed` (SplitMix64).
+ *   rkr_pruner_params: set != 0 copies params into the model, else out of it
+ *     (host or device array of exactly nparams floats).
+ *   rkr_pruner_forward: y (B floats) for features X (B x F) and scores t (B).
+ *   rkr_pruner_loss_grads: the loss and the gradient (nparams floats) of one
+ *     batch, B <= 2^20 (for checking the kernels).
+ *   rkr_pruner_train: `epochs` passes over npairs samples in shuffled batches
+ *     of `batch` (SplitMix64 from `seed`), Adam with step `lr`; *final_loss gets
+ *     the loss of the last batch.
+ * Arrays may be host or device memory unless stated; all calls synchronize.
+ */
+typedef struct rkr_pruner rkr_pruner;
+rkr_status rkr_pruner_create(int32_t F, int32_t H, uint64_t seed, rkr_pruner **out);
+int64_t rkr_pruner_nparams(const rkr_pruner *pr);
+rkr_status rkr_pruner_params(rkr_pruner *pr, int32_t set, float *params, int64_t count);
+rkr_status rkr_pruner_forward(rkr_pruner *pr, const float *X, const float *t, int64_t B, float *y,
+                              void *stream);
+rkr_status rkr_pruner_loss_grads(rkr_pruner *pr, const float *X, const float *t,
+                                 const float *target, int64_t B, float *loss, float *grads,
+                                 void *stream);
+rkr_status rkr_pruner_train(rkr_pruner *pr, const float *X, const float *t, const float *target,
+                            int64_t npairs, int32_t epochs, int32_t batch, float lr,
+                            uint64_t seed, float *final_loss, void *stream);
+void rkr_pruner_free(rkr_pruner *pr);
+
 rkr_status rkr_profile_start(void);
 rkr_status rkr_profile_stop(char *report, int64_t len);
 

@@ -26,7 +26,7 @@ from . import buildlib
 __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
            "rkr_query_approx", "rkr_query_exact_subsets", "rkr_query_approx_subsets",
            "rkr_screen_scores", "rkr_screen_scores_static",
-           "rkr_profile_start", "rkr_profile_stop", "EXPORTS"]
+           "rkr_profile_start", "rkr_profile_stop", "Pruner", "EXPORTS"]
 
 _lock = threading.Lock()
 _lib = None
@@ -98,6 +98,21 @@ def load() -> ctypes.CDLL:
         lib.rkr_kernel_launches.argtypes = []
         lib.rkr_screen_scores.restype = I32
         lib.rkr_screen_scores.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
+        lib.rkr_pruner_create.restype = I32
+        lib.rkr_pruner_create.argtypes = [I32, I32, ctypes.c_uint64, ctypes.POINTER(V)]
+        lib.rkr_pruner_nparams.restype = I64
+        lib.rkr_pruner_nparams.argtypes = [V]
+        lib.rkr_pruner_params.restype = I32
+        lib.rkr_pruner_params.argtypes = [V, I32, V, I64]
+        lib.rkr_pruner_forward.restype = I32
+        lib.rkr_pruner_forward.argtypes = [V, V, V, I64, V, V]
+        lib.rkr_pruner_loss_grads.restype = I32
+        lib.rkr_pruner_loss_grads.argtypes = [V, V, V, V, I64, ctypes.POINTER(ctypes.c_float), V, V]
+        lib.rkr_pruner_train.restype = I32
+        lib.rkr_pruner_train.argtypes = [V, V, V, V, I64, I32, I32, ctypes.c_float,
+                                         ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), V]
+        lib.rkr_pruner_free.restype = None
+        lib.rkr_pruner_free.argtypes = [V]
         lib.rkr_profile_start.restype = I32
         lib.rkr_profile_start.argtypes = []
         lib.rkr_profile_stop.restype = I32
@@ -306,6 +321,65 @@ def rkr_screen_scores_static(U, X, out_s, out_b, *, split: bool = False, stream=
         raise RKRError(1, "output shape must be (n, mx)")
     _check(lib.rkr_screen_scores_static(U.data_ptr(), n, X.data_ptr(), mx, d, int(split),
                                         out_s.data_ptr(), out_b.data_ptr(), _stream(stream)))
+
+
+class Pruner:
+    """The learned pruner's monotone rank regressor (rkr_pruner_*): F features, H hidden."""
+
+    def __init__(self, F: int = 65, H: int = 256, seed: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.rkr_pruner_create(F, H, seed, ctypes.byref(h)))
+        self._h, self.F, self.H = h, F, H
+        self.nparams = int(lib.rkr_pruner_nparams(h))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.nparams, np.float32)
+        _check(load().rkr_pruner_params(self._h, 0, a.ctypes.data, self.nparams))
+        return a
+
+    def set_params(self, a) -> None:
+        a = np.ascontiguousarray(a, np.float32)
+        _check(load().rkr_pruner_params(self._h, 1, a.ctypes.data, self.nparams))
+
+    def forward(self, X, t) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        y = np.empty(len(t), np.float32)
+        _check(load().rkr_pruner_forward(self._h, X.ctypes.data, t.ctypes.data, len(t),
+                                         y.ctypes.data, None))
+        return y
+
+    def loss_grads(self, X, t, target):
+        X = np.ascontiguousarray(X, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        target = np.ascontiguousarray(target, np.float32)
+        g = np.empty(self.nparams, np.float32)
+        loss = ctypes.c_float()
+        _check(load().rkr_pruner_loss_grads(self._h, X.ctypes.data, t.ctypes.data,
+                                            target.ctypes.data, len(t), ctypes.byref(loss),
+                                            g.ctypes.data, None))
+        return float(loss.value), g
+
+    def train(self, X, t, target, *, epochs=2, batch=4096, lr=1e-3, seed=0) -> float:
+        X = np.ascontiguousarray(X, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        target = np.ascontiguousarray(target, np.float32)
+        loss = ctypes.c_float()
+        _check(load().rkr_pruner_train(self._h, X.ctypes.data, t.ctypes.data, target.ctypes.data,
+                                       len(t), epochs, batch, lr, seed, ctypes.byref(loss), None))
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().rkr_pruner_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass
