@@ -195,7 +195,8 @@ rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t 
  *   bytes (each piece rounded up to 256 bytes); larger problems are rejected
  *   with RKR_EINVAL and a message giving both figures.
  *   U, X, out_s, out_b must be device (or managed) memory; host pointers are
- *   rejected with RKR_EINVAL.  Outputs as in rkr_screen_scores; the caller owns
+ *   rejected with RKR_EINVAL, and so is split = 2 (the E4M3 form of
+ *   rkr_screen_scores is not offered here).  Outputs as in rkr_screen_scores; the caller owns
  *   every buffer.
  *   The first call on a device looks up the array's address
  *   (cudaGetSymbolAddress, with that device current) and keeps it; make that

@@ -58,3 +58,13 @@ def test_static_screen_rejects_host_pointers():
         rkr._check(lib.rkr_screen_scores_static(U.ctypes.data, 4, U.ctypes.data, 4, 8, 0,
                                                 out.ctypes.data, out.ctypes.data, None))
     assert e.value.status == 1
+
+
+def test_static_screen_rejects_the_fp8_form():
+    U = torch.zeros((4, 8), device="cuda")
+    out = torch.empty((4, 4), device="cuda")
+    lib = rkr.load()
+    with pytest.raises(rkr.RKRError) as e:
+        rkr._check(lib.rkr_screen_scores_static(U.data_ptr(), 4, U.data_ptr(), 4, 8, 2,
+                                                out.data_ptr(), out.data_ptr(), None))
+    assert e.value.status == 1
