@@ -56,6 +56,7 @@ typedef enum {
 } rkr_status;
 
 typedef struct rkr_index rkr_index;
+typedef struct rkr_pruner rkr_pruner;  /* learned pruner (rkr_pruner_create) */
 
 /* Parameters of the pre-processing step (Alg. 1 inputs: tau, omega, s). */
 typedef struct {
@@ -222,6 +223,35 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  * on other threads beyond what the shared event list allows.
  */
 /*
+ * rkr_rank_pairs: exact ranks r(q, u, P) (Def. 1) of arbitrary (user, query)
+ * pairs: pair i is user pair_user[i] and query row pair_query[i] of Q (nq x d).
+ * The same exact machinery as rkr_query_exact (tail lists, count intervals,
+ * recount with near-tie resolution); out_rank[i] = 1 + #{p : s(u,p) > s(u,q)}.
+ * Needs exact_table.  Host or device arrays; RKR_EINVAL for an index out of range.
+ *
+ * rkr_pair_features: the pruner's inputs for pairs: out_X (npairs x 65) =
+ * (R u / ||u||, log ||u||) with R a 64 x d projection (row-major) chosen by the
+ * caller, and out_t = u.q / ||u|| (FP32).
+ *
+ * rkr_query_exact_learned: Def. 2 with a learned cut (not the paper's method):
+ * the candidates that the exact path's screens leave for each query are ranked
+ * by the pruner's predicted log rank, only the `keep` best of each query (and
+ * those tying with the keep-th) get exact ranks, and the k smallest (rank,
+ * index) among them are returned; stats->candidates counts the kept ones.
+ * Exact when the true k best survive the cut; recall is to be measured against
+ * rkr_query_exact.  keep >= k[i].
+ */
+rkr_status rkr_rank_pairs(rkr_index *idx, const float *Q, int32_t nq, int64_t npairs,
+                          const int32_t *pair_user, const int32_t *pair_query, int32_t *out_rank,
+                          void *stream);
+rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int32_t nq,
+                             int64_t npairs, const int32_t *pair_user, const int32_t *pair_query,
+                             float *out_X, float *out_t, void *stream);
+rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *R, const float *Q,
+                                   int32_t nq, const int32_t *k, int32_t keep, int32_t *out_users,
+                                   int32_t *out_ranks, rkr_query_stats *stats, void *stream);
+
+/*
  * Learned pruner (not in the paper): a monotone rank regressor
  *   h1 = relu(W1 x - softplus(A) t + b1), h2 = relu(softplus(V2) h1 + b2),
  *   y = softplus(v3) . h2 + b3  ~  log r(q, u, P),
@@ -243,7 +273,6 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  *     the loss of the last batch.
  * Arrays may be host or device memory unless stated; all calls synchronize.
  */
-typedef struct rkr_pruner rkr_pruner;
 rkr_status rkr_pruner_create(int32_t F, int32_t H, uint64_t seed, rkr_pruner **out);
 int64_t rkr_pruner_nparams(const rkr_pruner *pr);
 rkr_status rkr_pruner_params(rkr_pruner *pr, int32_t set, float *params, int64_t count);

@@ -26,7 +26,8 @@ from . import buildlib
 __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
            "rkr_query_approx", "rkr_query_exact_subsets", "rkr_query_approx_subsets",
            "rkr_screen_scores", "rkr_screen_scores_static",
-           "rkr_profile_start", "rkr_profile_stop", "Pruner", "EXPORTS"]
+           "rkr_profile_start", "rkr_profile_stop", "Pruner", "rkr_rank_pairs",
+           "rkr_pair_features", "rkr_query_exact_learned", "EXPORTS"]
 
 _lock = threading.Lock()
 _lib = None
@@ -111,6 +112,13 @@ def load() -> ctypes.CDLL:
         lib.rkr_pruner_train.restype = I32
         lib.rkr_pruner_train.argtypes = [V, V, V, V, I64, I32, I32, ctypes.c_float,
                                          ctypes.c_uint64, ctypes.POINTER(ctypes.c_float), V]
+        lib.rkr_rank_pairs.restype = I32
+        lib.rkr_rank_pairs.argtypes = [V, V, I32, I64, V, V, V, V]
+        lib.rkr_pair_features.restype = I32
+        lib.rkr_pair_features.argtypes = [V, V, V, I32, I64, V, V, V, V, V]
+        lib.rkr_query_exact_learned.restype = I32
+        lib.rkr_query_exact_learned.argtypes = [V, V, V, V, I32, V, I32, V, V,
+                                                ctypes.POINTER(QueryStats), V]
         lib.rkr_pruner_free.restype = None
         lib.rkr_pruner_free.argtypes = [V]
         lib.rkr_profile_start.restype = I32
@@ -292,6 +300,51 @@ def rkr_query_approx_subsets(index, Q, k, subsets, c: float, **kw):
     return rkr_query_approx(index, Q, k, c, subsets=subsets, **kw)
 
 
+def rkr_rank_pairs(index, Q, pair_user, pair_query, *, stream=None):
+    """Exact ranks (Def. 1) of (user, query) pairs; queries are rows of Q."""
+    lib = load()
+    nq, _ = _shape(Q)
+    pq, kq = _ptr(Q, np.float32)
+    u = np.ascontiguousarray(pair_user, np.int32)
+    q = np.ascontiguousarray(pair_query, np.int32)
+    out = np.empty(len(u), np.int32)
+    _check(lib.rkr_rank_pairs(index, pq, nq, len(u), u.ctypes.data, q.ctypes.data,
+                              out.ctypes.data, _stream(stream)))
+    return out
+
+
+def rkr_pair_features(index, R, Q, pair_user, pair_query, *, stream=None):
+    """The pruner's inputs for pairs: (X (npairs x 65), t (npairs))."""
+    lib = load()
+    nq, _ = _shape(Q)
+    R = np.ascontiguousarray(R, np.float32)
+    pq, kq = _ptr(Q, np.float32)
+    u = np.ascontiguousarray(pair_user, np.int32)
+    q = np.ascontiguousarray(pair_query, np.int32)
+    X = np.empty((len(u), 65), np.float32)
+    t = np.empty(len(u), np.float32)
+    _check(lib.rkr_pair_features(index, R.ctypes.data, pq, nq, len(u), u.ctypes.data,
+                                 q.ctypes.data, X.ctypes.data, t.ctypes.data, _stream(stream)))
+    return X, t
+
+
+def rkr_query_exact_learned(index, pruner, R, Q, k, keep: int, *, stream=None):
+    """Def. 2 with the candidates cut to `keep` per query by the pruner's predictions."""
+    lib = load()
+    nq, _ = _shape(Q)
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    off = np.concatenate([[0], np.cumsum(kk, dtype=np.int64)])
+    R = np.ascontiguousarray(R, np.float32)
+    pq, kq = _ptr(Q, np.float32)
+    users = np.empty(int(off[-1]), np.int32)
+    ranks = np.empty(int(off[-1]), np.int32)
+    stats = QueryStats()
+    _check(lib.rkr_query_exact_learned(index, pruner._h, R.ctypes.data, pq, nq, kk.ctypes.data,
+                                       keep, users.ctypes.data, ranks.ctypes.data,
+                                       ctypes.byref(stats), _stream(stream)))
+    return users, ranks, off, stats
+
+
 def rkr_screen_scores(U, X, *, split: bool = False, stream=None):
     """Tensor-core screened scores and their error bounds for every pair (n x mx each)."""
     lib = load()
@@ -408,6 +461,15 @@ class Index:
 
     def query_approx(self, Q, k, c, **kw):
         return rkr_query_approx(self._h, Q, k, c, **kw)
+
+    def rank_pairs(self, Q, pair_user, pair_query, **kw):
+        return rkr_rank_pairs(self._h, Q, pair_user, pair_query, **kw)
+
+    def pair_features(self, R, Q, pair_user, pair_query, **kw):
+        return rkr_pair_features(self._h, R, Q, pair_user, pair_query, **kw)
+
+    def query_exact_learned(self, pruner, R, Q, k, keep, **kw):
+        return rkr_query_exact_learned(self._h, pruner, R, Q, k, keep, **kw)
 
     def export(self, what: str) -> np.ndarray:
         i = self.info

@@ -172,6 +172,40 @@ struct OutView {
 
 using namespace rkr;
 
+__global__ void k_check_pairs(const int32_t *__restrict__ u, const int32_t *__restrict__ q,
+                              int64_t npairs, int64_t n, int nq, int *__restrict__ bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < npairs && (u[i] < 0 || u[i] >= n || q[i] < 0 || q[i] >= nq)) atomicExch(bad, 1);
+}
+
+static rkr_status check_pairs(const int32_t *u, const int32_t *q, int64_t npairs, int64_t n,
+                              int nq, int *bad_host, cudaStream_t st) {
+  int *bad = nullptr;
+  RKR_CUDA(cudaMallocAsync(&bad, sizeof(int), st));
+  RKR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  k_check_pairs<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(u, q, npairs, n, nq, bad);
+  note_launch();
+  RKR_CUDA(cudaMemcpyAsync(bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  cudaFreeAsync(bad, st);
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+__global__ void k_gather_rows(const float *__restrict__ X, int F, const int32_t *__restrict__ rows,
+                              int64_t count, float *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count * F) return;
+  out[i] = X[(int64_t)rows[i / F] * F + i % F];
+}
+
+static rkr_status gather_rows(const float *X, int F, const int32_t *rows, int64_t count,
+                              float *out, cudaStream_t st) {
+  k_gather_rows<<<(unsigned)((count * F + 255) / 256), 256, 0, st>>>(X, F, rows, count, out);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
 extern "C" {
 
 const char *rkr_last_error(void) { return g_err; }
@@ -483,6 +517,115 @@ rkr_status rkr_query_approx_subsets(rkr_index *idx, const float *Q, int32_t nq,
                                     void *stream) {
   return query_approx_impl(idx, Q, nq, k, subset_offs, subset_users, true, c, out_users,
                            out_nlow, out_nup, out_est, out_case, out_nc, stats, stream);
+}
+
+rkr_status rkr_rank_pairs(rkr_index *idx, const float *Q, int32_t nq, int64_t npairs,
+                          const int32_t *pair_user, const int32_t *pair_query, int32_t *out_rank,
+                          void *stream) {
+  g_err[0] = 0;
+  if (!idx || !Q || !pair_user || !pair_query || !out_rank)
+    return fail(RKR_EINVAL, "null argument");
+  if (nq < 1 || npairs < 0) return fail(RKR_EINVAL, "bad sizes");
+  if (!idx->has_exact) return fail(RKR_EINVAL, "index was built without exact_table");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> kh(nq, 1);
+  std::vector<int64_t> off(nq + 1, 0);
+  for (int q = 0; q < nq; ++q) off[q + 1] = q + 1;
+  QueryStage qs;
+  QueryCommon qc;
+  RKR_TRY(stage_queries(idx, Q, nq, kh.data(), off, st, qs, qc));
+  if (npairs == 0) return RKR_OK;
+  InView vu, vq;
+  RKR_TRY(vu.init(pair_user, sizeof(int32_t) * npairs, st));
+  RKR_TRY(vq.init(pair_query, sizeof(int32_t) * npairs, st));
+  int bad = 0;
+  RKR_TRY(check_pairs((const int32_t *)vu.dev, (const int32_t *)vq.dev, npairs, idx->n, nq,
+                      &bad, st));
+  if (bad) return fail(RKR_EINVAL, "pair user or query index out of range");
+  OutView orr;
+  RKR_TRY(orr.init(out_rank, sizeof(int32_t) * npairs, st));
+  RKR_TRY(run_rank_pairs(idx, qc, nq, npairs, (const int32_t *)vu.dev, (const int32_t *)vq.dev,
+                         (int32_t *)orr.dev, st));
+  RKR_TRY(orr.finish());
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int32_t nq,
+                             int64_t npairs, const int32_t *pair_user, const int32_t *pair_query,
+                             float *out_X, float *out_t, void *stream) {
+  g_err[0] = 0;
+  if (!idx || !R || !Q || !pair_user || !pair_query || !out_X || !out_t)
+    return fail(RKR_EINVAL, "null argument");
+  if (nq < 1 || npairs < 0) return fail(RKR_EINVAL, "bad sizes");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (npairs == 0) return RKR_OK;
+  InView vr, vqq, vu, vq;
+  RKR_TRY(vr.init(R, sizeof(float) * 64 * idx->d, st));
+  RKR_TRY(vqq.init(Q, sizeof(float) * (size_t)nq * idx->d, st));
+  RKR_TRY(vu.init(pair_user, sizeof(int32_t) * npairs, st));
+  RKR_TRY(vq.init(pair_query, sizeof(int32_t) * npairs, st));
+  int bad = 0;
+  RKR_TRY(check_pairs((const int32_t *)vu.dev, (const int32_t *)vq.dev, npairs, idx->n, nq,
+                      &bad, st));
+  if (bad) return fail(RKR_EINVAL, "pair user or query index out of range");
+  float *Xu = nullptr;
+  RKR_CUDA(cudaMallocAsync(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
+  struct Free {
+    float *p;
+    cudaStream_t s;
+    ~Free() { cudaFreeAsync(p, s); }
+  } fr{Xu, st};
+  RKR_TRY(user_features(idx, (const float *)vr.dev, Xu, st));
+  OutView ox, ot;
+  RKR_TRY(ox.init(out_X, sizeof(float) * 65 * (size_t)npairs, st));
+  RKR_TRY(ot.init(out_t, sizeof(float) * npairs, st));
+  RKR_TRY(gather_rows(Xu, 65, (const int32_t *)vu.dev, npairs, (float *)ox.dev, st));
+  RKR_TRY(pair_scores(idx, (const float *)vqq.dev, npairs, (const int32_t *)vu.dev,
+                      (const int32_t *)vq.dev, (float *)ot.dev, st));
+  RKR_TRY(ox.finish());
+  RKR_TRY(ot.finish());
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *R, const float *Q,
+                                   int32_t nq, const int32_t *k, int32_t keep, int32_t *out_users,
+                                   int32_t *out_ranks, rkr_query_stats *stats, void *stream) {
+  g_err[0] = 0;
+  if (!pr || !R || !out_users || !out_ranks) return fail(RKR_EINVAL, "null argument");
+  if (pruner_features(pr) != 65) return fail(RKR_EINVAL, "the pruner must take 65 features");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> kh;
+  std::vector<int64_t> off;
+  RKR_TRY(query_prologue(idx, Q, nq, k, st, kh, off));
+  if (!idx->has_exact) return fail(RKR_EINVAL, "index was built without exact_table");
+  for (int q = 0; q < nq; ++q)
+    if (keep < kh[q])
+      return fail(RKR_EINVAL, "keep = %d must be at least k[%d] = %d", keep, q, kh[q]);
+  QueryStage qs;
+  QueryCommon qc;
+  RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
+  InView vr;
+  RKR_TRY(vr.init(R, sizeof(float) * 64 * idx->d, st));
+  float *Xu = nullptr;
+  RKR_CUDA(cudaMallocAsync(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
+  struct Free {
+    float *p;
+    cudaStream_t s;
+    ~Free() { cudaFreeAsync(p, s); }
+  } fr{Xu, st};
+  RKR_TRY(user_features(idx, (const float *)vr.dev, Xu, st));
+  OutView ou, orr;
+  size_t tot = (size_t)off[nq];
+  RKR_TRY(ou.init(out_users, sizeof(int32_t) * tot, st));
+  RKR_TRY(orr.init(out_ranks, sizeof(int32_t) * tot, st));
+  RKR_TRY(run_query_exact_learned(idx, qc, nq, pr, Xu, keep, (int32_t *)ou.dev,
+                                  (int32_t *)orr.dev, stats, st));
+  RKR_TRY(ou.finish());
+  RKR_TRY(orr.finish());
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
 }
 
 rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t mx, int32_t d,

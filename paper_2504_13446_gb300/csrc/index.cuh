@@ -185,6 +185,29 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
                             int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
                             int32_t *case_d, int32_t *nc_d, rkr_query_stats *stats,
                             cudaStream_t st);
+// Learned pruner (pruner.cu): predictions of B pairs from a per-user feature table.
+rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t *uid,
+                                 const float *t, int64_t B, float *y, cudaStream_t st);
+int pruner_features(const rkr_pruner *pr);
+
+// Exact ranks of arbitrary (user, query) pairs of a staged batch (device arrays).
+rkr_status run_rank_pairs(const rkr_index *idx, const QueryCommon &qc, int nq, int64_t npairs,
+                          const int32_t *cu, const int32_t *cq, int32_t *out_rank,
+                          cudaStream_t st);
+
+// Per-user features of the pruner: 64 projections R u / ||u|| and log ||u||
+// (F = 65), and per-pair scores t = u.q / ||u||.
+rkr_status user_features(const rkr_index *idx, const float *R, float *Xu, cudaStream_t st);
+rkr_status pair_scores(const rkr_index *idx, const float *Qd, int64_t npairs, const int32_t *cu,
+                       const int32_t *cq, float *t, cudaStream_t st);
+
+// Exact query whose candidates are cut to `keep` per query by the pruner's
+// predicted log ranks before exact ranking (an approximate form of Def. 2).
+rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
+                                   rkr_pruner *pr, const float *Xu, int32_t keep,
+                                   int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
+                                   cudaStream_t st);
+
 rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
                            int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
                            cudaStream_t st);

@@ -153,6 +153,18 @@ __global__ void k_mlp_batch(int64_t B, int F, const int64_t *__restrict__ idx,
   }
 }
 
+// Gather rows of a per-user feature table: Xb[r] = Xu[uid[r]], tb[r] = t[r].
+__global__ void k_mlp_gather(int64_t B, int F, const int32_t *__restrict__ uid,
+                             const float *__restrict__ Xu, const float *__restrict__ t,
+                             __nv_bfloat16 *__restrict__ Xb, float *__restrict__ tb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= B * F) return;
+  const int64_t r = i / F, c = i % F;
+  const int64_t u = uid[r] < 0 ? 0 : uid[r];  // invalid rows read user 0 (ignored)
+  Xb[i] = __float2bfloat16_rn(Xu[u * F + c]);
+  if (c == 0) tb[r] = t[r];
+}
+
 // y[r] = w3 . h2[r] + b3 (one warp per row), and dy = (y - target) / B when asked.
 __global__ void k_mlp_out(int64_t B, int H, const __nv_bfloat16 *__restrict__ h2,
                           const float *__restrict__ w3, const float *__restrict__ p, int64_t ob3,
@@ -370,6 +382,27 @@ double normal(uint64_t &x) {
 }
 
 }  // namespace
+
+// Predictions for B pairs whose features are rows uid[r] of a per-user table Xu
+// (device arrays), in chunks of the scratch capacity.
+rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t *uid,
+                                 const float *t, int64_t B, float *y, cudaStream_t st) {
+  const int64_t chunk = 1 << 16;
+  RKR_TRY(ensure_cap(pr, std::min(B, chunk), st));
+  refresh_weights(pr, st);
+  for (int64_t a = 0; a < B; a += chunk) {
+    const int64_t b = std::min(B - a, chunk);
+    k_mlp_gather<<<(unsigned)((b * pr->F + 255) / 256), 256, 0, st>>>(b, pr->F, uid + a, Xu,
+                                                                      t + a, pr->Xb, pr->tb);
+    note_launch();
+    forward_batch(pr, b, false, st);
+    RKR_CUDA(cudaMemcpyAsync(y + a, pr->y, sizeof(float) * b, cudaMemcpyDeviceToDevice, st));
+  }
+  return RKR_OK;
+}
+
+int pruner_features(const rkr_pruner *pr) { return pr->F; }
+
 }  // namespace rkr
 
 extern "C" {

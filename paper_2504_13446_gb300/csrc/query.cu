@@ -495,7 +495,12 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int64_t u = cu[i];
-  if (u < 0) { cu_fb[i] = -1; return; }
+  if (u < 0) {  // an unused slot or a pruned candidate: never selected
+    cu_fb[i] = -1;
+    ccount[i] = 0xffffffffu;
+    clb[i] = 0xffffffffu;
+    return;
+  }
   const float *uu = U + u * d;
   const float *qq = Q + (int64_t)cq[i] * d;
   // u.q as an interval [tlo, thi] from the compensated product; the canonical
@@ -1406,9 +1411,120 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
   return RKR_OK;
 }
 
+struct LearnedPrune {
+  rkr_pruner *pr;
+  const float *Xu;   // per-user features
+  int32_t keep;      // candidates kept per query
+};
+
+// Per query (one block): candidates whose predicted log rank is above the keep-th
+// smallest prediction are dropped (cu = -1).
+__global__ void __launch_bounds__(256)
+    k_keep_best(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
+                int keep, const float *__restrict__ y, int32_t *__restrict__ cu,
+                unsigned long long *__restrict__ kept) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t bc[2];
+  __shared__ unsigned long long acc;
+  const int q = qa + blockIdx.x;
+  const int64_t base = qoff[q] - qoff[qa];
+  const int64_t cnt = qcount[q];
+  int32_t *c = cu + base;
+  const float *yy = y + base;
+  auto key_of = [&](int64_t i) {
+    const uint32_t b = __float_as_uint(yy[i]);
+    return (uint64_t)((b & 0x80000000u) ? ~b : (b | 0x80000000u));
+  };
+  if (cnt > keep) {
+    const uint64_t kth = block_kth(cnt, (uint64_t)keep, 32,
+                                   [&](int64_t i, uint64_t &key) {
+                                     if (c[i] < 0) return false;
+                                     key = key_of(i);
+                                     return true;
+                                   },
+                                   hist, bc);
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
+      if (c[i] >= 0 && key_of(i) > kth) c[i] = -1;
+    __syncthreads();
+  }
+  const int64_t left = block_count(cnt, [&](int64_t i) { return c[i] >= 0; }, &acc);
+  if (threadIdx.x == 0) atomicAdd(kept, (unsigned long long)left);
+}
+
+// t = u.q / ||u|| of each pair (FP32; 0 for an invalid user index).
+__global__ void k_pair_scores(int64_t npairs, const int32_t *__restrict__ cu,
+                              const int32_t *__restrict__ cq, const float *__restrict__ U,
+                              const float *__restrict__ Q, int d, float *__restrict__ t) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  const int64_t u = cu[i];
+  if (u < 0) { t[i] = 0.0f; return; }
+  const float *uu = U + u * d, *qq = Q + (int64_t)cq[i] * d;
+  float s = 0.0f, nn = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    s = fmaf(uu[k], qq[k], s);
+    nn = fmaf(uu[k], uu[k], nn);
+  }
+  t[i] = nn > 0.0f ? s / sqrtf(nn) : 0.0f;
+}
+
+// Per user: R u / ||u|| (64 values) and log ||u||.
+__global__ void k_user_features(int64_t n, int d, const float *__restrict__ U,
+                                const float *__restrict__ R, float *__restrict__ Xu) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const float *uu = U + u * d;
+  float nn = 0.0f;
+  for (int k = 0; k < d; ++k) nn = fmaf(uu[k], uu[k], nn);
+  const float nrm = sqrtf(nn), inv = nrm > 0.0f ? 1.0f / nrm : 0.0f;
+  for (int j = 0; j < 64; ++j) {
+    float a = 0.0f;
+    for (int k = 0; k < d; ++k) a = fmaf(R[j * d + k], uu[k], a);
+    Xu[u * 65 + j] = a * inv;
+  }
+  Xu[u * 65 + 64] = logf(fmaxf(nrm, 1e-30f));
+}
+
+rkr_status user_features(const rkr_index *idx, const float *R, float *Xu, cudaStream_t st) {
+  k_user_features<<<(unsigned)((idx->n + 127) / 128), 128, 0, st>>>(idx->n, idx->d, idx->U, R,
+                                                                     Xu);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+rkr_status pair_scores(const rkr_index *idx, const float *Qd, int64_t npairs, const int32_t *cu,
+                       const int32_t *cq, float *t, cudaStream_t st) {
+  if (npairs <= 0) return RKR_OK;
+  k_pair_scores<<<(unsigned)((npairs + 127) / 128), 128, 0, st>>>(npairs, cu, cq, idx->U, Qd,
+                                                                   idx->d, t);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
+static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, int nq,
+                                   const LearnedPrune *lp, int32_t *users_d, int32_t *ranks_d,
+                                   rkr_query_stats *stats, cudaStream_t st);
+
 rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
                            int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
                            cudaStream_t st) {
+  return query_exact_core(idx, qc, nq, nullptr, users_d, ranks_d, stats, st);
+}
+
+rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
+                                   rkr_pruner *pr, const float *Xu, int32_t keep,
+                                   int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
+                                   cudaStream_t st) {
+  const LearnedPrune lp{pr, Xu, keep};
+  return query_exact_core(idx, qc, nq, &lp, users_d, ranks_d, stats, st);
+}
+
+static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, int nq,
+                                   const LearnedPrune *lp, int32_t *users_d, int32_t *ranks_d,
+                                   rkr_query_stats *stats, cudaStream_t st) {
   DevBuf bl, bn, bt, bcap;
   int32_t *lstar_d;
   int64_t *ncand_d;
@@ -1430,7 +1546,7 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
   int32_t *qself;
   RKR_TRY(tmp_alloc(bqs, &qself, nq, st));
   RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
-  int64_t fallback = 0, list_fp64 = 0;
+  int64_t fallback = 0, list_fp64 = 0, kept_total = 0;
   unsigned long long lstat_host_fb = 0;
   Plan plan;
   Timer t1(st);
@@ -1473,6 +1589,27 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
       for (int q = qa; q < qb; ++q) total += hc[q];
     }
     Timer t3(st);
+    if (lp && cnt > 0) {  // learned pruning: keep the best-predicted candidates of each query
+      DevBuf bt2, by2, bk2;
+      float *tq, *yq;
+      unsigned long long *kept_d;
+      RKR_TRY(tmp_alloc(bt2, &tq, cnt, st));
+      RKR_TRY(tmp_alloc(by2, &yq, cnt, st));
+      RKR_TRY(tmp_alloc(bk2, &kept_d, 1, st));
+      RKR_CUDA(cudaMemsetAsync(kept_d, 0, sizeof(unsigned long long), st));
+      RKR_TRY(pair_scores(idx, qc.Qd, cnt, cu, cq, tq, st));
+      {
+        ProfScope prof("pruner_forward", st);
+        RKR_TRY(pruner_forward_gather(lp->pr, lp->Xu, cu, tq, cnt, yq, st));
+      }
+      k_keep_best<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, lp->keep, yq, cu, kept_d);
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+      unsigned long long kh = 0;
+      RKR_CUDA(cudaMemcpyAsync(&kh, kept_d, sizeof(kh), cudaMemcpyDeviceToHost, st));
+      RKR_CUDA(cudaStreamSynchronize(st));
+      kept_total += (int64_t)kh;
+    }
     if (cnt > 0) {
       DevBuf bfb, blb;
       int32_t *cu_fb;
@@ -1573,12 +1710,54 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
     stats->fp64_dots = 2 * total + (int64_t)tiesv[1] + list_fp64;
     stats->near_ties = (int64_t)tiesv[0];
     stats->recounted = fallback;
+    if (lp) stats->candidates = kept_total;  // candidates left by the learned cut
     stats->wide_queries = wide;
     stats->deep_queries = (int32_t)plan.deep.size();
     stats->ms_theta = ms_theta;
     stats->ms_resolve = ms_res;
     stats->ms_select = ms_sel;
   }
+  return RKR_OK;
+}
+
+__global__ void k_count_to_rank(int64_t n, const uint32_t *__restrict__ c,
+                                int32_t *__restrict__ r) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) r[i] = (int32_t)(c[i] + 1u);
+}
+
+rkr_status run_rank_pairs(const rkr_index *idx, const QueryCommon &qc, int nq, int64_t npairs,
+                          const int32_t *cu, const int32_t *cq, int32_t *out_rank,
+                          cudaStream_t st) {
+  if (npairs <= 0) return RKR_OK;
+  DevBuf bq, bc, bl, bf, bs, bt;
+  int32_t *qself, *cu_fb;
+  uint32_t *ccount, *clb;
+  unsigned long long *lstat, *ties;
+  RKR_TRY(tmp_alloc(bq, &qself, nq, st));
+  RKR_TRY(tmp_alloc(bc, &ccount, npairs, st));
+  RKR_TRY(tmp_alloc(bl, &clb, npairs, st));
+  RKR_TRY(tmp_alloc(bf, &cu_fb, npairs, st));
+  RKR_TRY(tmp_alloc(bs, &lstat, 2, st));
+  RKR_TRY(tmp_alloc(bt, &ties, 2, st));
+  RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(ties, 0, 2 * sizeof(unsigned long long), st));
+  RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
+  k_list_rank<<<(unsigned)((npairs + 127) / 128), 128, 0, st>>>(
+      npairs, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d, idx->xlist,
+      idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
+      idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
+      idx->ldx, kListG, idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, qself, lstat);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  unsigned long long ls[2] = {0, 0};
+  RKR_CUDA(cudaMemcpyAsync(ls, lstat, sizeof(ls), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (ls[0] > 0)  // pairs below their user's tail list: exact recount
+    RKR_TRY(recount_candidates(idx, qc.Qd, npairs, cu_fb, cq, qself, ccount, nullptr, ties, st));
+  k_count_to_rank<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(npairs, ccount, out_rank);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
   return RKR_OK;
 }
 
