@@ -13,6 +13,7 @@ host buffers, host-device copies included.  ``cpu_baseline`` times the FP64
 oracle on a bounded sample of users and queries and scales it to the workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                      [--case full|small|learned]
 """
 
 from __future__ import annotations
@@ -268,6 +269,127 @@ def bench_ours(args):
     print(json.dumps(out))
 
 
+def bench_learned(args):
+    """The learned cut on the 1M x 100k x 200 workload: a monotone rank regressor
+    (65 -> 256 -> 256 -> 1) trained on the GPU on 10M exact (query, user, rank)
+    samples that the GPU path itself produces for 1,000 training queries (each
+    query's 2,000 best users plus 8,000 random ones), the keep factor calibrated
+    on 200 held-out queries for recall >= 0.99, then the 10,000 bench queries
+    answered with and without the cut.  All training and calibration queries are
+    items of P disjoint from the bench queries."""
+    import torch
+    import paper_2504_13446_gb300 as rkr
+
+    dist, rank, ws = _dist()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w, pos = make_inputs("full")
+    U = torch.from_numpy(w.U).cuda()
+    P = torch.from_numpy(w.P).cuda()
+    Q = torch.from_numpy(w.Q).cuda()
+    k = w.k.astype(np.int32)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    idx, ms_build = timed(lambda: rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s,
+                                            fbounds="exact", exact_table=True, sample_pos=pos))
+    rng = np.random.default_rng(7)
+    Rp = (rng.standard_normal((64, w.d)) / math.sqrt(w.d)).astype(np.float32)
+    n_train, n_cal, top, rand = 1000, 200, 2000, 8000
+    Qx, _, kx = synth.disjoint_queries(w, n_train + n_cal, seed=8)
+    Qtr, Qcal, kcal = Qx[:n_train], Qx[n_train:], kx[n_train:]
+
+    # training samples: exact ranks from the GPU path
+    (tu, tr, toff, _), ms_top = timed(lambda: idx.query_exact(Qtr, top))
+    ru = rng.integers(0, w.n, size=n_train * rand).astype(np.int32)
+    rq = np.repeat(np.arange(n_train, dtype=np.int32), rand)
+    rr, ms_pairs = timed(lambda: idx.rank_pairs(Qtr, ru, rq))
+    pu = np.concatenate([tu, ru]).astype(np.int32)
+    pq = np.concatenate([np.repeat(np.arange(n_train, dtype=np.int32), top), rq])
+    target = np.log(np.concatenate([tr, rr]).astype(np.float64)).astype(np.float32)
+    (X, t), ms_feat = timed(lambda: idx.pair_features(Rp, Qtr, pu, pq))
+    net = rkr.Pruner(65, 256, seed=2)
+    epochs = int(os.environ.get("RKR_LEARNED_EPOCHS", "4"))
+    loss, ms_train = timed(lambda: net.train(X, t, target, epochs=epochs, batch=4096, lr=1e-3,
+                                             seed=3))
+    del X, t
+
+    # keep factor: the smallest alpha on the grid with recall >= 0.99 on held-out queries
+    def recall_of(users, ranks, off, plain_r):
+        hits = viol = 0
+        for q in range(len(off) - 1):
+            sl = slice(off[q], off[q + 1])
+            kth = plain_r[sl].max()
+            hits += int(np.sum(ranks[sl] <= kth))
+            viol += int(np.sum(ranks[sl] > C * kth))
+        return hits / float(off[-1]), viol
+
+    _, cal_r, _, _ = idx.query_exact(Qcal, kcal)
+    grid = [1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0, 16.0]
+    cal = {}
+    alpha = grid[-1]
+    for a in grid:
+        keep = np.ceil(a * kcal).astype(np.int32)
+        lu, lr, loff, _ = idx.query_exact_learned(net, Rp, Qcal, kcal, keep)
+        cal[a] = recall_of(lu, lr, loff, cal_r)[0]
+        if cal[a] >= 0.99:
+            alpha = a
+            break
+
+    # the bench queries, plain and cut
+    keep = np.ceil(alpha * k).astype(np.int32)
+    for _ in range(max(args.warmup, 1)):
+        idx.query_exact(Q, k)
+        idx.query_exact_learned(net, Rp, Q, k, keep)
+    ms_plain, ms_cut = [], []
+    rkr.rkr_profile_start()
+    for _ in range(args.steps):
+        (pu_, pr_, poff, pst), t_plain = timed(lambda: idx.query_exact(Q, k))
+        ms_plain.append(t_plain)
+    kernels_plain = rkr.rkr_profile_stop()
+    top_p = sorted(kernels_plain.items(), key=lambda kv: -kv[1][1])[:12]
+    rkr.rkr_profile_start()
+    for _ in range(args.steps):
+        (lu, lr, loff, lst), t_cut = timed(lambda: idx.query_exact_learned(net, Rp, Q, k, keep))
+        ms_cut.append(t_cut)
+    kernels = rkr.rkr_profile_stop()
+    recall, viol = recall_of(lu, lr, loff, pr_)
+    idx.close()
+    if rank != 0:
+        return
+    nq = w.Q.shape[0]
+    mp, mc = statistics.median(ms_plain), statistics.median(ms_cut)
+    top_k = sorted(kernels.items(), key=lambda kv: -kv[1][1])[:12]
+    print(json.dumps({
+        "case": "learned",
+        "metric": "queries/s", "value": nq / (mc / 1000.0), "unit": "queries/s",
+        "plain_exact_value": nq / (mp / 1000.0),
+        "ms_per_batch": {"learned": mc, "plain_exact": mp},
+        "steps": args.steps, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "exact reverse k-ranks with and without the learned cut: "
+                               "|U|=1,000,000 |P|=100,000 d=200 mixture, 10,000 queries from P, "
+                               "k in {10,50,100}; regressor 65->256->256->1",
+                   "keep": f"ceil({alpha} * k) per query"},
+        "recall_at_k": recall, "c_bound_violations": viol, "c": C,
+        "candidates": {"plain": pst.candidates, "learned": lst.candidates,
+                       "recounted_plain": pst.recounted, "recounted_learned": lst.recounted},
+        "calibration_recall": {str(a): r for a, r in cal.items()},
+        "training": {"queries": n_train, "samples": int(len(pu)), "epochs": epochs,
+                     "batch": 4096, "final_loss": loss,
+                     "ms": {"index_build": ms_build, "top_users": ms_top, "rank_pairs": ms_pairs,
+                            "features": ms_feat, "train": ms_train}},
+        "learned_kernels_ms_per_batch": {kk: round(v[1] / args.steps, 3) for kk, v in top_k},
+        "plain_kernels_ms_per_batch": {kk: round(v[1] / args.steps, 3) for kk, v in top_p},
+    }))
+
+
 def cpu_baseline(w, pos, n_sample=None, q_sample=None):
     """The oracle on a user sample (all items), scaled by n / n_sample; queries of the
     approximate step on a query sample, scaled by nq / q_sample."""
@@ -329,11 +451,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="full", choices=["full", "small"],
-                    help="small: a 40k-user profiling case (no CPU baseline, no e2e)")
+    ap.add_argument("--case", default="full", choices=["full", "small", "learned"],
+                    help="small: a 40k-user profiling case (no CPU baseline, no e2e); "
+                         "learned: train the rank regressor and compare the learned cut "
+                         "with the plain exact query")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.case == "learned":
+        bench_learned(args)
     else:
         bench_ours(args)
 

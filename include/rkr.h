@@ -233,13 +233,16 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  * (R u / ||u||, log ||u||) with R a 64 x d projection (row-major) chosen by the
  * caller, and out_t = u.q / ||u|| (FP32).
  *
- * rkr_query_exact_learned: Def. 2 with a learned cut (not the paper's method):
- * the candidates that the exact path's screens leave for each query are ranked
- * by the pruner's predicted log rank, only the `keep` best of each query (and
- * those tying with the keep-th) get exact ranks, and the k smallest (rank,
- * index) among them are returned; stats->candidates counts the kept ones.
- * Exact when the true k best survive the cut; recall is to be measured against
- * rkr_query_exact.  keep >= k[i].
+ * rkr_query_exact_learned: Def. 2 with a learned cut (not the paper's method).
+ * The exact path runs as in rkr_query_exact up to the recount: candidates whose
+ * rank the tail lists settle keep their exact rank, and of the candidates that
+ * would still need a recount over P only the keep[i] with the smallest
+ * predicted log rank (and those tying with the keep[i]-th) are recounted for
+ * query i; the others are dropped.  The k smallest (rank, index) among the rest
+ * are returned; stats->candidates counts the candidates left after the cut.
+ * Every returned rank is exact; the answer set is exact when the true k best
+ * survive the cut, and its recall is to be measured against rkr_query_exact.
+ * keep: nq int32 (host or device), keep[i] >= k[i], else RKR_EINVAL.
  */
 rkr_status rkr_rank_pairs(rkr_index *idx, const float *Q, int32_t nq, int64_t npairs,
                           const int32_t *pair_user, const int32_t *pair_query, int32_t *out_rank,
@@ -248,7 +251,8 @@ rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int
                              int64_t npairs, const int32_t *pair_user, const int32_t *pair_query,
                              float *out_X, float *out_t, void *stream);
 rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *R, const float *Q,
-                                   int32_t nq, const int32_t *k, int32_t keep, int32_t *out_users,
+                                   int32_t nq, const int32_t *k, const int32_t *keep,
+                                   int32_t *out_users,
                                    int32_t *out_ranks, rkr_query_stats *stats, void *stream);
 
 /*

@@ -117,7 +117,7 @@ def load() -> ctypes.CDLL:
         lib.rkr_pair_features.restype = I32
         lib.rkr_pair_features.argtypes = [V, V, V, I32, I64, V, V, V, V, V]
         lib.rkr_query_exact_learned.restype = I32
-        lib.rkr_query_exact_learned.argtypes = [V, V, V, V, I32, V, I32, V, V,
+        lib.rkr_query_exact_learned.argtypes = [V, V, V, V, I32, V, V, V, V,
                                                 ctypes.POINTER(QueryStats), V]
         lib.rkr_pruner_free.restype = None
         lib.rkr_pruner_free.argtypes = [V]
@@ -328,11 +328,13 @@ def rkr_pair_features(index, R, Q, pair_user, pair_query, *, stream=None):
     return X, t
 
 
-def rkr_query_exact_learned(index, pruner, R, Q, k, keep: int, *, stream=None):
-    """Def. 2 with the candidates cut to `keep` per query by the pruner's predictions."""
+def rkr_query_exact_learned(index, pruner, R, Q, k, keep, *, stream=None):
+    """Def. 2 with the candidates of query i cut to keep[i] (an int or one per query)
+    by the pruner's predictions."""
     lib = load()
     nq, _ = _shape(Q)
     kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    kp = np.ascontiguousarray(np.broadcast_to(np.asarray(keep, np.int32), (nq,)))
     off = np.concatenate([[0], np.cumsum(kk, dtype=np.int64)])
     R = np.ascontiguousarray(R, np.float32)
     pq, kq = _ptr(Q, np.float32)
@@ -340,7 +342,7 @@ def rkr_query_exact_learned(index, pruner, R, Q, k, keep: int, *, stream=None):
     ranks = np.empty(int(off[-1]), np.int32)
     stats = QueryStats()
     _check(lib.rkr_query_exact_learned(index, pruner._h, R.ctypes.data, pq, nq, kk.ctypes.data,
-                                       keep, users.ctypes.data, ranks.ctypes.data,
+                                       kp.ctypes.data, users.ctypes.data, ranks.ctypes.data,
                                        ctypes.byref(stats), _stream(stream)))
     return users, ranks, off, stats
 

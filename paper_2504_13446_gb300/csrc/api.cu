@@ -590,37 +590,48 @@ rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int
 }
 
 rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *R, const float *Q,
-                                   int32_t nq, const int32_t *k, int32_t keep, int32_t *out_users,
+                                   int32_t nq, const int32_t *k, const int32_t *keep, int32_t *out_users,
                                    int32_t *out_ranks, rkr_query_stats *stats, void *stream) {
   g_err[0] = 0;
-  if (!pr || !R || !out_users || !out_ranks) return fail(RKR_EINVAL, "null argument");
+  if (!pr || !R || !keep || !out_users || !out_ranks) return fail(RKR_EINVAL, "null argument");
   if (pruner_features(pr) != 65) return fail(RKR_EINVAL, "the pruner must take 65 features");
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int32_t> kh;
   std::vector<int64_t> off;
   RKR_TRY(query_prologue(idx, Q, nq, k, st, kh, off));
   if (!idx->has_exact) return fail(RKR_EINVAL, "index was built without exact_table");
+  std::vector<int32_t> keeph(nq);
+  if (is_device(keep)) {
+    RKR_CUDA(cudaMemcpyAsync(keeph.data(), keep, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+  } else {
+    memcpy(keeph.data(), keep, sizeof(int32_t) * nq);
+  }
   for (int q = 0; q < nq; ++q)
-    if (keep < kh[q])
-      return fail(RKR_EINVAL, "keep = %d must be at least k[%d] = %d", keep, q, kh[q]);
+    if (keeph[q] < kh[q])
+      return fail(RKR_EINVAL, "keep[%d] = %d must be at least k[%d] = %d", q, keeph[q], q, kh[q]);
   QueryStage qs;
   QueryCommon qc;
   RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
   InView vr;
   RKR_TRY(vr.init(R, sizeof(float) * 64 * idx->d, st));
   float *Xu = nullptr;
+  int32_t *keep_d = nullptr;
   RKR_CUDA(cudaMallocAsync(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
   struct Free {
-    float *p;
+    void *p;
     cudaStream_t s;
     ~Free() { cudaFreeAsync(p, s); }
   } fr{Xu, st};
+  RKR_CUDA(cudaMallocAsync(&keep_d, sizeof(int32_t) * nq, st));
+  Free fk{keep_d, st};
+  RKR_CUDA(cudaMemcpyAsync(keep_d, keeph.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
   RKR_TRY(user_features(idx, (const float *)vr.dev, Xu, st));
   OutView ou, orr;
   size_t tot = (size_t)off[nq];
   RKR_TRY(ou.init(out_users, sizeof(int32_t) * tot, st));
   RKR_TRY(orr.init(out_ranks, sizeof(int32_t) * tot, st));
-  RKR_TRY(run_query_exact_learned(idx, qc, nq, pr, Xu, keep, (int32_t *)ou.dev,
+  RKR_TRY(run_query_exact_learned(idx, qc, nq, pr, Xu, keep_d, (int32_t *)ou.dev,
                                   (int32_t *)orr.dev, stats, st));
   RKR_TRY(ou.finish());
   RKR_TRY(orr.finish());

@@ -201,10 +201,11 @@ rkr_status user_features(const rkr_index *idx, const float *R, float *Xu, cudaSt
 rkr_status pair_scores(const rkr_index *idx, const float *Qd, int64_t npairs, const int32_t *cu,
                        const int32_t *cq, float *t, cudaStream_t st);
 
-// Exact query whose candidates are cut to `keep` per query by the pruner's
-// predicted log ranks before exact ranking (an approximate form of Def. 2).
+// Exact query whose candidates still to be recounted over P are cut to
+// keep_d[q] per query (device array) by the pruner's predicted log ranks (an
+// approximate form of Def. 2; returned ranks stay exact).
 rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
-                                   rkr_pruner *pr, const float *Xu, int32_t keep,
+                                   rkr_pruner *pr, const float *Xu, const int32_t *keep_d,
                                    int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
                                    cudaStream_t st);
 

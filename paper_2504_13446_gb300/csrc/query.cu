@@ -1414,42 +1414,58 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
 struct LearnedPrune {
   rkr_pruner *pr;
   const float *Xu;   // per-user features
-  int32_t keep;      // candidates kept per query
+  const int32_t *keep;  // candidates kept per query (device, nq)
 };
 
-// Per query (one block): candidates whose predicted log rank is above the keep-th
-// smallest prediction are dropped (cu = -1).
+// Per query (one block), among the candidates still to be recounted (fb >= 0):
+// those whose predicted log rank y is above the keep[q]-th smallest prediction
+// are cut (fb = cu = -1, count = the largest key, so selection never takes them).
+// Candidates whose exact count is known already are not touched.
 __global__ void __launch_bounds__(256)
-    k_keep_best(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
-                int keep, const float *__restrict__ y, int32_t *__restrict__ cu,
-                unsigned long long *__restrict__ kept) {
+    k_learned_cut(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
+                  const int32_t *__restrict__ keep_q, const float *__restrict__ y,
+                  int32_t *__restrict__ fb_all, int32_t *__restrict__ cu_all,
+                  uint32_t *__restrict__ ccount, unsigned long long *__restrict__ ncut) {
   __shared__ uint32_t hist[256];
   __shared__ uint64_t bc[2];
   __shared__ unsigned long long acc;
   const int q = qa + blockIdx.x;
   const int64_t base = qoff[q] - qoff[qa];
   const int64_t cnt = qcount[q];
-  int32_t *c = cu + base;
+  const int64_t keep = keep_q[q];
+  int32_t *fb = fb_all + base, *cu = cu_all + base;
+  uint32_t *cc = ccount + base;
   const float *yy = y + base;
   auto key_of = [&](int64_t i) {
     const uint32_t b = __float_as_uint(yy[i]);
     return (uint64_t)((b & 0x80000000u) ? ~b : (b | 0x80000000u));
   };
-  if (cnt > keep) {
-    const uint64_t kth = block_kth(cnt, (uint64_t)keep, 32,
-                                   [&](int64_t i, uint64_t &key) {
-                                     if (c[i] < 0) return false;
-                                     key = key_of(i);
-                                     return true;
-                                   },
-                                   hist, bc);
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
-      if (c[i] >= 0 && key_of(i) > kth) c[i] = -1;
-    __syncthreads();
-  }
-  const int64_t left = block_count(cnt, [&](int64_t i) { return c[i] >= 0; }, &acc);
-  if (threadIdx.x == 0) atomicAdd(kept, (unsigned long long)left);
+  const int64_t open = block_count(cnt, [&](int64_t i) { return fb[i] >= 0; }, &acc);
+  if (open <= keep) return;
+  const uint64_t kth = block_kth(cnt, (uint64_t)keep, 32,
+                                 [&](int64_t i, uint64_t &key) {
+                                   if (fb[i] < 0) return false;
+                                   key = key_of(i);
+                                   return true;
+                                 },
+                                 hist, bc);
+  __syncthreads();
+  const int64_t cut = block_count(cnt, [&](int64_t i) { return fb[i] >= 0 && key_of(i) > kth; },
+                                  &acc);
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
+    if (fb[i] >= 0 && key_of(i) > kth) {
+      fb[i] = -1;
+      cu[i] = -1;
+      cc[i] = 0xffffffffu;
+    }
+  if (threadIdx.x == 0) atomicAdd(ncut, (unsigned long long)cut);
+}
+
+// Predictions scattered back to candidate slots: y[oi[j]] = yc[j].
+__global__ void k_scatter_y(int64_t n, const int32_t *__restrict__ oi,
+                            const float *__restrict__ yc, float *__restrict__ y) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) y[oi[j]] = yc[j];
 }
 
 // t = u.q / ||u|| of each pair (FP32; 0 for an invalid user index).
@@ -1515,11 +1531,53 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
 }
 
 rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
-                                   rkr_pruner *pr, const float *Xu, int32_t keep,
+                                   rkr_pruner *pr, const float *Xu, const int32_t *keep_d,
                                    int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
                                    cudaStream_t st) {
-  const LearnedPrune lp{pr, Xu, keep};
+  const LearnedPrune lp{pr, Xu, keep_d};
   return query_exact_core(idx, qc, nq, &lp, users_d, ranks_d, stats, st);
+}
+
+// The learned cut of one chunk: predictions for the candidates still to be
+// recounted (nfb of them, compacted), then k_learned_cut per query.
+static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const LearnedPrune *lp,
+                              int qa, int qb, int64_t cnt, int64_t nfb, const int64_t *qoff_rel,
+                              const uint32_t *cursor, int32_t *cu, const int32_t *cq,
+                              int32_t *cu_fb, uint32_t *ccount, int64_t *cut_total,
+                              cudaStream_t st) {
+  DevBuf b1, b2, b3, b4, b5, b6, b7, b8;
+  int32_t *fu, *fq, *fi;
+  unsigned long long *cur, *ncut;
+  float *tq, *yc, *y;
+  RKR_TRY(tmp_alloc(b1, &fu, nfb, st));
+  RKR_TRY(tmp_alloc(b2, &fq, nfb, st));
+  RKR_TRY(tmp_alloc(b3, &fi, nfb, st));
+  RKR_TRY(tmp_alloc(b4, &cur, 1, st));
+  RKR_TRY(tmp_alloc(b5, &ncut, 1, st));
+  RKR_TRY(tmp_alloc(b6, &tq, nfb, st));
+  RKR_TRY(tmp_alloc(b7, &yc, nfb, st));
+  RKR_TRY(tmp_alloc(b8, &y, cnt, st));
+  RKR_CUDA(cudaMemsetAsync(cur, 0, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(ncut, 0, sizeof(unsigned long long), st));
+  k_compact<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_fb, cq, cur, fu, fq, fi);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  RKR_TRY(pair_scores(idx, qc.Qd, nfb, fu, fq, tq, st));
+  {
+    ProfScope prof("pruner_forward", st);
+    RKR_TRY(pruner_forward_gather(lp->pr, lp->Xu, fu, tq, nfb, yc, st));
+  }
+  k_scatter_y<<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(nfb, fi, yc, y);
+  note_launch();
+  k_learned_cut<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, lp->keep, y, cu_fb, cu, ccount,
+                                         ncut);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  unsigned long long h = 0;
+  RKR_CUDA(cudaMemcpyAsync(&h, ncut, sizeof(h), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  *cut_total += (int64_t)h;
+  return RKR_OK;
 }
 
 static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, int nq,
@@ -1546,7 +1604,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   int32_t *qself;
   RKR_TRY(tmp_alloc(bqs, &qself, nq, st));
   RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
-  int64_t fallback = 0, list_fp64 = 0, kept_total = 0;
+  int64_t fallback = 0, list_fp64 = 0, cut_total = 0;
   unsigned long long lstat_host_fb = 0;
   Plan plan;
   Timer t1(st);
@@ -1589,27 +1647,6 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       for (int q = qa; q < qb; ++q) total += hc[q];
     }
     Timer t3(st);
-    if (lp && cnt > 0) {  // learned pruning: keep the best-predicted candidates of each query
-      DevBuf bt2, by2, bk2;
-      float *tq, *yq;
-      unsigned long long *kept_d;
-      RKR_TRY(tmp_alloc(bt2, &tq, cnt, st));
-      RKR_TRY(tmp_alloc(by2, &yq, cnt, st));
-      RKR_TRY(tmp_alloc(bk2, &kept_d, 1, st));
-      RKR_CUDA(cudaMemsetAsync(kept_d, 0, sizeof(unsigned long long), st));
-      RKR_TRY(pair_scores(idx, qc.Qd, cnt, cu, cq, tq, st));
-      {
-        ProfScope prof("pruner_forward", st);
-        RKR_TRY(pruner_forward_gather(lp->pr, lp->Xu, cu, tq, cnt, yq, st));
-      }
-      k_keep_best<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, lp->keep, yq, cu, kept_d);
-      note_launch();
-      RKR_CUDA(cudaGetLastError());
-      unsigned long long kh = 0;
-      RKR_CUDA(cudaMemcpyAsync(&kh, kept_d, sizeof(kh), cudaMemcpyDeviceToHost, st));
-      RKR_CUDA(cudaStreamSynchronize(st));
-      kept_total += (int64_t)kh;
-    }
     if (cnt > 0) {
       DevBuf bfb, blb;
       int32_t *cu_fb;
@@ -1650,6 +1687,20 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       unsigned long long ls[2] = {0, 0};
       RKR_CUDA(cudaMemcpyAsync(ls, lstat, sizeof(ls), cudaMemcpyDeviceToHost, st));
       RKR_CUDA(cudaStreamSynchronize(st));
+      if (lp && lstat_host_fb > 0) {  // learned cut of the candidates still to be recounted
+        RKR_TRY(learned_cut(idx, qc, lp, qa, qb, cnt, (int64_t)lstat_host_fb, qoff_rel, cursor,
+                            cu, cq, cu_fb, ccount, &cut_total, st));
+        lstat_host_fb = 0;
+        DevBuf bn4;
+        unsigned long long *nfb4;
+        RKR_TRY(tmp_alloc(bn4, &nfb4, 1, st));
+        RKR_CUDA(cudaMemsetAsync(nfb4, 0, sizeof(unsigned long long), st));
+        k_count_valid<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_fb, nfb4);
+        note_launch();
+        RKR_CUDA(cudaMemcpyAsync(&lstat_host_fb, nfb4, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        RKR_CUDA(cudaStreamSynchronize(st));
+      }
       fallback += (int64_t)lstat_host_fb;
       list_fp64 += (int64_t)ls[1];
       if (lstat_host_fb > 0) {
@@ -1710,7 +1761,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
     stats->fp64_dots = 2 * total + (int64_t)tiesv[1] + list_fp64;
     stats->near_ties = (int64_t)tiesv[0];
     stats->recounted = fallback;
-    if (lp) stats->candidates = kept_total;  // candidates left by the learned cut
+    if (lp) stats->candidates = total - cut_total;  // candidates left by the learned cut
     stats->wide_queries = wide;
     stats->deep_queries = (int32_t)plan.deep.size();
     stats->ms_theta = ms_theta;

@@ -16,6 +16,7 @@ product distributions the paper reports (Section 4.2, Fig. 2).
 from .workloads import (  # noqa: F401
     Workload,
     WORKLOADS,
+    disjoint_queries,
     gaussian_rows,
     mixture_rows,
     make_workload,

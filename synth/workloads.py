@@ -175,4 +175,16 @@ def make_workload(name: str, *, n: Optional[int] = None, m: Optional[int] = None
     raise ValueError(f"unknown workload {name!r}")
 
 
+def disjoint_queries(w: Workload, count: int, seed: int):
+    """`count` further queries drawn from P without replacement, none of them an item
+    that the workload already uses as a query; k uniform in {10, 50, 100}.
+    Returns (Q, item indices, k)."""
+    rng = np.random.default_rng(seed)
+    used = w.query_from_P[w.query_from_P >= 0]
+    pool = np.setdiff1d(np.arange(w.m, dtype=np.int64), used)
+    idx = rng.choice(pool, size=count, replace=False)
+    k = rng.choice(np.array([10, 50, 100], dtype=np.int32), size=count)
+    return w.P[idx].copy(), idx, k
+
+
 WORKLOADS = ("exact_small", "exact_batched", "approx", "learned", "uneven")

@@ -34,7 +34,9 @@ def test_rank_pairs_match_oracle():
 def test_learned_cut_returns_exact_ranks_with_high_recall():
     w = synth.make_workload("approx", n=20000, m=4000, nq=96)
     rng = np.random.default_rng(11)
-    gpu = rkr.Index(w.U, w.P, tau=w.tau, omega=w.omega, s=w.s, exact_table=True)
+    # a low floor rank puts the tail lists' end at rank ~32, so most candidates of
+    # the k = 50 and k = 100 queries need a recount over P: the set the cut acts on
+    gpu = rkr.Index(w.U, w.P, tau=w.tau, omega=w.omega, s=w.s, exact_table=True, floor_rank=32)
     Rp = (rng.standard_normal((64, w.d)) / np.sqrt(w.d)).astype(np.float32)
     train_q, eval_q = w.Q[:64], w.Q[64:]
     k_eval = w.k[64:]
@@ -49,7 +51,7 @@ def test_learned_cut_returns_exact_ranks_with_high_recall():
     net.train(X, t, np.log(r).astype(np.float32), epochs=30, batch=512, lr=2e-3, seed=3)
     # evaluation: the cut against the plain exact path
     plain_u, plain_r, off, plain_st = gpu.query_exact(eval_q, k_eval)
-    keep = int(k_eval.max())   # the cut bites on queries with more candidates than that
+    keep = 2 * k_eval          # recount at most 2k candidates per query
     lu, lr, loff, st = gpu.query_exact_learned(net, Rp, eval_q, k_eval, keep)
     assert (loff == off).all()
     R = oracle.ranks(w.U, w.P, eval_q)
@@ -61,7 +63,19 @@ def test_learned_cut_returns_exact_ranks_with_high_recall():
         kth = plain_r[sl].max()                      # the true k-th smallest rank
         hits += int(np.sum(got_r <= kth))            # tie-aware recall
     recall = hits / float(off[-1])
-    print(f"learned cut: keep {keep}, recall {recall:.4f}, exact ranks for {st.candidates} "
-          f"candidates instead of {plain_st.candidates}")
+    print(f"learned cut: keep 2k, recall {recall:.4f}, {st.candidates} candidates instead of "
+          f"{plain_st.candidates}, recounted {st.recounted} instead of {plain_st.recounted}")
     assert st.candidates < plain_st.candidates
+    assert st.recounted < plain_st.recounted
     assert recall >= 0.9
+    # keep as an array, one per query: a keep no smaller than any query's candidate
+    # count cuts nothing, so the answer is the plain exact one
+    big = np.full(len(eval_q), w.n, np.int32)
+    bu, br, boff, bst = gpu.query_exact_learned(net, Rp, eval_q, k_eval, big)
+    assert (bu == plain_u).all() and (br == plain_r).all() and (boff == off).all()
+    assert bst.candidates == plain_st.candidates
+    # and keep below k is rejected
+    small = k_eval.copy()
+    small[3] -= 1
+    with pytest.raises(rkr.RKRError):
+        gpu.query_exact_learned(net, Rp, eval_q, k_eval, small)
