@@ -399,6 +399,8 @@ struct EpiXT {
 // offsets and the largest screen bound of the entries.  One CTA per user;
 // overflowed lists are left as they are and marked unusable.
 constexpr int kGroupThreads = 1024;
+constexpr int kGroupPer = kListCapMax / kGroupThreads;  // list entries per thread
+static_assert(kGroupPer * kGroupThreads == kListCapMax, "list capacity");
 
 // j(theta) = #{i < tau : t_i <= theta} when it is known to lie in [jlo, jhi]:
 // the thresholds inside the bracket are compared in FP64 (no division).
@@ -414,6 +416,10 @@ __device__ __forceinline__ int exact_j_near(double theta, double fmin, double de
 // uses the screen bound of its item tile), (2) the list grouped by the
 // kListG-column list grid with column offsets, (3) the largest entry bound.
 // An overflowed list gives the trivial table XLO = 0, XHI = m.
+// Each thread loads all of its (at most kGroupPer) entries up front and keeps
+// them in registers, so a user's list is in flight at once and the grouping
+// can be written back in place after one barrier; a column index is computed
+// again when the entry is scattered.
 __global__ void __launch_bounds__(kGroupThreads)
     k_list_group(int64_t n, uint2 *__restrict__ list, const int64_t *__restrict__ loff,
                  const uint32_t *__restrict__ lcap, const uint32_t *__restrict__ lcnt,
@@ -424,13 +430,11 @@ __global__ void __launch_bounds__(kGroupThreads)
                  int bn, tc::Gacc gacc, float gcan, uint16_t *__restrict__ coff,
                  float *__restrict__ bmax) {
   extern __shared__ unsigned char lsm[];
-  uint2 *buf = (uint2 *)lsm;                                  // kListCapMax
-  uint32_t *cnt = (uint32_t *)(buf + kListCapMax);            // G + 2
+  uint32_t *cnt = (uint32_t *)lsm;                            // G + 2
   uint32_t *hlo = cnt + G + 2;                                // kXG + 1
   uint32_t *hhi = hlo + kXG + 1;                              // kXG + 1
   uint32_t *wsum = hhi + kXG + 1;                             // kGroupThreads / 32
   float *red = (float *)(wsum + kGroupThreads / 32);          // kGroupThreads / 32
-  uint16_t *cols = (uint16_t *)(red + kGroupThreads / 32);    // kListCapMax
   const int64_t u = blockIdx.x;
   const uint32_t L = lcnt[u];
   uint16_t *co = coff + u * (G + 2);
@@ -453,8 +457,22 @@ __global__ void __launch_bounds__(kGroupThreads)
   const double g0 = xg0[u], dx = ldx[u];
   const tc::RowBound ru = rowb[u];
   float bm = 0.0f;
-  for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-    const uint2 e = row[i];
+  uint2 ent[kGroupPer];
+#pragma unroll
+  for (int k = 0; k < kGroupPer; ++k) {
+    const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
+    if (i < L) ent[k] = row[i];
+  }
+  auto list_col = [&](float v) {
+    int jlo, jhi;
+    bin_interval(lb, g0, G, v, v, jlo, jhi);
+    return jlo == jhi ? jlo : exact_j_near((double)v, g0, dx, jlo, jhi);
+  };
+#pragma unroll
+  for (int k = 0; k < kGroupPer; ++k) {
+    const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
+    if (i >= L) break;
+    const uint2 e = ent[k];
     const float v = __uint_as_float(e.y);
     const float b = tc::screen_bound_tc(ru, tileb[e.x / bn], gacc, gcan);
     bm = fmaxf(bm, b);
@@ -464,12 +482,7 @@ __global__ void __launch_bounds__(kGroupThreads)
       atomicAdd(&hlo[clo], 1u);
       atomicAdd(&hhi[chi], 1u);
     }
-    int jlo, jhi;
-    bin_interval(lb, g0, G, v, v, jlo, jhi);
-    const int col = jlo == jhi ? jlo : exact_j_near((double)v, g0, dx, jlo, jhi);
-    buf[i] = e;
-    cols[i] = (uint16_t)col;
-    atomicAdd(&cnt[col], 1u);
+    atomicAdd(&cnt[list_col(v)], 1u);
   }
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -526,9 +539,12 @@ __global__ void __launch_bounds__(kGroupThreads)
   }
   if (threadIdx.x == kGroupThreads - 1) co[G + 1] = (uint16_t)run;
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
-    uint32_t pos = atomicAdd(&cnt[cols[i]], 1u);
-    row[pos] = buf[i];
+#pragma unroll
+  for (int k = 0; k < kGroupPer; ++k) {
+    const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
+    if (i >= L) break;
+    const uint32_t pos = atomicAdd(&cnt[list_col(__uint_as_float(ent[k].y))], 1u);
+    row[pos] = ent[k];
   }
 }
 
@@ -540,9 +556,8 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   idx->ptile_bn = bn;
   const int G = kListG;
   RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, G, idx->pmax, idx->ldx, idx->lbin, st));
-  size_t sm = sizeof(uint2) * kListCapMax + sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) +
-              sizeof(uint32_t) * (kGroupThreads / 32) + sizeof(float) * (kGroupThreads / 32) +
-              sizeof(uint16_t) * kListCapMax;
+  size_t sm = sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) +
+              sizeof(uint32_t) * (kGroupThreads / 32) + sizeof(float) * (kGroupThreads / 32);
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
   {
