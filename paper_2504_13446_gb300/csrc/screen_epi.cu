@@ -418,8 +418,7 @@ __device__ __forceinline__ int exact_j_near(double theta, double fmin, double de
 // An overflowed list gives the trivial table XLO = 0, XHI = m.
 // Each thread loads all of its (at most kGroupPer) entries up front and keeps
 // them in registers, so a user's list is in flight at once and the grouping
-// can be written back in place after one barrier; a column index is computed
-// again when the entry is scattered.
+// can be written back in place after one barrier.
 __global__ void __launch_bounds__(kGroupThreads)
     k_list_group(int64_t n, uint2 *__restrict__ list, const int64_t *__restrict__ loff,
                  const uint32_t *__restrict__ lcap, const uint32_t *__restrict__ lcnt,
@@ -435,6 +434,7 @@ __global__ void __launch_bounds__(kGroupThreads)
   uint32_t *hhi = hlo + kXG + 1;                              // kXG + 1
   uint32_t *wsum = hhi + kXG + 1;                             // kGroupThreads / 32
   float *red = (float *)(wsum + kGroupThreads / 32);          // kGroupThreads / 32
+  uint16_t *cols = (uint16_t *)(red + kGroupThreads / 32);    // kListCapMax
   const int64_t u = blockIdx.x;
   const uint32_t L = lcnt[u];
   uint16_t *co = coff + u * (G + 2);
@@ -482,7 +482,9 @@ __global__ void __launch_bounds__(kGroupThreads)
       atomicAdd(&hlo[clo], 1u);
       atomicAdd(&hhi[chi], 1u);
     }
-    atomicAdd(&cnt[list_col(v)], 1u);
+    const int col = list_col(v);
+    cols[i] = (uint16_t)col;
+    atomicAdd(&cnt[col], 1u);
   }
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(kGroupThreads)
   for (int k = 0; k < kGroupPer; ++k) {
     const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
     if (i >= L) break;
-    const uint32_t pos = atomicAdd(&cnt[list_col(__uint_as_float(ent[k].y))], 1u);
+    const uint32_t pos = atomicAdd(&cnt[cols[i]], 1u);
     row[pos] = ent[k];
   }
 }
@@ -557,7 +559,8 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   const int G = kListG;
   RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, G, idx->pmax, idx->ldx, idx->lbin, st));
   size_t sm = sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) +
-              sizeof(uint32_t) * (kGroupThreads / 32) + sizeof(float) * (kGroupThreads / 32);
+              sizeof(uint32_t) * (kGroupThreads / 32) + sizeof(float) * (kGroupThreads / 32) +
+              sizeof(uint16_t) * kListCapMax;
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
   {
