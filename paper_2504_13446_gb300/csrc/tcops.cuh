@@ -49,12 +49,45 @@ rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::
   op.ksteps = A.kp / 16;
   op.split = split;
   const size_t smem = tc::screen_smem_bytes<BN, STAGES, Epi>();
-  auto kern = tc::k_screen<BN, STAGES, Epi>;
-  RKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = std::min(sch.nunits, sm_count());
   if (grid < 1) return RKR_OK;
   ProfScope prof(Epi::name(), st,
                  2.0 * (double)A.rows * (double)B.rows * (double)A.kp * (split ? 3.0 : 1.0));
+  if (sch.mode == 0 && sch.nunits >= 2) {
+    // row-owned units: CTA pairs share each B chunk by multicast
+    auto pk = tc::k_screen_pair<BN, STAGES, Epi>;
+    RKR_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUtensorMap mBh2, mBl2;
+    RKR_TRY(make_map(&mBh2, B.hi, B.rows, B.kp, BN / 2));
+    RKR_TRY(make_map(&mBl2, B.lo, B.rows, B.kp, BN / 2));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(tc::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * (unsigned)((sm_count() + 1) / 2));
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, pk, &cfg) != cudaSuccess) {
+      (void)cudaGetLastError();
+      nclusters = 0;
+    }
+    const int npairs = (sch.nunits + 1) / 2;
+    if (nclusters >= 1) {
+      cfg.gridDim = dim3(2 * (unsigned)std::min(npairs, nclusters));
+      RKR_CUDA(cudaLaunchKernelEx(&cfg, pk, mAh, mAl, mBh2, mBl2, op, sch, epi, err_dev));
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+      return RKR_OK;
+    }
+  }
+  auto kern = tc::k_screen<BN, STAGES, Epi>;
+  RKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, tc::kThreads, smem, st>>>(mAh, mAl, mBh, mBl, op, sch, epi, err_dev);
   note_launch();
   RKR_CUDA(cudaGetLastError());
