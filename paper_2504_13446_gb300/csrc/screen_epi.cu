@@ -108,23 +108,47 @@ struct EpiFb {
     const int64_t left = ncols - c0;
     uint32_t keep = left >= 32 ? 0xffffffffu : left <= 0 ? 0u : (1u << left) - 1u;
     if (ts.row >= nrows) keep = 0;  // the warp stays together for the reservation below
-    float mx = -INFINITY, mn = INFINITY;
+    float mx, mn;   // extremes of the chunk's kept scores
+    if (keep == 0xffffffffu) {
+      float a[16], c[16];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const bool in = (keep >> j) & 1u;
-      mx = fmaxf(mx, in ? v[j] : -INFINITY);
-      mn = fminf(mn, in ? v[j] : INFINITY);
+      for (int j = 0; j < 16; ++j) {
+        a[j] = fmaxf(v[2 * j], v[2 * j + 1]);
+        c[j] = fminf(v[2 * j], v[2 * j + 1]);
+      }
+#pragma unroll
+      for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int j = 0; j < w; ++j) {
+          a[j] = fmaxf(a[j], a[j + w]);
+          c[j] = fminf(c[j], c[j + w]);
+        }
+      mx = a[0];
+      mn = c[0];
+    } else {
+      mx = -INFINITY;
+      mn = INFINITY;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const bool in = (keep >> j) & 1u;
+        mx = fmaxf(mx, in ? v[j] : -INFINITY);
+        mn = fminf(mn, in ? v[j] : INFINITY);
+      }
     }
     ts.mxlo = fmaxf(ts.mxlo, __fsub_rd(mx, ts.b));
     ts.mnhi = fminf(ts.mnhi, __fadd_ru(mn, ts.b));
     if (seed_out) return;
-    // v + b >= mxlo  <=  v >= mxlo - b rounded down (and likewise for the minimum)
+    // v + b >= mxlo  <=  v >= mxlo - b rounded down (and likewise for the minimum);
+    // a chunk whose own extremes pass neither test has nothing to queue
     const float tmax = __fsub_rd(ts.mxlo, ts.b), tmin = __fadd_ru(ts.mnhi, ts.b);
+    const bool hit = mx >= tmax || mn <= tmin;
+    if (!__any_sync(0xffffffffu, hit)) return;
     uint32_t mask = 0;
+    if (hit) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) mask |= (v[j] >= tmax || v[j] <= tmin ? 1u : 0u) << j;
-    mask &= keep;
-    if (!__any_sync(0xffffffffu, mask != 0u)) return;
+      for (int j = 0; j < 32; ++j) mask |= (v[j] >= tmax || v[j] <= tmin ? 1u : 0u) << j;
+      mask &= keep;
+    }
     // one queue reservation per warp and chunk
     const int lane = threadIdx.x & 31;
     const int cnt = __popc(mask);
