@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kGroupThreads)
                  const BinFP *__restrict__ xbin, const double *__restrict__ xg0,
                  uint32_t *__restrict__ XLO, uint32_t *__restrict__ XHI, uint32_t mcount,
                  const tc::RowBound *__restrict__ rowb, const tc::RowBound *__restrict__ tileb,
-                 int bn, tc::Gacc gacc, float gcan, uint16_t *__restrict__ coff,
+                 int bn_shift, tc::Gacc gacc, float gcan, uint16_t *__restrict__ coff,
                  float *__restrict__ bmax) {
   extern __shared__ unsigned char lsm[];
   uint32_t *cnt = (uint32_t *)lsm;                            // G + 2
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kGroupThreads)
     if (i >= L) break;
     const uint2 e = ent[k];
     const float v = __uint_as_float(e.y);
-    const float b = tc::screen_bound_tc(ru, tileb[e.x / bn], gacc, gcan);
+    const float b = tc::screen_bound_tc(ru, tileb[e.x >> bn_shift], gacc, gcan);
     bm = fmaxf(bm, b);
     int clo, chi;
     bin_interval(xb, g0, kXG, __fsub_rd(v, b), __fadd_ru(v, b), clo, chi);
@@ -580,6 +580,9 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   RKR_CUDA(cudaMemcpyAsync(idx->ptile3, tb, sizeof(tc::RowBound) * ntiles,
                            cudaMemcpyDeviceToDevice, st));
   idx->ptile_bn = bn;
+  int bn_shift = 0;
+  while ((1 << bn_shift) < bn) ++bn_shift;
+  if ((1 << bn_shift) != bn) return fail(RKR_EINTERNAL, "item tile width %d is not a power of two", bn);
   const int G = kListG;
   RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, G, idx->pmax, idx->ldx, idx->lbin, st));
   size_t sm = sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) +
@@ -591,7 +594,8 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
     const int prof_slot = prof_begin("k_list_group", st);
     k_list_group<<<(unsigned)idx->n, kGroupThreads, sm, st>>>(
         idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->lbin, idx->ldx, G,
-        idx->xbin, idx->xg0, idx->XLO, idx->XHI, (uint32_t)idx->m, idx->Ut.rb3, idx->ptile3, bn,
+        idx->xbin, idx->xg0, idx->XLO, idx->XHI, (uint32_t)idx->m, idx->Ut.rb3, idx->ptile3,
+        bn_shift,
         tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff, idx->xbmax);
     prof_end(prof_slot, st, 0.0);
   }
