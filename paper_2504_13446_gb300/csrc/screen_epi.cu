@@ -1132,10 +1132,8 @@ struct EpiSkim {
   static const char *name() { return "k_screen<EpiSkim>"; }
   struct Thread {
     float b, xsb, pxs;
-    int64_t u;
-    int rb1;
+    int64_t u, fu;      // current row; row whose terms prb, pxs hold
     tc::RowBound prb;
-    bool have_pf;
   };
   static constexpr size_t kSmem = 0;
   int64_t nrows, ncols;
@@ -1145,26 +1143,19 @@ struct EpiSkim {
   const float *xs;
   SkimList L;
 
-  __device__ void fetch_row(int rb, int r, Thread &ts) const {
-    const int64_t u = (int64_t)rb * tc::BM + r;
-    if (u < nrows) {
-      ts.prb = rowb[u];
-      ts.pxs = xs[u];
-    }
-  }
-  __device__ void unit_begin(char *, const tc::Unit &u, int, Thread &ts) const {
-    ts.rb1 = u.rb1;
-    ts.have_pf = false;
-  }
+  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &ts) const { ts.fu = -1; }
+  // row-owned units: a row's bound terms are loaded once for all its column tiles
   __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
-    if (!ts.have_pf) fetch_row(rb, r, ts);
     ts.u = (int64_t)rb * tc::BM + r;
+    if (ts.u != ts.fu && ts.u < nrows) {
+      ts.prb = rowb[ts.u];
+      ts.pxs = xs[ts.u];
+      ts.fu = ts.u;
+    }
     if (ts.u < nrows) {
       ts.b = tc::screen_bound_tc(ts.prb, tileb[ct], gacc, gcan);
       ts.xsb = __fsub_rd(ts.pxs, ts.b);
     }
-    ts.have_pf = rb + 1 < ts.rb1;
-    if (ts.have_pf) fetch_row(rb + 1, r, ts);
   }
   __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
@@ -1221,11 +1212,9 @@ struct EpiSkim {
   __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
 };
 
-int skim_regions(int64_t n, int64_t nq) {
-  const int nct = (int)((nq + kSkimBN - 1) / kSkimBN);
+int skim_regions(int64_t n, int64_t) {
   const int nrb = (int)((n + tc::BM - 1) / tc::BM);
-  const int parts = std::max(1, std::min((2 * sm_count() + nct - 1) / nct, nrb));
-  return std::max(1, std::min(nct * parts, sm_count()));
+  return std::max(1, std::min(nrb, sm_count()));
 }
 
 rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, const float *xs,
@@ -1233,8 +1222,9 @@ rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, con
   const int64_t n = idx->n, nq = Qt.rows;
   tc::RowBound *tb = nullptr;
   RKR_TRY(tc_tile_bounds(Qt, kSkimBN, 1, &tb, st));
-  const int nct = (int)((nq + kSkimBN - 1) / kSkimBN);
-  tc::Schedule sch = col_schedule(n, nq, kSkimBN, (2 * sm_count() + nct - 1) / nct);
+  // row-owned units: U is read once, the query tiles stay in L2 (a launch of
+  // CTA pairs uses at most as many regions as this)
+  const tc::Schedule sch = row_schedule(n, nq, kSkimBN);
   if (std::min(sch.nunits, sm_count()) != list.regions) {
     cudaFreeAsync(tb, st);
     return fail(RKR_EINTERNAL, "skim list regions do not match the launch");
