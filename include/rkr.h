@@ -328,6 +328,13 @@ uint64_t rkr_kernel_launches(void);
 /* Release an index (NULL is allowed). */
 void rkr_index_free(rkr_index *idx);
 
+/* Device memory (not in the paper): the library allocates index arrays and
+ * per-call temporaries from one stream-ordered pool per device and keeps what
+ * it frees there, so later builds and queries reuse it without mapping memory
+ * again.  This call waits for the device, then returns the pool's unused memory
+ * of the current device to the driver.  Errors: RKR_ECUDA. */
+rkr_status rkr_release_cached_memory(void);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *rkr_last_error(void);
 

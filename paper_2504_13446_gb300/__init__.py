@@ -27,7 +27,8 @@ __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_ex
            "rkr_query_approx", "rkr_query_exact_subsets", "rkr_query_approx_subsets",
            "rkr_screen_scores", "rkr_screen_scores_static",
            "rkr_profile_start", "rkr_profile_stop", "Pruner", "rkr_rank_pairs",
-           "rkr_pair_features", "rkr_query_exact_learned", "EXPORTS"]
+           "rkr_pair_features", "rkr_query_exact_learned", "rkr_release_cached_memory",
+           "EXPORTS"]
 
 _lock = threading.Lock()
 _lib = None
@@ -97,6 +98,8 @@ def load() -> ctypes.CDLL:
         lib.rkr_index_timings.argtypes = [V, ctypes.POINTER(ctypes.c_double), I32]
         lib.rkr_kernel_launches.restype = ctypes.c_uint64
         lib.rkr_kernel_launches.argtypes = []
+        lib.rkr_release_cached_memory.restype = ctypes.c_int32
+        lib.rkr_release_cached_memory.argtypes = []
         lib.rkr_screen_scores.restype = I32
         lib.rkr_screen_scores.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
         lib.rkr_pruner_create.restype = I32
@@ -152,6 +155,11 @@ def rkr_profile_stop() -> dict:
 def kernel_launches() -> int:
     """Kernels launched by librkr.so in this process so far."""
     return int(load().rkr_kernel_launches())
+
+
+def rkr_release_cached_memory() -> None:
+    """Return the device memory the library keeps for reuse to the driver."""
+    _check(load().rkr_release_cached_memory())
 
 
 def _check(st: int):

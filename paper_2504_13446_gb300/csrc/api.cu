@@ -23,6 +23,39 @@ static std::atomic<uint64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// One pool per device, created on first use with that device current; freed
+// blocks stay in it for later allocations.  Falls back to the device's default
+// pool if a pool cannot be created.
+cudaMemPool_t lib_pool() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static cudaMemPool_t pools[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    cudaMemPool_t d = nullptr;
+    cudaDeviceGetDefaultMemPool(&d, dev < 0 ? 0 : dev);
+    return d;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps pr = {};
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &pr) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      cudaDeviceGetDefaultMemPool(&p, dev);
+    }
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 struct ProfRec {
   const char *name;
   cudaEvent_t a, b;
@@ -118,7 +151,7 @@ struct InView {
       dev = p;
       return RKR_OK;
     }
-    cudaError_t e = cudaMallocAsync(&own, bytes ? bytes : 1, s);
+    cudaError_t e = pool_malloc_async(&own, bytes ? bytes : 1, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       own = nullptr;
@@ -150,7 +183,7 @@ struct OutView {
       dev = p;
       return RKR_OK;
     }
-    cudaError_t e = cudaMallocAsync(&own, b ? b : 1, s);
+    cudaError_t e = pool_malloc_async(&own, b ? b : 1, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       own = nullptr;
@@ -181,7 +214,7 @@ __global__ void k_check_pairs(const int32_t *__restrict__ u, const int32_t *__re
 static rkr_status check_pairs(const int32_t *u, const int32_t *q, int64_t npairs, int64_t n,
                               int nq, int *bad_host, cudaStream_t st) {
   int *bad = nullptr;
-  RKR_CUDA(cudaMallocAsync(&bad, sizeof(int), st));
+  RKR_CUDA(pool_malloc_async(&bad, sizeof(int), st));
   RKR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
   k_check_pairs<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(u, q, npairs, n, nq, bad);
   note_launch();
@@ -364,9 +397,9 @@ static rkr_status stage_subsets(rkr_index *idx, int32_t nq, const std::vector<in
   const int64_t total = so[nq];
   RKR_TRY(qs.vsu.init(subset_users, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1), st));
   const int64_t words = (idx->n + 31) / 32;
-  RKR_CUDA(cudaMallocAsync(&qs.member, sizeof(uint32_t) * (size_t)words * nq, st));
+  RKR_CUDA(pool_malloc_async(&qs.member, sizeof(uint32_t) * (size_t)words * nq, st));
   RKR_CUDA(cudaMemsetAsync(qs.member, 0, sizeof(uint32_t) * (size_t)words * nq, st));
-  RKR_CUDA(cudaMallocAsync(&qs.soff, sizeof(int64_t) * (nq + 2), st));
+  RKR_CUDA(pool_malloc_async(&qs.soff, sizeof(int64_t) * (nq + 2), st));
   int *bad = (int *)(qs.soff + nq + 1);
   RKR_CUDA(cudaMemcpyAsync(qs.soff, so.data(), sizeof(int64_t) * (nq + 1),
                            cudaMemcpyHostToDevice, st));
@@ -394,8 +427,8 @@ static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const in
   int ok = 0;
   RKR_TRY(all_finite((const float *)qs.vq.dev, (int64_t)nq * d, &ok, st));
   if (!ok) return fail(RKR_EINVAL, "Q must be finite");
-  RKR_CUDA(cudaMallocAsync(&qs.qnrm, sizeof(float) * nq, st));
-  RKR_CUDA(cudaMallocAsync(&qs.off_d, sizeof(int64_t) * (nq + 1), st));
+  RKR_CUDA(pool_malloc_async(&qs.qnrm, sizeof(float) * nq, st));
+  RKR_CUDA(pool_malloc_async(&qs.off_d, sizeof(int64_t) * (nq + 1), st));
   RKR_CUDA(cudaMemcpyAsync(qs.off_d, off.data(), sizeof(int64_t) * (nq + 1),
                            cudaMemcpyHostToDevice, st));
   RKR_TRY(row_norms((const float *)qs.vq.dev, nq, d, nullptr, qs.qnrm, st));
@@ -408,11 +441,11 @@ static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const in
   qc.bf = idx->binfp;
   qc.xbf = idx->xbin;
   if (qmax > idx->pmax) {  // |u.q| may exceed the range the stored bin bounds assume
-    RKR_CUDA(cudaMallocAsync(&qs.bf_own, sizeof(BinFP) * idx->n, st));
+    RKR_CUDA(pool_malloc_async(&qs.bf_own, sizeof(BinFP) * idx->n, st));
     RKR_TRY(make_binfp(idx, qmax, qs.bf_own, st));
     qc.bf = qs.bf_own;
     if (idx->xbin) {
-      RKR_CUDA(cudaMallocAsync(&qs.xbf_own, sizeof(BinFP) * idx->n, st));
+      RKR_CUDA(pool_malloc_async(&qs.xbf_own, sizeof(BinFP) * idx->n, st));
       RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, idx->xg, qmax, nullptr, qs.xbf_own, st));
       qc.xbf = qs.xbf_own;
     }
@@ -570,7 +603,7 @@ rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int
                       &bad, st));
   if (bad) return fail(RKR_EINVAL, "pair user or query index out of range");
   float *Xu = nullptr;
-  RKR_CUDA(cudaMallocAsync(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
+  RKR_CUDA(pool_malloc_async(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
   struct Free {
     float *p;
     cudaStream_t s;
@@ -617,13 +650,13 @@ rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *
   RKR_TRY(vr.init(R, sizeof(float) * 64 * idx->d, st));
   float *Xu = nullptr;
   int32_t *keep_d = nullptr;
-  RKR_CUDA(cudaMallocAsync(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
+  RKR_CUDA(pool_malloc_async(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
   struct Free {
     void *p;
     cudaStream_t s;
     ~Free() { cudaFreeAsync(p, s); }
   } fr{Xu, st};
-  RKR_CUDA(cudaMallocAsync(&keep_d, sizeof(int32_t) * nq, st));
+  RKR_CUDA(pool_malloc_async(&keep_d, sizeof(int32_t) * nq, st));
   Free fk{keep_d, st};
   RKR_CUDA(cudaMemcpyAsync(keep_d, keeph.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
   RKR_TRY(user_features(idx, (const float *)vr.dev, Xu, st));
@@ -660,7 +693,7 @@ rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t 
     ~Guard() { tc_free(*a); tc_free(*b); }
   } g{&A, &B};
   int *err;
-  RKR_CUDA(cudaMallocAsync(&err, sizeof(int), st));
+  RKR_CUDA(pool_malloc_async(&err, sizeof(int), st));
   RKR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   rkr_status r;
   if (split == 2) {
@@ -727,6 +760,13 @@ rkr_status rkr_index_export(const rkr_index *idx, int32_t what, void *dst, int64
   if (!src) return fail(RKR_EINVAL, "export %d is not part of this index", what);
   if (bytes != size) return fail(RKR_EINVAL, "export %d needs %lld bytes", what, (long long)size);
   RKR_CUDA(cudaMemcpy(dst, src, (size_t)size, cudaMemcpyDefault));
+  return RKR_OK;
+}
+
+rkr_status rkr_release_cached_memory(void) {
+  g_err[0] = 0;
+  RKR_CUDA(cudaDeviceSynchronize());
+  RKR_CUDA(cudaMemPoolTrimTo(lib_pool(), 0));
   return RKR_OK;
 }
 

@@ -58,7 +58,7 @@ __global__ void k_max_float(const float *__restrict__ x, int64_t count, unsigned
 
 rkr_status max_float(const float *x, int64_t count, float *out_host, cudaStream_t st) {
   unsigned *dv;
-  RKR_CUDA(cudaMallocAsync(&dv, sizeof(unsigned), st));
+  RKR_CUDA(pool_malloc_async(&dv, sizeof(unsigned), st));
   RKR_CUDA(cudaMemsetAsync(dv, 0, sizeof(unsigned), st));
   k_max_float<<<256, 256, 0, st>>>(x, count, dv); note_launch();
   unsigned h = 0;
@@ -80,7 +80,7 @@ __global__ void k_all_finite(const float *__restrict__ x, int64_t count, int *ba
 
 rkr_status all_finite(const float *x, int64_t count, int *ok_host, cudaStream_t st) {
   int *dv;
-  RKR_CUDA(cudaMallocAsync(&dv, sizeof(int), st));
+  RKR_CUDA(pool_malloc_async(&dv, sizeof(int), st));
   RKR_CUDA(cudaMemsetAsync(dv, 0, sizeof(int), st));
   k_all_finite<<<512, 256, 0, st>>>(x, count, dv); note_launch();
   int h = 0;
@@ -521,10 +521,13 @@ static uint64_t splitmix64(uint64_t &x) {
 
 template <class T>
 static rkr_status dalloc(T **p, size_t count) {
+  // index arrays: from the library pool, usable on every stream once this returns
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  cudaError_t e = pool_malloc_async(p, count * sizeof(T), (cudaStream_t)0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)0);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    *p = nullptr;
     return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
   }
   return RKR_OK;
@@ -808,8 +811,11 @@ void index_release(rkr_index *idx) {
                   idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
                   idx->xfloor, idx->xloff, idx->xlcap, idx->xlist, idx->xlcnt,
                   idx->xbmax, idx->ptile3, idx->xcoff, idx->ldx, idx->lbin, idx->phk, idx->phv};
+  // nothing may still use the arrays when they go back to the pool
+  cudaDeviceSynchronize();
   for (void *p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, (cudaStream_t)0);
+  cudaStreamSynchronize((cudaStream_t)0);
   tc_free(idx->Ut);
   tc_free(idx->Pt);
 }

@@ -15,6 +15,18 @@
 
 namespace rkr {
 
+// Device memory of the library comes from one stream-ordered pool per device
+// that keeps what is freed (its release threshold is unlimited), so index
+// builds and query batches reuse the same blocks instead of mapping and
+// unmapping tens of GB each time.  rkr_release_cached_memory trims it.
+cudaMemPool_t lib_pool();
+
+template <class T>
+inline cudaError_t pool_malloc_async(T **p, size_t bytes, cudaStream_t st) {
+  return cudaMallocFromPoolAsync((void **)p, bytes, lib_pool(), st);
+}
+
+
 constexpr int kMaxD = 256;          // largest supported dimension
 constexpr int kMaxLevels = 32;      // rank levels 2^L used by the candidate filter
 constexpr int kMaxK = 4096;         // largest k per query

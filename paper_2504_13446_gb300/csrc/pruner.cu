@@ -261,7 +261,7 @@ rkr_status ensure_cap(rkr_pruner *pr, int64_t B, cudaStream_t st) {
                   (void *)pr->tb, (void *)pr->d2, (void *)pr->d1, (void *)pr->tg})
     if (q) cudaFreeAsync(q, st);
   auto al = [&](auto **q, size_t count) -> rkr_status {
-    cudaError_t e = cudaMallocAsync((void **)q, count * sizeof(**q), st);
+    cudaError_t e = pool_malloc_async((void **)q, count * sizeof(**q), st);
     if (e != cudaSuccess) return cuda_fail(e, "pruner scratch");
     return RKR_OK;
   };
@@ -357,7 +357,7 @@ struct InDev {
       return RKR_OK;
     }
     cudaGetLastError();
-    cudaError_t e = cudaMallocAsync(&own, bytes ? bytes : 1, s);
+    cudaError_t e = pool_malloc_async(&own, bytes ? bytes : 1, s);
     if (e != cudaSuccess) return cuda_fail(e, "input staging");
     e = cudaMemcpyAsync(own, src, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "input staging copy");
@@ -544,7 +544,7 @@ rkr_status rkr_pruner_train(rkr_pruner *pr, const float *X, const float *t, cons
   const int64_t B = std::min<int64_t>(batch, npairs);
   RKR_TRY(ensure_cap(pr, B, st));
   int64_t *perm_d = nullptr;
-  RKR_CUDA(cudaMallocAsync(&perm_d, sizeof(int64_t) * npairs, st));
+  RKR_CUDA(pool_malloc_async(&perm_d, sizeof(int64_t) * npairs, st));
   std::vector<int64_t> perm(npairs);
   uint64_t x = seed;
   double last = 0.0;

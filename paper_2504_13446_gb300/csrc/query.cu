@@ -661,7 +661,7 @@ struct DevBuf {
 template <class T>
 static rkr_status tmp_alloc(DevBuf &b, T **out, size_t count, cudaStream_t st) {
   if (count == 0) count = 1;
-  cudaError_t e = cudaMallocAsync(&b.p, count * sizeof(T), st);
+  cudaError_t e = pool_malloc_async(&b.p, count * sizeof(T), st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     b.p = nullptr;
@@ -837,7 +837,7 @@ static rkr_status skim_queries(const rkr_index *idx, const QueryCommon &qc, int 
   L.rcap = cap / regions;
   const size_t ent = (size_t)L.rcap * regions;
   auto try_alloc = [&](DevBuf &b, auto **p, size_t count) -> bool {
-    cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(**p), st);
+    cudaError_t e = pool_malloc_async((void **)p, count * sizeof(**p), st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return false;

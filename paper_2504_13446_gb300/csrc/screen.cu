@@ -56,7 +56,7 @@ rkr_status tc_stage(const float *X, int64_t rows, int d, TcSide &out, cudaStream
   out.kp = (d + 15) / 16 * 16;
   size_t cnt = (size_t)std::max<int64_t>(rows, 1) * out.kp;
   auto alloc = [&](void **p, size_t bytes) -> rkr_status {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = pool_malloc_async(p, bytes, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", bytes);
@@ -79,10 +79,11 @@ rkr_status tc_stage(const float *X, int64_t rows, int d, TcSide &out, cudaStream
 
 void tc_free(TcSide &s) {
   if (!s.owned) return;
-  if (s.hi) cudaFree(s.hi);
-  if (s.lo) cudaFree(s.lo);
-  if (s.rb1) cudaFree(s.rb1);
-  if (s.rb3) cudaFree(s.rb3);
+  // back to the pool once nothing uses them (the staging may have run on any stream)
+  cudaDeviceSynchronize();
+  for (void *p : {(void *)s.hi, (void *)s.lo, (void *)s.rb1, (void *)s.rb3})
+    if (p) cudaFreeAsync(p, (cudaStream_t)0);
+  cudaStreamSynchronize((cudaStream_t)0);
   s.hi = s.lo = nullptr;
   s.rb1 = s.rb3 = nullptr;
 }
@@ -103,7 +104,7 @@ __global__ void k_tile_bounds(const tc::RowBound *__restrict__ rb, int64_t rows,
 rkr_status tc_tile_bounds(const TcSide &b, int bn, int split, tc::RowBound **out,
                           cudaStream_t st) {
   int ntiles = (int)((b.rows + bn - 1) / bn);
-  cudaError_t e = cudaMallocAsync((void **)out, sizeof(tc::RowBound) * std::max(ntiles, 1), st);
+  cudaError_t e = pool_malloc_async((void **)out, sizeof(tc::RowBound) * std::max(ntiles, 1), st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(RKR_ENOMEM, "tile bounds allocation failed");
@@ -338,13 +339,13 @@ rkr_status tc_scores_e4m3(const float *U, int64_t n, const float *X, int64_t mx,
                     (void *)tb})
       if (p) cudaFreeAsync(p, st);
   };
-  if (cudaMallocAsync((void **)&qa, (size_t)n * kp, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&qb, (size_t)mx * kp, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&sa, sizeof(float) * n, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&sb, sizeof(float) * mx, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&ra, sizeof(tc::RowBound) * n, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&rb, sizeof(tc::RowBound) * mx, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&tb, sizeof(tc::RowBound) * ntiles, st) != cudaSuccess) {
+  if (pool_malloc_async((void **)&qa, (size_t)n * kp, st) != cudaSuccess ||
+      pool_malloc_async((void **)&qb, (size_t)mx * kp, st) != cudaSuccess ||
+      pool_malloc_async((void **)&sa, sizeof(float) * n, st) != cudaSuccess ||
+      pool_malloc_async((void **)&sb, sizeof(float) * mx, st) != cudaSuccess ||
+      pool_malloc_async((void **)&ra, sizeof(tc::RowBound) * n, st) != cudaSuccess ||
+      pool_malloc_async((void **)&rb, sizeof(tc::RowBound) * mx, st) != cudaSuccess ||
+      pool_malloc_async((void **)&tb, sizeof(tc::RowBound) * ntiles, st) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     return fail(RKR_ENOMEM, "FP8 screen scratch allocation failed");

@@ -258,15 +258,15 @@ rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   int2 *qitems;
   int *flags;  // [0] screen error, [1] overflow, [2] missing extreme
   const unsigned long long cap = std::max<int64_t>(64 * n, 1 << 16);
-  RKR_CUDA(cudaMallocAsync(&kmaxlo, sizeof(unsigned long long) * n, st));
-  RKR_CUDA(cudaMallocAsync(&kminhi, sizeof(unsigned long long) * n, st));
-  RKR_CUDA(cudaMallocAsync(&kmax, sizeof(unsigned long long) * n, st));
-  RKR_CUDA(cudaMallocAsync(&kmin, sizeof(unsigned long long) * n, st));
-  RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
-  RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
+  RKR_CUDA(pool_malloc_async(&kmaxlo, sizeof(unsigned long long) * n, st));
+  RKR_CUDA(pool_malloc_async(&kminhi, sizeof(unsigned long long) * n, st));
+  RKR_CUDA(pool_malloc_async(&kmax, sizeof(unsigned long long) * n, st));
+  RKR_CUDA(pool_malloc_async(&kmin, sizeof(unsigned long long) * n, st));
+  RKR_CUDA(pool_malloc_async(&qcount, sizeof(unsigned long long), st));
+  RKR_CUDA(pool_malloc_async(&qitems, sizeof(int2) * cap, st));
   double2 *ival;
-  RKR_CUDA(cudaMallocAsync(&ival, sizeof(double2) * cap, st));
-  RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 4, st));
+  RKR_CUDA(pool_malloc_async(&ival, sizeof(double2) * cap, st));
+  RKR_CUDA(pool_malloc_async(&flags, sizeof(int) * 4, st));
   RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 4, st));
   const tc::Schedule sch = row_schedule(n, m, BN);
@@ -276,7 +276,7 @@ rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   a.q = PairQueue{qitems, qcount, cap, flags + 1};
   // seeding launch over the first columns (the largest norms), then the full pass
   float2 *seed;
-  RKR_CUDA(cudaMallocAsync(&seed, sizeof(float2) * 2 * n, st));
+  RKR_CUDA(pool_malloc_async(&seed, sizeof(float2) * 2 * n, st));
   TcSide head = Pt;
   head.owned = false;
   head.rows = std::min<int64_t>(m, 4 * BN);
@@ -612,8 +612,8 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   RKR_TRY(tc_tile_bounds(Pt, BN, 1, &tb, st));
   float *g0f;
   int *flags;
-  RKR_CUDA(cudaMallocAsync(&g0f, sizeof(float) * n, st));
-  RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 2, st));
+  RKR_CUDA(pool_malloc_async(&g0f, sizeof(float) * n, st));
+  RKR_CUDA(pool_malloc_async(&flags, sizeof(int) * 2, st));
   RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
   k_xgrid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, idx->fmin, idx->delta, idx->xfloor,
                                                        idx->xg0, g0f);
@@ -1075,10 +1075,10 @@ rkr_status tc_rank_table(const rkr_index *idx, const TcSide &Ut, cudaStream_t st
     for (void *p : {(void *)W, (void *)qitems, (void *)qcount, (void *)flags})
       if (p) cudaFreeAsync(p, st);
   };
-  if (cudaMallocAsync((void **)&W, sizeof(uint32_t) * (size_t)n * (tau + 1), st) != cudaSuccess ||
-      cudaMallocAsync((void **)&qitems, sizeof(int2) * cap, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&qcount, sizeof(unsigned long long), st) != cudaSuccess ||
-      cudaMallocAsync((void **)&flags, sizeof(int) * 2, st) != cudaSuccess) {
+  if (pool_malloc_async((void **)&W, sizeof(uint32_t) * (size_t)n * (tau + 1), st) != cudaSuccess ||
+      pool_malloc_async((void **)&qitems, sizeof(int2) * cap, st) != cudaSuccess ||
+      pool_malloc_async((void **)&qcount, sizeof(unsigned long long), st) != cudaSuccess ||
+      pool_malloc_async((void **)&flags, sizeof(int) * 2, st) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     return RKR_OK;  // not enough memory for the scratch: the CUDA-core kernel runs instead
@@ -1406,10 +1406,10 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   A.kp = Ut.kp;
   A.owned = false;
   size_t cnt = (size_t)nseg * A.kp;
-  RKR_CUDA(cudaMallocAsync((void **)&A.hi, cnt * 2, st));
-  RKR_CUDA(cudaMallocAsync((void **)&A.lo, cnt * 2, st));
-  RKR_CUDA(cudaMallocAsync((void **)&A.rb1, sizeof(tc::RowBound) * nseg, st));
-  RKR_CUDA(cudaMallocAsync((void **)&A.rb3, sizeof(tc::RowBound) * nseg, st));
+  RKR_CUDA(pool_malloc_async((void **)&A.hi, cnt * 2, st));
+  RKR_CUDA(pool_malloc_async((void **)&A.lo, cnt * 2, st));
+  RKR_CUDA(pool_malloc_async((void **)&A.rb1, sizeof(tc::RowBound) * nseg, st));
+  RKR_CUDA(pool_malloc_async((void **)&A.rb3, sizeof(tc::RowBound) * nseg, st));
   dim3 blk(32, 8);
   {
     const int prof_slot = prof_begin("k_gather_side", st);
@@ -1429,11 +1429,11 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
               : (unsigned long long)std::min<int64_t>(std::max<int64_t>(128 * ncand, 1 << 24),
                                                       (int64_t)1 << 30);
   unsigned long long *nfp64;
-  RKR_CUDA(cudaMallocAsync(&nfp64, sizeof(unsigned long long), st));
+  RKR_CUDA(pool_malloc_async(&nfp64, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(nfp64, 0, sizeof(unsigned long long), st));
-  RKR_CUDA(cudaMallocAsync(&qcount, sizeof(unsigned long long), st));
-  RKR_CUDA(cudaMallocAsync(&qitems, sizeof(int2) * cap, st));
-  RKR_CUDA(cudaMallocAsync(&flags, sizeof(int) * 2, st));
+  RKR_CUDA(pool_malloc_async(&qcount, sizeof(unsigned long long), st));
+  RKR_CUDA(pool_malloc_async(&qitems, sizeof(int2) * cap, st));
+  RKR_CUDA(pool_malloc_async(&flags, sizeof(int) * 2, st));
   RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
   EpiRC e;
