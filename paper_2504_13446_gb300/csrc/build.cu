@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "index.cuh"
+#include "sort.cuh"
 #include "simt.cuh"
 
 namespace rkr {
@@ -94,22 +95,8 @@ rkr_status all_finite(const float *x, int64_t count, int *ok_host, cudaStream_t 
 
 // ------------------------------------------------------------------ sort
 
-// One compare-exchange stage of a bitonic network over (key, val), ascending by
-// (key, val).  Padding entries carry key = UINT64_MAX, val = INT32_MAX.
-__global__ void k_bitonic(uint64_t *key, int32_t *val, int64_t N, int64_t j, int64_t k) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int64_t ixj = i ^ j;
-  if (ixj <= i) return;
-  bool asc = (i & k) == 0;
-  uint64_t a = key[i], b = key[ixj];
-  int32_t va = val[i], vb = val[ixj];
-  bool gt = (a > b) || (a == b && va > vb);
-  if (gt == asc) {
-    key[i] = b; key[ixj] = a;
-    val[i] = vb; val[ixj] = va;
-  }
-}
+// Sorts of (key, val) records use the tiled bitonic sort of sort.cuh, ascending
+// by (key, val).  Padding entries carry key = UINT64_MAX, val = INT32_MAX.
 
 // FNV-1a over the 32-bit patterns of a row.
 __device__ __forceinline__ uint64_t row_hash(const float *x, int d) {
@@ -172,19 +159,7 @@ rkr_status query_self(const rkr_index *idx, const float *Q, int nq, int32_t *qse
 }
 
 rkr_status sort_pairs(uint64_t *key, int32_t *val, int64_t N_pow2, cudaStream_t st) {
-  int bs = 256;
-  unsigned grid = (unsigned)((N_pow2 + bs - 1) / bs);
-  for (int64_t k = 2; k <= N_pow2; k <<= 1)
-    for (int64_t j = k >> 1; j > 0; j >>= 1) {
-      {
-        const int prof_slot = prof_begin("k_bitonic", st);
-        k_bitonic<<<grid, bs, 0, st>>>(key, val, N_pow2, j, k);
-        prof_end(prof_slot, st, 0.0);
-        note_launch();
-      }
-    }
-  RKR_CUDA(cudaGetLastError());
-  return RKR_OK;
+  return bitonic_sort(Sort64{key, val}, N_pow2, "k_sort<64>", st);
 }
 
 // Keys for the descending-norm sort: ~bits(norm) (norms are >= +0).

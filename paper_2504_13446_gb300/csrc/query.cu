@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "index.cuh"
+#include "sort.cuh"
 #include "select.cuh"
 #include "simt.cuh"
 #include "tcops.cuh"
@@ -383,24 +384,6 @@ __global__ void k_cand_theta(int64_t count, const int32_t *__restrict__ cu,
   key_hi[i] = (uint64_t)u;
   key_lo[i] = (bits >> 63) ? ~bits : (bits | 0x8000000000000000ull);
   val[i] = (int32_t)i;
-}
-
-// One compare-exchange stage of a bitonic network over ((hi, lo), val).
-__global__ void k_bitonic128(uint64_t *hi, uint64_t *lo, int32_t *val, int64_t N, int64_t j,
-                             int64_t k) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int64_t ixj = i ^ j;
-  if (ixj <= i) return;
-  bool asc = (i & k) == 0;
-  uint64_t ah = hi[i], bh = hi[ixj], al = lo[i], bl = lo[ixj];
-  int32_t va = val[i], vb = val[ixj];
-  bool gt = ah > bh || (ah == bh && (al > bl || (al == bl && va > vb)));
-  if (gt == asc) {
-    hi[i] = bh; hi[ixj] = ah;
-    lo[i] = bl; lo[ixj] = al;
-    val[i] = vb; val[ixj] = va;
-  }
 }
 
 // Segments of equal user in the sorted order: start index and length (runs
@@ -1212,16 +1195,7 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   }
   note_launch();
   RKR_CUDA(cudaGetLastError());
-  for (int64_t k = 2; k <= Np2; k <<= 1)
-    for (int64_t j = k >> 1; j > 0; j >>= 1) {
-      {
-        const int prof_slot = prof_begin("k_bitonic128", st);
-        k_bitonic128<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(khi, klo, val, Np2, j, k);
-        prof_end(prof_slot, st, 0.0);
-      }
-      note_launch();
-    }
-  RKR_CUDA(cudaGetLastError());
+  RKR_TRY(bitonic_sort(Sort128{khi, klo, val}, Np2, "k_sort<128>", st));
   RKR_CUDA(cudaMemsetAsync(nseg_d, 0, sizeof(unsigned long long), st));
   k_segments<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, khi, nseg_d, sstart, slen);
   note_launch();
