@@ -487,9 +487,29 @@ __global__ void __launch_bounds__(kGroupThreads)
     const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
     if (i < L) ent[k] = row[i];
   }
+  // Column c = #{x_j <= v} of the list grid x_j = g0 + j dx.  The FP32 column
+  // coordinate (v - f)(1/dx), f = fl(g0), taken with directed roundings, is
+  // within e(v) = (|v - f| 2^-21 + |g0| 2^-23) / dx of (v - g0) / dx: the
+  // roundings of f, of 1/dx, of the difference and of the product add up to less
+  // than |g0| 2^-24 / dx + |v - f| 2^-21.6 / dx.  Only a coordinate interval that
+  // straddles a column edge is settled in FP64.
+  // (1/dx <= invd32 (1 + 2^-22), since invd32 is 1/dx rounded to nearest twice, and
+  // |g0| <= |f| (1 + 2^-23); both factors are formed in FP32 rounding up)
+  const bool tight = lb.invd32 > 0.0f && lb.err <= 1e6f;
+  const float inv_up = __fmul_ru(lb.invd32, 1.0f + 0x1p-22f);
+  const float e1 = __fmul_ru(inv_up, 0x1p-21f * (1.0f + 0x1p-20f));
+  const float e0 = __fadd_ru(
+      __fmul_ru(__fmul_ru(fabsf(lb.fmin32), (1.0f + 0x1p-23f) * 0x1p-23f), inv_up), 0x1p-30f);
   auto list_col = [&](float v) {
     int jlo, jhi;
-    bin_interval(lb, g0, G, v, v, jlo, jhi);
+    if (tight) {
+      const float alo = __fsub_rd(v, lb.fmin32), ahi = __fsub_ru(v, lb.fmin32);
+      const float e = __fmaf_ru(fmaxf(fabsf(alo), fabsf(ahi)), e1, e0);
+      jlo = bin_lo(__fsub_rd(__fmul_rd(alo, lb.invd32), e), G);
+      jhi = bin_hi(__fadd_ru(__fmul_ru(ahi, lb.invd32), e), G);
+    } else {
+      bin_interval(lb, g0, G, v, v, jlo, jhi);
+    }
     return jlo == jhi ? jlo : exact_j_near((double)v, g0, dx, jlo, jhi);
   };
 #pragma unroll
