@@ -39,6 +39,14 @@ WORKLOAD = "approx"
 C = 2.0
 
 
+# DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of this bench command
+# on the 1M x 100k workload: the recount screen's two launches of a step moved
+# 6.58 GB (bounds launch, CTA pairs) and 0.084 GB (exact launch).  Null for any
+# other kernel, and to be retaken whenever the kernel changes.
+TRAFFIC_PER_LAUNCH = {"k_screen<EpiRC>": (6.58e9 + 0.084e9) / 2}
+
+
 def _load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -221,7 +229,8 @@ def bench_ours(args):
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         achieved = work / (t_ms / 1000.0) / 1e12
         roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC_PER_LAUNCH.get(name),
                 "launches_per_step": n_l / args.steps, "ms_per_launch": t_ms / n_l,
                 "peak_source": f"{peak_src} bf16 dense, sustained (kernel timed inside a "
                                "long step); flops = 2 x rows x cols x K' x 3 (split product)"}
