@@ -1022,6 +1022,75 @@ struct EpiTable {
   static constexpr int kTableBN = 256;
 };
 
+// The rank table with every sampled row of the same weight w (equal buckets):
+// the decided pairs of a row block are counted per (user, count c) in shared
+// memory, 16-bit counters packed two to a word, and each unit writes its users'
+// rows W[u][c] = w * count once, instead of one global reduction per pair.
+// Undecided pairs are queued exactly as in EpiTable.  Needs tau + 1 <= 512 bins
+// and fewer than 2^16 sampled rows.
+struct EpiTableSm {
+  static const char *name() { return "k_screen<EpiTable>"; }
+  static constexpr bool kResident = true;
+  static constexpr int kBinWords = 256;   // 512 16-bit counters per user
+  struct Thread {
+    int64_t u;
+    tc::RowBound ru;
+    BinFP bf;
+    double fm;
+  };
+  static constexpr size_t kSmem = sizeof(uint32_t) * tc::BM * kBinWords;
+  int64_t nrows, ncols;
+  int tau;
+  const tc::RowBound *rowb, *colb;
+  tc::Gacc gacc;
+  float gcan;
+  const BinFP *binfp;
+  const double *fmin;
+  uint32_t wconst;          // the common weight of the sampled rows
+  uint32_t *W;              // n x (tau + 1)
+  PairQueue q;
+  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &) const {
+    uint32_t *H = (uint32_t *)S;
+    for (int i = et; i < tc::BM * kBinWords; i += 256) H[i] = 0u;
+  }
+  __device__ __forceinline__ void tile_begin(char *, int rb, int, int r, int, Thread &ts) const {
+    ts.u = (int64_t)rb * tc::BM + r;
+    if (ts.u < nrows) {
+      ts.ru = rowb[ts.u];
+      ts.bf = binfp[ts.u];
+      ts.fm = fmin[ts.u];
+    }
+  }
+  __device__ __forceinline__ void chunk(char *S, int, int ct, int r, int col, uint32_t,
+                                        const float (&v)[32], Thread &ts) const {
+    if (ts.u >= nrows) return;
+    const int64_t c0 = (int64_t)ct * EpiTable::kTableBN + col;
+    uint32_t *H = (uint32_t *)S + r * kBinWords;
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      const int64_t p = c0 + j;
+      if (p >= ncols) break;
+      const float b = tc::screen_bound_tc(ts.ru, colb[p], gacc, gcan);
+      int jlo, jhi;
+      bin_interval(ts.bf, ts.fm, tau, __fsub_rd(v[j], b), __fadd_ru(v[j], b), jlo, jhi);
+      if (jlo == jhi) atomicAdd(&H[jlo >> 1], 1u << ((jlo & 1) * 16));
+      else q.push_agg((int)ts.u, (int)p);
+    }
+  }
+  __device__ __forceinline__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &) const {
+    const uint32_t *H = (const uint32_t *)S;
+    const int bins = tau + 1;
+    const int64_t row0 = (int64_t)u.rb0 * tc::BM;
+    for (int i = et; i < tc::BM * bins; i += 256) {
+      const int r = i / bins, c = i - r * bins;
+      if (row0 + r >= nrows) continue;
+      const uint32_t cnt = (H[r * kBinWords + (c >> 1)] >> ((c & 1) * 16)) & 0xffffu;
+      W[(row0 + r) * bins + c] = cnt * wconst;
+    }
+  }
+};
+
 // Queued pairs: canonical score, its threshold count, weighted add.
 __global__ void k_table_resolve(const int2 *__restrict__ items,
                                 const unsigned long long *__restrict__ count,
@@ -1113,7 +1182,26 @@ rkr_status tc_rank_table(const rkr_index *idx, const TcSide &Ut, cudaStream_t st
   e.binfp = idx->binfp; e.fmin = idx->fmin; e.w = idx->sw; e.W = W;
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
   constexpr int BN = EpiTable::kTableBN;
-  rkr_status s = launch_screen<BN, 4>(Ut, St, 1, row_schedule(n, nsamp, BN), e, flags, st);
+  // every sampled row of one weight (equal buckets): counts in shared memory
+  std::vector<uint32_t> wh(nsamp);
+  RKR_CUDA(cudaMemcpyAsync(wh.data(), idx->sw, sizeof(uint32_t) * nsamp, cudaMemcpyDeviceToHost,
+                           st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  bool uniform = nsamp > 0 && nsamp < 65536 && tau + 1 <= 2 * EpiTableSm::kBinWords;
+  for (int i = 1; i < nsamp && uniform; ++i) uniform = wh[i] == wh[0];
+  rkr_status s;
+  if (uniform) {
+    EpiTableSm es;
+    es.nrows = n; es.ncols = nsamp; es.tau = tau;
+    es.rowb = Ut.rb3; es.colb = St.rb3;
+    es.gacc = e.gacc; es.gcan = e.gcan;
+    es.binfp = idx->binfp; es.fmin = idx->fmin; es.wconst = wh[0]; es.W = W;
+    es.q = e.q;
+    static_assert(tc::screen_smem_bytes<BN, 2, EpiTableSm>() <= 232448, "table smem");
+    s = launch_screen<BN, 2>(Ut, St, 1, row_schedule(n, nsamp, BN), es, flags, st);
+  } else {
+    s = launch_screen<BN, 4>(Ut, St, 1, row_schedule(n, nsamp, BN), e, flags, st);
+  }
   if (s == RKR_OK) {
     {
       ProfScope prof("k_table_resolve", st);
