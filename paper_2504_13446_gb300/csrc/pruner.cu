@@ -72,23 +72,84 @@ __global__ void k_mlp_weights(int F, int H, const float *__restrict__ p, Off o,
 // A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn].  Epilogue:
 // v = acc + bias[n] + tcol[m] * wcol[n] (each term optional); zout (FP32) gets v,
 // hout (BF16) gets relu(v) or v, fout (FP32) gets v.
-constexpr int GT = 64, GK = 16;
+constexpr int GT = 128, GK = 16;   // 128 x 128 output tile, K in steps of 16
 __global__ void __launch_bounds__(256)
     k_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int64_t sam,
                 int64_t sak, const __nv_bfloat16 *__restrict__ B, int64_t sbk, int64_t sbn,
                 const float *__restrict__ bias, const float *__restrict__ tcol,
                 const float *__restrict__ wcol, int relu, float *__restrict__ zout,
                 __nv_bfloat16 *__restrict__ hout, float *__restrict__ fout, int64_t ldc) {
-  __shared__ float As[GK][GT + 1], Bs[GK][GT + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  __shared__ __align__(16) float As[GK][GT + 4];
+  __shared__ __align__(16) float Bs[GK][GT + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  // the loads run along whichever index is contiguous in memory
+  const bool a_m_fast = sam == 1, b_n_fast = sbn == 1;
+  float acc[8][8] = {};
+  for (int k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+    for (int t = 0; t < (GT * GK) / 256; ++t) {
+      const int e = tid + t * 256;
+      const int mm = a_m_fast ? e % GT : e / GK, kk = a_m_fast ? e / GT : e % GK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? __bfloat162float(A[gm * sam + gk * sak]) : 0.0f;
+      const int nn = b_n_fast ? e % GT : e / GK, kb = b_n_fast ? e / GT : e % GK;
+      const int gn = n0 + nn, gk2 = k0 + kb;
+      Bs[kb][nn] = (gn < N && gk2 < K) ? __bfloat162float(B[gk2 * sbk + gn * sbn]) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      // rows ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx
+      const float4 a0 = *(const float4 *)&As[kk][ty * 4];
+      const float4 a1 = *(const float4 *)&As[kk][64 + ty * 4];
+      const float4 b0 = *(const float4 *)&Bs[kk][tx * 4];
+      const float4 b1 = *(const float4 *)&Bs[kk][64 + tx * 4];
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (gn >= N) continue;
+      float v = acc[i][j];
+      if (bias) v += bias[gn];
+      if (tcol) v = fmaf(tcol[gm], wcol[gn], v);
+      const int64_t at = (int64_t)gm * ldc + gn;
+      if (zout) zout[at] = v;
+      if (fout) fout[at] = v;
+      if (hout) hout[at] = __float2bfloat16_rn(relu ? fmaxf(v, 0.0f) : v);
+    }
+  }
+}
+
+constexpr int GS = 64;   // small tile: 64 x 64 outputs, 4 x 4 per thread
+__global__ void __launch_bounds__(256)
+    k_gemm_bf16_small(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int64_t sam,
+                int64_t sak, const __nv_bfloat16 *__restrict__ B, int64_t sbk, int64_t sbn,
+                const float *__restrict__ bias, const float *__restrict__ tcol,
+                const float *__restrict__ wcol, int relu, float *__restrict__ zout,
+                __nv_bfloat16 *__restrict__ hout, float *__restrict__ fout, int64_t ldc) {
+  __shared__ float As[GK][GS + 1], Bs[GK][GS + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * GS, n0 = blockIdx.x * GS;
   float acc[4][4] = {};
   for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+    for (int e = threadIdx.x; e < GS * GK; e += 256) {
       const int mm = e / GK, kk = e % GK;
       const int gm = m0 + mm, gk = k0 + kk;
       As[kk][mm] = (gm < M && gk < K) ? __bfloat162float(A[gm * sam + gk * sak]) : 0.0f;
-      const int nn = e % GT, kb = e / GT;
+      const int nn = e % GS, kb = e / GS;
       const int gn = n0 + nn, gk2 = k0 + kb;
       Bs[kb][nn] = (gn < N && gk2 < K) ? __bfloat162float(B[gk2 * sbk + gn * sbn]) : 0.0f;
     }
@@ -131,9 +192,18 @@ static void gemm(int M, int N, int K, const __nv_bfloat16 *A, int64_t sam, int64
                  const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, const float *bias,
                  const float *tcol, const float *wcol, int relu, float *zout, __nv_bfloat16 *hout,
                  float *fout, int64_t ldc, cudaStream_t st) {
-  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-  k_gemm_bf16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, tcol, wcol, relu,
-                                    zout, hout, fout, ldc);
+  // large tiles when they still give every SM a block; the gradient products
+  // (small outputs, long K) keep more blocks with small tiles
+  const int64_t big = (int64_t)((N + GT - 1) / GT) * ((M + GT - 1) / GT);
+  if (big >= 152) {
+    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
+    k_gemm_bf16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, tcol, wcol, relu,
+                                      zout, hout, fout, ldc);
+  } else {
+    dim3 grid((N + GS - 1) / GS, (M + GS - 1) / GS);
+    k_gemm_bf16_small<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, tcol, wcol,
+                                            relu, zout, hout, fout, ldc);
+  }
   note_launch();
 }
 
