@@ -40,12 +40,20 @@ WORKLOAD = "approx"
 C = 2.0
 
 
-# DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of this bench command
-# on the 1M x 100k workload: the recount screen's two launches of a step moved
-# 6.58 GB (bounds launch, CTA pairs) and 0.084 GB (exact launch).  Null for any
-# other kernel, and to be retaken whenever the kernel changes.
-TRAFFIC_PER_LAUNCH = {"k_screen<EpiRC>": (6.58e9 + 0.084e9) / 2}
+# DRAM bytes (read + written) per screened row, per launch, of the screens whose
+# traffic was captured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on
+# the small profiling case (`--case small`: 40k users, all 100k items), where
+# the rows a launch screens are known.  A full-size launch of the same kernel
+# reads the same item side per row block, so its traffic scales with its rows;
+# the bench multiplies this figure by the rows of the timed launches.  Empty
+# until a capture of the current kernel exists (traffic is then reported null).
+TRAFFIC_PER_ROW = {}
+
+# Products the tensor cores issue per pair of each screen, relative to the
+# method's one inner product of length d: the split screens issue three
+# products over K padded to a multiple of 16.
+SPLIT_SCREENS = ("k_screen<EpiRC>", "k_screen<EpiXT>", "k_screen<EpiSkim>",
+                 "k_screen<EpiTable>", "k_screen<EpiTableSm>", "k_screen<EpiTheta>")
 
 
 def _load_peaks():
@@ -149,14 +157,46 @@ def make_inputs(case="full"):
     return w, pos
 
 
-def run_step(rkr, U, P, Q, k, pos, w, device=True):
+def run_step(rkr, U, P, Q, k, pos, w, device=True, keep=False):
     idx = rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s, fbounds="exact", exact_table=True,
                     sample_pos=pos)
     a = idx.query_approx(Q, k, C, device=device)
     e = idx.query_exact(Q, k, device=device)
     t = idx.timings()
+    if keep:
+        return a, e, t, idx
     idx.close()
     return a, e, t
+
+
+def roofline_of(kernels, steps, peaks, peak_src, launches_rows=None):
+    """Roofline entry of the kernel with the largest device time in the timed region.
+
+    For a tensor-core screen, achieved = the method's flops (one inner product of
+    length d per screened pair: 2 * rows * cols * d) / its device time, against the
+    measured dense BF16 peak; the products the tensor cores actually issue (three
+    for the split form, K padded to a multiple of 16) are reported beside it."""
+    name = max(kernels, key=lambda kk: kernels[kk][1])
+    n_l, t_ms, work = kernels[name]
+    if work <= 0:
+        return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "launches_per_step": n_l / steps,
+                "ms_per_launch": t_ms / n_l}
+    peak = peaks["bf16_tflops"]
+    achieved = work / (t_ms / 1000.0) / 1e12
+    out = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
+           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+           "launches_per_step": n_l / steps, "ms_per_launch": t_ms / n_l,
+           "peak_source": f"{peak_src} bf16 dense burst peak (MEASURED_PEAKS.json bf16_tflops); "
+                          "achieved = 2 x rows x cols x d (the method's inner products) / "
+                          "CUDA-event time of the launches"}
+    if "bf16_tflops_sustained" in peaks:
+        out["frac_of_sustained"] = achieved / peaks["bf16_tflops_sustained"]
+    if name in SPLIT_SCREENS:
+        out["tensor_products_issued_per_pair"] = "3 x K' (K' = d rounded up to 16)"
+    if name in TRAFFIC_PER_ROW and launches_rows:
+        out["traffic"] = TRAFFIC_PER_ROW[name] * launches_rows / n_l
+    return out
 
 
 def bench_ours(args):
@@ -196,51 +236,52 @@ def bench_ours(args):
     if dist:
         dist.barrier()
     launches = rkr.kernel_launches() - launches0
-    kernels = rkr.rkr_profile_stop()
+    prof = rkr.rkr_profile_stop()
     clocks = sampler.stop()
     ms = job_ms(ev0.elapsed_time(ev1) / args.steps, dist)
+    kernels = {kk: v for kk, v in prof.items() if not kk.startswith("span:")}
+    spans = {kk[5:]: v for kk, v in prof.items() if kk.startswith("span:")}
 
     if args.case == "small":
         if rank == 0:
             print(json.dumps({"case": "small (profiling)", "ms_per_step": ms,
                               "kernels_ms_per_step": {kk: round(v[1] / args.steps, 3)
-                                                      for kk, v in kernels.items()}}))
+                                                      for kk, v in kernels.items()},
+                              "screen_rows_per_step": {
+                                  kk: v[2] / (2.0 * w.m * w.d) / args.steps
+                                  for kk, v in kernels.items() if v[2] > 0},
+                              "exact_stats": qstats[-1][1]}))
         return
     # end to end through the C ABI with host buffers: inputs in pinned host memory,
     # copied to the device inside the library, results read back to host arrays
-    Uh, Ph, Qh = (torch.from_numpy(a).pin_memory() for a in (w.U, w.P, w.Q))
+    Uh, Ph, Qh = (torch.from_numpy(a_).pin_memory() for a_ in (w.U, w.P, w.Q))
     kh = w.k.astype(np.int32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    a_h, e_h, _ = run_step(rkr, Uh, Ph, Qh, kh, pos, w, device=False)
+    a_h, e_h, _, idx = run_step(rkr, Uh, Ph, Qh, kh, pos, w, device=False, keep=True)
     e2e_s = time.perf_counter() - t0
     h2d = w.U.nbytes + w.P.nbytes + w.Q.nbytes + 4 * w.Q.shape[0] + pos.nbytes
     d2h = sum(v.nbytes for kk, v in a_h.items() if isinstance(v, np.ndarray) and kk != "offsets")
     d2h += e_h[0].nbytes + e_h[1].nbytes
 
+    # quality of the approximate answers of the step against its exact answers
+    # (after the timed region): exact ranks of every returned user by the exact path
+    nq = w.Q.shape[0]
+    qid = np.repeat(np.arange(nq, dtype=np.int32), np.diff(a_h["offsets"]))
+    r_c = idx.rank_pairs(w.Q, a_h["users"], qid)
+    idx.close()
+    quality = approx_quality(r_c, a_h["offsets"], e_h[1], C)
+    quality["case_b_queries"] = int(np.sum(a_h["case"] == 2))
+    precision = screen_precision(rkr, U, P)
+
     if rank != 0:
         return
-    nq = w.Q.shape[0]
     value = job_value(ws, nq, ms)
-    mean = lambda key: float(np.mean([s[key] for s in stage]))  # noqa: E731
-    # dominant kernel: the largest device time of the timed region, with its algorithmic
-    # flops (2 * rows * cols * K' * products for a tensor-core screen)
+    mean = lambda key: float(np.mean([s_[key] for s_ in stage]))  # noqa: E731
+    rows_of = {kk: v[2] / (2.0 * w.m * w.d) for kk, v in kernels.items() if v[2] > 0}
     name = max(kernels, key=lambda kk: kernels[kk][1])
-    n_l, t_ms, work = kernels[name]
-    if work > 0:
-        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        achieved = work / (t_ms / 1000.0) / 1e12
-        roof = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_PER_LAUNCH.get(name),
-                "launches_per_step": n_l / args.steps, "ms_per_launch": t_ms / n_l,
-                "peak_source": f"{peak_src} bf16 dense, sustained (kernel timed inside a "
-                               "long step); flops = 2 x rows x cols x K' x 3 (split product)"}
-    else:
-        roof = {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "launches_per_step": n_l / args.steps,
-                "ms_per_launch": t_ms / n_l}
-    top = sorted(kernels.items(), key=lambda kv: -kv[1][1])[:12]
+    roof = roofline_of(kernels, args.steps, peaks, peak_src, rows_of.get(name))
+    top = sorted(kernels.items(), key=lambda kv: -kv[1][1])[:14]
     qa0, qe0 = qstats[-1]
     cpu = cpu_baseline(w, pos)
     out = {
@@ -271,16 +312,33 @@ def bench_ours(args):
         },
         "candidates": {"approx": qa0["candidates"], "exact": qe0["candidates"],
                        "exact_recounted": qe0["recounted"],
-                       "exact_near_ties": qe0["near_ties"], "fp64_dots_exact": qe0["fp64_dots"],
+                       "exact_recount_users": qe0["recount_users"],
+                       "exact_recount_open": qe0["recount_open"],
                        "wide_queries": [qa0["wide_queries"], qe0["wide_queries"]],
                        "deep_queries": [qa0["deep_queries"], qe0["deep_queries"]]},
+        "approx_quality": quality,
+        "precision": {
+            "screen_sample": precision,
+            "exact_path": {
+                "near_ties": qe0["near_ties"],
+                "flagged_fraction": (qe0["near_ties"] / (qe0["recount_open"] * w.m)
+                                     if qe0["recount_open"] else 0.0),
+                "flagged_fraction_definition": "item scores of the exact recount that needed "
+                                               "canonical FP64 / item scores it screened",
+                "fp64_dots": qe0["fp64_dots"],
+                "max_rel_screen_err": qe0["max_rel_screen_err"],
+                "max_screen_err_over_bound": qe0["max_screen_err_ratio"]},
+            "approx_path": {"fp64_dots": qa0["fp64_dots"], "candidates": qa0["candidates"]},
+        },
         "roofline": roof,
         "kernels_ms_per_step": {kk: round(v[1] / args.steps, 3) for kk, v in top},
+        "spans_ms_per_step": {kk: round(v[1] / args.steps, 3) for kk, v in spans.items()},
         "cpu_baseline": cpu,
         "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "library": rkr.version(),
     }
     print(json.dumps(out))
 
@@ -461,6 +519,63 @@ def bench_reference(args):
     print(json.dumps(out))
 
 
+def approx_quality(ranks_c, off, best, c):
+    """Quality of c-approximate answers against the exact ones (Def. 3; the
+    accuracy and overall ratio of Section 5, "Criteria"), per query, aggregated.
+
+    ranks_c: exact ranks of the users each approximate answer returned; best: the
+    exact answer's ranks (the k smallest, ascending); off: per-query offsets of
+    both.  Position i pairs the i-th smallest rank of the returned set with the
+    i-th smallest rank overall.  Recall counts returned users whose rank is at
+    most the k-th smallest; a c-bound violation is a returned user ranked above
+    c times the k-th smallest rank."""
+    ranks_c = np.asarray(ranks_c, np.float64)
+    best = np.asarray(best, np.float64)
+    nq = len(off) - 1
+    acc = np.empty(nq)
+    ratio = np.empty(nq)
+    rec = np.empty(nq)
+    viol = np.zeros(nq, np.int64)
+    for q in range(nq):
+        sl = slice(int(off[q]), int(off[q + 1]))
+        got = np.sort(ranks_c[sl], kind="stable")
+        b = best[sl]
+        kth = b[-1]
+        acc[q] = np.mean(got <= c * b)
+        ratio[q] = np.mean(got / b)
+        rec[q] = np.mean(got <= kth)
+        viol[q] = int(np.sum(got > c * kth))
+    worst = int(np.argmax(ratio)) if nq else -1
+    return {"queries": nq, "accuracy": float(acc.mean()), "overall_ratio": float(ratio.mean()),
+            "recall_at_k": float(rec.mean()), "c_bound_violations": int(viol.sum()),
+            "queries_with_violations": int(np.sum(viol > 0)),
+            "queries_below_accuracy_1": int(np.sum(acc < 1.0)),
+            "worst_query": {"index": worst, "overall_ratio": float(ratio[worst]) if nq else None,
+                            "accuracy": float(acc[worst]) if nq else None}}
+
+
+def screen_precision(rkr, U, P, rows=256):
+    """Error of the tensor-core screen against FP64 on a sample: the first `rows`
+    users against every item, single and split products.  The FP64 reference is
+    a float64 product of the float32 inputs on the GPU (its own rounding, about
+    1e-16 relative, is far below the screen's)."""
+    import torch
+    Us = U[:rows].contiguous()
+    ref = (Us.double() @ P.double().T).cpu().numpy()
+    nu = torch.linalg.vector_norm(Us.double(), dim=1).cpu().numpy()
+    npn = torch.linalg.vector_norm(P.double(), dim=1).cpu().numpy()
+    scale = np.outer(nu, npn)
+    out = {"sample": f"{rows} users x {P.shape[0]} items"}
+    for name, split in (("single_bf16", False), ("split_bf16", True)):
+        s_, b_ = rkr.rkr_screen_scores(Us, P, split=split)
+        err = np.abs(s_.astype(np.float64) - ref)
+        out[name] = {"max_abs_err": float(err.max()),
+                     "max_rel_err": float((err / scale).max()),
+                     "max_err_over_bound": float((err / b_.astype(np.float64)).max()),
+                     "mean_bound_rel": float((b_ / scale).mean())}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,6 +587,11 @@ def main():
                          "learned: train the rank regressor and compare the learned cut "
                          "with the plain exact query")
     args = ap.parse_args()
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl == "ours":
+        # one rank per GPU: load the build without cluster multicast
+        os.environ["RKR_LIB_VARIANT"] = "replica"
+        from paper_2504_13446_gb300 import buildlib
+        buildlib.build(variant="replica")
     if args.impl == "reference":
         bench_reference(args)
     elif args.case == "learned":

@@ -84,7 +84,10 @@ typedef struct {
   int64_t fp64_dots;        /* canonical FP64 inner products computed */
   int64_t near_ties;        /* item scores too close to u.q for the screen to decide */
   int32_t wide_queries;     /* queries whose cutoff fell to the last level */
-  double max_rel_screen_err;/* reserved */
+  double max_rel_screen_err;/* exact path: largest |s_hat - s(u,p)| / (||u|| ||p||) over the
+                               item scores of this call whose tensor-core screened value
+                               s_hat was compared with the canonical FP64 score s (near-ties
+                               in the tail lists); norms are FP32 upper bounds; 0 if none */
   double ms_theta;          /* device time of the u.q screening passes */
   double ms_resolve;        /* device time of candidate resolution */
   double ms_select;         /* device time of per-query selection */
@@ -95,6 +98,14 @@ typedef struct {
                                level is the smallest L with 2^L - 1 >= m / 128, or the
                                value of the environment variable RKR_SKIP_LEVEL; results
                                do not depend on it. */
+  int64_t recount_users;    /* exact path: distinct users among the recounted candidates */
+  int64_t recount_open;     /* exact path: recounted candidates whose count interval was still
+                               open after the interval pass; each of their m item scores is
+                               placed exactly, and near_ties of them needed FP64, so
+                               near_ties / (recount_open * m) is the flagged fraction */
+  double max_screen_err_ratio; /* exact path: largest |s_hat - s(u,p)| / b over the same pairs
+                               as max_rel_screen_err, b the rigorous screen bound (a sound
+                               bound keeps it <= 1) */
 } rkr_query_stats;
 
 /*
@@ -201,7 +212,9 @@ rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t 
  *   every buffer.
  *   The first call on a device looks up the array's address
  *   (cudaGetSymbolAddress, with that device current) and keeps it; make that
- *   first call before any stream capture.  Every call on a device uses the same
+ *   first call before any stream capture.  The kept address belongs to the
+ *   device's primary context: after cudaDeviceReset on that device the process
+ *   must not call this entry point again.  Every call on a device uses the same
  *   array: calls that overlap in time (several host threads or streams) race
  *   on it and must be serialized by the caller.  The call synchronizes
  *   `stream` before it returns.
@@ -217,9 +230,11 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  * on.  rkr_profile_stop synchronizes those events and writes one text line per
  * kernel, "name launches total_ms work", into report (len bytes including the
  * terminating NUL; RKR_EINVAL if it does not fit).  work is the summed
- * algorithmic work of the launches: 2 * rows * cols * K' * products flops for a
- * tensor-core screen (K' = d rounded up to 16, products = 3 for the split
- * product), 0 where none is stated.  Not thread-safe against concurrent queries
+ * algorithmic work of the launches: 2 * rows * cols * d flops for a tensor-core
+ * screen (one inner product of length d per pair: the method's work, not the
+ * three products of the split form or the padding of K), 0 where none is stated.
+ * Names starting with "span:" are stretches of work spanning several launches
+ * (their time overlaps the kernels listed inside them).  Not thread-safe against concurrent queries
  * on other threads beyond what the shared event list allows.
  */
 /*
@@ -325,6 +340,19 @@ rkr_status rkr_index_timings(const rkr_index *idx, double *out, int32_t count);
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t rkr_kernel_launches(void);
 
+/* Number of device allocations this library has requested in this process
+ * (stream-ordered pool allocations and the pruner's cudaMalloc calls; not in the
+ * paper).  A call that allocates nothing leaves it unchanged. */
+uint64_t rkr_device_allocations(void);
+
+/* Test hook (not in the paper): the number of try_wait rounds after which the
+ * epilogue warps of the tensor-core screens give up waiting for an accumulator
+ * tile; the kernel then records the timeout, lets the MMAs and loads already
+ * issued finish, and the call returns RKR_ETIMEOUT.  0 gives up at the first
+ * wait; a negative value restores the default (2^22 rounds).  Process-wide;
+ * takes effect for launches that start after the call.  RKR_EINVAL above 2^32 - 1. */
+rkr_status rkr_set_wait_limit(int64_t rounds);
+
 /* Release an index (NULL is allowed). */
 void rkr_index_free(rkr_index *idx);
 
@@ -338,7 +366,10 @@ rkr_status rkr_release_cached_memory(void);
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *rkr_last_error(void);
 
-/* Library version string. */
+/* Library version string; it names the build: the single-GPU build (row-owned
+ * screens run as CTA pairs that share B tiles by cluster multicast) or the
+ * replica build (no cluster multicast; same results bit for bit) that a
+ * process uses when it is one rank of a multi-GPU job. */
 const char *rkr_version(void);
 
 #ifdef __cplusplus

@@ -28,7 +28,7 @@ __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_ex
            "rkr_screen_scores", "rkr_screen_scores_static",
            "rkr_profile_start", "rkr_profile_stop", "Pruner", "rkr_rank_pairs",
            "rkr_pair_features", "rkr_query_exact_learned", "rkr_release_cached_memory",
-           "EXPORTS"]
+           "rkr_set_wait_limit", "device_allocations", "version", "EXPORTS"]
 
 _lock = threading.Lock()
 _lib = None
@@ -57,22 +57,26 @@ class QueryStats(ctypes.Structure):
                 ("wide_queries", ctypes.c_int32), ("max_rel_screen_err", ctypes.c_double),
                 ("ms_theta", ctypes.c_double), ("ms_resolve", ctypes.c_double),
                 ("ms_select", ctypes.c_double), ("recounted", ctypes.c_int64),
-                ("deep_queries", ctypes.c_int32)]
+                ("deep_queries", ctypes.c_int32), ("recount_users", ctypes.c_int64),
+                ("recount_open", ctypes.c_int64), ("max_screen_err_ratio", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 def load() -> ctypes.CDLL:
-    """Load librkr.so; raises RuntimeError when it has not been built."""
+    """Load the library build this process uses (``buildlib.selected_variant()``:
+    librkr.so, or librkr_replica.so with RKR_LIB_VARIANT=replica); raises
+    RuntimeError when it has not been built."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(buildlib.LIB):
-            raise RuntimeError(f"{buildlib.LIB} is missing: build it with "
+        path = buildlib.lib_path(buildlib.selected_variant())
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
                                "paper_2504_13446_gb300.buildlib.build()")
-        lib = ctypes.CDLL(buildlib.LIB)
+        lib = ctypes.CDLL(path)
         V, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
         lib.rkr_build.restype = I32
         lib.rkr_build.argtypes = [V, I64, V, I64, I32, ctypes.POINTER(_BuildParams), V,
@@ -130,6 +134,10 @@ def load() -> ctypes.CDLL:
         lib.rkr_profile_stop.argtypes = [ctypes.c_char_p, I64]
         lib.rkr_screen_scores_static.restype = I32
         lib.rkr_screen_scores_static.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
+        lib.rkr_device_allocations.restype = ctypes.c_uint64
+        lib.rkr_device_allocations.argtypes = []
+        lib.rkr_set_wait_limit.restype = I32
+        lib.rkr_set_wait_limit.argtypes = [I64]
         lib.rkr_last_error.restype = ctypes.c_char_p
         lib.rkr_version.restype = ctypes.c_char_p
         _lib = lib
@@ -155,6 +163,21 @@ def rkr_profile_stop() -> dict:
 def kernel_launches() -> int:
     """Kernels launched by librkr.so in this process so far."""
     return int(load().rkr_kernel_launches())
+
+
+def device_allocations() -> int:
+    """Device allocations librkr has requested in this process so far."""
+    return int(load().rkr_device_allocations())
+
+
+def rkr_set_wait_limit(rounds: int) -> None:
+    """Test hook: try_wait rounds of the screens' epilogue wait (negative = default)."""
+    _check(load().rkr_set_wait_limit(int(rounds)))
+
+
+def version() -> str:
+    """The library's version string, naming its build."""
+    return load().rkr_version().decode()
 
 
 def rkr_release_cached_memory() -> None:
@@ -210,6 +233,17 @@ def _empty(shape, dtype, device: bool):
 
 def _shape(x):
     return tuple(x.shape)
+
+
+def _same_device(*arrays):
+    """CUDA tensors among the arguments must be on the current device (the library
+    takes a device pointer as memory of the current device)."""
+    devs = {a.device.index for a in arrays if _is_torch(a) and a.is_cuda}
+    if devs:
+        import torch
+        cur = torch.cuda.current_device()
+        if devs != {cur}:
+            raise RKRError(1, f"CUDA tensors must be on the current device cuda:{cur}")
 
 
 def rkr_build(U, P, *, tau: int = 500, omega: int = 10, s: int = 100, fbounds: str = "exact",
@@ -359,7 +393,10 @@ def rkr_screen_scores(U, X, *, split: bool = False, stream=None):
     """Tensor-core screened scores and their error bounds for every pair (n x mx each)."""
     lib = load()
     n, d = _shape(U)
-    mx, _ = _shape(X)
+    mx, dx = _shape(X)
+    if dx != d:
+        raise RKRError(1, f"X has {dx} columns, U has {d}")
+    _same_device(U, X)
     pu, ku = _ptr(U, np.float32)
     px, kx = _ptr(X, np.float32)
     s = np.empty((n, mx), dtype=np.float32)
@@ -375,11 +412,17 @@ def rkr_screen_scores_static(U, X, out_s, out_b, *, split: bool = False, stream=
     U (n x d), X (mx x d), out_s and out_b (n x mx, float32) must be CUDA tensors."""
     lib = load()
     n, d = _shape(U)
-    mx, _ = _shape(X)
+    mx, dx = _shape(X)
+    if dx != d:
+        raise RKRError(1, f"X has {dx} columns, U has {d}")
     for t in (U, X, out_s, out_b):
         if not (_is_torch(t) and t.is_cuda and t.is_contiguous()
                 and str(t.dtype) == "torch.float32"):  # noqa: E129
             raise RKRError(1, "rkr_screen_scores_static takes contiguous float32 CUDA tensors")
+    import torch
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in (U, X, out_s, out_b)):
+        raise RKRError(1, f"every tensor must be on the current device cuda:{dev}")
     if tuple(out_s.shape) != (n, mx) or tuple(out_b.shape) != (n, mx):
         raise RKRError(1, "output shape must be (n, mx)")
     _check(lib.rkr_screen_scores_static(U.data_ptr(), n, X.data_ptr(), mx, d, int(split),

@@ -23,6 +23,16 @@ static std::atomic<uint64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static std::atomic<uint64_t> g_allocs{0};
+void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
+
+// Epilogue wait limit of the screens (rkr_set_wait_limit); negative = default.
+static std::atomic<int64_t> g_epi_wait{-1};
+uint32_t epi_wait_limit() {
+  const int64_t v = g_epi_wait.load(std::memory_order_relaxed);
+  return v < 0 ? tc::kWaitLimit : (uint32_t)v;
+}
+
 // One pool per device, created on first use with that device current; freed
 // blocks stay in it for later allocations.  Falls back to the device's default
 // pool if a pool cannot be created.
@@ -243,9 +253,24 @@ extern "C" {
 
 const char *rkr_last_error(void) { return g_err; }
 
-const char *rkr_version(void) { return "rkr 0.1 (sm_103a)"; }
+const char *rkr_version(void) {
+#ifdef RKR_CLUSTER_MULTICAST
+  return "rkr 0.2 (sm_103a, single-GPU build: CTA pairs with cluster multicast)";
+#else
+  return "rkr 0.2 (sm_103a, replica build: no cluster multicast)";
+#endif
+}
 
 uint64_t rkr_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+uint64_t rkr_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
+
+rkr_status rkr_set_wait_limit(int64_t rounds) {
+  if (rounds > (int64_t)UINT32_MAX) return fail(RKR_EINVAL, "wait limit %lld too large",
+                                                (long long)rounds);
+  g_epi_wait.store(rounds < 0 ? -1 : rounds, std::memory_order_relaxed);
+  return RKR_OK;
+}
 
 rkr_status rkr_index_timings(const rkr_index *idx, double *out, int32_t count) {
   if (!idx || !out || count < 0) return fail(RKR_EINVAL, "null argument");
@@ -677,7 +702,7 @@ rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t 
   g_err[0] = 0;
   if (!U || !X || !out_s || !out_b) return fail(RKR_EINVAL, "null argument");
   if (n < 1 || mx < 1 || d < 1 || d > kMaxD) return fail(RKR_EINVAL, "bad sizes");
-  if (n * mx > ((int64_t)1 << 31)) return fail(RKR_EINVAL, "n * mx too large");
+  if (mx > ((int64_t)1 << 31) / n) return fail(RKR_EINVAL, "n * mx too large");
   RKR_TRY(check_device());
   cudaStream_t st = (cudaStream_t)stream;
   InView vu, vx;

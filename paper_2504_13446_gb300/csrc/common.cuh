@@ -21,8 +21,12 @@ namespace rkr {
 // unmapping tens of GB each time.  rkr_release_cached_memory trims it.
 cudaMemPool_t lib_pool();
 
+// Count of device allocations the library has requested (rkr_device_allocations).
+void note_alloc();
+
 template <class T>
 inline cudaError_t pool_malloc_async(T **p, size_t bytes, cudaStream_t st) {
+  note_alloc();
   return cudaMallocFromPoolAsync((void **)p, bytes, lib_pool(), st);
 }
 
@@ -229,6 +233,16 @@ __device__ __forceinline__ bool in_subset(const uint32_t *__restrict__ member, i
 // Level boundaries: level L holds counts N <= B_L = scale * (2^L - 1).
 __host__ __device__ __forceinline__ uint64_t level_bound(int L, uint32_t scale) {
   return (uint64_t)scale * (((uint64_t)1 << L) - 1);
+}
+
+// Float with the given bit pattern (host and device).
+__host__ __device__ __forceinline__ float u32_float(uint32_t b) {
+  union {
+    uint32_t u;
+    float f;
+  } x;
+  x.u = b;
+  return x.f;
 }
 
 // Order-preserving key of a non-negative double.

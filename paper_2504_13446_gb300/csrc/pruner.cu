@@ -494,6 +494,7 @@ rkr_status rkr_pruner_create(int32_t F, int32_t H, uint64_t seed, rkr_pruner **o
   for (int64_t i = 0; i < (int64_t)H * H; ++i) init[o.V2 + i] = (float)(v2 + 0.1 * normal(x));
   for (int i = 0; i < H; ++i) init[o.v3 + i] = (float)v3;
   auto al = [&](auto **q, size_t count) -> rkr_status {
+    note_alloc();
     cudaError_t e = cudaMalloc((void **)q, count * sizeof(**q));
     if (e != cudaSuccess) return cuda_fail(e, "pruner allocation");
     return RKR_OK;

@@ -394,6 +394,7 @@ __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count || key_hi[i] == ~0ull) return;
   if (i > 0 && key_hi[i] == key_hi[i - 1]) return;
+  atomicAdd(&nseg[1], 1ull);   // distinct users
   int64_t e = i + 1;
   while (e < count && key_hi[e] == key_hi[i]) ++e;
   // a user's run is cut into segments of at most kRecountSeg thresholds, which
@@ -538,7 +539,15 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
       tlo = thi = theta;
       exact = true;
     }
-    if (canon_dot(uu, pp, d) > theta) ++above;
+    const double sc = canon_dot(uu, pp, d);
+    if (sc > theta) ++above;
+    // screen error of this pair against its canonical score: relative to the
+    // bound (at most 1 for a sound bound) and to the norm bounds ||u|| ||p||
+    const double er = fabs((double)v - sc);
+    const float ratio = (float)(er / (double)b);
+    const float rel = (float)(er / ((double)unrm[u] * (double)pnrm_s[p]));
+    atomicMax(&stat[2], (unsigned long long)__float_as_uint(ratio));
+    atomicMax(&stat[3], (unsigned long long)__float_as_uint(rel));
   }
   ccount[i] = above;
   clb[i] = above;
@@ -1145,7 +1154,7 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
                                      const int32_t *cu_all, const int32_t *cq_all,
                                      const int32_t *qself, uint32_t *ccount_all,
                                      uint32_t *clb_all, unsigned long long *ties_d,
-                                     cudaStream_t st) {
+                                     cudaStream_t st, int64_t *nusers = nullptr) {
   const int bs = 256;
   DevBuf bcu, bcq, bci, bcc, bcur;
   int32_t *cu, *cq, *ci;
@@ -1186,7 +1195,7 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   RKR_TRY(tmp_alloc(b6, &slen, cnt, st));
   RKR_TRY(tmp_alloc(b7, &hist, 2 * cnt, st));
   RKR_TRY(tmp_alloc(b8, &ths, cnt, st));
-  RKR_TRY(tmp_alloc(b9, &nseg_d, 1, st));
+  RKR_TRY(tmp_alloc(b9, &nseg_d, 2, st));
   {
     const int prof_slot = prof_begin("k_cand_theta", st);
     k_cand_theta<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(cnt, cu, cq, idx->U, Qd, idx->d,
@@ -1196,13 +1205,15 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   note_launch();
   RKR_CUDA(cudaGetLastError());
   RKR_TRY(bitonic_sort(Sort128{khi, klo, val}, Np2, "k_sort<128>", st));
-  RKR_CUDA(cudaMemsetAsync(nseg_d, 0, sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(nseg_d, 0, 2 * sizeof(unsigned long long), st));
   k_segments<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, khi, nseg_d, sstart, slen);
   note_launch();
   RKR_CUDA(cudaGetLastError());
-  unsigned long long nseg = 0;
-  RKR_CUDA(cudaMemcpyAsync(&nseg, nseg_d, sizeof(nseg), cudaMemcpyDeviceToHost, st));
+  unsigned long long segu[2] = {0, 0};
+  RKR_CUDA(cudaMemcpyAsync(segu, nseg_d, sizeof(segu), cudaMemcpyDeviceToHost, st));
   RKR_CUDA(cudaStreamSynchronize(st));
+  const unsigned long long nseg = segu[0];
+  if (nusers) *nusers += (int64_t)segu[1];
   DevBuf b10, b11;
   int32_t *suser, *sself;
   RKR_TRY(tmp_alloc(b10, &suser, nseg, st));
@@ -1219,7 +1230,7 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     RKR_CUDA(cudaMemsetAsync(hist_hi, 0, sizeof(uint32_t) * 2 * cnt, st));
   }
   {
-    ProfScope prof(clb_all ? "recount(bounds)" : "recount(exact)", st, (double)nseg);
+    ProfScope prof(clb_all ? "span:recount(bounds)" : "span:recount(exact)", st, 0.0);
     RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, sself,
                        ths, hist, hist_hi, st, refined));
   }
@@ -1573,12 +1584,14 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   RKR_CUDA(cudaMemsetAsync(ties_d, 0, 2 * sizeof(unsigned long long), st));
   DevBuf bls;
   unsigned long long *lstat;
-  RKR_TRY(tmp_alloc(bls, &lstat, 2, st));
+  RKR_TRY(tmp_alloc(bls, &lstat, 4, st));
   DevBuf bqs;
   int32_t *qself;
   RKR_TRY(tmp_alloc(bqs, &qself, nq, st));
   RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
   int64_t fallback = 0, list_fp64 = 0, cut_total = 0;
+  double err_ratio = 0.0, err_rel = 0.0;
+  int64_t recount_users = 0, recount_open = 0;
   unsigned long long lstat_host_fb = 0;
   Plan plan;
   Timer t1(st);
@@ -1627,7 +1640,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       uint32_t *clb;
       RKR_TRY(tmp_alloc(bfb, &cu_fb, cnt, st));
       RKR_TRY(tmp_alloc(blb, &clb, cnt, st));
-      RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
+      RKR_CUDA(cudaMemsetAsync(lstat, 0, 4 * sizeof(unsigned long long), st));
       {
         const int prof_slot = prof_begin("k_list_rank", st);
         k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
@@ -1658,9 +1671,11 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
                                  cudaMemcpyDeviceToHost, st));
         RKR_CUDA(cudaStreamSynchronize(st));
       }
-      unsigned long long ls[2] = {0, 0};
+      unsigned long long ls[4] = {0, 0, 0, 0};
       RKR_CUDA(cudaMemcpyAsync(ls, lstat, sizeof(ls), cudaMemcpyDeviceToHost, st));
       RKR_CUDA(cudaStreamSynchronize(st));
+      err_ratio = std::max(err_ratio, (double)u32_float((uint32_t)ls[2]));
+      err_rel = std::max(err_rel, (double)u32_float((uint32_t)ls[3]));
       if (lp && lstat_host_fb > 0) {  // learned cut of the candidates still to be recounted
         RKR_TRY(learned_cut(idx, qc, lp, qa, qb, cnt, (int64_t)lstat_host_fb, qoff_rel, cursor,
                             cu, cq, cu_fb, ccount, &cut_total, st));
@@ -1682,7 +1697,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
         // candidates that can still make the k smallest and whose interval is
         // open get their undecided items resolved
         RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr,
-                                   st));
+                                   st, &recount_users));
         {
           const int prof_slot = prof_begin("k_recount_filter", st);
           k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
@@ -1701,6 +1716,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
         note_launch();
         RKR_CUDA(cudaMemcpyAsync(&h2, nfb2, sizeof(h2), cudaMemcpyDeviceToHost, st));
         RKR_CUDA(cudaStreamSynchronize(st));
+        recount_open += (int64_t)h2;
         if (h2 > 0)
           RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, nullptr, ties_d,
                                      st));
@@ -1735,6 +1751,10 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
     stats->fp64_dots = 2 * total + (int64_t)tiesv[1] + list_fp64;
     stats->near_ties = (int64_t)tiesv[0];
     stats->recounted = fallback;
+    stats->recount_users = recount_users;
+    stats->recount_open = recount_open;
+    stats->max_rel_screen_err = err_rel;
+    stats->max_screen_err_ratio = err_ratio;
     if (lp) stats->candidates = total - cut_total;  // candidates left by the learned cut
     stats->wide_queries = wide;
     stats->deep_queries = (int32_t)plan.deep.size();
@@ -1763,9 +1783,9 @@ rkr_status run_rank_pairs(const rkr_index *idx, const QueryCommon &qc, int nq, i
   RKR_TRY(tmp_alloc(bc, &ccount, npairs, st));
   RKR_TRY(tmp_alloc(bl, &clb, npairs, st));
   RKR_TRY(tmp_alloc(bf, &cu_fb, npairs, st));
-  RKR_TRY(tmp_alloc(bs, &lstat, 2, st));
+  RKR_TRY(tmp_alloc(bs, &lstat, 4, st));
   RKR_TRY(tmp_alloc(bt, &ties, 2, st));
-  RKR_CUDA(cudaMemsetAsync(lstat, 0, 2 * sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(lstat, 0, 4 * sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(ties, 0, 2 * sizeof(unsigned long long), st));
   RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
   k_list_rank<<<(unsigned)((npairs + 127) / 128), 128, 0, st>>>(

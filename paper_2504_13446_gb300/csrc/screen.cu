@@ -450,7 +450,7 @@ extern "C" rkr_status rkr_screen_scores_static(const float *U, int64_t n, const 
   set_error("%s", "");
   if (!U || !X || !out_s || !out_b) return fail(RKR_EINVAL, "null argument");
   if (n < 1 || mx < 1 || d < 1 || d > kMaxD) return fail(RKR_EINVAL, "bad sizes");
-  if (n * mx > ((int64_t)1 << 31)) return fail(RKR_EINVAL, "n * mx too large");
+  if (mx > ((int64_t)1 << 31) / n) return fail(RKR_EINVAL, "n * mx too large");
   if (split != 0 && split != 1)  // the E4M3 form (split = 2) stages through allocated scratch
     return fail(RKR_EINVAL, "rkr_screen_scores_static takes split = 0 or 1 (the BF16 forms)");
   constexpr int BN = 256;

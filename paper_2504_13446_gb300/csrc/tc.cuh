@@ -55,10 +55,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Wait until the phase of the given parity has completed; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait until the phase of the given parity has completed; false after `limit`
+// unsuccessful try_wait rounds (limit 0 gives up at once).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t limit = kWaitLimit) {
   const uint32_t addr = smem_u32(bar);
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -78,30 +80,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
-}
-
-// Multicast form: the box lands at the same shared-memory offset in every CTA
-// of the cluster named in `mask`, and completes bytes on the mbarrier at the
-// same offset in each of them.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int x, int y,
-                                               uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// Every thread of every CTA in the cluster.
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
 }
 
 __device__ __forceinline__ void prefetch_map(const CUtensorMap *map) {
@@ -150,15 +128,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
-      : "memory");
-}
-
-// Arrives once on the mbarrier at this offset in every CTA of `mask` when the
-// MMAs issued so far by this thread complete.
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)), "h"(mask)
       : "memory");
 }
 
@@ -234,6 +203,7 @@ struct Operands {
   int ksteps;          // MMA steps per segment (32 bytes of K each)
   int split;           // 0: one segment hi.hi; 1: three segments hi.lo, lo.hi, hi.hi
   int fp8 = 0;         // 1: E4M3 operands (kind::f8f6f4, 128 elements per chunk)
+  uint32_t epi_wait = kWaitLimit;  // try_wait rounds of the epilogue's accumulator wait
 };
 
 // Per-row bound terms (FP32 upper bounds), see screen_bound_tc.

@@ -4,6 +4,9 @@
 #include <cuda.h>
 
 #include "tc_screen.cuh"
+#ifdef RKR_CLUSTER_MULTICAST
+#include "tc_pair.cuh"
+#endif
 
 namespace rkr {
 
@@ -33,7 +36,13 @@ int sm_count();
 rkr_status make_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t rows, int kp,
                     int box_rows);
 
-// Launch the screen kernel over A (users) x B (items or queries).
+// Rounds of the screens' epilogue accumulator wait before it gives up (a test
+// hook set by rkr_set_wait_limit; tc::kWaitLimit unless changed).
+uint32_t epi_wait_limit();
+
+// Launch the screen kernel over A (users) x B (items or queries).  Row-owned
+// schedules run as CTA pairs sharing B by cluster multicast in the single-GPU
+// build, and on the single-CTA kernel otherwise; both give the same bits.
 template <int BN, int STAGES, class Epi>
 rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::Schedule &sch,
                          const Epi &epi, int *err_dev, cudaStream_t st) {
@@ -48,11 +57,14 @@ rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::
   op.kchunks = (A.kp + tc::KCH - 1) / tc::KCH;
   op.ksteps = A.kp / 16;
   op.split = split;
+  op.epi_wait = epi_wait_limit();
   const size_t smem = tc::screen_smem_bytes<BN, STAGES, Epi>();
   int grid = std::min(sch.nunits, sm_count());
   if (grid < 1) return RKR_OK;
-  ProfScope prof(Epi::name(), st,
-                 2.0 * (double)A.rows * (double)B.rows * (double)A.kp * (split ? 3.0 : 1.0));
+  // the method's work: one inner product of length d per (row, column) pair,
+  // whatever number of products (split) and padding of K the screen issues
+  ProfScope prof(Epi::name(), st, 2.0 * (double)A.rows * (double)B.rows * (double)A.d);
+#ifdef RKR_CLUSTER_MULTICAST
   if (sch.mode == 0 && sch.nunits >= 2) {
     // row-owned units: CTA pairs share each B chunk by multicast
     auto pk = tc::k_screen_pair<BN, STAGES, Epi>;
@@ -86,6 +98,7 @@ rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::
       return RKR_OK;
     }
   }
+#endif
   auto kern = tc::k_screen<BN, STAGES, Epi>;
   RKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, tc::kThreads, smem, st>>>(mAh, mAl, mBh, mBl, op, sch, epi, err_dev);

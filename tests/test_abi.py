@@ -36,10 +36,50 @@ def test_library_builds_and_exports_every_symbol():
 
 def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
     import paper_2504_13446_gb300 as pkg
-    monkeypatch.setattr(pkg.buildlib, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(pkg.buildlib, "lib_path", lambda variant="single_gpu":
+                        str(tmp_path / "missing.so"))
     monkeypatch.setattr(pkg, "_lib", None)
     with pytest.raises(RuntimeError):
         pkg.load()
+
+
+def test_replica_build_exports_every_symbol_and_names_itself():
+    from paper_2504_13446_gb300 import buildlib
+    single = ctypes.CDLL(buildlib.build())
+    replica = ctypes.CDLL(buildlib.build(variant="replica"))
+    for name in _declared():
+        assert hasattr(replica, name), name
+    for lib in (single, replica):
+        lib.rkr_version.restype = ctypes.c_char_p
+    assert b"single-GPU build" in single.rkr_version()
+    assert b"replica build" in replica.rkr_version()
+
+
+def test_cluster_multicast_stays_out_of_the_replica_build():
+    """Only tc_pair.cuh names a multicast TMA load or commit, and no translation
+    unit of the replica build (the one a rank of a multi-GPU job loads) includes it."""
+    from paper_2504_13446_gb300 import buildlib
+    csrc = buildlib.CSRC
+    for f in sorted(os.listdir(csrc)):
+        text = open(os.path.join(csrc, f)).read()
+        if f != "tc_pair.cuh":
+            assert ".multicast::cluster" not in text, f
+    uses_pair = 0
+    for src in buildlib._sources():
+        assert "tc_pair.cuh" not in buildlib.included_headers(src, "replica"), src
+        uses_pair += "tc_pair.cuh" in buildlib.included_headers(src, "single_gpu")
+    assert uses_pair >= 1
+
+
+def test_variant_selection(monkeypatch):
+    from paper_2504_13446_gb300 import buildlib
+    monkeypatch.delenv("RKR_LIB_VARIANT", raising=False)
+    assert buildlib.selected_variant() == "single_gpu"
+    monkeypatch.setenv("RKR_LIB_VARIANT", "replica")
+    assert buildlib.lib_path(buildlib.selected_variant()).endswith("librkr_replica.so")
+    monkeypatch.setenv("RKR_LIB_VARIANT", "bogus")
+    with pytest.raises(RuntimeError):
+        buildlib.selected_variant()
 
 
 def test_oracle_is_not_imported_by_the_product():

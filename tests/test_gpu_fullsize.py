@@ -69,3 +69,32 @@ def test_approx_workload_full_size_exact_answers_and_index():
     assert (fmin[sample] == ora["fmin"]).all()
     assert (fmax[sample] == ora["fmax"]).all()
     assert (table[sample] == ora["N"]).all()
+
+
+def test_approx_workload_full_size_approximate_answers():
+    """The c-approximate query path at full size (1M x 100k x 200, tau 500, omega 10,
+    s 100, c = 2, all 10,000 queries in one batch) against the oracle's own full
+    index.  The oracle builds that index with the footnote's Cauchy-Schwarz
+    f-bounds (one FP64 norm per row) so that its full Alg. 1 table of 1M users is
+    affordable on the host; the GPU index is built the same way.  The query steps
+    (the u.q screen, the bounds lookup, R_low_k and R_up_k, Case A/B and the
+    interpolation) do not depend on how f_min and f_max were found.  For sampled
+    queries users, numerators, FP64 estimates, case and |U_c| must match bit for bit."""
+    w = synth.make_workload("approx")
+    sizes = oracle.bucket_sizes(w.m, w.omega)
+    pos = synth.sample_positions(w.seed, sizes, w.s)
+    rng = np.random.default_rng(23)
+    with rkr.Index(w.U, w.P, tau=w.tau, omega=w.omega, s=w.s, fbounds="cs",
+                   exact_table=False, sample_pos=pos) as idx:
+        got = idx.query_approx(w.Q, w.k, 2.0)
+    ora = oracle.build_index(w.U, w.P, w.tau, w.omega, w.s, pos, fbounds="cs")
+    queries = np.sort(rng.choice(w.Q.shape[0], 6, replace=False))
+    theta = oracle.scores(w.U, w.Q[queries])
+    for i, q in enumerate(queries):
+        want = oracle.approx_query_one(ora, theta[:, i], int(w.k[q]), 2.0)
+        sl = slice(got["offsets"][q], got["offsets"][q + 1])
+        assert (got["users"][sl] == want["users"]).all(), q
+        assert (got["n_low"][sl] == want["n_low"]).all(), q
+        assert (got["n_up"][sl] == want["n_up"]).all(), q
+        assert (got["est"][sl] == want["est"]).all(), q
+        assert got["case"][q] == want["case"] and got["nc"][q] == want["nc"], q

@@ -32,9 +32,29 @@ def test_static_screen_matches_allocating_screen(split):
         for _ in range(2):
             s = torch.full((n, mx), float("nan"), device="cuda")
             b = torch.full((n, mx), float("nan"), device="cuda")
+            allocs = rkr.device_allocations()
             rkr.rkr_screen_scores_static(Ud, Xd, s, b, split=split)
+            # the library requested no device memory for the call
+            assert rkr.device_allocations() == allocs
             assert (s.cpu().numpy() == s_ref).all()
             assert (b.cpu().numpy() == b_ref).all()
+
+
+def test_allocation_counter_moves_for_the_allocating_screen():
+    rng = np.random.default_rng(3)
+    U, X = _rows(rng, 40, 16), _rows(rng, 50, 16)
+    allocs = rkr.device_allocations()
+    rkr.rkr_screen_scores(U, X)
+    assert rkr.device_allocations() > allocs
+
+
+def test_static_screen_rejects_a_width_mismatch():
+    U = torch.zeros((4, 8), device="cuda")
+    X = torch.zeros((4, 6), device="cuda")
+    out = torch.empty((4, 4), device="cuda")
+    with pytest.raises(rkr.RKRError) as e:
+        rkr.rkr_screen_scores_static(U, X, out, out.clone())
+    assert e.value.status == 1 and "columns" in str(e.value)
 
 
 def test_static_screen_rejects_sizes_beyond_its_scratch():
