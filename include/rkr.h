@@ -158,6 +158,23 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
                             rkr_query_stats *stats, void *stream);
 
 /*
+ * rkr_query_approx_single: rkr_query_approx answered one query at a time (latency
+ * mode), as the paper runs its queries (Section 5: each query on its own).  Same
+ * arguments and outputs, bit for bit.  Per query: one pass over U computes u.q for
+ * every user (FP32 warp products with a rigorous bound; canonical FP64 only where
+ * the bound straddles a threshold) fused with the bounds lookup of Section 4.3
+ * step 1, then steps 2-3 run on the users whose lower bound is at most an upper
+ * estimate of R_up_k (every user the steps can return is among them).  Four
+ * kernel launches per query, no host synchronization until the call returns.
+ * The pass is bound by HBM bandwidth: about 4d + 48 bytes per user per query.
+ * Temporaries: about 37 bytes per user, reused by every query of the call.
+ */
+rkr_status rkr_query_approx_single(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   double c, int32_t *out_users, uint32_t *out_nlow,
+                                   uint32_t *out_nup, double *out_est, int32_t *out_case,
+                                   int32_t *out_nc, rkr_query_stats *stats, void *stream);
+
+/*
  * rkr_query_exact_subsets / rkr_query_approx_subsets: the same queries with a
  * user subset per query (a batched deployment form; the paper's queries use
  * all of U).  For query i only users in
@@ -355,6 +372,35 @@ rkr_status rkr_set_wait_limit(int64_t rounds);
 
 /* Release an index (NULL is allowed). */
 void rkr_index_free(rkr_index *idx);
+
+/*
+ * rkr_index_save / rkr_index_load: an index as a file (checkpoint/resume).  The
+ * paper builds its table once and serves any q, k and c from it (Section 4.1);
+ * a saved index serves the same queries in another process with results
+ * identical bit for bit.
+ *   Format: magic "RKRIDX01", format version, byte-order mark, a header with
+ *   the sizes (n, m, d), the build parameters (tau, omega, s, f-bounds mode,
+ *   floor rank, seed) and this library's layout constants, then every device
+ *   array of the index, then a 64-bit checksum (FNV-1a over 64-bit words) of
+ *   all preceding bytes.  Files are as large as the index in device memory.
+ *   rkr_index_save copies the arrays to the host through a pinned staging
+ *   buffer and writes them; it synchronizes the device.  RKR_EINVAL if the file
+ *   cannot be written.
+ *   rkr_index_load allocates the arrays on the current device (sm_103a only) and
+ *   fills them; RKR_EINVAL for a missing, truncated or corrupt file (checksum),
+ *   another format version, byte order or layout constants; RKR_ENOMEM if the
+ *   device cannot hold it.  On failure *out is NULL and nothing stays allocated.
+ */
+rkr_status rkr_index_save(const rkr_index *idx, const char *path);
+rkr_status rkr_index_load(const char *path, rkr_index **out);
+
+/* rkr_pruner_save / rkr_pruner_load: the learned pruner's F, H and FP32 master
+ * weights (flat order of rkr_pruner_params) as a file with the same framing
+ * (magic "RKRMLP01", version, byte-order mark, checksum).  Adam state is not
+ * saved: a loaded pruner predicts exactly as the saved one did.  Errors as for
+ * the index. */
+rkr_status rkr_pruner_save(rkr_pruner *pr, const char *path);
+rkr_status rkr_pruner_load(const char *path, rkr_pruner **out);
 
 /* Device memory (not in the paper): the library allocates index arrays and
  * per-call temporaries from one stream-ordered pool per device and keeps what

@@ -25,6 +25,7 @@ from . import buildlib
 
 __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
            "rkr_query_approx", "rkr_query_exact_subsets", "rkr_query_approx_subsets",
+           "rkr_query_approx_single",
            "rkr_screen_scores", "rkr_screen_scores_static",
            "rkr_profile_start", "rkr_profile_stop", "Pruner", "rkr_rank_pairs",
            "rkr_pair_features", "rkr_query_exact_learned", "rkr_release_cached_memory",
@@ -89,6 +90,9 @@ def load() -> ctypes.CDLL:
         lib.rkr_query_exact_subsets.restype = I32
         lib.rkr_query_exact_subsets.argtypes = [V, V, I32, V, V, V, V, V,
                                                 ctypes.POINTER(QueryStats), V]
+        lib.rkr_query_approx_single.restype = I32
+        lib.rkr_query_approx_single.argtypes = [V, V, I32, V, ctypes.c_double, V, V, V, V, V, V,
+                                                ctypes.POINTER(QueryStats), V]
         lib.rkr_query_approx_subsets.restype = I32
         lib.rkr_query_approx_subsets.argtypes = [V, V, I32, V, V, V, ctypes.c_double, V, V, V,
                                                  V, V, V, ctypes.POINTER(QueryStats), V]
@@ -134,6 +138,14 @@ def load() -> ctypes.CDLL:
         lib.rkr_profile_stop.argtypes = [ctypes.c_char_p, I64]
         lib.rkr_screen_scores_static.restype = I32
         lib.rkr_screen_scores_static.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
+        lib.rkr_index_save.restype = I32
+        lib.rkr_index_save.argtypes = [V, ctypes.c_char_p]
+        lib.rkr_index_load.restype = I32
+        lib.rkr_index_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(V)]
+        lib.rkr_pruner_save.restype = I32
+        lib.rkr_pruner_save.argtypes = [V, ctypes.c_char_p]
+        lib.rkr_pruner_load.restype = I32
+        lib.rkr_pruner_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(V)]
         lib.rkr_device_allocations.restype = ctypes.c_uint64
         lib.rkr_device_allocations.argtypes = []
         lib.rkr_set_wait_limit.restype = I32
@@ -301,10 +313,12 @@ def rkr_query_exact(index, Q, k, *, subsets=None, device: bool = False, stream=N
     return users, ranks, off, stats
 
 
-def rkr_query_approx(index, Q, k, c: float, *, subsets=None, device: bool = False, stream=None):
+def rkr_query_approx(index, Q, k, c: float, *, subsets=None, single: bool = False,
+                     device: bool = False, stream=None):
     """c-approximate reverse k-ranks (Section 4.3): dict of per-user and per-query outputs.
 
-    subsets: optional list of per-query user-id arrays (rkr_query_approx_subsets)."""
+    subsets: optional list of per-query user-id arrays (rkr_query_approx_subsets).
+    single: answer the queries one at a time (rkr_query_approx_single)."""
     lib = load()
     nq, _ = _shape(Q)
     kk = np.broadcast_to(np.asarray(k if not _is_torch(k) else k.cpu().numpy(), np.int32), (nq,))
@@ -319,7 +333,12 @@ def rkr_query_approx(index, Q, k, c: float, *, subsets=None, device: bool = Fals
             (("users", np.int32), ("n_low", np.uint32), ("n_up", np.uint32),
              ("est", np.float64), ("case", np.int32), ("nc", np.int32))]
     stats = QueryStats()
-    if subsets is None:
+    if single:
+        if subsets is not None:
+            raise ValueError("the one-at-a-time mode takes no subsets")
+        _check(lib.rkr_query_approx_single(index, pq, nq, pk, ctypes.c_double(c), *ptrs,
+                                           ctypes.byref(stats), _stream(stream)))
+    elif subsets is None:
         _check(lib.rkr_query_approx(index, pq, nq, pk, ctypes.c_double(c), *ptrs,
                                     ctypes.byref(stats), _stream(stream)))
     else:
@@ -330,6 +349,11 @@ def rkr_query_approx(index, Q, k, c: float, *, subsets=None, device: bool = Fals
     out["offsets"] = off
     out["stats"] = stats
     return out
+
+
+def rkr_query_approx_single(index, Q, k, c: float, **kw):
+    """rkr_query_approx answered one query at a time (latency mode)."""
+    return rkr_query_approx(index, Q, k, c, single=True, **kw)
 
 
 def rkr_query_exact_subsets(index, Q, k, subsets, **kw):
@@ -476,6 +500,24 @@ class Pruner:
                                        len(t), epochs, batch, lr, seed, ctypes.byref(loss), None))
         return float(loss.value)
 
+    def save(self, path: str) -> None:
+        """Write F, H and the weights to a file (rkr_pruner_save)."""
+        _check(load().rkr_pruner_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "Pruner":
+        """A pruner read from a file written by save (rkr_pruner_load)."""
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.rkr_pruner_load(os.fsencode(path), ctypes.byref(h)))
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.nparams = int(lib.rkr_pruner_nparams(h))
+        a = np.empty(obj.nparams, np.float32)
+        _check(lib.rkr_pruner_params(h, 0, a.ctypes.data, obj.nparams))
+        obj.F, obj.H = None, None
+        return obj
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             load().rkr_pruner_free(self._h)
@@ -505,9 +547,26 @@ class Index:
 
     def __init__(self, U, P, **kw):
         self._h: Optional[ctypes.c_void_p] = rkr_build(U, P, **kw)
+        self._read_info()
+
+    def _read_info(self):
         raw = (ctypes.c_int64 * 8)()
         _check(load().rkr_index_info(self._h, raw))
         self.info = _Info(*[int(v) for v in raw])
+
+    def save(self, path: str) -> None:
+        """Write the index to a file (rkr_index_save)."""
+        _check(load().rkr_index_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "Index":
+        """An index read from a file written by save (rkr_index_load)."""
+        h = ctypes.c_void_p()
+        _check(load().rkr_index_load(os.fsencode(path), ctypes.byref(h)))
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj._read_info()
+        return obj
 
     def query_exact(self, Q, k, **kw):
         return rkr_query_exact(self._h, Q, k, **kw)

@@ -138,7 +138,7 @@ static int is_device(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static rkr_status check_device() {
+rkr_status check_device() {
   int dev = 0;
   RKR_CUDA(cudaGetDevice(&dev));
   cudaDeviceProp pr;
@@ -330,6 +330,8 @@ rkr_status rkr_build(const float *U, int64_t n, const float *P, int64_t m, int32
   idx->fbounds = p.fbounds;
   idx->has_exact = p.exact_table ? 1 : 0;
   idx->floor_rank = p.floor_rank ? p.floor_rank : (int)(m / 16 > 2048 ? m / 16 : 2048);
+  idx->seed = p.seed;
+  idx->sampled_pos = p.sample_pos ? 1 : 0;
   rkr_status stt = build_index(idx, (const float *)vu.dev, (const float *)vp.dev, &p,
                                p.sample_pos ? spos.data() : nullptr, st);
   if (stt != RKR_OK) {
@@ -511,7 +513,7 @@ static rkr_status query_approx_impl(rkr_index *idx, const float *Q, int32_t nq,
                                     const int32_t *subset_users, bool subsets, double c,
                                     int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
                                     double *out_est, int32_t *out_case, int32_t *out_nc,
-                                    rkr_query_stats *stats, void *stream) {
+                                    rkr_query_stats *stats, void *stream, bool single = false) {
   g_err[0] = 0;
   if (!out_users) return fail(RKR_EINVAL, "null output");
   if (!(c >= 1.0) || !isfinite(c)) return fail(RKR_EINVAL, "c must be a finite value >= 1");
@@ -531,9 +533,14 @@ static rkr_status query_approx_impl(rkr_index *idx, const float *Q, int32_t nq,
   RKR_TRY(oes.init(out_est, sizeof(double) * tot, st));
   RKR_TRY(oca.init(out_case, sizeof(int32_t) * nq, st));
   RKR_TRY(onc.init(out_nc, sizeof(int32_t) * nq, st));
-  RKR_TRY(run_query_approx(idx, qc, nq, c, (int32_t *)ou.dev, (uint32_t *)olo.dev,
-                           (uint32_t *)oup.dev, (double *)oes.dev, (int32_t *)oca.dev,
-                           (int32_t *)onc.dev, stats, st));
+  if (single)
+    RKR_TRY(run_query_approx_single(idx, qc, nq, c, (int32_t *)ou.dev, (uint32_t *)olo.dev,
+                                    (uint32_t *)oup.dev, (double *)oes.dev, (int32_t *)oca.dev,
+                                    (int32_t *)onc.dev, stats, st));
+  else
+    RKR_TRY(run_query_approx(idx, qc, nq, c, (int32_t *)ou.dev, (uint32_t *)olo.dev,
+                             (uint32_t *)oup.dev, (double *)oes.dev, (int32_t *)oca.dev,
+                             (int32_t *)onc.dev, stats, st));
   RKR_TRY(ou.finish());
   RKR_TRY(olo.finish());
   RKR_TRY(oup.finish());
@@ -565,6 +572,14 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
                             rkr_query_stats *stats, void *stream) {
   return query_approx_impl(idx, Q, nq, k, nullptr, nullptr, false, c, out_users, out_nlow,
                            out_nup, out_est, out_case, out_nc, stats, stream);
+}
+
+rkr_status rkr_query_approx_single(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   double c, int32_t *out_users, uint32_t *out_nlow,
+                                   uint32_t *out_nup, double *out_est, int32_t *out_case,
+                                   int32_t *out_nc, rkr_query_stats *stats, void *stream) {
+  return query_approx_impl(idx, Q, nq, k, nullptr, nullptr, false, c, out_users, out_nlow,
+                           out_nup, out_est, out_case, out_nc, stats, stream, true);
 }
 
 rkr_status rkr_query_approx_subsets(rkr_index *idx, const float *Q, int32_t nq,

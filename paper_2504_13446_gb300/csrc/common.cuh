@@ -44,6 +44,9 @@ rkr_status cuda_fail(cudaError_t e, const char *what);
 // Count of kernels this library has launched (reported by rkr_kernel_launches).
 void note_launch();
 
+// RKR_EUNSUPPORTED unless the current device is sm_103 (GB300).
+rkr_status check_device();
+
 // Per-kernel device-time accounting, on while rkr_profile_start is in effect:
 // CUDA events recorded on the launching stream around a launch.  `work` is the
 // launch's algorithmic work (flops of a screen; 0 when not stated).
@@ -244,6 +247,52 @@ __host__ __device__ __forceinline__ float u32_float(uint32_t b) {
   x.u = b;
   return x.f;
 }
+
+// ------------------------------------------------------- host helpers
+
+// A stream-ordered temporary from the library pool, freed when it goes out of scope.
+struct DevBuf {
+  void *p = nullptr;
+  cudaStream_t st = nullptr;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+template <class T>
+inline rkr_status tmp_alloc(DevBuf &b, T **out, size_t count, cudaStream_t st) {
+  if (count == 0) count = 1;
+  cudaError_t e = pool_malloc_async(&b.p, count * sizeof(T), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+  }
+  b.st = st;
+  *out = (T *)b.p;
+  return RKR_OK;
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
 
 // Order-preserving key of a non-negative double.
 __device__ __forceinline__ uint64_t dkey(double x) { return (uint64_t)__double_as_longlong(x); }

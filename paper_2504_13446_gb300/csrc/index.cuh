@@ -15,6 +15,8 @@ struct rkr_index {
   int nsamp = 0;
   int nlev_a = 0;  // levels used with the sampled table (scale s)
   int nlev_x = 0;  // levels used with the exact table (scale 1)
+  uint64_t seed = 0;     // sampling seed of the build (recorded; the samples are stored)
+  int sampled_pos = 0;   // 1: sample positions were given by the caller
 
   // items and users (device)
   float *U = nullptr;        // n x d, caller order
@@ -185,10 +187,29 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
                             int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
                             int32_t *case_d, int32_t *nc_d, rkr_query_stats *stats,
                             cudaStream_t st);
+// Steps 2-3 of Section 4.3 for queries qa .. qa + nblocks - 1 over per-query
+// candidate lists (one CTA per query; see k_select_approx in query.cu).
+rkr_status launch_select_approx(int qa, int nblocks, const int64_t *qoff, const uint32_t *qcount,
+                                const int32_t *uid, const uint32_t *nlo, const uint32_t *nup,
+                                double *th, const int32_t *cj, const float *Qd,
+                                const int32_t *kq, double c, const int64_t *out_off,
+                                int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
+                                int32_t *case_d, int32_t *nc_d, int *err, cudaStream_t st,
+                                const rkr_index *idx);
+
+// The same query steps one query at a time (latency.cu): per query, u.q of every
+// user by an FP32 matrix-vector product with a rigorous bound fused with the
+// bounds lookup, then steps 2-3 on the users that can still matter.
+rkr_status run_query_approx_single(const rkr_index *idx, const QueryCommon &qc, int nq, double c,
+                                   int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d,
+                                   double *est_d, int32_t *case_d, int32_t *nc_d,
+                                   rkr_query_stats *stats, cudaStream_t st);
+
 // Learned pruner (pruner.cu): predictions of B pairs from a per-user feature table.
 rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t *uid,
                                  const float *t, int64_t B, float *y, cudaStream_t st);
 int pruner_features(const rkr_pruner *pr);
+int pruner_hidden(const rkr_pruner *pr);
 
 // Exact ranks of arbitrary (user, query) pairs of a staged batch (device arrays).
 rkr_status run_rank_pairs(const rkr_index *idx, const QueryCommon &qc, int nq, int64_t npairs,

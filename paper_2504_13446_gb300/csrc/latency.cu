@@ -1,0 +1,293 @@
+// latency.cu -- c-approximate queries one at a time (latency mode).
+//
+// The paper answers each query on its own: u.q for every user and the table
+// lookup of Section 4.3 step 1 (its dominant cost, O(nd) per query), then the
+// k-th smallest bounds, the Case A/B filter and the interpolation.  Per query
+// this runs four launches with no host synchronization between them:
+//
+//   k_latency_scan     one pass over U (FP32, coalesced): u.q of every user by
+//                      warp-level FP32 products with a rigorous error bound; the
+//                      bin j of Section 4.3 step 1 from that interval (canonical
+//                      FP64 u.q only when the interval straddles a threshold);
+//                      r_low, r_up numerators from the table; a histogram of
+//                      the upper-bound numerators
+//   k_latency_cut      from the histogram, T >= R_up_k (the k-th smallest upper
+//                      bound numerator), the bound of the users that can matter
+//   k_latency_compact  the users with r_low <= T
+//   k_select_approx    steps 1-3 on those users (query.cu)
+//
+// Every user that step 2 or 3 can return has r_low <= R_up_k (Case A takes the
+// k smallest r_up, all <= R_up_k, and r_low <= r_up; Case B prunes r_low >
+// R_up_k), and R_low_k <= R_up_k <= T, so the k smallest lower and upper
+// bounds lie among the compacted users: the answer equals the batched one bit
+// for bit.  The scan is bound by HBM: it reads U once (4d bytes per user) and
+// a few bytes of per-user data and table cells.
+#include <math.h>
+
+#include "index.cuh"
+
+namespace rkr {
+namespace {
+
+constexpr int kLatThreads = 256;
+constexpr int kLatRows = 8;      // rows per warp and sub-batch
+constexpr int kLatSub = 4;       // sub-batches: 32 rows per warp iteration, one per lane
+constexpr int kLatBins = 2048;
+
+// Bound factor of the warp product: every rounding (d FMAs in the lanes' chains,
+// 31 additions of the warp reduction) errs by at most 2^-24 times a partial sum,
+// and every partial sum is at most sum_k |u_k q_k| <= ||u|| ||q||; the canonical
+// FP64 sum differs from the exact value by at most d 2^-53 ||u|| ||q||.
+__host__ __device__ inline float latency_cfac(int d) {
+  const double c = ((double)(d + 36) * 0x1p-24 + (double)d * 0x1p-53 + 0x1p-40) * (1.0 + 0x1p-20);
+  return (float)c * (1.0f + 0x1p-20f);
+}
+
+template <int VEC>
+__device__ __forceinline__ float lane_dot(const float *__restrict__ row, const float *qs, int d,
+                                          int lane) {
+  float acc = 0.0f;
+  if (VEC == 4) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+    const int dv = d >> 2;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {  // d <= 256: at most two float4 per lane
+      const int c = lane + 32 * p;
+      if (c < dv) {
+        const float4 a = __ldcs(r4 + c);   // streamed: U is read once per query
+        const float4 b = q4[c];
+        acc = __fmaf_rn(a.x, b.x, acc);
+        acc = __fmaf_rn(a.y, b.y, acc);
+        acc = __fmaf_rn(a.z, b.z, acc);
+        acc = __fmaf_rn(a.w, b.w, acc);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {  // d <= 256
+      const int c = lane + 32 * p;
+      if (c < d) acc = __fmaf_rn(__ldcs(row + c), qs[c], acc);
+    }
+  }
+  return acc;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(kLatThreads)
+    k_latency_scan(const float *__restrict__ U, int64_t n, int d, const float *__restrict__ q,
+                   const float *__restrict__ qn_p, const float *__restrict__ unrm,
+                   const BinFP *__restrict__ bf, const double *__restrict__ fmin,
+                   const double *__restrict__ delta, const uint32_t *__restrict__ N, int tau,
+                   uint32_t top, int shift, uint32_t *__restrict__ nlo,
+                   uint32_t *__restrict__ nup, int32_t *__restrict__ jout,
+                   uint32_t *__restrict__ ghist, unsigned long long *__restrict__ nfp64) {
+  __shared__ __align__(16) float qs[kMaxD];
+  __shared__ uint32_t hist[kLatBins];
+  for (int i = threadIdx.x; i < kMaxD; i += blockDim.x) qs[i] = i < d ? q[i] : 0.0f;
+  for (int i = threadIdx.x; i < kLatBins; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const float qn = *qn_p;
+  const float cf = latency_cfac(d);
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (kLatThreads / 32) + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * (kLatThreads / 32);
+  constexpr int kPerIter = kLatRows * kLatSub;  // 32 rows: lane r finishes row r0 + r
+  uint32_t fp64 = 0;
+  for (int64_t r0 = gw * kPerIter; r0 < n; r0 += nw * kPerIter) {
+    float mine = 0.0f;
+#pragma unroll
+    for (int sb = 0; sb < kLatSub; ++sb) {
+      float part[kLatRows];
+#pragma unroll
+      for (int rr = 0; rr < kLatRows; ++rr) {
+        const int64_t u = r0 + sb * kLatRows + rr;
+        part[rr] = u < n ? lane_dot<VEC>(U + u * d, qs, d, lane) : 0.0f;
+      }
+#pragma unroll
+      for (int rr = 0; rr < kLatRows; ++rr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          part[rr] = __fadd_rn(part[rr], __shfl_xor_sync(0xffffffffu, part[rr], o));
+        if (lane == sb * kLatRows + rr) mine = part[rr];
+      }
+    }
+    const int64_t u = r0 + lane;
+    if (u >= n) continue;
+    const float b = __fadd_ru(__fmul_ru(__fmul_ru(cf, unrm[u]), qn), 1e-30f);
+    int jlo, jhi;
+    bin_interval(bf[u], fmin[u], tau, __fsub_rd(mine, b), __fadd_ru(mine, b), jlo, jhi);
+    int j = jlo;
+    if (jlo != jhi) {
+      ++fp64;
+      j = exact_j(canon_dot_slow(U + u * d, qs, d), fmin[u], delta[u], tau);
+    }
+    const uint32_t lo = j < tau ? N[u * tau + j] : 0u;
+    const uint32_t up = j >= 1 ? N[u * tau + j - 1] : top;
+    nlo[u] = lo;
+    nup[u] = up;
+    jout[u] = j;
+    atomicAdd(&hist[min(up >> shift, (uint32_t)(kLatBins - 1))], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kLatBins; i += blockDim.x)
+    if (hist[i]) atomicAdd(&ghist[i], hist[i]);
+  fp64 = __reduce_add_sync(0xffffffffu, fp64);
+  if (lane == 0 && fp64) atomicAdd(nfp64, (unsigned long long)fp64);
+}
+
+// T = upper end of the histogram bin holding the k-th smallest upper-bound
+// numerator (so T >= R_up_k); the histogram is cleared for the next query and
+// the candidate count of query q zeroed.
+__global__ void __launch_bounds__(1024)
+    k_latency_cut(uint32_t *__restrict__ ghist, const int32_t *__restrict__ kq, int q, int shift,
+                  uint32_t *__restrict__ T, uint32_t *__restrict__ qcount) {
+  __shared__ uint32_t h[kLatBins];
+  __shared__ uint32_t part[1024];
+  const int t = threadIdx.x;
+  for (int i = t; i < kLatBins; i += blockDim.x) {
+    h[i] = ghist[i];
+    ghist[i] = 0;
+  }
+  __syncthreads();
+  // each thread sums two bins; inclusive scan of the pair sums
+  const uint32_t mine = h[2 * t] + h[2 * t + 1];
+  part[t] = mine;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t v = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  const uint32_t k = (uint32_t)kq[q];
+  const uint32_t before = part[t] - mine;
+  if (before < k && part[t] >= k) {
+    const int bin = before + h[2 * t] >= k ? 2 * t : 2 * t + 1;
+    const uint64_t hi = ((uint64_t)(bin + 1) << shift) - 1;
+    *T = bin == kLatBins - 1 || hi > 0xffffffffull ? 0xffffffffu : (uint32_t)hi;
+    qcount[q] = 0;
+  }
+}
+
+__global__ void k_latency_compact(int64_t n, const uint32_t *__restrict__ nlo,
+                                  const uint32_t *__restrict__ nup, const int32_t *__restrict__ j,
+                                  const uint32_t *__restrict__ T, int q,
+                                  uint32_t *__restrict__ qcount, int32_t *__restrict__ cu,
+                                  uint32_t *__restrict__ clo, uint32_t *__restrict__ cup,
+                                  int32_t *__restrict__ cj, double *__restrict__ cth) {
+  const uint32_t t = *T;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const bool take = nlo[u] <= t;
+    const unsigned act = __ballot_sync(__activemask(), take);
+    if (!take) continue;
+    const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&qcount[q], (uint32_t)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    const uint32_t pos = base + __popc(act & ((1u << lane) - 1u));
+    cu[pos] = (int32_t)u;
+    clo[pos] = nlo[u];
+    cup[pos] = nup[u];
+    cj[pos] = j[u];
+    cth[pos] = __longlong_as_double(0x7ff8000000000000ll);  // u.q formed on demand
+  }
+}
+
+}  // namespace
+
+rkr_status run_query_approx_single(const rkr_index *idx, const QueryCommon &qc, int nq, double c,
+                                   int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d,
+                                   double *est_d, int32_t *case_d, int32_t *nc_d,
+                                   rkr_query_stats *stats, cudaStream_t st) {
+  const int64_t n = idx->n;
+  const int d = idx->d;
+  const uint32_t top = (uint32_t)(idx->m * idx->s);
+  int shift = 0;
+  while ((top >> shift) >= (uint32_t)kLatBins) ++shift;
+  DevBuf b1, b2, b3, b4, b5, b6, b7, b8, b9, b10, b11, b12;
+  uint32_t *nlo, *nup, *ghist, *T, *qcount, *clo, *cup;
+  int32_t *jall, *cu, *cj;
+  double *cth;
+  unsigned long long *nfp64;
+  int *err;
+  RKR_TRY(tmp_alloc(b1, &nlo, n, st));
+  RKR_TRY(tmp_alloc(b2, &nup, n, st));
+  RKR_TRY(tmp_alloc(b3, &jall, n, st));
+  RKR_TRY(tmp_alloc(b4, &ghist, kLatBins, st));
+  RKR_TRY(tmp_alloc(b5, &T, 1, st));
+  RKR_TRY(tmp_alloc(b6, &qcount, nq, st));
+  RKR_TRY(tmp_alloc(b7, &cu, n, st));
+  RKR_TRY(tmp_alloc(b8, &clo, n, st));
+  RKR_TRY(tmp_alloc(b9, &cup, n, st));
+  RKR_TRY(tmp_alloc(b10, &cj, n, st));
+  RKR_TRY(tmp_alloc(b11, &cth, n, st));
+  RKR_TRY(tmp_alloc(b12, &nfp64, 2, st));
+  err = (int *)(nfp64 + 1);
+  RKR_CUDA(cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * kLatBins, st));
+  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(uint32_t) * nq, st));
+  RKR_CUDA(cudaMemsetAsync(nfp64, 0, 2 * sizeof(unsigned long long), st));
+  const bool vec4 = (d % 4) == 0 && ((uintptr_t)idx->U % 16) == 0;
+  int blocks_per_sm = 0;
+  if (vec4)
+    RKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_latency_scan<4>,
+                                                           kLatThreads, 0));
+  else
+    RKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_latency_scan<1>,
+                                                           kLatThreads, 0));
+  const int64_t warps_needed = (n + 31) / 32;
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sm_count() * std::max(blocks_per_sm, 1),
+                           (warps_needed + kLatThreads / 32 - 1) / (kLatThreads / 32)));
+  const int cgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+  Timer t1(st);
+  double ms_scan = 0.0, ms_sel = 0.0;
+  for (int q = 0; q < nq; ++q) {
+    const float *qrow = qc.Qd + (int64_t)q * d;
+    {
+      ProfScope prof("k_latency_scan", st,
+                     (double)n * (4.0 * d + 4 + sizeof(BinFP) + 8 + 8 + 12));
+      if (vec4)
+        k_latency_scan<4><<<grid, kLatThreads, 0, st>>>(
+            idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
+            idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
+      else
+        k_latency_scan<1><<<grid, kLatThreads, 0, st>>>(
+            idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
+            idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
+      note_launch();
+    }
+    {
+      const int prof_slot = prof_begin("k_latency_cut", st);
+      k_latency_cut<<<1, 1024, 0, st>>>(ghist, qc.kq_d, q, shift, T, qcount);
+      prof_end(prof_slot, st, 0.0);
+      note_launch();
+    }
+    {
+      const int prof_slot = prof_begin("k_latency_compact", st);
+      k_latency_compact<<<cgrid, 256, 0, st>>>(n, nlo, nup, jall, T, q, qcount, cu, clo, cup, cj,
+                                               cth);
+      prof_end(prof_slot, st, 0.0);
+      note_launch();
+    }
+    RKR_TRY(launch_select_approx(q, 1, qc.out_off_d, qcount, cu, clo, cup, cth, cj, qc.Qd,
+                                 qc.kq_d, c, qc.out_off_d, users_d, nlo_d, nup_d, est_d, case_d,
+                                 nc_d, err, st, idx));
+  }
+  RKR_CUDA(cudaGetLastError());
+  ms_scan = t1.stop();
+  unsigned long long h[2] = {0, 0};
+  RKR_CUDA(cudaMemcpyAsync(h, nfp64, sizeof(h), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if ((int)h[1]) return fail(RKR_EINTERNAL, "fewer than k candidates for a query");
+  if (stats) {
+    stats->pairs = n * (int64_t)nq;
+    stats->fp64_dots = (int64_t)h[0];
+    stats->ms_theta = ms_scan;
+    stats->ms_select = ms_sel;
+  }
+  return RKR_OK;
+}
+
+}  // namespace rkr

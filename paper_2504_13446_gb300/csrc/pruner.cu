@@ -472,6 +472,7 @@ rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t 
 }
 
 int pruner_features(const rkr_pruner *pr) { return pr->F; }
+int pruner_hidden(const rkr_pruner *pr) { return pr->H; }
 
 }  // namespace rkr
 

@@ -642,49 +642,6 @@ __global__ void __launch_bounds__(kSelThreads)
 
 // ------------------------------------------------------------------- host
 
-struct DevBuf {
-  void *p = nullptr;
-  cudaStream_t st = nullptr;
-  ~DevBuf() {
-    if (p) cudaFreeAsync(p, st);
-  }
-};
-
-template <class T>
-static rkr_status tmp_alloc(DevBuf &b, T **out, size_t count, cudaStream_t st) {
-  if (count == 0) count = 1;
-  cudaError_t e = pool_malloc_async(&b.p, count * sizeof(T), st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    b.p = nullptr;
-    return fail(RKR_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
-  }
-  b.st = st;
-  *out = (T *)b.p;
-  return RKR_OK;
-}
-
-struct Timer {
-  cudaEvent_t a = nullptr, b = nullptr;
-  cudaStream_t st;
-  explicit Timer(cudaStream_t s) : st(s) {
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, st);
-  }
-  double stop() {
-    cudaEventRecord(b, st);
-    cudaEventSynchronize(b);
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, a, b);
-    return ms;
-  }
-  ~Timer() {
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-  }
-};
-
 // ------------------------------------------------------------ skim list
 
 // Entry e of region blockIdx.y (thread index within the region's count).
@@ -1393,6 +1350,28 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     stats->ms_resolve = ms_res;
     stats->ms_select = ms_sel;
   }
+  return RKR_OK;
+}
+
+rkr_status launch_select_approx(int qa, int nblocks, const int64_t *qoff, const uint32_t *qcount,
+                                const int32_t *uid, const uint32_t *nlo, const uint32_t *nup,
+                                double *th, const int32_t *cj, const float *Qd,
+                                const int32_t *kq, double c, const int64_t *out_off,
+                                int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
+                                int32_t *case_d, int32_t *nc_d, int *err, cudaStream_t st,
+                                const rkr_index *idx) {
+  ApproxCand C{uid, nlo, nup, th, cj, idx->U, Qd, idx->d};
+  size_t sm = sizeof(SortEnt) * kMaxK;
+  RKR_CUDA(cudaFuncSetAttribute(k_select_approx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm));
+  const int prof_slot = prof_begin("k_select_approx", st);
+  k_select_approx<<<nblocks, kSelThreads, sm, st>>>(qa, qoff, qcount, C, kq, c, (uint32_t)idx->s,
+                                                   idx->tau, idx->fmin, idx->delta, out_off,
+                                                   users_d, nlo_d, nup_d, est_d, case_d, nc_d,
+                                                   err);
+  prof_end(prof_slot, st, 0.0);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
   return RKR_OK;
 }
 

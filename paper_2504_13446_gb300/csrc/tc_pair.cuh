@@ -79,8 +79,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *acc_empty = acc_full + 2;
   uint64_t *drain = acc_empty + 2;
   uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+  // tmem_slot[1] records a failure of any role (the dynamic region is already at
+  // the shared-memory limit, so no static shared variable is added)
+  volatile uint32_t *s_failed = tmem_slot + 1;
   char *escratch = (char *)(tmem_slot + 4);
-  __shared__ int s_failed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rank = (int)cluster_rank();               // 0 or 1
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t kHalfB = (BN / 2) * KCH * 2;     // bytes of one B half
 
   if (threadIdx.x == 0) {
-    s_failed = 0;
+    *s_failed = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 2);   // the MMA commits of both CTAs
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       issued = it;
       if (failed) {
         atomicExch(err, 1);
-        s_failed = 1;
+        *s_failed = 1;
         for (uint32_t j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
           mbar_wait(&full[j % STAGES], (j / STAGES) & 1);
       }
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       if (failed) {
         atomicExch(err, 2);
-        s_failed = 1;
+        *s_failed = 1;
       }
       umma_commit(drain);
       mbar_wait(drain, 0);
@@ -226,13 +228,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (failed && lane == 0) {
       atomicExch(err, 3);
-      s_failed = 1;
+      *s_failed = 1;
     }
   }
   tc_fence_before();
   __syncthreads();
   cluster_sync();   // from here on neither CTA issues a load
-  if (warp == 0 && lane == 0 && s_failed) {
+  if (warp == 0 && lane == 0 && *s_failed) {
     for (uint32_t j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
       mbar_wait(&full[j % STAGES], (j / STAGES) & 1);
   }
