@@ -175,6 +175,50 @@ rkr_status rkr_query_approx_single(rkr_index *idx, const float *Q, int32_t nq, c
                                    int32_t *out_nc, rkr_query_stats *stats, void *stream);
 
 /*
+ * Sharded users (not in the paper: a deployment form in which the rows of U are
+ * split across processes or GPUs; each part builds its own index from its rows,
+ * the same P and the same build parameters and sample positions, so every
+ * per-user quantity equals that of one index over all users).
+ *
+ * rkr_query_approx_candidates: for each query i, the users of this index that
+ * the steps of Section 4.3 over the whole user set may need: every user whose
+ * lower-bound numerator is at most T_i, an upper estimate of this index's
+ * R_up_k computed with k[i] (k[i] <= n of this index; pass min(k, n) for a small
+ * part).  Outputs per candidate, query after query: out_users (local index +
+ * user_offset), out_nlow, out_nup (numerators) and out_est (the step-3 estimate
+ * of Section 4.3 from the canonical u.q); out_offs (nq + 1) gives each query's
+ * range.  capacity = entries the four output arrays hold; if more are found,
+ * out_offs is still filled (out_offs[nq] = entries needed) and RKR_ENOMEM is
+ * returned.
+ *
+ * rkr_merge_approx: the c-approximate answer from the union of the parts'
+ * candidates (in_offs, in_users, in_nlow, in_nup, in_est: per query, the
+ * concatenation of every part's candidates of that query).  Runs steps 1-3 of
+ * Section 4.3 on the union with the parts' s: the result equals rkr_query_approx
+ * on one index over all users, bit for bit (same outputs and order).  Host code
+ * only, host arrays only; needs no GPU.  RKR_EINVAL for bad arguments or a query
+ * with fewer than k entries.
+ *
+ * rkr_merge_exact: Def. 2 from the union of the parts' exact answers (in_users
+ * global ids, in_ranks; per query the concatenation of every part's
+ * min(k, n_part) best): the k smallest (rank, user), as rkr_query_exact on one
+ * index.  Host code only, host arrays only.  RKR_EINVAL for bad arguments, a
+ * user listed twice in a query, or fewer than k entries.
+ */
+rkr_status rkr_query_approx_candidates(rkr_index *idx, const float *Q, int32_t nq,
+                                       const int32_t *k, int64_t user_offset, int64_t capacity,
+                                       int64_t *out_offs, int32_t *out_users, uint32_t *out_nlow,
+                                       uint32_t *out_nup, double *out_est, void *stream);
+rkr_status rkr_merge_approx(int32_t nq, const int32_t *k, double c, int32_t s,
+                            const int64_t *in_offs, const int32_t *in_users,
+                            const uint32_t *in_nlow, const uint32_t *in_nup, const double *in_est,
+                            int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
+                            double *out_est, int32_t *out_case, int32_t *out_nc);
+rkr_status rkr_merge_exact(int32_t nq, const int32_t *k, const int64_t *in_offs,
+                           const int32_t *in_users, const int32_t *in_ranks, int32_t *out_users,
+                           int32_t *out_ranks);
+
+/*
  * rkr_query_exact_subsets / rkr_query_approx_subsets: the same queries with a
  * user subset per query (a batched deployment form; the paper's queries use
  * all of U).  For query i only users in

@@ -25,7 +25,8 @@ from . import buildlib
 
 __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_exact",
            "rkr_query_approx", "rkr_query_exact_subsets", "rkr_query_approx_subsets",
-           "rkr_query_approx_single",
+           "rkr_query_approx_single", "rkr_query_approx_candidates", "rkr_merge_approx",
+           "rkr_merge_exact",
            "rkr_screen_scores", "rkr_screen_scores_static",
            "rkr_profile_start", "rkr_profile_stop", "Pruner", "rkr_rank_pairs",
            "rkr_pair_features", "rkr_query_exact_learned", "rkr_release_cached_memory",
@@ -93,6 +94,13 @@ def load() -> ctypes.CDLL:
         lib.rkr_query_approx_single.restype = I32
         lib.rkr_query_approx_single.argtypes = [V, V, I32, V, ctypes.c_double, V, V, V, V, V, V,
                                                 ctypes.POINTER(QueryStats), V]
+        lib.rkr_query_approx_candidates.restype = I32
+        lib.rkr_query_approx_candidates.argtypes = [V, V, I32, V, I64, I64, V, V, V, V, V, V]
+        lib.rkr_merge_approx.restype = I32
+        lib.rkr_merge_approx.argtypes = [I32, V, ctypes.c_double, I32, V, V, V, V, V, V, V, V,
+                                         V, V, V]
+        lib.rkr_merge_exact.restype = I32
+        lib.rkr_merge_exact.argtypes = [I32, V, V, V, V, V, V]
         lib.rkr_query_approx_subsets.restype = I32
         lib.rkr_query_approx_subsets.argtypes = [V, V, I32, V, V, V, ctypes.c_double, V, V, V,
                                                  V, V, V, ctypes.POINTER(QueryStats), V]
@@ -356,6 +364,68 @@ def rkr_query_approx_single(index, Q, k, c: float, **kw):
     return rkr_query_approx(index, Q, k, c, single=True, **kw)
 
 
+def rkr_query_approx_candidates(index, Q, k, *, user_offset: int = 0, capacity=None,
+                                stream=None):
+    """Per-query candidates of one part of a sharded user set (rkr_query_approx_candidates):
+    dict of offsets (nq + 1) and per-candidate users (global ids), n_low, n_up, est."""
+    lib = load()
+    nq, _ = _shape(Q)
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    pq, kq = _ptr(Q, np.float32)
+    cap = int(capacity) if capacity is not None else int(max(1024, 16 * kk.sum()))
+    while True:
+        offs = np.empty(nq + 1, np.int64)
+        out = dict(users=np.empty(cap, np.int32), n_low=np.empty(cap, np.uint32),
+                   n_up=np.empty(cap, np.uint32), est=np.empty(cap, np.float64))
+        st = lib.rkr_query_approx_candidates(
+            index, pq, nq, kk.ctypes.data, int(user_offset), cap, offs.ctypes.data,
+            out["users"].ctypes.data, out["n_low"].ctypes.data, out["n_up"].ctypes.data,
+            out["est"].ctypes.data, _stream(stream))
+        if st == 2 and capacity is None and offs[-1] > cap:   # RKR_ENOMEM: grow and retry
+            cap = int(offs[-1])
+            continue
+        _check(st)
+        tot = int(offs[-1])
+        res = {key: v[:tot] for key, v in out.items()}
+        res["offsets"] = offs
+        return res
+
+
+def rkr_merge_approx(k, c: float, s: int, offs, users, n_low, n_up, est) -> dict:
+    """Steps 1-3 of Section 4.3 on the union of the parts' candidates (host code)."""
+    lib = load()
+    offs = np.ascontiguousarray(offs, np.int64)
+    nq = len(offs) - 1
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    ins = [np.ascontiguousarray(a, dt) for a, dt in ((users, np.int32), (n_low, np.uint32),
+                                                     (n_up, np.uint32), (est, np.float64))]
+    tot = int(kk.sum(dtype=np.int64))
+    out = dict(users=np.empty(tot, np.int32), n_low=np.empty(tot, np.uint32),
+               n_up=np.empty(tot, np.uint32), est=np.empty(tot, np.float64),
+               case=np.empty(nq, np.int32), nc=np.empty(nq, np.int32))
+    _check(lib.rkr_merge_approx(nq, kk.ctypes.data, ctypes.c_double(c), int(s), offs.ctypes.data,
+                                *[a.ctypes.data for a in ins],
+                                *[out[key].ctypes.data for key in
+                                  ("users", "n_low", "n_up", "est", "case", "nc")]))
+    out["offsets"] = np.concatenate([[0], np.cumsum(kk, dtype=np.int64)])
+    return out
+
+
+def rkr_merge_exact(k, offs, users, ranks):
+    """Def. 2 on the union of the parts' answers (host code): (users, ranks, offsets)."""
+    lib = load()
+    offs = np.ascontiguousarray(offs, np.int64)
+    nq = len(offs) - 1
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    u = np.ascontiguousarray(users, np.int32)
+    r = np.ascontiguousarray(ranks, np.int32)
+    tot = int(kk.sum(dtype=np.int64))
+    ou, orr = np.empty(tot, np.int32), np.empty(tot, np.int32)
+    _check(lib.rkr_merge_exact(nq, kk.ctypes.data, offs.ctypes.data, u.ctypes.data, r.ctypes.data,
+                               ou.ctypes.data, orr.ctypes.data))
+    return ou, orr, np.concatenate([[0], np.cumsum(kk, dtype=np.int64)])
+
+
 def rkr_query_exact_subsets(index, Q, k, subsets, **kw):
     """rkr_query_exact restricted to one user subset per query."""
     return rkr_query_exact(index, Q, k, subsets=subsets, **kw)
@@ -579,6 +649,9 @@ class Index:
 
     def pair_features(self, R, Q, pair_user, pair_query, **kw):
         return rkr_pair_features(self._h, R, Q, pair_user, pair_query, **kw)
+
+    def query_approx_candidates(self, Q, k, **kw):
+        return rkr_query_approx_candidates(self._h, Q, k, **kw)
 
     def query_exact_learned(self, pruner, R, Q, k, keep, **kw):
         return rkr_query_exact_learned(self._h, pruner, R, Q, k, keep, **kw)

@@ -582,6 +582,56 @@ rkr_status rkr_query_approx_single(rkr_index *idx, const float *Q, int32_t nq, c
                            out_nup, out_est, out_case, out_nc, stats, stream, true);
 }
 
+rkr_status rkr_query_approx_candidates(rkr_index *idx, const float *Q, int32_t nq,
+                                       const int32_t *k, int64_t user_offset, int64_t capacity,
+                                       int64_t *out_offs, int32_t *out_users, uint32_t *out_nlow,
+                                       uint32_t *out_nup, double *out_est, void *stream) {
+  g_err[0] = 0;
+  if (!out_offs || !out_users || !out_nlow || !out_nup || !out_est)
+    return fail(RKR_EINVAL, "null output");
+  if (capacity < 0) return fail(RKR_EINVAL, "capacity must be >= 0");
+  if (user_offset < 0 || idx == nullptr || user_offset + idx->n > ((int64_t)1 << 31))
+    return fail(RKR_EINVAL, "user ids with this offset must fit in int32");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> kh;
+  std::vector<int64_t> off;
+  RKR_TRY(query_prologue(idx, Q, nq, k, st, kh, off));
+  QueryStage qs;
+  QueryCommon qc;
+  RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
+  const size_t cap = (size_t)capacity;
+  OutView ou, olo, oup, oes;
+  RKR_TRY(ou.init(out_users, sizeof(int32_t) * cap, st));
+  RKR_TRY(olo.init(out_nlow, sizeof(uint32_t) * cap, st));
+  RKR_TRY(oup.init(out_nup, sizeof(uint32_t) * cap, st));
+  RKR_TRY(oes.init(out_est, sizeof(double) * cap, st));
+  std::vector<int64_t> offs(nq + 1, 0);
+  const rkr_status rs = run_query_approx_candidates(
+      idx, qc, nq, user_offset, capacity, offs.data(), (int32_t *)ou.dev, (uint32_t *)olo.dev,
+      (uint32_t *)oup.dev, (double *)oes.dev, st);
+  // the offsets are written even when the capacity was too small (they give the size)
+  if (is_device(out_offs))
+    RKR_CUDA(cudaMemcpyAsync(out_offs, offs.data(), sizeof(int64_t) * (nq + 1),
+                             cudaMemcpyHostToDevice, st));
+  else
+    memcpy(out_offs, offs.data(), sizeof(int64_t) * (nq + 1));
+  if (rs != RKR_OK) {
+    RKR_CUDA(cudaStreamSynchronize(st));
+    return rs;
+  }
+  const size_t tot = (size_t)offs[nq];
+  ou.bytes = sizeof(int32_t) * tot;
+  olo.bytes = sizeof(uint32_t) * tot;
+  oup.bytes = sizeof(uint32_t) * tot;
+  oes.bytes = sizeof(double) * tot;
+  RKR_TRY(ou.finish());
+  RKR_TRY(olo.finish());
+  RKR_TRY(oup.finish());
+  RKR_TRY(oes.finish());
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
 rkr_status rkr_query_approx_subsets(rkr_index *idx, const float *Q, int32_t nq,
                                     const int32_t *k, const int64_t *subset_offs,
                                     const int32_t *subset_users, double c, int32_t *out_users,

@@ -143,6 +143,20 @@ __device__ __forceinline__ int exact_j(double theta, double fmin, double delta, 
   return g;
 }
 
+// Step-3 estimate (Section 4.3): linear in u.q between (t_j, r_up) and (t_{j+1}, r_low).
+__device__ __forceinline__ double interp_est(double theta, int j, uint32_t nlo, uint32_t nup,
+                                             double fm, double dl, int tau, uint32_t s) {
+  double r_up = __dadd_rn(1.0, __ddiv_rn((double)nup, (double)s));
+  double r_low = __dadd_rn(1.0, __ddiv_rn((double)nlo, (double)s));
+  if (j >= 1 && j <= tau - 1) {
+    double tj = thr_at(fm, dl, j - 1);
+    double tj1 = thr_at(fm, dl, j);
+    double frac = __ddiv_rn(__dsub_rn(theta, tj), __dsub_rn(tj1, tj));
+    return __dsub_rn(r_up, __dmul_rn(__dsub_rn(r_up, r_low), frac));
+  }
+  return r_up;
+}
+
 // c(s) = #{i in [0, tau) : t_i < s}: the number of thresholds a score exceeds
 // (Alg. 1 counts p in column j when s(u,p) > t_j).
 __device__ __forceinline__ int exact_c(double s, double fmin, double delta, int tau) {

@@ -205,6 +205,15 @@ rkr_status run_query_approx_single(const rkr_index *idx, const QueryCommon &qc, 
                                    double *est_d, int32_t *case_d, int32_t *nc_d,
                                    rkr_query_stats *stats, cudaStream_t st);
 
+// Per query, the users whose lower-bound numerator is at most an upper estimate of
+// this index's R_up_k, with bounds and step-3 estimates (latency.cu); ids are
+// local + user_offset; offs_host gets nq + 1 offsets (also when RKR_ENOMEM says
+// the capacity was too small).
+rkr_status run_query_approx_candidates(const rkr_index *idx, const QueryCommon &qc, int nq,
+                                       int64_t user_offset, int64_t capacity, int64_t *offs_host,
+                                       int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d,
+                                       double *est_d, cudaStream_t st);
+
 // Learned pruner (pruner.cu): predictions of B pairs from a per-user feature table.
 rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t *uid,
                                  const float *t, int64_t B, float *y, cudaStream_t st);

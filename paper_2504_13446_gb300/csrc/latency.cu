@@ -195,7 +195,101 @@ __global__ void k_latency_compact(int64_t n, const uint32_t *__restrict__ nlo,
   }
 }
 
+// Step-3 estimate of each compacted candidate (canonical u.q) and its outputs at
+// `base`, with global user ids (local id + user_offset).
+__global__ void k_candidate_out(const uint32_t *__restrict__ qcount, int q,
+                                const int32_t *__restrict__ cu, const uint32_t *__restrict__ clo,
+                                const uint32_t *__restrict__ cup, const int32_t *__restrict__ cj,
+                                const float *__restrict__ U, const float *__restrict__ qrow, int d,
+                                const double *__restrict__ fmin, const double *__restrict__ delta,
+                                int tau, uint32_t s, int64_t user_offset, int64_t base,
+                                int32_t *__restrict__ ou, uint32_t *__restrict__ olo,
+                                uint32_t *__restrict__ oup, double *__restrict__ oest) {
+  const int64_t cnt = qcount[q];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = cu[i];
+    const double th = canon_dot(U + u * d, qrow, d);
+    ou[base + i] = (int32_t)(u + user_offset);
+    olo[base + i] = clo[i];
+    oup[base + i] = cup[i];
+    oest[base + i] = interp_est(th, cj[i], clo[i], cup[i], fmin[u], delta[u], tau, s);
+  }
+}
+
 }  // namespace
+
+// Per query, the users of this index whose lower bound is at most an upper
+// estimate T of this index's R_up_k, with their bounds and step-3 estimates.
+rkr_status run_query_approx_candidates(const rkr_index *idx, const QueryCommon &qc, int nq,
+                                       int64_t user_offset, int64_t capacity, int64_t *offs_host,
+                                       int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d,
+                                       double *est_d, cudaStream_t st) {
+  const int64_t n = idx->n;
+  const int d = idx->d;
+  const uint32_t top = (uint32_t)(idx->m * idx->s);
+  int shift = 0;
+  while ((top >> shift) >= (uint32_t)kLatBins) ++shift;
+  DevBuf b1, b2, b3, b4, b5, b6, b7, b8, b9, b10, b11, b12;
+  uint32_t *nlo, *nup, *ghist, *T, *qcount, *clo, *cup;
+  int32_t *jall, *cu, *cj;
+  double *cth;
+  unsigned long long *nfp64;
+  RKR_TRY(tmp_alloc(b1, &nlo, n, st));
+  RKR_TRY(tmp_alloc(b2, &nup, n, st));
+  RKR_TRY(tmp_alloc(b3, &jall, n, st));
+  RKR_TRY(tmp_alloc(b4, &ghist, kLatBins, st));
+  RKR_TRY(tmp_alloc(b5, &T, 1, st));
+  RKR_TRY(tmp_alloc(b6, &qcount, nq, st));
+  RKR_TRY(tmp_alloc(b7, &cu, n, st));
+  RKR_TRY(tmp_alloc(b8, &clo, n, st));
+  RKR_TRY(tmp_alloc(b9, &cup, n, st));
+  RKR_TRY(tmp_alloc(b10, &cj, n, st));
+  RKR_TRY(tmp_alloc(b11, &cth, n, st));
+  RKR_TRY(tmp_alloc(b12, &nfp64, 1, st));
+  RKR_CUDA(cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * kLatBins, st));
+  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(uint32_t) * nq, st));
+  RKR_CUDA(cudaMemsetAsync(nfp64, 0, sizeof(unsigned long long), st));
+  const bool vec4 = (d % 4) == 0 && ((uintptr_t)idx->U % 16) == 0;
+  const int grid = sm_count() * 4;
+  const int cgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+  offs_host[0] = 0;
+  for (int q = 0; q < nq; ++q) {
+    const float *qrow = qc.Qd + (int64_t)q * d;
+    if (vec4)
+      k_latency_scan<4><<<grid, kLatThreads, 0, st>>>(
+          idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
+          idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
+    else
+      k_latency_scan<1><<<grid, kLatThreads, 0, st>>>(
+          idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
+          idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
+    note_launch();
+    k_latency_cut<<<1, 1024, 0, st>>>(ghist, qc.kq_d, q, shift, T, qcount);
+    note_launch();
+    k_latency_compact<<<cgrid, 256, 0, st>>>(n, nlo, nup, jall, T, q, qcount, cu, clo, cup, cj,
+                                             cth);
+    note_launch();
+    RKR_CUDA(cudaGetLastError());
+    uint32_t cnt = 0;
+    RKR_CUDA(cudaMemcpyAsync(&cnt, qcount + q, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+    offs_host[q + 1] = offs_host[q] + cnt;
+    if (offs_host[q + 1] <= capacity && cnt > 0) {
+      k_candidate_out<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, 4 * sm_count()), 256, 0,
+                        st>>>(qcount, q, cu, clo, cup, cj, idx->U, qrow, d, idx->fmin,
+                              idx->delta, idx->tau, (uint32_t)idx->s, user_offset, offs_host[q],
+                              users_d, nlo_d, nup_d, est_d);
+      note_launch();
+      RKR_CUDA(cudaGetLastError());
+    }
+  }
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (offs_host[nq] > capacity)
+    return fail(RKR_ENOMEM, "candidate capacity %lld is below the %lld candidates found",
+                (long long)capacity, (long long)offs_host[nq]);
+  return RKR_OK;
+}
 
 rkr_status run_query_approx_single(const rkr_index *idx, const QueryCommon &qc, int nq, double c,
                                    int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d,

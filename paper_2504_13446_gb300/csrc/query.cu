@@ -173,20 +173,6 @@ __global__ void k_resolve_approx(int64_t count, const int32_t *__restrict__ cu,
   nup[i] = j >= 1 ? N[u * tau + j - 1] : top;
 }
 
-// Step-3 estimate (Section 4.3): linear in u.q between (t_j, r_up) and (t_{j+1}, r_low).
-__device__ __forceinline__ double interp_est(double theta, int j, uint32_t nlo, uint32_t nup,
-                                             double fm, double dl, int tau, uint32_t s) {
-  double r_up = __dadd_rn(1.0, __ddiv_rn((double)nup, (double)s));
-  double r_low = __dadd_rn(1.0, __ddiv_rn((double)nlo, (double)s));
-  if (j >= 1 && j <= tau - 1) {
-    double tj = thr_at(fm, dl, j - 1);
-    double tj1 = thr_at(fm, dl, j);
-    double frac = __ddiv_rn(__dsub_rn(theta, tj), __dsub_rn(tj1, tj));
-    return __dsub_rn(r_up, __dmul_rn(__dsub_rn(r_up, r_low), frac));
-  }
-  return r_up;
-}
-
 struct ApproxCand {
   const int32_t *uid;
   const uint32_t *nlo, *nup;
