@@ -14,7 +14,7 @@ copies included.  ``cpu_baseline`` times the FP64
 oracle on a bounded sample of users and queries and scales it to the workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                      [--case full|small|learned]
+                      [--case full|small|learned|latency|sweep]
 """
 
 from __future__ import annotations
@@ -313,6 +313,7 @@ def bench_ours(args):
         "candidates": {"approx": qa0["candidates"], "exact": qe0["candidates"],
                        "exact_recounted": qe0["recounted"],
                        "exact_recount_users": qe0["recount_users"],
+                       "exact_recount_split": qe0["recount_split"],
                        "exact_recount_open": qe0["recount_open"],
                        "wide_queries": [qa0["wide_queries"], qe0["wide_queries"]],
                        "deep_queries": [qa0["deep_queries"], qe0["deep_queries"]]},
@@ -464,6 +465,136 @@ def bench_learned(args):
     }))
 
 
+def bench_latency(args):
+    """Queries one at a time (rkr_query_approx_single) on the 1M x 100k x 200
+    index: the paper's per-query protocol (1,000 random items of P as queries,
+    each answered on its own).  Reports ms per query and the HBM bandwidth of the
+    scan kernel (its algorithmic bytes: U once, per-user bin data, two table
+    cells and the bound arrays it writes) against the measured copy bandwidth."""
+    import torch
+    import paper_2504_13446_gb300 as rkr
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    peaks, peak_src = _load_peaks()
+    w, pos = make_inputs("full")
+    U = torch.from_numpy(w.U).cuda()
+    P = torch.from_numpy(w.P).cuda()
+    nq = int(os.environ.get("RKR_LATENCY_QUERIES", "1000"))
+    Q = torch.from_numpy(w.Q[:nq]).cuda()
+    k = torch.from_numpy(w.k[:nq].astype(np.int32)).cuda()
+    stream = torch.cuda.current_stream()
+    idx = rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s, fbounds="exact", exact_table=False,
+                    sample_pos=pos)
+    for _ in range(max(args.warmup, 1)):
+        idx.query_approx(Q[:50], k[:50], C, single=True, device=True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    rkr.rkr_profile_start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one = idx.query_approx(Q, k, C, single=True, device=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = rkr.rkr_profile_stop()
+    clocks = sampler.stop()
+    ms_q = ev0.elapsed_time(ev1) / (args.steps * nq)
+    batch = idx.query_approx(Q, k, C, device=True)
+    same = all(bool((one[key] == batch[key]).all()) for key in
+               ("users", "n_low", "n_up", "est", "case", "nc"))
+    idx.close()
+    n_l, t_ms, work = prof["k_latency_scan"]
+    gbs = work / (t_ms / n_l / 1000.0) / n_l / 1e9
+    print(json.dumps({
+        "case": "latency (one query at a time)",
+        "metric": "ms/query", "value": ms_q, "unit": "ms/query", "higher_is_better": False,
+        "queries_per_s": 1000.0 / ms_q, "queries": nq, "steps": args.steps,
+        "config": {"workload": "c-approximate reverse k-ranks, one query at a time: "
+                               "|U|=1,000,000 |P|=100,000 d=200 mixture, tau=500, omega=10, "
+                               "s=100, c=2, 1,000 queries from P, k in {10,50,100}"},
+        "equals_batched_answer": same,
+        "roofline": {"kernel": "k_latency_scan", "bound": "hbm", "achieved": gbs,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                     "traffic": None, "ms_per_launch": t_ms / n_l,
+                     "bytes_per_launch": work / n_l,
+                     "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "kernels_ms_per_query": {kk: round(v[1] / (args.steps * nq), 5) for kk, v in prof.items()
+                                 if not kk.startswith("span:")},
+        "clocks": clocks,
+        "paper_context": "the paper's one-thread CPU query time at tau=500 is 57.8-501.9 ms on "
+                         "its datasets (Table 1; i9-10980XE)"}))
+
+
+SWEEP = [(100, 10, 100), (500, 10, 100), (1000, 10, 100),     # tau at omega 10, s 100
+         (500, 1, 1000), (500, 10, 10), (500, 10, 1000), (500, 100, 100)]
+
+
+def bench_sweep(args):
+    """The analogue of the paper's Table 1 on the 1M x 100k x 200 workload: for each
+    (tau, omega, s) of SWEEP, the build time of the c-approximate index, the time of
+    the 10,000-query batch (c = 2), the index's device memory, and the quality of the
+    answers against the exact ones (accuracy, overall ratio, recall, c-bound
+    violations).  The exact answers and the exact ranks of every returned user come
+    from one exact index (they do not depend on tau, omega or s)."""
+    import torch
+    import paper_2504_13446_gb300 as rkr
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w, pos0 = make_inputs("full")
+    U = torch.from_numpy(w.U).cuda()
+    P = torch.from_numpy(w.P).cuda()
+    Q = torch.from_numpy(w.Q).cuda()
+    k = w.k.astype(np.int32)
+    nq = w.Q.shape[0]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    exact = rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s, fbounds="exact", exact_table=True,
+                      sample_pos=pos0)
+    _, best, off, _ = exact.query_exact(Q, k)
+    qid = np.repeat(np.arange(nq, dtype=np.int32), np.diff(off))
+    rows = []
+    for tau, omega, s_ in SWEEP:
+        sizes = np.array([w.m // omega + (1 if l < w.m % omega else 0) for l in range(omega)])
+        pos = synth.sample_positions(w.seed, sizes, s_)
+        kw = dict(tau=tau, omega=omega, s=s_, fbounds="exact", exact_table=False, sample_pos=pos)
+        rkr.Index(U, P, **kw).close()                      # warm-up build
+        idx, ms_build = timed(lambda: rkr.Index(U, P, **kw))
+        idx.query_approx(Q, k, C, device=True)              # warm-up batch
+        a, ms_query = timed(lambda: idx.query_approx(Q, k, C, device=True))
+        mem = idx.device_bytes()
+        idx.close()
+        users = a["users"].cpu().numpy()
+        r_c = exact.rank_pairs(w.Q, users, qid)
+        qual = approx_quality(r_c, off, best, C)
+        rows.append({"tau": tau, "omega": omega, "s": s_, "build_ms": ms_build,
+                     "query_batch_ms": ms_query, "ms_per_query": ms_query / nq,
+                     "index_device_gb": mem / 1e9,
+                     "case_b_queries": int((a["case"].cpu().numpy() == 2).sum()),
+                     **{kk: qual[kk] for kk in ("accuracy", "overall_ratio", "recall_at_k",
+                                                 "c_bound_violations",
+                                                 "queries_with_violations")}})
+    exact.close()
+    print(json.dumps({
+        "case": "sweep (Table 1 analogue)",
+        "config": {"workload": "c-approximate reverse k-ranks: |U|=1,000,000 |P|=100,000 d=200 "
+                               "mixture (256 centres), 10,000 queries from P, k in {10,50,100}, "
+                               "c=2, exact f-bounds; one batch of all queries per setting"},
+        "rows": rows,
+        "paper_context": "Table 1 of the paper: query time, overall ratio and memory at tau = "
+                         "100/500/1000 on Amazon-Kindle, MovieLens and Netflix (real data, one "
+                         "CPU thread per query)"}))
+
+
 def cpu_baseline(w, pos, n_sample=None, q_sample=None):
     """The oracle on a user sample (all items), scaled by n / n_sample; queries of the
     approximate step on a query sample, scaled by nq / q_sample."""
@@ -582,7 +713,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="full", choices=["full", "small", "learned"],
+    ap.add_argument("--case", default="full",
+                    choices=["full", "small", "learned", "latency", "sweep"],
                     help="small: a 40k-user profiling case (no CPU baseline, no e2e); "
                          "learned: train the rank regressor and compare the learned cut "
                          "with the plain exact query")
@@ -596,6 +728,10 @@ def main():
         bench_reference(args)
     elif args.case == "learned":
         bench_learned(args)
+    elif args.case == "latency":
+        bench_latency(args)
+    elif args.case == "sweep":
+        bench_sweep(args)
     else:
         bench_ours(args)
 

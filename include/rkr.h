@@ -103,6 +103,10 @@ typedef struct {
                                open after the interval pass; each of their m item scores is
                                placed exactly, and near_ties of them needed FP64, so
                                near_ties / (recount_open * m) is the flagged fraction */
+  int64_t recount_split;    /* exact path: recounted candidates whose interval was still open
+                               after the single-product pass and went to the split pass */
+  int64_t learned_revived;  /* learned cut: cut candidates whose lower bound could still reach
+                               the k-th rank, recounted by the exact fallback */
   double max_screen_err_ratio; /* exact path: largest |s_hat - s(u,p)| / b over the same pairs
                                as max_rel_screen_err, b the rigorous screen bound (a sound
                                bound keeps it <= 1) */
@@ -314,10 +318,13 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  * rank the tail lists settle keep their exact rank, and of the candidates that
  * would still need a recount over P only the keep[i] with the smallest
  * predicted log rank (and those tying with the keep[i]-th) are recounted for
- * query i; the others are dropped.  The k smallest (rank, index) among the rest
- * are returned; stats->candidates counts the candidates left after the cut.
- * Every returned rank is exact; the answer set is exact when the true k best
- * survive the cut, and its recall is to be measured against rkr_query_exact.
+ * query i.  Exact fallback: after that recount, every cut candidate whose rank
+ * lower bound (from the tail lists and count tables) does not exceed the k-th
+ * smallest count found is recounted as well; the others cannot be among the k
+ * best.  So the answer equals rkr_query_exact's, users and ranks; the cut only
+ * saves the recount of candidates the fallback does not revive.
+ * stats->candidates counts the candidates left after the cut (revived ones
+ * included), stats->learned_revived the revived ones.
  * keep: nq int32 (host or device), keep[i] >= k[i], else RKR_EINVAL.
  */
 rkr_status rkr_rank_pairs(rkr_index *idx, const float *Q, int32_t nq, int64_t npairs,
@@ -436,6 +443,11 @@ void rkr_index_free(rkr_index *idx);
  *   device cannot hold it.  On failure *out is NULL and nothing stays allocated.
  */
 rkr_status rkr_index_save(const rkr_index *idx, const char *path);
+/* Device memory the index holds, in bytes (the sum of its arrays: the copies of
+ * U and P, their BF16 operands, the rank table, bounds and, with exact_table,
+ * the exact count table and tail lists); the file rkr_index_save writes is that
+ * size plus a small header. */
+rkr_status rkr_index_device_bytes(const rkr_index *idx, int64_t *out);
 rkr_status rkr_index_load(const char *path, rkr_index **out);
 
 /* rkr_pruner_save / rkr_pruner_load: the learned pruner's F, H and FP32 master

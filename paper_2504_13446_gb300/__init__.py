@@ -60,7 +60,8 @@ class QueryStats(ctypes.Structure):
                 ("ms_theta", ctypes.c_double), ("ms_resolve", ctypes.c_double),
                 ("ms_select", ctypes.c_double), ("recounted", ctypes.c_int64),
                 ("deep_queries", ctypes.c_int32), ("recount_users", ctypes.c_int64),
-                ("recount_open", ctypes.c_int64), ("max_screen_err_ratio", ctypes.c_double)]
+                ("recount_open", ctypes.c_int64), ("recount_split", ctypes.c_int64),
+                ("learned_revived", ctypes.c_int64), ("max_screen_err_ratio", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -146,6 +147,8 @@ def load() -> ctypes.CDLL:
         lib.rkr_profile_stop.argtypes = [ctypes.c_char_p, I64]
         lib.rkr_screen_scores_static.restype = I32
         lib.rkr_screen_scores_static.argtypes = [V, I64, V, I64, I32, I32, V, V, V]
+        lib.rkr_index_device_bytes.restype = I32
+        lib.rkr_index_device_bytes.argtypes = [V, ctypes.POINTER(I64)]
         lib.rkr_index_save.restype = I32
         lib.rkr_index_save.argtypes = [V, ctypes.c_char_p]
         lib.rkr_index_load.restype = I32
@@ -175,7 +178,7 @@ def rkr_profile_stop() -> dict:
     _check(load().rkr_profile_stop(buf, len(buf)))
     out = {}
     for line in buf.value.decode().splitlines():
-        name, n, ms, work = line.split()
+        name, n, ms, work = line.rsplit(maxsplit=3)
         out[name] = (int(n), float(ms), float(work))
     return out
 
@@ -623,6 +626,12 @@ class Index:
         raw = (ctypes.c_int64 * 8)()
         _check(load().rkr_index_info(self._h, raw))
         self.info = _Info(*[int(v) for v in raw])
+
+    def device_bytes(self) -> int:
+        """Device memory the index holds (rkr_index_device_bytes)."""
+        out = ctypes.c_int64()
+        _check(load().rkr_index_device_bytes(self._h, ctypes.byref(out)))
+        return int(out.value)
 
     def save(self, path: str) -> None:
         """Write the index to a file (rkr_index_save)."""

@@ -141,10 +141,13 @@ rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, con
                    const SkimList &list, int *err, cudaStream_t st);
 // refined[0] = queued undecided items, refined[1] = of those, canonical FP64 evaluations.
 // With hist_hi (bounds mode) nothing is queued: undecided items give count intervals.
+// split = 0 screens with the single BF16 product (bounds mode only: wider count
+// intervals for a third of the tensor work); the exact mode always splits.
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
                       const int32_t *seg_user, const int32_t *seg_self, const double *ths,
-                      uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined);
+                      uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined,
+                      int split = 1);
 constexpr int kXGrid = 128;
 constexpr int kRecountSeg = 1;      // thresholds per recount segment (one per screen row)
 constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)

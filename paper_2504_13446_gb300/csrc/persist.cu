@@ -145,6 +145,20 @@ rkr_status get(FILE *f, Hash &h, void *p, size_t bytes) {
 
 using namespace rkr;
 
+extern "C" rkr_status rkr_index_device_bytes(const rkr_index *idx_c, int64_t *out) {
+  set_error("%s", "");
+  if (!idx_c || !out) return fail(RKR_EINVAL, "null argument");
+  rkr_index *idx = const_cast<rkr_index *>(idx_c);  // arrays are only listed
+  int64_t list_entries = 0;
+  if (idx->has_exact)
+    RKR_CUDA(cudaMemcpy(&list_entries, idx->xloff + idx->n, sizeof(int64_t),
+                        cudaMemcpyDeviceToHost));
+  int64_t tot = 0;
+  for (const Arr &a : arrays(idx, list_entries)) tot += (int64_t)a.bytes;
+  *out = tot;
+  return RKR_OK;
+}
+
 extern "C" rkr_status rkr_index_save(const rkr_index *idx_c, const char *path) {
   set_error("%s", "");
   if (!idx_c || !path) return fail(RKR_EINVAL, "null argument");

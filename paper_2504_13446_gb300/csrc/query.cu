@@ -1097,7 +1097,8 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
                                      const int32_t *cu_all, const int32_t *cq_all,
                                      const int32_t *qself, uint32_t *ccount_all,
                                      uint32_t *clb_all, unsigned long long *ties_d,
-                                     cudaStream_t st, int64_t *nusers = nullptr) {
+                                     cudaStream_t st, int64_t *nusers = nullptr,
+                                     int split = 1) {
   const int bs = 256;
   DevBuf bcu, bcq, bci, bcc, bcur;
   int32_t *cu, *cq, *ci;
@@ -1173,9 +1174,11 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     RKR_CUDA(cudaMemsetAsync(hist_hi, 0, sizeof(uint32_t) * 2 * cnt, st));
   }
   {
-    ProfScope prof(clb_all ? "span:recount(bounds)" : "span:recount(exact)", st, 0.0);
+    ProfScope prof(clb_all ? (split ? "span:recount(bounds,split)" : "span:recount(bounds,single)")
+                           : "span:recount(exact)",
+                   st, 0.0);
     RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, sself,
-                       ths, hist, hist_hi, st, refined));
+                       ths, hist, hist_hi, st, refined, split));
   }
   {
     const int prof_slot = prof_begin("k_seg_suffix", st);
@@ -1375,7 +1378,8 @@ __global__ void __launch_bounds__(256)
     k_learned_cut(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
                   const int32_t *__restrict__ keep_q, const float *__restrict__ y,
                   int32_t *__restrict__ fb_all, int32_t *__restrict__ cu_all,
-                  uint32_t *__restrict__ ccount, unsigned long long *__restrict__ ncut) {
+                  uint32_t *__restrict__ ccount, int32_t *__restrict__ cutu_all,
+                  unsigned long long *__restrict__ ncut) {
   __shared__ uint32_t hist[256];
   __shared__ uint64_t bc[2];
   __shared__ unsigned long long acc;
@@ -1383,7 +1387,7 @@ __global__ void __launch_bounds__(256)
   const int64_t base = qoff[q] - qoff[qa];
   const int64_t cnt = qcount[q];
   const int64_t keep = keep_q[q];
-  int32_t *fb = fb_all + base, *cu = cu_all + base;
+  int32_t *fb = fb_all + base, *cu = cu_all + base, *cutu = cutu_all + base;
   uint32_t *cc = ccount + base;
   const float *yy = y + base;
   auto key_of = [&](int64_t i) {
@@ -1404,11 +1408,48 @@ __global__ void __launch_bounds__(256)
                                   &acc);
   for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
     if (fb[i] >= 0 && key_of(i) > kth) {
+      cutu[i] = cu[i];   // kept for the exact fallback
       fb[i] = -1;
       cu[i] = -1;
       cc[i] = 0xffffffffu;
     }
   if (threadIdx.x == 0) atomicAdd(ncut, (unsigned long long)cut);
+}
+
+// Exact fallback of the learned cut (one block per query).  cap = the k-th
+// smallest count among the candidates not cut, an upper bound of the k-th
+// smallest count of all candidates.  A cut candidate whose lower bound clb is at
+// most cap could still be among the k best: it is revived (its user restored and
+// sent to the recount).  The others have count >= clb > cap and cannot be.
+__global__ void __launch_bounds__(256)
+    k_learned_revive(int qa, const int64_t *__restrict__ qoff,
+                     const uint32_t *__restrict__ qcount, const int32_t *__restrict__ kq,
+                     const uint32_t *__restrict__ ccount, const uint32_t *__restrict__ clb,
+                     int32_t *__restrict__ fb_all, int32_t *__restrict__ cu_all,
+                     int32_t *__restrict__ cutu_all, unsigned long long *__restrict__ nrev) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t bc[2];
+  __shared__ unsigned long long acc;
+  const int q = qa + blockIdx.x;
+  const int64_t base = qoff[q] - qoff[qa];
+  const int64_t cnt = qcount[q];
+  const int k = kq[q];
+  if (cnt < k) return;
+  int32_t *fb = fb_all + base, *cu = cu_all + base, *cutu = cutu_all + base;
+  const uint32_t *cc = ccount + base, *lb = clb + base;
+  const uint64_t cap = block_kth(cnt, (uint64_t)k, 32,
+                                 [&](int64_t i, uint64_t &key) { key = cc[i]; return true; },
+                                 hist, bc);
+  const int64_t rev = block_count(cnt, [&](int64_t i) {
+    return cutu[i] >= 0 && (uint64_t)lb[i] <= cap;
+  }, &acc);
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
+    if (cutu[i] >= 0 && (uint64_t)lb[i] <= cap) {
+      cu[i] = cutu[i];
+      fb[i] = cutu[i];
+      cutu[i] = -1;
+    }
+  if (threadIdx.x == 0 && rev) atomicAdd(nrev, (unsigned long long)rev);
 }
 
 // Predictions scattered back to candidate slots: y[oi[j]] = yc[j].
@@ -1493,7 +1534,7 @@ rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, 
 static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const LearnedPrune *lp,
                               int qa, int qb, int64_t cnt, int64_t nfb, const int64_t *qoff_rel,
                               const uint32_t *cursor, int32_t *cu, const int32_t *cq,
-                              int32_t *cu_fb, uint32_t *ccount, int64_t *cut_total,
+                              int32_t *cu_fb, uint32_t *ccount, int32_t *cutu, int64_t *cut_total,
                               cudaStream_t st) {
   DevBuf b1, b2, b3, b4, b5, b6, b7, b8;
   int32_t *fu, *fq, *fi;
@@ -1520,7 +1561,7 @@ static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const
   k_scatter_y<<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(nfb, fi, yc, y);
   note_launch();
   k_learned_cut<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, lp->keep, y, cu_fb, cu, ccount,
-                                         ncut);
+                                         cutu, ncut);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   unsigned long long h = 0;
@@ -1556,7 +1597,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
   int64_t fallback = 0, list_fp64 = 0, cut_total = 0;
   double err_ratio = 0.0, err_rel = 0.0;
-  int64_t recount_users = 0, recount_open = 0;
+  int64_t recount_users = 0, recount_open = 0, recount_split = 0, revived = 0;
   unsigned long long lstat_host_fb = 0;
   Plan plan;
   Timer t1(st);
@@ -1641,9 +1682,15 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       RKR_CUDA(cudaStreamSynchronize(st));
       err_ratio = std::max(err_ratio, (double)u32_float((uint32_t)ls[2]));
       err_rel = std::max(err_rel, (double)u32_float((uint32_t)ls[3]));
+      DevBuf bcut;
+      int32_t *cutu = nullptr;
+      if (lp) {
+        RKR_TRY(tmp_alloc(bcut, &cutu, cnt, st));
+        RKR_CUDA(cudaMemsetAsync(cutu, 0xff, sizeof(int32_t) * cnt, st));
+      }
       if (lp && lstat_host_fb > 0) {  // learned cut of the candidates still to be recounted
         RKR_TRY(learned_cut(idx, qc, lp, qa, qb, cnt, (int64_t)lstat_host_fb, qoff_rel, cursor,
-                            cu, cq, cu_fb, ccount, &cut_total, st));
+                            cu, cq, cu_fb, ccount, cutu, &cut_total, st));
         lstat_host_fb = 0;
         DevBuf bn4;
         unsigned long long *nfb4;
@@ -1657,34 +1704,59 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       }
       fallback += (int64_t)lstat_host_fb;
       list_fp64 += (int64_t)ls[1];
-      if (lstat_host_fb > 0) {
+      auto recount_open_candidates = [&](unsigned long long h2) -> rkr_status {
         // count intervals for every remaining candidate, then the cap again; only
         // candidates that can still make the k smallest and whose interval is
-        // open get their undecided items resolved
-        RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr,
-                                   st, &recount_users));
-        {
-          const int prof_slot = prof_begin("k_recount_filter", st);
-          k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
-                                                   cu_fb);
-          prof_end(prof_slot, st, 0.0);
+        // open go on.  The first pass screens with the single BF16 product (a
+        // third of the tensor work, wider intervals), the second with the split
+        // product on the candidates still open; the exact pass then resolves the
+        // undecided items of those that remain.
+        for (int pass = 0; pass < 2 && h2 > 0; ++pass) {
+          RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr,
+                                     st, pass == 0 ? &recount_users : nullptr,
+                                     pass == 0 ? 0 : 1));
+          if (pass == 1) recount_split += (int64_t)h2;
+          {
+            const int prof_slot = prof_begin("k_recount_filter", st);
+            k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount,
+                                                     clb, cu_fb);
+            prof_end(prof_slot, st, 0.0);
+          }
+          note_launch();
+          k_drop_decided<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, ccount, clb, cu_fb);
+          note_launch();
+          RKR_CUDA(cudaGetLastError());
+          DevBuf bn3;
+          unsigned long long *nfb2;
+          RKR_TRY(tmp_alloc(bn3, &nfb2, 1, st));
+          RKR_CUDA(cudaMemsetAsync(nfb2, 0, sizeof(unsigned long long), st));
+          k_count_valid<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_fb, nfb2);
+          note_launch();
+          RKR_CUDA(cudaMemcpyAsync(&h2, nfb2, sizeof(h2), cudaMemcpyDeviceToHost, st));
+          RKR_CUDA(cudaStreamSynchronize(st));
         }
-        note_launch();
-        k_drop_decided<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, ccount, clb, cu_fb);
-        note_launch();
-        RKR_CUDA(cudaGetLastError());
-        DevBuf bn3;
-        unsigned long long *nfb2, h2 = 0;
-        RKR_TRY(tmp_alloc(bn3, &nfb2, 1, st));
-        RKR_CUDA(cudaMemsetAsync(nfb2, 0, sizeof(unsigned long long), st));
-        k_count_valid<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_fb, nfb2);
-        note_launch();
-        RKR_CUDA(cudaMemcpyAsync(&h2, nfb2, sizeof(h2), cudaMemcpyDeviceToHost, st));
-        RKR_CUDA(cudaStreamSynchronize(st));
         recount_open += (int64_t)h2;
         if (h2 > 0)
           RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, nullptr, ties_d,
                                      st));
+        return RKR_OK;
+      };
+      if (lstat_host_fb > 0) RKR_TRY(recount_open_candidates(lstat_host_fb));
+      if (lp && cut_total > 0) {
+        // exact fallback: cut candidates that could still be among the k best
+        DevBuf brv;
+        unsigned long long *nrev, hrev = 0;
+        RKR_TRY(tmp_alloc(brv, &nrev, 1, st));
+        RKR_CUDA(cudaMemsetAsync(nrev, 0, sizeof(unsigned long long), st));
+        k_learned_revive<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
+                                                  cu_fb, cu, cutu, nrev);
+        note_launch();
+        RKR_CUDA(cudaGetLastError());
+        RKR_CUDA(cudaMemcpyAsync(&hrev, nrev, sizeof(hrev), cudaMemcpyDeviceToHost, st));
+        RKR_CUDA(cudaStreamSynchronize(st));
+        revived += (int64_t)hrev;
+        fallback += (int64_t)hrev;
+        if (hrev > 0) RKR_TRY(recount_open_candidates(hrev));
       }
     }
     ms_res += t3.stop();
@@ -1718,9 +1790,11 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
     stats->recounted = fallback;
     stats->recount_users = recount_users;
     stats->recount_open = recount_open;
+    stats->recount_split = recount_split;
     stats->max_rel_screen_err = err_rel;
     stats->max_screen_err_ratio = err_ratio;
-    if (lp) stats->candidates = total - cut_total;  // candidates left by the learned cut
+    if (lp) stats->candidates = total - cut_total + revived;  // left by the learned cut
+    stats->learned_revived = revived;
     stats->wide_queries = wide;
     stats->deep_queries = (int32_t)plan.deep.size();
     stats->ms_theta = ms_theta;

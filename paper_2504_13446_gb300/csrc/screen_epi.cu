@@ -1504,7 +1504,10 @@ __global__ void k_gather_side(const __nv_bfloat16 *__restrict__ hi,
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
                       const int32_t *seg_user, const int32_t *seg_self, const double *ths,
-                      uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined) {
+                      uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined,
+                      int split) {
+  // the exact mode places every item, so it always runs the split product
+  if (!hist_hi) split = 1;
   constexpr int BN = 256;
   const int64_t m = idx->m;
   if (nseg <= 0) return RKR_OK;
@@ -1528,7 +1531,7 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   }
   note_launch();
   tc::RowBound *tb = nullptr;
-  RKR_TRY(tc_tile_bounds(Pt, BN, 1, &tb, st));
+  RKR_TRY(tc_tile_bounds(Pt, BN, split, &tb, st));
   unsigned long long *qcount;
   int2 *qitems;
   int *flags;
@@ -1545,12 +1548,12 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
   EpiRC e;
-  e.nseg = nseg; e.ncols = m; e.bn = BN; e.rowb = A.rb3; e.tileb = tb;
-  e.gacc = tc_gacc(A.kp, 1); e.gcan = tc_gcan(idx->d);
+  e.nseg = nseg; e.ncols = m; e.bn = BN; e.rowb = split ? A.rb3 : A.rb1; e.tileb = tb;
+  e.gacc = tc_gacc(A.kp, split); e.gcan = tc_gcan(idx->d);
   e.seg_start = seg_start; e.seg_len = seg_len; e.ths = ths; e.hist = hist;
   e.hist_hi = hist_hi; e.seg_self = seg_self;
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
-  rkr_status s = launch_screen<BN, 4>(A, Pt, 1, row_schedule(nseg, m, BN), e, flags, st);
+  rkr_status s = launch_screen<BN, 4>(A, Pt, split, row_schedule(nseg, m, BN), e, flags, st);
   if (s == RKR_OK && !hist_hi) {
     {
       const int prof_slot = prof_begin("k_rc_refine", st);
