@@ -476,7 +476,14 @@ def bench_latency(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     peaks, peak_src = _load_peaks()
-    w, pos = make_inputs("full")
+    n_users = int(os.environ.get("RKR_LATENCY_USERS", "0"))   # profiling: fewer users
+    if n_users:
+        w = synth.make_workload(WORKLOAD, n=n_users)
+        sizes = np.array([w.m // w.omega + (1 if l < w.m % w.omega else 0)
+                          for l in range(w.omega)])
+        pos = synth.sample_positions(w.seed, sizes, w.s)
+    else:
+        w, pos = make_inputs("full")
     U = torch.from_numpy(w.U).cuda()
     P = torch.from_numpy(w.P).cuda()
     nq = int(os.environ.get("RKR_LATENCY_QUERIES", "1000"))

@@ -373,6 +373,42 @@ rkr_status rkr_pruner_train(rkr_pruner *pr, const float *X, const float *t, cons
                             uint64_t seed, float *final_loss, void *stream);
 void rkr_pruner_free(rkr_pruner *pr);
 
+/*
+ * Tuning (not in the paper): launch choices that change speed, never results.
+ * Process-wide; the library starts from the defaults below.
+ *   rc_bn            column tile of the recount screen: 256 (4 stages) or 128 (6 stages)
+ *   rc_single_first  1: the recount runs a single-BF16-product interval pass before the
+ *                    split-product pass; 0: split product only (the near-tie policy)
+ *   skip_level       0: the default skip level of the query screens (smallest L with
+ *                    2^L - 1 >= m / 128); else that level L (1..30)
+ *   cand_budget_log2 candidates per screening chunk = 2^value, 20..30 (default 26)
+ *   latency_ctas_per_sm  CTAs per SM of the one-at-a-time scan, 0 = occupancy maximum
+ * rkr_tuning_set validates every field (RKR_EINVAL) and applies to calls that start
+ * after it returns; rkr_tuning_get reads the current values.
+ *
+ * rkr_autotune: picks the tuning for one workload by timed trials on it.  what is a
+ * bit set: 1 = rkr_query_exact, 2 = rkr_query_approx, 4 = rkr_query_approx_single
+ * (with c); the trial time is the sum of the chosen calls on (Q, nq, k).  Each
+ * candidate tuning (a grid over the fields above) runs once untimed, then once
+ * timed with CUDA events on `stream`; every trial's answers must equal the first
+ * trial's (else RKR_EINTERNAL: tuning must not change results).  The fastest is
+ * set process-wide and written to *out, its time to *out_ms.  cache_path (may be
+ * NULL): a JSON-lines file; a line whose key (n, m, d, nq, sum of k, what) matches
+ * is used without trials, and a new choice is appended to it.
+ */
+typedef struct {
+  int32_t rc_bn;
+  int32_t rc_single_first;
+  int32_t skip_level;
+  int32_t cand_budget_log2;
+  int32_t latency_ctas_per_sm;
+} rkr_tuning;
+rkr_status rkr_tuning_get(rkr_tuning *out);
+rkr_status rkr_tuning_set(const rkr_tuning *in);
+rkr_status rkr_autotune(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k, double c,
+                        int32_t what, const char *cache_path, rkr_tuning *out, double *out_ms,
+                        void *stream);
+
 rkr_status rkr_profile_start(void);
 rkr_status rkr_profile_stop(char *report, int64_t len);
 

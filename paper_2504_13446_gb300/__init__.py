@@ -30,7 +30,8 @@ __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_ex
            "rkr_screen_scores", "rkr_screen_scores_static",
            "rkr_profile_start", "rkr_profile_stop", "Pruner", "rkr_rank_pairs",
            "rkr_pair_features", "rkr_query_exact_learned", "rkr_release_cached_memory",
-           "rkr_set_wait_limit", "device_allocations", "version", "EXPORTS"]
+           "rkr_set_wait_limit", "device_allocations", "version", "EXPORTS", "Tuning",
+           "rkr_tuning_get", "rkr_tuning_set", "rkr_autotune"]
 
 _lock = threading.Lock()
 _lib = None
@@ -62,6 +63,16 @@ class QueryStats(ctypes.Structure):
                 ("deep_queries", ctypes.c_int32), ("recount_users", ctypes.c_int64),
                 ("recount_open", ctypes.c_int64), ("recount_split", ctypes.c_int64),
                 ("learned_revived", ctypes.c_int64), ("max_screen_err_ratio", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    """Launch choices that change speed, never results (rkr_tuning)."""
+    _fields_ = [("rc_bn", ctypes.c_int32), ("rc_single_first", ctypes.c_int32),
+                ("skip_level", ctypes.c_int32), ("cand_budget_log2", ctypes.c_int32),
+                ("latency_ctas_per_sm", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -157,6 +168,13 @@ def load() -> ctypes.CDLL:
         lib.rkr_pruner_save.argtypes = [V, ctypes.c_char_p]
         lib.rkr_pruner_load.restype = I32
         lib.rkr_pruner_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(V)]
+        lib.rkr_tuning_get.restype = I32
+        lib.rkr_tuning_get.argtypes = [ctypes.POINTER(Tuning)]
+        lib.rkr_tuning_set.restype = I32
+        lib.rkr_tuning_set.argtypes = [ctypes.POINTER(Tuning)]
+        lib.rkr_autotune.restype = I32
+        lib.rkr_autotune.argtypes = [V, V, I32, V, ctypes.c_double, I32, ctypes.c_char_p,
+                                     ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_double), V]
         lib.rkr_device_allocations.restype = ctypes.c_uint64
         lib.rkr_device_allocations.argtypes = []
         lib.rkr_set_wait_limit.restype = I32
@@ -186,6 +204,36 @@ def rkr_profile_stop() -> dict:
 def kernel_launches() -> int:
     """Kernels launched by librkr.so in this process so far."""
     return int(load().rkr_kernel_launches())
+
+
+def rkr_tuning_get() -> dict:
+    """The process-wide tuning."""
+    t = Tuning()
+    _check(load().rkr_tuning_get(ctypes.byref(t)))
+    return t.as_dict()
+
+
+def rkr_tuning_set(**fields) -> None:
+    """Change tuning fields (the others keep their values)."""
+    t = Tuning()
+    _check(load().rkr_tuning_get(ctypes.byref(t)))
+    for key, v in fields.items():
+        setattr(t, key, int(v))
+    _check(load().rkr_tuning_set(ctypes.byref(t)))
+
+
+def rkr_autotune(index, Q, k, *, c: float = 2.0, what: int = 3, cache_path=None, stream=None):
+    """Pick the tuning for this workload by timed trials (rkr_autotune): (tuning, ms)."""
+    lib = load()
+    nq, _ = _shape(Q)
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    pq, kq = _ptr(Q, np.float32)
+    t = Tuning()
+    ms = ctypes.c_double()
+    _check(lib.rkr_autotune(index, pq, nq, kk.ctypes.data, ctypes.c_double(c), int(what),
+                            os.fsencode(cache_path) if cache_path else None, ctypes.byref(t),
+                            ctypes.byref(ms), _stream(stream)))
+    return t.as_dict(), float(ms.value)
 
 
 def device_allocations() -> int:
@@ -658,6 +706,9 @@ class Index:
 
     def pair_features(self, R, Q, pair_user, pair_query, **kw):
         return rkr_pair_features(self._h, R, Q, pair_user, pair_query, **kw)
+
+    def autotune(self, Q, k, **kw):
+        return rkr_autotune(self._h, Q, k, **kw)
 
     def query_approx_candidates(self, Q, k, **kw):
         return rkr_query_approx_candidates(self._h, Q, k, **kw)

@@ -47,6 +47,9 @@ void note_launch();
 // RKR_EUNSUPPORTED unless the current device is sm_103 (GB300).
 rkr_status check_device();
 
+// The process-wide tuning (rkr_tuning_set / rkr_autotune), read at launch time.
+rkr_tuning tuning();
+
 // Per-kernel device-time accounting, on while rkr_profile_start is in effect:
 // CUDA events recorded on the launching stream around a launch.  `work` is the
 // launch's algorithmic work (flops of a screen; 0 when not stated).

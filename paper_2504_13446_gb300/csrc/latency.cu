@@ -43,34 +43,55 @@ __host__ __device__ inline float latency_cfac(int d) {
   return (float)c * (1.0f + 0x1p-20f);
 }
 
+// This lane's part of the dot products of kLatRows consecutive rows with q: every
+// load of the batch is issued before the first product, so a warp keeps
+// kLatRows rows in flight (row r0 + rr; rows at or past n contribute 0).
 template <int VEC>
-__device__ __forceinline__ float lane_dot(const float *__restrict__ row, const float *qs, int d,
-                                          int lane) {
-  float acc = 0.0f;
+__device__ __forceinline__ void lane_dots(const float *__restrict__ U, int64_t r0, int64_t n,
+                                          int d, const float *qs, int lane,
+                                          float (&part)[kLatRows]) {
   if (VEC == 4) {
-    const float4 *r4 = reinterpret_cast<const float4 *>(row);
-    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
     const int dv = d >> 2;
+    float4 a[kLatRows][2];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {  // d <= 256: at most two float4 per lane
-      const int c = lane + 32 * p;
-      if (c < dv) {
-        const float4 a = __ldcs(r4 + c);   // streamed: U is read once per query
-        const float4 b = q4[c];
-        acc = __fmaf_rn(a.x, b.x, acc);
-        acc = __fmaf_rn(a.y, b.y, acc);
-        acc = __fmaf_rn(a.z, b.z, acc);
-        acc = __fmaf_rn(a.w, b.w, acc);
+    for (int rr = 0; rr < kLatRows; ++rr) {
+      const float4 *r4 = reinterpret_cast<const float4 *>(U + (r0 + rr) * d);
+      const bool ok = r0 + rr < n;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {  // d <= 256: at most two float4 per lane
+        const int c = lane + 32 * p;
+        a[rr][p] = ok && c < dv ? __ldcs(r4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+    }
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+    const float4 b0 = q4[lane], b1 = q4[lane + 32];   // zero beyond d (qs is padded)
+#pragma unroll
+    for (int rr = 0; rr < kLatRows; ++rr) {
+      float acc = 0.0f;
+      acc = __fmaf_rn(a[rr][0].x, b0.x, acc);
+      acc = __fmaf_rn(a[rr][0].y, b0.y, acc);
+      acc = __fmaf_rn(a[rr][0].z, b0.z, acc);
+      acc = __fmaf_rn(a[rr][0].w, b0.w, acc);
+      acc = __fmaf_rn(a[rr][1].x, b1.x, acc);
+      acc = __fmaf_rn(a[rr][1].y, b1.y, acc);
+      acc = __fmaf_rn(a[rr][1].z, b1.z, acc);
+      acc = __fmaf_rn(a[rr][1].w, b1.w, acc);
+      part[rr] = acc;
     }
   } else {
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {  // d <= 256
-      const int c = lane + 32 * p;
-      if (c < d) acc = __fmaf_rn(__ldcs(row + c), qs[c], acc);
+    for (int rr = 0; rr < kLatRows; ++rr) {
+      const float *row = U + (r0 + rr) * d;
+      const bool ok = r0 + rr < n;
+      float acc = 0.0f;
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {  // d <= 256
+        const int c = lane + 32 * p;
+        if (ok && c < d) acc = __fmaf_rn(__ldcs(row + c), qs[c], acc);
+      }
+      part[rr] = acc;
     }
   }
-  return acc;
 }
 
 template <int VEC>
@@ -96,14 +117,16 @@ __global__ void __launch_bounds__(kLatThreads)
   uint32_t fp64 = 0;
   for (int64_t r0 = gw * kPerIter; r0 < n; r0 += nw * kPerIter) {
     float mine = 0.0f;
-#pragma unroll
+    // this lane's user: its bound and bin data are loaded while the rows stream in
+    const int64_t u = r0 + lane;
+    const bool live = u < n;
+    const float un = live ? unrm[u] : 0.0f;
+    const BinFP bu = live ? bf[u] : BinFP{0.f, 0.f, 0.f, 0.f};
+    const double fm = live ? fmin[u] : 0.0;
+#pragma unroll 1
     for (int sb = 0; sb < kLatSub; ++sb) {
       float part[kLatRows];
-#pragma unroll
-      for (int rr = 0; rr < kLatRows; ++rr) {
-        const int64_t u = r0 + sb * kLatRows + rr;
-        part[rr] = u < n ? lane_dot<VEC>(U + u * d, qs, d, lane) : 0.0f;
-      }
+      lane_dots<VEC>(U, r0 + sb * kLatRows, n, d, qs, lane, part);
 #pragma unroll
       for (int rr = 0; rr < kLatRows; ++rr) {
 #pragma unroll
@@ -112,15 +135,14 @@ __global__ void __launch_bounds__(kLatThreads)
         if (lane == sb * kLatRows + rr) mine = part[rr];
       }
     }
-    const int64_t u = r0 + lane;
-    if (u >= n) continue;
-    const float b = __fadd_ru(__fmul_ru(__fmul_ru(cf, unrm[u]), qn), 1e-30f);
+    if (!live) continue;
+    const float b = __fadd_ru(__fmul_ru(__fmul_ru(cf, un), qn), 1e-30f);
     int jlo, jhi;
-    bin_interval(bf[u], fmin[u], tau, __fsub_rd(mine, b), __fadd_ru(mine, b), jlo, jhi);
+    bin_interval(bu, fm, tau, __fsub_rd(mine, b), __fadd_ru(mine, b), jlo, jhi);
     int j = jlo;
     if (jlo != jhi) {
       ++fp64;
-      j = exact_j(canon_dot_slow(U + u * d, qs, d), fmin[u], delta[u], tau);
+      j = exact_j(canon_dot_slow(U + u * d, qs, d), fm, delta[u], tau);
     }
     const uint32_t lo = j < tau ? N[u * tau + j] : 0u;
     const uint32_t up = j >= 1 ? N[u * tau + j - 1] : top;
@@ -331,6 +353,8 @@ rkr_status run_query_approx_single(const rkr_index *idx, const QueryCommon &qc, 
     RKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_latency_scan<1>,
                                                            kLatThreads, 0));
   const int64_t warps_needed = (n + 31) / 32;
+  const int tuned = tuning().latency_ctas_per_sm;
+  if (tuned > 0) blocks_per_sm = std::min(std::max(blocks_per_sm, 1), tuned);
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((int64_t)sm_count() * std::max(blocks_per_sm, 1),
                            (warps_needed + kLatThreads / 32 - 1) / (kLatThreads / 32)));

@@ -806,6 +806,8 @@ static rkr_status skim_queries(const rkr_index *idx, const QueryCommon &qc, int 
 static int skip_level(const rkr_index *idx) {
   const char *env = getenv("RKR_SKIP_LEVEL");
   if (env && *env) return atoi(env);
+  const int tl = tuning().skip_level;
+  if (tl > 0) return tl;
   int64_t r = idx->m / 128;
   int L = 0;
   while (L < 31 && (((int64_t)1 << L) - 1) < r) ++L;
@@ -1064,7 +1066,7 @@ static std::vector<std::pair<int, int>> chunk_queries(const std::vector<int64_t>
   return out;
 }
 
-static int64_t candidate_budget() { return (int64_t)1 << 26; }
+static int64_t candidate_budget() { return (int64_t)1 << tuning().cand_budget_log2; }
 
 
 
@@ -1711,10 +1713,10 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
         // third of the tensor work, wider intervals), the second with the split
         // product on the candidates still open; the exact pass then resolves the
         // undecided items of those that remain.
-        for (int pass = 0; pass < 2 && h2 > 0; ++pass) {
+        for (int pass = tuning().rc_single_first ? 0 : 1; pass < 2 && h2 > 0; ++pass) {
+          const bool first = pass == 0 || !tuning().rc_single_first;
           RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr,
-                                     st, pass == 0 ? &recount_users : nullptr,
-                                     pass == 0 ? 0 : 1));
+                                     st, first ? &recount_users : nullptr, pass == 0 ? 0 : 1));
           if (pass == 1) recount_split += (int64_t)h2;
           {
             const int prof_slot = prof_begin("k_recount_filter", st);

@@ -1501,6 +1501,13 @@ __global__ void k_gather_side(const __nv_bfloat16 *__restrict__ hi,
   }
 }
 
+template <int BN, int STAGES>
+static rkr_status tc_recount_bn(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt,
+                                int64_t nseg, int64_t ncand, const int64_t *seg_start,
+                                const int32_t *seg_len, const int32_t *seg_user,
+                                const int32_t *seg_self, const double *ths, uint32_t *hist,
+                                uint32_t *hist_hi, cudaStream_t st, int64_t *refined, int split);
+
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
                       const int32_t *seg_user, const int32_t *seg_self, const double *ths,
@@ -1508,7 +1515,19 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       int split) {
   // the exact mode places every item, so it always runs the split product
   if (!hist_hi) split = 1;
-  constexpr int BN = 256;
+  if (tuning().rc_bn == 128)
+    return tc_recount_bn<128, 6>(idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user,
+                                 seg_self, ths, hist, hist_hi, st, refined, split);
+  return tc_recount_bn<256, 4>(idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user, seg_self,
+                               ths, hist, hist_hi, st, refined, split);
+}
+
+template <int BN, int STAGES>
+static rkr_status tc_recount_bn(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt,
+                                int64_t nseg, int64_t ncand, const int64_t *seg_start,
+                                const int32_t *seg_len, const int32_t *seg_user,
+                                const int32_t *seg_self, const double *ths, uint32_t *hist,
+                                uint32_t *hist_hi, cudaStream_t st, int64_t *refined, int split) {
   const int64_t m = idx->m;
   if (nseg <= 0) return RKR_OK;
   TcSide A;
@@ -1553,7 +1572,8 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
   e.seg_start = seg_start; e.seg_len = seg_len; e.ths = ths; e.hist = hist;
   e.hist_hi = hist_hi; e.seg_self = seg_self;
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
-  rkr_status s = launch_screen<BN, 4>(A, Pt, split, row_schedule(nseg, m, BN), e, flags, st);
+  rkr_status s =
+      launch_screen<BN, STAGES>(A, Pt, split, row_schedule(nseg, m, BN), e, flags, st);
   if (s == RKR_OK && !hist_hi) {
     {
       const int prof_slot = prof_begin("k_rc_refine", st);

@@ -1,0 +1,279 @@
+// tune.cu -- the process-wide tuning and the autotuner that picks it.
+//
+// Tuning fields change launch shapes and pass structure only; every result is
+// the same bit for bit (the autotuner checks that on every trial).  Choices
+// are cached in a JSON-lines file, one object per line:
+//   {"key": "n=...,m=...,d=...,nq=...,ksum=...,what=...", "rc_bn": 256,
+//    "rc_single_first": 1, "skip_level": 0, "cand_budget_log2": 26,
+//    "latency_ctas_per_sm": 0, "ms": 123.4}
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "index.cuh"
+
+namespace rkr {
+namespace {
+
+std::mutex g_tune_mu;
+rkr_tuning g_tune = {256, 1, 0, 26, 0};
+
+rkr_status check_tuning(const rkr_tuning &t) {
+  if (t.rc_bn != 128 && t.rc_bn != 256) return fail(RKR_EINVAL, "rc_bn must be 128 or 256");
+  if (t.rc_single_first != 0 && t.rc_single_first != 1)
+    return fail(RKR_EINVAL, "rc_single_first must be 0 or 1");
+  if (t.skip_level < 0 || t.skip_level > 30) return fail(RKR_EINVAL, "skip_level in [0, 30]");
+  if (t.cand_budget_log2 < 20 || t.cand_budget_log2 > 30)
+    return fail(RKR_EINVAL, "cand_budget_log2 in [20, 30]");
+  if (t.latency_ctas_per_sm < 0 || t.latency_ctas_per_sm > 32)
+    return fail(RKR_EINVAL, "latency_ctas_per_sm in [0, 32]");
+  return RKR_OK;
+}
+
+std::string tune_key(const rkr_index *idx, int nq, int64_t ksum, int what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "n=%lld,m=%lld,d=%d,nq=%d,ksum=%lld,what=%d", (long long)idx->n,
+           (long long)idx->m, idx->d, nq, (long long)ksum, what);
+  return buf;
+}
+
+// Value of "name": <int> on a cache line, or false.
+bool field(const char *line, const char *name, double *out) {
+  char pat[64];
+  snprintf(pat, sizeof(pat), "\"%s\":", name);
+  const char *p = strstr(line, pat);
+  if (!p) return false;
+  return sscanf(p + strlen(pat), " %lf", out) == 1;
+}
+
+bool cache_lookup(const char *path, const std::string &key, rkr_tuning *t, double *ms) {
+  if (!path) return false;
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  const std::string pat = "\"key\": \"" + key + "\"";
+  while (fgets(line, sizeof(line), f)) {
+    if (!strstr(line, pat.c_str())) continue;
+    double v[6];
+    if (field(line, "rc_bn", &v[0]) && field(line, "rc_single_first", &v[1]) &&
+        field(line, "skip_level", &v[2]) && field(line, "cand_budget_log2", &v[3]) &&
+        field(line, "latency_ctas_per_sm", &v[4]) && field(line, "ms", &v[5])) {
+      rkr_tuning c = {(int32_t)v[0], (int32_t)v[1], (int32_t)v[2], (int32_t)v[3],
+                      (int32_t)v[4]};
+      if (check_tuning(c) == RKR_OK) {
+        *t = c;
+        *ms = v[5];
+        found = true;   // the last matching line wins
+      }
+    }
+  }
+  fclose(f);
+  set_error("%s", "");
+  return found;
+}
+
+rkr_status cache_append(const char *path, const std::string &key, const rkr_tuning &t,
+                        double ms) {
+  if (!path) return RKR_OK;
+  FILE *f = fopen(path, "a");
+  if (!f) return fail(RKR_EINVAL, "cannot append to %s", path);
+  fprintf(f,
+          "{\"key\": \"%s\", \"rc_bn\": %d, \"rc_single_first\": %d, \"skip_level\": %d, "
+          "\"cand_budget_log2\": %d, \"latency_ctas_per_sm\": %d, \"ms\": %.4f}\n",
+          key.c_str(), t.rc_bn, t.rc_single_first, t.skip_level, t.cand_budget_log2,
+          t.latency_ctas_per_sm, ms);
+  if (fclose(f) != 0) return fail(RKR_EINVAL, "cannot write %s", path);
+  return RKR_OK;
+}
+
+int default_skip(const rkr_index *idx) {
+  int64_t r = idx->m / 128;
+  int L = 0;
+  while (L < 31 && (((int64_t)1 << L) - 1) < r) ++L;
+  return L;
+}
+
+// Device outputs of one trial, compared between trials.
+struct Outs {
+  std::vector<int32_t> eu, er, au, acase, anc, su;
+  std::vector<uint32_t> alo, aup, slo, sup;
+  std::vector<double> aest, sest;
+  bool operator==(const Outs &o) const {
+    return eu == o.eu && er == o.er && au == o.au && acase == o.acase && anc == o.anc &&
+           su == o.su && alo == o.alo && aup == o.aup && slo == o.slo && sup == o.sup &&
+           aest == o.aest && sest == o.sest;
+  }
+};
+
+}  // namespace
+
+rkr_tuning tuning() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune;
+}
+
+}  // namespace rkr
+
+using namespace rkr;
+
+extern "C" rkr_status rkr_tuning_get(rkr_tuning *out) {
+  if (!out) return fail(RKR_EINVAL, "null argument");
+  *out = tuning();
+  return RKR_OK;
+}
+
+extern "C" rkr_status rkr_tuning_set(const rkr_tuning *in) {
+  if (!in) return fail(RKR_EINVAL, "null argument");
+  RKR_TRY(check_tuning(*in));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune = *in;
+  return RKR_OK;
+}
+
+extern "C" rkr_status rkr_autotune(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   double c, int32_t what, const char *cache_path,
+                                   rkr_tuning *out, double *out_ms, void *stream) {
+  set_error("%s", "");
+  if (!idx || !Q || !k) return fail(RKR_EINVAL, "null argument");
+  if (nq < 1) return fail(RKR_EINVAL, "nq must be >= 1");
+  if (what < 1 || what > 7) return fail(RKR_EINVAL, "what must be a non-empty subset of 1|2|4");
+  if ((what & 1) && !idx->has_exact) return fail(RKR_EINVAL, "index has no exact table");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> kh(nq);
+  {
+    cudaPointerAttributes a;
+    const bool dev = cudaPointerGetAttributes(&a, k) == cudaSuccess &&
+                     (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (dev) RKR_CUDA(cudaMemcpy(kh.data(), k, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost));
+    else memcpy(kh.data(), k, sizeof(int32_t) * nq);
+  }
+  int64_t ksum = 0;
+  for (int q = 0; q < nq; ++q) ksum += kh[q];
+  const std::string key = tune_key(idx, nq, ksum, what);
+  const rkr_tuning before = tuning();
+  rkr_tuning best = before;
+  double best_ms = 0.0;
+  if (cache_lookup(cache_path, key, &best, &best_ms)) {
+    RKR_TRY(rkr_tuning_set(&best));
+    if (out) *out = best;
+    if (out_ms) *out_ms = best_ms;
+    return RKR_OK;
+  }
+  // candidate grid: only the fields the chosen calls depend on vary
+  const int ls = default_skip(idx);
+  std::vector<rkr_tuning> grid;
+  for (int bn : {256, 128})
+    for (int sf : {1, 0})
+      for (int sk : {0, ls - 1, ls + 1})
+        for (int lc : {0, 2, 4}) {
+          if (!(what & 1) && (bn != 256 || sf != 1)) continue;
+          if (!(what & 3) && sk != 0) continue;
+          if (!(what & 4) && lc != 0) continue;
+          if (sk < 0 || sk > 30 || (sk != 0 && sk == ls)) continue;
+          grid.push_back({bn, sf, sk, before.cand_budget_log2, lc});
+        }
+  const size_t tot = (size_t)ksum;
+  int32_t *users = nullptr, *ranks = nullptr, *icase = nullptr, *inc = nullptr;
+  uint32_t *nlo = nullptr, *nup = nullptr;
+  double *est = nullptr;
+  DevBuf b1, b2, b3, b4, b5, b6, b7;
+  RKR_TRY(tmp_alloc(b1, &users, tot, st));
+  RKR_TRY(tmp_alloc(b2, &ranks, tot, st));
+  RKR_TRY(tmp_alloc(b3, &nlo, tot, st));
+  RKR_TRY(tmp_alloc(b4, &nup, tot, st));
+  RKR_TRY(tmp_alloc(b5, &est, tot, st));
+  RKR_TRY(tmp_alloc(b6, &icase, nq, st));
+  RKR_TRY(tmp_alloc(b7, &inc, nq, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  cudaEvent_t e0, e1;
+  RKR_CUDA(cudaEventCreate(&e0));
+  RKR_CUDA(cudaEventCreate(&e1));
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evs{e0, e1};
+  auto run = [&](Outs *o) -> rkr_status {
+    if (what & 1) {
+      RKR_TRY(rkr_query_exact(idx, Q, nq, k, users, ranks, nullptr, st));
+      if (o) {
+        o->eu.resize(tot); o->er.resize(tot);
+        RKR_CUDA(cudaMemcpy(o->eu.data(), users, 4 * tot, cudaMemcpyDeviceToHost));
+        RKR_CUDA(cudaMemcpy(o->er.data(), ranks, 4 * tot, cudaMemcpyDeviceToHost));
+      }
+    }
+    for (int single = 0; single < 2; ++single) {
+      if (!(what & (single ? 4 : 2))) continue;
+      if (single)
+        RKR_TRY(rkr_query_approx_single(idx, Q, nq, k, c, users, nlo, nup, est, icase, inc,
+                                        nullptr, st));
+      else
+        RKR_TRY(rkr_query_approx(idx, Q, nq, k, c, users, nlo, nup, est, icase, inc, nullptr,
+                                 st));
+      if (o) {
+        auto &u = single ? o->su : o->au;
+        auto &lo = single ? o->slo : o->alo;
+        auto &up = single ? o->sup : o->aup;
+        auto &es = single ? o->sest : o->aest;
+        u.resize(tot); lo.resize(tot); up.resize(tot); es.resize(tot);
+        RKR_CUDA(cudaMemcpy(u.data(), users, 4 * tot, cudaMemcpyDeviceToHost));
+        RKR_CUDA(cudaMemcpy(lo.data(), nlo, 4 * tot, cudaMemcpyDeviceToHost));
+        RKR_CUDA(cudaMemcpy(up.data(), nup, 4 * tot, cudaMemcpyDeviceToHost));
+        RKR_CUDA(cudaMemcpy(es.data(), est, 8 * tot, cudaMemcpyDeviceToHost));
+        if (!single) {
+          o->acase.resize(nq); o->anc.resize(nq);
+          RKR_CUDA(cudaMemcpy(o->acase.data(), icase, 4 * nq, cudaMemcpyDeviceToHost));
+          RKR_CUDA(cudaMemcpy(o->anc.data(), inc, 4 * nq, cudaMemcpyDeviceToHost));
+        }
+      }
+    }
+    return RKR_OK;
+  };
+  Outs ref;
+  bool have_ref = false;
+  best_ms = -1.0;
+  for (const rkr_tuning &t : grid) {
+    RKR_TRY(rkr_tuning_set(&t));
+    Outs o;
+    rkr_status rs = run(&o);                  // untimed: warm-up and answer check
+    if (rs != RKR_OK) {
+      rkr_tuning_set(&before);
+      return rs;
+    }
+    if (!have_ref) {
+      ref = o;
+      have_ref = true;
+    } else if (!(o == ref)) {
+      rkr_tuning_set(&before);
+      return fail(RKR_EINTERNAL, "tuning (rc_bn %d, single_first %d, skip %d) changed the "
+                                 "answers", t.rc_bn, t.rc_single_first, t.skip_level);
+    }
+    RKR_CUDA(cudaStreamSynchronize(st));
+    RKR_CUDA(cudaEventRecord(e0, st));
+    rs = run(nullptr);
+    if (rs != RKR_OK) {
+      rkr_tuning_set(&before);
+      return rs;
+    }
+    RKR_CUDA(cudaEventRecord(e1, st));
+    RKR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    RKR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (best_ms < 0.0 || ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  RKR_TRY(rkr_tuning_set(&best));
+  RKR_TRY(cache_append(cache_path, key, best, best_ms));
+  if (out) *out = best;
+  if (out_ms) *out_ms = best_ms;
+  return RKR_OK;
+}

@@ -90,3 +90,18 @@ def test_oracle_is_not_imported_by_the_product():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_tuning_fields_are_validated_without_a_gpu():
+    import paper_2504_13446_gb300 as pkg
+    pkg.buildlib.build()
+    before = pkg.rkr_tuning_get()
+    try:
+        for bad in (dict(rc_bn=64), dict(rc_single_first=2), dict(skip_level=31),
+                    dict(cand_budget_log2=19), dict(latency_ctas_per_sm=-1)):
+            with pytest.raises(pkg.RKRError):
+                pkg.rkr_tuning_set(**bad)
+        pkg.rkr_tuning_set(rc_bn=128)
+        assert pkg.rkr_tuning_get()["rc_bn"] == 128
+    finally:
+        pkg.rkr_tuning_set(**before)
