@@ -510,6 +510,7 @@ def bench_latency(args):
     batch = idx.query_approx(Q, k, C, device=True)
     same = all(bool((one[key] == batch[key]).all()) for key in
                ("users", "n_low", "n_up", "est", "case", "nc"))
+    st1 = one["stats"]
     idx.close()
     n_l, t_ms, work = prof["k_latency_scan"]
     gbs = work / (t_ms / n_l / 1000.0) / n_l / 1e9
@@ -521,6 +522,7 @@ def bench_latency(args):
                                "|U|=1,000,000 |P|=100,000 d=200 mixture, tau=500, omega=10, "
                                "s=100, c=2, 1,000 queries from P, k in {10,50,100}"},
         "equals_batched_answer": same,
+        "canonical_fp64_fraction": st1.fp64_dots / max(st1.pairs, 1),
         "roofline": {"kernel": "k_latency_scan", "bound": "hbm", "achieved": gbs,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                      "traffic": None, "ms_per_launch": t_ms / n_l,

@@ -149,28 +149,39 @@ __global__ void __launch_bounds__(kLatThreads)
     nlo[u] = lo;
     nup[u] = up;
     jout[u] = j;
-    atomicAdd(&hist[min(up >> shift, (uint32_t)(kLatBins - 1))], 1u);
+    // lanes with the same bin add once (upper bounds crowd into few bins)
+    const unsigned bin = min(up >> shift, (uint32_t)(kLatBins - 1));
+    const unsigned peers = __match_any_sync(__activemask(), bin);
+    if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kLatBins; i += blockDim.x)
-    if (hist[i]) atomicAdd(&ghist[i], hist[i]);
+  // this CTA's histogram, stored whole (no atomics across CTAs)
+  uint32_t *mine_h = ghist + (size_t)blockIdx.x * kLatBins;
+  for (int i = threadIdx.x; i < kLatBins; i += blockDim.x) mine_h[i] = hist[i];
   fp64 = __reduce_add_sync(0xffffffffu, fp64);
   if (lane == 0 && fp64) atomicAdd(nfp64, (unsigned long long)fp64);
 }
 
+// Sum of the scan CTAs' histograms: thread b adds bin b over the `parts` rows.
+__global__ void __launch_bounds__(128)
+    k_latency_hsum(const uint32_t *__restrict__ parts_h, int parts, uint32_t *__restrict__ ghist) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= kLatBins) return;
+  uint32_t acc = 0;
+#pragma unroll 8
+  for (int g = 0; g < parts; ++g) acc += parts_h[(size_t)g * kLatBins + b];
+  ghist[b] = acc;
+}
+
 // T = upper end of the histogram bin holding the k-th smallest upper-bound
-// numerator (so T >= R_up_k); the histogram is cleared for the next query and
-// the candidate count of query q zeroed.
+// numerator (so T >= R_up_k); the candidate count of query q is zeroed.
 __global__ void __launch_bounds__(1024)
     k_latency_cut(uint32_t *__restrict__ ghist, const int32_t *__restrict__ kq, int q, int shift,
                   uint32_t *__restrict__ T, uint32_t *__restrict__ qcount) {
   __shared__ uint32_t h[kLatBins];
   __shared__ uint32_t part[1024];
   const int t = threadIdx.x;
-  for (int i = t; i < kLatBins; i += blockDim.x) {
-    h[i] = ghist[i];
-    ghist[i] = 0;
-  }
+  for (int i = t; i < kLatBins; i += blockDim.x) h[i] = ghist[i];
   __syncthreads();
   // each thread sums two bins; inclusive scan of the pair sums
   const uint32_t mine = h[2 * t] + h[2 * t + 1];
@@ -239,6 +250,80 @@ __global__ void k_candidate_out(const uint32_t *__restrict__ qcount, int q,
   }
 }
 
+// Scratch of the per-query bounds pass.
+struct ScanBufs {
+  uint32_t *nlo, *nup, *parts, *ghist, *T, *qcount;
+  int32_t *jall;
+  unsigned long long *nfp64;
+  int grid, shift;
+  uint32_t top;
+  bool vec4;
+};
+
+rkr_status alloc_scan(const rkr_index *idx, int nq, int ctas_per_sm, DevBuf (&b)[8], ScanBufs &sb,
+                      cudaStream_t st) {
+  const int64_t n = idx->n;
+  sb.top = (uint32_t)(idx->m * idx->s);
+  sb.shift = 0;
+  while ((sb.top >> sb.shift) >= (uint32_t)kLatBins) ++sb.shift;
+  sb.vec4 = (idx->d % 4) == 0 && ((uintptr_t)idx->U % 16) == 0;
+  int occ = 0;
+  if (sb.vec4)
+    RKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_latency_scan<4>, kLatThreads, 0));
+  else
+    RKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_latency_scan<1>, kLatThreads, 0));
+  occ = std::max(occ, 1);
+  if (ctas_per_sm > 0) occ = std::min(occ, ctas_per_sm);
+  const int64_t warps_needed = (n + 31) / 32;
+  sb.grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sm_count() * occ,
+                           (warps_needed + kLatThreads / 32 - 1) / (kLatThreads / 32)));
+  RKR_TRY(tmp_alloc(b[0], &sb.nlo, n, st));
+  RKR_TRY(tmp_alloc(b[1], &sb.nup, n, st));
+  RKR_TRY(tmp_alloc(b[2], &sb.jall, n, st));
+  RKR_TRY(tmp_alloc(b[3], &sb.parts, (size_t)sb.grid * kLatBins, st));
+  RKR_TRY(tmp_alloc(b[4], &sb.ghist, kLatBins, st));
+  RKR_TRY(tmp_alloc(b[5], &sb.T, 1, st));
+  RKR_TRY(tmp_alloc(b[6], &sb.qcount, nq, st));
+  RKR_TRY(tmp_alloc(b[7], &sb.nfp64, 2, st));
+  RKR_CUDA(cudaMemsetAsync(sb.qcount, 0, sizeof(uint32_t) * nq, st));
+  RKR_CUDA(cudaMemsetAsync(sb.nfp64, 0, 2 * sizeof(unsigned long long), st));
+  return RKR_OK;
+}
+
+// Bounds of every user for query q, their histogram and the cut T.
+rkr_status scan_pass(const rkr_index *idx, const QueryCommon &qc, int q, const ScanBufs &sb,
+                     cudaStream_t st) {
+  const float *qrow = qc.Qd + (int64_t)q * idx->d;
+  {
+    ProfScope prof("k_latency_scan", st,
+                   (double)idx->n * (4.0 * idx->d + 4 + sizeof(BinFP) + 8 + 8 + 12));
+    if (sb.vec4)
+      k_latency_scan<4><<<sb.grid, kLatThreads, 0, st>>>(
+          idx->U, idx->n, idx->d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta,
+          idx->N, idx->tau, sb.top, sb.shift, sb.nlo, sb.nup, sb.jall, sb.parts, sb.nfp64);
+    else
+      k_latency_scan<1><<<sb.grid, kLatThreads, 0, st>>>(
+          idx->U, idx->n, idx->d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta,
+          idx->N, idx->tau, sb.top, sb.shift, sb.nlo, sb.nup, sb.jall, sb.parts, sb.nfp64);
+    note_launch();
+  }
+  {
+    const int prof_slot = prof_begin("k_latency_hsum", st);
+    k_latency_hsum<<<kLatBins / 128, 128, 0, st>>>(sb.parts, sb.grid, sb.ghist);
+    prof_end(prof_slot, st, 0.0);
+    note_launch();
+  }
+  {
+    const int prof_slot = prof_begin("k_latency_cut", st);
+    k_latency_cut<<<1, 1024, 0, st>>>(sb.ghist, qc.kq_d, q, sb.shift, sb.T, sb.qcount);
+    prof_end(prof_slot, st, 0.0);
+    note_launch();
+  }
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
 }  // namespace
 
 // Per query, the users of this index whose lower bound is at most an upper
@@ -249,57 +334,33 @@ rkr_status run_query_approx_candidates(const rkr_index *idx, const QueryCommon &
                                        double *est_d, cudaStream_t st) {
   const int64_t n = idx->n;
   const int d = idx->d;
-  const uint32_t top = (uint32_t)(idx->m * idx->s);
-  int shift = 0;
-  while ((top >> shift) >= (uint32_t)kLatBins) ++shift;
-  DevBuf b1, b2, b3, b4, b5, b6, b7, b8, b9, b10, b11, b12;
-  uint32_t *nlo, *nup, *ghist, *T, *qcount, *clo, *cup;
-  int32_t *jall, *cu, *cj;
+  DevBuf bs[8], b7, b8, b9, b10, b11;
+  ScanBufs sb;
+  RKR_TRY(alloc_scan(idx, nq, tuning().latency_ctas_per_sm, bs, sb, st));
+  uint32_t *clo, *cup;
+  int32_t *cu, *cj;
   double *cth;
-  unsigned long long *nfp64;
-  RKR_TRY(tmp_alloc(b1, &nlo, n, st));
-  RKR_TRY(tmp_alloc(b2, &nup, n, st));
-  RKR_TRY(tmp_alloc(b3, &jall, n, st));
-  RKR_TRY(tmp_alloc(b4, &ghist, kLatBins, st));
-  RKR_TRY(tmp_alloc(b5, &T, 1, st));
-  RKR_TRY(tmp_alloc(b6, &qcount, nq, st));
   RKR_TRY(tmp_alloc(b7, &cu, n, st));
   RKR_TRY(tmp_alloc(b8, &clo, n, st));
   RKR_TRY(tmp_alloc(b9, &cup, n, st));
   RKR_TRY(tmp_alloc(b10, &cj, n, st));
   RKR_TRY(tmp_alloc(b11, &cth, n, st));
-  RKR_TRY(tmp_alloc(b12, &nfp64, 1, st));
-  RKR_CUDA(cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * kLatBins, st));
-  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(uint32_t) * nq, st));
-  RKR_CUDA(cudaMemsetAsync(nfp64, 0, sizeof(unsigned long long), st));
-  const bool vec4 = (d % 4) == 0 && ((uintptr_t)idx->U % 16) == 0;
-  const int grid = sm_count() * 4;
   const int cgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
   offs_host[0] = 0;
   for (int q = 0; q < nq; ++q) {
     const float *qrow = qc.Qd + (int64_t)q * d;
-    if (vec4)
-      k_latency_scan<4><<<grid, kLatThreads, 0, st>>>(
-          idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
-          idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
-    else
-      k_latency_scan<1><<<grid, kLatThreads, 0, st>>>(
-          idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
-          idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
-    note_launch();
-    k_latency_cut<<<1, 1024, 0, st>>>(ghist, qc.kq_d, q, shift, T, qcount);
-    note_launch();
-    k_latency_compact<<<cgrid, 256, 0, st>>>(n, nlo, nup, jall, T, q, qcount, cu, clo, cup, cj,
-                                             cth);
+    RKR_TRY(scan_pass(idx, qc, q, sb, st));
+    k_latency_compact<<<cgrid, 256, 0, st>>>(n, sb.nlo, sb.nup, sb.jall, sb.T, q, sb.qcount, cu,
+                                             clo, cup, cj, cth);
     note_launch();
     RKR_CUDA(cudaGetLastError());
     uint32_t cnt = 0;
-    RKR_CUDA(cudaMemcpyAsync(&cnt, qcount + q, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaMemcpyAsync(&cnt, sb.qcount + q, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     RKR_CUDA(cudaStreamSynchronize(st));
     offs_host[q + 1] = offs_host[q] + cnt;
     if (offs_host[q + 1] <= capacity && cnt > 0) {
       k_candidate_out<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, 4 * sm_count()), 256, 0,
-                        st>>>(qcount, q, cu, clo, cup, cj, idx->U, qrow, d, idx->fmin,
+                        st>>>(sb.qcount, q, cu, clo, cup, cj, idx->U, qrow, d, idx->fmin,
                               idx->delta, idx->tau, (uint32_t)idx->s, user_offset, offs_host[q],
                               users_d, nlo_d, nup_d, est_d);
       note_launch();
@@ -318,92 +379,44 @@ rkr_status run_query_approx_single(const rkr_index *idx, const QueryCommon &qc, 
                                    double *est_d, int32_t *case_d, int32_t *nc_d,
                                    rkr_query_stats *stats, cudaStream_t st) {
   const int64_t n = idx->n;
-  const int d = idx->d;
-  const uint32_t top = (uint32_t)(idx->m * idx->s);
-  int shift = 0;
-  while ((top >> shift) >= (uint32_t)kLatBins) ++shift;
-  DevBuf b1, b2, b3, b4, b5, b6, b7, b8, b9, b10, b11, b12;
-  uint32_t *nlo, *nup, *ghist, *T, *qcount, *clo, *cup;
-  int32_t *jall, *cu, *cj;
+  DevBuf bs[8], b7, b8, b9, b10, b11;
+  ScanBufs sb;
+  RKR_TRY(alloc_scan(idx, nq, tuning().latency_ctas_per_sm, bs, sb, st));
+  uint32_t *clo, *cup;
+  int32_t *cu, *cj;
   double *cth;
-  unsigned long long *nfp64;
-  int *err;
-  RKR_TRY(tmp_alloc(b1, &nlo, n, st));
-  RKR_TRY(tmp_alloc(b2, &nup, n, st));
-  RKR_TRY(tmp_alloc(b3, &jall, n, st));
-  RKR_TRY(tmp_alloc(b4, &ghist, kLatBins, st));
-  RKR_TRY(tmp_alloc(b5, &T, 1, st));
-  RKR_TRY(tmp_alloc(b6, &qcount, nq, st));
   RKR_TRY(tmp_alloc(b7, &cu, n, st));
   RKR_TRY(tmp_alloc(b8, &clo, n, st));
   RKR_TRY(tmp_alloc(b9, &cup, n, st));
   RKR_TRY(tmp_alloc(b10, &cj, n, st));
   RKR_TRY(tmp_alloc(b11, &cth, n, st));
-  RKR_TRY(tmp_alloc(b12, &nfp64, 2, st));
-  err = (int *)(nfp64 + 1);
-  RKR_CUDA(cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * kLatBins, st));
-  RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(uint32_t) * nq, st));
-  RKR_CUDA(cudaMemsetAsync(nfp64, 0, 2 * sizeof(unsigned long long), st));
-  const bool vec4 = (d % 4) == 0 && ((uintptr_t)idx->U % 16) == 0;
-  int blocks_per_sm = 0;
-  if (vec4)
-    RKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_latency_scan<4>,
-                                                           kLatThreads, 0));
-  else
-    RKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_latency_scan<1>,
-                                                           kLatThreads, 0));
-  const int64_t warps_needed = (n + 31) / 32;
-  const int tuned = tuning().latency_ctas_per_sm;
-  if (tuned > 0) blocks_per_sm = std::min(std::max(blocks_per_sm, 1), tuned);
-  const int grid = (int)std::max<int64_t>(
-      1, std::min<int64_t>((int64_t)sm_count() * std::max(blocks_per_sm, 1),
-                           (warps_needed + kLatThreads / 32 - 1) / (kLatThreads / 32)));
+  int *err = (int *)(sb.nfp64 + 1);
   const int cgrid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
   Timer t1(st);
-  double ms_scan = 0.0, ms_sel = 0.0;
   for (int q = 0; q < nq; ++q) {
-    const float *qrow = qc.Qd + (int64_t)q * d;
-    {
-      ProfScope prof("k_latency_scan", st,
-                     (double)n * (4.0 * d + 4 + sizeof(BinFP) + 8 + 8 + 12));
-      if (vec4)
-        k_latency_scan<4><<<grid, kLatThreads, 0, st>>>(
-            idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
-            idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
-      else
-        k_latency_scan<1><<<grid, kLatThreads, 0, st>>>(
-            idx->U, n, d, qrow, qc.qnrm + q, idx->unrm, qc.bf, idx->fmin, idx->delta, idx->N,
-            idx->tau, top, shift, nlo, nup, jall, ghist, nfp64);
-      note_launch();
-    }
-    {
-      const int prof_slot = prof_begin("k_latency_cut", st);
-      k_latency_cut<<<1, 1024, 0, st>>>(ghist, qc.kq_d, q, shift, T, qcount);
-      prof_end(prof_slot, st, 0.0);
-      note_launch();
-    }
+    RKR_TRY(scan_pass(idx, qc, q, sb, st));
     {
       const int prof_slot = prof_begin("k_latency_compact", st);
-      k_latency_compact<<<cgrid, 256, 0, st>>>(n, nlo, nup, jall, T, q, qcount, cu, clo, cup, cj,
-                                               cth);
+      k_latency_compact<<<cgrid, 256, 0, st>>>(n, sb.nlo, sb.nup, sb.jall, sb.T, q, sb.qcount, cu,
+                                               clo, cup, cj, cth);
       prof_end(prof_slot, st, 0.0);
       note_launch();
     }
-    RKR_TRY(launch_select_approx(q, 1, qc.out_off_d, qcount, cu, clo, cup, cth, cj, qc.Qd,
+    RKR_TRY(launch_select_approx(q, 1, qc.out_off_d, sb.qcount, cu, clo, cup, cth, cj, qc.Qd,
                                  qc.kq_d, c, qc.out_off_d, users_d, nlo_d, nup_d, est_d, case_d,
                                  nc_d, err, st, idx));
   }
   RKR_CUDA(cudaGetLastError());
-  ms_scan = t1.stop();
+  const double ms = t1.stop();
   unsigned long long h[2] = {0, 0};
-  RKR_CUDA(cudaMemcpyAsync(h, nfp64, sizeof(h), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaMemcpyAsync(h, sb.nfp64, sizeof(h), cudaMemcpyDeviceToHost, st));
   RKR_CUDA(cudaStreamSynchronize(st));
   if ((int)h[1]) return fail(RKR_EINTERNAL, "fewer than k candidates for a query");
   if (stats) {
     stats->pairs = n * (int64_t)nq;
+    stats->candidates = 0;
     stats->fp64_dots = (int64_t)h[0];
-    stats->ms_theta = ms_scan;
-    stats->ms_select = ms_sel;
+    stats->ms_theta = ms;
   }
   return RKR_OK;
 }
