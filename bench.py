@@ -14,7 +14,7 @@ copies included.  ``cpu_baseline`` times the FP64
 oracle on a bounded sample of users and queries and scales it to the workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                      [--case full|small|learned|latency|sweep]
+                      [--case full|small|learned|latency|sweep|uneven]
 """
 
 from __future__ import annotations
@@ -47,7 +47,11 @@ C = 2.0
 # reads the same item side per row block, so its traffic scales with its rows;
 # the bench multiplies this figure by the rows of the timed launches.  Empty
 # until a capture of the current kernel exists (traffic is then reported null).
-TRAFFIC_PER_ROW = {}
+TRAFFIC_PER_ROW = {
+    # k_screen_pair<EpiXT>, 40,000 rows: 348.7 + 2,205.4 MB and 351.2 + 2,202.4 MB in two
+    # launches; the tail-list writes (about 55 KB per user) dominate and scale with rows
+    "k_screen<EpiXT>": 63_850.0,
+}
 
 # Products the tensor cores issue per pair of each screen, relative to the
 # method's one inner product of length d: the split screens issue three
@@ -269,10 +273,15 @@ def bench_ours(args):
     nq = w.Q.shape[0]
     qid = np.repeat(np.arange(nq, dtype=np.int32), np.diff(a_h["offsets"]))
     r_c = idx.rank_pairs(w.Q, a_h["users"], qid)
-    idx.close()
     quality = approx_quality(r_c, a_h["offsets"], e_h[1], C)
     quality["case_b_queries"] = int(np.sum(a_h["case"] == 2))
     precision = screen_precision(rkr, U, P)
+    learned = None
+    if os.environ.get("RKR_BENCH_LEARNED", "1") != "0":
+        # the learned cut against the plain exact batch on the same index
+        # (outside the timed region)
+        learned = learned_comparison(rkr, w, U, P, Q, pos, 2, idx=idx)
+    idx.close()
 
     if rank != 0:
         return
@@ -318,6 +327,7 @@ def bench_ours(args):
                        "wide_queries": [qa0["wide_queries"], qe0["wide_queries"]],
                        "deep_queries": [qa0["deep_queries"], qe0["deep_queries"]]},
         "approx_quality": quality,
+        "learned_cut": learned,
         "precision": {
             "screen_sample": precision,
             "exact_path": {
@@ -344,23 +354,19 @@ def bench_ours(args):
     print(json.dumps(out))
 
 
-def bench_learned(args):
+def learned_comparison(rkr, w, U, P, Q, pos, steps, idx=None):
     """The learned cut on the 1M x 100k x 200 workload: a monotone rank regressor
     (65 -> 256 -> 256 -> 1) trained on the GPU on 10M exact (query, user, rank)
     samples that the GPU path itself produces for 1,000 training queries (each
     query's 2,000 best users plus 8,000 random ones), the keep factor calibrated
-    on 200 held-out queries for recall >= 0.99, then the 10,000 bench queries
-    answered with and without the cut.  All training and calibration queries are
-    items of P disjoint from the bench queries."""
+    on 200 held-out queries (the smallest on a grid whose cut needs no more than
+    1 % of its candidates revived), then the 10,000 bench queries answered with
+    and without the cut.  With its exact fallback the cut returns the exact
+    answer; the comparison reports time, candidates and revived candidates.
+    All training and calibration queries are items of P disjoint from the bench
+    queries."""
     import torch
-    import paper_2504_13446_gb300 as rkr
 
-    dist, rank, ws = _dist()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    w, pos = make_inputs("full")
-    U = torch.from_numpy(w.U).cuda()
-    P = torch.from_numpy(w.P).cuda()
-    Q = torch.from_numpy(w.Q).cuda()
     k = w.k.astype(np.int32)
     stream = torch.cuda.current_stream()
 
@@ -373,15 +379,17 @@ def bench_learned(args):
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1)
 
-    idx, ms_build = timed(lambda: rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s,
-                                            fbounds="exact", exact_table=True, sample_pos=pos))
+    own = idx is None
+    ms_build = None
+    if own:
+        idx, ms_build = timed(lambda: rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s,
+                                                fbounds="exact", exact_table=True,
+                                                sample_pos=pos))
     rng = np.random.default_rng(7)
     Rp = (rng.standard_normal((64, w.d)) / math.sqrt(w.d)).astype(np.float32)
     n_train, n_cal, top, rand = 1000, 200, 2000, 8000
     Qx, _, kx = synth.disjoint_queries(w, n_train + n_cal, seed=8)
     Qtr, Qcal, kcal = Qx[:n_train], Qx[n_train:], kx[n_train:]
-
-    # training samples: exact ranks from the GPU path
     (tu, tr, toff, _), ms_top = timed(lambda: idx.query_exact(Qtr, top))
     ru = rng.integers(0, w.n, size=n_train * rand).astype(np.int32)
     rq = np.repeat(np.arange(n_train, dtype=np.int32), rand)
@@ -395,144 +403,164 @@ def bench_learned(args):
     loss, ms_train = timed(lambda: net.train(X, t, target, epochs=epochs, batch=4096, lr=1e-3,
                                              seed=3))
     del X, t
-
-    # keep factor: the smallest alpha on the grid with recall >= 0.99 on held-out queries
-    def recall_of(users, ranks, off, plain_r):
-        hits = viol = 0
-        for q in range(len(off) - 1):
-            sl = slice(off[q], off[q + 1])
-            kth = plain_r[sl].max()
-            hits += int(np.sum(ranks[sl] <= kth))
-            viol += int(np.sum(ranks[sl] > C * kth))
-        return hits / float(off[-1]), viol
-
-    _, cal_r, _, _ = idx.query_exact(Qcal, kcal)
-    grid = [1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0, 16.0]
+    # keep factor: the smallest alpha on the grid whose cut revives at most 1 % of
+    # its remaining candidates on the held-out queries
+    grid = [1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0]
     cal = {}
     alpha = grid[-1]
     for a in grid:
         keep = np.ceil(a * kcal).astype(np.int32)
-        lu, lr, loff, _ = idx.query_exact_learned(net, Rp, Qcal, kcal, keep)
-        cal[a] = recall_of(lu, lr, loff, cal_r)[0]
-        if cal[a] >= 0.99:
+        _, _, _, cst = idx.query_exact_learned(net, Rp, Qcal, kcal, keep)
+        cal[a] = cst.learned_revived / max(cst.candidates, 1)
+        if cal[a] <= 0.01:
             alpha = a
             break
-
-    # the bench queries, plain and cut
     keep = np.ceil(alpha * k).astype(np.int32)
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(2):
         idx.query_exact(Q, k)
         idx.query_exact_learned(net, Rp, Q, k, keep)
     ms_plain, ms_cut = [], []
-    rkr.rkr_profile_start()
-    for _ in range(args.steps):
+    for _ in range(steps):
         (pu_, pr_, poff, pst), t_plain = timed(lambda: idx.query_exact(Q, k))
         ms_plain.append(t_plain)
-    kernels_plain = rkr.rkr_profile_stop()
-    top_p = sorted(kernels_plain.items(), key=lambda kv: -kv[1][1])[:12]
-    rkr.rkr_profile_start()
-    for _ in range(args.steps):
         (lu, lr, loff, lst), t_cut = timed(lambda: idx.query_exact_learned(net, Rp, Q, k, keep))
         ms_cut.append(t_cut)
-    kernels = rkr.rkr_profile_stop()
-    recall, viol = recall_of(lu, lr, loff, pr_)
-    idx.close()
-    if rank != 0:
-        return
-    nq = w.Q.shape[0]
+    same = bool((lu == pu_).all() and (lr == pr_).all())
+    hits = viol = 0
+    for q in range(len(loff) - 1):
+        sl = slice(loff[q], loff[q + 1])
+        kth = pr_[sl].max()
+        hits += int(np.sum(lr[sl] <= kth))
+        viol += int(np.sum(lr[sl] > C * kth))
+    if own:
+        idx.close()
     mp, mc = statistics.median(ms_plain), statistics.median(ms_cut)
-    top_k = sorted(kernels.items(), key=lambda kv: -kv[1][1])[:12]
+    return {
+        "ms_per_batch": {"learned": mc, "plain_exact": mp},
+        "speedup": mp / mc,
+        "answers_equal_plain_exact": same,
+        "recall_at_k": hits / float(loff[-1]), "c_bound_violations": viol,
+        "keep": f"ceil({alpha} * k) per query",
+        "candidates": {"plain": pst.candidates, "learned": lst.candidates,
+                       "revived_by_fallback": lst.learned_revived,
+                       "recounted_plain": pst.recounted, "recounted_learned": lst.recounted},
+        "calibration_revived_fraction": {str(a): r for a, r in cal.items()},
+        "training": {"queries": n_train, "samples": int(len(pu)), "epochs": epochs,
+                     "batch": 4096, "final_loss": loss,
+                     "ms": {"index_build": ms_build, "top_users": ms_top,
+                            "rank_pairs": ms_pairs, "features": ms_feat, "train": ms_train}},
+    }
+
+
+def bench_learned(args):
+    """The learned case on its own JSON line (see learned_comparison)."""
+    import torch
+    import paper_2504_13446_gb300 as rkr
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w, pos = make_inputs("full")
+    U = torch.from_numpy(w.U).cuda()
+    P = torch.from_numpy(w.P).cuda()
+    Q = torch.from_numpy(w.Q).cuda()
+    rkr.rkr_profile_start()
+    res = learned_comparison(rkr, w, U, P, Q, pos, args.steps)
+    kernels = rkr.rkr_profile_stop()
+    nq = w.Q.shape[0]
+    top_k = sorted(((kk, v) for kk, v in kernels.items() if not kk.startswith("span:")),
+                   key=lambda kv: -kv[1][1])[:12]
     print(json.dumps({
         "case": "learned",
-        "metric": "queries/s", "value": nq / (mc / 1000.0), "unit": "queries/s",
-        "plain_exact_value": nq / (mp / 1000.0),
-        "ms_per_batch": {"learned": mc, "plain_exact": mp},
+        "metric": "queries/s", "value": nq / (res["ms_per_batch"]["learned"] / 1000.0),
+        "unit": "queries/s",
+        "plain_exact_value": nq / (res["ms_per_batch"]["plain_exact"] / 1000.0),
         "steps": args.steps, "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "exact reverse k-ranks with and without the learned cut: "
                                "|U|=1,000,000 |P|=100,000 d=200 mixture, 10,000 queries from P, "
-                               "k in {10,50,100}; regressor 65->256->256->1",
-                   "keep": f"ceil({alpha} * k) per query"},
-        "recall_at_k": recall, "c_bound_violations": viol, "c": C,
-        "candidates": {"plain": pst.candidates, "learned": lst.candidates,
-                       "recounted_plain": pst.recounted, "recounted_learned": lst.recounted},
-        "calibration_recall": {str(a): r for a, r in cal.items()},
-        "training": {"queries": n_train, "samples": int(len(pu)), "epochs": epochs,
-                     "batch": 4096, "final_loss": loss,
-                     "ms": {"index_build": ms_build, "top_users": ms_top, "rank_pairs": ms_pairs,
-                            "features": ms_feat, "train": ms_train}},
-        "learned_kernels_ms_per_batch": {kk: round(v[1] / args.steps, 3) for kk, v in top_k},
-        "plain_kernels_ms_per_batch": {kk: round(v[1] / args.steps, 3) for kk, v in top_p},
-    }))
+                               "k in {10,50,100}; regressor 65->256->256->1"},
+        **res,
+        "kernels_ms_total": {kk: round(v[1], 3) for kk, v in top_k}}))
 
 
-def bench_latency(args):
-    """Queries one at a time (rkr_query_approx_single) on the 1M x 100k x 200
-    index: the paper's per-query protocol (1,000 random items of P as queries,
-    each answered on its own).  Reports ms per query and the HBM bandwidth of the
-    scan kernel (its algorithmic bytes: U once, per-user bin data, two table
-    cells and the bound arrays it writes) against the measured copy bandwidth."""
+def bench_uneven(args):
+    """The uneven batch at full size: |U| = 2M, |P| = 1M, d = 128 (mixture of 1,024
+    centres), 4,096 queries with k log-uniform in [1, 1000] and a user subset per
+    query (10-100 % of U in blocks of 1,024 users, passed as bitmaps).  The index
+    (tau 500, omega 10, s 100, exact tables with floor rank 2,048) is built once,
+    timed apart; a step is the exact batch and the c-approximate batch (c = 2) of
+    all 4,096 queries.  User-item scores/s counts |subset| * m per query."""
     import torch
     import paper_2504_13446_gb300 as rkr
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     peaks, peak_src = _load_peaks()
-    n_users = int(os.environ.get("RKR_LATENCY_USERS", "0"))   # profiling: fewer users
-    if n_users:
-        w = synth.make_workload(WORKLOAD, n=n_users)
-        sizes = np.array([w.m // w.omega + (1 if l < w.m % w.omega else 0)
-                          for l in range(w.omega)])
-        pos = synth.sample_positions(w.seed, sizes, w.s)
-    else:
-        w, pos = make_inputs("full")
+    t0 = time.perf_counter()
+    w = synth.make_workload("uneven")
+    bm = w.subset_bitmaps()
+    t_gen = time.perf_counter() - t0
     U = torch.from_numpy(w.U).cuda()
     P = torch.from_numpy(w.P).cuda()
-    nq = int(os.environ.get("RKR_LATENCY_QUERIES", "1000"))
-    Q = torch.from_numpy(w.Q[:nq]).cuda()
-    k = torch.from_numpy(w.k[:nq].astype(np.int32)).cuda()
+    Q = torch.from_numpy(w.Q).cuda()
+    k = torch.from_numpy(w.k.astype(np.int32)).cuda()
+    member = torch.from_numpy(bm.view(np.int32)).cuda()
+    sizes = np.array([int(np.unpackbits(r.view(np.uint8)).sum()) for r in bm[:64]])
+    subset_users = float(sum(int(np.minimum(b * 1024 + 1024, w.n).sum() - (b * 1024).sum())
+                             for b in w.subset_blocks))
     stream = torch.cuda.current_stream()
-    idx = rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s, fbounds="exact", exact_table=False,
-                    sample_pos=pos)
-    for _ in range(max(args.warmup, 1)):
-        idx.query_approx(Q[:50], k[:50], C, single=True, device=True)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    idx, ms_build = timed(lambda: rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s,
+                                            fbounds="exact", exact_table=True, floor_rank=2048))
+    for _ in range(max(1, args.warmup)):
+        idx.query_exact(Q, k, member=member, device=True)
+        idx.query_approx(Q, k, C, member=member, device=True)
     rkr.rkr_profile_start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    ms_e, ms_a = [], []
     for _ in range(args.steps):
-        one = idx.query_approx(Q, k, C, single=True, device=True)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+        (eu, er, eoff, est_), t_e = timed(lambda: idx.query_exact(Q, k, member=member,
+                                                                  device=True))
+        a, t_a = timed(lambda: idx.query_approx(Q, k, C, member=member, device=True))
+        ms_e.append(t_e)
+        ms_a.append(t_a)
     prof = rkr.rkr_profile_stop()
-    clocks = sampler.stop()
-    ms_q = ev0.elapsed_time(ev1) / (args.steps * nq)
-    batch = idx.query_approx(Q, k, C, device=True)
-    same = all(bool((one[key] == batch[key]).all()) for key in
-               ("users", "n_low", "n_up", "est", "case", "nc"))
-    st1 = one["stats"]
+    mem = idx.device_bytes()
     idx.close()
-    n_l, t_ms, work = prof["k_latency_scan"]
-    gbs = work / (t_ms / n_l / 1000.0) / n_l / 1e9
+    kernels = {kk: v for kk, v in prof.items() if not kk.startswith("span:")}
+    rows_of = {kk: v[2] / (2.0 * w.m * w.d) for kk, v in kernels.items() if v[2] > 0}
+    name = max(kernels, key=lambda kk: kernels[kk][1])
+    roof = roofline_of(kernels, args.steps, peaks, peak_src, rows_of.get(name))
+    me, ma = statistics.median(ms_e), statistics.median(ms_a)
+    nq = w.Q.shape[0]
     print(json.dumps({
-        "case": "latency (one query at a time)",
-        "metric": "ms/query", "value": ms_q, "unit": "ms/query", "higher_is_better": False,
-        "queries_per_s": 1000.0 / ms_q, "queries": nq, "steps": args.steps,
-        "config": {"workload": "c-approximate reverse k-ranks, one query at a time: "
-                               "|U|=1,000,000 |P|=100,000 d=200 mixture, tau=500, omega=10, "
-                               "s=100, c=2, 1,000 queries from P, k in {10,50,100}"},
-        "equals_batched_answer": same,
-        "canonical_fp64_fraction": st1.fp64_dots / max(st1.pairs, 1),
-        "roofline": {"kernel": "k_latency_scan", "bound": "hbm", "achieved": gbs,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-                     "traffic": None, "ms_per_launch": t_ms / n_l,
-                     "bytes_per_launch": work / n_l,
-                     "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
-        "kernels_ms_per_query": {kk: round(v[1] / (args.steps * nq), 5) for kk, v in prof.items()
-                                 if not kk.startswith("span:")},
-        "clocks": clocks,
-        "paper_context": "the paper's one-thread CPU query time at tau=500 is 57.8-501.9 ms on "
-                         "its datasets (Table 1; i9-10980XE)"}))
+        "case": "uneven (config 4)",
+        "metric": "queries/s", "unit": "queries/s",
+        "value": 2 * nq / ((me + ma) / 1000.0),
+        "exact_queries_per_s": nq / (me / 1000.0), "approx_queries_per_s": nq / (ma / 1000.0),
+        "user_item_scores_per_s": {"exact": subset_users * w.m / (me / 1000.0),
+                                   "approx": subset_users * w.m / (ma / 1000.0)},
+        "ms_per_batch": {"exact": me, "approx": ma, "index_build": ms_build},
+        "steps": args.steps, "higher_is_better": True, "data": "synthetic",
+        "dtype": "bf16+f32+f64",
+        "config": {"workload": "|U|=2,000,000 |P|=1,000,000 d=128 mixture (1,024 centres), "
+                               "4,096 queries, k log-uniform in [1,1000], per-query subsets of "
+                               "10-100% of U in 1,024-user blocks (bitmaps), tau=500, omega=10, "
+                               "s=100, exact tables with floor rank 2,048, c=2",
+                   "subset_users_total": subset_users, "k_max": int(w.k.max()),
+                   "k_mean": float(w.k.mean()), "first_subset_sizes": sizes[:4].tolist()},
+        "index_device_gb": mem / 1e9,
+        "stats_exact": est_.as_dict(),
+        "roofline": roof,
+        "kernels_ms_per_step": {kk: round(v[1] / args.steps, 3) for kk, v in
+                                sorted(kernels.items(), key=lambda kv: -kv[1][1])[:14]},
+        "generation_s": t_gen,
+        "screen": "BF16 single and split products; the E4M3 screen is not on this path"}))
 
 
 SWEEP = [(100, 10, 100), (500, 10, 100), (1000, 10, 100),     # tau at omega 10, s 100
@@ -723,7 +751,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="full",
-                    choices=["full", "small", "learned", "latency", "sweep"],
+                    choices=["full", "small", "learned", "latency", "sweep", "uneven"],
                     help="small: a 40k-user profiling case (no CPU baseline, no e2e); "
                          "learned: train the rank regressor and compare the learned cut "
                          "with the plain exact query")
@@ -741,6 +769,8 @@ def main():
         bench_latency(args)
     elif args.case == "sweep":
         bench_sweep(args)
+    elif args.case == "uneven":
+        bench_uneven(args)
     else:
         bench_ours(args)
 

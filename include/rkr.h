@@ -162,6 +162,24 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
                             rkr_query_stats *stats, void *stream);
 
 /*
+ * rkr_query_exact_bitmap / rkr_query_approx_bitmap: the subset forms with each
+ * query's users given as a bitmap instead of an id list (compact for large
+ * subsets: n / 8 bytes per query).  member: nq x words uint32 (host or device),
+ * words = (n + 31) / 32 exactly, bit u % 32 of word q * words + u / 32 set iff
+ * user u is in query q's subset; bits at or beyond n must be clear.  k[i] must
+ * not exceed the number of set bits of query i.  Results as for the _subsets
+ * forms.  RKR_EINVAL for a wrong word count, stray bits or too large a k.
+ */
+rkr_status rkr_query_exact_bitmap(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                  const uint32_t *member, int64_t words, int32_t *out_users,
+                                  int32_t *out_ranks, rkr_query_stats *stats, void *stream);
+rkr_status rkr_query_approx_bitmap(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   const uint32_t *member, int64_t words, double c,
+                                   int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
+                                   double *out_est, int32_t *out_case, int32_t *out_nc,
+                                   rkr_query_stats *stats, void *stream);
+
+/*
  * rkr_query_approx_single: rkr_query_approx answered one query at a time (latency
  * mode), as the paper runs its queries (Section 5: each query on its own).  Same
  * arguments and outputs, bit for bit.  Per query: one pass over U computes u.q for

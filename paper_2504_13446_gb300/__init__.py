@@ -103,6 +103,12 @@ def load() -> ctypes.CDLL:
         lib.rkr_query_exact_subsets.restype = I32
         lib.rkr_query_exact_subsets.argtypes = [V, V, I32, V, V, V, V, V,
                                                 ctypes.POINTER(QueryStats), V]
+        lib.rkr_query_exact_bitmap.restype = I32
+        lib.rkr_query_exact_bitmap.argtypes = [V, V, I32, V, V, I64, V, V,
+                                               ctypes.POINTER(QueryStats), V]
+        lib.rkr_query_approx_bitmap.restype = I32
+        lib.rkr_query_approx_bitmap.argtypes = [V, V, I32, V, V, I64, ctypes.c_double, V, V, V,
+                                                V, V, V, ctypes.POINTER(QueryStats), V]
         lib.rkr_query_approx_single.restype = I32
         lib.rkr_query_approx_single.argtypes = [V, V, I32, V, ctypes.c_double, V, V, V, V, V, V,
                                                 ctypes.POINTER(QueryStats), V]
@@ -347,10 +353,22 @@ def _subsets_csr(subsets, nq):
     return off, np.ascontiguousarray(users)
 
 
-def rkr_query_exact(index, Q, k, *, subsets=None, device: bool = False, stream=None):
+def _bitmap_ptr(member):
+    """(pointer, words, keepalive) of an (nq, words) uint32 bitmap (numpy or torch)."""
+    if _is_torch(member):
+        if not member.is_contiguous():
+            raise ValueError("bitmap tensor must be contiguous")
+        return ctypes.c_void_p(member.data_ptr()), int(member.shape[1]), member
+    a = np.ascontiguousarray(member, dtype=np.uint32)
+    return a.ctypes.data_as(ctypes.c_void_p), int(a.shape[1]), a
+
+
+def rkr_query_exact(index, Q, k, *, subsets=None, member=None, device: bool = False,
+                    stream=None):
     """Exact reverse k-ranks: (users, ranks, offsets, stats) with per-query segments.
 
-    subsets: optional list of per-query user-id arrays (rkr_query_exact_subsets)."""
+    subsets: optional list of per-query user-id arrays (rkr_query_exact_subsets).
+    member: optional (nq, (n + 31) // 32) uint32 subset bitmaps (rkr_query_exact_bitmap)."""
     lib = load()
     nq, _ = _shape(Q)
     kk = np.broadcast_to(np.asarray(k if not _is_torch(k) else k.cpu().numpy(), np.int32), (nq,))
@@ -362,7 +380,11 @@ def rkr_query_exact(index, Q, k, *, subsets=None, device: bool = False, stream=N
     pu, _ = _ptr(users, np.int32)
     pr, _ = _ptr(ranks, np.int32)
     stats = QueryStats()
-    if subsets is None:
+    if member is not None:
+        pm, words, km = _bitmap_ptr(member)
+        _check(lib.rkr_query_exact_bitmap(index, pq, nq, pk, pm, words, pu, pr,
+                                          ctypes.byref(stats), _stream(stream)))
+    elif subsets is None:
         _check(lib.rkr_query_exact(index, pq, nq, pk, pu, pr, ctypes.byref(stats),
                                    _stream(stream)))
     else:
@@ -373,7 +395,7 @@ def rkr_query_exact(index, Q, k, *, subsets=None, device: bool = False, stream=N
 
 
 def rkr_query_approx(index, Q, k, c: float, *, subsets=None, single: bool = False,
-                     device: bool = False, stream=None):
+                     member=None, device: bool = False, stream=None):
     """c-approximate reverse k-ranks (Section 4.3): dict of per-user and per-query outputs.
 
     subsets: optional list of per-query user-id arrays (rkr_query_approx_subsets).
@@ -392,7 +414,11 @@ def rkr_query_approx(index, Q, k, c: float, *, subsets=None, single: bool = Fals
             (("users", np.int32), ("n_low", np.uint32), ("n_up", np.uint32),
              ("est", np.float64), ("case", np.int32), ("nc", np.int32))]
     stats = QueryStats()
-    if single:
+    if member is not None:
+        pm, words, km = _bitmap_ptr(member)
+        _check(lib.rkr_query_approx_bitmap(index, pq, nq, pk, pm, words, ctypes.c_double(c),
+                                           *ptrs, ctypes.byref(stats), _stream(stream)))
+    elif single:
         if subsets is not None:
             raise ValueError("the one-at-a-time mode takes no subsets")
         _check(lib.rkr_query_approx_single(index, pq, nq, pk, ctypes.c_double(c), *ptrs,

@@ -359,6 +359,25 @@ __global__ void k_subset_bitmap(const int64_t *__restrict__ soff,
   }
 }
 
+// Per query: the number of member users and whether a bit at or beyond n is set.
+__global__ void k_bitmap_count(const uint32_t *__restrict__ member, int64_t words, int64_t n,
+                               unsigned long long *__restrict__ cnt, int *__restrict__ bad) {
+  const int64_t q = blockIdx.x;
+  const uint32_t *row = member + q * words;
+  const uint32_t tail = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xffffffffu;
+  unsigned long long c = 0;
+  for (int64_t w = threadIdx.x; w < words; w += blockDim.x) {
+    uint32_t v = row[w];
+    if (w == words - 1) {
+      if (v & ~tail) atomicExch(bad, 1);
+      v &= tail;
+    }
+    c += (unsigned long long)__popc(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt[q], c);
+}
+
 static rkr_status query_prologue(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
                                  cudaStream_t st, std::vector<int32_t> &kh,
                                  std::vector<int64_t> &off) {
@@ -444,6 +463,36 @@ static rkr_status stage_subsets(rkr_index *idx, int32_t nq, const std::vector<in
   return RKR_OK;
 }
 
+// Per-query subsets given directly as bitmaps (nq x words uint32, bit u of query q
+// at word q * words + u / 32); host or device memory.
+static rkr_status stage_bitmaps(rkr_index *idx, int32_t nq, const std::vector<int32_t> &kh,
+                                const uint32_t *member, int64_t words, cudaStream_t st,
+                                QueryStage &qs, QueryCommon &qc) {
+  if (!member) return fail(RKR_EINVAL, "null subset bitmap");
+  if (words != (idx->n + 31) / 32)
+    return fail(RKR_EINVAL, "bitmap rows must have (n + 31) / 32 = %lld words",
+                (long long)((idx->n + 31) / 32));
+  RKR_TRY(qs.vsu.init(member, sizeof(uint32_t) * (size_t)words * nq, st));
+  RKR_CUDA(pool_malloc_async(&qs.soff, sizeof(int64_t) * (nq + 1), st));
+  unsigned long long *cnt = (unsigned long long *)qs.soff;
+  int *bad = (int *)(qs.soff + nq);
+  RKR_CUDA(cudaMemsetAsync(qs.soff, 0, sizeof(int64_t) * (nq + 1), st));
+  k_bitmap_count<<<nq, 256, 0, st>>>((const uint32_t *)qs.vsu.dev, words, idx->n, cnt, bad);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  std::vector<unsigned long long> hc(nq + 1);
+  RKR_CUDA(cudaMemcpyAsync(hc.data(), qs.soff, sizeof(int64_t) * (nq + 1),
+                           cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if ((int)hc[nq]) return fail(RKR_EINVAL, "subset bitmaps set bits at or beyond n");
+  for (int q = 0; q < nq; ++q)
+    if ((unsigned long long)kh[q] > hc[q])
+      return fail(RKR_EINVAL, "k[%d] = %d exceeds the subset size %llu", q, kh[q], hc[q]);
+  qc.member = (const uint32_t *)qs.vsu.dev;
+  qc.mwords = words;
+  return RKR_OK;
+}
+
 static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const int32_t *k,
                                 const std::vector<int64_t> &off, cudaStream_t st,
                                 QueryStage &qs, QueryCommon &qc) {
@@ -485,7 +534,8 @@ static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const in
 static rkr_status query_exact_impl(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
                                    const int64_t *subset_offs, const int32_t *subset_users,
                                    bool subsets, int32_t *out_users, int32_t *out_ranks,
-                                   rkr_query_stats *stats, void *stream) {
+                                   rkr_query_stats *stats, void *stream,
+                                   const uint32_t *member = nullptr, int64_t words = -1) {
   g_err[0] = 0;
   if (!out_users || !out_ranks) return fail(RKR_EINVAL, "null output");
   cudaStream_t st = (cudaStream_t)stream;
@@ -496,6 +546,7 @@ static rkr_status query_exact_impl(rkr_index *idx, const float *Q, int32_t nq, c
   QueryStage qs;
   QueryCommon qc;
   if (subsets) RKR_TRY(stage_subsets(idx, nq, kh, subset_offs, subset_users, st, qs, qc));
+  if (words >= 0) RKR_TRY(stage_bitmaps(idx, nq, kh, member, words, st, qs, qc));
   RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
   OutView ou, orr;
   size_t tot = (size_t)off[nq];
@@ -513,7 +564,8 @@ static rkr_status query_approx_impl(rkr_index *idx, const float *Q, int32_t nq,
                                     const int32_t *subset_users, bool subsets, double c,
                                     int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
                                     double *out_est, int32_t *out_case, int32_t *out_nc,
-                                    rkr_query_stats *stats, void *stream, bool single = false) {
+                                    rkr_query_stats *stats, void *stream, bool single = false,
+                                    const uint32_t *member = nullptr, int64_t words = -1) {
   g_err[0] = 0;
   if (!out_users) return fail(RKR_EINVAL, "null output");
   if (!(c >= 1.0) || !isfinite(c)) return fail(RKR_EINVAL, "c must be a finite value >= 1");
@@ -524,6 +576,7 @@ static rkr_status query_approx_impl(rkr_index *idx, const float *Q, int32_t nq,
   QueryStage qs;
   QueryCommon qc;
   if (subsets) RKR_TRY(stage_subsets(idx, nq, kh, subset_offs, subset_users, st, qs, qc));
+  if (words >= 0) RKR_TRY(stage_bitmaps(idx, nq, kh, member, words, st, qs, qc));
   RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
   size_t tot = (size_t)off[nq];
   OutView ou, olo, oup, oes, oca, onc;
@@ -572,6 +625,23 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
                             rkr_query_stats *stats, void *stream) {
   return query_approx_impl(idx, Q, nq, k, nullptr, nullptr, false, c, out_users, out_nlow,
                            out_nup, out_est, out_case, out_nc, stats, stream);
+}
+
+rkr_status rkr_query_exact_bitmap(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                  const uint32_t *member, int64_t words, int32_t *out_users,
+                                  int32_t *out_ranks, rkr_query_stats *stats, void *stream) {
+  return query_exact_impl(idx, Q, nq, k, nullptr, nullptr, false, out_users, out_ranks, stats,
+                          stream, member, words < 0 ? 0 : words);
+}
+
+rkr_status rkr_query_approx_bitmap(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,
+                                   const uint32_t *member, int64_t words, double c,
+                                   int32_t *out_users, uint32_t *out_nlow, uint32_t *out_nup,
+                                   double *out_est, int32_t *out_case, int32_t *out_nc,
+                                   rkr_query_stats *stats, void *stream) {
+  return query_approx_impl(idx, Q, nq, k, nullptr, nullptr, false, c, out_users, out_nlow,
+                           out_nup, out_est, out_case, out_nc, stats, stream, false, member,
+                           words < 0 ? 0 : words);
 }
 
 rkr_status rkr_query_approx_single(rkr_index *idx, const float *Q, int32_t nq, const int32_t *k,

@@ -27,7 +27,7 @@
 #include "index.cuh"
 
 namespace rkr {
-namespace {
+namespace lat {
 
 constexpr int kLatThreads = 256;
 constexpr int kLatRows = 8;      // rows per warp and sub-batch
@@ -324,7 +324,9 @@ rkr_status scan_pass(const rkr_index *idx, const QueryCommon &qc, int q, const S
   return RKR_OK;
 }
 
-}  // namespace
+}  // namespace lat
+
+using namespace lat;
 
 // Per query, the users of this index whose lower bound is at most an upper
 // estimate T of this index's R_up_k, with their bounds and step-3 estimates.

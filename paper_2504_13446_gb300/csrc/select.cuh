@@ -9,44 +9,16 @@ namespace rkr {
 // (fn returns false for elements that do not take part).  MSB-first radix
 // select on 8-bit digits over an nbits-wide key.  Every thread of the block must
 // call it with the same arguments; the k-th smallest must exist.
-//
-// For large counts the digits above the highest set bit of any key are skipped
-// (they are zero for every key), and lanes of a warp that fall in the same
-// digit add to the histogram with one atomic: keys crowd into a few digits
-// (ranks and counts far below 2^32), and per-key atomics would serialize.
 template <class F>
 __device__ uint64_t block_kth(int64_t cnt, uint64_t k, int nbits, F fn, uint32_t *hist,
                               uint64_t *bc) {
   uint64_t prefix = 0, mask = 0;
-  int top = nbits - 8;
-  if (cnt >= 4096) {
-    if (threadIdx.x == 0) bc[0] = 0;
-    __syncthreads();
-    uint64_t any = 0;
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-      uint64_t key;
-      if (fn(i, key)) any |= key;
-    }
-    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)any);
-    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(any >> 32));
-    if ((threadIdx.x & 31) == 0 && (lo | hi))
-      atomicOr((unsigned long long *)&bc[0], ((unsigned long long)hi << 32) | lo);
-    __syncthreads();
-    const uint64_t all = bc[0];
-    __syncthreads();
-    const int hb = all ? 63 - __clzll((long long)all) : 0;   // highest set bit
-    top = min(nbits - 8, max(0, hb - hb % 8));
-  }
-  for (int shift = top; shift >= 0; shift -= 8) {
+  for (int shift = nbits - 8; shift >= 0; shift -= 8) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
-      const int64_t i = i0 + threadIdx.x;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
       uint64_t key;
-      const bool in = i < cnt && fn(i, key) && (key & mask) == prefix;
-      const unsigned dg = in ? (unsigned)((key >> shift) & 255u) : 256u;
-      const unsigned peers = __match_any_sync(0xffffffffu, dg);
-      if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[dg], __popc(peers));
+      if (fn(i, key) && (key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

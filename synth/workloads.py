@@ -80,8 +80,42 @@ class Workload:
     omega: int = 10
     s: int = 100
     query_from_P: Optional[np.ndarray] = None   # item index of queries drawn from P, -1 if fresh
-    subsets: Optional[list] = None              # per-query sorted int32 user ids, or None = all users
+    subsets_given: Optional[list] = None        # per-query sorted int32 user ids, or None
     seed: int = 0
+    subset_blocks: Optional[list] = None        # per-query ids of 1,024-user blocks (uneven)
+
+    @property
+    def subsets(self):
+        """Per-query sorted int32 user ids (None = all users); for block subsets the
+        ids are expanded on first use (large: avoid at full size, use bitmaps)."""
+        if self.subsets_given is None and self.subset_blocks is not None:
+            n = self.U.shape[0]
+            out = []
+            for blocks in self.subset_blocks:
+                ids = (blocks[:, None] * 1024 + np.arange(1024)[None, :]).ravel()
+                out.append(ids[ids < n].astype(np.int32))
+            self.subsets_given = out
+        return self.subsets_given
+
+    def subset_bitmaps(self) -> np.ndarray:
+        """(nq, (n + 31) // 32) uint32: bit u of row q set iff user u is in query q's subset."""
+        n = self.U.shape[0]
+        words = (n + 31) // 32
+        nq = self.Q.shape[0]
+        out = np.zeros((nq, words), dtype=np.uint32)
+        if self.subset_blocks is not None:
+            nblk = (n + 1023) // 1024
+            full = np.zeros((nq, nblk, 32), dtype=np.uint32)   # 32 words per 1,024-user block
+            for q, blocks in enumerate(self.subset_blocks):
+                full[q, blocks, :] = 0xFFFFFFFF
+            out = np.ascontiguousarray(full.reshape(nq, nblk * 32)[:, :words])
+            if n % 32:
+                out[:, words - 1] &= np.uint32((1 << (n % 32)) - 1)
+            return out
+        for q in range(nq):
+            ids = np.arange(n) if self.subsets is None else np.asarray(self.subsets[q])
+            np.bitwise_or.at(out[q], ids >> 5, (np.uint32(1) << (ids & 31).astype(np.uint32)))
+        return out
 
     @property
     def n(self):
@@ -159,19 +193,18 @@ def make_workload(name: str, *, n: Optional[int] = None, m: Optional[int] = None
         Q = mixture_rows(rng, centers, nq, 0.3, 0.5)
         k = np.clip(np.rint(np.exp(rng.uniform(0.0, math.log(1000.0), size=nq))), 1, 1000).astype(np.int32)
         nblk = (n + 1023) // 1024
-        subsets = []
+        blocks_q, sizes = [], []
         for _ in range(nq):
             frac = rng.uniform(0.1, 1.0)
             keep = rng.random(nblk) < frac
             if not keep.any():
                 keep[rng.integers(0, nblk)] = True
             blocks = np.nonzero(keep)[0]
-            ids = (blocks[:, None] * 1024 + np.arange(1024)[None, :]).ravel()
-            ids = ids[ids < n].astype(np.int32)
-            subsets.append(ids)
-        k = np.minimum(k, np.array([len(s_) for s_ in subsets], dtype=np.int32))
+            blocks_q.append(blocks)
+            sizes.append(int(np.minimum(blocks * 1024 + 1024, n).sum() - (blocks * 1024).sum()))
+        k = np.minimum(k, np.array(sizes, dtype=np.int32))
         return Workload(name, U, P, Q, k, query_from_P=np.full(nq, -1, dtype=np.int64),
-                        subsets=subsets, seed=seed)
+                        subset_blocks=blocks_q, seed=seed)
     raise ValueError(f"unknown workload {name!r}")
 
 

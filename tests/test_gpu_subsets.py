@@ -59,3 +59,22 @@ def test_subset_validation():
         gpu.query_exact(w.Q, 1, subsets=[np.array([500], np.int32)] * 3)
     users, ranks, off, _ = gpu.query_exact(w.Q, 1, subsets=[np.array([7], np.int32)] * 3)
     assert (users == 7).all()
+
+
+def test_bitmap_subsets_equal_id_subsets():
+    w = synth.make_workload("uneven", n=9001, m=2000, d=64, nq=12)
+    gpu = rkr.Index(w.U, w.P, tau=40, omega=4, s=30, exact_table=True)
+    bm = w.subset_bitmaps()
+    u1, r1, o1, _ = gpu.query_exact(w.Q, w.k, subsets=w.subsets)
+    u2, r2, o2, _ = gpu.query_exact(w.Q, w.k, member=bm)
+    assert (u1 == u2).all() and (r1 == r2).all()
+    a1 = gpu.query_approx(w.Q, w.k, 2.0, subsets=w.subsets)
+    a2 = gpu.query_approx(w.Q, w.k, 2.0, member=bm)
+    for key in ("users", "n_low", "n_up", "est", "case", "nc"):
+        assert (a1[key] == a2[key]).all(), key
+    bad = bm.copy()
+    bad[0, -1] |= np.uint32(1 << 31)          # a bit beyond n
+    with pytest.raises(rkr.RKRError):
+        gpu.query_exact(w.Q, w.k, member=bad)
+    with pytest.raises(rkr.RKRError):         # wrong row width
+        gpu.query_exact(w.Q, w.k, member=bm[:, :-1])

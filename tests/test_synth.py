@@ -24,3 +24,16 @@ def test_workloads_have_the_stated_shapes():
     assert w.U.shape == (1000, 100) and w.P.shape == (300, 100) and w.Q.shape == (10, 100)
     assert (w.query_from_P[:5] >= 0).all() and (w.query_from_P[5:] == -1).all()
     assert w.U.dtype == np.float32 and (w.k == 100).all()
+
+
+def test_uneven_subsets_as_blocks_ids_and_bitmaps_agree():
+    import numpy as np
+    from synth import make_workload
+    w = make_workload("uneven", n=5000, m=300, d=16, nq=6)
+    bm = w.subset_bitmaps()
+    assert bm.shape == (6, (5000 + 31) // 32)
+    for q, ids in enumerate(w.subsets):
+        bits = np.unpackbits(bm[q].view(np.uint8), bitorder="little")[:5000]
+        assert (np.nonzero(bits)[0] == ids).all()
+        assert w.k[q] <= len(ids)
+        assert not np.unpackbits(bm[q].view(np.uint8), bitorder="little")[5000:].any()
