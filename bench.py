@@ -563,6 +563,97 @@ def bench_uneven(args):
         "screen": "BF16 single and split products; the E4M3 screen is not on this path"}))
 
 
+def bench_latency(args):
+    """Queries one at a time (rkr_query_approx_single) on the 1M x 100k x 200
+    index: the paper's per-query protocol (1,000 random items of P as queries,
+    each answered on its own).  Reports ms per query and the HBM bandwidth of the
+    scan kernel (its algorithmic bytes: U once, per-user bin data, two table
+    cells and the bound arrays it writes) against the measured copy bandwidth."""
+    import torch
+    import paper_2504_13446_gb300 as rkr
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    peaks, peak_src = _load_peaks()
+    n_users = int(os.environ.get("RKR_LATENCY_USERS", "0"))   # profiling: fewer users
+    if n_users:
+        w = synth.make_workload(WORKLOAD, n=n_users)
+        sizes = np.array([w.m // w.omega + (1 if l < w.m % w.omega else 0)
+                          for l in range(w.omega)])
+        pos = synth.sample_positions(w.seed, sizes, w.s)
+    else:
+        w, pos = make_inputs("full")
+    U = torch.from_numpy(w.U).cuda()
+    P = torch.from_numpy(w.P).cuda()
+    nq = int(os.environ.get("RKR_LATENCY_QUERIES", "1000"))
+    Q = torch.from_numpy(w.Q[:nq]).cuda()
+    k = torch.from_numpy(w.k[:nq].astype(np.int32)).cuda()
+    stream = torch.cuda.current_stream()
+    idx = rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s, fbounds="exact", exact_table=False,
+                    sample_pos=pos)
+    for _ in range(max(args.warmup, 1)):
+        idx.query_approx(Q[:50], k[:50], C, single=True, device=True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    rkr.rkr_profile_start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one = idx.query_approx(Q, k, C, single=True, device=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = rkr.rkr_profile_stop()
+    clocks = sampler.stop()
+    ms_q = ev0.elapsed_time(ev1) / (args.steps * nq)
+    batch = idx.query_approx(Q, k, C, device=True)
+    same = all(bool((one[key] == batch[key]).all()) for key in
+               ("users", "n_low", "n_up", "est", "case", "nc"))
+    st1 = one["stats"]
+    # end to end per query through a graph-captured session: host query in, host
+    # answer out, copies and synchronization included
+    kh = w.k[:nq].astype(np.int32)
+    bu = batch["users"].cpu().numpy()
+    boff = batch["offsets"]
+    sess = rkr.Session(idx, max_k=int(kh.max()), c=C)
+    for q in range(min(20, nq)):
+        sess.query(w.Q[q], int(kh[q]))
+    lat = []
+    same_sess = True
+    for q in range(nq):
+        t0 = time.perf_counter()
+        got = sess.query(w.Q[q], int(kh[q]))
+        lat.append((time.perf_counter() - t0) * 1000.0)
+        same_sess &= bool((got["users"] == bu[boff[q]:boff[q + 1]]).all())
+    sess.close()
+    idx.close()
+    n_l, t_ms, work = prof["k_latency_scan"]
+    gbs = work / (t_ms / n_l / 1000.0) / n_l / 1e9
+    print(json.dumps({
+        "case": "latency (one query at a time)",
+        "metric": "ms/query", "value": ms_q, "unit": "ms/query", "higher_is_better": False,
+        "queries_per_s": 1000.0 / ms_q, "queries": nq, "steps": args.steps,
+        "config": {"workload": "c-approximate reverse k-ranks, one query at a time: "
+                               "|U|=1,000,000 |P|=100,000 d=200 mixture, tau=500, omega=10, "
+                               "s=100, c=2, 1,000 queries from P, k in {10,50,100}"},
+        "equals_batched_answer": same,
+        "session_e2e_ms": {"mean": float(np.mean(lat)), "p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99)),
+                           "note": "rkr_session_query: host query in, host answer out, one "
+                                   "CUDA graph replay per query",
+                           "equals_batched_answer": same_sess},
+        "canonical_fp64_fraction": st1.fp64_dots / max(st1.pairs, 1),
+        "roofline": {"kernel": "k_latency_scan", "bound": "hbm", "achieved": gbs,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                     "traffic": None, "ms_per_launch": t_ms / n_l,
+                     "bytes_per_launch": work / n_l,
+                     "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "kernels_ms_per_query": {kk: round(v[1] / (args.steps * nq), 5) for kk, v in prof.items()
+                                 if not kk.startswith("span:")},
+        "clocks": clocks,
+        "paper_context": "the paper's one-thread CPU query time at tau=500 is 57.8-501.9 ms on "
+                         "its datasets (Table 1; i9-10980XE)"}))
+
+
 SWEEP = [(100, 10, 100), (500, 10, 100), (1000, 10, 100),     # tau at omega 10, s 100
          (500, 1, 1000), (500, 10, 10), (500, 10, 1000), (500, 100, 100)]
 

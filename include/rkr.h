@@ -162,6 +162,29 @@ rkr_status rkr_query_approx(rkr_index *idx, const float *Q, int32_t nq, const in
                             rkr_query_stats *stats, void *stream);
 
 /*
+ * rkr_session_*: a serving form of rkr_query_approx_single for one query per call
+ * (not in the paper).  rkr_session_create keeps device buffers for one query and
+ * captures the query's launches (query norm, the scan of U fused with the bounds
+ * lookup, the cut, the compaction, steps 2-3) in a CUDA graph on a stream of its
+ * own, for this index, k <= max_k and this c.  rkr_session_query copies q (d
+ * floats, host or device) in, replays the graph and copies the outputs back:
+ * out_users, out_nlow, out_nup, out_est (k entries each), *out_case, *out_nc, as
+ * rkr_query_approx for that query, bit for bit (any output but out_users may be
+ * NULL; host or device).  A query whose norm exceeds the largest item norm (the
+ * captured bin bounds assume it does not) is answered by rkr_query_approx_single
+ * instead, with the same result.  Calls on one session must not overlap; the
+ * index must outlive the session.  RKR_EINVAL for bad arguments (max_k outside
+ * [1, min(n, 4096)], c < 1, k > max_k, non-finite q).
+ */
+typedef struct rkr_session rkr_session;
+rkr_status rkr_session_create(rkr_index *idx, int32_t max_k, double c, void *stream,
+                              rkr_session **out);
+rkr_status rkr_session_query(rkr_session *s, const float *q, int32_t k, int32_t *out_users,
+                             uint32_t *out_nlow, uint32_t *out_nup, double *out_est,
+                             int32_t *out_case, int32_t *out_nc);
+void rkr_session_free(rkr_session *s);
+
+/*
  * rkr_query_exact_bitmap / rkr_query_approx_bitmap: the subset forms with each
  * query's users given as a bitmap instead of an id list (compact for large
  * subsets: n / 8 bytes per query).  member: nq x words uint32 (host or device),
@@ -401,6 +424,8 @@ void rkr_pruner_free(rkr_pruner *pr);
  *                    2^L - 1 >= m / 128); else that level L (1..30)
  *   cand_budget_log2 candidates per screening chunk = 2^value, 20..30 (default 26)
  *   latency_ctas_per_sm  CTAs per SM of the one-at-a-time scan, 0 = occupancy maximum
+ *   latency_bulk     1: the one-at-a-time scan stages rows of U in shared memory with
+ *                    bulk copies (d a multiple of 4); 0: direct vector loads
  * rkr_tuning_set validates every field (RKR_EINVAL) and applies to calls that start
  * after it returns; rkr_tuning_get reads the current values.
  *
@@ -420,6 +445,7 @@ typedef struct {
   int32_t skip_level;
   int32_t cand_budget_log2;
   int32_t latency_ctas_per_sm;
+  int32_t latency_bulk;
 } rkr_tuning;
 rkr_status rkr_tuning_get(rkr_tuning *out);
 rkr_status rkr_tuning_set(const rkr_tuning *in);

@@ -31,7 +31,7 @@ __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_ex
            "rkr_profile_start", "rkr_profile_stop", "Pruner", "rkr_rank_pairs",
            "rkr_pair_features", "rkr_query_exact_learned", "rkr_release_cached_memory",
            "rkr_set_wait_limit", "device_allocations", "version", "EXPORTS", "Tuning",
-           "rkr_tuning_get", "rkr_tuning_set", "rkr_autotune"]
+           "rkr_tuning_get", "rkr_tuning_set", "rkr_autotune", "Session"]
 
 _lock = threading.Lock()
 _lib = None
@@ -72,7 +72,7 @@ class Tuning(ctypes.Structure):
     """Launch choices that change speed, never results (rkr_tuning)."""
     _fields_ = [("rc_bn", ctypes.c_int32), ("rc_single_first", ctypes.c_int32),
                 ("skip_level", ctypes.c_int32), ("cand_budget_log2", ctypes.c_int32),
-                ("latency_ctas_per_sm", ctypes.c_int32)]
+                ("latency_ctas_per_sm", ctypes.c_int32), ("latency_bulk", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -103,6 +103,12 @@ def load() -> ctypes.CDLL:
         lib.rkr_query_exact_subsets.restype = I32
         lib.rkr_query_exact_subsets.argtypes = [V, V, I32, V, V, V, V, V,
                                                 ctypes.POINTER(QueryStats), V]
+        lib.rkr_session_create.restype = I32
+        lib.rkr_session_create.argtypes = [V, I32, ctypes.c_double, V, ctypes.POINTER(V)]
+        lib.rkr_session_query.restype = I32
+        lib.rkr_session_query.argtypes = [V, V, I32, V, V, V, V, V, V]
+        lib.rkr_session_free.restype = None
+        lib.rkr_session_free.argtypes = [V]
         lib.rkr_query_exact_bitmap.restype = I32
         lib.rkr_query_exact_bitmap.argtypes = [V, V, I32, V, V, I64, V, V,
                                                ctypes.POINTER(QueryStats), V]
@@ -675,6 +681,45 @@ class Pruner:
             self.close()
         except Exception:
             pass
+
+
+class Session:
+    """One query per call with a captured CUDA graph (rkr_session_*)."""
+
+    def __init__(self, index: "Index", max_k: int, c: float = 2.0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.rkr_session_create(index._h, int(max_k), ctypes.c_double(c), None,
+                                      ctypes.byref(h)))
+        self._h, self.max_k, self.index = h, int(max_k), index
+
+    def query(self, q, k: int) -> dict:
+        """Answer one query (a d-vector, numpy or CUDA tensor); outputs as numpy arrays."""
+        pq, kq = _ptr(q, np.float32)
+        out = dict(users=np.empty(k, np.int32), n_low=np.empty(k, np.uint32),
+                   n_up=np.empty(k, np.uint32), est=np.empty(k, np.float64),
+                   case=np.empty(1, np.int32), nc=np.empty(1, np.int32))
+        _check(load().rkr_session_query(self._h, pq, int(k),
+                                        *[out[key].ctypes.data for key in
+                                          ("users", "n_low", "n_up", "est", "case", "nc")]))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().rkr_session_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 @dataclass

@@ -78,6 +78,9 @@ static std::vector<ProfRec> g_prof;
 int prof_begin(const char *name, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return -1;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cudaGetLastError();
+  if (cs != cudaStreamCaptureStatusNone) return -1;  // no timing events inside a graph
   ProfRec r{name, nullptr, nullptr, 0.0};
   if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
     cudaGetLastError();

@@ -5,7 +5,7 @@
 // are cached in a JSON-lines file, one object per line:
 //   {"key": "n=...,m=...,d=...,nq=...,ksum=...,what=...", "rc_bn": 256,
 //    "rc_single_first": 1, "skip_level": 0, "cand_budget_log2": 26,
-//    "latency_ctas_per_sm": 0, "ms": 123.4}
+//    "latency_ctas_per_sm": 0, "latency_bulk": 1, "ms": 123.4}
 #include <stdio.h>
 #include <string.h>
 
@@ -19,7 +19,7 @@ namespace rkr {
 namespace {
 
 std::mutex g_tune_mu;
-rkr_tuning g_tune = {256, 1, 0, 26, 0};
+rkr_tuning g_tune = {256, 1, 0, 26, 0, 1};
 
 rkr_status check_tuning(const rkr_tuning &t) {
   if (t.rc_bn != 128 && t.rc_bn != 256) return fail(RKR_EINVAL, "rc_bn must be 128 or 256");
@@ -30,6 +30,7 @@ rkr_status check_tuning(const rkr_tuning &t) {
     return fail(RKR_EINVAL, "cand_budget_log2 in [20, 30]");
   if (t.latency_ctas_per_sm < 0 || t.latency_ctas_per_sm > 32)
     return fail(RKR_EINVAL, "latency_ctas_per_sm in [0, 32]");
+  if (t.latency_bulk != 0 && t.latency_bulk != 1) return fail(RKR_EINVAL, "latency_bulk is 0 or 1");
   return RKR_OK;
 }
 
@@ -58,12 +59,13 @@ bool cache_lookup(const char *path, const std::string &key, rkr_tuning *t, doubl
   const std::string pat = "\"key\": \"" + key + "\"";
   while (fgets(line, sizeof(line), f)) {
     if (!strstr(line, pat.c_str())) continue;
-    double v[6];
+    double v[7];
     if (field(line, "rc_bn", &v[0]) && field(line, "rc_single_first", &v[1]) &&
         field(line, "skip_level", &v[2]) && field(line, "cand_budget_log2", &v[3]) &&
-        field(line, "latency_ctas_per_sm", &v[4]) && field(line, "ms", &v[5])) {
+        field(line, "latency_ctas_per_sm", &v[4]) && field(line, "ms", &v[5]) &&
+        field(line, "latency_bulk", &v[6])) {
       rkr_tuning c = {(int32_t)v[0], (int32_t)v[1], (int32_t)v[2], (int32_t)v[3],
-                      (int32_t)v[4]};
+                      (int32_t)v[4], (int32_t)v[6]};
       if (check_tuning(c) == RKR_OK) {
         *t = c;
         *ms = v[5];
@@ -83,9 +85,10 @@ rkr_status cache_append(const char *path, const std::string &key, const rkr_tuni
   if (!f) return fail(RKR_EINVAL, "cannot append to %s", path);
   fprintf(f,
           "{\"key\": \"%s\", \"rc_bn\": %d, \"rc_single_first\": %d, \"skip_level\": %d, "
-          "\"cand_budget_log2\": %d, \"latency_ctas_per_sm\": %d, \"ms\": %.4f}\n",
+          "\"cand_budget_log2\": %d, \"latency_ctas_per_sm\": %d, \"latency_bulk\": %d, "
+          "\"ms\": %.4f}\n",
           key.c_str(), t.rc_bn, t.rc_single_first, t.skip_level, t.cand_budget_log2,
-          t.latency_ctas_per_sm, ms);
+          t.latency_ctas_per_sm, t.latency_bulk, ms);
   if (fclose(f) != 0) return fail(RKR_EINVAL, "cannot write %s", path);
   return RKR_OK;
 }
@@ -170,13 +173,15 @@ extern "C" rkr_status rkr_autotune(rkr_index *idx, const float *Q, int32_t nq, c
   for (int bn : {256, 128})
     for (int sf : {1, 0})
       for (int sk : {0, ls - 1, ls + 1})
-        for (int lc : {0, 2, 4}) {
-          if (!(what & 1) && (bn != 256 || sf != 1)) continue;
-          if (!(what & 3) && sk != 0) continue;
-          if (!(what & 4) && lc != 0) continue;
-          if (sk < 0 || sk > 30 || (sk != 0 && sk == ls)) continue;
-          grid.push_back({bn, sf, sk, before.cand_budget_log2, lc});
-        }
+        for (int lc : {0, 2, 4})
+          for (int lb : {1, 0}) {
+            if (!(what & 1) && (bn != 256 || sf != 1)) continue;
+            if (!(what & 3) && sk != 0) continue;
+            if (!(what & 4) && (lc != 0 || lb != 1)) continue;
+            if (lb == 1 && lc != 0) continue;   // the bulk scan runs one CTA per SM
+            if (sk < 0 || sk > 30 || (sk != 0 && sk == ls)) continue;
+            grid.push_back({bn, sf, sk, before.cand_budget_log2, lc, lb});
+          }
   const size_t tot = (size_t)ksum;
   int32_t *users = nullptr, *ranks = nullptr, *icase = nullptr, *inc = nullptr;
   uint32_t *nlo = nullptr, *nup = nullptr;

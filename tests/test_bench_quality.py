@@ -43,3 +43,9 @@ def test_exact_answer_scores_perfectly():
     got = bench.approx_quality(ranks_c, off, best, 2.0)
     assert got["accuracy"] == 1.0 and got["overall_ratio"] == 1.0
     assert got["recall_at_k"] == 1.0 and got["c_bound_violations"] == 0
+
+
+def test_every_bench_case_has_its_function():
+    for name in ("bench_ours", "bench_learned", "bench_latency", "bench_sweep", "bench_uneven",
+                 "bench_reference", "learned_comparison", "cpu_baseline", "screen_precision"):
+        assert callable(getattr(bench, name, None)), name

@@ -52,3 +52,30 @@ def test_single_edge_cases():
     _run(w, 20, 3, 25, 1.0, 300)            # k = n, c = 1
     w.Q[1] *= np.float32(50.0)              # far outside the item norms
     _run(w, 20, 3, 25, 2.0, np.array([1, 7, 300, 30], np.int32))
+
+
+def test_session_graph_answers_equal_the_batch():
+    w = synth.make_workload("approx", n=5000, m=1500, d=48, nq=10)
+    pos = synth.sample_positions(3, oracle.bucket_sizes(w.m, 4), 40)
+    w.Q[7] *= np.float32(40.0)          # beyond the item norms: answered without the graph
+    with rkr.Index(w.U, w.P, tau=50, omega=4, s=40, sample_pos=pos, exact_table=False) as idx:
+        batch = idx.query_approx(w.Q, w.k, 2.0)
+        with rkr.Session(idx, max_k=int(w.k.max()), c=2.0) as sess:
+            for rep in range(2):       # the graph is replayed: nothing carries over
+                for q in range(w.Q.shape[0]):
+                    got = sess.query(w.Q[q], int(w.k[q]))
+                    sl = slice(batch["offsets"][q], batch["offsets"][q + 1])
+                    for key in ("users", "n_low", "n_up", "est"):
+                        assert (got[key] == batch[key][sl]).all(), (q, key)
+                    assert got["case"][0] == batch["case"][q] and got["nc"][0] == batch["nc"][q]
+            import torch
+            qd = torch.from_numpy(w.Q[2]).cuda()      # a device query vector
+            got = sess.query(qd, int(w.k[2]))
+            sl = slice(batch["offsets"][2], batch["offsets"][3])
+            assert (got["users"] == batch["users"][sl]).all()
+            with pytest.raises(rkr.RKRError):
+                sess.query(w.Q[0], int(w.k.max()) + 1)
+            bad = w.Q[0].copy()
+            bad[3] = np.nan
+            with pytest.raises(rkr.RKRError):
+                sess.query(bad, 1)

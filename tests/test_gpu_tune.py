@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 rkr = pytest.importorskip("paper_2504_13446_gb300")
 
 DEFAULT = dict(rc_bn=256, rc_single_first=1, skip_level=0, cand_budget_log2=26,
-               latency_ctas_per_sm=0)
+               latency_ctas_per_sm=0, latency_bulk=1)
 
 
 def _answers(idx, w):
@@ -35,7 +35,7 @@ def test_every_tuning_gives_the_same_answers(tmp_path):
             ref = _answers(idx, w)
             for fields in (dict(rc_bn=128), dict(rc_single_first=0), dict(skip_level=3),
                            dict(skip_level=9), dict(cand_budget_log2=20),
-                           dict(latency_ctas_per_sm=2)):
+                           dict(latency_ctas_per_sm=2), dict(latency_bulk=0)):
                 rkr.rkr_tuning_set(**{**DEFAULT, **fields})
                 got = _answers(idx, w)
                 for a, b in zip(got, ref):
