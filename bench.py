@@ -493,10 +493,22 @@ def bench_uneven(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     peaks, peak_src = _load_peaks()
+    t_start = time.perf_counter()
+
+    def note(msg):   # progress on stderr, flushed (the JSON line stays the only stdout)
+        print(f"[uneven {time.perf_counter() - t_start:8.1f} s] {msg}", file=sys.stderr,
+              flush=True)
+
     t0 = time.perf_counter()
-    w = synth.make_workload("uneven")
+    size = os.environ.get("RKR_UNEVEN_SIZE")   # "n,m,nq" for a reduced case
+    if size:
+        n_, m_, q_ = (int(v) for v in size.split(","))
+        w = synth.make_workload("uneven", n=n_, m=m_, nq=q_)
+    else:
+        w = synth.make_workload("uneven")
     bm = w.subset_bitmaps()
     t_gen = time.perf_counter() - t0
+    note(f"generated n={w.n} m={w.m} nq={w.Q.shape[0]}")
     U = torch.from_numpy(w.U).cuda()
     P = torch.from_numpy(w.P).cuda()
     Q = torch.from_numpy(w.Q).cuda()
@@ -516,11 +528,19 @@ def bench_uneven(args):
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1)
 
+    note("inputs on the device")
+    rkr.rkr_profile_start()
     idx, ms_build = timed(lambda: rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s,
                                             fbounds="exact", exact_table=True, floor_rank=2048))
+    note(f"index built in {ms_build:.0f} ms: {idx.timings()}")
+    build_prof = rkr.rkr_profile_stop()
+    note("build kernels: " + json.dumps({kk: round(v[1], 1) for kk, v in
+                                         sorted(build_prof.items(), key=lambda kv: -kv[1][1])[:8]}))
     for _ in range(max(1, args.warmup)):
-        idx.query_exact(Q, k, member=member, device=True)
-        idx.query_approx(Q, k, C, member=member, device=True)
+        (_, _, _, wst), t_w = timed(lambda: idx.query_exact(Q, k, member=member, device=True))
+        note(f"warm-up exact batch {t_w:.0f} ms: {json.dumps(wst.as_dict())}")
+        _, t_w = timed(lambda: idx.query_approx(Q, k, C, member=member, device=True))
+        note(f"warm-up approximate batch {t_w:.0f} ms")
     rkr.rkr_profile_start()
     ms_e, ms_a = [], []
     for _ in range(args.steps):
@@ -529,6 +549,7 @@ def bench_uneven(args):
         a, t_a = timed(lambda: idx.query_approx(Q, k, C, member=member, device=True))
         ms_e.append(t_e)
         ms_a.append(t_a)
+        note(f"step: exact {t_e:.0f} ms, approximate {t_a:.0f} ms")
     prof = rkr.rkr_profile_stop()
     mem = idx.device_bytes()
     idx.close()

@@ -1372,6 +1372,8 @@ struct LearnedPrune {
   const int32_t *keep;  // candidates kept per query (device, nq)
 };
 
+constexpr int64_t kLearnedUncut = 32;
+
 // Per query (one block), among the candidates still to be recounted (fb >= 0):
 // those whose predicted log rank y is above the keep[q]-th smallest prediction
 // are cut (fb = cu = -1, count = the largest key, so selection never takes them).
@@ -1397,7 +1399,10 @@ __global__ void __launch_bounds__(256)
     return (uint64_t)((b & 0x80000000u) ? ~b : (b | 0x80000000u));
   };
   const int64_t open = block_count(cnt, [&](int64_t i) { return fb[i] >= 0; }, &acc);
-  if (open <= keep) return;
+  // a query with far more candidates to recount than it keeps is left uncut: such
+  // candidates have weak rank lower bounds (their u.q lies below the tail lists)
+  // and the exact fallback would revive them anyway
+  if (open <= keep || open > kLearnedUncut * keep) return;
   const uint64_t kth = block_kth(cnt, (uint64_t)keep, 32,
                                  [&](int64_t i, uint64_t &key) {
                                    if (fb[i] < 0) return false;
