@@ -1,6 +1,9 @@
 // pruner.cu -- the learned pruner: a monotone rank regressor trained and run on
-// the GPU with hand-written BF16 kernels (operands rounded to BF16, FP32
-// accumulation and FP32 master weights).
+// the GPU.  Every matrix product (the two forward layers and the three backward
+// products) runs on the tcgen05 tensor cores through the screen kernel with a
+// dense epilogue (BF16 operands, FP32 accumulation in TMEM); the rest (output
+// layer, masks, column sums, Adam) are small elementwise kernels.  FP32 master
+// weights.
 //
 // Model (F non-monotone features x, the normalised score t = u.q / ||u||):
 //   h1 = relu(W1 x - softplus(A) t + b1),  h2 = relu(softplus(V2) h1 + b2),
@@ -9,6 +12,12 @@
 // and >= 0 after them, so y is non-increasing in t, as the rank of Def. 1 is.
 // Loss: 0.5 * mean((y - target)^2); Adam on the raw parameters.
 // Flattened parameter order: W1 (H x F), A (H), b1 (H), V2 (H x H), b2 (H), v3 (H), b3.
+//
+// Operand layouts (the tensor-core product D = A B^T takes both operands with K
+// contiguous, K padded to a multiple of 16 with zeros): X (B x Fp), W1 (H x Fp),
+// h1 (B x Hp), softplus(V2) (H x Hp) and its transpose; for the weight
+// gradients the batch is K, so dz2, h1, dz1 and X are also kept transposed
+// (H or Fp rows of `cap` entries, zero past the batch).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -17,18 +26,21 @@
 #include <vector>
 
 #include "index.cuh"
+#include "tcops.cuh"
 
 struct rkr_pruner {
-  int F = 0, H = 0;
+  int F = 0, H = 0, Fp = 0, Hp = 0;   // Fp, Hp: F, H rounded up to 16
   int64_t nparam = 0;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // master, grad, Adam moments
   int64_t step = 0;
   // effective BF16 weights of the current parameters
-  __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+  __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2t = nullptr;
   float *wt = nullptr, *w3 = nullptr;
-  // batch scratch (capacity cap rows)
+  int *err = nullptr;                 // error word of the tensor-core products
+  // batch scratch (capacity cap rows, a multiple of 16)
   int64_t cap = 0;
-  __nv_bfloat16 *Xb = nullptr, *h1 = nullptr, *h2 = nullptr, *d2b = nullptr, *d1b = nullptr;
+  __nv_bfloat16 *Xb = nullptr, *XbT = nullptr, *h1 = nullptr, *h1T = nullptr, *h2 = nullptr,
+                *d2b = nullptr, *d2T = nullptr, *d1T = nullptr;
   float *z1 = nullptr, *z2 = nullptr, *y = nullptr, *dy = nullptr, *tb = nullptr, *d2 = nullptr,
         *d1 = nullptr, *tg = nullptr;
 };
@@ -55,194 +67,157 @@ __device__ __forceinline__ float softplusf(float z) {
 }
 __device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
 
-// Effective weights: W1 and softplus(V2) in BF16, -softplus(A) and softplus(v3) in FP32.
-__global__ void k_mlp_weights(int F, int H, const float *__restrict__ p, Off o,
+// Effective weights: W1 (H x Fp) and softplus(V2) (H x Hp) in BF16 with zero
+// padding, the transpose of the latter, -softplus(A) and softplus(v3) in FP32.
+__global__ void k_mlp_weights(int F, int H, int Fp, int Hp, const float *__restrict__ p, Off o,
                               __nv_bfloat16 *__restrict__ W1b, __nv_bfloat16 *__restrict__ W2b,
-                              float *__restrict__ wt, float *__restrict__ w3) {
+                              __nv_bfloat16 *__restrict__ W2t, float *__restrict__ wt,
+                              float *__restrict__ w3) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < (int64_t)H * F) W1b[i] = __float2bfloat16_rn(p[o.W1 + i]);
-  if (i < (int64_t)H * H) W2b[i] = __float2bfloat16_rn(softplusf(p[o.V2 + i]));
+  if (i < (int64_t)H * Fp) {
+    const int64_t r = i / Fp, c = i % Fp;
+    W1b[i] = __float2bfloat16_rn(c < F ? p[o.W1 + r * F + c] : 0.0f);
+  }
+  if (i < (int64_t)H * Hp) {
+    const int64_t r = i / Hp, c = i % Hp;
+    W2b[i] = __float2bfloat16_rn(c < H ? softplusf(p[o.V2 + r * H + c]) : 0.0f);
+    W2t[i] = __float2bfloat16_rn(c < H ? softplusf(p[o.V2 + c * H + r]) : 0.0f);
+  }
   if (i < H) {
     wt[i] = -softplusf(p[o.A + i]);
     w3[i] = softplusf(p[o.v3 + i]);
   }
 }
 
-// C[m, n] = sum_k A(m, k) B(k, n) with BF16 operands and FP32 accumulation.
-// A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn].  Epilogue:
-// v = acc + bias[n] + tcol[m] * wcol[n] (each term optional); zout (FP32) gets v,
-// hout (BF16) gets relu(v) or v, fout (FP32) gets v.
-constexpr int GT = 128, GK = 16;   // 128 x 128 output tile, K in steps of 16
-__global__ void __launch_bounds__(256)
-    k_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int64_t sam,
-                int64_t sak, const __nv_bfloat16 *__restrict__ B, int64_t sbk, int64_t sbn,
-                const float *__restrict__ bias, const float *__restrict__ tcol,
-                const float *__restrict__ wcol, int relu, float *__restrict__ zout,
-                __nv_bfloat16 *__restrict__ hout, float *__restrict__ fout, int64_t ldc) {
-  __shared__ __align__(16) float As[GK][GT + 4];
-  __shared__ __align__(16) float Bs[GK][GT + 4];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-  // the loads run along whichever index is contiguous in memory
-  const bool a_m_fast = sam == 1, b_n_fast = sbn == 1;
-  float acc[8][8] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
-#pragma unroll
-    for (int t = 0; t < (GT * GK) / 256; ++t) {
-      const int e = tid + t * 256;
-      const int mm = a_m_fast ? e % GT : e / GK, kk = a_m_fast ? e / GT : e % GK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? __bfloat162float(A[gm * sam + gk * sak]) : 0.0f;
-      const int nn = b_n_fast ? e % GT : e / GK, kb = b_n_fast ? e / GT : e % GK;
-      const int gn = n0 + nn, gk2 = k0 + kb;
-      Bs[kb][nn] = (gn < N && gk2 < K) ? __bfloat162float(B[gk2 * sbk + gn * sbn]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      // rows ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx
-      const float4 a0 = *(const float4 *)&As[kk][ty * 4];
-      const float4 a1 = *(const float4 *)&As[kk][64 + ty * 4];
-      const float4 b0 = *(const float4 *)&Bs[kk][tx * 4];
-      const float4 b1 = *(const float4 *)&Bs[kk][64 + tx * 4];
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+// Dense epilogue of a tensor-core product D (M x N): v = acc + bias[col] +
+// tcol[row] * wcol[col] (each term optional); zout / fout get v (FP32), hout
+// gets relu(v) or v in BF16, houtT the same transposed (houtT[col * ldt + row]).
+struct EpiDense {
+  static const char *name() { return "k_screen<EpiDense>"; }
+  struct Thread {
+    int64_t row;
+  };
+  static constexpr size_t kSmem = 0;
+  int64_t M, N;
+  int bn;
+  const float *bias, *tcol, *wcol;
+  int relu;
+  float *zout;
+  int64_t ldz;
+  float *fout;
+  int64_t ldf;
+  __nv_bfloat16 *hout;
+  int64_t ldh;
+  __nv_bfloat16 *houtT;
+  int64_t ldt;
+  __device__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ void tile_begin(char *, int rb, int, int r, int, Thread &ts) const {
+    ts.row = (int64_t)rb * tc::BM + r;
   }
+  __device__ void chunk(char *, int, int ct, int, int col, uint32_t, const float (&v)[32],
+                        Thread &ts) const {
+    if (ts.row >= M) return;
+    const int64_t c0 = (int64_t)ct * bn + col;
+    const float tr = tcol ? tcol[ts.row] : 0.0f;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
-      if (gn >= N) continue;
-      float v = acc[i][j];
-      if (bias) v += bias[gn];
-      if (tcol) v = fmaf(tcol[gm], wcol[gn], v);
-      const int64_t at = (int64_t)gm * ldc + gn;
-      if (zout) zout[at] = v;
-      if (fout) fout[at] = v;
-      if (hout) hout[at] = __float2bfloat16_rn(relu ? fmaxf(v, 0.0f) : v);
-    }
-  }
-}
-
-constexpr int GS = 64;   // small tile: 64 x 64 outputs, 4 x 4 per thread
-__global__ void __launch_bounds__(256)
-    k_gemm_bf16_small(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int64_t sam,
-                int64_t sak, const __nv_bfloat16 *__restrict__ B, int64_t sbk, int64_t sbn,
-                const float *__restrict__ bias, const float *__restrict__ tcol,
-                const float *__restrict__ wcol, int relu, float *__restrict__ zout,
-                __nv_bfloat16 *__restrict__ hout, float *__restrict__ fout, int64_t ldc) {
-  __shared__ float As[GK][GS + 1], Bs[GK][GS + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * GS, n0 = blockIdx.x * GS;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = threadIdx.x; e < GS * GK; e += 256) {
-      const int mm = e / GK, kk = e % GK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? __bfloat162float(A[gm * sam + gk * sak]) : 0.0f;
-      const int nn = e % GS, kb = e / GS;
-      const int gn = n0 + nn, gk2 = k0 + kb;
-      Bs[kb][nn] = (gn < N && gk2 < K) ? __bfloat162float(B[gk2 * sbk + gn * sbn]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = As[kk][ty * 4 + i];
-        b[i] = Bs[kk][tx * 4 + i];
+    for (int j = 0; j < 32; ++j) {
+      const int64_t c = c0 + j;
+      if (c < N) {
+        float x = v[j];
+        if (bias) x += bias[c];
+        if (tcol) x = fmaf(tr, wcol[c], x);
+        if (zout) zout[ts.row * ldz + c] = x;
+        if (fout) fout[ts.row * ldf + c] = x;
+        const __nv_bfloat16 h = __float2bfloat16_rn(relu ? fmaxf(x, 0.0f) : x);
+        if (hout) hout[ts.row * ldh + c] = h;
+        if (houtT) houtT[c * ldt + ts.row] = h;
       }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + ty * 4 + i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx * 4 + j;
-      if (gn >= N) continue;
-      float v = acc[i][j];
-      if (bias) v += bias[gn];
-      if (tcol) v = fmaf(tcol[gm], wcol[gn], v);
-      const int64_t at = (int64_t)gm * ldc + gn;
-      if (zout) zout[at] = v;
-      if (fout) fout[at] = v;
-      if (hout) hout[at] = __float2bfloat16_rn(relu ? fmaxf(v, 0.0f) : v);
     }
   }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *, const tc::Unit &, int, Thread &) const {}
+};
+
+// D = A B^T on the tensor cores: A rows of K = kp BF16 values (pitch kp), B
+// likewise; the epilogue gets D's (row, column) entries.
+rkr_status dense(const __nv_bfloat16 *A, int64_t M, const __nv_bfloat16 *B, int64_t N, int kp,
+                 EpiDense e, int *err, cudaStream_t st) {
+  constexpr int BN = 256;
+  TcSide a, b;
+  a.rows = M;
+  a.d = kp;
+  a.kp = kp;
+  a.hi = a.lo = const_cast<__nv_bfloat16 *>(A);
+  a.owned = false;
+  b.rows = N;
+  b.d = kp;
+  b.kp = kp;
+  b.hi = b.lo = const_cast<__nv_bfloat16 *>(B);
+  b.owned = false;
+  e.M = M;
+  e.N = N;
+  e.bn = BN;
+  return launch_screen<BN, 4>(a, b, 0, row_schedule(M, N, BN), e, err, st);
 }
 
-static void gemm(int M, int N, int K, const __nv_bfloat16 *A, int64_t sam, int64_t sak,
-                 const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, const float *bias,
-                 const float *tcol, const float *wcol, int relu, float *zout, __nv_bfloat16 *hout,
-                 float *fout, int64_t ldc, cudaStream_t st) {
-  // large tiles when they still give every SM a block; the gradient products
-  // (small outputs, long K) keep more blocks with small tiles
-  const int64_t big = (int64_t)((N + GT - 1) / GT) * ((M + GT - 1) / GT);
-  if (big >= 152) {
-    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-    k_gemm_bf16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, tcol, wcol, relu,
-                                      zout, hout, fout, ldc);
-  } else {
-    dim3 grid((N + GS - 1) / GS, (M + GS - 1) / GS);
-    k_gemm_bf16_small<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, tcol, wcol,
-                                            relu, zout, hout, fout, ldc);
-  }
-  note_launch();
+EpiDense dense_epi() {
+  EpiDense e;
+  e.M = e.N = 0;
+  e.bn = 256;
+  e.bias = e.tcol = e.wcol = nullptr;
+  e.relu = 0;
+  e.zout = e.fout = nullptr;
+  e.hout = e.houtT = nullptr;
+  e.ldz = e.ldf = e.ldh = e.ldt = 0;
+  return e;
 }
 
-// Gather a batch: BF16 features, FP32 scores and targets.
-__global__ void k_mlp_batch(int64_t B, int F, const int64_t *__restrict__ idx,
-                            const float *__restrict__ X, const float *__restrict__ t,
-                            const float *__restrict__ target, __nv_bfloat16 *__restrict__ Xb,
+// Gather a batch into X (cap x Fp) and its transpose (Fp x cap), FP32 scores and
+// targets; rows [B, Bp) and columns [F, Fp) are written as zeros.
+__global__ void k_mlp_batch(int64_t B, int64_t Bp, int F, int Fp, int64_t cap,
+                            const int64_t *__restrict__ idx, const float *__restrict__ X,
+                            const float *__restrict__ t, const float *__restrict__ target,
+                            __nv_bfloat16 *__restrict__ Xb, __nv_bfloat16 *__restrict__ XbT,
                             float *__restrict__ tb, float *__restrict__ tg) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= B * F) return;
-  const int64_t r = i / F, c = i % F;
-  const int64_t s = idx ? idx[r] : r;
-  Xb[i] = __float2bfloat16_rn(X[s * F + c]);
+  if (i >= Bp * Fp) return;
+  const int64_t r = i / Fp, c = i % Fp;
+  const bool live = r < B && c < F;
+  const int64_t s = live ? (idx ? idx[r] : r) : 0;
+  const __nv_bfloat16 x = __float2bfloat16_rn(live ? X[s * F + c] : 0.0f);
+  Xb[r * Fp + c] = x;
+  if (XbT) XbT[c * cap + r] = x;
   if (c == 0) {
-    tb[r] = t[s];
-    if (target) tg[r] = target[s];
+    tb[r] = r < B ? t[idx ? idx[r] : r] : 0.0f;
+    if (tg) tg[r] = r < B && target ? target[idx ? idx[r] : r] : 0.0f;
   }
 }
 
-// Gather rows of a per-user feature table: Xb[r] = Xu[uid[r]], tb[r] = t[r].
-__global__ void k_mlp_gather(int64_t B, int F, const int32_t *__restrict__ uid,
+// Gather rows of a per-user feature table: X[r] = Xu[uid[r]], tb[r] = t[r].
+__global__ void k_mlp_gather(int64_t B, int F, int Fp, const int32_t *__restrict__ uid,
                              const float *__restrict__ Xu, const float *__restrict__ t,
                              __nv_bfloat16 *__restrict__ Xb, float *__restrict__ tb) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= B * F) return;
-  const int64_t r = i / F, c = i % F;
+  if (i >= B * Fp) return;
+  const int64_t r = i / Fp, c = i % Fp;
   const int64_t u = uid[r] < 0 ? 0 : uid[r];  // invalid rows read user 0 (ignored)
-  Xb[i] = __float2bfloat16_rn(Xu[u * F + c]);
+  Xb[r * Fp + c] = __float2bfloat16_rn(c < F ? Xu[u * F + c] : 0.0f);
   if (c == 0) tb[r] = t[r];
 }
 
-// y[r] = w3 . h2[r] + b3 (one warp per row), and dy = (y - target) / B when asked.
-__global__ void k_mlp_out(int64_t B, int H, const __nv_bfloat16 *__restrict__ h2,
+// y[r] = w3 . h2[r] + b3 (one warp per row), and dy = (y - target) / B when asked
+// (dy = 0 for the padding rows [B, cap)).
+__global__ void k_mlp_out(int64_t B, int64_t cap, int H, const __nv_bfloat16 *__restrict__ h2,
                           const float *__restrict__ w3, const float *__restrict__ p, int64_t ob3,
                           float *__restrict__ y, const float *__restrict__ tg,
                           float *__restrict__ dy) {
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (r >= B) return;
+  if (r >= (dy ? cap : B)) return;
+  if (r >= B) {
+    if (lane == 0) dy[r] = 0.0f;
+    return;
+  }
   float acc = 0.0f;
   for (int n = lane; n < H; n += 32) acc = fmaf(__bfloat162float(h2[r * H + n]), w3[n], acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -253,25 +228,32 @@ __global__ void k_mlp_out(int64_t B, int H, const __nv_bfloat16 *__restrict__ h2
   }
 }
 
-// dz2 = dy[r] * w3[n] * (z2 > 0), FP32 and BF16.
-__global__ void k_mlp_dz2(int64_t B, int H, const float *__restrict__ dy,
+// dz2 = dy[r] * w3[n] * (z2 > 0): FP32 (B x H), BF16 (cap x Hp) and transposed
+// BF16 (H x cap); zero on the padding rows.
+__global__ void k_mlp_dz2(int64_t B, int64_t cap, int H, int Hp, const float *__restrict__ dy,
                           const float *__restrict__ w3, const float *__restrict__ z2,
-                          float *__restrict__ d2, __nv_bfloat16 *__restrict__ d2b) {
+                          float *__restrict__ d2, __nv_bfloat16 *__restrict__ d2b,
+                          __nv_bfloat16 *__restrict__ d2T) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= B * H) return;
-  const float v = z2[i] > 0.0f ? dy[i / H] * w3[i % H] : 0.0f;
-  d2[i] = v;
-  d2b[i] = __float2bfloat16_rn(v);
+  if (i >= cap * H) return;
+  const int64_t r = i / H, c = i % H;
+  const float v = r < B && z2[i] > 0.0f ? dy[r] * w3[c] : 0.0f;
+  if (r < B) d2[i] = v;
+  const __nv_bfloat16 vb = __float2bfloat16_rn(v);
+  d2b[r * Hp + c] = vb;
+  d2T[c * cap + r] = vb;
 }
 
-// dz1 = (dz2 W2)[r, k] * (z1 > 0) in place of the product, FP32 and BF16.
-__global__ void k_mlp_dz1(int64_t B, int H, const float *__restrict__ z1, float *__restrict__ d1,
-                          __nv_bfloat16 *__restrict__ d1b) {
+// dz1 = (dz2 W2)[r, k] * (z1 > 0) in place of the product (FP32), and transposed
+// BF16 (H x cap); zero on the padding rows.
+__global__ void k_mlp_dz1(int64_t B, int64_t cap, int H, const float *__restrict__ z1,
+                          float *__restrict__ d1, __nv_bfloat16 *__restrict__ d1T) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= B * H) return;
-  const float v = z1[i] > 0.0f ? d1[i] : 0.0f;
-  d1[i] = v;
-  d1b[i] = __float2bfloat16_rn(v);
+  if (i >= cap * H) return;
+  const int64_t r = i / H, c = i % H;
+  const float v = r < B && z1[i] > 0.0f ? d1[i] : 0.0f;
+  if (r < B) d1[i] = v;
+  d1T[c * cap + r] = __float2bfloat16_rn(v);
 }
 
 // out[n] = sum_r f(D[r, n]) * rowscale[r]: f = relu when asked, rowscale = 1 when null.
@@ -323,23 +305,33 @@ __global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict
   p[i] -= lr * (mi / b1c) / (sqrtf(vi / b2c) + 1e-8f);
 }
 
+int64_t round16(int64_t x) { return (x + 15) / 16 * 16; }
+
 rkr_status ensure_cap(rkr_pruner *pr, int64_t B, cudaStream_t st) {
+  B = round16(B);
   if (B <= pr->cap) return RKR_OK;
-  const int H = pr->H, F = pr->F;
-  for (void *q : {(void *)pr->Xb, (void *)pr->h1, (void *)pr->h2, (void *)pr->d2b,
-                  (void *)pr->d1b, (void *)pr->z1, (void *)pr->z2, (void *)pr->y, (void *)pr->dy,
-                  (void *)pr->tb, (void *)pr->d2, (void *)pr->d1, (void *)pr->tg})
+  const int H = pr->H, Fp = pr->Fp, Hp = pr->Hp;
+  for (void *q : {(void *)pr->Xb, (void *)pr->XbT, (void *)pr->h1, (void *)pr->h1T,
+                  (void *)pr->h2, (void *)pr->d2b, (void *)pr->d2T, (void *)pr->d1T,
+                  (void *)pr->z1, (void *)pr->z2, (void *)pr->y, (void *)pr->dy, (void *)pr->tb,
+                  (void *)pr->d2, (void *)pr->d1, (void *)pr->tg})
     if (q) cudaFreeAsync(q, st);
   auto al = [&](auto **q, size_t count) -> rkr_status {
     cudaError_t e = pool_malloc_async((void **)q, count * sizeof(**q), st);
     if (e != cudaSuccess) return cuda_fail(e, "pruner scratch");
+    // padding entries of the operands must read as zeros
+    e = cudaMemsetAsync(*q, 0, count * sizeof(**q), st);
+    if (e != cudaSuccess) return cuda_fail(e, "pruner scratch");
     return RKR_OK;
   };
-  RKR_TRY(al(&pr->Xb, (size_t)B * F));
-  RKR_TRY(al(&pr->h1, (size_t)B * H));
+  RKR_TRY(al(&pr->Xb, (size_t)B * Fp));
+  RKR_TRY(al(&pr->XbT, (size_t)Fp * B));
+  RKR_TRY(al(&pr->h1, (size_t)B * Hp));
+  RKR_TRY(al(&pr->h1T, (size_t)H * B));
   RKR_TRY(al(&pr->h2, (size_t)B * H));
-  RKR_TRY(al(&pr->d2b, (size_t)B * H));
-  RKR_TRY(al(&pr->d1b, (size_t)B * H));
+  RKR_TRY(al(&pr->d2b, (size_t)B * Hp));
+  RKR_TRY(al(&pr->d2T, (size_t)H * B));
+  RKR_TRY(al(&pr->d1T, (size_t)H * B));
   RKR_TRY(al(&pr->z1, (size_t)B * H));
   RKR_TRY(al(&pr->z2, (size_t)B * H));
   RKR_TRY(al(&pr->d2, (size_t)B * H));
@@ -354,62 +346,102 @@ rkr_status ensure_cap(rkr_pruner *pr, int64_t B, cudaStream_t st) {
 
 void refresh_weights(rkr_pruner *pr, cudaStream_t st) {
   const Off o(pr->F, pr->H);
-  const int64_t cnt = std::max<int64_t>((int64_t)pr->H * pr->F, (int64_t)pr->H * pr->H);
-  k_mlp_weights<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(pr->F, pr->H, pr->p, o, pr->W1b,
-                                                                pr->W2b, pr->wt, pr->w3);
+  const int64_t cnt = std::max<int64_t>((int64_t)pr->H * pr->Fp, (int64_t)pr->H * pr->Hp);
+  k_mlp_weights<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
+      pr->F, pr->H, pr->Fp, pr->Hp, pr->p, o, pr->W1b, pr->W2b, pr->W2t, pr->wt, pr->w3);
   note_launch();
 }
 
-// Forward pass of the batch already gathered in Xb / tb; y in pr->y.
-void forward_batch(rkr_pruner *pr, int64_t B, bool with_grad, cudaStream_t st) {
-  const int F = pr->F, H = pr->H;
-  const Off o(F, H);
+// Forward pass of the batch already gathered in Xb / tb; y in pr->y.  With
+// with_grad, h1 is also kept transposed and dy formed for the backward pass.
+rkr_status forward_batch(rkr_pruner *pr, int64_t B, bool with_grad, cudaStream_t st) {
+  const int H = pr->H;
+  const Off o(pr->F, H);
   // z1 = X W1^T + b1 + t wt^T, h1 = relu(z1)
-  gemm((int)B, H, F, pr->Xb, F, 1, pr->W1b, 1, F, pr->p + o.b1, pr->tb, pr->wt, 1, pr->z1,
-       pr->h1, nullptr, H, st);
+  EpiDense e1 = dense_epi();
+  e1.bias = pr->p + o.b1;
+  e1.tcol = pr->tb;
+  e1.wcol = pr->wt;
+  e1.relu = 1;
+  e1.zout = pr->z1;
+  e1.ldz = H;
+  e1.hout = pr->h1;
+  e1.ldh = pr->Hp;
+  if (with_grad) {
+    e1.houtT = pr->h1T;
+    e1.ldt = pr->cap;
+  }
+  RKR_TRY(dense(pr->Xb, B, pr->W1b, H, pr->Fp, e1, pr->err, st));
   // z2 = h1 W2^T + b2, h2 = relu(z2)
-  gemm((int)B, H, H, pr->h1, H, 1, pr->W2b, 1, H, pr->p + o.b2, nullptr, nullptr, 1, pr->z2,
-       pr->h2, nullptr, H, st);
-  k_mlp_out<<<(unsigned)((B * 32 + 255) / 256), 256, 0, st>>>(
-      B, H, pr->h2, pr->w3, pr->p, o.b3, pr->y, with_grad ? pr->tg : nullptr,
+  EpiDense e2 = dense_epi();
+  e2.bias = pr->p + o.b2;
+  e2.relu = 1;
+  e2.zout = pr->z2;
+  e2.ldz = H;
+  e2.hout = pr->h2;
+  e2.ldh = H;
+  RKR_TRY(dense(pr->h1, B, pr->W2b, H, pr->Hp, e2, pr->err, st));
+  const int64_t rows = with_grad ? pr->cap : B;
+  k_mlp_out<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
+      B, pr->cap, H, pr->h2, pr->w3, pr->p, o.b3, pr->y, with_grad ? pr->tg : nullptr,
       with_grad ? pr->dy : nullptr);
   note_launch();
+  return RKR_OK;
 }
 
 // Backward pass of the batch of the last forward: gradients of the raw
-// parameters into pr->g (same order as the flat parameter vector).
-void backward_batch(rkr_pruner *pr, int64_t B, cudaStream_t st) {
+// parameters into pr->g (same order as the flat parameter vector).  The batch
+// is K of the weight-gradient products; padding rows carry zeros.
+rkr_status backward_batch(rkr_pruner *pr, int64_t B, cudaStream_t st) {
   const int F = pr->F, H = pr->H;
   const Off o(F, H);
-  const unsigned nb = (unsigned)((B * H + 255) / 256);
+  const int64_t cap = pr->cap;
+  const unsigned nb = (unsigned)((cap * H + 255) / 256);
   // dw3 = h2^T dy (the chain rule to v3 follows)
   k_colsum<<<H, 256, 0, st>>>(B, H, pr->z2, 1, pr->dy, pr->g + o.v3);
   note_launch();
   // dz2 = dy w3^T * (z2 > 0); db2 = column sums
-  k_mlp_dz2<<<nb, 256, 0, st>>>(B, H, pr->dy, pr->w3, pr->z2, pr->d2, pr->d2b);
+  k_mlp_dz2<<<nb, 256, 0, st>>>(B, cap, H, pr->Hp, pr->dy, pr->w3, pr->z2, pr->d2, pr->d2b,
+                                pr->d2T);
   note_launch();
   k_colsum<<<H, 256, 0, st>>>(B, H, pr->d2, 0, nullptr, pr->g + o.b2);
   note_launch();
-  // dW2 = dz2^T h1 (H x H)
-  gemm(H, H, (int)B, pr->d2b, 1, H, pr->h1, H, 1, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
-       pr->g + o.V2, H, st);
+  // dW2 = dz2^T h1 (H x H): K = the batch
+  EpiDense ew2 = dense_epi();
+  ew2.fout = pr->g + o.V2;
+  ew2.ldf = H;
+  RKR_TRY(dense(pr->d2T, H, pr->h1T, H, (int)cap, ew2, pr->err, st));
   // dh1 = dz2 W2 (B x H), then dz1 = dh1 * (z1 > 0)
-  gemm((int)B, H, H, pr->d2b, H, 1, pr->W2b, H, 1, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
-       pr->d1, H, st);
-  k_mlp_dz1<<<nb, 256, 0, st>>>(B, H, pr->z1, pr->d1, pr->d1b);
+  EpiDense eh1 = dense_epi();
+  eh1.fout = pr->d1;
+  eh1.ldf = H;
+  RKR_TRY(dense(pr->d2b, B, pr->W2t, H, pr->Hp, eh1, pr->err, st));
+  k_mlp_dz1<<<nb, 256, 0, st>>>(B, cap, H, pr->z1, pr->d1, pr->d1T);
   note_launch();
   // db1 = column sums; d(wt) = dz1^T t
   k_colsum<<<H, 256, 0, st>>>(B, H, pr->d1, 0, nullptr, pr->g + o.b1);
   note_launch();
   k_colsum<<<H, 256, 0, st>>>(B, H, pr->d1, 0, pr->tb, pr->g + o.A);
   note_launch();
-  // dW1 = dz1^T X (H x F)
-  gemm(H, F, (int)B, pr->d1b, 1, H, pr->Xb, F, 1, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
-       pr->g + o.W1, F, st);
+  // dW1 = dz1^T X (H x F): K = the batch
+  EpiDense ew1 = dense_epi();
+  ew1.fout = pr->g + o.W1;
+  ew1.ldf = F;
+  RKR_TRY(dense(pr->d1T, H, pr->XbT, F, (int)cap, ew1, pr->err, st));
   // constrained parameters and db3
   const int64_t cnt = std::max<int64_t>((int64_t)H * H, 1);
   k_mlp_chain<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(H, pr->p, o, pr->g, pr->dy, B);
   note_launch();
+  return RKR_OK;
+}
+
+// The products' error word: RKR_ETIMEOUT when a bounded wait gave up.
+rkr_status check_err(rkr_pruner *pr, cudaStream_t st) {
+  int h = 0;
+  RKR_CUDA(cudaMemcpyAsync(&h, pr->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (h) return fail(RKR_ETIMEOUT, "pruner product wait timed out (%d)", h);
+  return RKR_OK;
 }
 
 // A device view of an input array: the array itself when it is device memory,
@@ -462,13 +494,13 @@ rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t 
   refresh_weights(pr, st);
   for (int64_t a = 0; a < B; a += chunk) {
     const int64_t b = std::min(B - a, chunk);
-    k_mlp_gather<<<(unsigned)((b * pr->F + 255) / 256), 256, 0, st>>>(b, pr->F, uid + a, Xu,
-                                                                      t + a, pr->Xb, pr->tb);
+    k_mlp_gather<<<(unsigned)((b * pr->Fp + 255) / 256), 256, 0, st>>>(b, pr->F, pr->Fp, uid + a,
+                                                                       Xu, t + a, pr->Xb, pr->tb);
     note_launch();
-    forward_batch(pr, b, false, st);
+    RKR_TRY(forward_batch(pr, b, false, st));
     RKR_CUDA(cudaMemcpyAsync(y + a, pr->y, sizeof(float) * b, cudaMemcpyDeviceToDevice, st));
   }
-  return RKR_OK;
+  return check_err(pr, st);
 }
 
 int pruner_features(const rkr_pruner *pr) { return pr->F; }
@@ -485,6 +517,8 @@ rkr_status rkr_pruner_create(int32_t F, int32_t H, uint64_t seed, rkr_pruner **o
   rkr_pruner *pr = new rkr_pruner();
   pr->F = F;
   pr->H = H;
+  pr->Fp = (F + 15) / 16 * 16;
+  pr->Hp = (H + 15) / 16 * 16;
   const Off o(F, H);
   pr->nparam = o.n;
   std::vector<float> init(o.n, 0.0f);
@@ -505,8 +539,10 @@ rkr_status rkr_pruner_create(int32_t F, int32_t H, uint64_t seed, rkr_pruner **o
   if (s == RKR_OK) s = al(&pr->g, o.n);
   if (s == RKR_OK) s = al(&pr->m, o.n);
   if (s == RKR_OK) s = al(&pr->v, o.n);
-  if (s == RKR_OK) s = al(&pr->W1b, (size_t)H * F);
-  if (s == RKR_OK) s = al(&pr->W2b, (size_t)H * H);
+  if (s == RKR_OK) s = al(&pr->W1b, (size_t)H * pr->Fp);
+  if (s == RKR_OK) s = al(&pr->W2b, (size_t)H * pr->Hp);
+  if (s == RKR_OK) s = al(&pr->W2t, (size_t)H * pr->Hp);
+  if (s == RKR_OK) s = al(&pr->err, 1);
   if (s == RKR_OK) s = al(&pr->wt, (size_t)H);
   if (s == RKR_OK) s = al(&pr->w3, (size_t)H);
   if (s == RKR_OK && cudaMemcpy(pr->p, init.data(), sizeof(float) * o.n, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -515,6 +551,7 @@ rkr_status rkr_pruner_create(int32_t F, int32_t H, uint64_t seed, rkr_pruner **o
     cudaMemset(pr->m, 0, sizeof(float) * o.n);
     cudaMemset(pr->v, 0, sizeof(float) * o.n);
     cudaMemset(pr->g, 0, sizeof(float) * o.n);
+    cudaMemset(pr->err, 0, sizeof(int));
   }
   if (s != RKR_OK) {
     rkr_pruner_free(pr);
@@ -553,14 +590,15 @@ rkr_status rkr_pruner_forward(rkr_pruner *pr, const float *X, const float *t, in
   refresh_weights(pr, st);
   for (int64_t a = 0; a < B; a += chunk) {
     const int64_t b = std::min(B - a, chunk);
-    k_mlp_batch<<<(unsigned)((b * pr->F + 255) / 256), 256, 0, st>>>(
-        b, pr->F, nullptr, X + a * pr->F, t + a, nullptr, pr->Xb, pr->tb, pr->tg);
+    k_mlp_batch<<<(unsigned)((b * pr->Fp + 255) / 256), 256, 0, st>>>(
+        b, b, pr->F, pr->Fp, pr->cap, nullptr, X + a * pr->F, t + a, nullptr, pr->Xb, nullptr,
+        pr->tb, nullptr);
     note_launch();
-    forward_batch(pr, b, false, st);
+    RKR_TRY(forward_batch(pr, b, false, st));
     RKR_CUDA(cudaMemcpyAsync(y + a, pr->y, sizeof(float) * b, cudaMemcpyDefault, st));
   }
   RKR_CUDA(cudaStreamSynchronize(st));
-  return RKR_OK;
+  return check_err(pr, st);
 }
 
 rkr_status rkr_pruner_loss_grads(rkr_pruner *pr, const float *X, const float *t,
@@ -579,11 +617,13 @@ rkr_status rkr_pruner_loss_grads(rkr_pruner *pr, const float *X, const float *t,
   target = (const float *)vg.p;
   RKR_TRY(ensure_cap(pr, B, st));
   refresh_weights(pr, st);
-  k_mlp_batch<<<(unsigned)((B * pr->F + 255) / 256), 256, 0, st>>>(B, pr->F, nullptr, X, t,
-                                                                   target, pr->Xb, pr->tb, pr->tg);
+  k_mlp_batch<<<(unsigned)((pr->cap * pr->Fp + 255) / 256), 256, 0, st>>>(
+      B, pr->cap, pr->F, pr->Fp, pr->cap, nullptr, X, t, target, pr->Xb, pr->XbT, pr->tb,
+      pr->tg);
   note_launch();
-  forward_batch(pr, B, true, st);
-  backward_batch(pr, B, st);
+  RKR_TRY(forward_batch(pr, B, true, st));
+  RKR_TRY(backward_batch(pr, B, st));
+  RKR_TRY(check_err(pr, st));
   RKR_CUDA(cudaMemcpyAsync(grads, pr->g, sizeof(float) * pr->nparam, cudaMemcpyDefault, st));
   if (loss) {
     std::vector<float> y(B), tg(B);
@@ -627,11 +667,12 @@ rkr_status rkr_pruner_train(rkr_pruner *pr, const float *X, const float *t, cons
                              cudaMemcpyHostToDevice, st));
     for (int64_t a = 0; a + B <= npairs; a += B) {
       refresh_weights(pr, st);
-      k_mlp_batch<<<(unsigned)((B * pr->F + 255) / 256), 256, 0, st>>>(
-          B, pr->F, perm_d + a, X, t, target, pr->Xb, pr->tb, pr->tg);
+      k_mlp_batch<<<(unsigned)((pr->cap * pr->Fp + 255) / 256), 256, 0, st>>>(
+          B, pr->cap, pr->F, pr->Fp, pr->cap, perm_d + a, X, t, target, pr->Xb, pr->XbT,
+          pr->tb, pr->tg);
       note_launch();
-      forward_batch(pr, B, true, st);
-      backward_batch(pr, B, st);
+      RKR_TRY(forward_batch(pr, B, true, st));
+      RKR_TRY(backward_batch(pr, B, st));
       pr->step += 1;
       const float b1c = 1.0f - powf(0.9f, (float)pr->step), b2c = 1.0f - powf(0.999f, (float)pr->step);
       k_adam<<<(unsigned)((pr->nparam + 255) / 256), 256, 0, st>>>(pr->nparam, pr->p, pr->g,
@@ -639,6 +680,7 @@ rkr_status rkr_pruner_train(rkr_pruner *pr, const float *X, const float *t, cons
       note_launch();
     }
     RKR_CUDA(cudaStreamSynchronize(st));  // the host permutation is rewritten next epoch
+    RKR_TRY(check_err(pr, st));
   }
   // loss of the last batch
   if (final_loss) {
@@ -658,10 +700,11 @@ void rkr_pruner_free(rkr_pruner *pr) {
   if (!pr) return;
   cudaDeviceSynchronize();
   for (void *q : {(void *)pr->p, (void *)pr->g, (void *)pr->m, (void *)pr->v, (void *)pr->W1b,
-                  (void *)pr->W2b, (void *)pr->wt, (void *)pr->w3, (void *)pr->Xb, (void *)pr->h1,
-                  (void *)pr->h2, (void *)pr->d2b, (void *)pr->d1b, (void *)pr->z1, (void *)pr->z2,
-                  (void *)pr->y, (void *)pr->dy, (void *)pr->tb, (void *)pr->d2, (void *)pr->d1,
-                  (void *)pr->tg})
+                  (void *)pr->W2b, (void *)pr->W2t, (void *)pr->wt, (void *)pr->w3,
+                  (void *)pr->err, (void *)pr->Xb, (void *)pr->XbT, (void *)pr->h1,
+                  (void *)pr->h1T, (void *)pr->h2, (void *)pr->d2b, (void *)pr->d2T,
+                  (void *)pr->d1T, (void *)pr->z1, (void *)pr->z2, (void *)pr->y, (void *)pr->dy,
+                  (void *)pr->tb, (void *)pr->d2, (void *)pr->d1, (void *)pr->tg})
     if (q) cudaFree(q);
   delete pr;
 }
