@@ -359,8 +359,9 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  * rank the tail lists settle keep their exact rank, and of the candidates that
  * would still need a recount over P only the keep[i] with the smallest
  * predicted log rank (and those tying with the keep[i]-th) are recounted for
- * query i (a query with more than 32 keep[i] candidates to recount is not cut:
- * their rank lower bounds are too weak for the fallback to spare them).  Exact
+ * query i (a query with more than 32 keep[i] candidates to recount that are also
+ * more than a quarter of all users is not cut: their rank lower bounds are too
+ * weak for the fallback to spare them).  Exact
  * fallback: after that recount, every cut candidate whose rank
  * lower bound (from the tail lists and count tables) does not exceed the k-th
  * smallest count found is recounted as well; the others cannot be among the k

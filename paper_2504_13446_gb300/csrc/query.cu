@@ -1383,7 +1383,7 @@ __global__ void __launch_bounds__(256)
                   const int32_t *__restrict__ keep_q, const float *__restrict__ y,
                   int32_t *__restrict__ fb_all, int32_t *__restrict__ cu_all,
                   uint32_t *__restrict__ ccount, int32_t *__restrict__ cutu_all,
-                  unsigned long long *__restrict__ ncut) {
+                  int64_t n_users, unsigned long long *__restrict__ ncut) {
   __shared__ uint32_t hist[256];
   __shared__ uint64_t bc[2];
   __shared__ unsigned long long acc;
@@ -1399,10 +1399,10 @@ __global__ void __launch_bounds__(256)
     return (uint64_t)((b & 0x80000000u) ? ~b : (b | 0x80000000u));
   };
   const int64_t open = block_count(cnt, [&](int64_t i) { return fb[i] >= 0; }, &acc);
-  // a query with far more candidates to recount than it keeps is left uncut: such
-  // candidates have weak rank lower bounds (their u.q lies below the tail lists)
-  // and the exact fallback would revive them anyway
-  if (open <= keep || open > kLearnedUncut * keep) return;
+  // a query whose candidates to recount are a large part of all users and far more
+  // than it keeps is left uncut: such candidates have weak rank lower bounds (u.q
+  // lies below the tail lists) and the exact fallback would revive them anyway
+  if (open <= keep || (open > kLearnedUncut * keep && open > n_users / 4)) return;
   const uint64_t kth = block_kth(cnt, (uint64_t)keep, 32,
                                  [&](int64_t i, uint64_t &key) {
                                    if (fb[i] < 0) return false;
@@ -1568,7 +1568,7 @@ static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const
   k_scatter_y<<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(nfb, fi, yc, y);
   note_launch();
   k_learned_cut<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, lp->keep, y, cu_fb, cu, ccount,
-                                         cutu, ncut);
+                                         cutu, idx->n, ncut);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   unsigned long long h = 0;
