@@ -403,48 +403,60 @@ def learned_comparison(rkr, w, U, P, Q, pos, steps, idx=None):
     loss, ms_train = timed(lambda: net.train(X, t, target, epochs=epochs, batch=4096, lr=1e-3,
                                              seed=3))
     del X, t
-    # keep factor: the smallest alpha on the grid whose cut revives at most 1 % of
-    # its remaining candidates on the held-out queries
+    # keep factor of the plain cut: the smallest alpha on the grid with recall >= 0.99
+    # on the held-out queries (judged by the exact query)
+    def recall_of(lr_, loff_, plain_r_):
+        hits = viol = 0
+        for q in range(len(loff_) - 1):
+            sl = slice(loff_[q], loff_[q + 1])
+            kth = plain_r_[sl].max()
+            hits += int(np.sum(lr_[sl] <= kth))
+            viol += int(np.sum(lr_[sl] > C * kth))
+        return hits / float(loff_[-1]), viol
+
+    _, cal_r, _, _ = idx.query_exact(Qcal, kcal)
     grid = [1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0]
     cal = {}
     alpha = grid[-1]
     for a in grid:
         keep = np.ceil(a * kcal).astype(np.int32)
-        _, _, _, cst = idx.query_exact_learned(net, Rp, Qcal, kcal, keep)
-        cal[a] = cst.learned_revived / max(cst.candidates, 1)
-        if cal[a] <= 0.01:
+        _, lr_c, loff_c, _ = idx.query_exact_learned(net, Rp, Qcal, kcal, keep, certify=False)
+        cal[a] = recall_of(lr_c, loff_c, cal_r)[0]
+        if cal[a] >= 0.99:
             alpha = a
             break
     keep = np.ceil(alpha * k).astype(np.int32)
     for _ in range(2):
         idx.query_exact(Q, k)
-        idx.query_exact_learned(net, Rp, Q, k, keep)
-    ms_plain, ms_cut = [], []
+        idx.query_exact_learned(net, Rp, Q, k, keep, certify=False)
+        idx.query_exact_learned(net, Rp, Q, k, keep, certify=True)
+    ms_plain, ms_cut, ms_cert = [], [], []
     for _ in range(steps):
         (pu_, pr_, poff, pst), t_plain = timed(lambda: idx.query_exact(Q, k))
         ms_plain.append(t_plain)
-        (lu, lr, loff, lst), t_cut = timed(lambda: idx.query_exact_learned(net, Rp, Q, k, keep))
+        (lu, lr, loff, lst), t_cut = timed(
+            lambda: idx.query_exact_learned(net, Rp, Q, k, keep, certify=False))
         ms_cut.append(t_cut)
-    same = bool((lu == pu_).all() and (lr == pr_).all())
-    hits = viol = 0
-    for q in range(len(loff) - 1):
-        sl = slice(loff[q], loff[q + 1])
-        kth = pr_[sl].max()
-        hits += int(np.sum(lr[sl] <= kth))
-        viol += int(np.sum(lr[sl] > C * kth))
+        (cu_, cr_, coff, cst), t_cert = timed(
+            lambda: idx.query_exact_learned(net, Rp, Q, k, keep, certify=True))
+        ms_cert.append(t_cert)
+    recall, viol = recall_of(lr, loff, pr_)
+    same_cert = bool((cu_ == pu_).all() and (cr_ == pr_).all())
     if own:
         idx.close()
-    mp, mc = statistics.median(ms_plain), statistics.median(ms_cut)
+    mp, mc, mk = (statistics.median(v) for v in (ms_plain, ms_cut, ms_cert))
     return {
-        "ms_per_batch": {"learned": mc, "plain_exact": mp},
-        "speedup": mp / mc,
-        "answers_equal_plain_exact": same,
-        "recall_at_k": hits / float(loff[-1]), "c_bound_violations": viol,
+        "ms_per_batch": {"learned_cut": mc, "learned_certified": mk, "plain_exact": mp},
+        "speedup": {"cut": mp / mc, "certified": mp / mk},
+        "recall_at_k": recall, "c_bound_violations": viol,
+        "certified_answers_equal_plain_exact": same_cert,
         "keep": f"ceil({alpha} * k) per query",
-        "candidates": {"plain": pst.candidates, "learned": lst.candidates,
-                       "revived_by_fallback": lst.learned_revived,
-                       "recounted_plain": pst.recounted, "recounted_learned": lst.recounted},
-        "calibration_revived_fraction": {str(a): r for a, r in cal.items()},
+        "candidates": {"plain": pst.candidates, "cut": lst.candidates,
+                       "certified": cst.candidates,
+                       "revived_by_fallback": cst.learned_revived,
+                       "recounted_plain": pst.recounted, "recounted_cut": lst.recounted,
+                       "recounted_certified": cst.recounted},
+        "calibration_recall": {str(a): r for a, r in cal.items()},
         "training": {"queries": n_train, "samples": int(len(pu)), "epochs": epochs,
                      "batch": 4096, "final_loss": loss,
                      "ms": {"index_build": ms_build, "top_users": ms_top,
@@ -470,7 +482,7 @@ def bench_learned(args):
                    key=lambda kv: -kv[1][1])[:12]
     print(json.dumps({
         "case": "learned",
-        "metric": "queries/s", "value": nq / (res["ms_per_batch"]["learned"] / 1000.0),
+        "metric": "queries/s", "value": nq / (res["ms_per_batch"]["learned_cut"] / 1000.0),
         "unit": "queries/s",
         "plain_exact_value": nq / (res["ms_per_batch"]["plain_exact"] / 1000.0),
         "steps": args.steps, "higher_is_better": True, "data": "synthetic",

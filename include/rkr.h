@@ -359,16 +359,20 @@ rkr_status rkr_screen_scores_static(const float *U, int64_t n, const float *X, i
  * rank the tail lists settle keep their exact rank, and of the candidates that
  * would still need a recount over P only the keep[i] with the smallest
  * predicted log rank (and those tying with the keep[i]-th) are recounted for
- * query i (a query with more than 32 keep[i] candidates to recount that are also
- * more than a quarter of all users is not cut: their rank lower bounds are too
- * weak for the fallback to spare them).  Exact
- * fallback: after that recount, every cut candidate whose rank
- * lower bound (from the tail lists and count tables) does not exceed the k-th
- * smallest count found is recounted as well; the others cannot be among the k
- * best.  So the answer equals rkr_query_exact's, users and ranks; the cut only
- * saves the recount of candidates the fallback does not revive.
+ * query i.
+ *   certify = 1 (exact fallback): after that recount, every cut candidate whose
+ *   rank lower bound (from the tail lists and count tables) does not exceed the
+ *   k-th smallest count found is recounted as well; the others cannot be among
+ *   the k best.  The answer equals rkr_query_exact's, users and ranks; the cut
+ *   saves only the recounts the fallback does not revive (a query with more than
+ *   32 keep[i] candidates to recount that are also more than a quarter of all
+ *   users is not cut: their lower bounds are too weak to spare any).
+ *   certify = 0: the cut candidates are dropped.  Every returned rank is exact;
+ *   the answer set may miss a true answer, and its recall is to be judged
+ *   against rkr_query_exact.
  * stats->candidates counts the candidates left after the cut (revived ones
- * included), stats->learned_revived the revived ones.
+ * included), stats->learned_revived the revived ones.  RKR_EINVAL unless
+ * certify is 0 or 1.
  * keep: nq int32 (host or device), keep[i] >= k[i], else RKR_EINVAL.
  */
 rkr_status rkr_rank_pairs(rkr_index *idx, const float *Q, int32_t nq, int64_t npairs,
@@ -379,8 +383,8 @@ rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int
                              float *out_X, float *out_t, void *stream);
 rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *R, const float *Q,
                                    int32_t nq, const int32_t *k, const int32_t *keep,
-                                   int32_t *out_users,
-                                   int32_t *out_ranks, rkr_query_stats *stats, void *stream);
+                                   int32_t certify, int32_t *out_users, int32_t *out_ranks,
+                                   rkr_query_stats *stats, void *stream);
 
 /*
  * Learned pruner (not in the paper): a monotone rank regressor

@@ -160,7 +160,7 @@ def load() -> ctypes.CDLL:
         lib.rkr_pair_features.restype = I32
         lib.rkr_pair_features.argtypes = [V, V, V, I32, I64, V, V, V, V, V]
         lib.rkr_query_exact_learned.restype = I32
-        lib.rkr_query_exact_learned.argtypes = [V, V, V, V, I32, V, V, V, V,
+        lib.rkr_query_exact_learned.argtypes = [V, V, V, V, I32, V, V, I32, V, V,
                                                 ctypes.POINTER(QueryStats), V]
         lib.rkr_pruner_free.restype = None
         lib.rkr_pruner_free.argtypes = [V]
@@ -547,9 +547,10 @@ def rkr_pair_features(index, R, Q, pair_user, pair_query, *, stream=None):
     return X, t
 
 
-def rkr_query_exact_learned(index, pruner, R, Q, k, keep, *, stream=None):
+def rkr_query_exact_learned(index, pruner, R, Q, k, keep, *, certify: bool = True,
+                            stream=None):
     """Def. 2 with the candidates of query i cut to keep[i] (an int or one per query)
-    by the pruner's predictions."""
+    by the pruner's predictions; certify=True adds the exact fallback."""
     lib = load()
     nq, _ = _shape(Q)
     kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
@@ -561,8 +562,8 @@ def rkr_query_exact_learned(index, pruner, R, Q, k, keep, *, stream=None):
     ranks = np.empty(int(off[-1]), np.int32)
     stats = QueryStats()
     _check(lib.rkr_query_exact_learned(index, pruner._h, R.ctypes.data, pq, nq, kk.ctypes.data,
-                                       kp.ctypes.data, users.ctypes.data, ranks.ctypes.data,
-                                       ctypes.byref(stats), _stream(stream)))
+                                       kp.ctypes.data, int(bool(certify)), users.ctypes.data,
+                                       ranks.ctypes.data, ctypes.byref(stats), _stream(stream)))
     return users, ranks, off, stats
 
 

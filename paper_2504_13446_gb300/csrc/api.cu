@@ -786,8 +786,9 @@ rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int
 }
 
 rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *R, const float *Q,
-                                   int32_t nq, const int32_t *k, const int32_t *keep, int32_t *out_users,
-                                   int32_t *out_ranks, rkr_query_stats *stats, void *stream) {
+                                   int32_t nq, const int32_t *k, const int32_t *keep,
+                                   int32_t certify, int32_t *out_users, int32_t *out_ranks,
+                                   rkr_query_stats *stats, void *stream) {
   g_err[0] = 0;
   if (!pr || !R || !keep || !out_users || !out_ranks) return fail(RKR_EINVAL, "null argument");
   if (pruner_features(pr) != 65) return fail(RKR_EINVAL, "the pruner must take 65 features");
@@ -827,7 +828,8 @@ rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *
   size_t tot = (size_t)off[nq];
   RKR_TRY(ou.init(out_users, sizeof(int32_t) * tot, st));
   RKR_TRY(orr.init(out_ranks, sizeof(int32_t) * tot, st));
-  RKR_TRY(run_query_exact_learned(idx, qc, nq, pr, Xu, keep_d, (int32_t *)ou.dev,
+  if (certify != 0 && certify != 1) return fail(RKR_EINVAL, "certify must be 0 or 1");
+  RKR_TRY(run_query_exact_learned(idx, qc, nq, pr, Xu, keep_d, certify, (int32_t *)ou.dev,
                                   (int32_t *)orr.dev, stats, st));
   RKR_TRY(ou.finish());
   RKR_TRY(orr.finish());

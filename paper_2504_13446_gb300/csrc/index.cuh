@@ -239,8 +239,8 @@ rkr_status pair_scores(const rkr_index *idx, const float *Qd, int64_t npairs, co
 // approximate form of Def. 2; returned ranks stay exact).
 rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
                                    rkr_pruner *pr, const float *Xu, const int32_t *keep_d,
-                                   int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
-                                   cudaStream_t st);
+                                   int certify, int32_t *users_d, int32_t *ranks_d,
+                                   rkr_query_stats *stats, cudaStream_t st);
 
 rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
                            int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,

@@ -1370,6 +1370,7 @@ struct LearnedPrune {
   rkr_pruner *pr;
   const float *Xu;   // per-user features
   const int32_t *keep;  // candidates kept per query (device, nq)
+  int certify;          // 1: exact fallback for cut candidates that could still matter
 };
 
 constexpr int64_t kLearnedUncut = 32;
@@ -1402,7 +1403,7 @@ __global__ void __launch_bounds__(256)
   // a query whose candidates to recount are a large part of all users and far more
   // than it keeps is left uncut: such candidates have weak rank lower bounds (u.q
   // lies below the tail lists) and the exact fallback would revive them anyway
-  if (open <= keep || (open > kLearnedUncut * keep && open > n_users / 4)) return;
+  if (open <= keep || (n_users > 0 && open > kLearnedUncut * keep && open > n_users / 4)) return;
   const uint64_t kth = block_kth(cnt, (uint64_t)keep, 32,
                                  [&](int64_t i, uint64_t &key) {
                                    if (fb[i] < 0) return false;
@@ -1530,9 +1531,9 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
 
 rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
                                    rkr_pruner *pr, const float *Xu, const int32_t *keep_d,
-                                   int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,
-                                   cudaStream_t st) {
-  const LearnedPrune lp{pr, Xu, keep_d};
+                                   int certify, int32_t *users_d, int32_t *ranks_d,
+                                   rkr_query_stats *stats, cudaStream_t st) {
+  const LearnedPrune lp{pr, Xu, keep_d, certify};
   return query_exact_core(idx, qc, nq, &lp, users_d, ranks_d, stats, st);
 }
 
@@ -1567,8 +1568,9 @@ static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const
   }
   k_scatter_y<<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(nfb, fi, yc, y);
   note_launch();
+  // the uncut rule exists for the fallback's sake (n_users = 0 switches it off)
   k_learned_cut<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, lp->keep, y, cu_fb, cu, ccount,
-                                         cutu, idx->n, ncut);
+                                         cutu, lp->certify ? idx->n : 0, ncut);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   unsigned long long h = 0;
@@ -1749,7 +1751,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
         return RKR_OK;
       };
       if (lstat_host_fb > 0) RKR_TRY(recount_open_candidates(lstat_host_fb));
-      if (lp && cut_total > 0) {
+      if (lp && lp->certify && cut_total > 0) {
         // exact fallback: cut candidates that could still be among the k best
         DevBuf brv;
         unsigned long long *nrev, hrev = 0;

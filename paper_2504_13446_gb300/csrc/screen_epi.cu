@@ -512,23 +512,43 @@ __global__ void __launch_bounds__(kGroupThreads)
     }
     return jlo == jhi ? jlo : exact_j_near((double)v, g0, dx, jlo, jhi);
   };
+  // Most entries lie just above x_0 (on the bench data about 80 % fall in the
+  // first four columns of the count grid): a warp counts those columns with
+  // ballots, one shared atomic per column, and only the rest with per-entry
+  // atomics, which would otherwise serialize on a handful of addresses.
+  const int lane_g = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < kGroupPer; ++k) {
     const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
-    if (i >= L) break;
-    const uint2 e = ent[k];
-    const float v = __uint_as_float(e.y);
-    const float b = tc::screen_bound_tc(ru, tileb[e.x >> bn_shift], gacc, gcan);
-    bm = fmaxf(bm, b);
-    int clo, chi;
-    bin_interval(xb, g0, kXG, __fsub_rd(v, b), __fadd_ru(v, b), clo, chi);
-    if (chi > 0) {
-      atomicAdd(&hlo[clo], 1u);
-      atomicAdd(&hhi[chi], 1u);
+    const bool live = i < L;
+    if (!__any_sync(0xffffffffu, live)) break;
+    int clo = -1, chi = -1;
+    if (live) {
+      const uint2 e = ent[k];
+      const float v = __uint_as_float(e.y);
+      const float b = tc::screen_bound_tc(ru, tileb[e.x >> bn_shift], gacc, gcan);
+      bm = fmaxf(bm, b);
+      int jl, jh;
+      bin_interval(xb, g0, kXG, __fsub_rd(v, b), __fadd_ru(v, b), jl, jh);
+      if (jh > 0) {
+        clo = jl;
+        chi = jh;
+      }
+      const int col = list_col(v);
+      cols[i] = (uint16_t)col;
+      atomicAdd(&cnt[col], 1u);
     }
-    const int col = list_col(v);
-    cols[i] = (uint16_t)col;
-    atomicAdd(&cnt[col], 1u);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const unsigned ml = __ballot_sync(0xffffffffu, clo == c);
+      const unsigned mh = __ballot_sync(0xffffffffu, chi == c);
+      if (lane_g == 0) {
+        if (ml) atomicAdd(&hlo[c], (uint32_t)__popc(ml));
+        if (mh) atomicAdd(&hhi[c], (uint32_t)__popc(mh));
+      }
+    }
+    if (clo >= 4) atomicAdd(&hlo[clo], 1u);
+    if (chi >= 4) atomicAdd(&hhi[chi], 1u);
   }
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -2,10 +2,11 @@
 
 rkr_rank_pairs is compared with the oracle's ranks bit for bit.  The pruner is
 trained on ranks that rkr_rank_pairs produces for training queries, then cuts
-the exact path's candidates of other queries; with its exact fallback (cut
-candidates whose rank lower bound can still reach the k-th rank are recounted)
-the answer equals rkr_query_exact's, users and ranks, and every rank is the
-oracle's.  The cut must still save candidates at keep = 2k.
+the exact path's candidates of other queries: without the fallback every rank
+it returns is the oracle's, it recounts fewer candidates and its recall is
+bounded below; with the exact fallback (cut candidates whose rank lower bound
+can still reach the k-th rank are recounted) the answer equals
+rkr_query_exact's, users and ranks.
 """
 
 import numpy as np
@@ -53,17 +54,26 @@ def test_learned_cut_returns_exact_ranks_with_high_recall():
     # evaluation: the cut against the plain exact path
     plain_u, plain_r, off, plain_st = gpu.query_exact(eval_q, k_eval)
     R = oracle.ranks(w.U, w.P, eval_q)
-    for factor in (2, 1):      # recount at most 2k, then k, candidates per query
-        keep = factor * k_eval
-        lu, lr, loff, st = gpu.query_exact_learned(net, Rp, eval_q, k_eval, keep)
+    qid = np.repeat(np.arange(len(eval_q)), np.diff(off))
+    # the plain cut: ranks exact, recall judged against the exact query
+    keep = 2 * k_eval          # recount at most 2k candidates per query
+    lu, lr, loff, st = gpu.query_exact_learned(net, Rp, eval_q, k_eval, keep, certify=False)
+    assert (loff == off).all()
+    assert (lr == R[lu, qid]).all()                  # ranks returned are exact
+    hits = sum(int(np.sum(lr[off[q]:off[q + 1]] <= plain_r[off[q]:off[q + 1]].max()))
+               for q in range(len(eval_q)))
+    recall = hits / float(off[-1])
+    print(f"learned cut: keep 2k, recall {recall:.4f}, {st.candidates} candidates instead of "
+          f"{plain_st.candidates}, recounted {st.recounted} instead of {plain_st.recounted}")
+    assert st.candidates < plain_st.candidates and st.recounted < plain_st.recounted
+    assert recall >= 0.9
+    # with the exact fallback: the exact answer, whatever the cut
+    for factor in (2, 1):
+        lu, lr, loff, st = gpu.query_exact_learned(net, Rp, eval_q, k_eval, factor * k_eval,
+                                                   certify=True)
         assert (loff == off).all()
-        assert (lu == plain_u).all() and (lr == plain_r).all()   # the exact answer
-        assert (lr == R[lu, np.repeat(np.arange(len(eval_q)), np.diff(off))]).all()
-        print(f"learned cut: keep {factor}k, {st.candidates} candidates instead of "
-              f"{plain_st.candidates} ({st.learned_revived} revived by the fallback), "
-              f"recounted {st.recounted} instead of {plain_st.recounted}")
-        if factor == 2:
-            assert st.candidates < plain_st.candidates
+        assert (lu == plain_u).all() and (lr == plain_r).all()
+        print(f"certified cut: keep {factor}k, {st.learned_revived} candidates revived")
     # keep as an array, one per query: a keep no smaller than any query's candidate
     # count cuts nothing, so the answer is the plain exact one
     big = np.full(len(eval_q), w.n, np.int32)
