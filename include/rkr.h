@@ -433,6 +433,13 @@ void rkr_pruner_free(rkr_pruner *pr);
  *   latency_ctas_per_sm  CTAs per SM of the one-at-a-time scan, 0 = occupancy maximum
  *   latency_bulk     1: the one-at-a-time scan stages rows of U in shared memory with
  *                    bulk copies (d a multiple of 4); 0: direct vector loads
+ *   rc_seg_min       0: the recount screens one row per candidate (user, query); k >= 2:
+ *                    a user with at least k candidates is screened once per segment of
+ *                    up to 32 of its thresholds, counted together in the epilogue
+ *   screen_form      tensor-core screens over row-owned work (index build, recount):
+ *                    0 one CTA per SM; 1 CTA pairs sharing each B chunk by cluster
+ *                    multicast; 2 CTA pairs issuing 2-SM MMAs (M = 256), each CTA
+ *                    staging half of B.  The multicast-free build runs every form as 0.
  * rkr_tuning_set validates every field (RKR_EINVAL) and applies to calls that start
  * after it returns; rkr_tuning_get reads the current values.
  *
@@ -453,6 +460,8 @@ typedef struct {
   int32_t cand_budget_log2;
   int32_t latency_ctas_per_sm;
   int32_t latency_bulk;
+  int32_t screen_form;
+  int32_t rc_seg_min;
 } rkr_tuning;
 rkr_status rkr_tuning_get(rkr_tuning *out);
 rkr_status rkr_tuning_set(const rkr_tuning *in);

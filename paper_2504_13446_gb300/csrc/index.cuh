@@ -143,13 +143,19 @@ rkr_status tc_skim(const rkr_index *idx, const TcSide &Ut, const TcSide &Qt, con
 // With hist_hi (bounds mode) nothing is queued: undecided items give count intervals.
 // split = 0 screens with the single BF16 product (bounds mode only: wider count
 // intervals for a third of the tensor work); the exact mode always splits.
+// Segments of one threshold pass seg_self (the item equal to the query, or -1);
+// segments of several thresholds (up to kRecountSeg) pass self_col / self_pos
+// instead: per candidate slot of the segment, the columns of items equal to a
+// threshold's query in ascending order (-1 after the last) and the number of the
+// segment's thresholds below each such item's score.
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
                       const int32_t *seg_user, const int32_t *seg_self, const double *ths,
                       uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined,
-                      int split = 1);
+                      int split = 1, const int32_t *self_col = nullptr,
+                      const int32_t *self_pos = nullptr);
 constexpr int kXGrid = 128;
-constexpr int kRecountSeg = 1;      // thresholds per recount segment (one per screen row)
+constexpr int kRecountSeg = 32;     // thresholds per recount segment (one per screen row)
 constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)
 constexpr int kListG = 1024;        // columns of the list grid (finer than the count grid)
 rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStream_t st);

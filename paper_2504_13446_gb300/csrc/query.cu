@@ -372,9 +372,15 @@ __global__ void k_cand_theta(int64_t count, const int32_t *__restrict__ cu,
   val[i] = (int32_t)i;
 }
 
-// Segments of equal user in the sorted order: start index and length (runs
-// longer than kRecountSeg are cut).
-__global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
+// Segments of equal user in the sorted order: start index and length.  A user
+// with fewer than seg_min thresholds (or every user, seg_min = 0) gets one
+// segment per threshold; a longer run is cut into near-equal segments of at
+// most kRecountSeg.  Segments
+// of one threshold take slots from the front of [0, count), longer ones from
+// the back, so that each kind is one range for its recount screen; seg_len of
+// the slots between stays 0.
+// nseg[0] = front slots, nseg[1] = distinct users, nseg[2] = back slots.
+__global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi, int seg_min,
                            unsigned long long *__restrict__ nseg, int64_t *__restrict__ seg_start,
                            int32_t *__restrict__ seg_len) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -383,32 +389,68 @@ __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi,
   atomicAdd(&nseg[1], 1ull);   // distinct users
   int64_t e = i + 1;
   while (e < count && key_hi[e] == key_hi[i]) ++e;
-  // a user's run is cut into segments of at most kRecountSeg thresholds, which
-  // the recount screen keeps in registers
-  for (int64_t a = i; a < e; a += kRecountSeg) {
-    unsigned long long slot = atomicAdd(nseg, 1ull);
+  const int64_t run = e - i;
+  if (seg_min == 0 || run < seg_min) {   // one row per threshold
+    for (int64_t a = i; a < e; ++a) {
+      const int64_t slot = (int64_t)atomicAdd(&nseg[0], 1ull);
+      seg_start[slot] = a;
+      seg_len[slot] = 1;
+    }
+    return;
+  }
+  // pieces of nearly equal length, at most kRecountSeg each
+  const int64_t np = (run + kRecountSeg - 1) / kRecountSeg;
+  for (int64_t p = 0; p < np; ++p) {
+    const int64_t a = i + run * p / np, b = i + run * (p + 1) / np;
+    const int64_t slot = count - 1 - (int64_t)atomicAdd(&nseg[2], 1ull);
     seg_start[slot] = a;
-    seg_len[slot] = (int32_t)(e - a < kRecountSeg ? e - a : kRecountSeg);
+    seg_len[slot] = (int32_t)(b - a);
   }
 }
 
 // Per segment: its user, its thresholds in sorted order, and a zeroed histogram
-// of L + 1 slots at hist[2 st0] (segments are disjoint since L >= 1).
+// of L + 1 slots at hist[2 st0] (segments are disjoint since L >= 1).  A
+// one-threshold segment records the item tying exactly with its u.q (the query
+// itself when it is an item of P) in seg_self; a longer one lists such items
+// of all its thresholds in self_col (ascending, each once, -1 after the last),
+// each with its exact position in self_pos: its canonical score is its query's
+// threshold, so it exceeds exactly the thresholds below that one.
 __global__ void k_seg_prep(int64_t nseg, const int64_t *__restrict__ seg_start,
                            const int32_t *__restrict__ seg_len, const uint64_t *__restrict__ key_hi,
                            const int32_t *__restrict__ order, const double *__restrict__ th,
                            const int32_t *__restrict__ cq, const int32_t *__restrict__ qself,
                            int32_t *__restrict__ seg_user, int32_t *__restrict__ seg_self,
-                           double *__restrict__ ths, uint32_t *__restrict__ hist) {
+                           double *__restrict__ ths, uint32_t *__restrict__ hist,
+                           int32_t *__restrict__ self_col, int32_t *__restrict__ self_pos) {
   int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (sg >= nseg) return;
+  const int L = seg_len[sg];
+  if (L == 0) return;   // a slot between the two ranges
   int64_t st0 = seg_start[sg];
-  int L = seg_len[sg];
   seg_user[sg] = (int32_t)key_hi[st0];
-  // one-threshold segments: the item tying exactly with that candidate's u.q
   seg_self[sg] = L == 1 ? qself[cq[order[st0]]] : -1;
   for (int i = 0; i < L; ++i) ths[st0 + i] = th[order[st0 + i]];
   for (int i = 0; i <= L; ++i) hist[2 * st0 + i] = 0;
+  if (L == 1) return;
+  int32_t *sc = self_col + st0, *sp = self_pos + st0;
+  int ns = 0;
+  for (int i = 0; i < L; ++i) {
+    const int32_t c = qself[cq[order[st0 + i]]];
+    if (c < 0) continue;
+    int pos = i;
+    while (pos > 0 && ths[st0 + pos - 1] == ths[st0 + i]) --pos;
+    int at = ns;
+    while (at > 0 && sc[at - 1] > c) --at;
+    if (at > 0 && sc[at - 1] == c) continue;   // the same item for an equal query
+    for (int j = ns; j > at; --j) {
+      sc[j] = sc[j - 1];
+      sp[j] = sp[j - 1];
+    }
+    sc[at] = c;
+    sp[at] = pos;
+    ++ns;
+  }
+  for (int j = ns; j < L; ++j) sc[j] = -1;
 }
 
 // hist[pos] counts items whose score exceeds exactly the first pos thresholds;
@@ -416,7 +458,7 @@ __global__ void k_seg_prep(int64_t nseg, const int64_t *__restrict__ seg_start,
 __global__ void k_seg_suffix(int64_t nseg, const int64_t *__restrict__ seg_start,
                              const int32_t *__restrict__ seg_len, uint32_t *__restrict__ hist) {
   int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (sg >= nseg) return;
+  if (sg >= nseg || seg_len[sg] == 0) return;
   uint32_t *h = hist + 2 * seg_start[sg];
   uint32_t run = 0;
   for (int i = seg_len[sg]; i >= 1; --i) {
@@ -432,8 +474,9 @@ __global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_s
                                  const uint32_t *__restrict__ hist, uint32_t *__restrict__ ccount) {
   int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (sg >= nseg) return;
-  int64_t st0 = seg_start[sg];
   int L = seg_len[sg];
+  if (L == 0) return;
+  int64_t st0 = seg_start[sg];
   const uint32_t *h = hist + 2 * st0;
   for (int i = 0; i < L; ++i) ccount[order[st0 + i]] = h[i + 1];
 }
@@ -1141,7 +1184,7 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   RKR_TRY(tmp_alloc(b6, &slen, cnt, st));
   RKR_TRY(tmp_alloc(b7, &hist, 2 * cnt, st));
   RKR_TRY(tmp_alloc(b8, &ths, cnt, st));
-  RKR_TRY(tmp_alloc(b9, &nseg_d, 2, st));
+  RKR_TRY(tmp_alloc(b9, &nseg_d, 3, st));
   {
     const int prof_slot = prof_begin("k_cand_theta", st);
     k_cand_theta<<<(unsigned)((Np2 + bs - 1) / bs), bs, 0, st>>>(cnt, cu, cq, idx->U, Qd, idx->d,
@@ -1151,21 +1194,26 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   note_launch();
   RKR_CUDA(cudaGetLastError());
   RKR_TRY(bitonic_sort(Sort128{khi, klo, val}, Np2, "k_sort<128>", st));
-  RKR_CUDA(cudaMemsetAsync(nseg_d, 0, 2 * sizeof(unsigned long long), st));
-  k_segments<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, khi, nseg_d, sstart, slen);
+  RKR_CUDA(cudaMemsetAsync(nseg_d, 0, 3 * sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(slen, 0, sizeof(int32_t) * cnt, st));
+  k_segments<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(cnt, khi, tuning().rc_seg_min,
+                                                              nseg_d, sstart, slen);
   note_launch();
   RKR_CUDA(cudaGetLastError());
-  unsigned long long segu[2] = {0, 0};
+  unsigned long long segu[3] = {0, 0, 0};
   RKR_CUDA(cudaMemcpyAsync(segu, nseg_d, sizeof(segu), cudaMemcpyDeviceToHost, st));
   RKR_CUDA(cudaStreamSynchronize(st));
-  const unsigned long long nseg = segu[0];
+  const int64_t n1 = (int64_t)segu[0], n2 = (int64_t)segu[2], off2 = cnt - n2;
   if (nusers) *nusers += (int64_t)segu[1];
-  DevBuf b10, b11;
-  int32_t *suser, *sself;
-  RKR_TRY(tmp_alloc(b10, &suser, nseg, st));
-  RKR_TRY(tmp_alloc(b11, &sself, nseg, st));
-  k_seg_prep<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>(
-      (int64_t)nseg, sstart, slen, khi, val, th, cq, qself, suser, sself, ths, hist);
+  // per segment slot (front range: one threshold; back range: several)
+  DevBuf b10, b11, b12, b13;
+  int32_t *suser, *sself, *scol, *spos;
+  RKR_TRY(tmp_alloc(b10, &suser, cnt, st));
+  RKR_TRY(tmp_alloc(b11, &sself, cnt, st));
+  RKR_TRY(tmp_alloc(b12, &scol, cnt, st));
+  RKR_TRY(tmp_alloc(b13, &spos, cnt, st));
+  k_seg_prep<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, st>>>(
+      cnt, sstart, slen, khi, val, th, cq, qself, suser, sself, ths, hist, scol, spos);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   int64_t refined[2] = {0, 0};
@@ -1179,9 +1227,19 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     ProfScope prof(clb_all ? (split ? "span:recount(bounds,split)" : "span:recount(bounds,single)")
                            : "span:recount(exact)",
                    st, 0.0);
-    RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, (int64_t)nseg, cnt, sstart, slen, suser, sself,
-                       ths, hist, hist_hi, st, refined, split));
+    if (n1 > 0)
+      RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, n1, cnt, sstart, slen, suser, sself, ths, hist,
+                         hist_hi, st, refined, split));
+    if (n2 > 0) {
+      int64_t ref2[2] = {0, 0};
+      RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, n2, cnt, sstart + off2, slen + off2,
+                         suser + off2, sself + off2, ths, hist, hist_hi, st, ref2, split, scol,
+                         spos));
+      refined[0] += ref2[0];
+      refined[1] += ref2[1];
+    }
   }
+  const int64_t nseg = cnt;   // the kernels below walk every slot and skip the empty ones
   {
     const int prof_slot = prof_begin("k_seg_suffix", st);
     k_seg_suffix<<<(unsigned)((nseg + bs - 1) / bs), bs, 0, st>>>((int64_t)nseg, sstart, slen,

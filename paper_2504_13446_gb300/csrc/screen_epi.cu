@@ -32,6 +32,27 @@ __device__ __forceinline__ double dkey_inverse(uint64_t k) {
   return __longlong_as_double((long long)b);
 }
 
+// The bound terms of a column tile, loaded one tile ahead: take(ct) returns
+// tile ct's terms (prefetched when ct is the tile expected next) and starts the
+// load of tile ct + 1, whose latency then overlaps the current tile's work.
+struct TilePrefetch {
+  tc::RowBound next;
+  int nct;   // the column tile `next` holds
+  __device__ __forceinline__ void start(const tc::RowBound *tileb, int ct) {
+    nct = ct;
+    next = tileb[ct];
+  }
+  __device__ __forceinline__ tc::RowBound take(const tc::RowBound *tileb, int ct, int64_t ncols,
+                                               int bn) {
+    const tc::RowBound cur = ct == nct ? next : tileb[ct];
+    if ((int64_t)(ct + 1) * bn < ncols) {
+      nct = ct + 1;
+      next = tileb[ct + 1];
+    }
+    return cur;
+  }
+};
+
 // Queue of (row, column) pairs with a capacity; overflow raises a flag.
 struct PairQueue {
   int2 *items;
@@ -73,6 +94,8 @@ struct EpiFb {
   struct Thread {
     float b, mxlo, mnhi;
     int64_t row;
+    tc::RowBound ru;     // the row's bound terms
+    TilePrefetch tp;     // the bound terms of the next column tile
   };
   static constexpr size_t kSmem = 0;
   int64_t nrows, ncols;
@@ -87,6 +110,8 @@ struct EpiFb {
                                              Thread &ts) const {
     ts.mxlo = -INFINITY;
     ts.mnhi = INFINITY;
+    ts.row = -1;
+    ts.tp.start(tileb, u.ct0);
     if (seed) {
       const int w = (et >> 5) + 2, lane = et & 31;
       const int64_t row = (int64_t)u.rb0 * tc::BM + (w & 3) * 32 + lane;
@@ -99,8 +124,11 @@ struct EpiFb {
   }
   __device__ __forceinline__ void tile_begin(char *, int rb, int ct, int r, int,
                                              Thread &ts) const {
-    ts.row = (int64_t)rb * tc::BM + r;
-    ts.b = ts.row < nrows ? tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan) : 0.0f;
+    const int64_t row = (int64_t)rb * tc::BM + r;
+    if (row != ts.row && row < nrows) ts.ru = rowb[row];   // once per row
+    ts.row = row;
+    const tc::RowBound tb = ts.tp.take(tileb, ct, ncols, bn);
+    ts.b = ts.row < nrows ? tc::screen_bound_tc(ts.ru, tb, gacc, gcan) : 0.0f;
   }
   __device__ __forceinline__ void chunk(char *, int, int ct, int, int col, uint32_t,
                                         const float (&v)[32], Thread &ts) const {
@@ -348,14 +376,17 @@ __global__ void k_xgrid(int64_t n, const double *__restrict__ fmin,
 struct EpiXT {
   static const char *name() { return "k_screen<EpiXT>"; }
   struct Thread {
-    float skip, b;
+    float skip, b, g0;
     int64_t row;
     int64_t off;
     uint32_t cap;
+    tc::RowBound ru;     // the row's bound terms
+    TilePrefetch tp;     // the bound terms of the next column tile
   };
-  // list cursors of the block's 128 rows, then a 32 x 33 staging tile per warp
+  // list cursors of the block's 128 rows, then a 32 x 32 staging tile per warp
+  // stored [column][lane] (a lane's lookups hit its own bank)
   static constexpr size_t kStageOff = sizeof(uint32_t) * 128;
-  static constexpr size_t kSmem = kStageOff + sizeof(float) * 8 * 32 * 33;
+  static constexpr size_t kSmem = kStageOff + sizeof(float) * 8 * 32 * 32;
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
@@ -369,16 +400,24 @@ struct EpiXT {
   const uint32_t *lcapv;
   uint32_t *lcnt;      // n: entries (> capacity marks an overflow)
   __device__ uint32_t *lslot(char *S) const { return (uint32_t *)S; }
-  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &) const {
+  __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &ts) const {
     if (et < 128) lslot(S)[et] = 0;
+    ts.row = -1;
+    ts.tp.start(tileb, u.ct0);
   }
   __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
-    ts.row = (int64_t)rb * tc::BM + r;
+    const int64_t row = (int64_t)rb * tc::BM + r;
+    if (row != ts.row && row < nrows) {   // the row's data, once per row
+      ts.ru = rowb[row];
+      ts.g0 = g0f[row];
+      ts.off = loff[row];
+      ts.cap = lcapv[row];
+    }
+    ts.row = row;
+    const tc::RowBound tb = ts.tp.take(tileb, ct, ncols, bn);
     if (ts.row < nrows) {
-      ts.b = tc::screen_bound_tc(rowb[ts.row], tileb[ct], gacc, gcan);
-      ts.skip = __fsub_rd(g0f[ts.row], ts.b);  // s_hat <= skip implies s <= x_0
-      ts.off = loff[ts.row];
-      ts.cap = lcapv[ts.row];
+      ts.b = tc::screen_bound_tc(ts.ru, tb, gacc, gcan);
+      ts.skip = __fsub_rd(ts.g0, ts.b);  // s_hat <= skip implies s <= x_0
     } else {
       ts.skip = INFINITY;
     }
@@ -390,11 +429,11 @@ struct EpiXT {
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
     const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
-    float *tile = (float *)(S + kStageOff) + warp * 32 * 33 + lane * 33;
+    float *tile = (float *)(S + kStageOff) + warp * 32 * 32 + lane;
     uint32_t mask = 0;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      tile[j] = v[j];
+      tile[j * 32] = v[j];
       mask |= (v[j] > ts.skip ? 1u : 0u) << j;
     }
     const int64_t left = ncols - c0;
@@ -404,7 +443,8 @@ struct EpiXT {
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      if (pos < ts.cap) list[ts.off + pos] = make_uint2((uint32_t)(c0 + j), __float_as_uint(tile[j]));
+      if (pos < ts.cap)
+        list[ts.off + pos] = make_uint2((uint32_t)(c0 + j), __float_as_uint(tile[j * 32]));
       ++pos;
     }
   }
@@ -512,43 +552,23 @@ __global__ void __launch_bounds__(kGroupThreads)
     }
     return jlo == jhi ? jlo : exact_j_near((double)v, g0, dx, jlo, jhi);
   };
-  // Most entries lie just above x_0 (on the bench data about 80 % fall in the
-  // first four columns of the count grid): a warp counts those columns with
-  // ballots, one shared atomic per column, and only the rest with per-entry
-  // atomics, which would otherwise serialize on a handful of addresses.
-  const int lane_g = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < kGroupPer; ++k) {
     const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
-    const bool live = i < L;
-    if (!__any_sync(0xffffffffu, live)) break;
-    int clo = -1, chi = -1;
-    if (live) {
-      const uint2 e = ent[k];
-      const float v = __uint_as_float(e.y);
-      const float b = tc::screen_bound_tc(ru, tileb[e.x >> bn_shift], gacc, gcan);
-      bm = fmaxf(bm, b);
-      int jl, jh;
-      bin_interval(xb, g0, kXG, __fsub_rd(v, b), __fadd_ru(v, b), jl, jh);
-      if (jh > 0) {
-        clo = jl;
-        chi = jh;
-      }
-      const int col = list_col(v);
-      cols[i] = (uint16_t)col;
-      atomicAdd(&cnt[col], 1u);
+    if (i >= L) break;
+    const uint2 e = ent[k];
+    const float v = __uint_as_float(e.y);
+    const float b = tc::screen_bound_tc(ru, tileb[e.x >> bn_shift], gacc, gcan);
+    bm = fmaxf(bm, b);
+    int clo, chi;
+    bin_interval(xb, g0, kXG, __fsub_rd(v, b), __fadd_ru(v, b), clo, chi);
+    if (chi > 0) {
+      atomicAdd(&hlo[clo], 1u);
+      atomicAdd(&hhi[chi], 1u);
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const unsigned ml = __ballot_sync(0xffffffffu, clo == c);
-      const unsigned mh = __ballot_sync(0xffffffffu, chi == c);
-      if (lane_g == 0) {
-        if (ml) atomicAdd(&hlo[c], (uint32_t)__popc(ml));
-        if (mh) atomicAdd(&hhi[c], (uint32_t)__popc(mh));
-      }
-    }
-    if (clo >= 4) atomicAdd(&hlo[clo], 1u);
-    if (chi >= 4) atomicAdd(&hhi[chi], 1u);
+    const int col = list_col(v);
+    cols[i] = (uint16_t)col;
+    atomicAdd(&cnt[col], 1u);
   }
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1012,14 +1032,17 @@ struct EpiTable {
   const uint32_t *w;        // weight of each sampled row
   uint32_t *W;              // n x (tau + 1)
   PairQueue q;
-  __device__ __forceinline__ void unit_begin(char *, const tc::Unit &, int, Thread &) const {}
+  __device__ __forceinline__ void unit_begin(char *, const tc::Unit &, int, Thread &ts) const {
+    ts.u = -1;
+  }
   __device__ __forceinline__ void tile_begin(char *, int rb, int, int r, int, Thread &ts) const {
-    ts.u = (int64_t)rb * tc::BM + r;
-    if (ts.u < nrows) {
-      ts.ru = rowb[ts.u];
-      ts.bf = binfp[ts.u];
-      ts.fm = fmin[ts.u];
+    const int64_t u = (int64_t)rb * tc::BM + r;
+    if (u != ts.u && u < nrows) {   // the row's data, once per row
+      ts.ru = rowb[u];
+      ts.bf = binfp[u];
+      ts.fm = fmin[u];
     }
+    ts.u = u;
   }
   __device__ __forceinline__ void chunk(char *, int, int ct, int, int col, uint32_t,
                                         const float (&v)[32], Thread &ts) const {
@@ -1069,17 +1092,19 @@ struct EpiTableSm {
   uint32_t wconst;          // the common weight of the sampled rows
   uint32_t *W;              // n x (tau + 1)
   PairQueue q;
-  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &) const {
+  __device__ void unit_begin(char *S, const tc::Unit &, int et, Thread &ts) const {
     uint32_t *H = (uint32_t *)S;
     for (int i = et; i < tc::BM * kBinWords; i += 256) H[i] = 0u;
+    ts.u = -1;
   }
   __device__ __forceinline__ void tile_begin(char *, int rb, int, int r, int, Thread &ts) const {
-    ts.u = (int64_t)rb * tc::BM + r;
-    if (ts.u < nrows) {
-      ts.ru = rowb[ts.u];
-      ts.bf = binfp[ts.u];
-      ts.fm = fmin[ts.u];
+    const int64_t u = (int64_t)rb * tc::BM + r;
+    if (u != ts.u && u < nrows) {   // the row's data, once per row
+      ts.ru = rowb[u];
+      ts.bf = binfp[u];
+      ts.fm = fmin[u];
     }
+    ts.u = u;
   }
   __device__ __forceinline__ void chunk(char *S, int, int ct, int r, int col, uint32_t,
                                         const float (&v)[32], Thread &ts) const {
@@ -1384,6 +1409,8 @@ struct EpiRC {
     int64_t self;                // item tying exactly with u.q (never above), or -1
     uint32_t *h, *hh;
     uint32_t clo, chi;           // items certainly / possibly above u.q
+    tc::RowBound ru;             // the row's bound terms
+    TilePrefetch tp;             // the bound terms of the next column tile
   };
   static constexpr size_t kSmem = 0;
   int64_t nseg, ncols;
@@ -1407,7 +1434,9 @@ struct EpiRC {
     ts.sg = (int64_t)u.rb0 * tc::BM + r;
     ts.clo = 0;
     ts.chi = 0;
+    ts.tp.start(tileb, u.ct0);
     if (ts.sg < nseg) {
+      ts.ru = rowb[ts.sg];
       const int64_t st0 = seg_start[ts.sg];
       const double t = ths[st0];
       ts.h = hist + 2 * st0;
@@ -1422,7 +1451,8 @@ struct EpiRC {
     }
   }
   __device__ __forceinline__ void tile_begin(char *, int, int ct, int, int, Thread &ts) const {
-    ts.b = ts.sg < nseg ? tc::screen_bound_tc(rowb[ts.sg], tileb[ct], gacc, gcan) : 0.0f;
+    const tc::RowBound tb = ts.tp.take(tileb, ct, ncols, bn);
+    ts.b = ts.sg < nseg ? tc::screen_bound_tc(ts.ru, tb, gacc, gcan) : 0.0f;
   }
   __device__ __forceinline__ void chunk(char *, int, int ct, int, int col, uint32_t,
                                         const float (&v)[32], Thread &ts) const {
@@ -1459,6 +1489,176 @@ struct EpiRC {
   }
 };
 
+
+// Several thresholds per row (segments of one user's candidates, at most
+// kRecountSeg, sorted ascending): the user's scores are compared with all of
+// them.  Per item, pos_lo = #{i : t_i certainly below the score} and pos_hi =
+// #{i : t_i possibly below it} (binary searches over the row's thresholds in
+// shared memory); the position histograms of the row give the counts after a
+// suffix sum.  Bounds mode histograms pos_lo and pos_hi; exact mode histograms
+// the items with pos_lo = pos_hi and queues the others.  Items scoring
+// certainly above every threshold are only counted, items certainly below all
+// of them skipped.  The item equal to a threshold's query (its canonical score
+// is that threshold) has a known position and is counted there.
+struct EpiRCm {
+  static const char *name() { return "k_screen<EpiRCm>"; }
+  static constexpr int kL = kRecountSeg;
+  struct Thread {
+    float b, t0, tl;     // bound; lowest threshold rounded down, highest rounded up
+    int64_t sg, st0;
+    int L;
+    uint32_t top;        // this thread's items certainly above every threshold
+    int scur, send;      // cursor over the segment's self columns
+    int64_t snext;       // next self column, or INT64_MAX
+    tc::RowBound ru;     // the row's bound terms
+    TilePrefetch tp;     // the bound terms of the next column tile
+  };
+  // Per warp a staging tile of 32 x 32 scores, then per row the thresholds
+  // (rounded down) and the pos_lo and pos_hi histograms.  Every table is stored
+  // index-major (element i of row r at i * 128 + r, the tile as [column][lane]),
+  // so the 32 lanes of a warp, which hold 32 rows, always hit 32 different
+  // banks whatever index each lane looks up.
+  static constexpr size_t kThrOff = sizeof(float) * 8 * 32 * 32;
+  static constexpr size_t kHloOff = kThrOff + sizeof(float) * 128 * kL;
+  static constexpr size_t kHhiOff = kHloOff + sizeof(uint32_t) * 128 * (kL + 1);
+  static constexpr size_t kSmem = kHhiOff + sizeof(uint32_t) * 128 * (kL + 1);
+  int64_t nseg, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  tc::Gacc gacc;
+  float gcan;
+  const int64_t *seg_start;
+  const int32_t *seg_len;
+  const double *ths;
+  const int32_t *self_col;   // per segment slot i: a self column (ascending), or -1
+  const int32_t *self_pos;   // its exact position among the thresholds
+  uint32_t *hist, *hist_hi;  // hist_hi null: exact mode
+  PairQueue q;
+  // row r's tables; element i at [i * 128]
+  __device__ static float *thr(char *S, int r) { return (float *)(S + kThrOff) + r; }
+  __device__ static uint32_t *hlo(char *S, int r) { return (uint32_t *)(S + kHloOff) + r; }
+  __device__ static uint32_t *hhi(char *S, int r) { return (uint32_t *)(S + kHhiOff) + r; }
+  // #{i < L : t[i] < x} over ascending t (stride 128)
+  __device__ static int count_below(const float *t, int L, float x) {
+    int a = 0, n = L;
+    while (n > 0) {
+      const int h = n >> 1;
+      if (t[(a + h) * 128] < x) { a += h + 1; n -= h + 1; } else { n = h; }
+    }
+    return a;
+  }
+  __device__ void next_self(Thread &ts) const {
+    ++ts.scur;
+    const int c = ts.scur < ts.send ? self_col[ts.scur] : -1;
+    ts.snext = c >= 0 ? (int64_t)c : INT64_MAX;
+  }
+  __device__ __forceinline__ void unit_begin(char *S, const tc::Unit &u, int et,
+                                             Thread &ts) const {
+    const int w = (et >> 5) + 2, lane = et & 31;
+    const int r = (w & 3) * 32 + lane, half = et >> 7;
+    ts.sg = (int64_t)u.rb0 * tc::BM + r;
+    ts.top = 0;
+    ts.L = 0;
+    ts.snext = INT64_MAX;
+    ts.tp.start(tileb, u.ct0);
+    if (ts.sg >= nseg) return;
+    ts.ru = rowb[ts.sg];
+    ts.st0 = seg_start[ts.sg];
+    ts.L = seg_len[ts.sg];
+    const double *t = ths + ts.st0;
+    ts.t0 = __double2float_rd(t[0]);
+    ts.tl = __double2float_ru(t[ts.L - 1]);
+    if (half == 0) {
+      float *tr = thr(S, r);
+      for (int i = 0; i < ts.L; ++i) tr[i * 128] = __double2float_rd(t[i]);
+      for (int i = 0; i <= ts.L; ++i) {
+        hlo(S, r)[i * 128] = 0;
+        hhi(S, r)[i * 128] = 0;
+      }
+    }
+    ts.scur = (int)ts.st0 - 1;
+    ts.send = (int)(ts.st0 + ts.L);
+    next_self(ts);
+  }
+  __device__ __forceinline__ void tile_begin(char *, int, int ct, int, int, Thread &ts) const {
+    const tc::RowBound tb = ts.tp.take(tileb, ct, ncols, bn);
+    ts.b = ts.sg < nseg ? tc::screen_bound_tc(ts.ru, tb, gacc, gcan) : 0.0f;
+  }
+  __device__ __forceinline__ void chunk(char *S, int, int ct, int r, int col, uint32_t,
+                                        const float (&v)[32], Thread &ts) const {
+    if (ts.L == 0) return;
+    const int64_t c0 = (int64_t)ct * bn + col;
+    // self columns before this chunk belong to the other half of the row
+    while (ts.snext < c0) next_self(ts);
+    uint32_t smask = 0;
+    while (ts.snext < c0 + 32) {
+      smask |= 1u << (int)(ts.snext - c0);
+      const int pos = self_pos[ts.scur];
+      atomicAdd(&hlo(S, r)[pos * 128], 1u);
+      if (hist_hi) atomicAdd(&hhi(S, r)[pos * 128], 1u);
+      next_self(ts);
+    }
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
+    float *tile = (float *)S + warp * 32 * 32 + lane;   // column j at [j * 32]
+    uint32_t any = 0, topm = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      tile[j * 32] = v[j];
+      any |= (__fadd_ru(v[j], ts.b) > ts.t0 ? 1u : 0u) << j;
+      topm |= (__fsub_rd(v[j], ts.b) > ts.tl ? 1u : 0u) << j;
+    }
+    const int64_t left = ncols - c0;
+    uint32_t keep = ~smask;
+    if (left < 32) keep &= left <= 0 ? 0u : (1u << left) - 1u;
+    topm &= keep;
+    any &= keep;
+    ts.top += __popc(topm);
+    uint32_t mid = any & ~topm;
+    const float *tr = thr(S, r);
+    while (mid) {
+      const int j = __ffs(mid) - 1;
+      mid &= mid - 1u;
+      const float x = tile[j * 32];
+      const float lo = __fsub_rd(x, ts.b), hi = __fadd_ru(x, ts.b);
+      // with d_i = t_i rounded down: lo > d_i gives lo >= next(d_i) > t_i
+      // (certainly above); hi > t_i gives hi > d_i (so d_i < hi: possibly above)
+      // one search for the score itself, then short walks to the interval's ends
+      const int p = count_below(tr, ts.L, x);
+      int plo = p, phi = p;
+      while (plo > 0 && !(tr[(plo - 1) * 128] < lo)) --plo;
+      while (phi < ts.L && tr[phi * 128] < hi) ++phi;
+      if (hist_hi) {
+        atomicAdd(&hlo(S, r)[plo * 128], 1u);
+        atomicAdd(&hhi(S, r)[phi * 128], 1u);
+      } else if (plo == phi) {
+        atomicAdd(&hlo(S, r)[plo * 128], 1u);
+      } else {
+        q.push((int)ts.sg, (int)(c0 + j));
+      }
+    }
+  }
+  __device__ __forceinline__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ __forceinline__ void unit_end(char *S, const tc::Unit &, int et, Thread &ts) const {
+    const int w = (et >> 5) + 2, lane = et & 31;
+    const int r = (w & 3) * 32 + lane, half = et >> 7;
+    if (ts.L > 0 && ts.top) {
+      atomicAdd(&hlo(S, r)[ts.L * 128], ts.top);
+      if (hist_hi) atomicAdd(&hhi(S, r)[ts.L * 128], ts.top);
+    }
+    tc::epi_sync();
+    if (ts.L == 0 || half != 0) return;
+    // position 0 (above no threshold) is never read
+    uint32_t *h = hist + 2 * ts.st0, *hh = hist_hi ? hist_hi + 2 * ts.st0 : nullptr;
+    for (int i = 1; i <= ts.L; ++i) {
+      const uint32_t a = hlo(S, r)[i * 128];
+      if (a) atomicAdd(&h[i], a);
+      if (hh) {
+        const uint32_t b2 = hhi(S, r)[i * 128];
+        if (b2) atomicAdd(&hh[i], b2);
+      }
+    }
+  }
+};
 
 // Exact position of each queued score among its segment's thresholds.  A
 // CUDA-core FP32 dot product with its bound settles most items; the rest are
@@ -1521,33 +1721,57 @@ __global__ void k_gather_side(const __nv_bfloat16 *__restrict__ hi,
   }
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, class Epi>
 static rkr_status tc_recount_bn(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt,
                                 int64_t nseg, int64_t ncand, const int64_t *seg_start,
                                 const int32_t *seg_len, const int32_t *seg_user,
                                 const int32_t *seg_self, const double *ths, uint32_t *hist,
-                                uint32_t *hist_hi, cudaStream_t st, int64_t *refined, int split);
+                                uint32_t *hist_hi, cudaStream_t st, int64_t *refined, int split,
+                                const int32_t *self_col, const int32_t *self_pos);
 
 rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, int64_t nseg,
                       int64_t ncand, const int64_t *seg_start, const int32_t *seg_len,
                       const int32_t *seg_user, const int32_t *seg_self, const double *ths,
                       uint32_t *hist, uint32_t *hist_hi, cudaStream_t st, int64_t *refined,
-                      int split) {
+                      int split, const int32_t *self_col, const int32_t *self_pos) {
   // the exact mode places every item, so it always runs the split product
   if (!hist_hi) split = 1;
+  if (self_col) {   // segments of several thresholds
+    if (tuning().rc_bn == 128)
+      return tc_recount_bn<128, tc::stages1<128, EpiRCm>(), EpiRCm>(
+          idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user, seg_self, ths, hist, hist_hi,
+          st, refined, split, self_col, self_pos);
+    return tc_recount_bn<256, tc::stages1<256, EpiRCm>(), EpiRCm>(
+        idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user, seg_self, ths, hist, hist_hi, st,
+        refined, split, self_col, self_pos);
+  }
   if (tuning().rc_bn == 128)
-    return tc_recount_bn<128, 6>(idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user,
-                                 seg_self, ths, hist, hist_hi, st, refined, split);
-  return tc_recount_bn<256, 4>(idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user, seg_self,
-                               ths, hist, hist_hi, st, refined, split);
+    return tc_recount_bn<128, 6, EpiRC>(idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user,
+                                        seg_self, ths, hist, hist_hi, st, refined, split,
+                                        nullptr, nullptr);
+  return tc_recount_bn<256, 4, EpiRC>(idx, Ut, Pt, nseg, ncand, seg_start, seg_len, seg_user,
+                                      seg_self, ths, hist, hist_hi, st, refined, split, nullptr,
+                                      nullptr);
 }
 
-template <int BN, int STAGES>
+template <class Epi>
+static void set_recount_fields(Epi &e, const int32_t *, const int32_t *, const int32_t *seg_self) {
+  e.seg_self = seg_self;
+}
+template <>
+void set_recount_fields<EpiRCm>(EpiRCm &e, const int32_t *self_col, const int32_t *self_pos,
+                                const int32_t *) {
+  e.self_col = self_col;
+  e.self_pos = self_pos;
+}
+
+template <int BN, int STAGES, class Epi>
 static rkr_status tc_recount_bn(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt,
                                 int64_t nseg, int64_t ncand, const int64_t *seg_start,
                                 const int32_t *seg_len, const int32_t *seg_user,
                                 const int32_t *seg_self, const double *ths, uint32_t *hist,
-                                uint32_t *hist_hi, cudaStream_t st, int64_t *refined, int split) {
+                                uint32_t *hist_hi, cudaStream_t st, int64_t *refined, int split,
+                                const int32_t *self_col, const int32_t *self_pos) {
   const int64_t m = idx->m;
   if (nseg <= 0) return RKR_OK;
   TcSide A;
@@ -1586,11 +1810,12 @@ static rkr_status tc_recount_bn(const rkr_index *idx, const TcSide &Ut, const Tc
   RKR_CUDA(pool_malloc_async(&flags, sizeof(int) * 2, st));
   RKR_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
-  EpiRC e;
+  Epi e;
   e.nseg = nseg; e.ncols = m; e.bn = BN; e.rowb = split ? A.rb3 : A.rb1; e.tileb = tb;
   e.gacc = tc_gacc(A.kp, split); e.gcan = tc_gcan(idx->d);
   e.seg_start = seg_start; e.seg_len = seg_len; e.ths = ths; e.hist = hist;
-  e.hist_hi = hist_hi; e.seg_self = seg_self;
+  e.hist_hi = hist_hi;
+  set_recount_fields(e, self_col, self_pos, seg_self);
   e.q = PairQueue{qitems, qcount, cap, flags + 1};
   rkr_status s =
       launch_screen<BN, STAGES>(A, Pt, split, row_schedule(nseg, m, BN), e, flags, st);

@@ -69,6 +69,7 @@ __device__ __forceinline__ bool epi_vote_any(bool p) {
 
 template <int BN>
 struct Layout {
+  static_assert(BN == 128 || BN == 256, "column tiles of 128 or 256");
   static constexpr uint32_t kA = BM * KCH * 2;      // 16 KB
   static constexpr uint32_t kB = BN * KCH * 2;
   static constexpr uint32_t kStage = kA + kB;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kc = 0; kc < nk; ++kc, ++it) {
               const int s = it % STAGES;
               const uint32_t ph = (it / STAGES) & 1;
-              if (!mbar_wait(&empty[s], ph ^ 1)) { failed = true; break; }
+              if (!mbar_wait(&empty[s], ph ^ 1, kWaitLimit, true)) { failed = true; break; }
               unsigned char *sa = stages + (size_t)s * L::kStage;
               unsigned char *sb = sa + L::kA;
               const int g = kc / op.kchunks, c = kc - g * op.kchunks;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int ct = u.ct0; ct < u.ct1 && !failed; ++ct, ++t) {
             const int b = t & 1;
             const uint32_t aph = (t >> 1) & 1;
-            if (!mbar_wait(&acc_empty[b], aph ^ 1)) { failed = true; break; }
+            if (!mbar_wait(&acc_empty[b], aph ^ 1, kWaitLimit, true)) { failed = true; break; }
             tc_fence_after();
             const uint32_t dt = tmem + (uint32_t)(b * BN);
             for (int kc = 0; kc < nk; ++kc, ++it) {
@@ -212,12 +213,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           epi.tile_begin(escratch, rb, ct, r, half, ts);
           const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
+          // 64 columns per TMEM load (one wait), handed out as two chunks of 32
 #pragma unroll 1
-          for (int cc = 0; cc < BN / 64; ++cc) {
+          for (int cc = 0; cc < BN / 64; cc += 2) {
             const int col = half * (BN / 2) + cc * 32;
-            float v[32];
-            tmem_ld32(trow + col, v);
-            epi.chunk(escratch, rb, ct, r, col, trow + (uint32_t)col, v, ts);
+            float v[64];
+            tmem_ld64(trow + col, v);
+            epi.chunk(escratch, rb, ct, r, col, trow + (uint32_t)col,
+                      *reinterpret_cast<const float(*)[32]>(v), ts);
+            epi.chunk(escratch, rb, ct, r, col + 32, trow + (uint32_t)(col + 32),
+                      *reinterpret_cast<const float(*)[32]>(v + 32), ts);
           }
           epi.tile_end(escratch, rb, ct, r, half, ts);
           tc_fence_before();
@@ -237,6 +242,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     tmem_dealloc(tmem, kTmemCols);
   }
+}
+
+// Stages of the single-CTA and multicast forms that fit beside the epilogue's
+// scratch (at most 4).
+template <int BN, class Epi>
+constexpr int stages1() {
+  constexpr size_t avail = 232448 - 1024 - 16 - 8 * 13 - Epi::kSmem;
+  constexpr int s = (int)(avail / Layout<BN>::kStage);
+  return s > 4 ? 4 : s;
 }
 
 template <int BN, int STAGES, class Epi>

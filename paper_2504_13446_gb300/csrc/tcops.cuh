@@ -40,9 +40,45 @@ rkr_status make_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t rows, i
 // hook set by rkr_set_wait_limit; tc::kWaitLimit unless changed).
 uint32_t epi_wait_limit();
 
-// Launch the screen kernel over A (users) x B (items or queries).  Row-owned
-// schedules run as CTA pairs sharing B by cluster multicast in the single-GPU
-// build, and on the single-CTA kernel otherwise; both give the same bits.
+#ifdef RKR_CLUSTER_MULTICAST
+// Launch a CTA-pair kernel (clusters of two, one per pair of row blocks, at most
+// as many clusters as fit at once).  False when no cluster fits (nothing launched).
+template <class K, class Epi>
+bool launch_cluster_pairs(K kern, size_t smem, const tc::Schedule &sch, cudaStream_t st,
+                          const CUtensorMap &mAh, const CUtensorMap &mAl, const CUtensorMap &mBh,
+                          const CUtensorMap &mBl, const tc::Operands &op, const Epi &epi,
+                          int *err_dev) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(tc::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(2 * (unsigned)((sm_count() + 1) / 2));
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    nclusters = 0;
+  }
+  const int npairs = (sch.nunits + 1) / 2;
+  if (nclusters < 1) return false;
+  cfg.gridDim = dim3(2 * (unsigned)std::min(npairs, nclusters));
+  if (cudaLaunchKernelEx(&cfg, kern, mAh, mAl, mBh, mBl, op, sch, epi, err_dev) != cudaSuccess)
+    return false;
+  note_launch();
+  return true;
+}
+#endif
+
+// Launch the screen kernel over A (users) x B (items or queries).  In the
+// single-GPU build row-owned schedules run on CTA pairs, either sharing B by
+// cluster multicast or as 2-SM MMAs (the tuning's screen_form), and on the
+// single-CTA kernel otherwise.  Every form bounds its scores by the same bound.
 template <int BN, int STAGES, class Epi>
 rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::Schedule &sch,
                          const Epi &epi, int *err_dev, cudaStream_t st) {
@@ -65,38 +101,30 @@ rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::
   // whatever number of products (split) and padding of K the screen issues
   ProfScope prof(Epi::name(), st, 2.0 * (double)A.rows * (double)B.rows * (double)A.d);
 #ifdef RKR_CLUSTER_MULTICAST
-  if (sch.mode == 0 && sch.nunits >= 2) {
+  const int form = tuning().screen_form;
+  if (sch.mode == 0 && sch.nunits >= 2 && form == 2) {
+    // row-owned units: 2-SM MMAs over CTA pairs, each CTA staging half of B
+    constexpr int S2 = tc::stages2<BN, Epi>();
+    const size_t smem2 = tc::screen2_smem_bytes<BN, S2, Epi>();
+    auto pk = tc::k_screen_2sm<BN, S2, Epi>;
+    RKR_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    CUtensorMap mBh2, mBl2;
+    RKR_TRY(make_map(&mBh2, B.hi, B.rows, B.kp, BN / 2));
+    RKR_TRY(make_map(&mBl2, B.lo, B.rows, B.kp, BN / 2));
+    if (launch_cluster_pairs(pk, smem2, sch, st, mAh, mAl, mBh2, mBl2, op, epi, err_dev))
+      return RKR_OK;
+    RKR_CUDA(cudaGetLastError());
+  }
+  if (sch.mode == 0 && sch.nunits >= 2 && form == 1) {
     // row-owned units: CTA pairs share each B chunk by multicast
     auto pk = tc::k_screen_pair<BN, STAGES, Epi>;
     RKR_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CUtensorMap mBh2, mBl2;
     RKR_TRY(make_map(&mBh2, B.hi, B.rows, B.kp, BN / 2));
     RKR_TRY(make_map(&mBl2, B.lo, B.rows, B.kp, BN / 2));
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(tc::kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(2 * (unsigned)((sm_count() + 1) / 2));
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, pk, &cfg) != cudaSuccess) {
-      (void)cudaGetLastError();
-      nclusters = 0;
-    }
-    const int npairs = (sch.nunits + 1) / 2;
-    if (nclusters >= 1) {
-      cfg.gridDim = dim3(2 * (unsigned)std::min(npairs, nclusters));
-      RKR_CUDA(cudaLaunchKernelEx(&cfg, pk, mAh, mAl, mBh2, mBl2, op, sch, epi, err_dev));
-      note_launch();
-      RKR_CUDA(cudaGetLastError());
+    if (launch_cluster_pairs(pk, smem, sch, st, mAh, mAl, mBh2, mBl2, op, epi, err_dev))
       return RKR_OK;
-    }
+    RKR_CUDA(cudaGetLastError());
   }
 #endif
   auto kern = tc::k_screen<BN, STAGES, Epi>;

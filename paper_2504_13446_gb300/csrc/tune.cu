@@ -5,7 +5,8 @@
 // are cached in a JSON-lines file, one object per line:
 //   {"key": "n=...,m=...,d=...,nq=...,ksum=...,what=...", "rc_bn": 256,
 //    "rc_single_first": 1, "skip_level": 0, "cand_budget_log2": 26,
-//    "latency_ctas_per_sm": 0, "latency_bulk": 1, "ms": 123.4}
+//    "latency_ctas_per_sm": 0, "latency_bulk": 0, "screen_form": 1, "rc_seg_min": 0,
+//    "ms": 123.4}
 #include <stdio.h>
 #include <string.h>
 
@@ -19,7 +20,7 @@ namespace rkr {
 namespace {
 
 std::mutex g_tune_mu;
-rkr_tuning g_tune = {256, 1, 0, 26, 0, 1};
+rkr_tuning g_tune = {256, 1, 0, 26, 0, 0, 1, 0};
 
 rkr_status check_tuning(const rkr_tuning &t) {
   if (t.rc_bn != 128 && t.rc_bn != 256) return fail(RKR_EINVAL, "rc_bn must be 128 or 256");
@@ -31,6 +32,9 @@ rkr_status check_tuning(const rkr_tuning &t) {
   if (t.latency_ctas_per_sm < 0 || t.latency_ctas_per_sm > 32)
     return fail(RKR_EINVAL, "latency_ctas_per_sm in [0, 32]");
   if (t.latency_bulk != 0 && t.latency_bulk != 1) return fail(RKR_EINVAL, "latency_bulk is 0 or 1");
+  if (t.screen_form < 0 || t.screen_form > 2) return fail(RKR_EINVAL, "screen_form in [0, 2]");
+  if (t.rc_seg_min < 0 || t.rc_seg_min == 1 || t.rc_seg_min > kRecountSeg)
+    return fail(RKR_EINVAL, "rc_seg_min is 0 or in [2, %d]", kRecountSeg);
   return RKR_OK;
 }
 
@@ -59,13 +63,14 @@ bool cache_lookup(const char *path, const std::string &key, rkr_tuning *t, doubl
   const std::string pat = "\"key\": \"" + key + "\"";
   while (fgets(line, sizeof(line), f)) {
     if (!strstr(line, pat.c_str())) continue;
-    double v[7];
+    double v[9];
     if (field(line, "rc_bn", &v[0]) && field(line, "rc_single_first", &v[1]) &&
         field(line, "skip_level", &v[2]) && field(line, "cand_budget_log2", &v[3]) &&
         field(line, "latency_ctas_per_sm", &v[4]) && field(line, "ms", &v[5]) &&
-        field(line, "latency_bulk", &v[6])) {
+        field(line, "latency_bulk", &v[6]) && field(line, "screen_form", &v[7]) &&
+        field(line, "rc_seg_min", &v[8])) {
       rkr_tuning c = {(int32_t)v[0], (int32_t)v[1], (int32_t)v[2], (int32_t)v[3],
-                      (int32_t)v[4], (int32_t)v[6]};
+                      (int32_t)v[4], (int32_t)v[6], (int32_t)v[7], (int32_t)v[8]};
       if (check_tuning(c) == RKR_OK) {
         *t = c;
         *ms = v[5];
@@ -86,9 +91,9 @@ rkr_status cache_append(const char *path, const std::string &key, const rkr_tuni
   fprintf(f,
           "{\"key\": \"%s\", \"rc_bn\": %d, \"rc_single_first\": %d, \"skip_level\": %d, "
           "\"cand_budget_log2\": %d, \"latency_ctas_per_sm\": %d, \"latency_bulk\": %d, "
-          "\"ms\": %.4f}\n",
+          "\"screen_form\": %d, \"rc_seg_min\": %d, \"ms\": %.4f}\n",
           key.c_str(), t.rc_bn, t.rc_single_first, t.skip_level, t.cand_budget_log2,
-          t.latency_ctas_per_sm, t.latency_bulk, ms);
+          t.latency_ctas_per_sm, t.latency_bulk, t.screen_form, t.rc_seg_min, ms);
   if (fclose(f) != 0) return fail(RKR_EINVAL, "cannot write %s", path);
   return RKR_OK;
 }
@@ -170,18 +175,25 @@ extern "C" rkr_status rkr_autotune(rkr_index *idx, const float *Q, int32_t nq, c
   // candidate grid: only the fields the chosen calls depend on vary
   const int ls = default_skip(idx);
   std::vector<rkr_tuning> grid;
+  // the screen form is tried with every other field at its current value
+  const int alt_form = before.screen_form == 2 ? 1 : 2;
   for (int bn : {256, 128})
     for (int sf : {1, 0})
       for (int sk : {0, ls - 1, ls + 1})
         for (int lc : {0, 2, 4})
-          for (int lb : {1, 0}) {
-            if (!(what & 1) && (bn != 256 || sf != 1)) continue;
-            if (!(what & 3) && sk != 0) continue;
-            if (!(what & 4) && (lc != 0 || lb != 1)) continue;
-            if (lb == 1 && lc != 0) continue;   // the bulk scan runs one CTA per SM
-            if (sk < 0 || sk > 30 || (sk != 0 && sk == ls)) continue;
-            grid.push_back({bn, sf, sk, before.cand_budget_log2, lc, lb});
-          }
+          for (int lb : {0, 1})
+            for (int form : {before.screen_form, alt_form}) {
+              if (!(what & 1) && (bn != 256 || sf != 1)) continue;
+              if (!(what & 3) && sk != 0) continue;
+              if (!(what & 4) && (lc != 0 || lb != 0)) continue;
+              if (lb == 1 && lc != 0) continue;   // the bulk scan runs one CTA per SM
+              if (sk < 0 || sk > 30 || (sk != 0 && sk == ls)) continue;
+              if (form != before.screen_form &&
+                  (!(what & 1) || bn != 256 || sf != 1 || sk != 0 || lc != 0 || lb != 0))
+                continue;
+              grid.push_back({bn, sf, sk, before.cand_budget_log2, lc, lb, form,
+                              before.rc_seg_min});
+            }
   const size_t tot = (size_t)ksum;
   int32_t *users = nullptr, *ranks = nullptr, *icase = nullptr, *inc = nullptr;
   uint32_t *nlo = nullptr, *nup = nullptr;

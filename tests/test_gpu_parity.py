@@ -234,3 +234,27 @@ def test_recount_below_the_tail_lists(floor_rank):
     check_exact_table(ora, gpu, U, P, floor_rank=floor_rank)
     st = check_exact(U, P, Q, k, gpu)
     assert st.recounted > 0 and st.wide_queries > 0
+
+
+@pytest.mark.parametrize("split_first", [1, 0])
+def test_recount_many_thresholds_per_user(split_first):
+    """Forty tiny-norm queries make every user a candidate of each of them, so
+    the recount (with multi-threshold segments switched on) compares each
+    user's scores with forty sorted thresholds (two segments of 20).  Items of P among the queries (one of them
+    twice) tie exactly with their own threshold and sit at a known position
+    among the others; a copy of a tiny query gives equal thresholds."""
+    rng = np.random.default_rng(77)
+    U, P = _rows(rng, 1500, 40), _rows(rng, 3000, 40)
+    scales = np.geomspace(1e-4, 3e-2, 38).astype(np.float32)
+    tiny = scales[:, None] * P[100:138]
+    Q = np.vstack([tiny, tiny[5:6], P[3:4], P[3:4], P[10:14], _rows(rng, 4, 40)])
+    k = rng.integers(1, 80, size=Q.shape[0]).astype(np.int32)
+    before = rkr.rkr_tuning_get()
+    try:
+        rkr.rkr_tuning_set(rc_single_first=split_first, rc_seg_min=4)
+        ora, gpu = build_pair(U, P, 40, 6, 30, floor_rank=8)
+        st = check_exact(U, P, Q, k, gpu)
+        assert st.recounted > 0 and st.recount_users > 0
+        assert st.recounted > 10 * st.recount_users   # many thresholds per user
+    finally:
+        rkr.rkr_tuning_set(**before)

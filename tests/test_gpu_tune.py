@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 rkr = pytest.importorskip("paper_2504_13446_gb300")
 
 DEFAULT = dict(rc_bn=256, rc_single_first=1, skip_level=0, cand_budget_log2=26,
-               latency_ctas_per_sm=0, latency_bulk=1)
+               latency_ctas_per_sm=0, latency_bulk=0, screen_form=1, rc_seg_min=0)
 
 
 def _answers(idx, w):
@@ -35,7 +35,9 @@ def test_every_tuning_gives_the_same_answers(tmp_path):
             ref = _answers(idx, w)
             for fields in (dict(rc_bn=128), dict(rc_single_first=0), dict(skip_level=3),
                            dict(skip_level=9), dict(cand_budget_log2=20),
-                           dict(latency_ctas_per_sm=2), dict(latency_bulk=0)):
+                           dict(latency_ctas_per_sm=2), dict(latency_bulk=1),
+                           dict(screen_form=0), dict(screen_form=2), dict(rc_seg_min=2),
+                           dict(rc_seg_min=4, rc_single_first=0)):
                 rkr.rkr_tuning_set(**{**DEFAULT, **fields})
                 got = _answers(idx, w)
                 for a, b in zip(got, ref):
@@ -52,5 +54,29 @@ def test_every_tuning_gives_the_same_answers(tmp_path):
             t2, ms2 = idx.autotune(w.Q, w.k, what=7, cache_path=str(cache))   # from the cache
             assert t2 == t1 and ms2 == pytest.approx(ms1, abs=1e-3)
             assert len(cache.read_text().splitlines()) == 1
+    finally:
+        rkr.rkr_tuning_set(**DEFAULT)
+
+
+def test_screen_forms_build_the_same_index():
+    # 157 row blocks of 128 users: the last CTA pair has one block past the end
+    w = synth.make_workload("approx", n=20000, m=3000, d=72, nq=30)
+    pos = synth.sample_positions(4, oracle.bucket_sizes(w.m, 5), 30)
+    names = ("fmin", "fmax", "table", "xlo", "xhi", "xgrid")
+    ref = None
+    try:
+        for form in (0, 1, 2):
+            rkr.rkr_tuning_set(**{**DEFAULT, "screen_form": form})
+            with rkr.Index(w.U, w.P, tau=48, omega=5, s=30, sample_pos=pos, exact_table=True,
+                           floor_rank=40) as idx:
+                got = [idx.export(x) for x in names]
+                got += list(idx.query_exact(w.Q, w.k)[:2])
+                a = idx.query_approx(w.Q, w.k, 2.0)
+                got += [a[key] for key in ("users", "n_low", "n_up", "est", "case", "nc")]
+            if ref is None:
+                ref = got
+                continue
+            for i, (x, y) in enumerate(zip(got, ref)):
+                assert np.array_equal(x, y), (form, i)
     finally:
         rkr.rkr_tuning_set(**DEFAULT)
