@@ -1513,12 +1513,13 @@ struct EpiRCm {
     tc::RowBound ru;     // the row's bound terms
     TilePrefetch tp;     // the bound terms of the next column tile
   };
-  // Per warp a staging tile of 32 x 32 scores, then per row the thresholds
-  // (rounded down) and the pos_lo and pos_hi histograms.  Every table is stored
-  // index-major (element i of row r at i * 128 + r, the tile as [column][lane]),
-  // so the 32 lanes of a warp, which hold 32 rows, always hit 32 different
-  // banks whatever index each lane looks up.
-  static constexpr size_t kThrOff = sizeof(float) * 8 * 32 * 32;
+  // Per row the thresholds (rounded down; +inf beyond L, so that a search over
+  // all kL slots needs no bound) and the pos_lo and pos_hi histograms.  Every
+  // table is stored index-major (element i of row r at i * 128 + r), so the 32
+  // lanes of a warp, which hold 32 rows, always hit 32 different banks whatever
+  // index each lane looks up.
+  static_assert(kL == 32, "the branch-free search takes five steps");
+  static constexpr size_t kThrOff = 0;
   static constexpr size_t kHloOff = kThrOff + sizeof(float) * 128 * kL;
   static constexpr size_t kHhiOff = kHloOff + sizeof(uint32_t) * 128 * (kL + 1);
   static constexpr size_t kSmem = kHhiOff + sizeof(uint32_t) * 128 * (kL + 1);
@@ -1538,14 +1539,13 @@ struct EpiRCm {
   __device__ static float *thr(char *S, int r) { return (float *)(S + kThrOff) + r; }
   __device__ static uint32_t *hlo(char *S, int r) { return (uint32_t *)(S + kHloOff) + r; }
   __device__ static uint32_t *hhi(char *S, int r) { return (uint32_t *)(S + kHhiOff) + r; }
-  // #{i < L : t[i] < x} over ascending t (stride 128)
-  __device__ static int count_below(const float *t, int L, float x) {
-    int a = 0, n = L;
-    while (n > 0) {
-      const int h = n >> 1;
-      if (t[(a + h) * 128] < x) { a += h + 1; n -= h + 1; } else { n = h; }
-    }
-    return a;
+  // #{i < 32 : t[i] < x} over ascending t (stride 128): five branch-free steps
+  __device__ static int count_below(const float *t, float x) {
+    int p = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1)
+      p += t[(p + step - 1) * 128] < x ? step : 0;
+    return p + (t[p * 128] < x ? 1 : 0);
   }
   __device__ void next_self(Thread &ts) const {
     ++ts.scur;
@@ -1570,7 +1570,7 @@ struct EpiRCm {
     ts.tl = __double2float_ru(t[ts.L - 1]);
     if (half == 0) {
       float *tr = thr(S, r);
-      for (int i = 0; i < ts.L; ++i) tr[i * 128] = __double2float_rd(t[i]);
+      for (int i = 0; i < kL; ++i) tr[i * 128] = i < ts.L ? __double2float_rd(t[i]) : INFINITY;
       for (int i = 0; i <= ts.L; ++i) {
         hlo(S, r)[i * 128] = 0;
         hhi(S, r)[i * 128] = 0;
@@ -1598,12 +1598,9 @@ struct EpiRCm {
       if (hist_hi) atomicAdd(&hhi(S, r)[pos * 128], 1u);
       next_self(ts);
     }
-    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
-    float *tile = (float *)S + warp * 32 * 32 + lane;   // column j at [j * 32]
     uint32_t any = 0, topm = 0;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      tile[j * 32] = v[j];
       any |= (__fadd_ru(v[j], ts.b) > ts.t0 ? 1u : 0u) << j;
       topm |= (__fsub_rd(v[j], ts.b) > ts.tl ? 1u : 0u) << j;
     }
@@ -1613,20 +1610,19 @@ struct EpiRCm {
     topm &= keep;
     any &= keep;
     ts.top += __popc(topm);
-    uint32_t mid = any & ~topm;
+    const uint32_t mid = any & ~topm;
+    if (!mid) return;
     const float *tr = thr(S, r);
-    while (mid) {
-      const int j = __ffs(mid) - 1;
-      mid &= mid - 1u;
-      const float x = tile[j * 32];
-      const float lo = __fsub_rd(x, ts.b), hi = __fadd_ru(x, ts.b);
+    // every column in a static slot (no staging, no data-dependent loop); the
+    // searches of different columns are independent, so their loads overlap
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (!((mid >> j) & 1u)) continue;
+      const float lo = __fsub_rd(v[j], ts.b), hi = __fadd_ru(v[j], ts.b);
       // with d_i = t_i rounded down: lo > d_i gives lo >= next(d_i) > t_i
       // (certainly above); hi > t_i gives hi > d_i (so d_i < hi: possibly above)
-      // one search for the score itself, then short walks to the interval's ends
-      const int p = count_below(tr, ts.L, x);
-      int plo = p, phi = p;
-      while (plo > 0 && !(tr[(plo - 1) * 128] < lo)) --plo;
-      while (phi < ts.L && tr[phi * 128] < hi) ++phi;
+      const int plo = count_below(tr, lo);
+      const int phi = count_below(tr, hi);
       if (hist_hi) {
         atomicAdd(&hlo(S, r)[plo * 128], 1u);
         atomicAdd(&hhi(S, r)[phi * 128], 1u);
