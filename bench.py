@@ -542,8 +542,11 @@ def bench_uneven(args):
 
     note("inputs on the device")
     rkr.rkr_profile_start()
+    # the exact tables with the deep count grid below the tail lists (exact_table = 2):
+    # the queries' k reaches 1,000, far below the floor rank for many users
+    xt = int(os.environ.get("RKR_UNEVEN_EXACT_TABLE", "2"))
     idx, ms_build = timed(lambda: rkr.Index(U, P, tau=w.tau, omega=w.omega, s=w.s,
-                                            fbounds="exact", exact_table=True, floor_rank=2048))
+                                            fbounds="exact", exact_table=xt, floor_rank=2048))
     note(f"index built in {ms_build:.0f} ms: {idx.timings()}")
     build_prof = rkr.rkr_profile_stop()
     note("build kernels: " + json.dumps({kk: round(v[1], 1) for kk, v in
@@ -581,10 +584,12 @@ def bench_uneven(args):
         "ms_per_batch": {"exact": me, "approx": ma, "index_build": ms_build},
         "steps": args.steps, "higher_is_better": True, "data": "synthetic",
         "dtype": "bf16+f32+f64",
-        "config": {"workload": "|U|=2,000,000 |P|=1,000,000 d=128 mixture (1,024 centres), "
-                               "4,096 queries, k log-uniform in [1,1000], per-query subsets of "
+        "config": {"workload": f"|U|={w.n:,} |P|={w.m:,} d={w.d} mixture (1,024 centres), "
+                               f"{nq:,} queries, k log-uniform in [1,1000], per-query subsets of "
                                "10-100% of U in 1,024-user blocks (bitmaps), tau=500, omega=10, "
-                               "s=100, exact tables with floor rank 2,048, c=2",
+                               "s=100, exact tables with floor rank 2,048"
+                               + (" and the deep count grid" if xt == 2 else "") + ", c=2",
+                   "tuning": rkr.rkr_tuning_get(),
                    "subset_users_total": subset_users, "k_max": int(w.k.max()),
                    "k_mean": float(w.k.mean()), "first_subset_sizes": sizes[:4].tolist()},
         "index_device_gb": mem / 1e9,

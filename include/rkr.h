@@ -45,6 +45,9 @@
 extern "C" {
 #endif
 
+/* Points of the deep count grid of an index built with exact_table = 2. */
+#define RKR_DEEP_GRID 64
+
 typedef enum {
   RKR_OK = 0,
   RKR_EINVAL = 1,        /* invalid argument (null pointer, size, k, c, non-finite input) */
@@ -66,7 +69,10 @@ typedef struct {
   int32_t fbounds;          /* 0: f_min/f_max are the exact min/max of u.p over P
                                (Section 4.2, step 2); 1: +-||u|| * max ||p||
                                (the bounded-domain variant of the footnote) */
-  int32_t exact_table;      /* 1: also build the exact count table rkr_query_exact needs */
+  int32_t exact_table;      /* 1: also build the exact count table rkr_query_exact needs;
+                               2: also a deep count grid below the tail lists (one more
+                               screen of U x P at build time; exact queries whose ranks lie
+                               below the floor rank then recount far fewer candidates) */
   int32_t floor_rank;       /* exact table: counts are kept exact only above the
                                threshold whose estimated rank is floor_rank; 0 = default
                                max(2048, m / 16).  Only speed depends on it. */
@@ -486,7 +492,14 @@ typedef enum {
                                x_j = x_0 + j * step; x_0 is the threshold t of the sampled
                                table's last column whose estimated count is >= floor_rank,
                                x_{G-1} = f_max */
-  RKR_EXPORT_PNORM = 8      /* double[m]: FP64 norms of P in original order */
+  RKR_EXPORT_PNORM = 8,     /* double[m]: FP64 norms of P in original order */
+  RKR_EXPORT_DLO = 10,      /* uint32[n * RKR_DEEP_GRID]: lower bound of #{p : s(u,p) > y_c}
+                               on the deep grid (exact_table = 2) */
+  RKR_EXPORT_DHI = 11,      /* uint32[n * RKR_DEEP_GRID]: upper bound of the same count */
+  RKR_EXPORT_DGRID = 12     /* double[n * 2]: (y_0, step) of each user's deep grid,
+                               y_c = y_0 + c * step; y_0 is the threshold t of the sampled
+                               table's last column whose estimated count is >= m / 8 (not
+                               above x_0), y_{RKR_DEEP_GRID - 1} = x_0 */
 } rkr_export_what;
 
 /* Copy one internal array to dst (host or device); bytes must equal its size. */

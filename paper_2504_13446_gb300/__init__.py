@@ -36,7 +36,9 @@ __all__ = ["RKRError", "Index", "QueryStats", "load", "rkr_build", "rkr_query_ex
 _lock = threading.Lock()
 _lib = None
 
-EXPORTS = dict(perm=1, fmin=2, fmax=3, table=4, samples=5, xlo=6, xgrid=7, pnorm=8, xhi=9)
+EXPORTS = dict(perm=1, fmin=2, fmax=3, table=4, samples=5, xlo=6, xgrid=7, pnorm=8, xhi=9,
+               dlo=10, dhi=11, dgrid=12)
+DEEP_GRID = 64   # points of the deep count grid (RKR_DEEP_GRID)
 _STATUS = {0: "RKR_OK", 1: "RKR_EINVAL", 2: "RKR_ENOMEM", 3: "RKR_ECUDA", 4: "RKR_ETIMEOUT",
            5: "RKR_EUNSUPPORTED", 6: "RKR_EINTERNAL"}
 
@@ -331,9 +333,12 @@ def _same_device(*arrays):
 
 
 def rkr_build(U, P, *, tau: int = 500, omega: int = 10, s: int = 100, fbounds: str = "exact",
-              exact_table: bool = True, floor_rank: int = 0, sample_pos=None, seed: int = 0,
+              exact_table=True, floor_rank: int = 0, sample_pos=None, seed: int = 0,
               stream=None) -> ctypes.c_void_p:
-    """Pre-processing (Alg. 1); returns an opaque index handle (free with rkr_index_free)."""
+    """Pre-processing (Alg. 1); returns an opaque index handle (free with rkr_index_free).
+
+    exact_table: False / 0 none, True / 1 the exact count table, 2 that and the
+    deep count grid below the tail lists."""
     lib = load()
     n, d = _shape(U)
     m, d2 = _shape(P)
@@ -795,7 +800,9 @@ class Index:
                       fmax=((i.n,), np.float64), table=((i.n, i.tau), np.uint32),
                       samples=((i.nsamp,), np.int32), xlo=((i.n, i.xg), np.uint32),
                       xhi=((i.n, i.xg), np.uint32),
-                      xgrid=((i.n, 2), np.float64), pnorm=((i.m,), np.float64))
+                      xgrid=((i.n, 2), np.float64), pnorm=((i.m,), np.float64),
+                      dlo=((i.n, DEEP_GRID), np.uint32), dhi=((i.n, DEEP_GRID), np.uint32),
+                      dgrid=((i.n, 2), np.float64))
         shape, dt = shapes[what]
         a = np.empty(shape, dtype=dt)
         _check(load().rkr_index_export(self._h, EXPORTS[what], a.ctypes.data_as(ctypes.c_void_p),

@@ -298,6 +298,7 @@ rkr_status rkr_build(const float *U, int64_t n, const float *P, int64_t m, int32
     return fail(RKR_EINVAL, "m * s must be < 2^32");
   if ((int64_t)p.omega * p.s > ((int64_t)1 << 26)) return fail(RKR_EINVAL, "omega * s too large");
   if (p.fbounds != 0 && p.fbounds != 1) return fail(RKR_EINVAL, "fbounds must be 0 or 1");
+  if (p.exact_table < 0 || p.exact_table > 2) return fail(RKR_EINVAL, "exact_table must be 0, 1 or 2");
   if (p.floor_rank < 0) return fail(RKR_EINVAL, "floor_rank must be >= 0");
   RKR_TRY(check_device());
   cudaStream_t st = (cudaStream_t)stream;
@@ -331,7 +332,7 @@ rkr_status rkr_build(const float *U, int64_t n, const float *P, int64_t m, int32
   idx->omega = p.omega;
   idx->s = p.s;
   idx->fbounds = p.fbounds;
-  idx->has_exact = p.exact_table ? 1 : 0;
+  idx->has_exact = p.exact_table;
   idx->floor_rank = p.floor_rank ? p.floor_rank : (int)(m / 16 > 2048 ? m / 16 : 2048);
   idx->seed = p.seed;
   idx->sampled_pos = p.sample_pos ? 1 : 0;
@@ -920,6 +921,19 @@ rkr_status rkr_index_export(const rkr_index *idx, int32_t what, void *dst, int64
       return RKR_OK;
     }
     case RKR_EXPORT_PNORM: src = idx->pnorm; size = 8 * idx->m; break;
+    case RKR_EXPORT_DLO: src = idx->DLO; size = 4 * idx->n * (int64_t)idx->dg; break;
+    case RKR_EXPORT_DHI: src = idx->DHI; size = 4 * idx->n * (int64_t)idx->dg; break;
+    case RKR_EXPORT_DGRID: {
+      if (!idx->yg0) return fail(RKR_EINVAL, "index has no deep grid");
+      if (bytes != 16 * idx->n) return fail(RKR_EINVAL, "export %d needs %lld bytes", what,
+                                            (long long)(16 * idx->n));
+      std::vector<double> a(idx->n), b(idx->n), o(2 * idx->n);
+      RKR_CUDA(cudaMemcpy(a.data(), idx->yg0, 8 * idx->n, cudaMemcpyDeviceToHost));
+      RKR_CUDA(cudaMemcpy(b.data(), idx->ydx, 8 * idx->n, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < idx->n; ++i) { o[2 * i] = a[i]; o[2 * i + 1] = b[i]; }
+      RKR_CUDA(cudaMemcpy(dst, o.data(), 16 * idx->n, cudaMemcpyDefault));
+      return RKR_OK;
+    }
     default: return fail(RKR_EINVAL, "unknown export %d", what);
   }
   if (!src) return fail(RKR_EINVAL, "export %d is not part of this index", what);

@@ -7,6 +7,7 @@
 //   rank-table numerators N from the sampled rows                      Alg. 1 step 3, Eq. 1
 //   level tables JU / JL that map a bin to the rank level it implies   (candidate filter)
 //   exact count table XLO / XHI bounding #{p : s(u,p) > t_j}           (exact path)
+//   deep count grid DLO / DHI below the tail lists (exact_table = 2)   (exact path)
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -468,6 +469,23 @@ __global__ void k_floor_cols(int64_t n, int tau, const uint32_t *__restrict__ N,
   fl[u] = a > 0 ? a - 1 : 0;
 }
 
+// Per user: the deep grid's base (the sampled table's threshold of column
+// col[u]), its top point x_0 rounded up and its base rounded down to float.
+__global__ void k_ygrid(int64_t n, const double *__restrict__ fmin,
+                        const double *__restrict__ delta, const int32_t *__restrict__ col,
+                        const int32_t *__restrict__ xfloor, const double *__restrict__ xg0,
+                        double *__restrict__ yg0, float *__restrict__ ytop,
+                        float *__restrict__ ybot) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  // the base never lies above x_0
+  const int c = col[u] < xfloor[u] ? col[u] : xfloor[u];
+  const double g = thr_at(fmin[u], delta[u], c);
+  yg0[u] = g;
+  ytop[u] = __double2float_ru(xg0[u]);
+  ybot[u] = __double2float_rd(g);
+}
+
 // Capacity of each user's tail list: 1.5 times the sampled table's estimate of
 // the count above the floor threshold, plus 256, at most kListCapMax (0 when
 // lists are disabled).  Lists that overflow are detected and not used.
@@ -758,6 +776,32 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
       RKR_CUDA(cudaStreamSynchronize(st));
     }
     RKR_TRY(tc_exact_table(idx, idx->Ut, idx->Pt, st, nullptr));
+    if (idx->has_exact == 2) {
+      // deep count grid from the sampled table's threshold of estimated count
+      // m / 8 up to x_0
+      idx->dg = kDGrid;
+      RKR_TRY(dalloc(&idx->yg0, n));
+      RKR_TRY(dalloc(&idx->ydx, n));
+      RKR_TRY(dalloc(&idx->ybin, n));
+      RKR_TRY(dalloc(&idx->DLO, (size_t)n * kDGrid));
+      RKR_TRY(dalloc(&idx->DHI, (size_t)n * kDGrid));
+      DevBuf bcol, btop, bbot;
+      int32_t *col;
+      float *ytop, *ybot;
+      RKR_TRY(tmp_alloc(bcol, &col, n, st));
+      RKR_TRY(tmp_alloc(btop, &ytop, n, st));
+      RKR_TRY(tmp_alloc(bbot, &ybot, n, st));
+      k_floor_cols<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(
+          n, tau, idx->N, (uint32_t)s, (uint64_t)(m / 8 > 1 ? m / 8 : 1), col);
+      note_launch();
+      k_ygrid<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, idx->fmin, idx->delta, col,
+                                                            idx->xfloor, idx->xg0, idx->yg0,
+                                                            ytop, ybot);
+      note_launch();
+      RKR_TRY(make_binfp_grid(idx, idx->yg0, idx->xg0, kDGrid, idx->pmax, idx->ydx, idx->ybin,
+                              st));
+      RKR_TRY(tc_deep_table(idx, idx->Ut, idx->Pt, ytop, ybot, st));
+    }
     idx->nlev_x = levels_for((uint64_t)m);
     RKR_TRY(dalloc(&idx->XJU, (size_t)n * kMaxLevels));
     RKR_TRY(dalloc(&idx->XJL, (size_t)n * kMaxLevels));
@@ -785,7 +829,8 @@ void index_release(rkr_index *idx) {
                   idx->JU,     idx->JL,   idx->S,    idx->snrm, idx->sw,    idx->samp_items,
                   idx->xg0,    idx->xdx,  idx->xbin, idx->XLO,  idx->XHI,   idx->XJU,   idx->XJL,
                   idx->xfloor, idx->xloff, idx->xlcap, idx->xlist, idx->xlcnt,
-                  idx->xbmax, idx->ptile3, idx->xcoff, idx->ldx, idx->lbin, idx->phk, idx->phv};
+                  idx->xbmax, idx->ptile3, idx->xcoff, idx->ldx, idx->lbin, idx->phk, idx->phv,
+                  idx->yg0,   idx->ydx,  idx->ybin, idx->DLO,  idx->DHI};
   // nothing may still use the arrays when they go back to the pool
   cudaDeviceSynchronize();
   for (void *p : ptrs)

@@ -46,6 +46,14 @@ struct rkr_index {
   int16_t *XJU = nullptr, *XJL = nullptr;   // n x 32
   int32_t *xfloor = nullptr;                // n: paper column of x_0
 
+  // deep count grid below the tail lists (exact_table = 2): y_c = yg0 + c * ydx,
+  // c = 0 .. dg - 1, from the sampled table's threshold whose estimated count
+  // reaches m / 8 up to x_0; DLO / DHI bound #{p : s(u,p) > y_c}
+  int dg = 0;
+  double *yg0 = nullptr, *ydx = nullptr;    // n
+  rkr::BinFP *ybin = nullptr;               // n
+  uint32_t *DLO = nullptr, *DHI = nullptr;  // n x dg
+
   // tail lists: per user, every item whose screened score may exceed x_0 (the
   // exact grid's floor), grouped by exact-grid column; user u's entries are
   // xlist[xloff[u] .. xloff[u] + xlcnt[u]) within a capacity xlcap[u]
@@ -93,6 +101,12 @@ rkr_status make_binfp_grid(const rkr_index *idx, const double *g0, const double 
 // Tensor-core screens (screen_epi.cu).
 rkr_status tc_fbounds(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, double *fmin,
                       double *fmax, cudaStream_t st);
+// Deep count grid (DLO / DHI on y_c, grid in yg0 / ydx / ybin): one
+// single-product screen of U x P whose epilogue histograms each score's grid
+// interval per user; ytop[u] / ybot[u] = the grid's top point rounded up and
+// its first point rounded down to float.
+rkr_status tc_deep_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, const float *ytop,
+                         const float *ybot, cudaStream_t st);
 rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cudaStream_t st,
                           int64_t *refined);
 // Arguments of one screening pass over a query batch (see screen_epi.cu).
@@ -155,6 +169,7 @@ rkr_status tc_recount(const rkr_index *idx, const TcSide &Ut, const TcSide &Pt, 
                       int split = 1, const int32_t *self_col = nullptr,
                       const int32_t *self_pos = nullptr);
 constexpr int kXGrid = 128;
+constexpr int kDGrid = RKR_DEEP_GRID;   // points of the deep count grid (exact_table = 2)
 constexpr int kRecountSeg = 32;     // thresholds per recount segment (one per screen row)
 constexpr int kListCapMax = 16384;  // entries per user list (< 2^16: 16-bit column offsets)
 constexpr int kListG = 1024;        // columns of the list grid (finer than the count grid)

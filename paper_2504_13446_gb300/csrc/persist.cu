@@ -25,7 +25,7 @@ namespace {
 
 constexpr char kMagic[8] = {'R', 'K', 'R', 'I', 'D', 'X', '0', '1'};
 constexpr char kPrunerMagic[8] = {'R', 'K', 'R', 'M', 'L', 'P', '0', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;   // 2: deep count grid and its layout constant
 constexpr uint32_t kBom = 0x01020304u;
 constexpr size_t kChunk = (size_t)64 << 20;
 
@@ -63,7 +63,7 @@ struct Hash {
 struct Header {
   int64_t n, m, d, tau, omega, s, fbounds, has_exact, floor_rank, nsamp, nlev_a, nlev_x, xg,
       lists, phn, ptile_bn, kp, list_entries, seed, sampled_pos, c_listg, c_xgrid, c_levels,
-      c_maxd;
+      c_maxd, dg, c_dgrid;
   float pmax;
   float pad;
   double build_ms[8];
@@ -108,6 +108,15 @@ std::vector<Arr> arrays(rkr_index *x, int64_t list_entries) {
         {42, (void **)&x->xlcap, n * 4},       {43, (void **)&x->xloff, (n + 1) * 8},
         {44, (void **)&x->xlist, (uint64_t)std::max<int64_t>(list_entries, 1) * 8},
         {45, (void **)&x->XJU, n * kMaxLevels * 2}, {46, (void **)&x->XJL, n * kMaxLevels * 2},
+    };
+    a.insert(a.end(), e.begin(), e.end());
+  }
+  if (x->dg > 0) {
+    const uint64_t dg = (uint64_t)x->dg;
+    std::vector<Arr> e = {
+        {47, (void **)&x->yg0, n * 8},         {48, (void **)&x->ydx, n * 8},
+        {49, (void **)&x->ybin, n * sizeof(BinFP)},
+        {50, (void **)&x->DLO, n * dg * 4},    {51, (void **)&x->DHI, n * dg * 4},
     };
     a.insert(a.end(), e.begin(), e.end());
   }
@@ -176,6 +185,7 @@ extern "C" rkr_status rkr_index_save(const rkr_index *idx_c, const char *path) {
   hd.ptile_bn = idx->ptile_bn; hd.kp = idx->Ut.kp; hd.list_entries = list_entries;
   hd.seed = (int64_t)idx->seed; hd.sampled_pos = idx->sampled_pos;
   hd.c_listg = kListG; hd.c_xgrid = kXGrid; hd.c_levels = kMaxLevels; hd.c_maxd = kMaxD;
+  hd.dg = idx->dg; hd.c_dgrid = kDGrid;
   hd.pmax = idx->pmax;
   for (int i = 0; i < 8; ++i) hd.build_ms[i] = idx->build_ms[i];
   File fh;
@@ -233,11 +243,12 @@ extern "C" rkr_status rkr_index_load(const char *path, rkr_index **out) {
   Header hd;
   RKR_TRY(get(fh.f, h, &hd, sizeof(hd)));
   if (hd.c_listg != kListG || hd.c_xgrid != kXGrid || hd.c_levels != kMaxLevels ||
-      hd.c_maxd != kMaxD)
+      hd.c_maxd != kMaxD || hd.c_dgrid != kDGrid)
     return fail(RKR_EINVAL, "index file was written with other layout constants");
   if (hd.n < 1 || hd.m < 1 || hd.d < 1 || hd.d > kMaxD || hd.tau < 2 || hd.omega < 1 ||
       hd.s < 1 || hd.nsamp < 1 || hd.kp != (hd.d + 15) / 16 * 16 || hd.phn < hd.m ||
-      hd.list_entries < 0 || (hd.has_exact && hd.xg != kXGrid))
+      hd.list_entries < 0 || (hd.has_exact && hd.xg != kXGrid) ||
+      (hd.dg != 0 && (hd.dg != kDGrid || hd.has_exact != 2)))
     return fail(RKR_EINVAL, "index file header is inconsistent");
   rkr_index *idx = new (std::nothrow) rkr_index();
   if (!idx) return fail(RKR_ENOMEM, "host allocation failed");
@@ -253,6 +264,7 @@ extern "C" rkr_status rkr_index_load(const char *path, rkr_index **out) {
   idx->n = hd.n; idx->m = hd.m; idx->d = (int)hd.d; idx->tau = (int)hd.tau;
   idx->omega = (int)hd.omega; idx->s = (int)hd.s; idx->fbounds = (int)hd.fbounds;
   idx->has_exact = (int)hd.has_exact; idx->floor_rank = (int)hd.floor_rank;
+  idx->dg = (int)hd.dg;
   idx->nsamp = (int)hd.nsamp; idx->nlev_a = (int)hd.nlev_a; idx->nlev_x = (int)hd.nlev_x;
   idx->xg = (int)hd.xg; idx->lists = (int)hd.lists; idx->phn = hd.phn;
   idx->ptile_bn = (int)hd.ptile_bn; idx->seed = (uint64_t)hd.seed;

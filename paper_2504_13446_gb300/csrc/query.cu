@@ -481,6 +481,16 @@ __global__ void k_scatter_counts(int64_t nseg, const int64_t *__restrict__ seg_s
   for (int i = 0; i < L; ++i) ccount[order[st0 + i]] = h[i + 1];
 }
 
+// The deep count grid of an index (dg = 0: none).
+struct DeepGrid {
+  int dg;
+  const double *yg0, *ydx;
+  const uint32_t *DLO, *DHI;
+};
+inline DeepGrid deep_grid(const rkr_index *idx) {
+  return DeepGrid{idx->dg, idx->yg0, idx->ydx, idx->DLO, idx->DHI};
+}
+
 // Exact ranks from the tail lists.  A candidate (u, q) with u.q >= x_0(u)
 // has rank 1 + #{p in list(u) : s(u,p) > u.q}, since every item scoring above
 // x_0 is in the list.  Entries are grouped by exact-grid column: whole
@@ -504,7 +514,7 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             const uint32_t *__restrict__ XHI, uint32_t mtop,
                             uint32_t *__restrict__ ccount, uint32_t *__restrict__ clb,
                             int32_t *__restrict__ cu_fb, const int32_t *__restrict__ qself,
-                            unsigned long long *__restrict__ stat) {
+                            DeepGrid deep, unsigned long long *__restrict__ stat) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int64_t u = cu[i];
@@ -531,8 +541,18 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   if (L > xlcap[u] || thi < xg0[u]) {
     // bounds from the exact count table at the bins of both ends of u.q
     const int jl = exact_j(tlo, xg0[u], xdx[u], GX), jh = exact_j(thi, xg0[u], xdx[u], GX);
-    ccount[i] = jl >= 1 ? XHI[u * GX + jl - 1] : mtop;
-    clb[i] = jh < GX ? XLO[u * GX + jh] : 0u;
+    uint32_t ub = jl >= 1 ? XHI[u * GX + jl - 1] : mtop;
+    uint32_t lb = jh < GX ? XLO[u * GX + jh] : 0u;
+    if (deep.dg > 0 && thi < xg0[u]) {
+      // below x_0: the deep grid's counts at y_{kl - 1} <= tlo and y_{kh} > thi
+      const int G2 = deep.dg;
+      const int kl = exact_j(tlo, deep.yg0[u], deep.ydx[u], G2);
+      const int kh = exact_j(thi, deep.yg0[u], deep.ydx[u], G2);
+      if (kl >= 1) ub = min(ub, deep.DHI[u * G2 + kl - 1]);
+      if (kh < G2) lb = max(lb, deep.DLO[u * G2 + kh]);
+    }
+    ccount[i] = ub;
+    clb[i] = lb;
     cu_fb[i] = (int32_t)u;
     atomicAdd(&stat[0], 1ull);
     return;
@@ -1721,7 +1741,8 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
             idx->xlist, idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
             idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
             idx->ldx, kListG,
-            idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, qself, lstat);
+            idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, qself, deep_grid(idx),
+            lstat);
         prof_end(prof_slot, st, 0.0);
       }
       note_launch();
@@ -1898,7 +1919,8 @@ rkr_status run_rank_pairs(const rkr_index *idx, const QueryCommon &qc, int nq, i
       npairs, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d, idx->xlist,
       idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
       idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
-      idx->ldx, kListG, idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, qself, lstat);
+      idx->ldx, kListG, idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, qself,
+      deep_grid(idx), lstat);
   note_launch();
   RKR_CUDA(cudaGetLastError());
   unsigned long long ls[2] = {0, 0};

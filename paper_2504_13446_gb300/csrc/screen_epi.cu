@@ -698,6 +698,133 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
   return RKR_OK;
 }
 
+// ============================================================ deep grid
+
+// Count intervals on the deep grid y_c = yg0 + c * ydx, c = 0 .. G - 1 (G =
+// kDGrid), every item of P: the interval [v - b, v + b] of a screened score
+// gives bounds [jl, jh] of c(s) = #{c : y_c < s} (bin_interval); the item adds
+// to Hlo[jl] and Hhi[jh], and DLO[c] = #{jl > c} <= #{p : s(u,p) > y_c} <=
+// #{jh > c} = DHI[c], as for the exact grid of the tail lists.  Items whose
+// upper end lies below y_0 add to no count and are skipped after one compare;
+// items certainly above the whole grid (jl = G) are only counted.  The two
+// histograms of a row are one array of 64-bit words (Hlo in the low half, Hhi
+// in the high half: one atomic when jl = jh), per row in shared memory and
+// stored [bin][row] so that a warp's 32 rows never share a bank.
+struct EpiDeep {
+  static const char *name() { return "k_screen<EpiDeep>"; }
+  static constexpr int kBins = kDGrid + 1;
+  struct Thread {
+    float b, top_lo;     // bound; lower ends above top_lo are above the whole grid
+    float bot_hi;        // upper ends below bot_hi are below the whole grid
+    int64_t row;
+    uint32_t top;        // this thread's items certainly above every y_c
+    BinFP bf;
+    double g0;
+    tc::RowBound ru;
+    TilePrefetch tp;
+  };
+  static constexpr size_t kSmem = sizeof(unsigned long long) * 128 * kBins;
+  int64_t nrows, ncols;
+  int bn;
+  const tc::RowBound *rowb, *tileb;
+  tc::Gacc gacc;
+  float gcan;
+  const BinFP *ybin;
+  const double *yg0;
+  const float *ytop;       // per row: the grid's top point rounded up to float
+  const float *ybot;       // per row: the grid's first point rounded down to float
+  uint32_t *DLO, *DHI;     // n x kDGrid
+  __device__ static unsigned long long *hist(char *S, int r) {
+    return (unsigned long long *)S + r;
+  }
+  __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &ts) const {
+    for (int i = et; i < 128 * kBins; i += 256) ((unsigned long long *)S)[i] = 0ull;
+    ts.row = -1;
+    ts.top = 0;
+    ts.tp.start(tileb, u.ct0);
+  }
+  __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
+    const int64_t row = (int64_t)rb * tc::BM + r;
+    if (row != ts.row && row < nrows) {   // the row's data, once per row
+      ts.ru = rowb[row];
+      ts.bf = ybin[row];
+      ts.g0 = yg0[row];
+      ts.top_lo = ytop[row];
+      ts.bot_hi = ybot[row];
+    }
+    ts.row = row;
+    const tc::RowBound tb = ts.tp.take(tileb, ct, ncols, bn);
+    ts.b = ts.row < nrows ? tc::screen_bound_tc(ts.ru, tb, gacc, gcan) : 0.0f;
+  }
+  __device__ void chunk(char *S, int, int ct, int r, int col, uint32_t, const float (&v)[32],
+                        Thread &ts) const {
+    if (ts.row >= nrows) return;
+    const int64_t c0 = (int64_t)ct * bn + col;
+    const int64_t left = ncols - c0;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      if (j >= left) break;
+      const float lo = __fsub_rd(v[j], ts.b), hi = __fadd_ru(v[j], ts.b);
+      if (hi < ts.bot_hi) continue;                   // below the grid: counts nowhere
+      if (lo > ts.top_lo) { ++ts.top; continue; }   // above every grid point
+      int jl, jh;
+      bin_interval(ts.bf, ts.g0, kDGrid, lo, hi, jl, jh);
+      if (jh == 0) continue;
+      if (jl == jh) {
+        atomicAdd(&hist(S, r)[jl * 128], 0x100000001ull);
+      } else {
+        atomicAdd(&hist(S, r)[jl * 128], 1ull);
+        atomicAdd(&hist(S, r)[jh * 128], 0x100000000ull);
+      }
+    }
+  }
+  __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
+  __device__ void unit_end(char *S, const tc::Unit &u, int et, Thread &ts) const {
+    const int w = (et >> 5) + 2, lane = et & 31;
+    const int r = (w & 3) * 32 + lane, half = et >> 7;
+    const int64_t row = (int64_t)u.rb0 * tc::BM + r;
+    if (row < nrows && ts.top)
+      atomicAdd(&hist(S, r)[kDGrid * 128], (unsigned long long)ts.top * 0x100000001ull);
+    tc::epi_sync();
+    if (row >= nrows || half != 0) return;
+    // DLO[c] = sum over bins above c
+    uint32_t rl = 0, rh = 0;
+    for (int c = kDGrid; c >= 1; --c) {
+      const unsigned long long hv = hist(S, r)[c * 128];
+      rl += (uint32_t)hv;
+      rh += (uint32_t)(hv >> 32);
+      DLO[row * kDGrid + (c - 1)] = rl;
+      DHI[row * kDGrid + (c - 1)] = rh;
+    }
+  }
+};
+
+rkr_status tc_deep_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, const float *ytop,
+                         const float *ybot, cudaStream_t st) {
+  constexpr int BN = 256;
+  const int64_t n = idx->n, m = idx->m;
+  int *flags;
+  tc::RowBound *tb = nullptr;
+  RKR_CUDA(pool_malloc_async(&flags, sizeof(int) * 2, st));
+  RKR_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 2, st));
+  RKR_TRY(tc_tile_bounds(Pt, BN, 0, &tb, st));
+  EpiDeep e;
+  e.nrows = n; e.ncols = m; e.bn = BN; e.rowb = Ut.rb1; e.tileb = tb;
+  e.gacc = tc_gacc(Ut.kp, 0); e.gcan = tc_gcan(idx->d);
+  e.ybin = idx->ybin; e.yg0 = idx->yg0; e.ytop = ytop; e.ybot = ybot;
+  e.DLO = idx->DLO; e.DHI = idx->DHI;
+  rkr_status s = launch_screen<BN, tc::stages1<BN, EpiDeep>()>(Ut, Pt, 0, row_schedule(n, m, BN),
+                                                              e, flags, st);
+  int hf[2] = {0, 0};
+  cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
+  cudaError_t err = cudaStreamSynchronize(st);
+  for (void *p : {(void *)tb, (void *)flags}) cudaFreeAsync(p, st);
+  if (err != cudaSuccess) return cuda_fail(err, "tc_deep_table");
+  RKR_TRY(s);
+  if (hf[0]) return fail(RKR_ETIMEOUT, "deep-grid screen wait timed out (%d)", hf[0]);
+  return RKR_OK;
+}
+
 // ================================================================= theta
 
 constexpr int kThetaBN = 128;

@@ -258,3 +258,42 @@ def test_recount_many_thresholds_per_user(split_first):
         assert st.recounted > 10 * st.recount_users   # many thresholds per user
     finally:
         rkr.rkr_tuning_set(**before)
+
+
+def check_deep_grid(gpu, U, P):
+    """The deep count grid: DLO <= #{p : s(u,p) > y_c} <= DHI for every user and
+    grid point, y_c = y_0 + c * step from the exported grid."""
+    S = oracle.scores(U, P)
+    grid = gpu.export("dgrid")
+    dlo, dhi = gpu.export("dlo"), gpu.export("dhi")
+    G = dlo.shape[1]
+    x0 = gpu.export("xgrid")[:, 0]
+    assert G == rkr.DEEP_GRID
+    for i in range(U.shape[0]):
+        assert grid[i, 0] <= x0[i], i
+        y = grid[i, 0] + np.arange(G, dtype=np.float64) * grid[i, 1]
+        srt = np.sort(S[i])
+        cnt = S.shape[1] - np.searchsorted(srt, y, side="right")
+        assert (dlo[i] <= cnt).all() and (cnt <= dhi[i]).all(), i
+
+
+@pytest.mark.parametrize("floor_rank", [8, 40])
+def test_deep_grid_bounds_and_fewer_recounts(floor_rank):
+    """exact_table = 2 adds the deep count grid below the tail lists: its bounds
+    hold for every user against brute-force counts, the answers stay the
+    oracle's, and queries deep below the floor rank recount fewer candidates."""
+    rng = np.random.default_rng(100 + floor_rank)
+    U, P = _rows(rng, 3000, 48), _rows(rng, 4000, 48)
+    Q = np.vstack([P[:6], 1e-3 * P[6:9], _rows(rng, 3, 48), np.zeros((1, 48), np.float32)])
+    k = np.array([1, 5, 20, 60, 7, 13, 30, 2, 50, 9, 25, 3, 11], dtype=np.int32)
+    pos = synth.sample_positions(0, oracle.bucket_sizes(P.shape[0], 6), 30)
+    plain = rkr.Index(U, P, tau=40, omega=6, s=30, sample_pos=pos, exact_table=True,
+                      floor_rank=floor_rank)
+    deep = rkr.Index(U, P, tau=40, omega=6, s=30, sample_pos=pos, exact_table=2,
+                     floor_rank=floor_rank)
+    check_deep_grid(deep, U, P)
+    st_plain = check_exact(U, P, Q, k, plain)
+    st_deep = check_exact(U, P, Q, k, deep)
+    assert st_deep.recounted < st_plain.recounted, (st_deep.recounted, st_plain.recounted)
+    with pytest.raises(rkr.RKRError):
+        rkr.Index(U, P, tau=40, omega=6, s=30, sample_pos=pos, exact_table=3)

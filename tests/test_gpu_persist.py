@@ -28,14 +28,17 @@ def _index_and_queries(exact_table=True):
     return w, idx
 
 
-@pytest.mark.parametrize("exact_table", [True, False])
+@pytest.mark.parametrize("exact_table", [True, False, 2])
 def test_round_trip_answers_bit_for_bit(tmp_path, exact_table):
     w, idx = _index_and_queries(exact_table)
     path = str(tmp_path / "index.rkr")
     with idx:
         a0 = idx.query_approx(w.Q, w.k, 2.0)
         e0 = idx.query_exact(w.Q, w.k) if exact_table else None
-        ex0 = {n: idx.export(n) for n in ("perm", "fmin", "fmax", "table", "samples", "pnorm")}
+        names = ("perm", "fmin", "fmax", "table", "samples", "pnorm")
+        if exact_table == 2:
+            names += ("dlo", "dhi", "dgrid")
+        ex0 = {n: idx.export(n) for n in names}
         idx.save(path)
     with rkr.Index.load(path) as idx2:
         assert idx2.info == idx.info
