@@ -312,6 +312,7 @@ def bench_ours(args):
                         "10,000 queries from P, k in {10,50,100}, c=2, tau=500, omega=10, s=100",
             "l2": "inputs larger than L2 (U is 800 MB)",
             "parallelism": f"replicas x{ws}",
+            "tuning": rkr.rkr_tuning_get(),
         },
         "user_item_scores_per_s": w.n * w.m / (ms / 1000.0),
         "phases_ms": {
@@ -567,6 +568,8 @@ def bench_uneven(args):
         note(f"step: exact {t_e:.0f} ms, approximate {t_a:.0f} ms")
     prof = rkr.rkr_profile_stop()
     mem = idx.device_bytes()
+    note("screen forms against the floor thresholds")
+    forms = screen_forms_at_floor(rkr, idx, w)
     idx.close()
     kernels = {kk: v for kk, v in prof.items() if not kk.startswith("span:")}
     rows_of = {kk: v[2] / (2.0 * w.m * w.d) for kk, v in kernels.items() if v[2] > 0}
@@ -598,7 +601,27 @@ def bench_uneven(args):
         "kernels_ms_per_step": {kk: round(v[1] / args.steps, 3) for kk, v in
                                 sorted(kernels.items(), key=lambda kv: -kv[1][1])[:14]},
         "generation_s": t_gen,
-        "screen": "BF16 single and split products; the E4M3 screen is not on this path"}))
+        "screen": "BF16 single and split products; the E4M3 screen is not on this path",
+        "screen_forms_at_floor": forms}))
+
+
+def screen_forms_at_floor(rkr, idx, w, users=128, seed=5):
+    """After the timed region: for a sample of users and every item, the fraction
+    of (user, item) pairs whose screened interval [s_hat - b, s_hat + b] contains
+    the user's floor threshold x_0 (the comparison the exact table and the recount
+    must settle), for the E4M3 screen, the single and the split BF16 products."""
+    rng = np.random.default_rng(seed)
+    sample = np.sort(rng.choice(w.n, size=min(users, w.n), replace=False))
+    x0 = idx.export("xgrid")[sample, 0][:, None]
+    out = {"users": int(len(sample)), "items": int(w.m), "threshold": "x_0 (floor rank)"}
+    for name, split in (("e4m3", 2), ("bf16_single", False), ("bf16_split", True)):
+        sc, b = rkr.rkr_screen_scores(w.U[sample], w.P, split=split)
+        open_ = np.abs(sc.astype(np.float64) - x0) <= b
+        out[name] = {"undecided_fraction": float(open_.mean()),
+                     "median_bound_over_abs_score":
+                         float(np.median(b / np.maximum(np.abs(sc), 1e-30)))}
+        del sc, b, open_
+    return out
 
 
 def bench_latency(args):
@@ -884,7 +907,13 @@ def main():
                     help="small: a 40k-user profiling case (no CPU baseline, no e2e); "
                          "learned: train the rank regressor and compare the learned cut "
                          "with the plain exact query")
+    ap.add_argument("--tuning", default=None,
+                    help='rkr_tuning fields as JSON (e.g. \'{"rc_seg_min": 4}\'), set before '
+                         "the run; the line reports the tuning in effect")
     args = ap.parse_args()
+    if args.tuning and args.impl == "ours":
+        import paper_2504_13446_gb300 as rkr
+        rkr.rkr_tuning_set(**json.loads(args.tuning))
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl == "ours":
         # one rank per GPU: load the build without cluster multicast
         os.environ["RKR_LIB_VARIANT"] = "replica"

@@ -446,6 +446,10 @@ void rkr_pruner_free(rkr_pruner *pr);
  *                    0 one CTA per SM; 1 CTA pairs sharing each B chunk by cluster
  *                    multicast; 2 CTA pairs issuing 2-SM MMAs (M = 256), each CTA
  *                    staging half of B.  The multicast-free build runs every form as 0.
+ *   split_cat        1: split-product screens whose sides carry concatenated operands
+ *                    ([hi | lo | hi] rows of U, [lo | hi | hi] rows of P and Q) run as one
+ *                    pass over K = 3 K' (fewer pipeline stages when K' is not a multiple
+ *                    of 64, the same MMAs in the same order); 0: three K' segments
  * rkr_tuning_set validates every field (RKR_EINVAL) and applies to calls that start
  * after it returns; rkr_tuning_get reads the current values.
  *
@@ -468,6 +472,7 @@ typedef struct {
   int32_t latency_bulk;
   int32_t screen_form;
   int32_t rc_seg_min;
+  int32_t split_cat;
 } rkr_tuning;
 rkr_status rkr_tuning_get(rkr_tuning *out);
 rkr_status rkr_tuning_set(const rkr_tuning *in);

@@ -75,7 +75,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("rc_bn", ctypes.c_int32), ("rc_single_first", ctypes.c_int32),
                 ("skip_level", ctypes.c_int32), ("cand_budget_log2", ctypes.c_int32),
                 ("latency_ctas_per_sm", ctypes.c_int32), ("latency_bulk", ctypes.c_int32),
-                ("screen_form", ctypes.c_int32), ("rc_seg_min", ctypes.c_int32)]
+                ("screen_form", ctypes.c_int32), ("rc_seg_min", ctypes.c_int32),
+                ("split_cat", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

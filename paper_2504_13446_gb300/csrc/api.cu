@@ -531,6 +531,7 @@ static rkr_status stage_queries(rkr_index *idx, const float *Q, int nq, const in
     }
   }
   RKR_TRY(tc_stage(qc.Qd, nq, d, qs.Qt, st));
+  RKR_TRY(tc_make_cat(qs.Qt, 2, st));
   qc.Qt = qs.Qt;
   return RKR_OK;
 }
@@ -868,6 +869,10 @@ rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t 
   } else {
     RKR_TRY(tc_stage((const float *)vu.dev, n, d, A, st));
     RKR_TRY(tc_stage((const float *)vx.dev, mx, d, B, st));
+    if (split == 1) {
+      RKR_TRY(tc_make_cat(A, 1, st));
+      RKR_TRY(tc_make_cat(B, 2, st));
+    }
     r = tc_scores(A, B, split, (float *)os.dev, (float *)ob.dev, err, st);
   }
   int herr = 0;

@@ -582,6 +582,8 @@ rkr_status build_index(rkr_index *idx, const float *U_dev, const float *P_dev,
   RKR_TRY(max_float(idx->pnrm_s, m, &idx->pmax, st));
   RKR_TRY(tc_stage(idx->U, n, d, idx->Ut, st));
   RKR_TRY(tc_stage(idx->Ps, m, d, idx->Pt, st));
+  RKR_TRY(tc_make_cat(idx->Ut, 1, st));
+  RKR_TRY(tc_make_cat(idx->Pt, 2, st));
   // hash table of the sorted item rows (a query equal to an item ties with it exactly)
   idx->phn = Np2;
   RKR_TRY(dalloc(&idx->phk, Np2));

@@ -164,6 +164,9 @@ extern "C" rkr_status rkr_index_device_bytes(const rkr_index *idx_c, int64_t *ou
                         cudaMemcpyDeviceToHost));
   int64_t tot = 0;
   for (const Arr &a : arrays(idx, list_entries)) tot += (int64_t)a.bytes;
+  // the concatenated split operands (derived, not saved)
+  for (const TcSide *t : {&idx->Ut, &idx->Pt})
+    if (t->cat) tot += (int64_t)t->rows * 3 * t->kp * 2;
   *out = tot;
   return RKR_OK;
 }
@@ -312,6 +315,10 @@ extern "C" rkr_status rkr_index_load(const char *path, rkr_index **out) {
   if (sum != want) return fail(RKR_EINVAL, "index file checksum mismatch");
   char extra;
   if (fread(&extra, 1, 1, fh.f) != 0) return fail(RKR_EINVAL, "index file has trailing bytes");
+  // the concatenated split operands are derived from hi and lo, not stored
+  RKR_TRY(tc_make_cat(idx->Ut, 1, (cudaStream_t)0));
+  RKR_TRY(tc_make_cat(idx->Pt, 2, (cudaStream_t)0));
+  RKR_CUDA(cudaStreamSynchronize((cudaStream_t)0));
   *out = idx;
   guard.x = nullptr;
   return RKR_OK;

@@ -77,15 +77,51 @@ rkr_status tc_stage(const float *X, int64_t rows, int d, TcSide &out, cudaStream
   return RKR_OK;
 }
 
+// cat row = three kp-wide segments: role 1 (A) [hi | lo | hi], role 2 (B) [lo | hi | hi],
+// so that segment g of A times segment g of B is the split's g-th product.
+__global__ void k_make_cat(const __nv_bfloat16 *__restrict__ hi,
+                           const __nv_bfloat16 *__restrict__ lo, int64_t rows, int kp, int role,
+                           __nv_bfloat16 *__restrict__ cat) {
+  const int64_t words = (int64_t)kp / 8;   // 16-byte words per segment
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows * 3 * words) return;
+  const int64_t r = i / (3 * words), w = i - r * 3 * words;
+  const int g = (int)(w / words);
+  const int64_t c = w - (int64_t)g * words;
+  const bool from_lo = role == 1 ? g == 1 : g == 0;
+  const uint4 *src = (const uint4 *)((from_lo ? lo : hi) + r * kp) + c;
+  ((uint4 *)(cat + r * 3 * kp))[w] = *src;
+}
+
+rkr_status tc_make_cat(TcSide &s, int role, cudaStream_t st) {
+  if (s.cat || s.rows <= 0 || split_chunks_cat(s.kp) >= split_chunks_segmented(s.kp))
+    return RKR_OK;
+  const size_t bytes = (size_t)s.rows * 3 * s.kp * 2;
+  cudaError_t e = pool_malloc_async((void **)&s.cat, bytes, st);
+  if (e != cudaSuccess) {   // the segmented form still works: go on without
+    cudaGetLastError();
+    s.cat = nullptr;
+    return RKR_OK;
+  }
+  s.cat_role = role;
+  const int64_t total = s.rows * 3 * (s.kp / 8);
+  k_make_cat<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s.hi, s.lo, s.rows, s.kp, role,
+                                                              s.cat);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
 void tc_free(TcSide &s) {
   if (!s.owned) return;
   // back to the pool once nothing uses them (the staging may have run on any stream)
   cudaDeviceSynchronize();
-  for (void *p : {(void *)s.hi, (void *)s.lo, (void *)s.rb1, (void *)s.rb3})
+  for (void *p : {(void *)s.hi, (void *)s.lo, (void *)s.rb1, (void *)s.rb3, (void *)s.cat})
     if (p) cudaFreeAsync(p, (cudaStream_t)0);
   cudaStreamSynchronize((cudaStream_t)0);
-  s.hi = s.lo = nullptr;
+  s.hi = s.lo = s.cat = nullptr;
   s.rb1 = s.rb3 = nullptr;
+  s.cat_role = 0;
 }
 
 __global__ void k_tile_bounds(const tc::RowBound *__restrict__ rb, int64_t rows, int bn,

@@ -705,11 +705,13 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
 // gives bounds [jl, jh] of c(s) = #{c : y_c < s} (bin_interval); the item adds
 // to Hlo[jl] and Hhi[jh], and DLO[c] = #{jl > c} <= #{p : s(u,p) > y_c} <=
 // #{jh > c} = DHI[c], as for the exact grid of the tail lists.  Items whose
-// upper end lies below y_0 add to no count and are skipped after one compare;
-// items certainly above the whole grid (jl = G) are only counted.  The two
-// histograms of a row are one array of 64-bit words (Hlo in the low half, Hhi
-// in the high half: one atomic when jl = jh), per row in shared memory and
-// stored [bin][row] so that a warp's 32 rows never share a bank.
+// upper end lies below y_0 add to no count; items certainly above the whole
+// grid (jl = G) are only counted.  Scores inside the grid are about an eighth
+// of all: each lane marks its in-grid scores of a chunk in a bit mask, parks
+// the chunk in a shared tile and walks only its own marked ones, so a warp
+// spends the bin arithmetic on the largest per-lane count of the chunk instead
+// of on all 32 columns.  The histograms are 32-bit counters per row in shared
+// memory, stored [bin][row] so that a warp's 32 rows never share a bank.
 struct EpiDeep {
   static const char *name() { return "k_screen<EpiDeep>"; }
   static constexpr int kBins = kDGrid + 1;
@@ -723,7 +725,9 @@ struct EpiDeep {
     tc::RowBound ru;
     TilePrefetch tp;
   };
-  static constexpr size_t kSmem = sizeof(unsigned long long) * 128 * kBins;
+  static constexpr size_t kHist = sizeof(uint32_t) * 128 * kBins;   // one of Hlo, Hhi
+  static constexpr size_t kStageOff = 2 * kHist;
+  static constexpr size_t kSmem = kStageOff + sizeof(float) * 8 * 32 * 32;
   int64_t nrows, ncols;
   int bn;
   const tc::RowBound *rowb, *tileb;
@@ -734,11 +738,10 @@ struct EpiDeep {
   const float *ytop;       // per row: the grid's top point rounded up to float
   const float *ybot;       // per row: the grid's first point rounded down to float
   uint32_t *DLO, *DHI;     // n x kDGrid
-  __device__ static unsigned long long *hist(char *S, int r) {
-    return (unsigned long long *)S + r;
-  }
+  __device__ static uint32_t *hlo(char *S, int r) { return (uint32_t *)S + r; }
+  __device__ static uint32_t *hhi(char *S, int r) { return (uint32_t *)(S + kHist) + r; }
   __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &ts) const {
-    for (int i = et; i < 128 * kBins; i += 256) ((unsigned long long *)S)[i] = 0ull;
+    for (int i = et; i < 2 * 128 * kBins; i += 256) ((uint32_t *)S)[i] = 0u;
     ts.row = -1;
     ts.top = 0;
     ts.tp.start(tileb, u.ct0);
@@ -760,22 +763,37 @@ struct EpiDeep {
                         Thread &ts) const {
     if (ts.row >= nrows) return;
     const int64_t c0 = (int64_t)ct * bn + col;
-    const int64_t left = ncols - c0;
-#pragma unroll 8
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
+    float *tile = (float *)(S + kStageOff) + warp * 32 * 32 + lane;
+    // in-grid scores: upper end at or above the grid's first point, lower end not
+    // above its top; the lower end of s_hat - b is above top_lo iff s_hat > top_lo + b
+    // up to the rounding, which is taken on the bin side below
+    uint32_t mask = 0, above = 0;
+#pragma unroll
     for (int j = 0; j < 32; ++j) {
-      if (j >= left) break;
-      const float lo = __fsub_rd(v[j], ts.b), hi = __fadd_ru(v[j], ts.b);
-      if (hi < ts.bot_hi) continue;                   // below the grid: counts nowhere
-      if (lo > ts.top_lo) { ++ts.top; continue; }   // above every grid point
+      tile[j * 32] = v[j];
+      const float hi = __fadd_ru(v[j], ts.b), lo = __fsub_rd(v[j], ts.b);
+      mask |= (hi >= ts.bot_hi ? 1u : 0u) << j;
+      above |= (lo > ts.top_lo ? 1u : 0u) << j;
+    }
+    const int64_t left = ncols - c0;
+    if (left < 32) {
+      const uint32_t keep = left <= 0 ? 0u : (1u << left) - 1u;
+      mask &= keep;
+      above &= keep;
+    }
+    above &= mask;
+    ts.top += (uint32_t)__popc(above);
+    mask &= ~above;
+    while (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const float x = tile[j * 32];
       int jl, jh;
-      bin_interval(ts.bf, ts.g0, kDGrid, lo, hi, jl, jh);
+      bin_interval(ts.bf, ts.g0, kDGrid, __fsub_rd(x, ts.b), __fadd_ru(x, ts.b), jl, jh);
       if (jh == 0) continue;
-      if (jl == jh) {
-        atomicAdd(&hist(S, r)[jl * 128], 0x100000001ull);
-      } else {
-        atomicAdd(&hist(S, r)[jl * 128], 1ull);
-        atomicAdd(&hist(S, r)[jh * 128], 0x100000000ull);
-      }
+      atomicAdd(&hlo(S, r)[jl * 128], 1u);
+      atomicAdd(&hhi(S, r)[jh * 128], 1u);
     }
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
@@ -783,16 +801,17 @@ struct EpiDeep {
     const int w = (et >> 5) + 2, lane = et & 31;
     const int r = (w & 3) * 32 + lane, half = et >> 7;
     const int64_t row = (int64_t)u.rb0 * tc::BM + r;
-    if (row < nrows && ts.top)
-      atomicAdd(&hist(S, r)[kDGrid * 128], (unsigned long long)ts.top * 0x100000001ull);
+    if (row < nrows && ts.top) {
+      atomicAdd(&hlo(S, r)[kDGrid * 128], ts.top);
+      atomicAdd(&hhi(S, r)[kDGrid * 128], ts.top);
+    }
     tc::epi_sync();
     if (row >= nrows || half != 0) return;
     // DLO[c] = sum over bins above c
     uint32_t rl = 0, rh = 0;
     for (int c = kDGrid; c >= 1; --c) {
-      const unsigned long long hv = hist(S, r)[c * 128];
-      rl += (uint32_t)hv;
-      rh += (uint32_t)(hv >> 32);
+      rl += hlo(S, r)[c * 128];
+      rh += hhi(S, r)[c * 128];
       DLO[row * kDGrid + (c - 1)] = rl;
       DHI[row * kDGrid + (c - 1)] = rh;
     }
@@ -801,7 +820,8 @@ struct EpiDeep {
 
 rkr_status tc_deep_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, const float *ytop,
                          const float *ybot, cudaStream_t st) {
-  constexpr int BN = 256;
+  // 128-column tiles: four 32 KB stages fit beside the histograms and the tile
+  constexpr int BN = 128;
   const int64_t n = idx->n, m = idx->m;
   int *flags;
   tc::RowBound *tb = nullptr;
@@ -1176,10 +1196,11 @@ struct EpiTable {
     if (ts.u >= nrows) return;
     const int64_t c0 = (int64_t)ct * kTableBN + col;
     uint32_t *Wu = W + ts.u * (tau + 1);
-#pragma unroll 4
+    // fully unrolled with predicates so that v stays in registers
+#pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int64_t p = c0 + j;
-      if (p >= ncols) break;
+      if (p >= ncols) continue;
       const float b = tc::screen_bound_tc(ts.ru, colb[p], gacc, gcan);
       int jlo, jhi;
       bin_interval(ts.bf, ts.fm, tau, __fsub_rd(v[j], b), __fadd_ru(v[j], b), jlo, jhi);
@@ -1238,10 +1259,11 @@ struct EpiTableSm {
     if (ts.u >= nrows) return;
     const int64_t c0 = (int64_t)ct * EpiTable::kTableBN + col;
     uint32_t *H = (uint32_t *)S + r * kBinWords;
-#pragma unroll 4
+    // fully unrolled with predicates so that v stays in registers
+#pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int64_t p = c0 + j;
-      if (p >= ncols) break;
+      if (p >= ncols) continue;
       const float b = tc::screen_bound_tc(ts.ru, colb[p], gacc, gcan);
       int jlo, jhi;
       bin_interval(ts.bf, ts.fm, tau, __fsub_rd(v[j], b), __fadd_ru(v[j], b), jlo, jhi);

@@ -18,11 +18,24 @@ struct TcSide {
   __nv_bfloat16 *hi = nullptr, *lo = nullptr;
   tc::RowBound *rb1 = nullptr;   // single product terms
   tc::RowBound *rb3 = nullptr;   // split product terms
+  // Split operand with the three products' K ranges side by side (row pitch
+  // 3 kp): [hi | lo | hi] for A (cat_role 1), [lo | hi | hi] for B (cat_role 2).
+  // One pass over K = 3 kp issues the split's MMAs in the same order on the same
+  // slices, so the scores are bit-identical, in fewer pipeline stages when kp is
+  // not a multiple of 64 (d = 200: 10 stages per tile instead of 12).
+  __nv_bfloat16 *cat = nullptr;
+  int cat_role = 0;
   bool owned = true;
 };
 
 // Stage float rows into a TcSide (allocates).  rows may be 0.
 rkr_status tc_stage(const float *X, int64_t rows, int d, TcSide &out, cudaStream_t st);
+// K chunks of one split-product tile: three segments of kp, or one of 3 kp.
+inline int split_chunks_segmented(int kp) { return 3 * ((kp + 63) / 64); }
+inline int split_chunks_cat(int kp) { return (3 * kp + 63) / 64; }
+// Build the side's concatenated split operand for the given role (1 = A, 2 = B)
+// from hi and lo (allocates); nothing is built when it would save no stage.
+rkr_status tc_make_cat(TcSide &s, int role, cudaStream_t st);
 void tc_free(TcSide &s);
 
 // Per column-tile maxima of the bound terms of a side used as B with tiles of bn rows.
@@ -82,17 +95,23 @@ bool launch_cluster_pairs(K kern, size_t smem, const tc::Schedule &sch, cudaStre
 template <int BN, int STAGES, class Epi>
 rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::Schedule &sch,
                          const Epi &epi, int *err_dev, cudaStream_t st) {
+  // a split product over concatenated operands runs as one pass over K = 3 kp
+  const bool cat = split == 1 && tuning().split_cat && A.cat && B.cat && A.cat_role == 1 &&
+                   B.cat_role == 2;
+  const __nv_bfloat16 *ah = cat ? A.cat : A.hi, *al = cat ? A.cat : A.lo;
+  const __nv_bfloat16 *bh = cat ? B.cat : B.hi, *bl = cat ? B.cat : B.lo;
+  const int kw = cat ? 3 * A.kp : A.kp;
   CUtensorMap mAh, mAl, mBh, mBl;
-  RKR_TRY(make_map(&mAh, A.hi, A.rows, A.kp, tc::BM));
-  RKR_TRY(make_map(&mAl, A.lo, A.rows, A.kp, tc::BM));
-  RKR_TRY(make_map(&mBh, B.hi, B.rows, B.kp, BN));
-  RKR_TRY(make_map(&mBl, B.lo, B.rows, B.kp, BN));
+  RKR_TRY(make_map(&mAh, ah, A.rows, kw, tc::BM));
+  RKR_TRY(make_map(&mAl, al, A.rows, kw, tc::BM));
+  RKR_TRY(make_map(&mBh, bh, B.rows, kw, BN));
+  RKR_TRY(make_map(&mBl, bl, B.rows, kw, BN));
   tc::Operands op;
   op.nrows = A.rows;
   op.ncols = B.rows;
-  op.kchunks = (A.kp + tc::KCH - 1) / tc::KCH;
-  op.ksteps = A.kp / 16;
-  op.split = split;
+  op.kchunks = (kw + tc::KCH - 1) / tc::KCH;
+  op.ksteps = kw / 16;
+  op.split = cat ? 0 : split;
   op.epi_wait = epi_wait_limit();
   const size_t smem = tc::screen_smem_bytes<BN, STAGES, Epi>();
   int grid = std::min(sch.nunits, sm_count());
@@ -109,8 +128,8 @@ rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::
     auto pk = tc::k_screen_2sm<BN, S2, Epi>;
     RKR_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
     CUtensorMap mBh2, mBl2;
-    RKR_TRY(make_map(&mBh2, B.hi, B.rows, B.kp, BN / 2));
-    RKR_TRY(make_map(&mBl2, B.lo, B.rows, B.kp, BN / 2));
+    RKR_TRY(make_map(&mBh2, bh, B.rows, kw, BN / 2));
+    RKR_TRY(make_map(&mBl2, bl, B.rows, kw, BN / 2));
     if (launch_cluster_pairs(pk, smem2, sch, st, mAh, mAl, mBh2, mBl2, op, epi, err_dev))
       return RKR_OK;
     RKR_CUDA(cudaGetLastError());
@@ -120,8 +139,8 @@ rkr_status launch_screen(const TcSide &A, const TcSide &B, int split, const tc::
     auto pk = tc::k_screen_pair<BN, STAGES, Epi>;
     RKR_CUDA(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CUtensorMap mBh2, mBl2;
-    RKR_TRY(make_map(&mBh2, B.hi, B.rows, B.kp, BN / 2));
-    RKR_TRY(make_map(&mBl2, B.lo, B.rows, B.kp, BN / 2));
+    RKR_TRY(make_map(&mBh2, bh, B.rows, kw, BN / 2));
+    RKR_TRY(make_map(&mBl2, bl, B.rows, kw, BN / 2));
     if (launch_cluster_pairs(pk, smem, sch, st, mAh, mAl, mBh2, mBl2, op, epi, err_dev))
       return RKR_OK;
     RKR_CUDA(cudaGetLastError());

@@ -98,3 +98,64 @@ def test_approx_workload_full_size_approximate_answers():
         assert (got["n_up"][sl] == want["n_up"]).all(), q
         assert (got["est"][sl] == want["est"]).all(), q
         assert got["case"][q] == want["case"] and got["nc"][q] == want["nc"], q
+
+
+def test_uneven_workload_full_size():
+    """The uneven batch at full size: 2M users x 1M items x d = 128 (mixture of 1,024
+    centres), 4,096 queries with k log-uniform in [1, 1000] and a user subset per query
+    (10-100 % of U in 1,024-user blocks, as bitmaps); exact tables with floor rank 2,048
+    and the deep count grid, as the benchmark builds them.  For sampled queries every
+    returned user is in the query's subset and its rank is the oracle's; sampled members
+    of the subset outside the answer rank no better than the k-th.  For sampled users
+    f_min, f_max and the Eq. 1 numerators equal the oracle's, and the deep grid's count
+    bounds hold against brute-force counts.  The c-approximate answers of sampled
+    queries are k distinct users of their subsets."""
+    w = synth.make_workload("uneven")
+    member = w.subset_bitmaps()
+    sizes = oracle.bucket_sizes(w.m, w.omega)
+    pos = synth.sample_positions(w.seed, sizes, w.s)
+    rng = np.random.default_rng(24)
+    with rkr.Index(w.U, w.P, tau=w.tau, omega=w.omega, s=w.s, fbounds="exact",
+                   exact_table=2, floor_rank=2048, sample_pos=pos) as idx:
+        users, ranks, off, _ = idx.query_exact(w.Q, w.k, member=member)
+        approx = idx.query_approx(w.Q, w.k, 2.0, member=member)
+        sample = np.sort(rng.choice(w.n, size=12, replace=False))
+        fmin, fmax = idx.export("fmin")[sample], idx.export("fmax")[sample]
+        table = idx.export("table")[sample]
+        grid, dlo, dhi = (idx.export(x)[sample] for x in ("dgrid", "dlo", "dhi"))
+
+    def in_subset(q, u):
+        return ((member[q, u >> 5] >> (u & 31)) & 1).astype(bool)
+
+    # small, median and large k, and two more at random
+    order = np.argsort(w.k, kind="stable")
+    queries = np.unique(np.concatenate([order[[0, len(order) // 2, -1]],
+                                        rng.choice(w.Q.shape[0], 2, replace=False)]))
+    for q in queries:
+        sl = slice(off[q], off[q + 1])
+        u, r = users[sl], ranks[sl]
+        assert len(u) == w.k[q] and in_subset(q, u).all(), q
+        picked = u if len(u) <= 24 else np.concatenate([u[:12], rng.choice(u[12:], 12,
+                                                                          replace=False)])
+        want = oracle.ranks(w.U[picked], w.P, w.Q[q:q + 1])[:, 0]
+        pos_of = {int(x): i for i, x in enumerate(u)}
+        assert all(r[pos_of[int(x)]] == y for x, y in zip(picked, want)), q
+        key = r.astype(np.int64) * (1 << 32) + u.astype(np.int64)
+        assert (np.diff(key) > 0).all(), q
+        kth, last = int(r.max()), int(u[r == r.max()].max())
+        cand = rng.choice(w.n, size=400, replace=False)
+        others = np.setdiff1d(cand[in_subset(q, cand)], u)[:150]
+        ro = oracle.ranks(w.U[others], w.P, w.Q[q:q + 1])[:, 0]
+        assert ((ro > kth) | ((ro == kth) & (others > last))).all(), q
+        asl = slice(approx["offsets"][q], approx["offsets"][q + 1])
+        au = approx["users"][asl]
+        assert len(au) == w.k[q] and in_subset(q, au).all() and len(np.unique(au)) == len(au)
+    ora = oracle.build_index(w.U[sample], w.P, w.tau, w.omega, w.s, pos)
+    assert (fmin == ora["fmin"]).all() and (fmax == ora["fmax"]).all()
+    assert (table == ora["N"]).all()
+    S = oracle.scores(w.U[sample], w.P)
+    G = dlo.shape[1]
+    for i in range(len(sample)):
+        y = grid[i, 0] + np.arange(G, dtype=np.float64) * grid[i, 1]
+        cnt = S.shape[1] - np.searchsorted(np.sort(S[i]), y, side="right")
+        assert (dlo[i] <= cnt).all() and (cnt <= dhi[i]).all(), i

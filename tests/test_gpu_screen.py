@@ -39,6 +39,23 @@ def test_screen_within_bound(n, mx, d, split):
     assert np.median(ratio) < 0.5
 
 
+@pytest.mark.parametrize("d", [200, 32, 72])
+def test_split_over_concatenated_operands_is_bit_identical(d):
+    """The split product run as one pass over [hi | lo | hi] x [lo | hi | hi] (K = 3 K')
+    issues the same MMAs in the same order as the three K' segments: equal bits."""
+    rng = np.random.default_rng(d)
+    U, X = _rows(rng, 300, d), _rows(rng, 700, d)
+    before = rkr.rkr_tuning_get()
+    try:
+        rkr.rkr_tuning_set(split_cat=1)
+        s1, b1 = rkr.rkr_screen_scores(U, X, split=True)
+        rkr.rkr_tuning_set(split_cat=0)
+        s0, b0 = rkr.rkr_screen_scores(U, X, split=True)
+    finally:
+        rkr.rkr_tuning_set(**before)
+    assert (s1 == s0).all() and (b1 == b0).all()
+
+
 def test_screen_integer_data_is_exact_when_representable():
     """Small integers are exact in bf16 and their products sum exactly in FP32."""
     rng = np.random.default_rng(1)

@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 rkr = pytest.importorskip("paper_2504_13446_gb300")
 
 DEFAULT = dict(rc_bn=256, rc_single_first=1, skip_level=0, cand_budget_log2=26,
-               latency_ctas_per_sm=0, latency_bulk=0, screen_form=1, rc_seg_min=0)
+               latency_ctas_per_sm=0, latency_bulk=0, screen_form=1, rc_seg_min=0,
+               split_cat=1)
 
 
 def _answers(idx, w):
@@ -37,7 +38,7 @@ def test_every_tuning_gives_the_same_answers(tmp_path):
                            dict(skip_level=9), dict(cand_budget_log2=20),
                            dict(latency_ctas_per_sm=2), dict(latency_bulk=1),
                            dict(screen_form=0), dict(screen_form=2), dict(rc_seg_min=2),
-                           dict(rc_seg_min=4, rc_single_first=0)):
+                           dict(rc_seg_min=4, rc_single_first=0), dict(split_cat=0)):
                 rkr.rkr_tuning_set(**{**DEFAULT, **fields})
                 got = _answers(idx, w)
                 for a, b in zip(got, ref):
@@ -65,8 +66,10 @@ def test_screen_forms_build_the_same_index():
     names = ("fmin", "fmax", "table", "xlo", "xhi", "xgrid")
     ref = None
     try:
-        for form in (0, 1, 2):
-            rkr.rkr_tuning_set(**{**DEFAULT, "screen_form": form})
+        # the split product's two operand layouts (d = 72: K' = 80 gives 4 stages per
+        # tile concatenated against 6 in segments)
+        for form, cat in ((0, 1), (1, 1), (2, 1), (1, 0), (2, 0)):
+            rkr.rkr_tuning_set(**{**DEFAULT, "screen_form": form, "split_cat": cat})
             with rkr.Index(w.U, w.P, tau=48, omega=5, s=30, sample_pos=pos, exact_table=True,
                            floor_rank=40) as idx:
                 got = [idx.export(x) for x in names]
@@ -77,6 +80,6 @@ def test_screen_forms_build_the_same_index():
                 ref = got
                 continue
             for i, (x, y) in enumerate(zip(got, ref)):
-                assert np.array_equal(x, y), (form, i)
+                assert np.array_equal(x, y), (form, cat, i)
     finally:
         rkr.rkr_tuning_set(**DEFAULT)
