@@ -35,6 +35,22 @@ __device__ __forceinline__ double dkey_inverse(uint64_t k) {
 // The bound terms of a column tile, loaded one tile ahead: take(ct) returns
 // tile ct's terms (prefetched when ct is the tile expected next) and starts the
 // load of tile ct + 1, whose latency then overlaps the current tile's work.
+// 32-bit mask of a predicate over the columns j = 0..31 of a chunk, built as four
+// independent OR chains (one chain of 32 dependent ORs serializes the epilogue
+// warps, of which only two share a scheduler).
+template <class F>
+__device__ __forceinline__ uint32_t bitmask32(F &&pred) {
+  uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    m0 |= (pred(j) ? 1u : 0u) << j;
+    m1 |= (pred(j + 1) ? 1u : 0u) << (j + 1);
+    m2 |= (pred(j + 2) ? 1u : 0u) << (j + 2);
+    m3 |= (pred(j + 3) ? 1u : 0u) << (j + 3);
+  }
+  return (m0 | m1) | (m2 | m3);
+}
+
 struct TilePrefetch {
   tc::RowBound next;
   int nct;   // the column tile `next` holds
@@ -174,7 +190,7 @@ struct EpiFb {
     uint32_t mask = 0;
     if (hit) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) mask |= (v[j] >= tmax || v[j] <= tmin ? 1u : 0u) << j;
+      mask = bitmask32([&](int j) { return v[j] >= tmax || v[j] <= tmin; });
       mask &= keep;
     }
     // one queue reservation per warp and chunk
@@ -430,12 +446,9 @@ struct EpiXT {
     const int64_t c0 = (int64_t)ct * bn + col;
     const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
     float *tile = (float *)(S + kStageOff) + warp * 32 * 32 + lane;
-    uint32_t mask = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      tile[j * 32] = v[j];
-      mask |= (v[j] > ts.skip ? 1u : 0u) << j;
-    }
+    for (int j = 0; j < 32; ++j) tile[j * 32] = v[j];
+    uint32_t mask = bitmask32([&](int j) { return v[j] > ts.skip; });
     const int64_t left = ncols - c0;
     if (left < 32) mask &= left <= 0 ? 0u : (1u << left) - 1u;
     if (!mask) return;
@@ -706,12 +719,12 @@ rkr_status tc_exact_table(rkr_index *idx, const TcSide &Ut, const TcSide &Pt, cu
 // to Hlo[jl] and Hhi[jh], and DLO[c] = #{jl > c} <= #{p : s(u,p) > y_c} <=
 // #{jh > c} = DHI[c], as for the exact grid of the tail lists.  Items whose
 // upper end lies below y_0 add to no count; items certainly above the whole
-// grid (jl = G) are only counted.  Scores inside the grid are about an eighth
-// of all: each lane marks its in-grid scores of a chunk in a bit mask, parks
-// the chunk in a shared tile and walks only its own marked ones, so a warp
-// spends the bin arithmetic on the largest per-lane count of the chunk instead
-// of on all 32 columns.  The histograms are 32-bit counters per row in shared
-// memory, stored [bin][row] so that a warp's 32 rows never share a bank.
+// grid go to bin G of both histograms.  Scores reaching the grid are about an
+// eighth of all: each lane marks them in a bit mask, parks the chunk in a
+// shared tile and walks only its own marked ones (branch-free bin arithmetic),
+// so a warp spends it on the largest per-lane count of the chunk instead of on
+// all 32 columns.  The histograms are 32-bit counters per row in shared memory,
+// stored [bin][row] so that a warp's 32 rows never share a bank.
 struct EpiDeep {
   static const char *name() { return "k_screen<EpiDeep>"; }
   static constexpr int kBins = kDGrid + 1;
@@ -719,7 +732,6 @@ struct EpiDeep {
     float b, top_lo;     // bound; lower ends above top_lo are above the whole grid
     float bot_hi;        // upper ends below bot_hi are below the whole grid
     int64_t row;
-    uint32_t top;        // this thread's items certainly above every y_c
     BinFP bf;
     double g0;
     tc::RowBound ru;
@@ -743,7 +755,6 @@ struct EpiDeep {
   __device__ void unit_begin(char *S, const tc::Unit &u, int et, Thread &ts) const {
     for (int i = et; i < 2 * 128 * kBins; i += 256) ((uint32_t *)S)[i] = 0u;
     ts.row = -1;
-    ts.top = 0;
     ts.tp.start(tileb, u.ct0);
   }
   __device__ void tile_begin(char *, int rb, int ct, int r, int, Thread &ts) const {
@@ -765,33 +776,36 @@ struct EpiDeep {
     const int64_t c0 = (int64_t)ct * bn + col;
     const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 2;
     float *tile = (float *)(S + kStageOff) + warp * 32 * 32 + lane;
-    // in-grid scores: upper end at or above the grid's first point, lower end not
-    // above its top; the lower end of s_hat - b is above top_lo iff s_hat > top_lo + b
-    // up to the rounding, which is taken on the bin side below
-    uint32_t mask = 0, above = 0;
+    // scores whose upper end reaches the grid's first point (the others count nowhere)
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      tile[j * 32] = v[j];
-      const float hi = __fadd_ru(v[j], ts.b), lo = __fsub_rd(v[j], ts.b);
-      mask |= (hi >= ts.bot_hi ? 1u : 0u) << j;
-      above |= (lo > ts.top_lo ? 1u : 0u) << j;
-    }
+    for (int j = 0; j < 32; ++j) tile[j * 32] = v[j];
+    uint32_t mask = bitmask32([&](int j) { return __fadd_ru(v[j], ts.b) >= ts.bot_hi; });
     const int64_t left = ncols - c0;
-    if (left < 32) {
-      const uint32_t keep = left <= 0 ? 0u : (1u << left) - 1u;
-      mask &= keep;
-      above &= keep;
-    }
-    above &= mask;
-    ts.top += (uint32_t)__popc(above);
-    mask &= ~above;
+    if (left < 32) mask &= left <= 0 ? 0u : (1u << left) - 1u;
+    const BinFP &bf = ts.bf;
+    const bool fast = bf.invd32 > 0.0f && bf.err <= 1e6f;   // the row's grid has a step
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
       const float x = tile[j * 32];
+      const float lo = __fsub_rd(x, ts.b), hi = __fadd_ru(x, ts.b);
       int jl, jh;
-      bin_interval(ts.bf, ts.g0, kDGrid, __fsub_rd(x, ts.b), __fadd_ru(x, ts.b), jl, jh);
-      if (jh == 0) continue;
+      if (fast) {
+        // bin_interval without branches: the clamps of bin_lo / bin_hi by fminf /
+        // fmaxf (which also send a NaN lower end to 0), a NaN upper end to G
+        float vlo, vhi;
+        bin_coord(bf, lo, hi, vlo, vhi);
+        jl = (int)ceilf(fminf(fmaxf(vlo, 0.0f), (float)kDGrid));
+        const float ch = fminf(floorf(fmaxf(vhi, -1.0f)) + 1.0f, (float)kDGrid);
+        jh = vhi == vhi ? (int)ch : kDGrid;
+      } else {
+        bin_interval(bf, ts.g0, kDGrid, lo, hi, jl, jh);
+      }
+      // certainly above the whole grid: c = G exactly; jh = 0 adds to bin 0, which no
+      // count reads
+      const bool top = lo > ts.top_lo;
+      jl = top ? kDGrid : jl;
+      jh = top ? kDGrid : jh;
       atomicAdd(&hlo(S, r)[jl * 128], 1u);
       atomicAdd(&hhi(S, r)[jh * 128], 1u);
     }
@@ -801,10 +815,6 @@ struct EpiDeep {
     const int w = (et >> 5) + 2, lane = et & 31;
     const int r = (w & 3) * 32 + lane, half = et >> 7;
     const int64_t row = (int64_t)u.rb0 * tc::BM + r;
-    if (row < nrows && ts.top) {
-      atomicAdd(&hlo(S, r)[kDGrid * 128], ts.top);
-      atomicAdd(&hhi(S, r)[kDGrid * 128], ts.top);
-    }
     tc::epi_sync();
     if (row >= nrows || half != 0) return;
     // DLO[c] = sum over bins above c
@@ -1007,10 +1017,8 @@ struct EpiTheta {
   __device__ void chunk(char *S, int, int ct, int r, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * kThetaBN + col;
-    uint32_t pm = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)  // v <= xsb: lower bound above the skip level (NaN kept)
-      pm |= (v[j] <= ts.xsb ? 0u : 1u) << j;
+    // v <= xsb: lower bound above the skip level (NaN kept)
+    uint32_t pm = bitmask32([&](int j) { return !(v[j] <= ts.xsb); });
     const int64_t left = ncols - c0;
     if (left < 32) pm &= left <= 0 ? 0u : (1u << left) - 1u;
     if (ts.u >= nrows) pm = 0;
@@ -1462,10 +1470,8 @@ struct EpiSkim {
   __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * kSkimBN + col;
-    uint32_t pm = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)  // v <= xsb: lower bound above the skip level (NaN kept)
-      pm |= (v[j] <= ts.xsb ? 0u : 1u) << j;
+    // v <= xsb: lower bound above the skip level (NaN kept)
+    uint32_t pm = bitmask32([&](int j) { return !(v[j] <= ts.xsb); });
     const int64_t left = ncols - c0;
     if (left < 32) pm &= left <= 0 ? 0u : (1u << left) - 1u;
     if (ts.u >= nrows) pm = 0;
@@ -1606,12 +1612,8 @@ struct EpiRC {
   __device__ __forceinline__ void chunk(char *, int, int ct, int, int col, uint32_t,
                                         const float (&v)[32], Thread &ts) const {
     const int64_t c0 = (int64_t)ct * bn + col;
-    uint32_t mlo = 0, mhi = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      mlo |= (__fsub_rd(v[j], ts.b) > ts.tup ? 1u : 0u) << j;
-      mhi |= (__fadd_ru(v[j], ts.b) > ts.tdn ? 1u : 0u) << j;
-    }
+    uint32_t mlo = bitmask32([&](int j) { return __fsub_rd(v[j], ts.b) > ts.tup; });
+    uint32_t mhi = bitmask32([&](int j) { return __fadd_ru(v[j], ts.b) > ts.tdn; });
     const int64_t left = ncols - c0;
     if (left < 32) {
       const uint32_t keep = left <= 0 ? 0u : (1u << left) - 1u;
@@ -1747,12 +1749,8 @@ struct EpiRCm {
       if (hist_hi) atomicAdd(&hhi(S, r)[pos * 128], 1u);
       next_self(ts);
     }
-    uint32_t any = 0, topm = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      any |= (__fadd_ru(v[j], ts.b) > ts.t0 ? 1u : 0u) << j;
-      topm |= (__fsub_rd(v[j], ts.b) > ts.tl ? 1u : 0u) << j;
-    }
+    uint32_t any = bitmask32([&](int j) { return __fadd_ru(v[j], ts.b) > ts.t0; });
+    uint32_t topm = bitmask32([&](int j) { return __fsub_rd(v[j], ts.b) > ts.tl; });
     const int64_t left = ncols - c0;
     uint32_t keep = ~smask;
     if (left < 32) keep &= left <= 0 ? 0u : (1u << left) - 1u;

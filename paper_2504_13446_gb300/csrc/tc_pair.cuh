@@ -209,17 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (real) {
           epi.tile_begin(escratch, rb, ct, r, half, ts);
           const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
-          // 64 columns per TMEM load (one wait), handed out as two chunks of 32
-#pragma unroll 1
-          for (int cc = 0; cc < BN / 64; cc += 2) {
-            const int col = half * (BN / 2) + cc * 32;
-            float v[64];
-            tmem_ld64(trow + col, v);
-            epi.chunk(escratch, rb, ct, r, col, trow + (uint32_t)col,
-                      *reinterpret_cast<const float(*)[32]>(v), ts);
-            epi.chunk(escratch, rb, ct, r, col + 32, trow + (uint32_t)(col + 32),
-                      *reinterpret_cast<const float(*)[32]>(v + 32), ts);
-          }
+          epi_tile_columns<BN>(epi, escratch, rb, ct, r, half, trow, ts);
           epi.tile_end(escratch, rb, ct, r, half, ts);
         }
         tc_fence_before();
@@ -490,17 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (real) {
           epi.tile_begin(escratch, rb, ct, r, half, ts);
           const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
-          // 64 columns per TMEM load (one wait), handed out as two chunks of 32
-#pragma unroll 1
-          for (int cc = 0; cc < BN / 64; cc += 2) {
-            const int col = half * (BN / 2) + cc * 32;
-            float v[64];
-            tmem_ld64(trow + col, v);
-            epi.chunk(escratch, rb, ct, r, col, trow + (uint32_t)col,
-                      *reinterpret_cast<const float(*)[32]>(v), ts);
-            epi.chunk(escratch, rb, ct, r, col + 32, trow + (uint32_t)(col + 32),
-                      *reinterpret_cast<const float(*)[32]>(v + 32), ts);
-          }
+          epi_tile_columns<BN>(epi, escratch, rb, ct, r, half, trow, ts);
           epi.tile_end(escratch, rb, ct, r, half, ts);
         }
         tc_fence_before();

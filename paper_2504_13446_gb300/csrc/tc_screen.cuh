@@ -67,6 +67,24 @@ __device__ __forceinline__ bool epi_vote_any(bool p) {
   return r != 0;
 }
 
+// This thread's half row of an accumulator tile (TMEM row address trow): 64
+// columns per TMEM load (one wait), handed to the epilogue as chunks of 32.
+template <int BN, class Epi>
+__device__ __forceinline__ void epi_tile_columns(const Epi &epi, char *S, int rb, int ct, int r,
+                                                 int half, uint32_t trow,
+                                                 typename Epi::Thread &ts) {
+#pragma unroll 1
+  for (int cc = 0; cc < BN / 64; cc += 2) {
+    const int col = half * (BN / 2) + cc * 32;
+    float v[64];
+    tmem_ld64(trow + col, v);
+    epi.chunk(S, rb, ct, r, col, trow + (uint32_t)col,
+              *reinterpret_cast<const float(*)[32]>(v), ts);
+    epi.chunk(S, rb, ct, r, col + 32, trow + (uint32_t)(col + 32),
+              *reinterpret_cast<const float(*)[32]>(v + 32), ts);
+  }
+}
+
 template <int BN>
 struct Layout {
   static_assert(BN == 128 || BN == 256, "column tiles of 128 or 256");
@@ -213,17 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           epi.tile_begin(escratch, rb, ct, r, half, ts);
           const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
-          // 64 columns per TMEM load (one wait), handed out as two chunks of 32
-#pragma unroll 1
-          for (int cc = 0; cc < BN / 64; cc += 2) {
-            const int col = half * (BN / 2) + cc * 32;
-            float v[64];
-            tmem_ld64(trow + col, v);
-            epi.chunk(escratch, rb, ct, r, col, trow + (uint32_t)col,
-                      *reinterpret_cast<const float(*)[32]>(v), ts);
-            epi.chunk(escratch, rb, ct, r, col + 32, trow + (uint32_t)(col + 32),
-                      *reinterpret_cast<const float(*)[32]>(v + 32), ts);
-          }
+          epi_tile_columns<BN>(epi, escratch, rb, ct, r, half, trow, ts);
           epi.tile_end(escratch, rb, ct, r, half, ts);
           tc_fence_before();
           __syncwarp();
