@@ -48,9 +48,10 @@ C = 2.0
 # the bench multiplies this figure by the rows of the timed launches.  Empty
 # until a capture of the current kernel exists (traffic is then reported null).
 TRAFFIC_PER_ROW = {
-    # k_screen_pair<EpiXT>, 40,000 rows: 348.7 + 2,205.4 MB and 351.2 + 2,202.4 MB in two
-    # launches; the tail-list writes (about 55 KB per user) dominate and scale with rows
-    "k_screen<EpiXT>": 63_850.0,
+    # k_screen_pair<EpiXT> (concatenated split operands), 40,000 rows of the 1M x 100k
+    # workload's generator with all items: 495.6 MB read + 2,235.0 MB written in one
+    # launch; the tail-list writes (about 55 KB per user) dominate and scale with rows
+    "k_screen<EpiXT>": 68_265.0,
 }
 
 # Products the tensor cores issue per pair of each screen, relative to the
