@@ -326,6 +326,8 @@ def bench_ours(args):
                        "exact_recount_users": qe0["recount_users"],
                        "exact_recount_split": qe0["recount_split"],
                        "exact_recount_open": qe0["recount_open"],
+                       "exact_prefix_rows": qe0["prefix_rows"],
+                       "exact_prefix_pruned": qe0["prefix_pruned"],
                        "wide_queries": [qa0["wide_queries"], qe0["wide_queries"]],
                        "deep_queries": [qa0["deep_queries"], qe0["deep_queries"]]},
         "approx_quality": quality,

@@ -104,7 +104,8 @@ typedef struct {
                                level is the smallest L with 2^L - 1 >= m / 128, or the
                                value of the environment variable RKR_SKIP_LEVEL; results
                                do not depend on it. */
-  int64_t recount_users;    /* exact path: distinct users among the recounted candidates */
+  int64_t recount_users;    /* exact path: distinct users among the candidates of each
+                               interval pass over all of P, summed over those passes */
   int64_t recount_open;     /* exact path: recounted candidates whose count interval was still
                                open after the interval pass; each of their m item scores is
                                placed exactly, and near_ties of them needed FP64, so
@@ -116,6 +117,10 @@ typedef struct {
   double max_screen_err_ratio; /* exact path: largest |s_hat - s(u,p)| / b over the same pairs
                                as max_rel_screen_err, b the rigorous screen bound (a sound
                                bound keeps it <= 1) */
+  int64_t prefix_rows;      /* exact path: candidates screened against the norm-sorted prefix
+                               of P first (tuning rc_prefix) */
+  int64_t prefix_pruned;    /* of those, candidates dropped by their prefix lower bound
+                               without a recount over all of P */
 } rkr_query_stats;
 
 /*
@@ -450,6 +455,15 @@ void rkr_pruner_free(rkr_pruner *pr);
  *                    ([hi | lo | hi] rows of U, [lo | hi | hi] rows of P and Q) run as one
  *                    pass over K = 3 K' (fewer pipeline stages when K' is not a multiple
  *                    of 64, the same MMAs in the same order); 0: three K' segments
+ *   rc_prefix        0: off; p in [2, 64]: early termination over the norm-sorted items
+ *                    (the order Alg. 1 sorts P in).  When a query has many candidates to
+ *                    recount, all of them are first screened against the first m / p items
+ *                    only (rounded down to 256); a candidate's certain count there is a
+ *                    lower bound of its count over P.  The query's candidates with the
+ *                    smallest possible counts there are recounted over all of P, which
+ *                    gives a cap on the k-th smallest count, and every other candidate
+ *                    whose prefix lower bound exceeds that cap is dropped unrecounted.
+ *                    Default 4.
  * rkr_tuning_set validates every field (RKR_EINVAL) and applies to calls that start
  * after it returns; rkr_tuning_get reads the current values.
  *
@@ -473,6 +487,7 @@ typedef struct {
   int32_t screen_form;
   int32_t rc_seg_min;
   int32_t split_cat;
+  int32_t rc_prefix;
 } rkr_tuning;
 rkr_status rkr_tuning_get(rkr_tuning *out);
 rkr_status rkr_tuning_set(const rkr_tuning *in);

@@ -64,7 +64,8 @@ class QueryStats(ctypes.Structure):
                 ("ms_select", ctypes.c_double), ("recounted", ctypes.c_int64),
                 ("deep_queries", ctypes.c_int32), ("recount_users", ctypes.c_int64),
                 ("recount_open", ctypes.c_int64), ("recount_split", ctypes.c_int64),
-                ("learned_revived", ctypes.c_int64), ("max_screen_err_ratio", ctypes.c_double)]
+                ("learned_revived", ctypes.c_int64), ("max_screen_err_ratio", ctypes.c_double),
+                ("prefix_rows", ctypes.c_int64), ("prefix_pruned", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -76,7 +77,7 @@ class Tuning(ctypes.Structure):
                 ("skip_level", ctypes.c_int32), ("cand_budget_log2", ctypes.c_int32),
                 ("latency_ctas_per_sm", ctypes.c_int32), ("latency_bulk", ctypes.c_int32),
                 ("screen_form", ctypes.c_int32), ("rc_seg_min", ctypes.c_int32),
-                ("split_cat", ctypes.c_int32)]
+                ("split_cat", ctypes.c_int32), ("rc_prefix", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

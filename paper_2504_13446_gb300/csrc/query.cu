@@ -638,6 +638,71 @@ __global__ void k_count_valid(int64_t n, const int32_t *__restrict__ v,
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// Early termination over the norm-sorted items (tuning rc_prefix).  A query
+// takes part when at least prefix_min_rows(k) of its candidates still need a
+// recount; those candidates are copied to cu_pre for the prefix pass.
+__host__ __device__ inline int64_t prefix_pick_rows(int k) { return k * 8 > 256 ? k * 8 : 256; }
+__host__ __device__ inline int64_t prefix_min_rows(int k) { return 8 * prefix_pick_rows(k); }
+
+__global__ void __launch_bounds__(256)
+    k_prefix_split(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
+                   const int32_t *__restrict__ kq, const int32_t *__restrict__ cu_fb,
+                   int32_t *__restrict__ cu_pre, unsigned long long *__restrict__ npre) {
+  __shared__ unsigned long long acc;
+  const int q = qa + blockIdx.x;
+  const int64_t base = qoff[q] - qoff[qa];
+  const int64_t cnt = qcount[q];
+  const int32_t *fb = cu_fb + base;
+  const int64_t nr = block_count(cnt, [&](int64_t i) { return fb[i] >= 0; }, &acc);
+  if (nr < prefix_min_rows(kq[q])) return;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) cu_pre[base + i] = fb[i];
+  if (threadIdx.x == 0) atomicAdd(npre, (unsigned long long)nr);
+}
+
+// Per query of the prefix pass: every prefix row's lower bound takes its certain
+// count over the prefix (a subset of P); the prefix_pick_rows(k) rows with the
+// smallest possible prefix counts (ties included) stay in cu_fb for a recount
+// over all of P, the others are parked in cu_park until the cap is known.
+__global__ void __launch_bounds__(256)
+    k_prefix_pick(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
+                  const int32_t *__restrict__ kq, const int32_t *__restrict__ cu_pre,
+                  const uint32_t *__restrict__ hi1, const uint32_t *__restrict__ lo1,
+                  uint32_t *__restrict__ clb, int32_t *__restrict__ cu_fb,
+                  int32_t *__restrict__ cu_park) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t bc[2];
+  __shared__ unsigned long long acc;
+  const int q = qa + blockIdx.x;
+  const int64_t base = qoff[q] - qoff[qa];
+  const int64_t cnt = qcount[q];
+  const int32_t *pre = cu_pre + base;
+  const int64_t np = block_count(cnt, [&](int64_t i) { return pre[i] >= 0; }, &acc);
+  const uint64_t k2 = (uint64_t)prefix_pick_rows(kq[q]);
+  if (np <= (int64_t)k2) return;
+  const uint32_t *h = hi1 + base, *l = lo1 + base;
+  const uint64_t T = block_kth(cnt, k2, 32,
+                               [&](int64_t i, uint64_t &key) {
+                                 key = h[i];
+                                 return pre[i] >= 0;
+                               },
+                               hist, bc);
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    if (pre[i] < 0) continue;
+    clb[base + i] = max(clb[base + i], l[i]);
+    if ((uint64_t)h[i] > T) {
+      cu_park[base + i] = cu_fb[base + i];
+      cu_fb[base + i] = -1;
+    }
+  }
+}
+
+// Parked rows that the cap did not drop go back to the recount.
+__global__ void k_prefix_unpark(int64_t n, const int32_t *__restrict__ cu_park,
+                                int32_t *__restrict__ cu_fb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && cu_park[i] >= 0) cu_fb[i] = cu_park[i];
+}
+
 // One CTA per query: the k smallest (rank, index) among its candidates.
 __global__ void __launch_bounds__(kSelThreads)
     k_select_exact(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
@@ -1158,12 +1223,15 @@ __global__ void k_scatter_back(int64_t n, const int32_t *__restrict__ oi,
 // tensor-core pass over P per user.  ccount[i] = #{p : s(u_i, p) > u_i.q_i}.
 // With clb_all (bounds mode) items the screen cannot place are not resolved:
 // ccount gets an upper and clb a lower bound of the count instead.
+// With ncols > 0 only the first ncols items of the norm-sorted P are screened.
 static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int64_t total,
                                      const int32_t *cu_all, const int32_t *cq_all,
                                      const int32_t *qself, uint32_t *ccount_all,
                                      uint32_t *clb_all, unsigned long long *ties_d,
                                      cudaStream_t st, int64_t *nusers = nullptr,
-                                     int split = 1) {
+                                     int split = 1, int64_t ncols = 0) {
+  TcSide Pv = idx->Pt;   // a view: the same rows, possibly fewer of them
+  if (ncols > 0 && ncols < Pv.rows) Pv.rows = ncols;
   const int bs = 256;
   DevBuf bcu, bcq, bci, bcc, bcur;
   int32_t *cu, *cq, *ci;
@@ -1244,15 +1312,16 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
     RKR_CUDA(cudaMemsetAsync(hist_hi, 0, sizeof(uint32_t) * 2 * cnt, st));
   }
   {
-    ProfScope prof(clb_all ? (split ? "span:recount(bounds,split)" : "span:recount(bounds,single)")
-                           : "span:recount(exact)",
+    ProfScope prof(ncols > 0   ? "span:recount(prefix)"
+                   : clb_all ? (split ? "span:recount(bounds,split)" : "span:recount(bounds,single)")
+                             : "span:recount(exact)",
                    st, 0.0);
     if (n1 > 0)
-      RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, n1, cnt, sstart, slen, suser, sself, ths, hist,
+      RKR_TRY(tc_recount(idx, idx->Ut, Pv, n1, cnt, sstart, slen, suser, sself, ths, hist,
                          hist_hi, st, refined, split));
     if (n2 > 0) {
       int64_t ref2[2] = {0, 0};
-      RKR_TRY(tc_recount(idx, idx->Ut, idx->Pt, n2, cnt, sstart + off2, slen + off2,
+      RKR_TRY(tc_recount(idx, idx->Ut, Pv, n2, cnt, sstart + off2, slen + off2,
                          suser + off2, sself + off2, ths, hist, hist_hi, st, ref2, split, scol,
                          spos));
       refined[0] += ref2[0];
@@ -1305,6 +1374,91 @@ __global__ void k_drop_decided(int64_t n, const uint32_t *__restrict__ ccount,
                                const uint32_t *__restrict__ clb, int32_t *__restrict__ cu_fb) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n && cu_fb[i] >= 0 && ccount[i] == clb[i]) cu_fb[i] = -1;
+}
+
+static rkr_status count_valid(const int32_t *v, int64_t n, unsigned long long *out,
+                              cudaStream_t st) {
+  DevBuf b;
+  unsigned long long *d;
+  RKR_TRY(tmp_alloc(b, &d, 1, st));
+  RKR_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+  k_count_valid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, v, d);
+  note_launch();
+  RKR_CUDA(cudaMemcpyAsync(out, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return RKR_OK;
+}
+
+// Early termination over the norm-sorted items (tuning rc_prefix; Alg. 1 sorts P
+// by descending norm).  For the queries with many candidates still to recount,
+// every such candidate is first screened against the first m1 items only: its
+// certain count there is a lower bound of its count over P, and its possible
+// count there ranks how promising it is.  The query's most promising candidates
+// are recounted over all of P, the cap (k-th smallest count upper bound) is taken
+// again, and every other candidate whose prefix lower bound exceeds the cap is
+// dropped unrecounted: it cannot be among the k smallest ranks.  The rest go back
+// to the recount.  On return *h2 is the number of candidates still to recount.
+static rkr_status prefix_prune(const rkr_index *idx, const QueryCommon &qc, int qa, int qb,
+                               int64_t cnt, const int64_t *qoff_rel, const uint32_t *cursor,
+                               const int32_t *cq, const int32_t *qself, uint32_t *ccount,
+                               uint32_t *clb, int32_t *cu_fb, int64_t *recount_users,
+                               unsigned long long *h2, int64_t *rows, int64_t *pruned,
+                               cudaStream_t st) {
+  const int64_t m1 = idx->m / tuning().rc_prefix / 256 * 256;
+  if (m1 < 256 || m1 >= idx->m) return RKR_OK;
+  DevBuf b1, b2, b3, b4, b5;
+  int32_t *cu_pre, *cu_park;
+  uint32_t *hi1, *lo1;
+  unsigned long long *npre_d, npre = 0;
+  RKR_TRY(tmp_alloc(b1, &cu_pre, cnt, st));
+  RKR_TRY(tmp_alloc(b2, &cu_park, cnt, st));
+  RKR_TRY(tmp_alloc(b3, &hi1, cnt, st));
+  RKR_TRY(tmp_alloc(b4, &lo1, cnt, st));
+  RKR_TRY(tmp_alloc(b5, &npre_d, 1, st));
+  RKR_CUDA(cudaMemsetAsync(cu_pre, 0xff, sizeof(int32_t) * cnt, st));
+  RKR_CUDA(cudaMemsetAsync(cu_park, 0xff, sizeof(int32_t) * cnt, st));
+  RKR_CUDA(cudaMemsetAsync(hi1, 0xff, sizeof(uint32_t) * cnt, st));
+  RKR_CUDA(cudaMemsetAsync(lo1, 0, sizeof(uint32_t) * cnt, st));
+  RKR_CUDA(cudaMemsetAsync(npre_d, 0, sizeof(unsigned long long), st));
+  k_prefix_split<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, cu_fb, cu_pre, npre_d);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  RKR_CUDA(cudaMemcpyAsync(&npre, npre_d, sizeof(npre), cudaMemcpyDeviceToHost, st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  if (npre == 0) return RKR_OK;
+  *rows += (int64_t)npre;
+  // certain (lo1) and possible (hi1) counts over the prefix, single product
+  RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_pre, cq, qself, hi1, lo1, nullptr, st, nullptr,
+                             0, m1));
+  k_prefix_pick<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, cu_pre, hi1, lo1, clb,
+                                          cu_fb, cu_park);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  unsigned long long parked = 0, kept = 0, h = 0;
+  RKR_TRY(count_valid(cu_park, cnt, &parked, st));
+  RKR_TRY(count_valid(cu_fb, cnt, &h, st));
+  if (h > 0)  // the promising rows and the other queries' rows, over all of P
+    RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr, st,
+                               recount_users, tuning().rc_single_first ? 0 : 1));
+  {
+    const int prof_slot = prof_begin("k_recount_filter", st);
+    k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
+    k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
+                                              cu_park);
+    prof_end(prof_slot, st, 0.0);
+  }
+  note_launch();
+  note_launch();
+  k_drop_decided<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, ccount, clb, cu_fb);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  RKR_TRY(count_valid(cu_park, cnt, &kept, st));
+  *pruned += (int64_t)(parked - kept);
+  k_prefix_unpark<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_park, cu_fb);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  RKR_TRY(count_valid(cu_fb, cnt, h2, st));
+  return RKR_OK;
 }
 
 rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq, double c,
@@ -1685,6 +1839,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   int64_t fallback = 0, list_fp64 = 0, cut_total = 0;
   double err_ratio = 0.0, err_rel = 0.0;
   int64_t recount_users = 0, recount_open = 0, recount_split = 0, revived = 0;
+  int64_t prefix_rows = 0, prefix_pruned = 0;
   unsigned long long lstat_host_fb = 0;
   Plan plan;
   Timer t1(st);
@@ -1829,6 +1984,9 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
                                      st));
         return RKR_OK;
       };
+      if (!lp && tuning().rc_prefix > 0 && lstat_host_fb >= (unsigned long long)prefix_min_rows(1))
+        RKR_TRY(prefix_prune(idx, qc, qa, qb, cnt, qoff_rel, cursor, cq, qself, ccount, clb, cu_fb,
+                             &recount_users, &lstat_host_fb, &prefix_rows, &prefix_pruned, st));
       if (lstat_host_fb > 0) RKR_TRY(recount_open_candidates(lstat_host_fb));
       if (lp && lp->certify && cut_total > 0) {
         // exact fallback: cut candidates that could still be among the k best
@@ -1883,6 +2041,8 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
     stats->max_screen_err_ratio = err_ratio;
     if (lp) stats->candidates = total - cut_total + revived;  // left by the learned cut
     stats->learned_revived = revived;
+    stats->prefix_rows = prefix_rows;
+    stats->prefix_pruned = prefix_pruned;
     stats->wide_queries = wide;
     stats->deep_queries = (int32_t)plan.deep.size();
     stats->ms_theta = ms_theta;

@@ -474,10 +474,13 @@ struct EpiXT {
 // Group each user's tail list by the exact-grid column of the screened score,
 // col(v) = #{j : x_j <= v} in 0..G (counting sort), and record the column
 // offsets and the largest screen bound of the entries.  One CTA per user;
-// overflowed lists are left as they are and marked unusable.
-constexpr int kGroupThreads = 1024;
-constexpr int kGroupPer = kListCapMax / kGroupThreads;  // list entries per thread
-static_assert(kGroupPer * kGroupThreads == kListCapMax, "list capacity");
+// overflowed lists are left as they are and marked unusable.  Each thread keeps
+// kGroupPer entries in registers (64 registers a thread): lists of up to
+// kGroupShort entries run in CTAs of 512 threads, two resident per SM so that one
+// user's list loads overlap another's counting; longer lists in CTAs of 1,024.
+constexpr int kGroupPer = 16;                            // list entries per thread
+constexpr int kGroupShort = 512 * kGroupPer;             // capacity of a 512-thread CTA
+static_assert(1024 * kGroupPer == kListCapMax, "list capacity");
 
 // j(theta) = #{i < tau : t_i <= theta} when it is known to lie in [jlo, jhi]:
 // the thresholds inside the bracket are compared in FP64 (no division).
@@ -488,56 +491,74 @@ __device__ __forceinline__ int exact_j_near(double theta, double fmin, double de
   return g;
 }
 
-// One block per user: (1) the exact count table XLO/XHI on the kXG-column grid
-// from the user's list (every item above x_0 is in it; each entry's interval
-// uses the screen bound of its item tile), (2) the list grouped by the
-// kListG-column list grid with column offsets, (3) the largest entry bound.
-// An overflowed list gives the trivial table XLO = 0, XHI = m.
-// Each thread loads all of its (at most kGroupPer) entries up front and keeps
-// them in registers, so a user's list is in flight at once and the grouping
-// can be written back in place after one barrier.
-__global__ void __launch_bounds__(kGroupThreads)
-    k_list_group(int64_t n, uint2 *__restrict__ list, const int64_t *__restrict__ loff,
-                 const uint32_t *__restrict__ lcap, const uint32_t *__restrict__ lcnt,
-                 const BinFP *__restrict__ lbin, const double *__restrict__ ldx, int G,
-                 const BinFP *__restrict__ xbin, const double *__restrict__ xg0,
-                 uint32_t *__restrict__ XLO, uint32_t *__restrict__ XHI, uint32_t mcount,
-                 const tc::RowBound *__restrict__ rowb, const tc::RowBound *__restrict__ tileb,
-                 int bn_shift, tc::Gacc gacc, float gcan, uint16_t *__restrict__ coff,
-                 float *__restrict__ bmax) {
-  extern __shared__ unsigned char lsm[];
+struct ListGroupArgs {
+  int64_t n;
+  uint2 *list;
+  const int64_t *loff;
+  const uint32_t *lcap, *lcnt;
+  const BinFP *lbin;
+  const double *ldx;
+  int G;
+  const BinFP *xbin;
+  const double *xg0;
+  uint32_t *XLO, *XHI;
+  uint32_t mcount;
+  const tc::RowBound *rowb, *tileb;
+  int bn_shift;
+  tc::Gacc gacc;
+  float gcan;
+  uint16_t *coff;
+  float *bmax;
+};
+
+template <int T>
+constexpr size_t list_group_smem(int G) {
+  return sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) + sizeof(uint32_t) * (T / 32) +
+         sizeof(float) * (T / 32) + sizeof(uint16_t) * T * kGroupPer;
+}
+
+// One user's list with T threads: (1) the exact count table XLO/XHI on the
+// kXG-column grid from the user's list (every item above x_0 is in it; each
+// entry's interval uses the screen bound of its item tile), (2) the list grouped
+// by the kListG-column list grid with column offsets, (3) the largest entry bound.
+// An overflowed list gives the trivial table XLO = 0, XHI = m.  The entries
+// (at most T * kGroupPer) are all loaded up front, so the grouping can be written
+// back in place after one barrier.
+template <int T>
+__device__ __forceinline__ void list_group_user(const ListGroupArgs &a, int64_t u,
+                                                unsigned char *lsm) {
+  const int G = a.G;
   uint32_t *cnt = (uint32_t *)lsm;                            // G + 2
   uint32_t *hlo = cnt + G + 2;                                // kXG + 1
   uint32_t *hhi = hlo + kXG + 1;                              // kXG + 1
-  uint32_t *wsum = hhi + kXG + 1;                             // kGroupThreads / 32
-  float *red = (float *)(wsum + kGroupThreads / 32);          // kGroupThreads / 32
-  uint16_t *cols = (uint16_t *)(red + kGroupThreads / 32);    // kListCapMax
-  const int64_t u = blockIdx.x;
-  const uint32_t L = lcnt[u];
-  uint16_t *co = coff + u * (G + 2);
-  if (L > lcap[u]) {  // overflow: the list is incomplete
-    if (threadIdx.x == 0) bmax[u] = INFINITY;
-    for (int c = threadIdx.x; c < kXG; c += blockDim.x) {
-      XLO[u * kXG + c] = 0u;
-      XHI[u * kXG + c] = mcount;
+  uint32_t *wsum = hhi + kXG + 1;                             // T / 32
+  float *red = (float *)(wsum + T / 32);                      // T / 32
+  uint16_t *cols = (uint16_t *)(red + T / 32);                // T * kGroupPer
+  const uint32_t L = a.lcnt[u];
+  uint16_t *co = a.coff + u * (G + 2);
+  if (L > a.lcap[u]) {  // overflow: the list is incomplete
+    if (threadIdx.x == 0) a.bmax[u] = INFINITY;
+    for (int c = threadIdx.x; c < kXG; c += T) {
+      a.XLO[u * kXG + c] = 0u;
+      a.XHI[u * kXG + c] = a.mcount;
     }
     return;
   }
-  for (int c = threadIdx.x; c < G + 2; c += blockDim.x) cnt[c] = 0;
-  for (int c = threadIdx.x; c <= kXG; c += blockDim.x) {
+  for (int c = threadIdx.x; c < G + 2; c += T) cnt[c] = 0;
+  for (int c = threadIdx.x; c <= kXG; c += T) {
     hlo[c] = 0;
     hhi[c] = 0;
   }
   __syncthreads();
-  uint2 *row = list + loff[u];
-  const BinFP lb = lbin[u], xb = xbin[u];
-  const double g0 = xg0[u], dx = ldx[u];
-  const tc::RowBound ru = rowb[u];
+  uint2 *row = a.list + a.loff[u];
+  const BinFP lb = a.lbin[u], xb = a.xbin[u];
+  const double g0 = a.xg0[u], dx = a.ldx[u];
+  const tc::RowBound ru = a.rowb[u];
   float bm = 0.0f;
   uint2 ent[kGroupPer];
 #pragma unroll
   for (int k = 0; k < kGroupPer; ++k) {
-    const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
+    const uint32_t i = threadIdx.x + (uint32_t)k * T;
     if (i < L) ent[k] = row[i];
   }
   // Column c = #{x_j <= v} of the list grid x_j = g0 + j dx.  The FP32 column
@@ -567,11 +588,11 @@ __global__ void __launch_bounds__(kGroupThreads)
   };
 #pragma unroll
   for (int k = 0; k < kGroupPer; ++k) {
-    const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
+    const uint32_t i = threadIdx.x + (uint32_t)k * T;
     if (i >= L) break;
     const uint2 e = ent[k];
     const float v = __uint_as_float(e.y);
-    const float b = tc::screen_bound_tc(ru, tileb[e.x >> bn_shift], gacc, gcan);
+    const float b = tc::screen_bound_tc(ru, a.tileb[e.x >> a.bn_shift], a.gacc, a.gcan);
     bm = fmaxf(bm, b);
     int clo, chi;
     bin_interval(xb, g0, kXG, __fsub_rd(v, b), __fadd_ru(v, b), clo, chi);
@@ -606,17 +627,17 @@ __global__ void __launch_bounds__(kGroupThreads)
       const int c = 1 + lane * kPer + t;
       rl += hlo[c];
       rh += hhi[c];
-      XLO[u * kXG + (c - 1)] = rl;
-      XHI[u * kXG + (c - 1)] = rh;
+      a.XLO[u * kXG + (c - 1)] = rl;
+      a.XHI[u * kXG + (c - 1)] = rh;
     }
     if (lane == 0) {
       float m2 = 0.0f;
-      for (int w = 0; w < kGroupThreads / 32; ++w) m2 = fmaxf(m2, red[w]);
-      bmax[u] = m2;
+      for (int w = 0; w < T / 32; ++w) m2 = fmaxf(m2, red[w]);
+      a.bmax[u] = m2;
     }
   }
   // list grid: exclusive prefix over the G + 1 columns, a contiguous run per thread
-  const int per = (G + 1 + kGroupThreads - 1) / kGroupThreads;
+  const int per = (G + 1 + T - 1) / T;
   const int c0 = threadIdx.x * per, c1 = min(G + 1, c0 + per);
   uint32_t part = 0;
   for (int c = c0; c < c1; ++c) part += cnt[c];
@@ -636,14 +657,40 @@ __global__ void __launch_bounds__(kGroupThreads)
     co[c] = (uint16_t)run;
     run += t;
   }
-  if (threadIdx.x == kGroupThreads - 1) co[G + 1] = (uint16_t)run;
+  if (threadIdx.x == T - 1) co[G + 1] = (uint16_t)run;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kGroupPer; ++k) {
-    const uint32_t i = threadIdx.x + (uint32_t)k * kGroupThreads;
+    const uint32_t i = threadIdx.x + (uint32_t)k * T;
     if (i >= L) break;
     const uint32_t pos = atomicAdd(&cnt[cols[i]], 1u);
     row[pos] = ent[k];
+  }
+}
+
+// Lists of at most kGroupShort entries (and overflowed lists), one CTA per user;
+// the longer ones are appended to `longu` for k_list_group_long.
+__global__ void __launch_bounds__(512, 2) k_list_group(ListGroupArgs a, int32_t *longu,
+                                                      unsigned int *nlong) {
+  extern __shared__ unsigned char lsm[];
+  const int64_t u = blockIdx.x;
+  const uint32_t L = a.lcnt[u];
+  if (L > kGroupShort && L <= a.lcap[u]) {
+    if (threadIdx.x == 0) longu[atomicAdd(nlong, 1u)] = (int32_t)u;
+    return;
+  }
+  list_group_user<512>(a, u, lsm);
+}
+
+// The longer lists, in CTAs of 1,024 threads over the users k_list_group set aside.
+__global__ void __launch_bounds__(1024) k_list_group_long(ListGroupArgs a,
+                                                          const int32_t *longu,
+                                                          const unsigned int *nlong) {
+  extern __shared__ unsigned char lsm[];
+  const unsigned int cnt = *nlong;
+  for (unsigned int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    list_group_user<1024>(a, longu[i], lsm);
+    __syncthreads();   // the shared tables are reused by the next user
   }
 }
 
@@ -658,21 +705,32 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   if ((1 << bn_shift) != bn) return fail(RKR_EINTERNAL, "item tile width %d is not a power of two", bn);
   const int G = kListG;
   RKR_TRY(make_binfp_grid(idx, idx->xg0, idx->fmax, G, idx->pmax, idx->ldx, idx->lbin, st));
-  size_t sm = sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) +
-              sizeof(uint32_t) * (kGroupThreads / 32) + sizeof(float) * (kGroupThreads / 32) +
-              sizeof(uint16_t) * kListCapMax;
+  ListGroupArgs a;
+  a.n = idx->n; a.list = idx->xlist; a.loff = idx->xloff; a.lcap = idx->xlcap;
+  a.lcnt = idx->xlcnt; a.lbin = idx->lbin; a.ldx = idx->ldx; a.G = G; a.xbin = idx->xbin;
+  a.xg0 = idx->xg0; a.XLO = idx->XLO; a.XHI = idx->XHI; a.mcount = (uint32_t)idx->m;
+  a.rowb = idx->Ut.rb3; a.tileb = idx->ptile3; a.bn_shift = bn_shift;
+  a.gacc = tc_gacc(idx->Ut.kp, 1); a.gcan = tc_gcan(idx->d); a.coff = idx->xcoff;
+  a.bmax = idx->xbmax;
+  DevBuf bl, bc;
+  int32_t *longu;
+  unsigned int *nlong;
+  RKR_TRY(tmp_alloc(bl, &longu, idx->n, st));
+  RKR_TRY(tmp_alloc(bc, &nlong, 1, st));
+  RKR_CUDA(cudaMemsetAsync(nlong, 0, sizeof(unsigned int), st));
+  const size_t sm1 = list_group_smem<512>(G), sm2 = list_group_smem<1024>(G);
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sm));
+                                (int)sm1));
+  RKR_CUDA(cudaFuncSetAttribute(k_list_group_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm2));
   {
     const int prof_slot = prof_begin("k_list_group", st);
-    k_list_group<<<(unsigned)idx->n, kGroupThreads, sm, st>>>(
-        idx->n, idx->xlist, idx->xloff, idx->xlcap, idx->xlcnt, idx->lbin, idx->ldx, G,
-        idx->xbin, idx->xg0, idx->XLO, idx->XHI, (uint32_t)idx->m, idx->Ut.rb3, idx->ptile3,
-        bn_shift,
-        tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xcoff, idx->xbmax);
+    k_list_group<<<(unsigned)idx->n, 512, sm1, st>>>(a, longu, nlong);
+    note_launch();
+    k_list_group_long<<<(unsigned)sm_count(), 1024, sm2, st>>>(a, longu, nlong);
+    note_launch();
     prof_end(prof_slot, st, 0.0);
   }
-  note_launch();
   RKR_CUDA(cudaGetLastError());
   return RKR_OK;
 }
@@ -1915,7 +1973,7 @@ static rkr_status tc_recount_bn(const rkr_index *idx, const TcSide &Ut, const Tc
                                 const int32_t *seg_self, const double *ths, uint32_t *hist,
                                 uint32_t *hist_hi, cudaStream_t st, int64_t *refined, int split,
                                 const int32_t *self_col, const int32_t *self_pos) {
-  const int64_t m = idx->m;
+  const int64_t m = Pt.rows;   // all of P, or a prefix of the norm-sorted items
   if (nseg <= 0) return RKR_OK;
   TcSide A;
   A.rows = nseg;

@@ -6,7 +6,7 @@
 //   {"key": "n=...,m=...,d=...,nq=...,ksum=...,what=...", "rc_bn": 256,
 //    "rc_single_first": 1, "skip_level": 0, "cand_budget_log2": 26,
 //    "latency_ctas_per_sm": 0, "latency_bulk": 0, "screen_form": 1, "rc_seg_min": 0,
-//    "split_cat": 1, "ms": 123.4}
+//    "split_cat": 1, "rc_prefix": 4, "ms": 123.4}
 #include <stdio.h>
 #include <string.h>
 
@@ -20,7 +20,7 @@ namespace rkr {
 namespace {
 
 std::mutex g_tune_mu;
-rkr_tuning g_tune = {256, 1, 0, 26, 0, 0, 1, 0, 1};
+rkr_tuning g_tune = {256, 1, 0, 26, 0, 0, 1, 0, 1, 4};
 
 rkr_status check_tuning(const rkr_tuning &t) {
   if (t.rc_bn != 128 && t.rc_bn != 256) return fail(RKR_EINVAL, "rc_bn must be 128 or 256");
@@ -36,6 +36,8 @@ rkr_status check_tuning(const rkr_tuning &t) {
   if (t.rc_seg_min < 0 || t.rc_seg_min == 1 || t.rc_seg_min > kRecountSeg)
     return fail(RKR_EINVAL, "rc_seg_min is 0 or in [2, %d]", kRecountSeg);
   if (t.split_cat != 0 && t.split_cat != 1) return fail(RKR_EINVAL, "split_cat is 0 or 1");
+  if (t.rc_prefix != 0 && (t.rc_prefix < 2 || t.rc_prefix > 64))
+    return fail(RKR_EINVAL, "rc_prefix is 0 or in [2, 64]");
   return RKR_OK;
 }
 
@@ -64,7 +66,7 @@ bool cache_lookup(const char *path, const std::string &key, rkr_tuning *t, doubl
   const std::string pat = "\"key\": \"" + key + "\"";
   while (fgets(line, sizeof(line), f)) {
     if (!strstr(line, pat.c_str())) continue;
-    double v[10];
+    double v[11];
     if (field(line, "rc_bn", &v[0]) && field(line, "rc_single_first", &v[1]) &&
         field(line, "skip_level", &v[2]) && field(line, "cand_budget_log2", &v[3]) &&
         field(line, "latency_ctas_per_sm", &v[4]) && field(line, "ms", &v[5]) &&
@@ -72,9 +74,11 @@ bool cache_lookup(const char *path, const std::string &key, rkr_tuning *t, doubl
         field(line, "rc_seg_min", &v[8])) {
       // lines written before split_cat existed ran the concatenated form
       if (!field(line, "split_cat", &v[9])) v[9] = 1.0;
+      // and before rc_prefix existed, without the prefix pass
+      if (!field(line, "rc_prefix", &v[10])) v[10] = 0.0;
       rkr_tuning c = {(int32_t)v[0], (int32_t)v[1], (int32_t)v[2], (int32_t)v[3],
                       (int32_t)v[4], (int32_t)v[6], (int32_t)v[7], (int32_t)v[8],
-                      (int32_t)v[9]};
+                      (int32_t)v[9], (int32_t)v[10]};
       if (check_tuning(c) == RKR_OK) {
         *t = c;
         *ms = v[5];
@@ -95,9 +99,11 @@ rkr_status cache_append(const char *path, const std::string &key, const rkr_tuni
   fprintf(f,
           "{\"key\": \"%s\", \"rc_bn\": %d, \"rc_single_first\": %d, \"skip_level\": %d, "
           "\"cand_budget_log2\": %d, \"latency_ctas_per_sm\": %d, \"latency_bulk\": %d, "
-          "\"screen_form\": %d, \"rc_seg_min\": %d, \"split_cat\": %d, \"ms\": %.4f}\n",
+          "\"screen_form\": %d, \"rc_seg_min\": %d, \"split_cat\": %d, \"rc_prefix\": %d, "
+          "\"ms\": %.4f}\n",
           key.c_str(), t.rc_bn, t.rc_single_first, t.skip_level, t.cand_budget_log2,
-          t.latency_ctas_per_sm, t.latency_bulk, t.screen_form, t.rc_seg_min, t.split_cat, ms);
+          t.latency_ctas_per_sm, t.latency_bulk, t.screen_form, t.rc_seg_min, t.split_cat,
+          t.rc_prefix, ms);
   if (fclose(f) != 0) return fail(RKR_EINVAL, "cannot write %s", path);
   return RKR_OK;
 }
@@ -196,7 +202,7 @@ extern "C" rkr_status rkr_autotune(rkr_index *idx, const float *Q, int32_t nq, c
                   (!(what & 1) || bn != 256 || sf != 1 || sk != 0 || lc != 0 || lb != 0))
                 continue;
               grid.push_back({bn, sf, sk, before.cand_budget_log2, lc, lb, form,
-                              before.rc_seg_min, before.split_cat});
+                              before.rc_seg_min, before.split_cat, before.rc_prefix});
             }
   const size_t tot = (size_t)ksum;
   int32_t *users = nullptr, *ranks = nullptr, *icase = nullptr, *inc = nullptr;

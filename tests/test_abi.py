@@ -100,7 +100,8 @@ def test_tuning_fields_are_validated_without_a_gpu():
         for bad in (dict(rc_bn=64), dict(rc_single_first=2), dict(skip_level=31),
                     dict(cand_budget_log2=19), dict(latency_ctas_per_sm=-1),
                     dict(latency_bulk=2), dict(screen_form=3), dict(rc_seg_min=1),
-                    dict(rc_seg_min=33), dict(split_cat=2)):
+                    dict(rc_seg_min=33), dict(split_cat=2), dict(rc_prefix=1),
+                    dict(rc_prefix=65), dict(rc_prefix=-1)):
             with pytest.raises(pkg.RKRError):
                 pkg.rkr_tuning_set(**bad)
         pkg.rkr_tuning_set(rc_bn=128)

@@ -236,6 +236,42 @@ def test_recount_below_the_tail_lists(floor_rank):
     assert st.recounted > 0 and st.wide_queries > 0
 
 
+def test_prefix_prune_over_norm_sorted_items():
+    """Early termination over the norm-sorted items: tiny-norm and zero queries
+    make every user a recount candidate, so those queries take the prefix pass
+    (every candidate screened against the first m / p items, the most promising
+    recounted over all of P for the cap, the others dropped when their prefix
+    count already exceeds it).  The items lean towards one direction, so users'
+    counts at u.q = 0 spread from a few hundred to most of P.  Answers equal the
+    oracle's for every prefix length and with the pass switched off."""
+    rng = np.random.default_rng(5)
+    d = 48
+    lean = np.zeros(d, np.float32)
+    lean[0] = 0.5
+    U, P = _rows(rng, 6000, d), (_rows(rng, 5000, d) + lean).astype(np.float32)
+    Q = np.vstack([1e-3 * P[:4], np.zeros((1, d), np.float32), P[4:7], _rows(rng, 2, d)])
+    k = np.array([1, 10, 32, 4, 17, 5, 40, 8, 3, 21], dtype=np.int32)
+    before = rkr.rkr_tuning_get()
+    try:
+        ora, gpu = build_pair(U, P, 40, 6, 30, floor_rank=40)
+        ref = gpu.query_exact(Q, k)
+        for p in (0, 2, 4, 16):
+            rkr.rkr_tuning_set(rc_prefix=p)
+            st = check_exact(U, P, Q, k, gpu)
+            got = gpu.query_exact(Q, k)
+            assert (got[0] == ref[0]).all() and (got[1] == ref[1]).all(), p
+            if p == 0:
+                assert st.prefix_rows == 0 and st.prefix_pruned == 0
+                continue
+            assert st.prefix_rows >= 5 * 2048, p      # the five wide queries
+            if p == 2:
+                assert st.prefix_pruned > st.prefix_rows // 2, st.prefix_pruned
+            if p == 4:
+                assert st.prefix_pruned > 0
+    finally:
+        rkr.rkr_tuning_set(**before)
+
+
 @pytest.mark.parametrize("split_first", [1, 0])
 def test_recount_many_thresholds_per_user(split_first):
     """Forty tiny-norm queries make every user a candidate of each of them, so

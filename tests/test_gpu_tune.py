@@ -15,7 +15,7 @@ rkr = pytest.importorskip("paper_2504_13446_gb300")
 
 DEFAULT = dict(rc_bn=256, rc_single_first=1, skip_level=0, cand_budget_log2=26,
                latency_ctas_per_sm=0, latency_bulk=0, screen_form=1, rc_seg_min=0,
-               split_cat=1)
+               split_cat=1, rc_prefix=4)
 
 
 def _answers(idx, w):
@@ -38,7 +38,8 @@ def test_every_tuning_gives_the_same_answers(tmp_path):
                            dict(skip_level=9), dict(cand_budget_log2=20),
                            dict(latency_ctas_per_sm=2), dict(latency_bulk=1),
                            dict(screen_form=0), dict(screen_form=2), dict(rc_seg_min=2),
-                           dict(rc_seg_min=4, rc_single_first=0), dict(split_cat=0)):
+                           dict(rc_seg_min=4, rc_single_first=0), dict(split_cat=0),
+                           dict(rc_prefix=0), dict(rc_prefix=2)):
                 rkr.rkr_tuning_set(**{**DEFAULT, **fields})
                 got = _answers(idx, w)
                 for a, b in zip(got, ref):
