@@ -446,6 +446,28 @@ def learned_comparison(rkr, w, U, P, Q, pos, steps, idx=None):
         ms_cert.append(t_cert)
     recall, viol = recall_of(lr, loff, pr_)
     same_cert = bool((cu_ == pu_).all() and (cr_ == pr_).all())
+    # the network tabulated per user (rkr_pruner_invert): one lookup per candidate
+    G = 64
+    _, ms_invert = timed(lambda: net.invert(idx, Rp, G))
+    for _ in range(2):
+        idx.query_exact_learned(net, Rp, Q, k, keep, certify=False)
+    ms_tcut, ms_tcert = [], []
+    for _ in range(steps):
+        (tu_, tr_, toff_, tst), t_tc = timed(
+            lambda: idx.query_exact_learned(net, Rp, Q, k, keep, certify=False))
+        ms_tcut.append(t_tc)
+        (tcu, tcr, _, tcst), t_tk = timed(
+            lambda: idx.query_exact_learned(net, Rp, Q, k, keep, certify=True))
+        ms_tcert.append(t_tk)
+    t_recall, t_viol = recall_of(tr_, toff_, pr_)
+    table = {"grid_points": G, "ms_invert": ms_invert,
+             "ms_per_batch": {"learned_cut": statistics.median(ms_tcut),
+                              "learned_certified": statistics.median(ms_tcert)},
+             "recall_at_k": t_recall, "c_bound_violations": t_viol,
+             "certified_answers_equal_plain_exact": bool((tcu == pu_).all() and
+                                                         (tcr == pr_).all()),
+             "recounted_cut": tst.recounted}
+    net.invert(idx, Rp, 0)
     if own:
         idx.close()
     mp, mc, mk = (statistics.median(v) for v in (ms_plain, ms_cut, ms_cert))
@@ -460,6 +482,7 @@ def learned_comparison(rkr, w, U, P, Q, pos, steps, idx=None):
                        "revived_by_fallback": cst.learned_revived,
                        "recounted_plain": pst.recounted, "recounted_cut": lst.recounted,
                        "recounted_certified": cst.recounted},
+        "per_user_tables": table,
         "calibration_recall": {str(a): r for a, r in cal.items()},
         "training": {"queries": n_train, "samples": int(len(pu)), "epochs": epochs,
                      "batch": 4096, "final_loss": loss,

@@ -392,6 +392,29 @@ rkr_status rkr_rank_pairs(rkr_index *idx, const float *Q, int32_t nq, int64_t np
 rkr_status rkr_pair_features(rkr_index *idx, const float *R, const float *Q, int32_t nq,
                              int64_t npairs, const int32_t *pair_user, const int32_t *pair_query,
                              float *out_X, float *out_t, void *stream);
+/*
+ * rkr_pruner_invert: per-user tables of the trained network (not in the paper).
+ * The network's output y never increases with t = u.q / ||u||, so for each user
+ * it is one non-increasing function of t, tabulated once: tab[u][g] = y(x_u, t_g)
+ * on G points t_g = t_0 + g (t_{G-1} - t_0) / (G - 1) spanning [f_min(u), f_max(u)]
+ * / ||u||, the values t takes for the items of P.  Reading the same table the
+ * other way gives each user's score cut-off for any predicted log rank: y <= Y
+ * exactly where t is at least the table's crossing of Y.  While the pruner holds
+ * tables built for this index and this R (64 x d, host or device),
+ * rkr_query_exact_learned predicts each candidate by one lookup and a linear
+ * interpolation between the two grid points around its t (t outside the grid
+ * takes the end value) instead of a forward pass.  The pruner owns the tables
+ * (n x G FP32 and 8 bytes per user); G = 0 frees them; new weights
+ * (rkr_pruner_params, rkr_pruner_train) drop them.  G in [2, 1024], else
+ * RKR_EINVAL; the pruner must take 65 features.
+ */
+rkr_status rkr_pruner_invert(rkr_pruner *pr, rkr_index *idx, const float *R, int32_t G,
+                             void *stream);
+/* rkr_pruner_table: copies of the tables of rkr_pruner_invert: tab (n x G FP32,
+ * user-major) and grid (n x 2 FP32: t_0 and the step of each user's grid); host or
+ * device arrays.  RKR_EINVAL if the pruner holds no tables or they are not n x G. */
+rkr_status rkr_pruner_table(const rkr_pruner *pr, int64_t n, int32_t G, float *tab,
+                            float *grid);
 rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *R, const float *Q,
                                    int32_t nq, const int32_t *k, const int32_t *keep,
                                    int32_t certify, int32_t *out_users, int32_t *out_ranks,

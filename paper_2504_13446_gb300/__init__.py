@@ -167,6 +167,10 @@ def load() -> ctypes.CDLL:
         lib.rkr_query_exact_learned.restype = I32
         lib.rkr_query_exact_learned.argtypes = [V, V, V, V, I32, V, V, I32, V, V,
                                                 ctypes.POINTER(QueryStats), V]
+        lib.rkr_pruner_invert.restype = I32
+        lib.rkr_pruner_invert.argtypes = [V, V, V, I32, V]
+        lib.rkr_pruner_table.restype = I32
+        lib.rkr_pruner_table.argtypes = [V, I64, I32, V, V]
         lib.rkr_pruner_free.restype = None
         lib.rkr_pruner_free.argtypes = [V]
         lib.rkr_profile_start.restype = I32
@@ -661,6 +665,21 @@ class Pruner:
         _check(load().rkr_pruner_train(self._h, X.ctypes.data, t.ctypes.data, target.ctypes.data,
                                        len(t), epochs, batch, lr, seed, ctypes.byref(loss), None))
         return float(loss.value)
+
+    def invert(self, index, R, G: int = 64, stream=None) -> None:
+        """Tabulate the network per user of `index` (an Index) on G points of t
+        (rkr_pruner_invert); learned queries on that index with the same R then
+        predict by table lookup.  G = 0 drops the tables."""
+        R = np.ascontiguousarray(R, np.float32)
+        _check(load().rkr_pruner_invert(self._h, index._h, R.ctypes.data, int(G),
+                                        _stream(stream)))
+
+    def table(self, n: int, G: int):
+        """The tables of invert: (tab (n x G), grid (n x 2): t_0 and step per user)."""
+        tab = np.empty((n, G), np.float32)
+        grid = np.empty((n, 2), np.float32)
+        _check(load().rkr_pruner_table(self._h, n, G, tab.ctypes.data, grid.ctypes.data))
+        return tab, grid
 
     def save(self, path: str) -> None:
         """Write F, H and the weights to a file (rkr_pruner_save)."""

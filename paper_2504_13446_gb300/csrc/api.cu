@@ -26,6 +26,9 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static std::atomic<uint64_t> g_allocs{0};
 void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
+static std::atomic<uint64_t> g_index_serial{0};
+uint64_t next_index_serial() { return g_index_serial.fetch_add(1, std::memory_order_relaxed) + 1; }
+
 // Epilogue wait limit of the screens (rkr_set_wait_limit); negative = default.
 static std::atomic<int64_t> g_epi_wait{-1};
 uint32_t epi_wait_limit() {
@@ -826,17 +829,50 @@ rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *
   Free fk{keep_d, st};
   RKR_CUDA(cudaMemcpyAsync(keep_d, keeph.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
   RKR_TRY(user_features(idx, (const float *)vr.dev, Xu, st));
+  std::vector<float> Rh(64 * (size_t)idx->d);
+  RKR_CUDA(cudaMemcpyAsync(Rh.data(), vr.dev, sizeof(float) * Rh.size(), cudaMemcpyDeviceToHost,
+                           st));
+  RKR_CUDA(cudaStreamSynchronize(st));
+  const bool use_table = pruner_table_matches(pr, idx, Rh);
   OutView ou, orr;
   size_t tot = (size_t)off[nq];
   RKR_TRY(ou.init(out_users, sizeof(int32_t) * tot, st));
   RKR_TRY(orr.init(out_ranks, sizeof(int32_t) * tot, st));
   if (certify != 0 && certify != 1) return fail(RKR_EINVAL, "certify must be 0 or 1");
-  RKR_TRY(run_query_exact_learned(idx, qc, nq, pr, Xu, keep_d, certify, (int32_t *)ou.dev,
-                                  (int32_t *)orr.dev, stats, st));
+  RKR_TRY(run_query_exact_learned(idx, qc, nq, pr, Xu, keep_d, certify, use_table,
+                                  (int32_t *)ou.dev, (int32_t *)orr.dev, stats, st));
   RKR_TRY(ou.finish());
   RKR_TRY(orr.finish());
   RKR_CUDA(cudaStreamSynchronize(st));
   return RKR_OK;
+}
+
+rkr_status rkr_pruner_invert(rkr_pruner *pr, rkr_index *idx, const float *R, int32_t G,
+                             void *stream) {
+  g_err[0] = 0;
+  if (!pr || !idx) return fail(RKR_EINVAL, "null argument");
+  if (G != 0 && (G < 2 || G > 1024)) return fail(RKR_EINVAL, "G must be 0 or in [2, 1024]");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (G == 0) {
+    RKR_CUDA(cudaStreamSynchronize(st));
+    pruner_drop_table(pr);
+    return RKR_OK;
+  }
+  if (!R) return fail(RKR_EINVAL, "null argument");
+  if (pruner_features(pr) != 65) return fail(RKR_EINVAL, "the pruner must take 65 features");
+  RKR_TRY(check_device());
+  InView vr;
+  RKR_TRY(vr.init(R, sizeof(float) * 64 * idx->d, st));
+  std::vector<float> Rh(64 * (size_t)idx->d);
+  RKR_CUDA(cudaMemcpyAsync(Rh.data(), vr.dev, sizeof(float) * Rh.size(), cudaMemcpyDeviceToHost,
+                           st));
+  float *Xu = nullptr;
+  RKR_CUDA(pool_malloc_async(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
+  rkr_status s = user_features(idx, (const float *)vr.dev, Xu, st);
+  if (s == RKR_OK) s = pruner_build_table(pr, idx, Xu, Rh, G, st);
+  cudaFreeAsync(Xu, st);
+  RKR_CUDA(cudaStreamSynchronize(st));
+  return s;
 }
 
 rkr_status rkr_screen_scores(const float *U, int64_t n, const float *X, int64_t mx, int32_t d,

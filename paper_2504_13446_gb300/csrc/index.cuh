@@ -1,10 +1,17 @@
 // index.cuh -- the device-resident index behind rkr_index.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 #include "tcops.cuh"
 
+namespace rkr {
+uint64_t next_index_serial();   // a number no other index of this process has had
+}
+
 struct rkr_index {
+  uint64_t serial = rkr::next_index_serial();
   // sizes
   int64_t n = 0, m = 0;
   int d = 0;
@@ -244,6 +251,20 @@ rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t 
 int pruner_features(const rkr_pruner *pr);
 int pruner_hidden(const rkr_pruner *pr);
 
+// Per-user prediction tables of the pruner (rkr_pruner_invert): tab[u][g] =
+// y(x_u, t_g) on a grid of G values of t over [f_min, f_max] / ||u||, built from
+// the per-user features Xu of the projection R (64 x d, host copy Rh).
+rkr_status pruner_build_table(rkr_pruner *pr, const rkr_index *idx, const float *Xu,
+                              const std::vector<float> &Rh, int G, cudaStream_t st);
+void pruner_drop_table(rkr_pruner *pr);
+// True when the pruner holds tables built for this index and projection.
+bool pruner_table_matches(const rkr_pruner *pr, const rkr_index *idx,
+                          const std::vector<float> &Rh);
+// Predictions of B pairs (users uid, scores t) from the tables: linear
+// interpolation in t between the two grid points around it.
+rkr_status pruner_table_predict(const rkr_pruner *pr, const int32_t *uid, const float *t,
+                                int64_t B, float *y, cudaStream_t st);
+
 // Exact ranks of arbitrary (user, query) pairs of a staged batch (device arrays).
 rkr_status run_rank_pairs(const rkr_index *idx, const QueryCommon &qc, int nq, int64_t npairs,
                           const int32_t *cu, const int32_t *cq, int32_t *out_rank,
@@ -258,10 +279,11 @@ rkr_status pair_scores(const rkr_index *idx, const float *Qd, int64_t npairs, co
 // Exact query whose candidates still to be recounted over P are cut to
 // keep_d[q] per query (device array) by the pruner's predicted log ranks (an
 // approximate form of Def. 2; returned ranks stay exact).
+// With use_table the predictions come from the pruner's per-user tables.
 rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
                                    rkr_pruner *pr, const float *Xu, const int32_t *keep_d,
-                                   int certify, int32_t *users_d, int32_t *ranks_d,
-                                   rkr_query_stats *stats, cudaStream_t st);
+                                   int certify, bool use_table, int32_t *users_d,
+                                   int32_t *ranks_d, rkr_query_stats *stats, cudaStream_t st);
 
 rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
                            int32_t *users_d, int32_t *ranks_d, rkr_query_stats *stats,

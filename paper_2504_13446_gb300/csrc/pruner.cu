@@ -43,6 +43,14 @@ struct rkr_pruner {
                 *d2b = nullptr, *d2T = nullptr, *d1T = nullptr;
   float *z1 = nullptr, *z2 = nullptr, *y = nullptr, *dy = nullptr, *tb = nullptr, *d2 = nullptr,
         *d1 = nullptr, *tg = nullptr;
+  // per-user prediction tables (rkr_pruner_invert): tab[u * tabG + g] = y(x_u, t_g),
+  // tgrid[u] = (t_0, step) of user u's grid t_g = t_0 + g * step
+  float *tab = nullptr;
+  float2 *tgrid = nullptr;
+  int tabG = 0;
+  int64_t tabn = 0;
+  uint64_t tab_serial = 0;          // the index they were built for
+  std::vector<float> tab_R;         // and the feature projection
 };
 
 namespace rkr {
@@ -503,6 +511,132 @@ rkr_status pruner_forward_gather(rkr_pruner *pr, const float *Xu, const int32_t 
   return check_err(pr, st);
 }
 
+namespace {
+
+// User u's grid: t_g = t_0 + g * step over [f_min, f_max] / ||u||, the range of
+// t = u.q / ||u|| for q in P (||u|| in FP32, as the pair scores take it).
+__global__ void k_tab_grid(int64_t n, int d, const float *__restrict__ U,
+                           const double *__restrict__ fmin, const double *__restrict__ fmax,
+                           int G, float2 *__restrict__ tg) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const float *uu = U + u * d;
+  float nn = 0.0f;
+  for (int k = 0; k < d; ++k) nn = fmaf(uu[k], uu[k], nn);
+  const float nrm = sqrtf(nn);
+  float t0 = 0.0f, t1 = 0.0f;
+  if (nrm > 0.0f) {
+    t0 = (float)(fmin[u] / (double)nrm);
+    t1 = (float)(fmax[u] / (double)nrm);
+  }
+  tg[u] = make_float2(t0, t1 > t0 ? (t1 - t0) / (float)(G - 1) : 0.0f);
+}
+
+// Rows of the table for users [u0, u0 + nu): row r is user u0 + r / G at t_{r % G}.
+__global__ void k_tab_inputs(int64_t u0, int64_t nu, int G, const float2 *__restrict__ tg,
+                             int32_t *__restrict__ uid, float *__restrict__ t) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nu * G) return;
+  const int64_t u = u0 + r / G;
+  const int g = (int)(r % G);
+  const float2 gr = tg[u];
+  uid[r] = (int32_t)u;
+  t[r] = fmaf((float)g, gr.y, gr.x);
+}
+
+// y of pair i from user uid[i]'s table at t[i]: the grid coordinate x = (t - t_0) /
+// step clamped to [0, G - 1], then linear interpolation between its two grid
+// points.  The network never increases with t, so neither does the table nor its
+// interpolation, which lies between the two grid values around t.
+__global__ void k_tab_predict(int64_t B, const int32_t *__restrict__ uid,
+                              const float *__restrict__ t, const float *__restrict__ tab,
+                              const float2 *__restrict__ tg, int G, float *__restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const int64_t u = uid[i];
+  if (u < 0) { y[i] = 0.0f; return; }
+  const float2 gr = tg[u];
+  float x = gr.y > 0.0f ? (t[i] - gr.x) / gr.y : 0.0f;
+  x = fminf(fmaxf(x, 0.0f), (float)(G - 1));   // fmaxf also maps NaN to 0
+  const int j = min((int)x, G - 2);
+  const float f = x - (float)j;
+  const float *row = tab + u * G;
+  y[i] = fmaf(f, row[j + 1] - row[j], row[j]);
+}
+
+}  // namespace
+
+void pruner_drop_table(rkr_pruner *pr) {
+  if (pr->tab) cudaFree(pr->tab);
+  if (pr->tgrid) cudaFree(pr->tgrid);
+  pr->tab = nullptr;
+  pr->tgrid = nullptr;
+  pr->tabG = 0;
+  pr->tabn = 0;
+  pr->tab_serial = 0;
+  pr->tab_R.clear();
+}
+
+rkr_status pruner_build_table(rkr_pruner *pr, const rkr_index *idx, const float *Xu,
+                              const std::vector<float> &Rh, int G, cudaStream_t st) {
+  RKR_CUDA(cudaStreamSynchronize(st));
+  pruner_drop_table(pr);
+  if (G == 0) return RKR_OK;
+  const int64_t n = idx->n;
+  note_alloc();
+  RKR_CUDA(cudaMalloc((void **)&pr->tab, sizeof(float) * (size_t)n * G));
+  note_alloc();
+  cudaError_t e = cudaMalloc((void **)&pr->tgrid, sizeof(float2) * (size_t)n);
+  if (e != cudaSuccess) {
+    pruner_drop_table(pr);
+    return cuda_fail(e, "pruner table allocation");
+  }
+  k_tab_grid<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, idx->d, idx->U, idx->fmin,
+                                                          idx->fmax, G, pr->tgrid);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  // about four million table rows per forward call
+  const int64_t users = std::max<int64_t>(1, ((int64_t)1 << 22) / G);
+  const int64_t rows = std::min(users, n) * G;
+  DevBuf bu, bt;
+  int32_t *uid;
+  float *t;
+  RKR_TRY(tmp_alloc(bu, &uid, rows, st));
+  RKR_TRY(tmp_alloc(bt, &t, rows, st));
+  for (int64_t u0 = 0; u0 < n; u0 += users) {
+    const int64_t nu = std::min(users, n - u0);
+    k_tab_inputs<<<(unsigned)((nu * G + 255) / 256), 256, 0, st>>>(u0, nu, G, pr->tgrid, uid, t);
+    note_launch();
+    rkr_status s = pruner_forward_gather(pr, Xu, uid, t, nu * G, pr->tab + u0 * G, st);
+    if (s != RKR_OK) {
+      cudaStreamSynchronize(st);
+      pruner_drop_table(pr);
+      return s;
+    }
+  }
+  RKR_CUDA(cudaStreamSynchronize(st));
+  pr->tabG = G;
+  pr->tabn = n;
+  pr->tab_serial = idx->serial;
+  pr->tab_R = Rh;
+  return RKR_OK;
+}
+
+bool pruner_table_matches(const rkr_pruner *pr, const rkr_index *idx,
+                          const std::vector<float> &Rh) {
+  return pr->tab && pr->tabn == idx->n && pr->tab_serial == idx->serial && pr->tab_R == Rh;
+}
+
+rkr_status pruner_table_predict(const rkr_pruner *pr, const int32_t *uid, const float *t,
+                                int64_t B, float *y, cudaStream_t st) {
+  if (B <= 0) return RKR_OK;
+  k_tab_predict<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(B, uid, t, pr->tab, pr->tgrid,
+                                                             pr->tabG, y);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
+  return RKR_OK;
+}
+
 int pruner_features(const rkr_pruner *pr) { return pr->F; }
 int pruner_hidden(const rkr_pruner *pr) { return pr->H; }
 
@@ -570,7 +704,10 @@ rkr_status rkr_pruner_params(rkr_pruner *pr, int32_t set, float *params, int64_t
   cudaError_t e = set ? cudaMemcpy(pr->p, params, sizeof(float) * count, cudaMemcpyDefault)
                       : cudaMemcpy(params, pr->p, sizeof(float) * count, cudaMemcpyDefault);
   if (e != cudaSuccess) return cuda_fail(e, "rkr_pruner_params");
-  if (set) pr->step = 0;
+  if (set) {
+    pr->step = 0;
+    pruner_drop_table(pr);   // new weights: the tables no longer hold
+  }
   return RKR_OK;
 }
 
@@ -655,6 +792,7 @@ rkr_status rkr_pruner_train(rkr_pruner *pr, const float *X, const float *t, cons
   target = (const float *)vg.p;
   const int64_t B = std::min<int64_t>(batch, npairs);
   RKR_TRY(ensure_cap(pr, B, st));
+  pruner_drop_table(pr);   // training changes the weights the tables were built from
   int64_t *perm_d = nullptr;
   RKR_CUDA(pool_malloc_async(&perm_d, sizeof(int64_t) * npairs, st));
   std::vector<int64_t> perm(npairs);
@@ -696,9 +834,24 @@ rkr_status rkr_pruner_train(rkr_pruner *pr, const float *X, const float *t, cons
   return RKR_OK;
 }
 
+rkr_status rkr_pruner_table(const rkr_pruner *pr, int64_t n, int32_t G, float *tab,
+                            float *grid) {
+  using namespace rkr;
+  if (!pr || !tab || !grid) return fail(RKR_EINVAL, "null argument");
+  if (!pr->tab) return fail(RKR_EINVAL, "the pruner holds no tables (rkr_pruner_invert)");
+  if (n != pr->tabn || G != pr->tabG)
+    return fail(RKR_EINVAL, "the tables are %lld x %d", (long long)pr->tabn, pr->tabG);
+  cudaError_t e = cudaMemcpy(tab, pr->tab, sizeof(float) * (size_t)n * G, cudaMemcpyDefault);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(grid, pr->tgrid, sizeof(float2) * (size_t)n, cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(e, "rkr_pruner_table");
+  return RKR_OK;
+}
+
 void rkr_pruner_free(rkr_pruner *pr) {
   if (!pr) return;
   cudaDeviceSynchronize();
+  rkr::pruner_drop_table(pr);
   for (void *q : {(void *)pr->p, (void *)pr->g, (void *)pr->m, (void *)pr->v, (void *)pr->W1b,
                   (void *)pr->W2b, (void *)pr->W2t, (void *)pr->wt, (void *)pr->w3,
                   (void *)pr->err, (void *)pr->Xb, (void *)pr->XbT, (void *)pr->h1,

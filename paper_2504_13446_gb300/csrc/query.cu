@@ -138,27 +138,38 @@ __global__ void k_cutoff_fine(int nq, const uint32_t *__restrict__ fine,
 // --------------------------------------------------------- approximate path
 
 __global__ void k_resolve_approx(int64_t count, const int32_t *__restrict__ cu,
-                                 const int32_t *__restrict__ cq, const float *__restrict__ U,
-                                 const float *__restrict__ Q, int d,
+                                 const int32_t *__restrict__ cq, const float *__restrict__ cx,
+                                 const tc::RowBound *__restrict__ urb,
+                                 const tc::RowBound *__restrict__ qrb, tc::Gacc gacc, float gcan,
+                                 const float *__restrict__ U, const float *__restrict__ Q, int d,
                                  const double *__restrict__ fmin,
                                  const double *__restrict__ delta, const BinFP *__restrict__ bf,
                                  const uint32_t *__restrict__ N,
                                  int tau, uint32_t top, double *__restrict__ th,
                                  int32_t *__restrict__ cj, uint32_t *__restrict__ nlo,
-                                 uint32_t *__restrict__ nup) {
+                                 uint32_t *__restrict__ nup,
+                                 unsigned long long *__restrict__ nfp64) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   int64_t u = cu[i];
   if (u < 0) return;  // unused slot at the end of a query's segment
   int q = cq[i];
   const float *uu = U + u * d, *qq = Q + (int64_t)q * d;
-  // j from the compensated interval of u.q when both ends fall in one bin; the
-  // canonical u.q otherwise.  u.q itself is formed later, only for the users
-  // whose step-3 estimate is needed (NaN marks it as not yet formed).
-  double tlo, thi;
-  dot2_interval(uu, qq, d, tlo, thi);
-  int jlo, jhi;
-  bin_interval(bf[u], fmin[u], tau, __double2float_rd(tlo), __double2float_ru(thi), jlo, jhi);
+  // j from the screened score and its bound when both ends fall in one bin (no
+  // row is read); else from the compensated interval of u.q; else from the
+  // canonical u.q.  u.q itself is formed later, only for the users whose step-3
+  // estimate is needed (NaN marks it as not yet formed).
+  int jlo = 0, jhi = tau;
+  const float x = cx[i];
+  if (x == x) {   // NaN: the candidate has no screened score
+    const float b = tc::screen_bound_tc(urb[u], qrb[q], gacc, gcan);
+    bin_interval(bf[u], fmin[u], tau, __fsub_rd(x, b), __fadd_ru(x, b), jlo, jhi);
+  }
+  if (jlo != jhi) {
+    double tlo, thi;
+    dot2_interval(uu, qq, d, tlo, thi);
+    bin_interval(bf[u], fmin[u], tau, __double2float_rd(tlo), __double2float_ru(thi), jlo, jhi);
+  }
   int j;
   if (jlo == jhi) {
     j = jlo;
@@ -167,6 +178,7 @@ __global__ void k_resolve_approx(int64_t count, const int32_t *__restrict__ cu,
     const double theta = canon_dot(uu, qq, d);
     j = exact_j(theta, fmin[u], delta[u], tau);
     th[i] = theta;
+    atomicAdd(nfp64, 1ull);
   }
   cj[i] = j;
   nlo[i] = j < tau ? N[u * tau + j] : 0u;
@@ -180,6 +192,7 @@ struct ApproxCand {
   const int32_t *j;
   const float *U, *Q;  // rows, for forming u.q on demand
   int d;
+  unsigned long long *nfp64;   // canonical products formed (may be null)
 };
 
 constexpr int kSelThreads = 256;
@@ -219,6 +232,7 @@ __global__ void __launch_bounds__(kSelThreads)
     if (t != t) {  // not formed yet: the canonical u.q, kept for later calls
       t = canon_dot(C.U + (int64_t)u * C.d, qrow, C.d);
       th[i] = t;
+      if (C.nfp64) atomicAdd(C.nfp64, 1ull);
     }
     return interp_est(t, cj[i], nlo[i], nup[i], fmin[u], delta[u], tau, s);
   };
@@ -499,7 +513,8 @@ inline DeepGrid deep_grid(const rkr_index *idx) {
 // own bound, an FP32 dot product with its bound, or canonically.  Candidates below x_0 (or with an overflowed list) are
 // passed on, unchanged, in cu_fb for the recount screen; others get -1 there.
 __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
-                            const int32_t *__restrict__ cq, const float *__restrict__ U,
+                            const int32_t *__restrict__ cq, const float *__restrict__ cx,
+                            const tc::RowBound *__restrict__ qrb, const float *__restrict__ U,
                             const float *__restrict__ unrm, const float *__restrict__ Q,
                             const float *__restrict__ Ps, const float *__restrict__ pnrm_s, int d,
                             const uint2 *__restrict__ xlist,
@@ -526,28 +541,58 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   }
   const float *uu = U + u * d;
   const float *qq = Q + (int64_t)cq[i] * d;
-  // u.q as an interval [tlo, thi] from the compensated product; the canonical
-  // value is formed only where the interval cannot settle a comparison
-  double tlo, thi;
-  dot2_interval(uu, qq, d, tlo, thi);
-  double theta = 0.0;
-  bool exact = false;
-  const uint32_t L = xlcnt[u];
-  if (L <= xlcap[u] && tlo < xg0[u] && thi >= xg0[u]) {
-    theta = canon_dot(uu, qq, d);
-    tlo = thi = theta;
-    exact = true;
+  // u.q as an interval [tlo, thi], tightened only where a comparison needs it:
+  // first the candidate's screened score and its bound (no row is read), then
+  // the compensated product, then the canonical value
+  double tlo = -INFINITY, thi = INFINITY;
+  int state = 1;   // 0: screened interval, 1: compensated, 2: canonical
+  const float sx = cx ? cx[i] : __int_as_float(0x7fffffff);
+  if (sx == sx) {
+    const float b = tc::screen_bound_tc(rb3[u], qrb[cq[i]], gacc, gcan);
+    tlo = (double)__fsub_rd(sx, b);
+    thi = (double)__fadd_ru(sx, b);
+    state = 0;
+  } else {
+    dot2_interval(uu, qq, d, tlo, thi);
   }
-  if (L > xlcap[u] || thi < xg0[u]) {
+  double theta = 0.0;
+  auto tighten = [&]() {
+    if (state == 0) {
+      dot2_interval(uu, qq, d, tlo, thi);
+      state = 1;
+    } else {
+      theta = canon_dot(uu, qq, d);
+      tlo = thi = theta;
+      state = 2;
+      atomicAdd(&stat[4], 1ull);
+    }
+  };
+  const uint32_t L = xlcnt[u];
+  const double x0 = xg0[u];
+  while (state < 2 && L <= xlcap[u] && tlo < x0 && thi >= x0) tighten();
+  if (L > xlcap[u] || thi < x0) {
     // bounds from the exact count table at the bins of both ends of u.q
-    const int jl = exact_j(tlo, xg0[u], xdx[u], GX), jh = exact_j(thi, xg0[u], xdx[u], GX);
+    int jl = exact_j(tlo, x0, xdx[u], GX), jh = exact_j(thi, x0, xdx[u], GX);
+    const int G2 = deep.dg;
+    const bool below = G2 > 0 && thi < x0;
+    int kl = 0, kh = 0;
+    if (below) {
+      kl = exact_j(tlo, deep.yg0[u], deep.ydx[u], G2);
+      kh = exact_j(thi, deep.yg0[u], deep.ydx[u], G2);
+    }
+    if (state == 0 && (jl != jh || kl != kh)) {   // as tight as the compensated product gives
+      tighten();
+      jl = exact_j(tlo, x0, xdx[u], GX);
+      jh = exact_j(thi, x0, xdx[u], GX);
+      if (below) {
+        kl = exact_j(tlo, deep.yg0[u], deep.ydx[u], G2);
+        kh = exact_j(thi, deep.yg0[u], deep.ydx[u], G2);
+      }
+    }
     uint32_t ub = jl >= 1 ? XHI[u * GX + jl - 1] : mtop;
     uint32_t lb = jh < GX ? XLO[u * GX + jh] : 0u;
-    if (deep.dg > 0 && thi < xg0[u]) {
+    if (below) {
       // below x_0: the deep grid's counts at y_{kl - 1} <= tlo and y_{kh} > thi
-      const int G2 = deep.dg;
-      const int kl = exact_j(tlo, deep.yg0[u], deep.ydx[u], G2);
-      const int kh = exact_j(thi, deep.yg0[u], deep.ydx[u], G2);
       if (kl >= 1) ub = min(ub, deep.DHI[u * G2 + kl - 1]);
       if (kh < G2) lb = max(lb, deep.DLO[u * G2 + kh]);
     }
@@ -577,17 +622,18 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
     const float b = tc::screen_bound_tc(ru, ptile[p / pbn], gacc, gcan);
     if ((double)__fsub_rd(v, b) > thi) { ++above; continue; }
     if ((double)__fadd_ru(v, b) <= tlo) continue;
+    if (state == 0) {   // the screened interval of u.q cannot place it: compensate, look again
+      tighten();
+      --e;
+      continue;
+    }
     const float *pp = Ps + (int64_t)p * d;
     double slo, shi;
     dot2_interval(uu, pp, d, slo, shi);
     if (slo > thi) { ++above; continue; }
     if (shi <= tlo) continue;
     atomicAdd(&stat[1], 1ull);
-    if (!exact) {
-      theta = canon_dot(uu, qq, d);
-      tlo = thi = theta;
-      exact = true;
-    }
+    if (state < 2) tighten();   // the canonical u.q
     const double sc = canon_dot(uu, pp, d);
     if (sc > theta) ++above;
     // screen error of this pair against its canonical score: relative to the
@@ -602,11 +648,14 @@ __global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
   clb[i] = above;
 }
 
+// Threads of the per-query filters: a query may have a million candidates.
+constexpr int kFilterThreads = 512;
+
 // Per query: cap = k-th smallest of (exact count, or upper bound for candidates
 // still to be recounted).  A candidate whose lower bound exceeds the cap cannot
 // be among the k smallest ranks: it is dropped from the recount and given the
 // largest key.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFilterThreads)
     k_recount_filter(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
                      const int32_t *__restrict__ kq, uint32_t *__restrict__ ccount,
                      const uint32_t *__restrict__ clb, int32_t *__restrict__ cu_fb) {
@@ -663,7 +712,7 @@ __global__ void __launch_bounds__(256)
 // count over the prefix (a subset of P); the prefix_pick_rows(k) rows with the
 // smallest possible prefix counts (ties included) stay in cu_fb for a recount
 // over all of P, the others are parked in cu_park until the cap is known.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFilterThreads)
     k_prefix_pick(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
                   const int32_t *__restrict__ kq, const int32_t *__restrict__ cu_pre,
                   const uint32_t *__restrict__ hi1, const uint32_t *__restrict__ lo1,
@@ -827,14 +876,16 @@ __global__ void k_list_fine(SkimList L, const uint32_t *__restrict__ jj,
 }
 
 // Pass 2 on the list: entries of queries [qa, qb) whose lower bound may reach
-// the query's refined cap, appended to the query's candidate segment.
+// the query's refined cap, appended to the query's candidate segment with their
+// screened score (its bound settles most later decisions about u.q).
 __global__ void k_list_emit(SkimList L, const uint32_t *__restrict__ jj,
                             const uint32_t *__restrict__ lv, int qa, int qb,
                             const int32_t *__restrict__ lstar, int lskip,
                             const uint32_t *__restrict__ cap, const uint32_t *__restrict__ tlo,
                             int tau, const int64_t *__restrict__ qoff,
                             uint32_t *__restrict__ qcursor, int32_t *__restrict__ cand_u,
-                            int32_t *__restrict__ cand_q, int *__restrict__ ovf) {
+                            int32_t *__restrict__ cand_q, float *__restrict__ cand_x,
+                            int *__restrict__ ovf) {
   int64_t e;
   if (!list_entry(L, e)) return;
   const int q = L.q[e];
@@ -853,6 +904,7 @@ __global__ void k_list_emit(SkimList L, const uint32_t *__restrict__ jj,
   }
   cand_u[at] = (int32_t)u;
   cand_q[at] = q;
+  cand_x[at] = L.x[e];
 }
 
 // Shared front half: passes 1 and 3 and the cutoffs; per-query candidate counts.
@@ -1116,7 +1168,8 @@ static rkr_status screen_plan(const rkr_index *idx, const QueryCommon &qc, int n
 static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, int qa, int qb,
                                   const Grid &g, const Plan &plan, const int32_t *lstar_d,
                                   const uint32_t *cap_d, const int64_t *qoff_d, uint32_t *cursor_d,
-                                  int32_t *cand_u, int32_t *cand_q, cudaStream_t st) {
+                                  int32_t *cand_u, int32_t *cand_q, float *cand_x,
+                                  cudaStream_t st) {
   TcSide sub = qc.Qt;
   sub.owned = false;
   sub.rows = qb - qa;
@@ -1145,7 +1198,7 @@ static rkr_status emit_candidates(const rkr_index *idx, const QueryCommon &qc, i
         const int prof_slot = prof_begin("k_list_emit", st);
         k_list_emit<<<list_grid(plan), 256, 0, st>>>(plan.list, plan.jj, plan.lv, qa, qb, lstar_d,
                                                      plan.lskip, cap_d, g.tlo, g.tau, qoff_d,
-                                                     cursor_d, cand_u, cand_q, flag + 1);
+                                                     cursor_d, cand_u, cand_q, cand_x, flag + 1);
         prof_end(prof_slot, st, 0.0);
       }
       note_launch();
@@ -1229,7 +1282,8 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
                                      const int32_t *qself, uint32_t *ccount_all,
                                      uint32_t *clb_all, unsigned long long *ties_d,
                                      cudaStream_t st, int64_t *nusers = nullptr,
-                                     int split = 1, int64_t ncols = 0) {
+                                     int split = 1, int64_t ncols = 0,
+                                     int64_t *ncanon = nullptr) {
   TcSide Pv = idx->Pt;   // a view: the same rows, possibly fewer of them
   if (ncols > 0 && ncols < Pv.rows) Pv.rows = ncols;
   const int bs = 256;
@@ -1254,6 +1308,7 @@ static rkr_status recount_candidates(const rkr_index *idx, const float *Qd, int6
   RKR_CUDA(cudaStreamSynchronize(st));
   const int64_t cnt = (int64_t)hc;
   if (cnt == 0) return RKR_OK;
+  if (ncanon) *ncanon += cnt;   // k_cand_theta forms each row's canonical u.q
   RKR_TRY(tmp_alloc(bcc, &ccount, cnt, st));
   int64_t Np2 = 1;
   while (Np2 < cnt) Np2 <<= 1;
@@ -1403,7 +1458,7 @@ static rkr_status prefix_prune(const rkr_index *idx, const QueryCommon &qc, int 
                                const int32_t *cq, const int32_t *qself, uint32_t *ccount,
                                uint32_t *clb, int32_t *cu_fb, int64_t *recount_users,
                                unsigned long long *h2, int64_t *rows, int64_t *pruned,
-                               cudaStream_t st) {
+                               int64_t *ncanon, cudaStream_t st) {
   const int64_t m1 = idx->m / tuning().rc_prefix / 256 * 256;
   if (m1 < 256 || m1 >= idx->m) return RKR_OK;
   DevBuf b1, b2, b3, b4, b5;
@@ -1429,8 +1484,8 @@ static rkr_status prefix_prune(const rkr_index *idx, const QueryCommon &qc, int 
   *rows += (int64_t)npre;
   // certain (lo1) and possible (hi1) counts over the prefix, single product
   RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_pre, cq, qself, hi1, lo1, nullptr, st, nullptr,
-                             0, m1));
-  k_prefix_pick<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, cu_pre, hi1, lo1, clb,
+                             0, m1, ncanon));
+  k_prefix_pick<<<qb - qa, kFilterThreads, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, cu_pre, hi1, lo1, clb,
                                           cu_fb, cu_park);
   note_launch();
   RKR_CUDA(cudaGetLastError());
@@ -1439,11 +1494,11 @@ static rkr_status prefix_prune(const rkr_index *idx, const QueryCommon &qc, int 
   RKR_TRY(count_valid(cu_fb, cnt, &h, st));
   if (h > 0)  // the promising rows and the other queries' rows, over all of P
     RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr, st,
-                               recount_users, tuning().rc_single_first ? 0 : 1));
+                               recount_users, tuning().rc_single_first ? 0 : 1, 0, ncanon));
   {
     const int prof_slot = prof_begin("k_recount_filter", st);
-    k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
-    k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
+    k_recount_filter<<<qb - qa, kFilterThreads, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
+    k_recount_filter<<<qb - qa, kFilterThreads, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb,
                                               cu_park);
     prof_end(prof_slot, st, 0.0);
   }
@@ -1472,10 +1527,13 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
   RKR_TRY(tmp_alloc(bl, &lstar_d, nq, st));
   RKR_TRY(tmp_alloc(bn, &ncand_d, nq, st));
   RKR_TRY(tmp_alloc(bcap, &cap_d, nq, st));
-  DevBuf bse;
+  DevBuf bse, bnf;
   int *sel_err;
+  unsigned long long *nfp64_d;
   RKR_TRY(tmp_alloc(bse, &sel_err, 1, st));
   RKR_CUDA(cudaMemsetAsync(sel_err, 0, sizeof(int), st));
+  RKR_TRY(tmp_alloc(bnf, &nfp64_d, 1, st));
+  RKR_CUDA(cudaMemsetAsync(nfp64_d, 0, sizeof(unsigned long long), st));
   Plan plan;
   Timer t1(st);
   const Grid grid{qc.bf,  idx->fmin, idx->tau, idx->JU, idx->JL, idx->nlev_a,
@@ -1495,11 +1553,14 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
   for (auto ch : chunk_queries(plan.ncand, candidate_budget())) {
     int qa = ch.first, qb = ch.second;
     int64_t cnt = qoff[qb] - qoff[qa];
-    DevBuf b1, b2, b3, b4, b5, b6, b7, b8;
+    DevBuf b1, b2, b3, b4, b5, b6, b7, b8, b9;
     int32_t *cu, *cq, *cj;
     uint32_t *cursor, *nlo, *nup;
     double *th;
+    float *cx;
     int64_t *qoff_rel;
+    RKR_TRY(tmp_alloc(b9, &cx, cnt, st));
+    RKR_CUDA(cudaMemsetAsync(cx, 0xff, sizeof(float) * std::max<int64_t>(cnt, 1), st));  // NaN
     RKR_TRY(tmp_alloc(b1, &cu, cnt, st));
     RKR_TRY(tmp_alloc(b2, &cq, cnt, st));
     RKR_TRY(tmp_alloc(b3, &cursor, nq, st));
@@ -1517,7 +1578,7 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     RKR_CUDA(cudaMemsetAsync(cu, 0xff, sizeof(int32_t) * std::max<int64_t>(cnt, 1), st));
     Timer t2(st);
     RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, plan, lstar_d, cap_d, qoff_rel, cursor, cu, cq,
-                            st));
+                            cx, st));
     ms_theta += t2.stop();
     {
       std::vector<uint32_t> hc(nq);
@@ -1531,8 +1592,9 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
       {
         const int prof_slot = prof_begin("k_resolve_approx", st);
         k_resolve_approx<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
-            cnt, cu, cq, idx->U, qc.Qd, idx->d, idx->fmin, idx->delta, qc.bf, idx->N, idx->tau,
-            (uint32_t)(idx->m * idx->s), th, cj, nlo, nup);
+            cnt, cu, cq, cx, idx->Ut.rb3, qc.Qt.rb3, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d),
+            idx->U, qc.Qd, idx->d, idx->fmin, idx->delta, qc.bf, idx->N, idx->tau,
+            (uint32_t)(idx->m * idx->s), th, cj, nlo, nup, nfp64_d);
         prof_end(prof_slot, st, 0.0);
         note_launch();
       }
@@ -1540,7 +1602,7 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
     }
     ms_res += t3.stop();
     Timer t4(st);
-    ApproxCand C{cu, nlo, nup, th, cj, idx->U, qc.Qd, idx->d};
+    ApproxCand C{cu, nlo, nup, th, cj, idx->U, qc.Qd, idx->d, nfp64_d};
     size_t sm = sizeof(SortEnt) * kMaxK;
     RKR_CUDA(cudaFuncSetAttribute(k_select_approx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
@@ -1565,7 +1627,10 @@ rkr_status run_query_approx(const rkr_index *idx, const QueryCommon &qc, int nq,
   if (stats) {
     stats->pairs = idx->n * (int64_t)nq;
     stats->candidates = total;
-    stats->fp64_dots = total;
+    unsigned long long nf = 0;
+    RKR_CUDA(cudaMemcpyAsync(&nf, nfp64_d, sizeof(nf), cudaMemcpyDeviceToHost, st));
+    RKR_CUDA(cudaStreamSynchronize(st));
+    stats->fp64_dots = (int64_t)nf;
     stats->near_ties = 0;
     stats->wide_queries = wide;
     stats->deep_queries = (int32_t)plan.deep.size();
@@ -1583,7 +1648,7 @@ rkr_status launch_select_approx(int qa, int nblocks, const int64_t *qoff, const 
                                 int32_t *users_d, uint32_t *nlo_d, uint32_t *nup_d, double *est_d,
                                 int32_t *case_d, int32_t *nc_d, int *err, cudaStream_t st,
                                 const rkr_index *idx) {
-  ApproxCand C{uid, nlo, nup, th, cj, idx->U, Qd, idx->d};
+  ApproxCand C{uid, nlo, nup, th, cj, idx->U, Qd, idx->d, nullptr};
   size_t sm = sizeof(SortEnt) * kMaxK;
   RKR_CUDA(cudaFuncSetAttribute(k_select_approx, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm));
@@ -1603,6 +1668,7 @@ struct LearnedPrune {
   const float *Xu;   // per-user features
   const int32_t *keep;  // candidates kept per query (device, nq)
   int certify;          // 1: exact fallback for cut candidates that could still matter
+  bool table;           // predictions from the pruner's per-user tables
 };
 
 constexpr int64_t kLearnedUncut = 32;
@@ -1763,9 +1829,9 @@ rkr_status run_query_exact(const rkr_index *idx, const QueryCommon &qc, int nq,
 
 rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, int nq,
                                    rkr_pruner *pr, const float *Xu, const int32_t *keep_d,
-                                   int certify, int32_t *users_d, int32_t *ranks_d,
-                                   rkr_query_stats *stats, cudaStream_t st) {
-  const LearnedPrune lp{pr, Xu, keep_d, certify};
+                                   int certify, bool use_table, int32_t *users_d,
+                                   int32_t *ranks_d, rkr_query_stats *stats, cudaStream_t st) {
+  const LearnedPrune lp{pr, Xu, keep_d, certify, use_table};
   return query_exact_core(idx, qc, nq, &lp, users_d, ranks_d, stats, st);
 }
 
@@ -1794,7 +1860,10 @@ static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const
   note_launch();
   RKR_CUDA(cudaGetLastError());
   RKR_TRY(pair_scores(idx, qc.Qd, nfb, fu, fq, tq, st));
-  {
+  if (lp->table) {   // one lookup per pair in the user's table
+    ProfScope prof("pruner_table", st);
+    RKR_TRY(pruner_table_predict(lp->pr, fu, tq, nfb, yc, st));
+  } else {
     ProfScope prof("pruner_forward", st);
     RKR_TRY(pruner_forward_gather(lp->pr, lp->Xu, fu, tq, nfb, yc, st));
   }
@@ -1831,7 +1900,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   RKR_CUDA(cudaMemsetAsync(ties_d, 0, 2 * sizeof(unsigned long long), st));
   DevBuf bls;
   unsigned long long *lstat;
-  RKR_TRY(tmp_alloc(bls, &lstat, 4, st));
+  RKR_TRY(tmp_alloc(bls, &lstat, 5, st));
   DevBuf bqs;
   int32_t *qself;
   RKR_TRY(tmp_alloc(bqs, &qself, nq, st));
@@ -1839,7 +1908,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   int64_t fallback = 0, list_fp64 = 0, cut_total = 0;
   double err_ratio = 0.0, err_rel = 0.0;
   int64_t recount_users = 0, recount_open = 0, recount_split = 0, revived = 0;
-  int64_t prefix_rows = 0, prefix_pruned = 0;
+  int64_t prefix_rows = 0, prefix_pruned = 0, canon_rows = 0, canon_theta = 0;
   unsigned long long lstat_host_fb = 0;
   Plan plan;
   Timer t1(st);
@@ -1855,10 +1924,13 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   for (auto ch : chunk_queries(plan.ncand, candidate_budget())) {
     int qa = ch.first, qb = ch.second;
     int64_t cnt = qoff[qb] - qoff[qa];
-    DevBuf b1, b2, b3, b4, b8;
+    DevBuf b1, b2, b3, b4, b8, b9;
     int32_t *cu, *cq;
     uint32_t *cursor, *ccount;
+    float *cx;
     int64_t *qoff_rel;
+    RKR_TRY(tmp_alloc(b9, &cx, cnt, st));
+    RKR_CUDA(cudaMemsetAsync(cx, 0xff, sizeof(float) * std::max<int64_t>(cnt, 1), st));  // NaN
     RKR_TRY(tmp_alloc(b1, &cu, cnt, st));
     RKR_TRY(tmp_alloc(b2, &cq, cnt, st));
     RKR_TRY(tmp_alloc(b3, &cursor, nq, st));
@@ -1872,7 +1944,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
     RKR_CUDA(cudaMemsetAsync(cu, 0xff, sizeof(int32_t) * std::max<int64_t>(cnt, 1), st));
     Timer t2(st);
     RKR_TRY(emit_candidates(idx, qc, qa, qb, grid, plan, lstar_d, cap_d, qoff_rel, cursor, cu, cq,
-                            st));
+                            cx, st));
     ms_theta += t2.stop();
     {
       std::vector<uint32_t> hc(nq);
@@ -1888,11 +1960,11 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       uint32_t *clb;
       RKR_TRY(tmp_alloc(bfb, &cu_fb, cnt, st));
       RKR_TRY(tmp_alloc(blb, &clb, cnt, st));
-      RKR_CUDA(cudaMemsetAsync(lstat, 0, 4 * sizeof(unsigned long long), st));
+      RKR_CUDA(cudaMemsetAsync(lstat, 0, 5 * sizeof(unsigned long long), st));
       {
         const int prof_slot = prof_begin("k_list_rank", st);
         k_list_rank<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(
-            cnt, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d,
+            cnt, cu, cq, cx, qc.Qt.rb3, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d,
             idx->xlist, idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
             idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
             idx->ldx, kListG,
@@ -1904,7 +1976,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       RKR_CUDA(cudaGetLastError());
       {
         const int prof_slot = prof_begin("k_recount_filter", st);
-        k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
+        k_recount_filter<<<qb - qa, kFilterThreads, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount, clb, cu_fb);
         prof_end(prof_slot, st, 0.0);
       }
       note_launch();
@@ -1920,8 +1992,9 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
                                  cudaMemcpyDeviceToHost, st));
         RKR_CUDA(cudaStreamSynchronize(st));
       }
-      unsigned long long ls[4] = {0, 0, 0, 0};
+      unsigned long long ls[5] = {0, 0, 0, 0, 0};
       RKR_CUDA(cudaMemcpyAsync(ls, lstat, sizeof(ls), cudaMemcpyDeviceToHost, st));
+      canon_theta += (int64_t)ls[4];
       RKR_CUDA(cudaStreamSynchronize(st));
       err_ratio = std::max(err_ratio, (double)u32_float((uint32_t)ls[2]));
       err_rel = std::max(err_rel, (double)u32_float((uint32_t)ls[3]));
@@ -1957,11 +2030,12 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
         for (int pass = tuning().rc_single_first ? 0 : 1; pass < 2 && h2 > 0; ++pass) {
           const bool first = pass == 0 || !tuning().rc_single_first;
           RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, clb, nullptr,
-                                     st, first ? &recount_users : nullptr, pass == 0 ? 0 : 1));
+                                     st, first ? &recount_users : nullptr, pass == 0 ? 0 : 1, 0,
+                                     &canon_rows));
           if (pass == 1) recount_split += (int64_t)h2;
           {
             const int prof_slot = prof_begin("k_recount_filter", st);
-            k_recount_filter<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount,
+            k_recount_filter<<<qb - qa, kFilterThreads, 0, st>>>(qa, qoff_rel, cursor, qc.kq_d, ccount,
                                                      clb, cu_fb);
             prof_end(prof_slot, st, 0.0);
           }
@@ -1981,12 +2055,13 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
         recount_open += (int64_t)h2;
         if (h2 > 0)
           RKR_TRY(recount_candidates(idx, qc.Qd, cnt, cu_fb, cq, qself, ccount, nullptr, ties_d,
-                                     st));
+                                     st, nullptr, 1, 0, &canon_rows));
         return RKR_OK;
       };
       if (!lp && tuning().rc_prefix > 0 && lstat_host_fb >= (unsigned long long)prefix_min_rows(1))
         RKR_TRY(prefix_prune(idx, qc, qa, qb, cnt, qoff_rel, cursor, cq, qself, ccount, clb, cu_fb,
-                             &recount_users, &lstat_host_fb, &prefix_rows, &prefix_pruned, st));
+                             &recount_users, &lstat_host_fb, &prefix_rows, &prefix_pruned,
+                             &canon_rows, st));
       if (lstat_host_fb > 0) RKR_TRY(recount_open_candidates(lstat_host_fb));
       if (lp && lp->certify && cut_total > 0) {
         // exact fallback: cut candidates that could still be among the k best
@@ -2031,7 +2106,9 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
   if (stats) {
     stats->pairs = idx->n * (int64_t)nq;
     stats->candidates = total;
-    stats->fp64_dots = 2 * total + (int64_t)tiesv[1] + list_fp64;
+    // canonical u.q of list-ranked candidates that needed it, of every recounted
+    // row, the near-tie items of the recount and the list entries next to u.q
+    stats->fp64_dots = canon_theta + canon_rows + (int64_t)tiesv[1] + list_fp64;
     stats->near_ties = (int64_t)tiesv[0];
     stats->recounted = fallback;
     stats->recount_users = recount_users;
@@ -2070,13 +2147,14 @@ rkr_status run_rank_pairs(const rkr_index *idx, const QueryCommon &qc, int nq, i
   RKR_TRY(tmp_alloc(bc, &ccount, npairs, st));
   RKR_TRY(tmp_alloc(bl, &clb, npairs, st));
   RKR_TRY(tmp_alloc(bf, &cu_fb, npairs, st));
-  RKR_TRY(tmp_alloc(bs, &lstat, 4, st));
+  RKR_TRY(tmp_alloc(bs, &lstat, 5, st));
   RKR_TRY(tmp_alloc(bt, &ties, 2, st));
-  RKR_CUDA(cudaMemsetAsync(lstat, 0, 4 * sizeof(unsigned long long), st));
+  RKR_CUDA(cudaMemsetAsync(lstat, 0, 5 * sizeof(unsigned long long), st));
   RKR_CUDA(cudaMemsetAsync(ties, 0, 2 * sizeof(unsigned long long), st));
   RKR_TRY(query_self(idx, qc.Qd, nq, qself, st));
   k_list_rank<<<(unsigned)((npairs + 127) / 128), 128, 0, st>>>(
-      npairs, cu, cq, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d, idx->xlist,
+      npairs, cu, cq, nullptr, nullptr, idx->U, idx->unrm, qc.Qd, idx->Ps, idx->pnrm_s, idx->d,
+      idx->xlist,
       idx->xloff, idx->xlcap, idx->xcoff, idx->xlcnt, idx->xbmax, idx->Ut.rb3, idx->ptile3,
       idx->ptile_bn, tc_gacc(idx->Ut.kp, 1), tc_gcan(idx->d), idx->xg0, idx->xdx, idx->xg,
       idx->ldx, kListG, idx->XLO, idx->XHI, (uint32_t)idx->m, ccount, clb, cu_fb, qself,

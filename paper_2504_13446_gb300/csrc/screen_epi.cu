@@ -473,14 +473,18 @@ struct EpiXT {
 
 // Group each user's tail list by the exact-grid column of the screened score,
 // col(v) = #{j : x_j <= v} in 0..G (counting sort), and record the column
-// offsets and the largest screen bound of the entries.  One CTA per user;
-// overflowed lists are left as they are and marked unusable.  Each thread keeps
-// kGroupPer entries in registers (64 registers a thread): lists of up to
-// kGroupShort entries run in CTAs of 512 threads, two resident per SM so that one
-// user's list loads overlap another's counting; longer lists in CTAs of 1,024.
-constexpr int kGroupPer = 16;                            // list entries per thread
-constexpr int kGroupShort = 512 * kGroupPer;             // capacity of a 512-thread CTA
-static_assert(1024 * kGroupPer == kListCapMax, "list capacity");
+// offsets and the largest screen bound of the entries.  One CTA of 512 threads
+// per user, two resident per SM so that one user's list loads overlap another's
+// counting; overflowed lists are left as they are and marked unusable.  A thread
+// keeps kGroupPer entries in registers (64 registers a thread), so that a list
+// is in flight at once and can be written back in place.  Lists longer than
+// 512 * kGroupPer entries are set aside and grouped by a second launch whose
+// threads also keep up to kGroupExt entries in shared memory (a larger shared
+// footprint for every CTA of the first launch would leave less room for L1).
+constexpr int kGroupThreads = 512;
+constexpr int kGroupPer = 16;                            // list entries per thread, registers
+constexpr int kGroupExt = 16;                            // and in shared memory
+static_assert(kGroupThreads * (kGroupPer + kGroupExt) == kListCapMax, "list capacity");
 
 // j(theta) = #{i < tau : t_i <= theta} when it is known to lie in [jlo, jhi]:
 // the thresholds inside the bracket are compared in FP64 (no division).
@@ -511,29 +515,32 @@ struct ListGroupArgs {
   float *bmax;
 };
 
-template <int T>
+template <bool EXT>
 constexpr size_t list_group_smem(int G) {
-  return sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) + sizeof(uint32_t) * (T / 32) +
-         sizeof(float) * (T / 32) + sizeof(uint16_t) * T * kGroupPer;
+  return sizeof(uint2) * (EXT ? kGroupThreads * kGroupExt : 0) +
+         sizeof(uint32_t) * (G + 2 + 2 * (kXG + 1)) + sizeof(uint32_t) * (kGroupThreads / 32) +
+         sizeof(float) * (kGroupThreads / 32) +
+         sizeof(uint16_t) * kGroupThreads * (kGroupPer + (EXT ? kGroupExt : 0));
 }
 
-// One user's list with T threads: (1) the exact count table XLO/XHI on the
-// kXG-column grid from the user's list (every item above x_0 is in it; each
-// entry's interval uses the screen bound of its item tile), (2) the list grouped
-// by the kListG-column list grid with column offsets, (3) the largest entry bound.
-// An overflowed list gives the trivial table XLO = 0, XHI = m.  The entries
-// (at most T * kGroupPer) are all loaded up front, so the grouping can be written
-// back in place after one barrier.
-template <int T>
+// One user's list: (1) the exact count table XLO/XHI on the kXG-column grid
+// from the user's list (every item above x_0 is in it; each entry's interval
+// uses the screen bound of its item tile), (2) the list grouped by the
+// kListG-column list grid with column offsets, (3) the largest entry bound.  An
+// overflowed list gives the trivial table XLO = 0, XHI = m.  All entries are
+// loaded up front, so the grouping can be written back in place after one barrier.
+template <bool EXT>
 __device__ __forceinline__ void list_group_user(const ListGroupArgs &a, int64_t u,
                                                 unsigned char *lsm) {
+  constexpr int T = kGroupThreads;
   const int G = a.G;
-  uint32_t *cnt = (uint32_t *)lsm;                            // G + 2
+  uint2 *ext = (uint2 *)lsm;                                  // T * kGroupExt (EXT)
+  uint32_t *cnt = (uint32_t *)(ext + (EXT ? T * kGroupExt : 0));   // G + 2
   uint32_t *hlo = cnt + G + 2;                                // kXG + 1
   uint32_t *hhi = hlo + kXG + 1;                              // kXG + 1
   uint32_t *wsum = hhi + kXG + 1;                             // T / 32
   float *red = (float *)(wsum + T / 32);                      // T / 32
-  uint16_t *cols = (uint16_t *)(red + T / 32);                // T * kGroupPer
+  uint16_t *cols = (uint16_t *)(red + T / 32);                // T * (kGroupPer [+ kGroupExt])
   const uint32_t L = a.lcnt[u];
   uint16_t *co = a.coff + u * (G + 2);
   if (L > a.lcap[u]) {  // overflow: the list is incomplete
@@ -561,6 +568,8 @@ __device__ __forceinline__ void list_group_user(const ListGroupArgs &a, int64_t 
     const uint32_t i = threadIdx.x + (uint32_t)k * T;
     if (i < L) ent[k] = row[i];
   }
+  if (EXT)
+    for (uint32_t i = T * kGroupPer + threadIdx.x; i < L; i += T) ext[i - T * kGroupPer] = row[i];
   // Column c = #{x_j <= v} of the list grid x_j = g0 + j dx.  The FP32 column
   // coordinate (v - f)(1/dx), f = fl(g0), taken with directed roundings, is
   // within e(v) = (|v - f| 2^-21 + |g0| 2^-23) / dx of (v - g0) / dx: the
@@ -586,11 +595,7 @@ __device__ __forceinline__ void list_group_user(const ListGroupArgs &a, int64_t 
     }
     return jlo == jhi ? jlo : exact_j_near((double)v, g0, dx, jlo, jhi);
   };
-#pragma unroll
-  for (int k = 0; k < kGroupPer; ++k) {
-    const uint32_t i = threadIdx.x + (uint32_t)k * T;
-    if (i >= L) break;
-    const uint2 e = ent[k];
+  auto count_entry = [&](uint32_t i, const uint2 e) {
     const float v = __uint_as_float(e.y);
     const float b = tc::screen_bound_tc(ru, a.tileb[e.x >> a.bn_shift], a.gacc, a.gcan);
     bm = fmaxf(bm, b);
@@ -603,7 +608,17 @@ __device__ __forceinline__ void list_group_user(const ListGroupArgs &a, int64_t 
     const int col = list_col(v);
     cols[i] = (uint16_t)col;
     atomicAdd(&cnt[col], 1u);
+  };
+#pragma unroll
+  for (int k = 0; k < kGroupPer; ++k) {
+    const uint32_t i = threadIdx.x + (uint32_t)k * T;
+    if (i >= L) break;
+    count_entry(i, ent[k]);
   }
+  // (each thread reads back only the shared entries it stored itself)
+  if (EXT)
+    for (uint32_t i = T * kGroupPer + threadIdx.x; i < L; i += T)
+      count_entry(i, ext[i - T * kGroupPer]);
   for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = bm;
@@ -666,30 +681,36 @@ __device__ __forceinline__ void list_group_user(const ListGroupArgs &a, int64_t 
     const uint32_t pos = atomicAdd(&cnt[cols[i]], 1u);
     row[pos] = ent[k];
   }
+  if (EXT)
+    for (uint32_t i = T * kGroupPer + threadIdx.x; i < L; i += T) {
+      const uint32_t pos = atomicAdd(&cnt[cols[i]], 1u);
+      row[pos] = ext[i - T * kGroupPer];
+    }
 }
 
-// Lists of at most kGroupShort entries (and overflowed lists), one CTA per user;
-// the longer ones are appended to `longu` for k_list_group_long.
-__global__ void __launch_bounds__(512, 2) k_list_group(ListGroupArgs a, int32_t *longu,
-                                                      unsigned int *nlong) {
-  extern __shared__ unsigned char lsm[];
+// Every user whose list fits the registers (and overflowed lists); the longer
+// ones are appended to longu for k_list_group_long.
+__global__ void __launch_bounds__(kGroupThreads, 2) k_list_group(ListGroupArgs a,
+                                                                int32_t *longu,
+                                                                unsigned int *nlong) {
+  extern __shared__ __align__(16) unsigned char lsm[];
   const int64_t u = blockIdx.x;
   const uint32_t L = a.lcnt[u];
-  if (L > kGroupShort && L <= a.lcap[u]) {
+  if (L > (uint32_t)(kGroupThreads * kGroupPer) && L <= a.lcap[u]) {
     if (threadIdx.x == 0) longu[atomicAdd(nlong, 1u)] = (int32_t)u;
     return;
   }
-  list_group_user<512>(a, u, lsm);
+  list_group_user<false>(a, u, lsm);
 }
 
-// The longer lists, in CTAs of 1,024 threads over the users k_list_group set aside.
-__global__ void __launch_bounds__(1024) k_list_group_long(ListGroupArgs a,
-                                                          const int32_t *longu,
-                                                          const unsigned int *nlong) {
-  extern __shared__ unsigned char lsm[];
+// The longer lists, persistent CTAs over the users k_list_group set aside.
+__global__ void __launch_bounds__(kGroupThreads, 2) k_list_group_long(ListGroupArgs a,
+                                                                     const int32_t *longu,
+                                                                     const unsigned int *nlong) {
+  extern __shared__ __align__(16) unsigned char lsm[];
   const unsigned int cnt = *nlong;
   for (unsigned int i = blockIdx.x; i < cnt; i += gridDim.x) {
-    list_group_user<1024>(a, longu[i], lsm);
+    list_group_user<true>(a, longu[i], lsm);
     __syncthreads();   // the shared tables are reused by the next user
   }
 }
@@ -718,16 +739,16 @@ rkr_status tc_sort_lists(rkr_index *idx, const tc::RowBound *tb, int bn, cudaStr
   RKR_TRY(tmp_alloc(bl, &longu, idx->n, st));
   RKR_TRY(tmp_alloc(bc, &nlong, 1, st));
   RKR_CUDA(cudaMemsetAsync(nlong, 0, sizeof(unsigned int), st));
-  const size_t sm1 = list_group_smem<512>(G), sm2 = list_group_smem<1024>(G);
+  const size_t sm1 = list_group_smem<false>(G), sm2 = list_group_smem<true>(G);
   RKR_CUDA(cudaFuncSetAttribute(k_list_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm1));
   RKR_CUDA(cudaFuncSetAttribute(k_list_group_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm2));
   {
     const int prof_slot = prof_begin("k_list_group", st);
-    k_list_group<<<(unsigned)idx->n, 512, sm1, st>>>(a, longu, nlong);
+    k_list_group<<<(unsigned)idx->n, kGroupThreads, sm1, st>>>(a, longu, nlong);
     note_launch();
-    k_list_group_long<<<(unsigned)sm_count(), 1024, sm2, st>>>(a, longu, nlong);
+    k_list_group_long<<<(unsigned)(2 * sm_count()), kGroupThreads, sm2, st>>>(a, longu, nlong);
     note_launch();
     prof_end(prof_slot, st, 0.0);
   }

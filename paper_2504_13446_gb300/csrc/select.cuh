@@ -9,14 +9,27 @@ namespace rkr {
 // (fn returns false for elements that do not take part).  MSB-first radix
 // select on 8-bit digits over an nbits-wide key.  Every thread of the block must
 // call it with the same arguments; the k-th smallest must exist.
+// A thread evaluates four keys before it adds any to the histogram, so that
+// their loads are in flight together: one CTA may have to walk a million keys.
 template <class F>
 __device__ uint64_t block_kth(int64_t cnt, uint64_t k, int nbits, F fn, uint32_t *hist,
                               uint64_t *bc) {
   uint64_t prefix = 0, mask = 0;
+  const int64_t T = blockDim.x;
   for (int shift = nbits - 8; shift >= 0; shift -= 8) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    int64_t i = threadIdx.x;
+    for (; i + 3 * T < cnt; i += 4 * T) {
+      uint64_t key[4];
+      bool in[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) in[j] = fn(i + j * T, key[j]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (in[j] && (key[j] & mask) == prefix) atomicAdd(&hist[(key[j] >> shift) & 255u], 1u);
+    }
+    for (; i < cnt; i += T) {
       uint64_t key;
       if (fn(i, key) && (key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
     }

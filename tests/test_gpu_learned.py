@@ -85,3 +85,60 @@ def test_learned_cut_returns_exact_ranks_with_high_recall():
     small[3] -= 1
     with pytest.raises(rkr.RKRError):
         gpu.query_exact_learned(net, Rp, eval_q, k_eval, small)
+
+
+def test_pruner_tables_match_the_network_and_cut_exactly():
+    """rkr_pruner_invert tabulates the network per user on a grid of t; each table
+    row never increases (the network is monotone in t by construction), its
+    entries are the network's outputs at the grid points, and a learned query
+    that predicts by table lookup returns exact ranks, and with the fallback the
+    exact answer.  New weights drop the tables."""
+    w = synth.make_workload("approx", n=8000, m=3000, nq=64)
+    rng = np.random.default_rng(21)
+    gpu = rkr.Index(w.U, w.P, tau=w.tau, omega=w.omega, s=w.s, exact_table=True, floor_rank=32)
+    Rp = (rng.standard_normal((64, w.d)) / np.sqrt(w.d)).astype(np.float32)
+    train_q, eval_q, k_eval = w.Q[:32], w.Q[32:], w.k[32:]
+    users_t, _, _, _ = gpu.query_exact(train_q, 200)
+    pu = np.concatenate([rng.integers(0, w.n, size=32 * 200), users_t]).astype(np.int32)
+    pq = np.concatenate([np.repeat(np.arange(32), 200), np.repeat(np.arange(32), 200)])
+    pq = pq.astype(np.int32)
+    r = gpu.rank_pairs(train_q, pu, pq)
+    X, t = gpu.pair_features(Rp, train_q, pu, pq)
+    net = rkr.Pruner(65, 256, seed=4)
+    net.train(X, t, np.log(r).astype(np.float32), epochs=10, batch=512, lr=2e-3, seed=5)
+    G = 32
+    net.invert(gpu, Rp, G)
+    tab, grid = net.table(w.n, G)
+    assert np.isfinite(tab).all() and (np.diff(tab, axis=1) <= 0).all()
+    fmin, fmax = gpu.export("fmin"), gpu.export("fmax")
+    unorm = np.linalg.norm(w.U.astype(np.float64), axis=1)
+    assert np.allclose(grid[:, 0], fmin / unorm, rtol=1e-5, atol=1e-6)
+    assert np.allclose(grid[:, 0] + (G - 1) * grid[:, 1].astype(np.float64), fmax / unorm,
+                       rtol=1e-4, atol=1e-5)
+    # entries are the network's outputs at the grid points of sampled users
+    su = rng.choice(w.n, 50, replace=False).astype(np.int32)
+    Xs, _ = gpu.pair_features(Rp, eval_q, su, np.zeros(len(su), np.int32))
+    tg = (grid[su, 0][:, None].astype(np.float64)
+          + np.arange(G)[None, :] * grid[su, 1][:, None].astype(np.float64)).astype(np.float32)
+    y = net.forward(np.repeat(Xs, G, axis=0), tg.reshape(-1)).reshape(len(su), G)
+    assert np.allclose(y, tab[su], rtol=1e-4, atol=1e-4), np.abs(y - tab[su]).max()
+    # learned queries by table lookup
+    plain_u, plain_r, off, _ = gpu.query_exact(eval_q, k_eval)
+    R = oracle.ranks(w.U, w.P, eval_q)
+    qid = np.repeat(np.arange(len(eval_q)), np.diff(off))
+    lu, lr, loff, st = gpu.query_exact_learned(net, Rp, eval_q, k_eval, 2 * k_eval,
+                                               certify=False)
+    assert (loff == off).all() and (lr == R[lu, qid]).all()
+    cu, cr, coff, _ = gpu.query_exact_learned(net, Rp, eval_q, k_eval, k_eval, certify=True)
+    assert (cu == plain_u).all() and (cr == plain_r).all()
+    # another projection does not match the tables: the network predicts, same answer
+    Rq = Rp * np.float32(1.5)
+    cu2, cr2, _, _ = gpu.query_exact_learned(net, Rq, eval_q, k_eval, k_eval, certify=True)
+    assert (cu2 == plain_u).all() and (cr2 == plain_r).all()
+    # new weights drop the tables; G = 0 is accepted with or without them
+    net.set_params(net.get_params())
+    with pytest.raises(rkr.RKRError):
+        net.table(w.n, G)
+    net.invert(gpu, Rp, 0)
+    with pytest.raises(rkr.RKRError):
+        net.invert(gpu, Rp, 1)
