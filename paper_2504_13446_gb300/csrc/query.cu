@@ -397,21 +397,39 @@ __global__ void k_cand_theta(int64_t count, const int32_t *__restrict__ cu,
 __global__ void k_segments(int64_t count, const uint64_t *__restrict__ key_hi, int seg_min,
                            unsigned long long *__restrict__ nseg, int64_t *__restrict__ seg_start,
                            int32_t *__restrict__ seg_len) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= count || key_hi[i] == ~0ull) return;
-  if (i > 0 && key_hi[i] == key_hi[i - 1]) return;
-  atomicAdd(&nseg[1], 1ull);   // distinct users
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool first = i < count && key_hi[i] != ~0ull && (i == 0 || key_hi[i] != key_hi[i - 1]);
   int64_t e = i + 1;
-  while (e < count && key_hi[e] == key_hi[i]) ++e;
-  const int64_t run = e - i;
-  if (seg_min == 0 || run < seg_min) {   // one row per threshold
+  if (first)
+    while (e < count && key_hi[e] == key_hi[i]) ++e;
+  const int64_t run = first ? e - i : 0;
+  const bool single = first && (seg_min == 0 || run < seg_min);
+  // one atomic per warp for the distinct users and for the one-threshold slots
+  // (a million candidates of one query would otherwise queue on one address)
+  const int lane = threadIdx.x & 31;
+  const unsigned nfirst = __popc(__ballot_sync(0xffffffffu, first));
+  unsigned long long mine = single ? (unsigned long long)run : 0ull, incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned long long tot = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31) {
+    if (tot) base = atomicAdd(&nseg[0], tot);
+    if (nfirst) atomicAdd(&nseg[1], (unsigned long long)nfirst);   // distinct users
+  }
+  base = __shfl_sync(0xffffffffu, base, 31);
+  if (single) {   // one row per threshold
+    const int64_t slot0 = (int64_t)(base + incl - mine);
     for (int64_t a = i; a < e; ++a) {
-      const int64_t slot = (int64_t)atomicAdd(&nseg[0], 1ull);
-      seg_start[slot] = a;
-      seg_len[slot] = 1;
+      seg_start[slot0 + (a - i)] = a;
+      seg_len[slot0 + (a - i)] = 1;
     }
     return;
   }
+  if (!first) return;
   // pieces of nearly equal length, at most kRecountSeg each
   const int64_t np = (run + kRecountSeg - 1) / kRecountSeg;
   for (int64_t p = 0; p < np; ++p) {
@@ -512,7 +530,9 @@ inline DeepGrid deep_grid(const rkr_index *idx) {
 // two columns within the screen bound of u.q are settled one by one, by their
 // own bound, an FP32 dot product with its bound, or canonically.  Candidates below x_0 (or with an overflowed list) are
 // passed on, unchanged, in cu_fb for the recount screen; others get -1 there.
-__global__ void k_list_rank(int64_t count, const int32_t *__restrict__ cu,
+// 64 registers a thread (eight 128-thread blocks per SM): the kernel waits on
+// scattered reads of each candidate's user data and list, so warps in flight matter.
+__global__ void __launch_bounds__(128, 8) k_list_rank(int64_t count, const int32_t *__restrict__ cu,
                             const int32_t *__restrict__ cq, const float *__restrict__ cx,
                             const tc::RowBound *__restrict__ qrb, const float *__restrict__ U,
                             const float *__restrict__ unrm, const float *__restrict__ Q,

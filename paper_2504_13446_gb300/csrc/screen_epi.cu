@@ -1524,7 +1524,9 @@ struct EpiSkim {
     int64_t u, fu;      // current row; row whose terms prb, pxs hold
     tc::RowBound prb;
   };
-  static constexpr size_t kSmem = 0;
+  // a 32 x 32 staging tile per epilogue warp, stored [column][lane]: a lane reads
+  // back its own emitted scores from shared memory, not from TMEM
+  static constexpr size_t kSmem = sizeof(float) * 8 * 32 * 32;
   int64_t nrows, ncols;
   const tc::RowBound *rowb, *tileb;
   tc::Gacc gacc;
@@ -1546,7 +1548,7 @@ struct EpiSkim {
       ts.xsb = __fsub_rd(ts.pxs, ts.b);
     }
   }
-  __device__ void chunk(char *, int, int ct, int, int col, uint32_t tm, const float (&v)[32],
+  __device__ void chunk(char *S, int, int ct, int, int col, uint32_t, const float (&v)[32],
                         Thread &ts) const {
     const int64_t c0 = (int64_t)ct * kSkimBN + col;
     // v <= xsb: lower bound above the skip level (NaN kept)
@@ -1570,29 +1572,20 @@ struct EpiSkim {
     base = __shfl_sync(0xffffffffu, base, 0);
     int64_t pos = (int64_t)base + incl - n;
     const int64_t rbase = (int64_t)blockIdx.x * L.rcap;
-    uint32_t any = __reduce_or_sync(0xffffffffu, pm);
-    while (any) {
-      int jj[4];
+    // each lane walks its own emitted columns, in column order
+    float *tile = (float *)S + ((threadIdx.x >> 5) - 2) * 32 * 32 + lane;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        jj[i] = any ? __ffs(any) - 1 : -1;
-        any &= any - 1u;
+    for (int j = 0; j < 32; ++j) tile[j * 32] = v[j];
+    uint32_t mine = pm;
+    while (mine) {
+      const int j = __ffs(mine) - 1;
+      mine &= mine - 1u;
+      if (pos < L.rcap) {  // entries past the region are dropped; cnt records them
+        L.u[rbase + pos] = (int32_t)ts.u;
+        L.q[rbase + pos] = (int32_t)(c0 + j);
+        L.x[rbase + pos] = tile[j * 32];
       }
-      float x[4];
-      tc::tmem_ld1x4(tm + (uint32_t)jj[0], tm + (uint32_t)(jj[1] < 0 ? jj[0] : jj[1]),
-                     tm + (uint32_t)(jj[2] < 0 ? jj[0] : jj[2]),
-                     tm + (uint32_t)(jj[3] < 0 ? jj[0] : jj[3]), x);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (jj[i] >= 0 && ((pm >> (jj[i] & 31)) & 1u)) {
-          if (pos < L.rcap) {  // entries past the region are dropped; cnt records them
-            L.u[rbase + pos] = (int32_t)ts.u;
-            L.q[rbase + pos] = (int32_t)(c0 + jj[i]);
-            L.x[rbase + pos] = x[i];
-          }
-          ++pos;
-        }
-      }
+      ++pos;
     }
   }
   __device__ void tile_end(char *, int, int, int, int, Thread &) const {}
