@@ -1802,6 +1802,31 @@ __global__ void k_pair_scores(int64_t npairs, const int32_t *__restrict__ cu,
   t[i] = nn > 0.0f ? s / sqrtf(nn) : 0.0f;
 }
 
+// t of compacted candidate pairs: x / ||u|| from the screened score x = cx[fi] of
+// the pair (the network needs no exact t), else the FP32 product of the rows.
+__global__ void k_pair_t(int64_t npairs, const int32_t *__restrict__ fu,
+                         const int32_t *__restrict__ fq, const int32_t *__restrict__ fi,
+                         const float *__restrict__ cx, const float *__restrict__ unrm,
+                         const float *__restrict__ U, const float *__restrict__ Q, int d,
+                         float *__restrict__ t) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  const int64_t u = fu[i];
+  const float x = cx[fi[i]];
+  const float nu = unrm[u];
+  if (x == x && nu > 0.0f) {
+    t[i] = x / nu;
+    return;
+  }
+  const float *uu = U + u * d, *qq = Q + (int64_t)fq[i] * d;
+  float s = 0.0f, nn = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    s = fmaf(uu[k], qq[k], s);
+    nn = fmaf(uu[k], uu[k], nn);
+  }
+  t[i] = nn > 0.0f ? s / sqrtf(nn) : 0.0f;
+}
+
 // Per user: R u / ||u|| (64 values) and log ||u||.
 __global__ void k_user_features(int64_t n, int d, const float *__restrict__ U,
                                 const float *__restrict__ R, float *__restrict__ Xu) {
@@ -1860,8 +1885,8 @@ rkr_status run_query_exact_learned(const rkr_index *idx, const QueryCommon &qc, 
 static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const LearnedPrune *lp,
                               int qa, int qb, int64_t cnt, int64_t nfb, const int64_t *qoff_rel,
                               const uint32_t *cursor, int32_t *cu, const int32_t *cq,
-                              int32_t *cu_fb, uint32_t *ccount, int32_t *cutu, int64_t *cut_total,
-                              cudaStream_t st) {
+                              const float *cx, int32_t *cu_fb, uint32_t *ccount, int32_t *cutu,
+                              int64_t *cut_total, cudaStream_t st) {
   DevBuf b1, b2, b3, b4, b5, b6, b7, b8;
   int32_t *fu, *fq, *fi;
   unsigned long long *cur, *ncut;
@@ -1879,7 +1904,12 @@ static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const
   k_compact<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, cu_fb, cq, cur, fu, fq, fi);
   note_launch();
   RKR_CUDA(cudaGetLastError());
-  RKR_TRY(pair_scores(idx, qc.Qd, nfb, fu, fq, tq, st));
+  // the network's input t = u.q / ||u||: from the candidate's screened score where
+  // it has one (no row is read), else from the rows
+  k_pair_t<<<(unsigned)((nfb + 127) / 128), 128, 0, st>>>(nfb, fu, fq, fi, cx, idx->unrm, idx->U,
+                                                          qc.Qd, idx->d, tq);
+  note_launch();
+  RKR_CUDA(cudaGetLastError());
   if (lp->table) {   // one lookup per pair in the user's table
     ProfScope prof("pruner_table", st);
     RKR_TRY(pruner_table_predict(lp->pr, fu, tq, nfb, yc, st));
@@ -2026,7 +2056,7 @@ static rkr_status query_exact_core(const rkr_index *idx, const QueryCommon &qc, 
       }
       if (lp && lstat_host_fb > 0) {  // learned cut of the candidates still to be recounted
         RKR_TRY(learned_cut(idx, qc, lp, qa, qb, cnt, (int64_t)lstat_host_fb, qoff_rel, cursor,
-                            cu, cq, cu_fb, ccount, cutu, &cut_total, st));
+                            cu, cq, cx, cu_fb, ccount, cutu, &cut_total, st));
         lstat_host_fb = 0;
         DevBuf bn4;
         unsigned long long *nfb4;
