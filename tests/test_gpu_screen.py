@@ -39,6 +39,21 @@ def test_screen_within_bound(n, mx, d, split):
     assert np.median(ratio) < 0.5
 
 
+@pytest.mark.parametrize("split", [False, True])
+def test_screen_within_bound_on_the_bench_items(split):
+    """The bound at the bench workload's width and length: 64 users of its
+    generator (Gaussian mixture, d = 200) against all 100,000 of its items,
+    every one of the 6.4M pairs within its bound of the canonical score."""
+    import synth
+    w = synth.make_workload("approx", n=64, nq=1)
+    s, b = rkr.rkr_screen_scores(w.U, w.P, split=split)
+    S = oracle.scores(w.U, w.P)
+    ratio = np.abs(s.astype(np.float64) - S) / b
+    assert np.isfinite(s).all() and (b > 0).all()
+    assert ratio.max() <= 1.0, f"max error/bound {ratio.max()}"
+    assert np.median(ratio) < 0.5
+
+
 @pytest.mark.parametrize("d", [200, 32, 72])
 def test_split_over_concatenated_operands_is_bit_identical(d):
     """The split product run as one pass over [hi | lo | hi] x [lo | hi | hi] (K = 3 K')
