@@ -460,9 +460,11 @@ def learned_comparison(rkr, w, U, P, Q, pos, steps, idx=None):
             lambda: idx.query_exact_learned(net, Rp, Q, k, keep, certify=True))
         ms_tcert.append(t_tk)
     t_recall, t_viol = recall_of(tr_, toff_, pr_)
+    mtc, mtk = statistics.median(ms_tcut), statistics.median(ms_tcert)
+    mplain = statistics.median(ms_plain)
     table = {"grid_points": G, "ms_invert": ms_invert,
-             "ms_per_batch": {"learned_cut": statistics.median(ms_tcut),
-                              "learned_certified": statistics.median(ms_tcert)},
+             "ms_per_batch": {"learned_cut": mtc, "learned_certified": mtk},
+             "speedup_over_plain_exact": {"cut": mplain / mtc, "certified": mplain / mtk},
              "recall_at_k": t_recall, "c_bound_violations": t_viol,
              "certified_answers_equal_plain_exact": bool((tcu == pu_).all() and
                                                          (tcr == pr_).all()),

@@ -817,23 +817,27 @@ rkr_status rkr_query_exact_learned(rkr_index *idx, rkr_pruner *pr, const float *
   RKR_TRY(stage_queries(idx, Q, nq, k, off, st, qs, qc));
   InView vr;
   RKR_TRY(vr.init(R, sizeof(float) * 64 * idx->d, st));
-  float *Xu = nullptr;
-  int32_t *keep_d = nullptr;
-  RKR_CUDA(pool_malloc_async(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
-  struct Free {
-    void *p;
-    cudaStream_t s;
-    ~Free() { cudaFreeAsync(p, s); }
-  } fr{Xu, st};
-  RKR_CUDA(pool_malloc_async(&keep_d, sizeof(int32_t) * nq, st));
-  Free fk{keep_d, st};
-  RKR_CUDA(cudaMemcpyAsync(keep_d, keeph.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
-  RKR_TRY(user_features(idx, (const float *)vr.dev, Xu, st));
   std::vector<float> Rh(64 * (size_t)idx->d);
   RKR_CUDA(cudaMemcpyAsync(Rh.data(), vr.dev, sizeof(float) * Rh.size(), cudaMemcpyDeviceToHost,
                            st));
   RKR_CUDA(cudaStreamSynchronize(st));
+  // with tables for this index and projection the features are not needed
   const bool use_table = pruner_table_matches(pr, idx, Rh);
+  float *Xu = nullptr;
+  int32_t *keep_d = nullptr;
+  struct Free {
+    void *p;
+    cudaStream_t s;
+    ~Free() {
+      if (p) cudaFreeAsync(p, s);
+    }
+  };
+  if (!use_table) RKR_CUDA(pool_malloc_async(&Xu, sizeof(float) * 65 * (size_t)idx->n, st));
+  Free fr{Xu, st};
+  RKR_CUDA(pool_malloc_async(&keep_d, sizeof(int32_t) * nq, st));
+  Free fk{keep_d, st};
+  RKR_CUDA(cudaMemcpyAsync(keep_d, keeph.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+  if (!use_table) RKR_TRY(user_features(idx, (const float *)vr.dev, Xu, st));
   OutView ou, orr;
   size_t tot = (size_t)off[nq];
   RKR_TRY(ou.init(out_users, sizeof(int32_t) * tot, st));

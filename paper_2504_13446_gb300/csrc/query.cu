@@ -1697,7 +1697,7 @@ constexpr int64_t kLearnedUncut = 32;
 // those whose predicted log rank y is above the keep[q]-th smallest prediction
 // are cut (fb = cu = -1, count = the largest key, so selection never takes them).
 // Candidates whose exact count is known already are not touched.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFilterThreads)
     k_learned_cut(int qa, const int64_t *__restrict__ qoff, const uint32_t *__restrict__ qcount,
                   const int32_t *__restrict__ keep_q, const float *__restrict__ y,
                   int32_t *__restrict__ fb_all, int32_t *__restrict__ cu_all,
@@ -1920,7 +1920,7 @@ static rkr_status learned_cut(const rkr_index *idx, const QueryCommon &qc, const
   k_scatter_y<<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(nfb, fi, yc, y);
   note_launch();
   // the uncut rule exists for the fallback's sake (n_users = 0 switches it off)
-  k_learned_cut<<<qb - qa, 256, 0, st>>>(qa, qoff_rel, cursor, lp->keep, y, cu_fb, cu, ccount,
+  k_learned_cut<<<qb - qa, kFilterThreads, 0, st>>>(qa, qoff_rel, cursor, lp->keep, y, cu_fb, cu, ccount,
                                          cutu, lp->certify ? idx->n : 0, ncut);
   note_launch();
   RKR_CUDA(cudaGetLastError());
